@@ -1,0 +1,426 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+No test here compares the oracle with itself: each checks a closed form, an
+identity the paper states (Sec. 3, Eqs. 11-19), an independent derivation, a
+brute-force dense computation, or a continuum limit.  All run on the CPU.
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+from scipy.special import erf
+
+import oracle
+from oracle import DIRICHLET as D, PERIODIC as P, UNSCREENED as U, SCREENED as S
+import workloads
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- helpers
+def exact_weights(order):
+    """Independent derivation: solve the Vandermonde moment system in exact rationals.
+
+    Symmetric stencil sum_{p=-m}^{m} c_p f(p) = f''(0) for f = x^{2q}, q = 0..m.
+    """
+    m = order // 2
+    # unknowns c_0, c_1..c_m (c_{-p} = c_p); equations for x^0, x^2, ..., x^{2m}
+    A = [[Fraction(0)] * (m + 1) for _ in range(m + 1)]
+    rhs = [Fraction(0)] * (m + 1)
+    for q in range(m + 1):
+        A[q][0] = Fraction(1 if q == 0 else 0)
+        for p in range(1, m + 1):
+            A[q][p] = Fraction(2 * p ** (2 * q))
+        rhs[q] = Fraction(2 if q == 1 else 0)
+    # Gauss-Jordan in rationals
+    n = m + 1
+    M = [row[:] + [rhs[i]] for i, row in enumerate(A)]
+    for c in range(n):
+        piv = next(r for r in range(c, n) if M[r][c] != 0)
+        M[c], M[piv] = M[piv], M[c]
+        inv = 1 / M[c][c]
+        M[c] = [v * inv for v in M[c]]
+        for r in range(n):
+            if r != c and M[r][c] != 0:
+                f = M[r][c]
+                M[r] = [a - f * b for a, b in zip(M[r], M[c])]
+    return [M[i][n] for i in range(n)]
+
+
+def stencil_matrix(n, h, bc, order):
+    """Sparse 1D second-derivative stencil built from the exact rational weights."""
+    w = [float(x) for x in exact_weights(order)]
+    m = order // 2
+    rows, cols, vals = [], [], []
+    for i in range(n):
+        for p in range(-m, m + 1):
+            j = i + p
+            if bc == P:
+                j %= n
+            elif not (0 <= j < n):
+                continue
+            rows.append(i)
+            cols.append(j)
+            vals.append(w[abs(p)] / h ** 2)
+    return sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
+
+
+def sparse_laplacian(plan):
+    L1, L2, L3 = (stencil_matrix(plan.n[a], plan.h[a], plan.bc[a], plan.fd_order) for a in range(3))
+    I1, I2, I3 = (sp.identity(k, format="csr") for k in plan.n)
+    return (sp.kron(I3, sp.kron(I2, L1)) + sp.kron(I3, sp.kron(L2, I1)) + sp.kron(L3, sp.kron(I2, I1))).tocsr()
+
+
+def small_orbitals(n, h, bc, n_orb, seed, kernel=U):
+    sysd = workloads.System(n=n, h=h, bc=bc, kernel=kernel, n_orb=n_orb, n_centres=3, seed=seed)
+    return workloads.make_orbitals(sysd), sysd
+
+
+# ---------------------------------------------------------------- P1: FD weights
+@pytest.mark.parametrize("order", [2, 4, 6, 8, 10, 12])
+def test_fd_weights_match_exact_rational_derivation(order):
+    w = oracle.fd_weights(order)
+    ex = exact_weights(order)
+    assert np.max(np.abs(w - np.array([float(x) for x in ex]))) < 1e-14
+
+
+def test_fd_weights_match_textbook_table():
+    with open(os.path.join(GOLDEN, "fd_weights_textbook.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            order, vals = line.split(":")
+            ref = np.array([float(Fraction(v)) for v in vals.split()])
+            assert np.max(np.abs(oracle.fd_weights(int(order)) - ref)) < 1e-15
+
+
+@pytest.mark.parametrize("order", [2, 4, 8, 12])
+def test_fd_weights_exact_on_polynomials(order):
+    m = order // 2
+    w = oracle.fd_weights(order)
+    x0 = 0.37
+    for q in range(0, 2 * m + 2):
+        f = lambda x: x ** q
+        d2 = q * (q - 1) * x0 ** (q - 2) if q >= 2 else 0.0
+        approx = w[0] * f(x0) + sum(w[p] * (f(x0 + p) + f(x0 - p)) for p in range(1, m + 1))
+        assert abs(approx - d2) <= 1e-9 * max(1.0, abs(d2)) * (m + 1) ** q / 10
+
+
+def test_fd_symbol_order12():
+    w = oracle.fd_weights(12)
+    th = np.linspace(1e-3, 0.9, 200)
+    sym = w[0] + 2 * sum(w[p] * np.cos(p * th) for p in range(1, 7))
+    # symbol = -theta^2 + O(theta^14): error within rounding plus a theta^14 term
+    assert np.all(np.abs(sym + th ** 2) <= 1e-14 + 1e-3 * th ** 14)
+    # and the theta^14 term is really there (order exactly 12, not higher)
+    assert np.abs(sym[-1] + th[-1] ** 2) > 1e-6 * th[-1] ** 14
+    th_all = np.linspace(0, np.pi, 2001)
+    sym_all = w[0] + 2 * sum(w[p] * np.cos(p * th_all) for p in range(1, 7))
+    assert sym_all.max() <= 1e-15 and abs(sym_all.min() + 7.0729) < 1e-3
+
+
+# ---------------------------------------------------------------- P2/P3: 1D closed forms
+@pytest.mark.parametrize("n,h", [(9, 0.5), (16, 0.3)])
+def test_order2_dirichlet_closed_form(n, h):
+    L = oracle.lap1d(n, h, D, 2)
+    k = np.arange(1, n + 1)
+    lam = -(4 / h ** 2) * np.sin(k * np.pi / (2 * (n + 1))) ** 2
+    i = np.arange(1, n + 1)
+    V = np.sqrt(2 / (n + 1)) * np.sin(np.outer(i, k) * np.pi / (n + 1))
+    assert np.max(np.abs(L @ V - V * lam)) < 1e-12 / h ** 2
+    lam_o, V_o = oracle.eig1d(L)
+    assert np.max(np.abs(np.sort(lam) - lam_o)) < 1e-12 / h ** 2
+    # eigenvectors agree up to sign (simple spectrum)
+    Vs = V[:, np.argsort(lam)]
+    assert np.max(np.abs(np.abs(np.sum(Vs * V_o, axis=0)) - 1)) < 1e-12
+
+
+@pytest.mark.parametrize("n,order", [(8, 2), (12, 12), (15, 12), (7, 6)])
+def test_periodic_closed_form(n, order):
+    h = 0.41
+    L = oracle.lap1d(n, h, P, order)
+    w = [float(x) for x in exact_weights(order)]
+    m = order // 2
+    th = 2 * np.pi * np.arange(n) / n
+    lam = (w[0] + 2 * sum(w[p] * np.cos(p * th) for p in range(1, m + 1))) / h ** 2
+    x = np.arange(n)
+    for kk in range(n):
+        c = np.cos(th[kk] * x)
+        s = np.sin(th[kk] * x)
+        assert np.max(np.abs(L @ c - lam[kk] * c)) < 1e-11
+        assert np.max(np.abs(L @ s - lam[kk] * s)) < 1e-11
+    lam_o, V_o = oracle.eig1d(L)
+    assert np.max(np.abs(np.sort(lam) - lam_o)) < 1e-11
+    assert np.max(np.abs(V_o.T @ V_o - np.eye(n))) < 1e-13
+
+
+def test_order12_dirichlet_needs_dense_eig():
+    # for order > 2 the truncated Toeplitz matrix is not diagonalised by sines (Sec. 3 keeps a dense eig)
+    n, h = 32, 0.5
+    L = oracle.lap1d(n, h, D, 12)
+    k = np.arange(1, n + 1)
+    V = np.sqrt(2 / (n + 1)) * np.sin(np.outer(k, k) * np.pi / (n + 1))
+    off = V.T @ L @ V
+    assert np.max(np.abs(off - np.diag(np.diag(off)))) > 0.1
+    lam, Vo = oracle.eig1d(L)
+    assert np.max(np.abs(L @ Vo - Vo * lam)) < 1e-12 * np.abs(lam).max()
+    assert lam.max() < 0
+
+
+# ---------------------------------------------------------------- kernel f
+def test_kernel_f_values():
+    lam = np.array([-1.0, -0.25, -4.0])
+    assert np.allclose(oracle.kernel_f(lam, U), 4 * np.pi / -lam, rtol=1e-15)
+    w = 0.11
+    ref = 4 * np.pi / -lam * (1 - np.exp(lam / (4 * w * w)))
+    assert np.allclose(oracle.kernel_f(lam, S, w), ref, rtol=1e-13)
+    assert oracle.kernel_f(np.array([0.0]), S, w)[0] == pytest.approx(np.pi / w ** 2, rel=1e-15)
+    # continuity at mu -> 0
+    assert oracle.kernel_f(np.array([-1e-10]), S, w)[0] == pytest.approx(np.pi / w ** 2, rel=1e-8)
+    with pytest.raises(ValueError):
+        oracle.kernel_f(np.array([0.0]), U)
+
+
+def test_fully_periodic_unscreened_rejected():
+    with pytest.raises(ValueError):
+        oracle.Plan((6, 6, 6), (0.5,) * 3, (P, P, P), U)
+    oracle.Plan((6, 6, 6), (0.5,) * 3, (P, P, D), U)  # slab is fine
+
+
+# ---------------------------------------------------------------- P4: eigenvectors of L
+def _closed_vec(n, h, bc, order, mode):
+    if bc == D:
+        assert order == 2
+        i = np.arange(1, n + 1)
+        v = np.sin(i * mode * np.pi / (n + 1))
+        lam = -(4 / h ** 2) * np.sin(mode * np.pi / (2 * (n + 1))) ** 2
+    else:
+        w = [float(x) for x in exact_weights(order)]
+        th = 2 * np.pi * mode / n
+        v = np.cos(th * np.arange(n))
+        lam = (w[0] + 2 * sum(w[p] * np.cos(p * th) for p in range(1, order // 2 + 1))) / h ** 2
+    return v, lam
+
+
+@pytest.mark.parametrize("n,h,bc,kind,order,modes", [
+    ((7, 9, 11), (0.5, 0.45, 0.4), (D, P, D), U, 2, (2, 3, 5)),
+    ((8, 10, 12), (0.4, 0.5, 0.3), (P, P, P), S, 12, (1, 3, 0)),
+    ((10, 6, 9), (0.3, 0.3, 0.3), (P, D, P), S, 2, (4, 1, 2)),
+])
+def test_fL_on_kronecker_eigenvector(n, h, bc, kind, order, modes):
+    plan = oracle.Plan(n, h, bc, kind, fd_order=order)
+    vs, lams = zip(*[_closed_vec(n[a], h[a], bc[a], order, modes[a]) for a in range(3)])
+    v = np.kron(vs[2], np.kron(vs[1], vs[0]))           # x1 fastest
+    fl = oracle.kernel_f(np.array([sum(lams)]), kind)[0]
+    x = oracle.apply_fL(plan, v)
+    assert np.max(np.abs(x - fl * v)) < 1e-12 * fl * np.abs(v).max()
+
+
+def test_screened_constant_mode_periodic():
+    plan = oracle.Plan((8, 9, 10), (0.3, 0.3, 0.3), (P, P, P), S, omega=0.11)
+    x = oracle.apply_fL(plan, np.ones(plan.N))
+    assert np.max(np.abs(x - np.pi / 0.11 ** 2)) < 1e-10 * np.pi / 0.11 ** 2
+
+
+# ---------------------------------------------------------------- P5 / P11: Poisson identity, CG
+@pytest.mark.parametrize("n,h,bc", [((10, 11, 12), (0.5, 0.45, 0.4), (D, D, D)),
+                                    ((8, 9, 14), (0.5, 0.5, 0.35), (P, P, D))])
+def test_minus_L_fL_is_4pi(n, h, bc):
+    plan = oracle.Plan(n, h, bc, U)
+    L = sparse_laplacian(plan)
+    b = workloads.random_field(plan.N, 1, 7)[:, 0]
+    x = oracle.apply_fL(plan, b)
+    r = -(L @ x) - 4 * np.pi * b
+    assert np.max(np.abs(r)) < 1e-11 * 4 * np.pi * np.abs(b).max() * (np.abs(L).max())
+
+
+def test_cg_cross_check_unscreened_dirichlet():
+    plan = oracle.Plan((9, 10, 11), (0.5,) * 3, (D, D, D), U)
+    A = -sparse_laplacian(plan)
+    b = workloads.random_field(plan.N, 1, 3)[:, 0]
+    x_cg, info = spla.cg(A, 4 * np.pi * b, rtol=1e-14, atol=0.0, maxiter=20000)
+    assert info == 0
+    x = oracle.apply_fL(plan, b)
+    assert np.max(np.abs(x - x_cg)) < 1e-9 * np.abs(x).max()
+
+
+# ---------------------------------------------------------------- P6: symmetry, positivity
+@pytest.mark.parametrize("bc,kind", [((D, D, D), U), ((P, P, P), S), ((P, D, P), U)])
+def test_fL_symmetric_positive(bc, kind):
+    plan = oracle.Plan((7, 8, 9), (0.4, 0.5, 0.45), bc, kind)
+    a, b = workloads.random_field(plan.N, 2, 11).T
+    fa, fb = oracle.apply_fL(plan, a), oracle.apply_fL(plan, b)
+    assert abs(a @ fb - fa @ b) < 1e-12 * abs(a @ fb) + 1e-12 * np.linalg.norm(a) * np.linalg.norm(fb)
+    assert b @ fb > 0 and a @ fa > 0
+
+
+# ---------------------------------------------------------------- P8: brute force dense
+@pytest.mark.parametrize("n,h,bc,kind", [
+    ((6, 7, 8), (0.5, 0.4, 0.3), (P, P, D), U),
+    ((5, 6, 7), (0.6, 0.5, 0.4), (D, D, D), U),
+    ((6, 5, 7), (0.5, 0.5, 0.5), (P, P, P), S),
+    ((7, 6, 5), (0.4, 0.5, 0.6), (D, P, D), S),
+])
+def test_apply_fL_matches_dense_matrix_function(n, h, bc, kind):
+    plan = oracle.Plan(n, h, bc, kind)
+    G = oracle.dense_fL(plan)
+    B = workloads.random_field(plan.N, 3, 5)
+    X = oracle.apply_fL(plan, B)
+    assert np.max(np.abs(G @ B - X)) < 1e-11 * np.abs(X).max()
+
+
+def test_vx_and_energy_match_dense_definition():
+    n, h, bc = (6, 7, 8), (0.5, 0.45, 0.4), (D, P, D)
+    psi, sysd = small_orbitals(n, h, bc, 4, 21)
+    plan = oracle.Plan(n, h, bc, U)
+    G = oracle.dense_fL(plan)
+    g = np.array([1.0, 0.7, 0.4, 1.0])
+    vx_ref = np.zeros_like(psi)
+    e_ref = 0.0
+    for a in range(4):          # Eq. 3-4 written out with the dense Green's matrix
+        for b in range(4):
+            phi = G @ (psi[:, b] * psi[:, a])
+            vx_ref[:, a] -= g[b] * psi[:, b] * phi
+            e_ref -= 0.5 * g[a] * g[b] * plan.dV * np.sum(psi[:, a] * phi * psi[:, b])
+    vx, e = oracle.vx_apply(plan, psi, g)
+    assert np.max(np.abs(vx - vx_ref)) < 1e-12 * np.abs(vx_ref).max()
+    assert abs(e - e_ref) < 1e-12 * abs(e_ref)
+
+
+# ---------------------------------------------------------------- P7: Vx on the occupied space
+def test_vx_projection_symmetric_nsd_and_trace():
+    psi, sysd = small_orbitals((8, 9, 10), (0.45,) * 3, (D, D, D), 5, 31)
+    plan = oracle.Plan(sysd.n, sysd.h, sysd.bc, U)
+    vx, e = oracle.vx_apply(plan, psi)
+    M = plan.dV * psi.T @ vx
+    assert np.max(np.abs(M - M.T)) < 1e-12 * np.abs(M).max()
+    assert np.linalg.eigvalsh(M).max() < 1e-12 * np.abs(M).max()
+    assert abs(e - 0.5 * np.trace(M)) < 1e-12 * abs(e)
+    assert e < 0
+    assert abs(oracle.exchange_energy(plan, psi) - e) < 1e-12 * abs(e)
+
+
+def test_energy_parseval_with_occupations():
+    psi, sysd = small_orbitals((7, 8, 9), (0.5,) * 3, (P, P, P), 4, 41, kernel=S)
+    plan = oracle.Plan(sysd.n, sysd.h, sysd.bc, S)
+    g = np.array([1.0, 0.5, 0.25, 0.9])
+    vx, e = oracle.vx_apply(plan, psi, g)
+    M = plan.dV * psi.T @ vx
+    assert abs(e - 0.5 * np.sum(g * np.diag(M))) < 1e-12 * abs(e)
+    assert abs(oracle.exchange_energy(plan, psi, g) - e) < 1e-12 * abs(e)
+
+
+# ---------------------------------------------------------------- P9: invariances
+def test_invariances():
+    n, h, bc = (6, 7, 9), (0.5, 0.45, 0.4), (D, P, D)
+    psi, sysd = small_orbitals(n, h, bc, 3, 51, kernel=S)
+    plan = oracle.Plan(n, h, bc, S)
+    vx, e = oracle.vx_apply(plan, psi)
+    # ordered and symmetric enumerations agree
+    vx_o, e_o = oracle.vx_apply(plan, psi, ordered=True)
+    assert np.max(np.abs(vx - vx_o)) < 1e-12 * np.abs(vx).max() and abs(e - e_o) < 1e-12 * abs(e)
+    # orbital rotation: E invariant, VxPsi -> VxPsi U
+    U_, _ = np.linalg.qr(np.random.default_rng(0).standard_normal((3, 3)))
+    vx_r, e_r = oracle.vx_apply(plan, psi @ U_)
+    assert abs(e_r - e) < 1e-12 * abs(e)
+    assert np.max(np.abs(vx_r - vx @ U_)) < 1e-12 * np.abs(vx).max()
+    # scaling: Vx(c psi) = c^3 Vx(psi), E(c psi) = c^4 E(psi)
+    c = 1.7
+    vx_c, e_c = oracle.vx_apply(plan, c * psi)
+    assert np.max(np.abs(vx_c - c ** 3 * vx)) < 1e-12 * np.abs(vx_c).max()
+    assert abs(e_c - c ** 4 * e) < 1e-12 * abs(e_c)
+    # axis permutation: swap x1 <-> x3
+    n1, n2, n3 = n
+    cube = psi.reshape(n3, n2, n1, 3)
+    psi_p = np.ascontiguousarray(cube.transpose(2, 1, 0, 3)).reshape(-1, 3)
+    plan_p = oracle.Plan((n3, n2, n1), (h[2], h[1], h[0]), (bc[2], bc[1], bc[0]), S)
+    vx_p, e_p = oracle.vx_apply(plan_p, psi_p)
+    vx_back = vx_p.reshape(n1, n2, n3, 3).transpose(2, 1, 0, 3).reshape(-1, 3)
+    assert abs(e_p - e) < 1e-12 * abs(e)
+    assert np.max(np.abs(vx_back - vx)) < 1e-12 * np.abs(vx).max()
+
+
+def test_degenerate_cases():
+    plan = oracle.Plan((5, 6, 7), (0.5,) * 3, (D, D, D), U)
+    # zero orbital contributes nothing
+    psi = np.zeros((plan.N, 2))
+    psi[:, 0] = workloads.random_field(plan.N, 1, 2)[:, 0]
+    vx, e = oracle.vx_apply(plan, psi)
+    assert np.all(vx[:, 1] == 0)
+    vx1, e1 = oracle.vx_apply(plan, psi[:, :1])
+    assert np.max(np.abs(vx1[:, 0] - vx[:, 0])) == 0 and e1 == e
+    # a single orbital: Vx psi = -psi f(L)(psi^2), E = -1/2 dV <psi^2, f(L) psi^2>
+    p = psi[:, 0]
+    phi = oracle.apply_fL(plan, p * p)
+    assert np.max(np.abs(vx1[:, 0] + p * phi)) < 1e-13 * np.abs(p * phi).max()
+
+
+# ---------------------------------------------------------------- P10: continuum limit (constants 4 pi, w)
+def test_screened_periodic_gaussian_continuum_limit():
+    Lbox, n = 12.0, 60
+    h = Lbox / n
+    w, alpha = 0.11, 1.5
+    plan = oracle.Plan((n, n, n), (h,) * 3, (P, P, P), S, omega=w)
+    x = np.arange(n) * h
+    c0 = np.array([5.9, 6.1, 6.05])
+
+    def d(ax):
+        dd = x - c0[ax]
+        return (dd + Lbox / 2) % Lbox - Lbox / 2
+    dx, dy, dz = d(0), d(1), d(2)
+    r2 = dz[:, None, None] ** 2 + dy[None, :, None] ** 2 + dx[None, None, :] ** 2
+    rho = (alpha / np.pi) ** 1.5 * np.exp(-alpha * r2)
+    phi = oracle.apply_fL(plan, rho.reshape(-1)).reshape(n, n, n)
+    cc = 1.0 / np.sqrt(1.0 / alpha + 1.0 / w ** 2)
+    rng = np.random.default_rng(1)
+    pts = rng.integers(0, n, size=(40, 3))
+    err = 0.0
+    ref_max = 0.0
+    for (i3, i2, i1) in pts:
+        r0 = np.array([x[i1], x[i2], x[i3]])
+        tot = 0.0
+        for a in range(-4, 5):
+            for b in range(-4, 5):
+                for c in range(-4, 5):
+                    rr = np.linalg.norm(r0 - c0 + Lbox * np.array([a, b, c]))
+                    if rr < 1e-12:
+                        tot += 2 * np.sqrt(alpha / np.pi) - 2 * cc / np.sqrt(np.pi)
+                    else:
+                        tot += (erf(np.sqrt(alpha) * rr) - erf(cc * rr)) / rr
+        err = max(err, abs(phi[i3, i2, i1] - tot))
+        ref_max = max(ref_max, abs(tot))
+    assert err < 1e-5 * ref_max
+
+
+# ---------------------------------------------------------------- P12: gradient
+def test_energy_gradient_finite_differences():
+    psi, sysd = small_orbitals((6, 7, 8), (0.5,) * 3, (D, D, D), 3, 61)
+    plan = oracle.Plan(sysd.n, sysd.h, sysd.bc, U)
+    g = np.array([1.0, 0.8, 0.6])
+    grad = oracle.energy_gradient(plan, psi, g)
+    rng = np.random.default_rng(5)
+    step = 1e-4
+    for _ in range(16):
+        r, k = int(rng.integers(plan.N)), int(rng.integers(3))
+        pp, pm = psi.copy(), psi.copy()
+        pp[r, k] += step
+        pm[r, k] -= step
+        fd = (oracle.exchange_energy(plan, pp, g) - oracle.exchange_energy(plan, pm, g)) / (2 * step)
+        assert abs(fd - grad[r, k]) < 1e-7 * np.abs(grad).max()
+
+
+# ---------------------------------------------------------------- ACE tail
+def test_ace_reproduces_vx_on_occupied_space():
+    psi, sysd = small_orbitals((7, 8, 9), (0.45,) * 3, (P, P, D), 4, 71)
+    plan = oracle.Plan(sysd.n, sysd.h, sysd.bc, U)
+    vx, _ = oracle.vx_apply(plan, psi)
+    xi, M, R = oracle.ace(plan, psi, vx)
+    assert np.max(np.abs(np.tril(R, -1))) == 0.0
+    assert np.max(np.abs(R.T @ R + M)) < 1e-12 * np.abs(M).max()
+    Vace_psi = -xi @ (plan.dV * xi.T @ psi)
+    assert np.max(np.abs(Vace_psi - vx)) < 1e-11 * np.abs(vx).max()

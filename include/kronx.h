@@ -1,0 +1,204 @@
+/*
+ * kronx — exact-exchange operator on a finite-difference grid through the
+ * Kronecker-product representation of f(L), for one GPU (sm_103a).
+ *
+ * Method: Jing & Suryanarayana, "Efficient real space formalism for hybrid
+ * density functionals" (arXiv 2406.16998).
+ *
+ *   Sec. 2, Eqs. 3-5:  (Vx psi)_i = -sum_j g_j psi_j * phi_ij,
+ *                      phi_ij     = f(L) (psi_i * psi_j),
+ *                      E_x        = -1/2 dV sum_ij g_i g_j <psi_i psi_j, phi_ij>.
+ *   Sec. 3, Eqs. 11-19: L = I3(x)I2(x)L1 + I3(x)L2(x)I1 + L3(x)I2(x)I1,
+ *                      Lk = Vk Lambda_k Vk^T,
+ *                      f(L) b = (V3(x)V2(x)V1) f(l1+l2+l3) (V3(x)V2(x)V1)^T b,
+ *                      applied as three mode products, a diagonal scaling and
+ *                      three inverse mode products (Roth's relationship, Eq. 19).
+ *   Kernel f (Sec. 3 after Eq. 18): unscreened f = -4 pi / lambda; screened
+ *                      f = (4 pi / mu)(1 - exp(-mu / (4 w^2))), mu = -lambda,
+ *                      f(0) = pi / w^2 (the transform of erfc(w r)/r, Sec. 2.2).
+ *
+ * Conventions shared by every call
+ *   - Grid vectors have N = n1*n2*n3 entries, x1 fastest, then x2, then x3.
+ *   - Orbital blocks are n_orb grid vectors stored one after the other
+ *     (orbital k occupies elements [k*N, (k+1)*N)), float64.
+ *   - Unless a call says "host", every pointer argument is a device pointer on
+ *     the current CUDA device, owned by the caller, and must stay valid until
+ *     the work queued on `stream` has finished.  Plans, batches and their
+ *     workspaces are owned by the library.
+ *   - Work is queued asynchronously on `stream` (a cudaStream_t; NULL is the
+ *     legacy default stream).  Calls return before the GPU has finished.
+ *   - Every call returns 0 (KX_OK) or a KX_ERR_* code; no C++ exception crosses
+ *     this boundary.  kx_last_error_detail() gives a one-line explanation of the
+ *     last failure on the calling host thread.
+ *   - Integration weights: <a, b> = dV * sum(a * b), dV = h1*h2*h3.
+ */
+#ifndef KRONX_H
+#define KRONX_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque handles. */
+typedef struct kx_plan_s kx_plan;
+typedef struct kx_batch_s kx_batch;
+/* cudaStream_t-compatible stream handle. */
+typedef struct CUstream_st *kx_stream;
+
+/* Boundary condition per axis (Sec. 2: Dirichlet in vacuum directions,
+ * periodic in extended directions). */
+#define KX_DIRICHLET 0
+#define KX_PERIODIC  1
+
+/* Kernel f (Sec. 3, after Eq. 18). */
+#define KX_UNSCREENED 0 /* f = -4 pi / lambda            (PBE0, Eq. 5)  */
+#define KX_SCREENED   1 /* erfc(w r)/r, w = kx_kernel.omega (HSE, Eq. 10) */
+
+/* Arithmetic of the mode products. */
+#define KX_FP64  0 /* plain float64 on the CUDA cores (the baseline path)            */
+#define KX_F16X3 1 /* tensor cores: fp16 hi/lo split of both operands, three products
+                      (hi*hi + hi*lo + lo*hi) accumulated in fp32, per-pair power-of-two
+                      scaling; energy and outputs accumulated in fp32/fp64            */
+
+/* Error codes. */
+#define KX_OK              0
+#define KX_ERR_ARG         1 /* invalid argument (sizes, pointers, enum values)        */
+#define KX_ERR_SINGULAR    2 /* unscreened kernel with all axes periodic: lambda = 0   */
+#define KX_ERR_NOMEM       3 /* a device or host allocation failed                    */
+#define KX_ERR_CUDA        4 /* a CUDA runtime call or kernel launch failed            */
+#define KX_ERR_TIMEOUT     5 /* a bounded wait inside a kernel ran out                 */
+#define KX_ERR_UNSUPPORTED 6 /* valid request outside what this build implements      */
+
+/* Grid and finite-difference operator (Sec. 3, Eqs. 11-12).
+ *   n[a]      points per axis, 2 <= n[a] <= 128; for KX_F16X3, n[a] % 8 == 0.
+ *   h[a]      spacing (bohr), > 0.
+ *   bc[a]     KX_DIRICHLET (homogeneous, unknowns at x_i = (i+1) h) or
+ *             KX_PERIODIC (x_i = i h, circulant Lk).
+ *   fd_order  even, 2..24: centred stencil of half-width fd_order/2. */
+typedef struct {
+    int n[3];
+    double h[3];
+    int bc[3];
+    int fd_order;
+} kx_grid;
+
+/* Kernel choice: kind = KX_UNSCREENED or KX_SCREENED, omega (bohr^-1) > 0 for
+ * the screened kernel. */
+typedef struct {
+    int kind;
+    double omega;
+} kx_kernel;
+
+/* kx_plan_create — set-up of one grid/kernel (Sec. 3, Eqs. 12-13 and the f
+ * table of Eq. 19).  Builds L1, L2, L3, diagonalises each on the GPU in float64
+ * (cyclic Jacobi), evaluates f(l1_i + l2_j + l3_k) for all N spectral points in
+ * float64, and prepares the operands of the chosen precision.  Synchronous:
+ * returns after the set-up kernels have finished.
+ *   grid, kernel   host pointers, read only during the call.
+ *   precision      KX_FP64 or KX_F16X3.
+ *   out            host pointer receiving the plan handle.
+ * Errors: KX_ERR_ARG, KX_ERR_SINGULAR (unscreened and every axis periodic),
+ * KX_ERR_UNSUPPORTED (sizes outside the limits above), KX_ERR_NOMEM, KX_ERR_CUDA. */
+int kx_plan_create(const kx_grid *grid, const kx_kernel *kernel, int precision, kx_plan **out);
+
+/* kx_plan_destroy — frees the plan and its workspaces (synchronises the device
+ * first).  NULL is accepted. */
+int kx_plan_destroy(kx_plan *plan);
+
+/* kx_plan_eig — copies the float64 set-up of one axis to host memory:
+ * lam[n] (eigenvalues of L_axis, ascending) and V[n*n] (row-major, V[x*n + k] is
+ * component x of eigenvector k), so that L_axis V = V diag(lam) (Sec. 3, Eq. 13).
+ * Either host pointer may be NULL.  Synchronous. */
+int kx_plan_eig(const kx_plan *plan, int axis, double *lam, double *V);
+
+/* kx_plan_ftable — copies the float64 f table (N entries, index
+ * k1 + n1*(k2 + n2*k3), value f(l1_k1 + l2_k2 + l3_k3)) to host memory.
+ * Synchronous. */
+int kx_plan_ftable(const kx_plan *plan, double *f);
+
+/* kx_apply_fL — X = f(L) B for n_rhs independent right-hand sides (Sec. 3,
+ * Eq. 18-19).  b and x hold n_rhs grid vectors each (float64); b is read only,
+ * x must not overlap b.  n_rhs >= 0 (0 is a no-op). */
+int kx_apply_fL(kx_plan *plan, int n_rhs, const double *b, double *x, kx_stream stream);
+
+/* kx_vx_apply — the exact-exchange apply and energy (Sec. 2, Eqs. 3-5 / 8-10 at
+ * the Gamma point, one spin channel).  Every unordered pair (i <= j) is solved
+ * once (n_orb (n_orb+1)/2 solves of Eq. 19).
+ *   psi     n_orb orbitals (float64), read only.
+ *   occ     n_orb occupations g (float64) or NULL for g = 1.
+ *   vx_psi  out: n_orb grid vectors (float64), (Vx psi)_i; must not overlap psi.
+ *   e_x     out: one float64, E_x = -1/2 dV sum_ij g_i g_j <rho_ij, phi_ij>;
+ *           may be NULL.
+ * n_orb >= 1. */
+int kx_vx_apply(kx_plan *plan, int n_orb, const double *psi, const double *occ,
+                double *vx_psi, double *e_x, kx_stream stream);
+
+/* kx_vx_apply_host — kx_vx_apply on HOST buffers (pinned memory recommended):
+ * copies psi (and occ) to library-owned device buffers, runs the apply and
+ * copies vx_psi and e_x back, all queued on `stream`; returns after the stream
+ * has finished.  psi, occ (nullable), vx_psi, e_x (nullable) are host pointers. */
+int kx_vx_apply_host(kx_plan *plan, int n_orb, const double *psi, const double *occ,
+                     double *vx_psi, double *e_x, kx_stream stream);
+
+/* kx_energy — E_x alone (no inverse transforms): by Parseval, with V orthogonal,
+ * <rho, f(L) rho> = sum_k f(Lambda)_k ((V^T rho)_k)^2 (Sec. 3, Eq. 15-16).
+ * Arguments as in kx_vx_apply; e_x must not be NULL. */
+int kx_energy(kx_plan *plan, int n_orb, const double *psi, const double *occ, double *e_x,
+              kx_stream stream);
+
+/* kx_ace — adaptively compressed exchange tail (the ACE construction that
+ * Sec. 4 cites; float64 throughout):
+ *   M = dV psi^T W (n_orb x n_orb, W = vx_psi),  -M = R^T R (Cholesky, R upper),
+ *   xi = W R^{-1}, so that -xi (dV xi^T psi) = W.
+ *   psi, vx_psi  inputs (n_orb grid vectors each).
+ *   xi           out: n_orb grid vectors; must not overlap the inputs.
+ *   M_out        out (nullable): n_orb*n_orb float64, row-major, M before factoring.
+ * Returns KX_ERR_ARG if -M is not positive definite (detected on the GPU; the
+ * call then synchronises the stream to read the flag).  1 <= n_orb <= 256. */
+int kx_ace(kx_plan *plan, int n_orb, const double *psi, const double *vx_psi, double *xi,
+           double *M_out, kx_stream stream);
+
+/* kx_batch_create — groups n_sys plans (different grids, kernels and orbital
+ * counts) into one CUDA graph that runs every system's kx_vx_apply.  Workspaces
+ * are reserved here so that the graph holds no allocation.
+ *   plans[n_sys], n_orb[n_sys]  host arrays.  out: host pointer for the handle. */
+int kx_batch_create(int n_sys, kx_plan *const *plans, const int *n_orb, kx_batch **out);
+
+/* kx_batch_run — replays the graph on `stream`.  psi[s], vx_psi[s] (host arrays
+ * of device pointers) are system s's orbitals and output; e_x (device, n_sys
+ * float64, nullable) receives each system's E_x.  The graph is re-captured when
+ * the pointer set differs from the previous run. */
+int kx_batch_run(kx_batch *batch, const double *const *psi, double *const *vx_psi, double *e_x,
+                 kx_stream stream);
+
+/* kx_batch_destroy — frees the batch (not its plans).  NULL is accepted. */
+int kx_batch_destroy(kx_batch *batch);
+
+/* kx_autotune — times the launch shapes this build offers for `plan` at n_orb
+ * orbitals (for up to budget_ms milliseconds, on an internal stream, with
+ * synthetic orbitals) and keeps the fastest in the plan.  Synchronous. */
+int kx_autotune(kx_plan *plan, int n_orb, int budget_ms);
+
+/* kx_plan_status — reads and clears the plan's device status word (set by a
+ * kernel whose bounded wait ran out).  Synchronises `stream`.  *status_out
+ * receives KX_OK or KX_ERR_TIMEOUT.  status_out is a host pointer. */
+int kx_plan_status(kx_plan *plan, int *status_out, kx_stream stream);
+
+/* kx_selftest_wait — failure-path self-test of the bounded waits the kernels
+ * use (no counterpart in the paper): one CTA waits on an mbarrier phase that
+ * nothing completes, gives up after max_cycles SM clock cycles
+ * (1 <= max_cycles <= 2e9), records KX_ERR_TIMEOUT in the plan's status word
+ * and returns; read the word with kx_plan_status.  The GPU context stays usable. */
+int kx_selftest_wait(kx_plan *plan, long long max_cycles, kx_stream stream);
+
+/* kx_last_error_detail — copies the last error message of the calling host
+ * thread into buf (host, len bytes, NUL-terminated).  Returns the last code. */
+int kx_last_error_detail(char *buf, int len);
+
+/* kx_strerror — static name of an error code. */
+const char *kx_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KRONX_H */

@@ -1,0 +1,444 @@
+// C ABI of kronx: argument checks, plan lifetime, workspaces, dispatch to the
+// float64 and tensor-core paths, CUDA-graph batches and the launch-shape tuner.
+#include "kx_internal.h"
+
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+namespace kx {
+
+static thread_local int g_last_code = KX_OK;
+static thread_local char g_last_msg[512] = "";
+
+int set_error(int code, const std::string &msg) {
+    g_last_code = code;
+    std::snprintf(g_last_msg, sizeof(g_last_msg), "%s", msg.c_str());
+    return code;
+}
+
+int cuda_error(cudaError_t e, const char *what) {
+    int code = (e == cudaErrorMemoryAllocation) ? KX_ERR_NOMEM : KX_ERR_CUDA;
+    return set_error(code, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// Host-side fault injection for the failure-path tests: KX_FAULT=alloc makes the
+// next workspace allocation report KX_ERR_NOMEM without touching the device.
+static bool fault_alloc() {
+    const char *f = std::getenv("KX_FAULT");
+    return f && std::strcmp(f, "alloc") == 0;
+}
+
+int ensure_workspace(kx_plan *p, size_t bytes) {
+    if (p->ws.bytes >= bytes) return KX_OK;
+    if (fault_alloc()) return set_error(KX_ERR_NOMEM, "workspace allocation failed (injected by KX_FAULT=alloc)");
+    if (p->ws.ptr) {
+        KX_CUDA_TRY(cudaFree(p->ws.ptr));  // implicit device synchronisation
+        p->ws.ptr = nullptr;
+        p->ws.bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&p->ws.ptr, bytes);
+    if (e != cudaSuccess) {
+        p->ws.ptr = nullptr;
+        return cuda_error(e, "workspace cudaMalloc");
+    }
+    p->ws.bytes = bytes;
+    return KX_OK;
+}
+
+int ensure_pairs(kx_plan *p, int n_orb, cudaStream_t s) {
+    (void)s;
+    if (p->ws_norb == n_orb) return KX_OK;
+    const size_t P = (size_t)n_orb * (n_orb + 1) / 2;
+    if (P > p->pairs_cap) {
+        cudaFree(p->d_pairs);
+        p->d_pairs = nullptr;
+        p->pairs_cap = 0;
+        cudaError_t e = cudaMalloc(&p->d_pairs, sizeof(int) * 2 * P);
+        if (e != cudaSuccess) return cuda_error(e, "pair list cudaMalloc");
+        p->pairs_cap = P;
+    }
+    std::vector<int> h(2 * P);
+    size_t k = 0;
+    for (int i = 0; i < n_orb; ++i)
+        for (int j = i; j < n_orb; ++j) {
+            h[2 * k] = i;
+            h[2 * k + 1] = j;
+            ++k;
+        }
+    KX_CUDA_TRY(cudaMemcpy(p->d_pairs, h.data(), sizeof(int) * 2 * P, cudaMemcpyHostToDevice));
+    p->ws_norb = n_orb;
+    return KX_OK;
+}
+
+static int reserve(kx_plan *p, int n_orb) {
+    int rc = ensure_pairs(p, n_orb, nullptr);
+    if (rc) return rc;
+    if (p->precision == KX_FP64) {
+        const long P = (long)n_orb * (n_orb + 1) / 2;
+        const size_t budget = (size_t)2 << 30;
+        long c = (long)std::max<size_t>(1, budget / (3 * p->N * sizeof(double)));
+        return ensure_workspace(p, fp64_workspace_bytes(p, std::min(c, P)));
+    }
+    const long P = (long)n_orb * (n_orb + 1) / 2;
+    const long chunk = std::min<long>(tc_default_chunk(p, n_orb), P);
+    return ensure_workspace(p, tc_workspace_bytes(p, n_orb, chunk));
+}
+
+static int dispatch_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, double *vx, double *ex,
+                       bool energy_only, cudaStream_t s) {
+    if (p->precision == KX_FP64) return fp64_vx(p, n_orb, psi, occ, vx, ex, energy_only, s);
+    return tc_vx(p, n_orb, psi, occ, vx, ex, energy_only, s);
+}
+
+static int check_plan(const kx_plan *p) {
+    if (!p) return set_error(KX_ERR_ARG, "plan is NULL");
+    return KX_OK;
+}
+
+}  // namespace kx
+
+using namespace kx;
+
+struct kx_batch_s {
+    std::vector<kx_plan *> plans;
+    std::vector<int> n_orb;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<const double *> last_psi;
+    std::vector<double *> last_vx;
+    double *last_ex = nullptr;
+    int device = 0;
+};
+
+extern "C" {
+
+const char *kx_strerror(int code) {
+    switch (code) {
+        case KX_OK: return "KX_OK";
+        case KX_ERR_ARG: return "KX_ERR_ARG";
+        case KX_ERR_SINGULAR: return "KX_ERR_SINGULAR";
+        case KX_ERR_NOMEM: return "KX_ERR_NOMEM";
+        case KX_ERR_CUDA: return "KX_ERR_CUDA";
+        case KX_ERR_TIMEOUT: return "KX_ERR_TIMEOUT";
+        case KX_ERR_UNSUPPORTED: return "KX_ERR_UNSUPPORTED";
+        default: return "KX_ERR_UNKNOWN";
+    }
+}
+
+int kx_last_error_detail(char *buf, int len) {
+    if (buf && len > 0) std::snprintf(buf, (size_t)len, "%s", g_last_msg);
+    return g_last_code;
+}
+
+int kx_plan_create(const kx_grid *grid, const kx_kernel *kernel, int precision, kx_plan **out) {
+    if (!grid || !kernel || !out) return set_error(KX_ERR_ARG, "kx_plan_create: NULL argument");
+    *out = nullptr;
+    for (int a = 0; a < 3; ++a) {
+        if (grid->n[a] < 2) return set_error(KX_ERR_ARG, "kx_plan_create: n[a] must be >= 2");
+        if (grid->n[a] > kMaxN) return set_error(KX_ERR_UNSUPPORTED, "kx_plan_create: n[a] > 128");
+        if (!(grid->h[a] > 0.0)) return set_error(KX_ERR_ARG, "kx_plan_create: h[a] must be > 0");
+        if (grid->bc[a] != KX_DIRICHLET && grid->bc[a] != KX_PERIODIC)
+            return set_error(KX_ERR_ARG, "kx_plan_create: bc[a] must be KX_DIRICHLET or KX_PERIODIC");
+    }
+    if (grid->fd_order < 2 || grid->fd_order % 2 || grid->fd_order > 24)
+        return set_error(KX_ERR_ARG, "kx_plan_create: fd_order must be even, 2..24");
+    if (kernel->kind != KX_UNSCREENED && kernel->kind != KX_SCREENED)
+        return set_error(KX_ERR_ARG, "kx_plan_create: unknown kernel kind");
+    if (kernel->kind == KX_SCREENED && !(kernel->omega > 0.0))
+        return set_error(KX_ERR_ARG, "kx_plan_create: omega must be > 0 for the screened kernel");
+    if (precision != KX_FP64 && precision != KX_F16X3)
+        return set_error(KX_ERR_ARG, "kx_plan_create: unknown precision");
+    if (precision == KX_F16X3)
+        for (int a = 0; a < 3; ++a)
+            if (grid->n[a] % 8)
+                return set_error(KX_ERR_UNSUPPORTED, "kx_plan_create: KX_F16X3 needs n[a] % 8 == 0");
+    if (kernel->kind == KX_UNSCREENED && grid->bc[0] == KX_PERIODIC && grid->bc[1] == KX_PERIODIC &&
+        grid->bc[2] == KX_PERIODIC)
+        return set_error(KX_ERR_SINGULAR, "kx_plan_create: unscreened kernel with all axes periodic is singular");
+
+    kx_plan *p = new (std::nothrow) kx_plan_s();
+    if (!p) return set_error(KX_ERR_NOMEM, "kx_plan_create: host allocation failed");
+    for (int a = 0; a < 3; ++a) {
+        p->n[a] = grid->n[a];
+        p->h[a] = grid->h[a];
+        p->bc[a] = grid->bc[a];
+        p->np[a] = round_up(grid->n[a], 16);
+    }
+    p->fd_order = grid->fd_order;
+    p->kind = kernel->kind;
+    p->omega = kernel->omega;
+    p->precision = precision;
+    p->N = (size_t)p->n[0] * p->n[1] * p->n[2];
+    p->dV = p->h[0] * p->h[1] * p->h[2];
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (e != cudaSuccess) {
+        delete p;
+        return cuda_error(e, "kx_plan_create: no usable CUDA device");
+    }
+    int rc = plan_setup(p);
+    if (rc) {
+        plan_free(p);
+        delete p;
+        return rc;
+    }
+    *out = p;
+    return KX_OK;
+}
+
+int kx_plan_destroy(kx_plan *plan) {
+    if (!plan) return KX_OK;
+    cudaSetDevice(plan->device);
+    cudaDeviceSynchronize();
+    plan_free(plan);
+    delete plan;
+    return KX_OK;
+}
+
+int kx_plan_eig(const kx_plan *plan, int axis, double *lam, double *V) {
+    if (int rc = check_plan(plan)) return rc;
+    if (axis < 0 || axis > 2) return set_error(KX_ERR_ARG, "kx_plan_eig: axis must be 0, 1 or 2");
+    const int n = plan->n[axis];
+    if (lam) KX_CUDA_TRY(cudaMemcpy(lam, plan->d_lam[axis], sizeof(double) * n, cudaMemcpyDeviceToHost));
+    if (V) KX_CUDA_TRY(cudaMemcpy(V, plan->d_V[axis], sizeof(double) * n * n, cudaMemcpyDeviceToHost));
+    return KX_OK;
+}
+
+int kx_plan_ftable(const kx_plan *plan, double *f) {
+    if (int rc = check_plan(plan)) return rc;
+    if (!f) return set_error(KX_ERR_ARG, "kx_plan_ftable: NULL output");
+    KX_CUDA_TRY(cudaMemcpy(f, plan->d_f64, sizeof(double) * plan->N, cudaMemcpyDeviceToHost));
+    return KX_OK;
+}
+
+int kx_apply_fL(kx_plan *plan, int n_rhs, const double *b, double *x, kx_stream stream) {
+    if (int rc = check_plan(plan)) return rc;
+    if (n_rhs < 0) return set_error(KX_ERR_ARG, "kx_apply_fL: n_rhs < 0");
+    if (n_rhs == 0) return KX_OK;
+    if (!b || !x) return set_error(KX_ERR_ARG, "kx_apply_fL: NULL buffer");
+    if (b == x) return set_error(KX_ERR_ARG, "kx_apply_fL: x must not overlap b");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (plan->precision == KX_FP64) return fp64_apply_fL(plan, n_rhs, b, x, s);
+    return tc_apply_fL(plan, n_rhs, b, x, s);
+}
+
+int kx_vx_apply(kx_plan *plan, int n_orb, const double *psi, const double *occ, double *vx_psi, double *e_x,
+                kx_stream stream) {
+    if (int rc = check_plan(plan)) return rc;
+    if (n_orb < 1 || n_orb > 4096) return set_error(KX_ERR_ARG, "kx_vx_apply: n_orb must be in 1..4096");
+    if (!psi || !vx_psi) return set_error(KX_ERR_ARG, "kx_vx_apply: NULL buffer");
+    if (psi == vx_psi) return set_error(KX_ERR_ARG, "kx_vx_apply: vx_psi must not overlap psi");
+    return dispatch_vx(plan, n_orb, psi, occ, vx_psi, e_x, false, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int kx_energy(kx_plan *plan, int n_orb, const double *psi, const double *occ, double *e_x, kx_stream stream) {
+    if (int rc = check_plan(plan)) return rc;
+    if (n_orb < 1 || n_orb > 4096) return set_error(KX_ERR_ARG, "kx_energy: n_orb must be in 1..4096");
+    if (!psi || !e_x) return set_error(KX_ERR_ARG, "kx_energy: NULL buffer");
+    return dispatch_vx(plan, n_orb, psi, occ, nullptr, e_x, true, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int kx_vx_apply_host(kx_plan *plan, int n_orb, const double *psi, const double *occ, double *vx_psi, double *e_x,
+                     kx_stream stream) {
+    if (int rc = check_plan(plan)) return rc;
+    if (n_orb < 1 || n_orb > 4096) return set_error(KX_ERR_ARG, "kx_vx_apply_host: n_orb must be in 1..4096");
+    if (!psi || !vx_psi) return set_error(KX_ERR_ARG, "kx_vx_apply_host: NULL buffer");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const size_t vec = sizeof(double) * (size_t)n_orb * plan->N;
+    const size_t need = 2 * vec + sizeof(double) * (n_orb + 1) + 512;
+    if (plan->ws_host.bytes < need) {
+        if (fault_alloc()) return set_error(KX_ERR_NOMEM, "staging allocation failed (injected by KX_FAULT=alloc)");
+        cudaFree(plan->ws_host.ptr);
+        plan->ws_host.ptr = nullptr;
+        plan->ws_host.bytes = 0;
+        cudaError_t e = cudaMalloc(&plan->ws_host.ptr, need);
+        if (e != cudaSuccess) return cuda_error(e, "kx_vx_apply_host staging cudaMalloc");
+        plan->ws_host.bytes = need;
+    }
+    double *d_psi = (double *)plan->ws_host.ptr;
+    double *d_vx = d_psi + (size_t)n_orb * plan->N;
+    double *d_ex = d_vx + (size_t)n_orb * plan->N;
+    double *d_occ = occ ? d_ex + 1 : nullptr;
+    KX_CUDA_TRY(cudaMemcpyAsync(d_psi, psi, vec, cudaMemcpyHostToDevice, s));
+    if (occ) KX_CUDA_TRY(cudaMemcpyAsync(d_occ, occ, sizeof(double) * n_orb, cudaMemcpyHostToDevice, s));
+    int rc = dispatch_vx(plan, n_orb, d_psi, d_occ, d_vx, d_ex, false, s);
+    if (rc) return rc;
+    KX_CUDA_TRY(cudaMemcpyAsync(vx_psi, d_vx, vec, cudaMemcpyDeviceToHost, s));
+    if (e_x) KX_CUDA_TRY(cudaMemcpyAsync(e_x, d_ex, sizeof(double), cudaMemcpyDeviceToHost, s));
+    KX_CUDA_TRY(cudaStreamSynchronize(s));
+    return KX_OK;
+}
+
+int kx_ace(kx_plan *plan, int n_orb, const double *psi, const double *vx_psi, double *xi, double *M_out,
+           kx_stream stream) {
+    if (int rc = check_plan(plan)) return rc;
+    if (n_orb < 1 || n_orb > 256) return set_error(KX_ERR_ARG, "kx_ace: n_orb must be in 1..256");
+    if (!psi || !vx_psi || !xi) return set_error(KX_ERR_ARG, "kx_ace: NULL buffer");
+    if (xi == psi || xi == vx_psi) return set_error(KX_ERR_ARG, "kx_ace: xi must not overlap the inputs");
+    return ace_run(plan, n_orb, psi, vx_psi, xi, M_out, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int kx_plan_status(kx_plan *plan, int *status_out, kx_stream stream) {
+    if (int rc = check_plan(plan)) return rc;
+    if (!status_out) return set_error(KX_ERR_ARG, "kx_plan_status: NULL output");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int h = 0;
+    KX_CUDA_TRY(cudaMemcpyAsync(&h, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    KX_CUDA_TRY(cudaMemsetAsync(plan->d_status, 0, sizeof(int), s));
+    KX_CUDA_TRY(cudaStreamSynchronize(s));
+    *status_out = h;
+    return KX_OK;
+}
+
+int kx_selftest_wait(kx_plan *plan, long long max_cycles, kx_stream stream) {
+    if (int rc = check_plan(plan)) return rc;
+    if (max_cycles < 1 || max_cycles > 2000000000LL) return set_error(KX_ERR_ARG, "kx_selftest_wait: bad limit");
+    return selftest_wait(plan, max_cycles, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int kx_batch_create(int n_sys, kx_plan *const *plans, const int *n_orb, kx_batch **out) {
+    if (n_sys < 1 || !plans || !n_orb || !out) return set_error(KX_ERR_ARG, "kx_batch_create: bad arguments");
+    *out = nullptr;
+    for (int i = 0; i < n_sys; ++i) {
+        if (!plans[i]) return set_error(KX_ERR_ARG, "kx_batch_create: NULL plan");
+        if (n_orb[i] < 1 || n_orb[i] > 4096) return set_error(KX_ERR_ARG, "kx_batch_create: n_orb out of range");
+        for (int j = 0; j < i; ++j)
+            if (plans[j] == plans[i] && n_orb[j] != n_orb[i])
+                return set_error(KX_ERR_ARG, "kx_batch_create: a plan shared by two systems needs one n_orb");
+    }
+    kx_batch *b = new (std::nothrow) kx_batch_s();
+    if (!b) return set_error(KX_ERR_NOMEM, "kx_batch_create: host allocation failed");
+    b->plans.assign(plans, plans + n_sys);
+    b->n_orb.assign(n_orb, n_orb + n_sys);
+    for (int i = 0; i < n_sys; ++i) {
+        int rc = reserve(plans[i], n_orb[i]);
+        if (rc) {
+            delete b;
+            return rc;
+        }
+    }
+    cudaGetDevice(&b->device);
+    cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete b;
+        return cuda_error(e, "kx_batch_create: stream");
+    }
+    *out = b;
+    return KX_OK;
+}
+
+int kx_batch_run(kx_batch *batch, const double *const *psi, double *const *vx_psi, double *e_x, kx_stream stream) {
+    if (!batch || !psi || !vx_psi) return set_error(KX_ERR_ARG, "kx_batch_run: bad arguments");
+    const int n = (int)batch->plans.size();
+    bool same = batch->exec != nullptr && batch->last_ex == e_x;
+    for (int i = 0; same && i < n; ++i) same = batch->last_psi[i] == psi[i] && batch->last_vx[i] == vx_psi[i];
+    if (!same) {
+        if (batch->exec) cudaGraphExecDestroy(batch->exec);
+        if (batch->graph) cudaGraphDestroy(batch->graph);
+        batch->exec = nullptr;
+        batch->graph = nullptr;
+        KX_CUDA_TRY(cudaStreamBeginCapture(batch->cap, cudaStreamCaptureModeThreadLocal));
+        int rc = KX_OK;
+        for (int i = 0; i < n && rc == KX_OK; ++i)
+            rc = dispatch_vx(batch->plans[i], batch->n_orb[i], psi[i], nullptr, vx_psi[i], e_x ? e_x + i : nullptr,
+                             false, batch->cap);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(batch->cap, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_error(e, "kx_batch_run: capture");
+        batch->graph = g;
+        e = cudaGraphInstantiate(&batch->exec, g, 0);
+        if (e != cudaSuccess) return cuda_error(e, "kx_batch_run: instantiate");
+        batch->last_psi.assign(psi, psi + n);
+        batch->last_vx.assign(vx_psi, vx_psi + n);
+        batch->last_ex = e_x;
+    }
+    KX_CUDA_TRY(cudaGraphLaunch(batch->exec, reinterpret_cast<cudaStream_t>(stream)));
+    return KX_OK;
+}
+
+int kx_batch_destroy(kx_batch *batch) {
+    if (!batch) return KX_OK;
+    if (batch->exec) cudaGraphExecDestroy(batch->exec);
+    if (batch->graph) cudaGraphDestroy(batch->graph);
+    if (batch->cap) cudaStreamDestroy(batch->cap);
+    delete batch;
+    return KX_OK;
+}
+
+int kx_autotune(kx_plan *plan, int n_orb, int budget_ms) {
+    if (int rc = check_plan(plan)) return rc;
+    if (n_orb < 1 || n_orb > 4096 || budget_ms < 0) return set_error(KX_ERR_ARG, "kx_autotune: bad arguments");
+    if (plan->precision == KX_FP64) return KX_OK;  // single launch shape
+    const size_t vec = sizeof(double) * (size_t)n_orb * plan->N;
+    double *buf = nullptr;
+    KX_CUDA_TRY(cudaMalloc(&buf, 2 * vec + sizeof(double)));
+    double *psi = buf, *vx = buf + (size_t)n_orb * plan->N, *ex = vx + (size_t)n_orb * plan->N;
+    {
+        // deterministic non-trivial orbitals: a smooth bump per orbital
+        std::vector<double> h((size_t)n_orb * plan->N);
+        for (int k = 0; k < n_orb; ++k)
+            for (size_t x = 0; x < plan->N; ++x) {
+                size_t x1 = x % plan->n[0], x2 = (x / plan->n[0]) % plan->n[1], x3 = x / (plan->n[0] * plan->n[1]);
+                double u = std::sin(3.14159 * (x1 + 1) / (plan->n[0] + 1) * (1 + k % 3)) *
+                           std::sin(3.14159 * (x2 + 1) / (plan->n[1] + 1)) *
+                           std::sin(3.14159 * (x3 + 1) / (plan->n[2] + 1) * (1 + k % 2));
+                h[(size_t)k * plan->N + x] = u;
+            }
+        cudaMemcpy(psi, h.data(), vec, cudaMemcpyHostToDevice);
+    }
+    cudaStream_t s;
+    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const TuneParams orig = plan->tune;
+    TuneParams best = orig;
+    float best_ms = 1e30f;
+    const long P = (long)n_orb * (n_orb + 1) / 2;
+    const int ctas[] = {1, 2, 3, 4};
+    const long chunks[] = {256, 512, 1024, 2048};
+    auto t_start = std::chrono::steady_clock::now();
+    int rc = KX_OK;
+    for (int c : ctas) {
+        for (long ch : chunks) {
+            if (ch > 2 * P && ch != chunks[0]) continue;
+            double elapsed = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+            if (elapsed > budget_ms && best_ms < 1e30f) break;
+            plan->tune.ctas_per_sm = c;
+            plan->tune.chunk_pairs = ch;
+            rc = tc_vx(plan, n_orb, psi, nullptr, vx, ex, false, s);  // warm-up (also sizes the workspace)
+            if (rc) break;
+            cudaEventRecord(e0, s);
+            rc = tc_vx(plan, n_orb, psi, nullptr, vx, ex, false, s);
+            cudaEventRecord(e1, s);
+            if (rc) break;
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = plan->tune;
+            }
+        }
+        if (rc) break;
+    }
+    plan->tune = rc ? orig : best;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(s);
+    cudaFree(buf);
+    return rc;
+}
+
+}  // extern "C"

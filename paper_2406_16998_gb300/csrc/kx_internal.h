@@ -1,0 +1,115 @@
+// Internal declarations shared by the kronx translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/kronx.h"
+
+namespace kx {
+
+// Thread-local error state behind kx_last_error_detail().
+int set_error(int code, const std::string &msg);
+int cuda_error(cudaError_t e, const char *what);
+
+#define KX_CUDA_TRY(expr)                                   \
+    do {                                                    \
+        cudaError_t _e = (expr);                            \
+        if (_e != cudaSuccess) return ::kx::cuda_error(_e, #expr); \
+    } while (0)
+
+#define KX_LAUNCH_CHECK(what)                               \
+    do {                                                    \
+        cudaError_t _e = cudaGetLastError();                \
+        if (_e != cudaSuccess) return ::kx::cuda_error(_e, what); \
+    } while (0)
+
+constexpr int kMaxN = 128;       // per-axis limit of this build
+constexpr int kTile = 128;       // tcgen05 M (rows of pencils per tile)
+constexpr float kVScale = 16384.f;  // V operand scale 2^14 (|V| <= 1)
+constexpr int kVScaleExp = 14;
+
+inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// Launch-shape choices kept per plan (set by kx_autotune).
+struct TuneParams {
+    int ctas_per_sm = 2;      // resident CTAs per SM for the tensor passes
+    long chunk_pairs = 0;     // pairs per chunk (0 = choose from the workspace budget)
+};
+
+// Device workspace, grown on demand and reused across calls.
+struct Workspace {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace kx
+
+struct kx_plan_s {
+    int n[3];
+    double h[3];
+    int bc[3];
+    int fd_order;
+    int kind;
+    double omega;
+    int precision;
+    int device;
+    int num_sms;
+    size_t N;
+    double dV;
+    double fmax = 0.0;  // max of the f table (set-up)
+    int np[3];  // per-axis size padded to a multiple of 16 (tensor-core K and N)
+
+    // float64 set-up (device)
+    double *d_lam[3] = {nullptr, nullptr, nullptr};   // n[a]
+    double *d_V[3] = {nullptr, nullptr, nullptr};     // n[a] x n[a], row-major V[x][k]
+    double *d_f64 = nullptr;                          // N, index k1 + n1 (k2 + n2 k3)
+    float *d_f32 = nullptr;                           // N, same layout
+
+    // tensor-core operands (device): per axis, hi and lo fp16 blocks of the
+    // np x np zero-padded, 2^14-scaled V in 8x8 core-matrix order
+    __half *d_Vs[3] = {nullptr, nullptr, nullptr};    // [2][np*np]: hi block then lo block
+
+    int *d_status = nullptr;                          // bounded-wait status word
+
+    kx::TuneParams tune;
+    kx::Workspace ws;        // chunk buffers and per-pair scratch
+    kx::Workspace ws_host;   // device staging for kx_vx_apply_host
+    int ws_norb = -1;        // orbital count the pair list currently describes
+    int *d_pairs = nullptr;  // int2 per pair (i, j), symmetric enumeration
+    size_t pairs_cap = 0;
+};
+
+namespace kx {
+
+// ---- set-up (kx_setup.cu)
+int plan_setup(kx_plan *p);          // eig, f tables, split operands (synchronous)
+void plan_free(kx_plan *p);
+
+// ---- workspace (kx_capi.cu)
+int ensure_workspace(kx_plan *p, size_t bytes);
+int ensure_pairs(kx_plan *p, int n_orb, cudaStream_t s);
+
+// ---- FP64 path (kx_fp64.cu)
+int fp64_apply_fL(kx_plan *p, int n_rhs, const double *b, double *x, cudaStream_t s);
+int fp64_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, double *vx, double *ex,
+            bool energy_only, cudaStream_t s);
+size_t fp64_workspace_bytes(const kx_plan *p, long chunk);
+
+// ---- tensor-core path (kx_tc.cu)
+int tc_apply_fL(kx_plan *p, int n_rhs, const double *b, double *x, cudaStream_t s);
+int tc_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, double *vx, double *ex,
+          bool energy_only, cudaStream_t s);
+size_t tc_workspace_bytes(const kx_plan *p, int n_orb, long chunk);
+long tc_default_chunk(const kx_plan *p, int n_orb);
+int selftest_wait(kx_plan *p, long long max_cycles, cudaStream_t s);
+
+// ---- ACE tail (kx_ace.cu)
+int ace_run(kx_plan *p, int n_orb, const double *psi, const double *W, double *xi, double *M_out,
+            cudaStream_t s);
+
+}  // namespace kx

@@ -1,0 +1,700 @@
+// Tensor-core (tcgen05) path of Eq. 19: every mode product runs as 128-row
+// tiles of pencils (M) against the zero-padded n x n eigenvector block (K = N =
+// n rounded up to 16) held in shared memory, accumulating in TMEM.
+//
+// Precision (KX_F16X3): both operands are split into fp16 hi + lo halves after
+// scaling by a power of two (2^14 for V, |V| <= 1; per item for the data), and
+// D = A_hi B_hi + A_hi B_lo + A_lo B_hi is accumulated in fp32.  Each half has
+// 11 significant bits, so the product keeps ~22 bits; the power-of-two scales
+// are undone exactly in the epilogue.
+//
+// Passes over a chunk of items (pair products or caller vectors), all in the
+// natural grid layout (x1 fastest) of fp32 scratch:
+//   X3F  rho = psi_i psi_j (prologue), contract x3 with V3   [A MN-major]
+//   X2F  contract x2 with V2                                  [A MN-major]
+//   X1   contract x1 with V1, scale by f(Lambda) (+ Parseval energy), contract
+//        back with V1^T                                       [A K-major]
+//   X2I  contract k2 with V2^T                                [A MN-major]
+//   X3I  contract k3 with V3^T; epilogue accumulates g_j psi_j phi_ij into row i
+//        and g_i psi_i phi_ij into row j (pair mode) or stores phi (vector mode)
+#include "kx_internal.h"
+#include "kx_tc_ptx.cuh"
+
+#include <algorithm>
+#include <cmath>
+
+namespace kx {
+namespace {
+
+enum PassKind { P_X3F = 0, P_X2F = 1, P_X1 = 2, P_X2I = 3, P_X3I = 4 };
+
+constexpr int kThreads = 256;
+
+struct PassArgs {
+    int n1, n2, n3;
+    int nc;                // contraction length of this pass
+    int np;                // nc rounded up to 16 (MMA K and N)
+    long long rows_pp;     // rows (pencils) per item
+    long long total_rows;  // items * rows_pp
+    long long N;
+    const float *in;
+    float *out;
+    const __half *Vs;      // [2][np*np]: hi block, lo block (8x8 core-matrix order)
+    const int2 *pairs;     // pair mode: (i, j) of each item of the chunk
+    const float *psi32;    // [n_orb][N]
+    const float *orb_max;  // [n_orb] max |psi|
+    const float *src_max;  // vector mode: per-item max |b|
+    int rhs_mode;
+    const float *in_max;   // per-item max |input| (passes after X3F)
+    float *out_max;        // per-item max |output| (nullable)
+    const float *f32;      // f(Lambda), natural layout
+    float mid_bound;       // fmax * sqrt(n1)
+    double *e_partial;     // per-CTA energy partial (nullable)
+    int energy_only;
+    const double *occ;
+    float *acc;            // [n_orb][N] accumulators (pair mode, X3I)
+    double *xout;          // vector mode output of X3I (fp64)
+    int *status;
+    long long timeout_cycles;
+};
+
+__device__ __forceinline__ int scale_exp(float mx) {
+    // e such that mx * 2^e < 2^14 (mx = m 2^k, m in [0.5, 1)  =>  e = 14 - k)
+    int k = 0;
+    if (mx > 0.f && isfinite(mx)) frexpf(mx, &k);
+    return 14 - k;
+}
+
+__device__ __forceinline__ void split8(const float *v, uint4 &hi, uint4 &lo) {
+    __half2 h[4], l[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        __half2 hh = __floats2half2_rn(v[2 * i], v[2 * i + 1]);
+        float2 hf = __half22float2(hh);
+        h[i] = hh;
+        l[i] = __floats2half2_rn(v[2 * i] - hf.x, v[2 * i + 1] - hf.y);
+    }
+    hi = *reinterpret_cast<uint4 *>(h);
+    lo = *reinterpret_cast<uint4 *>(l);
+}
+
+__device__ __forceinline__ void ld8(const float *p, float *v) {
+    float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+    float4 b = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+
+template <int PASS>
+__device__ __forceinline__ float item_in_max(const PassArgs &a, long long item) {
+    if (PASS == P_X3F) {
+        if (a.rhs_mode) return a.src_max[item];
+        int2 ij = a.pairs[item];
+        return a.orb_max[ij.x] * a.orb_max[ij.y];
+    }
+    return a.in_max[item];
+}
+
+// Stage one 128-row tile of the A operand (scaled, split) into shared memory.
+template <int PASS>
+__device__ __forceinline__ void load_tile(const PassArgs &a, long long tile, uint8_t *Ahi, uint8_t *Alo) {
+    const int kp = a.np;
+    const int tid = threadIdx.x;
+    if (PASS == P_X1) {
+        // K-major: element (m, k) at (m/8)*(kp*16) + (k/8)*128 + (m%8)*16 + (k%8)*2.
+        const int nkc = kp >> 3;
+        const int ntask = 128 * nkc;
+        for (int t = tid; t < ntask; t += blockDim.x) {
+            const int mi = t & 7;
+            const int kc = (t >> 3) % nkc;
+            const int mg = (t >> 3) / nkc;
+            const long long R = tile * 128 + mg * 8 + mi;
+            float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (R < a.total_rows && kc * 8 < a.nc) {
+                const long long item = R / a.rows_pp, local = R % a.rows_pp;
+                ld8(a.in + item * a.N + local * a.n1 + kc * 8, v);
+                const float s = ldexpf(1.f, scale_exp(item_in_max<PASS>(a, item)));
+#pragma unroll
+                for (int c = 0; c < 8; ++c) v[c] *= s;
+            }
+            uint4 hi, lo;
+            split8(v, hi, lo);
+            const int off = mg * (kp * 16) + kc * 128 + mi * 16;
+            *reinterpret_cast<uint4 *>(Ahi + off) = hi;
+            *reinterpret_cast<uint4 *>(Alo + off) = lo;
+        }
+    } else {
+        // MN-major: element (m, k) at (m/8)*128 + (k/8)*2048 + (k%8)*16 + (m%8)*2.
+        const int ntask = 16 * kp;
+        const long long n12 = (long long)a.n1 * a.n2;
+        for (int t = tid; t < ntask; t += blockDim.x) {
+            const int ki = t & 7;
+            const int g = (t >> 3) & 15;
+            const int kg = t >> 7;
+            const int k = kg * 8 + ki;
+            const long long R0 = tile * 128 + g * 8;
+            float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (R0 < a.total_rows && k < a.nc) {
+                const long long item = R0 / a.rows_pp, local = R0 % a.rows_pp;
+                const float s = ldexpf(1.f, scale_exp(item_in_max<PASS>(a, item)));
+                if (PASS == P_X3F) {
+                    const long long x = (long long)k * n12 + local;  // (x3 = k, position = local)
+                    if (a.rhs_mode) {
+                        ld8(a.in + item * a.N + x, v);
+                    } else {
+                        const int2 ij = a.pairs[item];
+                        float u[8];
+                        ld8(a.psi32 + (long long)ij.x * a.N + x, v);
+                        ld8(a.psi32 + (long long)ij.y * a.N + x, u);
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) v[c] *= u[c];
+                    }
+                } else if (PASS == P_X2F || PASS == P_X2I) {
+                    const long long k3 = local / a.n1, x1 = local % a.n1;  // rows (k3, x1)
+                    ld8(a.in + item * a.N + k3 * n12 + (long long)k * a.n1 + x1, v);
+                } else {  // P_X3I: rows = positions, K = k3
+                    ld8(a.in + item * a.N + (long long)k * n12 + local, v);
+                }
+#pragma unroll
+                for (int c = 0; c < 8; ++c) v[c] *= s;
+            }
+            uint4 hi, lo;
+            split8(v, hi, lo);
+            const int off = g * 128 + kg * 2048 + ki * 16;
+            *reinterpret_cast<uint4 *>(Ahi + off) = hi;
+            *reinterpret_cast<uint4 *>(Alo + off) = lo;
+        }
+    }
+}
+
+// D = A_hi B_hi + A_hi B_lo + A_lo B_hi over K = np (single issuing thread).
+__device__ __forceinline__ void issue_split_mma(uint32_t tmem_d, uint32_t a_hi, uint32_t a_lo, bool a_kmajor,
+                                                uint32_t v_hi, uint32_t v_lo, bool inverse, int np) {
+    const uint32_t idesc = ptx::idesc_f16(128, np, a_kmajor ? 0 : 1, inverse ? 0 : 1);
+    const uint32_t a_lbo = a_kmajor ? 128u : 2048u;
+    const uint32_t a_sbo = a_kmajor ? (uint32_t)(np * 16) : 128u;
+    const uint32_t a_step = a_kmajor ? 256u : 4096u;
+    // V stored as 8x8 core matrices, row block of 8 x-rows = np*16 bytes.
+    //   forward  (B[x][k] = V[x][k]): MN-major, K (=x) stride np*16, N (=k) stride 128
+    //   inverse  (B[k][x] = V[x][k]): K-major,  K (=k) stride 128,   N (=x) stride np*16
+    const uint32_t b_lbo = inverse ? 128u : (uint32_t)(np * 16);
+    const uint32_t b_sbo = inverse ? (uint32_t)(np * 16) : 128u;
+    const uint32_t b_step = inverse ? 256u : (uint32_t)(np * 32);
+    const int nks = np >> 4;
+    for (int ks = 0; ks < nks; ++ks) {
+        const uint64_t ah = ptx::sdesc(a_hi + ks * a_step, a_lbo, a_sbo);
+        const uint64_t al = ptx::sdesc(a_lo + ks * a_step, a_lbo, a_sbo);
+        const uint64_t bh = ptx::sdesc(v_hi + ks * b_step, b_lbo, b_sbo);
+        const uint64_t bl = ptx::sdesc(v_lo + ks * b_step, b_lbo, b_sbo);
+        ptx::mma_f16(tmem_d, ah, bh, idesc, ks > 0 ? 1u : 0u);
+        ptx::mma_f16(tmem_d, ah, bl, idesc, 1u);
+        ptx::mma_f16(tmem_d, al, bh, idesc, 1u);
+    }
+}
+
+__device__ __forceinline__ bool wait_mma(uint64_t *bar, uint32_t phase, const PassArgs &a, volatile int *flag) {
+    if (threadIdx.x == 0) {
+        if (!ptx::mbar_wait_bounded(bar, phase, a.timeout_cycles)) {
+            *flag = 1;
+            atomicExch(a.status, KX_ERR_TIMEOUT);
+        }
+    }
+    __syncthreads();
+    return *flag == 0;
+}
+
+__device__ __forceinline__ void track_max(float *out_max, long long item, float m, bool valid) {
+    if (out_max == nullptr) return;
+    const long long item0 = __shfl_sync(0xffffffffu, item, 0);
+    const bool same = __all_sync(0xffffffffu, !valid || item == item0);
+    if (same) {
+        float r = valid ? m : 0.f;
+        for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
+        if ((threadIdx.x & 31) == 0 && r > 0.f) atomicMax(reinterpret_cast<int *>(out_max + item0), __float_as_int(r));
+    } else if (valid && m > 0.f) {
+        atomicMax(reinterpret_cast<int *>(out_max + item), __float_as_int(m));
+    }
+}
+
+template <int PASS>
+__global__ void __launch_bounds__(kThreads, 2) tc_pass_kernel(const PassArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int np = a.np;
+    uint8_t *Ahi = smem;
+    uint8_t *Alo = Ahi + 128 * np * 2;
+    uint8_t *Vhi = Alo + 128 * np * 2;
+    uint8_t *Vlo = Vhi + np * np * 2;
+    __shared__ uint64_t mbar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int s_flag;
+    __shared__ double s_red[kThreads / 32];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) {
+        ptx::tmem_alloc(&tmem_slot, 128);
+        ptx::tmem_relinquish();
+    }
+    if (tid == 0) {
+        ptx::mbar_init(&mbar, 1);
+        ptx::fence_mbar_init();
+        s_flag = 0;
+    }
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(a.Vs);
+        uint4 *dst = reinterpret_cast<uint4 *>(Vhi);
+        const int n16 = (2 * np * np * 2) / 16;
+        for (int i = tid; i < n16; i += blockDim.x) dst[i] = __ldg(src + i);
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    const uint32_t sAhi = ptx::smem_u32(Ahi), sAlo = ptx::smem_u32(Alo);
+    const uint32_t sVhi = ptx::smem_u32(Vhi), sVlo = ptx::smem_u32(Vlo);
+    const int q = warp & 3, half = warp >> 2;
+    const int m = 32 * q + lane;                       // TMEM lane == tile row of this thread
+    const uint32_t t_row = tmem + ((uint32_t)(32 * q) << 16);
+    const long long n12 = (long long)a.n1 * a.n2;
+    const int nchunk = np >> 3;
+
+    uint32_t phase = 0;
+    double e_acc = 0.0;
+    bool ok = true;
+    const long long n_tiles = (a.total_rows + 127) / 128;
+    for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        load_tile<PASS>(a, tile, Ahi, Alo);
+        ptx::fence_proxy_async_smem();
+        ptx::tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            ptx::tc_fence_after();
+            const bool inv = (PASS == P_X2I || PASS == P_X3I);
+            issue_split_mma(tmem, sAhi, sAlo, PASS == P_X1, sVhi, sVlo, inv, np);
+            ptx::mma_commit(&mbar);
+        }
+        ok = wait_mma(&mbar, phase, a, &s_flag);
+        phase ^= 1;
+        if (!ok) break;
+        ptx::tc_fence_after();
+
+        const long long R = tile * 128 + m;
+        const bool valid = R < a.total_rows;
+        const long long item = valid ? R / a.rows_pp : 0;
+        const long long local = valid ? R % a.rows_pp : 0;
+        const float in_mx = valid ? item_in_max<PASS>(a, item) : 0.f;
+        const int e_in = scale_exp(in_mx);
+        const float unscale = ldexpf(1.f, -(e_in + kVScaleExp));
+        float my_max = 0.f;
+
+        if (PASS == P_X1) {
+            // forward x1 done: Y = D * unscale; energy; X = f Y; split into the K-major A buffer
+            const float mid_mx = a.mid_bound * in_mx;
+            const int e_mid = scale_exp(mid_mx);
+            const float s_mid = ldexpf(1.f, e_mid);
+            double w = 0.0;
+            if (valid && a.e_partial != nullptr && !a.rhs_mode) {
+                int2 ij = a.pairs[item];
+                w = (ij.x == ij.y) ? 1.0 : 2.0;
+                if (a.occ) w *= a.occ[ij.x] * a.occ[ij.y];
+            }
+            float e_row = 0.f;
+            for (int c8 = half; c8 < nchunk; c8 += 2) {
+                float v[8];
+                ptx::tmem_ld8(t_row + 8 * c8, v);
+                const bool cvalid = valid && (8 * c8 < a.nc);
+                float fk[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                if (cvalid) ld8(a.f32 + local * a.n1 + 8 * c8, fk);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const float y = v[c] * unscale;
+                    e_row = fmaf(fk[c] * y, y, e_row);
+                    v[c] = fk[c] * y * s_mid;
+                }
+                if (!a.energy_only) {
+                    uint4 hi, lo;
+                    split8(v, hi, lo);
+                    const int off = (m >> 3) * (np * 16) + c8 * 128 + (m & 7) * 16;
+                    *reinterpret_cast<uint4 *>(Ahi + off) = hi;
+                    *reinterpret_cast<uint4 *>(Alo + off) = lo;
+                }
+            }
+            e_acc += w * (double)e_row;
+            if (!a.energy_only) {
+                ptx::fence_proxy_async_smem();
+                ptx::tc_fence_before();
+                __syncthreads();
+                if (tid == 0) {
+                    ptx::tc_fence_after();
+                    issue_split_mma(tmem, sAhi, sAlo, true, sVhi, sVlo, true, np);
+                    ptx::mma_commit(&mbar);
+                }
+                ok = wait_mma(&mbar, phase, a, &s_flag);
+                phase ^= 1;
+                if (!ok) break;
+                ptx::tc_fence_after();
+                const float unscale2 = ldexpf(1.f, -(e_mid + kVScaleExp));
+                for (int c8 = half; c8 < nchunk; c8 += 2) {
+                    float v[8];
+                    ptx::tmem_ld8(t_row + 8 * c8, v);
+                    if (valid && 8 * c8 < a.nc) {
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) {
+                            v[c] *= unscale2;
+                            my_max = fmaxf(my_max, fabsf(v[c]));
+                        }
+                        float4 *dst = reinterpret_cast<float4 *>(a.out + item * a.N + local * a.n1 + 8 * c8);
+                        dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+                        dst[1] = make_float4(v[4], v[5], v[6], v[7]);
+                    }
+                }
+                track_max(a.out_max, item, my_max, valid);
+            }
+        } else if (PASS == P_X3I) {
+            int2 ij = make_int2(0, 0);
+            float gi = 1.f, gj = 1.f;
+            if (valid && !a.rhs_mode) {
+                ij = a.pairs[item];
+                if (a.occ) {
+                    gi = (float)a.occ[ij.x];
+                    gj = (float)a.occ[ij.y];
+                }
+            }
+            for (int c8 = half; c8 < nchunk; c8 += 2) {
+                float v[8];
+                ptx::tmem_ld8(t_row + 8 * c8, v);
+                if (!valid) continue;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const int col = 8 * c8 + c;
+                    if (col >= a.nc) break;
+                    const float phi = v[c] * unscale;
+                    const long long idx = (long long)col * n12 + local;
+                    if (a.rhs_mode) {
+                        a.xout[item * a.N + idx] = (double)phi;
+                    } else {
+                        const float pj = __ldg(a.psi32 + (long long)ij.y * a.N + idx);
+                        ptx::red_add_f32(a.acc + (long long)ij.x * a.N + idx, gj * pj * phi);
+                        if (ij.x != ij.y) {
+                            const float pi = __ldg(a.psi32 + (long long)ij.x * a.N + idx);
+                            ptx::red_add_f32(a.acc + (long long)ij.y * a.N + idx, gi * pi * phi);
+                        }
+                    }
+                }
+            }
+        } else {
+            // transposed write into the natural layout of the next pass's input
+            for (int c8 = half; c8 < nchunk; c8 += 2) {
+                float v[8];
+                ptx::tmem_ld8(t_row + 8 * c8, v);
+                if (!valid) continue;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const int col = 8 * c8 + c;
+                    if (col >= a.nc) break;
+                    const float y = v[c] * unscale;
+                    my_max = fmaxf(my_max, fabsf(y));
+                    long long dst;
+                    if (PASS == P_X3F) {
+                        dst = (long long)col * n12 + local;  // [k3][position]
+                    } else {
+                        const long long k3 = local / a.n1, x1 = local % a.n1;
+                        dst = k3 * n12 + (long long)col * a.n1 + x1;  // [k3][k2 or x2][x1]
+                    }
+                    a.out[item * a.N + dst] = y;
+                }
+            }
+            track_max(a.out_max, item, my_max, valid);
+        }
+        ptx::tc_fence_before();
+        __syncthreads();
+    }
+    if (!ok) {
+        // a wait ran out: give the outstanding MMAs one more bounded wait before freeing TMEM
+        if (tid == 0) ptx::mbar_wait_bounded(&mbar, phase ^ 1, a.timeout_cycles);
+        __syncthreads();
+    }
+    if (a.e_partial != nullptr) {
+        double e = e_acc;
+        for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+        if (lane == 0) s_red[warp] = e;
+        __syncthreads();
+        if (tid == 0) {
+            double s = 0.0;
+            for (int w = 0; w < kThreads / 32; ++w) s += s_red[w];
+            a.e_partial[blockIdx.x] = s;
+        }
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        ptx::tc_fence_after();
+        ptx::tmem_dealloc(tmem, 128);
+    }
+}
+
+// psi (fp64) -> psi32 and per-vector max |value|.
+__global__ void prep_kernel(const double *__restrict__ src, float *__restrict__ dst, float *__restrict__ vmax,
+                            int n_vec, long long N) {
+    const int v = blockIdx.y;
+    float m = 0.f;
+    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < N; x += (long long)gridDim.x * blockDim.x) {
+        const float f = (float)src[(long long)v * N + x];
+        dst[(long long)v * N + x] = f;
+        m = fmaxf(m, fabsf(f));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(reinterpret_cast<int *>(vmax + v), __float_as_int(m));
+}
+
+__global__ void finalize_kernel(const float *__restrict__ acc, double *__restrict__ vx, long long n) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+        vx[e] = -(double)acc[e];
+}
+
+__global__ void energy_add_kernel(const double *__restrict__ partial, int n, double factor, double *e_x) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int b = 0; b < n; ++b) s += partial[b];
+        *e_x += factor * s;
+    }
+}
+
+// Failure-path self-test: wait on an mbarrier phase that nothing completes; the
+// bounded wait gives up and the status word records KX_ERR_TIMEOUT.
+__global__ void selftest_wait_kernel(long long max_cycles, int *status) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        ptx::mbar_init(&bar, 1);
+        ptx::fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !ptx::mbar_wait_bounded(&bar, 0, max_cycles)) atomicExch(status, KX_ERR_TIMEOUT);
+}
+
+size_t pass_smem(int np) { return (size_t)2 * 128 * np * 2 + (size_t)2 * np * np * 2 + 1024; }
+
+template <int PASS>
+int launch_pass(const kx_plan *p, PassArgs a, int axis, cudaStream_t s, int *grid_out) {
+    a.nc = p->n[axis];
+    a.np = p->np[axis];
+    a.Vs = p->d_Vs[axis];
+    a.n1 = p->n[0];
+    a.n2 = p->n[1];
+    a.n3 = p->n[2];
+    a.N = (long long)p->N;
+    a.status = p->d_status;
+    a.timeout_cycles = 4000000000LL;  // ~2 s at the SM clock
+    const size_t smem = pass_smem(a.np);
+    KX_CUDA_TRY(cudaFuncSetAttribute(tc_pass_kernel<PASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    KX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_pass_kernel<PASS>, kThreads, smem));
+    per_sm = std::max(1, std::min(per_sm, std::min(p->tune.ctas_per_sm, 4)));
+    const long long n_tiles = (a.total_rows + 127) / 128;
+    const int grid = (int)std::max(1LL, std::min<long long>(n_tiles, (long long)p->num_sms * per_sm));
+    if (grid_out) *grid_out = grid;
+    tc_pass_kernel<PASS><<<grid, kThreads, smem, s>>>(a);
+    KX_LAUNCH_CHECK("tc_pass_kernel launch");
+    return KX_OK;
+}
+
+struct TcLayout {
+    float *psi32, *acc, *T0, *T1, *orb_max, *mx;
+    double *partial;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+TcLayout carve(kx_plan *p, int n_vec, long chunk, bool with_acc) {
+    TcLayout L{};
+    uint8_t *b = reinterpret_cast<uint8_t *>(p->ws.ptr);
+    size_t off = 0;
+    auto take = [&](size_t bytes) { uint8_t *r = b + off; off += align256(bytes); return r; };
+    L.psi32 = (float *)take(sizeof(float) * (size_t)n_vec * p->N);
+    L.acc = with_acc ? (float *)take(sizeof(float) * (size_t)n_vec * p->N) : nullptr;
+    L.T0 = (float *)take(sizeof(float) * (size_t)chunk * p->N);
+    L.T1 = (float *)take(sizeof(float) * (size_t)chunk * p->N);
+    L.orb_max = (float *)take(sizeof(float) * (size_t)n_vec);
+    L.mx = (float *)take(sizeof(float) * 4 * (size_t)chunk);
+    L.partial = (double *)take(sizeof(double) * 4096);
+    return L;
+}
+
+}  // namespace
+
+long tc_default_chunk(const kx_plan *p, int n_orb) {
+    if (p->tune.chunk_pairs > 0) return p->tune.chunk_pairs;
+    const size_t budget = (size_t)4 << 30;  // both chunk buffers together
+    long c = (long)std::max<size_t>(1, budget / (2 * p->N * sizeof(float)));
+    return std::max(1L, std::min<long>(c, 2048));
+}
+
+size_t tc_workspace_bytes(const kx_plan *p, int n_vec, long chunk) {
+    return align256(sizeof(float) * (size_t)n_vec * p->N) * 2 + align256(sizeof(float) * (size_t)chunk * p->N) * 2 +
+           align256(sizeof(float) * n_vec) + align256(sizeof(float) * 4 * chunk) + align256(sizeof(double) * 4096) +
+           4096;
+}
+
+static float fmax_sqrt(const kx_plan *p) {
+    // bound of |f(Lambda) (V1^T y)| / max|y| used for the mid-pass split scale
+    return (float)(p->fmax * std::sqrt((double)p->n[0]) * 1.0001);
+}
+
+int tc_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, double *vx, double *ex, bool energy_only,
+          cudaStream_t s) {
+    int rc = ensure_pairs(p, n_orb, s);
+    if (rc) return rc;
+    const long P = (long)n_orb * (n_orb + 1) / 2;
+    const long chunk = std::min<long>(tc_default_chunk(p, n_orb), P);
+    rc = ensure_workspace(p, tc_workspace_bytes(p, n_orb, chunk));
+    if (rc) return rc;
+    TcLayout L = carve(p, n_orb, chunk, !energy_only);
+    const long long N = (long long)p->N;
+
+    KX_CUDA_TRY(cudaMemsetAsync(L.orb_max, 0, sizeof(float) * n_orb, s));
+    {
+        dim3 g((unsigned)std::min<long long>((N + 255) / 256, 64), (unsigned)n_orb);
+        prep_kernel<<<g, 256, 0, s>>>(psi, L.psi32, L.orb_max, n_orb, N);
+        KX_LAUNCH_CHECK("prep_kernel launch");
+    }
+    if (!energy_only) KX_CUDA_TRY(cudaMemsetAsync(L.acc, 0, sizeof(float) * (size_t)n_orb * N, s));
+    if (ex) KX_CUDA_TRY(cudaMemsetAsync(ex, 0, sizeof(double), s));
+    const int2 *pairs = reinterpret_cast<const int2 *>(p->d_pairs);
+    const float mid_bound = fmax_sqrt(p);
+
+    for (long c0 = 0; c0 < P; c0 += chunk) {
+        const long R = std::min<long>(chunk, P - c0);
+        KX_CUDA_TRY(cudaMemsetAsync(L.mx, 0, sizeof(float) * 4 * chunk, s));
+        float *mx1 = L.mx, *mx2 = L.mx + chunk, *mx3 = L.mx + 2 * chunk, *mx4 = L.mx + 3 * chunk;
+        PassArgs a{};
+        a.pairs = pairs + c0;
+        a.psi32 = L.psi32;
+        a.orb_max = L.orb_max;
+        a.occ = occ;
+        a.f32 = p->d_f32;
+        a.mid_bound = mid_bound;
+
+        a.rows_pp = (long long)p->n[0] * p->n[1];
+        a.total_rows = R * a.rows_pp;
+        a.out = L.T0;
+        a.out_max = mx1;
+        if ((rc = launch_pass<P_X3F>(p, a, 2, s, nullptr))) return rc;
+
+        a.rows_pp = (long long)p->n[2] * p->n[0];
+        a.total_rows = R * a.rows_pp;
+        a.in = L.T0;
+        a.in_max = mx1;
+        a.out = L.T1;
+        a.out_max = mx2;
+        if ((rc = launch_pass<P_X2F>(p, a, 1, s, nullptr))) return rc;
+
+        a.rows_pp = (long long)p->n[2] * p->n[1];
+        a.total_rows = R * a.rows_pp;
+        a.in = L.T1;
+        a.in_max = mx2;
+        a.out = L.T0;
+        a.out_max = mx3;
+        a.e_partial = ex ? L.partial : nullptr;
+        a.energy_only = energy_only ? 1 : 0;
+        int grid = 0;
+        if ((rc = launch_pass<P_X1>(p, a, 0, s, &grid))) return rc;
+        if (ex) {
+            energy_add_kernel<<<1, 32, 0, s>>>(L.partial, grid, -0.5 * p->dV, ex);
+            KX_LAUNCH_CHECK("energy_add_kernel launch");
+        }
+        a.e_partial = nullptr;
+        a.energy_only = 0;
+        if (energy_only) continue;
+
+        a.rows_pp = (long long)p->n[2] * p->n[0];
+        a.total_rows = R * a.rows_pp;
+        a.in = L.T0;
+        a.in_max = mx3;
+        a.out = L.T1;
+        a.out_max = mx4;
+        if ((rc = launch_pass<P_X2I>(p, a, 1, s, nullptr))) return rc;
+
+        a.rows_pp = (long long)p->n[0] * p->n[1];
+        a.total_rows = R * a.rows_pp;
+        a.in = L.T1;
+        a.in_max = mx4;
+        a.out = nullptr;
+        a.out_max = nullptr;
+        a.acc = L.acc;
+        if ((rc = launch_pass<P_X3I>(p, a, 2, s, nullptr))) return rc;
+    }
+    if (!energy_only) {
+        const long long n = (long long)n_orb * N;
+        finalize_kernel<<<(unsigned)std::min<long long>((n + 255) / 256, 8LL * p->num_sms), 256, 0, s>>>(L.acc, vx, n);
+        KX_LAUNCH_CHECK("finalize_kernel launch");
+    }
+    return KX_OK;
+}
+
+int selftest_wait(kx_plan *p, long long max_cycles, cudaStream_t s) {
+    selftest_wait_kernel<<<1, 32, 0, s>>>(max_cycles, p->d_status);
+    KX_LAUNCH_CHECK("selftest_wait_kernel launch");
+    return KX_OK;
+}
+
+int tc_apply_fL(kx_plan *p, int n_rhs, const double *b, double *x, cudaStream_t s) {
+    const long chunk = std::min<long>(tc_default_chunk(p, 1), n_rhs);
+    int rc = ensure_workspace(p, tc_workspace_bytes(p, (int)chunk, chunk));
+    if (rc) return rc;
+    TcLayout L = carve(p, (int)chunk, chunk, false);
+    const long long N = (long long)p->N;
+    const float mid_bound = fmax_sqrt(p);
+    for (long c0 = 0; c0 < n_rhs; c0 += chunk) {
+        const long R = std::min<long>(chunk, n_rhs - c0);
+        KX_CUDA_TRY(cudaMemsetAsync(L.orb_max, 0, sizeof(float) * R, s));
+        KX_CUDA_TRY(cudaMemsetAsync(L.mx, 0, sizeof(float) * 4 * chunk, s));
+        dim3 g((unsigned)std::min<long long>((N + 255) / 256, 64), (unsigned)R);
+        prep_kernel<<<g, 256, 0, s>>>(b + c0 * N, L.psi32, L.orb_max, (int)R, N);
+        KX_LAUNCH_CHECK("prep_kernel launch");
+        float *mx1 = L.mx, *mx2 = L.mx + chunk, *mx3 = L.mx + 2 * chunk, *mx4 = L.mx + 3 * chunk;
+        PassArgs a{};
+        a.rhs_mode = 1;
+        a.f32 = p->d_f32;
+        a.mid_bound = mid_bound;
+        a.src_max = L.orb_max;
+
+        a.rows_pp = (long long)p->n[0] * p->n[1];
+        a.total_rows = R * a.rows_pp;
+        a.in = L.psi32;
+        a.out = L.T0;
+        a.out_max = mx1;
+        if ((rc = launch_pass<P_X3F>(p, a, 2, s, nullptr))) return rc;
+        a.rows_pp = (long long)p->n[2] * p->n[0];
+        a.total_rows = R * a.rows_pp;
+        a.in = L.T0;
+        a.in_max = mx1;
+        a.out = L.T1;
+        a.out_max = mx2;
+        if ((rc = launch_pass<P_X2F>(p, a, 1, s, nullptr))) return rc;
+        a.rows_pp = (long long)p->n[2] * p->n[1];
+        a.total_rows = R * a.rows_pp;
+        a.in = L.T1;
+        a.in_max = mx2;
+        a.out = L.T0;
+        a.out_max = mx3;
+        if ((rc = launch_pass<P_X1>(p, a, 0, s, nullptr))) return rc;
+        a.rows_pp = (long long)p->n[2] * p->n[0];
+        a.total_rows = R * a.rows_pp;
+        a.in = L.T0;
+        a.in_max = mx3;
+        a.out = L.T1;
+        a.out_max = mx4;
+        if ((rc = launch_pass<P_X2I>(p, a, 1, s, nullptr))) return rc;
+        a.rows_pp = (long long)p->n[0] * p->n[1];
+        a.total_rows = R * a.rows_pp;
+        a.in = L.T1;
+        a.in_max = mx4;
+        a.out = nullptr;
+        a.out_max = nullptr;
+        a.xout = x + c0 * N;
+        if ((rc = launch_pass<P_X3I>(p, a, 2, s, nullptr))) return rc;
+    }
+    return KX_OK;
+}
+
+}  // namespace kx

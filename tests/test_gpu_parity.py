@@ -1,0 +1,299 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Tolerances (stated once, used everywhere below):
+  KX_FP64  : max-norm relative 1e-11 (float64 end to end; only summation order
+             differs from the oracle).
+  KX_F16X3 : Vx psi and f(L) b max-norm relative <= 1e-5, E_x relative <= 1e-6
+             (the accuracy target of the split-precision path; each fp16 hi/lo
+             product carries ~2^-22 relative error, six chained products plus fp32
+             accumulation stay well inside these bounds).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from workloads import DIRICHLET as D, PERIODIC as P, UNSCREENED as U, SCREENED as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {0: dict(vx=1e-11, ex=1e-11, fl=1e-11), 1: dict(vx=1e-5, ex=1e-6, fl=1e-5)}
+
+
+@pytest.fixture(scope="module")
+def kx():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2406_16998_gb300 import build
+    build.build()
+    import paper_2406_16998_gb300 as k
+    return k
+
+
+def relmax(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def system(n, h, bc, kind, n_orb, seed, centres=4):
+    return workloads.System(n=n, h=h, bc=bc, kernel=kind, n_orb=n_orb, n_centres=centres, seed=seed)
+
+
+# Grids chosen to span several 128-row tiles with ragged tails, padded K/N
+# (sizes not multiples of 16), non-cubic shapes and mixed boundary conditions.
+SMALL = [
+    ((24, 40, 16), (0.45, 0.4, 0.5), (D, D, D), U, 5),
+    ((16, 24, 48), (0.5, 0.5, 0.4), (P, P, D), U, 4),
+    ((40, 32, 24), (0.4, 0.45, 0.5), (P, P, P), S, 4),
+    ((8, 16, 8), (0.6, 0.5, 0.6), (D, P, D), S, 3),
+    ((56, 8, 16), (0.3, 0.6, 0.5), (D, D, P), S, 2),
+]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("case", range(len(SMALL)))
+def test_vx_apply_matches_oracle(kx, prec, case):
+    n, h, bc, kind, n_orb = SMALL[case]
+    sysd = system(n, h, bc, kind, n_orb, 100 + case)
+    psi = workloads.make_orbitals(sysd)
+    op = oracle.Plan(n, h, bc, kind)
+    vx_ref, ex_ref = oracle.vx_apply(op, psi)
+    plan = kx.Plan(n, h, bc, kind, precision=prec)
+    vx, ex = kx.kx_vx_apply(plan, dev(psi.T))
+    torch.cuda.synchronize()
+    assert plan.status() == kx.KX_OK
+    vx = vx.cpu().numpy().T
+    assert relmax(vx, vx_ref) < TOL[prec]["vx"]
+    assert abs(ex.item() - ex_ref) < TOL[prec]["ex"] * abs(ex_ref)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_energy_only_and_occupations(kx, prec):
+    n, h, bc, kind, n_orb = SMALL[0]
+    sysd = system(n, h, bc, kind, n_orb, 7)
+    psi = workloads.make_orbitals(sysd)
+    occ = np.array([1.0, 0.9, 0.6, 0.35, 0.1])
+    op = oracle.Plan(n, h, bc, kind)
+    vx_ref, ex_ref = oracle.vx_apply(op, psi, occ)
+    plan = kx.Plan(n, h, bc, kind, precision=prec)
+    vx, ex = kx.kx_vx_apply(plan, dev(psi.T), occ=dev(occ))
+    e_only = kx.kx_energy(plan, dev(psi.T), occ=dev(occ))
+    torch.cuda.synchronize()
+    assert relmax(vx.cpu().numpy().T, vx_ref) < TOL[prec]["vx"]
+    assert abs(ex.item() - ex_ref) < TOL[prec]["ex"] * abs(ex_ref)
+    assert abs(e_only.item() - ex_ref) < TOL[prec]["ex"] * abs(ex_ref)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("case", [0, 2, 3])
+def test_apply_fL_matches_oracle(kx, prec, case):
+    n, h, bc, kind, _ = SMALL[case]
+    op = oracle.Plan(n, h, bc, kind)
+    B = workloads.random_field(op.N, 3, 9 + case)
+    X_ref = oracle.apply_fL(op, B)
+    plan = kx.Plan(n, h, bc, kind, precision=prec)
+    X = kx.kx_apply_fL(plan, dev(B.T)).cpu().numpy().T
+    for r in range(3):
+        assert relmax(X[:, r], X_ref[:, r]) < TOL[prec]["fl"]
+
+
+def test_fp64_odd_sizes(kx):
+    n, h, bc = (7, 9, 11), (0.5, 0.45, 0.4), (D, P, D)
+    sysd = system(n, h, bc, S, 3, 17)
+    psi = workloads.make_orbitals(sysd)
+    op = oracle.Plan(n, h, bc, S)
+    vx_ref, ex_ref = oracle.vx_apply(op, psi)
+    plan = kx.Plan(n, h, bc, S, precision=0)
+    vx, ex = kx.kx_vx_apply(plan, dev(psi.T))
+    assert relmax(vx.cpu().numpy().T, vx_ref) < 1e-11
+    assert abs(ex.item() - ex_ref) < 1e-11 * abs(ex_ref)
+
+
+def test_setup_eigendecomposition_and_ftable(kx):
+    n, h, bc, kind = (24, 40, 16), (0.45, 0.4, 0.5), (D, P, D), S
+    op = oracle.Plan(n, h, bc, kind)
+    plan = kx.Plan(n, h, bc, kind, precision=1)
+    for a in range(3):
+        lam, V = plan.eig(a)
+        L = oracle.lap1d(n[a], h[a], bc[a], 12)
+        scale = np.abs(op.lam[a]).max()
+        assert np.max(np.abs(lam - op.lam[a])) < 1e-12 * scale
+        assert np.max(np.abs(L @ V - V * lam)) < 1e-12 * scale
+        assert np.max(np.abs(V.T @ V - np.eye(n[a]))) < 1e-13
+    f = plan.ftable()
+    assert relmax(f, op.fdiag.reshape(-1)) < 1e-12
+
+
+def test_single_orbital_and_tiny_grid(kx):
+    n, h, bc = (8, 8, 8), (0.5,) * 3, (D, D, D)
+    sysd = system(n, h, bc, U, 1, 23)
+    psi = workloads.make_orbitals(sysd)
+    op = oracle.Plan(n, h, bc, U)
+    vx_ref, ex_ref = oracle.vx_apply(op, psi)
+    for prec in (0, 1):
+        plan = kx.Plan(n, h, bc, U, precision=prec)
+        vx, ex = kx.kx_vx_apply(plan, dev(psi.T))
+        assert relmax(vx.cpu().numpy().T, vx_ref) < TOL[prec]["vx"]
+        assert abs(ex.item() - ex_ref) < TOL[prec]["ex"] * abs(ex_ref)
+
+
+def test_max_axis_128(kx):
+    n, h, bc = (128, 8, 16), (0.2, 0.5, 0.5), (D, P, D)
+    sysd = system(n, h, bc, S, 2, 29)
+    psi = workloads.make_orbitals(sysd)
+    op = oracle.Plan(n, h, bc, S)
+    vx_ref, ex_ref = oracle.vx_apply(op, psi)
+    plan = kx.Plan(n, h, bc, S, precision=1)
+    vx, ex = kx.kx_vx_apply(plan, dev(psi.T))
+    assert relmax(vx.cpu().numpy().T, vx_ref) < 1e-5
+    assert abs(ex.item() - ex_ref) < 1e-6 * abs(ex_ref)
+
+
+def test_zero_orbital(kx):
+    n, h, bc = (16, 16, 16), (0.5,) * 3, (D, D, D)
+    sysd = system(n, h, bc, U, 2, 31)
+    psi = workloads.make_orbitals(sysd)
+    psi[:, 1] = 0.0
+    op = oracle.Plan(n, h, bc, U)
+    vx_ref, ex_ref = oracle.vx_apply(op, psi)
+    plan = kx.Plan(n, h, bc, U, precision=1)
+    vx, ex = kx.kx_vx_apply(plan, dev(psi.T))
+    vx = vx.cpu().numpy().T
+    assert np.all(vx[:, 1] == 0.0)
+    assert relmax(vx, vx_ref) < 1e-5 and abs(ex.item() - ex_ref) < 1e-6 * abs(ex_ref)
+
+
+def test_ace_matches_oracle(kx):
+    n, h, bc, kind, n_orb = SMALL[1]
+    sysd = system(n, h, bc, kind, n_orb, 37)
+    psi = workloads.make_orbitals(sysd)
+    op = oracle.Plan(n, h, bc, kind)
+    vx_ref, _ = oracle.vx_apply(op, psi)
+    xi_ref, M_ref, _ = oracle.ace(op, psi, vx_ref)
+    plan = kx.Plan(n, h, bc, kind, precision=0)
+    xi, M = kx.kx_ace(plan, dev(psi.T), dev(vx_ref.T))
+    assert relmax(M.cpu().numpy(), M_ref) < 1e-12
+    assert relmax(xi.cpu().numpy().T, xi_ref) < 1e-10
+
+
+def test_batch_equals_individual_runs(kx):
+    cases = [SMALL[0], SMALL[2], SMALL[3]]
+    plans, psis, refs = [], [], []
+    for c, (n, h, bc, kind, n_orb) in enumerate(cases):
+        sysd = system(n, h, bc, kind, n_orb, 41 + c)
+        psi = workloads.make_orbitals(sysd)
+        plans.append(kx.Plan(n, h, bc, kind, precision=1))
+        psis.append(dev(psi.T))
+        refs.append(oracle.vx_apply(oracle.Plan(n, h, bc, kind), psi))
+    outs = [torch.empty_like(p) for p in psis]
+    ex = torch.empty(len(cases), dtype=torch.float64, device="cuda")
+    b = kx.Batch(plans, [p.shape[0] for p in psis])
+    for _ in range(2):  # second run replays the captured graph
+        b.run(psis, outs, ex)
+    torch.cuda.synchronize()
+    for k, (vx_ref, ex_ref) in enumerate(refs):
+        single, e1 = kx.kx_vx_apply(plans[k], psis[k])
+        assert relmax(outs[k].cpu().numpy().T, vx_ref) < 1e-5
+        assert abs(ex[k].item() - ex_ref) < 1e-6 * abs(ex_ref)
+        assert relmax(outs[k].cpu().numpy(), single.cpu().numpy()) < 1e-6
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_autograd_matches_oracle_gradient(kx, prec):
+    n, h, bc, kind, n_orb = SMALL[3]
+    sysd = system(n, h, bc, kind, n_orb, 43)
+    psi = workloads.make_orbitals(sysd)
+    op = oracle.Plan(n, h, bc, kind)
+    g_ref = oracle.energy_gradient(op, psi)
+    e_ref = oracle.exchange_energy(op, psi)
+    plan = kx.Plan(n, h, bc, kind, precision=prec)
+    x = dev(psi.T).requires_grad_(True)
+    e = kx.exchange_energy(x, plan)
+    e.backward()
+    assert abs(e.item() - e_ref) < TOL[prec]["ex"] * abs(e_ref)
+    assert relmax(x.grad.cpu().numpy().T, g_ref) < TOL[prec]["vx"]
+
+
+def test_autograd_central_differences_fp64(kx):
+    n, h, bc, kind, n_orb = (8, 16, 8), (0.6, 0.5, 0.6), (D, P, D), S, 3
+    sysd = system(n, h, bc, kind, n_orb, 47)
+    psi = workloads.make_orbitals(sysd)
+    plan = kx.Plan(n, h, bc, kind, precision=0)
+    x = dev(psi.T).requires_grad_(True)
+    kx.exchange_energy(x, plan).backward()
+    grad = x.grad.cpu().numpy()
+    rng = np.random.default_rng(3)
+    step = 1e-4
+    for _ in range(16):
+        k, r = int(rng.integers(n_orb)), int(rng.integers(plan.N))
+        pp = psi.T.copy()
+        pm = psi.T.copy()
+        pp[k, r] += step
+        pm[k, r] -= step
+        ep = kx.kx_energy(plan, dev(pp)).item()
+        em = kx.kx_energy(plan, dev(pm)).item()
+        fd = (ep - em) / (2 * step)
+        assert abs(fd - grad[k, r]) < 1e-7 * np.abs(grad).max()
+
+
+def test_failure_paths(kx, monkeypatch):
+    # bounded wait that nothing completes: the kernel gives up, status reports the timeout
+    plan = kx.Plan((8, 8, 8), (0.5,) * 3, (D, D, D), U, precision=1)
+    assert plan.status() == kx.KX_OK
+    kx.kx_selftest_wait(plan, 2_000_000)
+    assert plan.status() == kx.KX_ERR_TIMEOUT
+    assert plan.status() == kx.KX_OK  # cleared by the read
+    # the context is still usable afterwards
+    psi = workloads.make_orbitals(system((8, 8, 8), (0.5,) * 3, (D, D, D), U, 2, 53))
+    vx, ex = kx.kx_vx_apply(plan, dev(psi.T))
+    assert np.isfinite(ex.item())
+    # injected allocation failure on a fresh plan
+    monkeypatch.setenv("KX_FAULT", "alloc")
+    plan2 = kx.Plan((8, 8, 8), (0.5,) * 3, (D, D, D), U, precision=1)
+    with pytest.raises(kx.KxError) as ei:
+        kx.kx_vx_apply(plan2, dev(psi.T))
+    assert ei.value.code == kx.KX_ERR_NOMEM
+    monkeypatch.delenv("KX_FAULT")
+    kx.kx_vx_apply(plan2, dev(psi.T))
+    # singular request
+    with pytest.raises(kx.KxError) as ei:
+        kx.Plan((8, 8, 8), (0.5,) * 3, (P, P, P), U)
+    assert ei.value.code == kx.KX_ERR_SINGULAR
+    # shape checks in the binding
+    with pytest.raises(ValueError):
+        kx.kx_vx_apply(plan, dev(psi.T[:, :-8]))
+
+
+# --------------------------------------------------------------------------
+# Full-size workloads, in the launch configuration the benchmark times:
+# sampled orbitals against the oracle (one orbital's row of pair solves), and
+# E_x through the identity E_x = 1/2 sum_i g_i dV <psi_i, (Vx psi)_i>.
+# --------------------------------------------------------------------------
+def _row_reference(op, psi, i):
+    pairs = [(i, j) for j in range(psi.shape[1])]
+    vx, _ = oracle.vx_apply(op, psi, ordered=True, pairs=pairs)
+    return vx[:, i]
+
+
+@pytest.mark.parametrize("name,sample", [("C2", (0, 37)), ("C3", (5,))])
+def test_full_size_sampled(kx, name, sample):
+    sysd = getattr(workloads, name)
+    psi = workloads.make_orbitals(sysd)
+    op = oracle.Plan(sysd.n, sysd.h, sysd.bc, sysd.kernel, sysd.omega)
+    plan = kx.Plan.for_system(sysd, precision=1)
+    vx, ex = kx.kx_vx_apply(plan, dev(psi.T))
+    torch.cuda.synchronize()
+    assert plan.status() == kx.KX_OK
+    vx_h = vx.cpu().numpy()
+    M_diag = sysd.dV * np.einsum("ij,ij->i", psi.T, vx_h)
+    assert abs(ex.item() - 0.5 * M_diag.sum()) < 1e-6 * abs(ex.item())
+    scale = np.abs(vx_h).max()
+    for i in sample:
+        ref = _row_reference(op, psi, i)
+        assert np.max(np.abs(vx_h[i] - ref)) < 1e-5 * scale

@@ -1,0 +1,330 @@
+"""Benchmark of the exact-exchange apply (Vx psi and E_x) on one GB300.
+
+A step is one kx_vx_apply over the whole workload: the 96^3 isolated-box system
+(Dirichlet, unscreened, 12th-order FD, h = 0.25 bohr, 64 orbitals, 2080
+symmetric pair solves), inputs resident in HBM.  The metric is pair-solves/s of
+the split-precision tensor-core path; the float64 GPU path, the error against
+it, an end-to-end host-buffer run and the FP64 CPU oracle are reported beside.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl kronx|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the workload
+(weak scaling, no data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "pair-solves/s and Vx*psi time, split-precision vs FP64 on 1 GB300 at stated error"
+UNIT = "pair-solves/s"
+SYS = workloads.C2
+WORKLOAD = ("96x96x96 isolated box, Dirichlet, unscreened f=-4pi/lambda, 12th-order FD, h=0.25 bohr, "
+            "64 orbitals, 2080 symmetric pair solves + Vx*psi + E_x per step")
+DATA = "synthetic: seeded s/p Gaussian-sum orbitals on 24 random atom centres, FP64 CholeskyQR2-orthonormalised"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["kronx", "reference"], default="kronx")
+    ap.add_argument("--no-extras", action="store_true", help="skip FP64/e2e/oracle legs (profiling runs)")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), float(d.get("bf16_tflops_sustained", d["bf16_tflops"])), "measured"
+    except Exception:
+        return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms while running."""
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", "--query-gpu=" + ",".join(self.FIELDS),
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.5)
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == len(self.FIELDS):
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            for k, nm in enumerate(names):
+                if r[3 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def dist_setup(n_gpus):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if n_gpus > 1 and world != n_gpus:
+        raise SystemExit(f"--gpus {n_gpus} needs torchrun with {n_gpus} ranks (WORLD_SIZE={world})")
+    if torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(psi, budget_s=12.0):
+    """The FP64 oracle as it stands, on a bounded sample of the workload's pairs."""
+    import oracle
+    op = oracle.Plan(SYS.n, SYS.h, SYS.bc, SYS.kernel, SYS.omega)
+    n_orb = psi.shape[1]
+    pairs = oracle.pair_list(n_orb, ordered=False)
+    t0 = time.perf_counter()
+    done = 0
+    while done < len(pairs):
+        chunk = pairs[done:done + 4]
+        oracle.vx_apply(op, psi, pairs=chunk)
+        done += len(chunk)
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": UNIT, "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+            "sample": f"first {done} of {len(pairs)} symmetric pairs of the workload (pair product, f(L) by "
+                      f"mode products, both accumulations), {dt:.1f} s of NumPy FP64"}
+
+
+def run_reference(args):
+    """Reference arm: the oracle (FP64 NumPy, host cores) on bounded samples of the same workload."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    psi = workloads.make_orbitals(SYS)
+    op = oracle.Plan(SYS.n, SYS.h, SYS.bc, SYS.kernel, SYS.omega)
+    pairs = oracle.pair_list(SYS.n_orb, ordered=False)
+    per_step = 4
+    for w in range(args.warmup):
+        oracle.vx_apply(op, psi, pairs=pairs[w * per_step:(w + 1) * per_step])
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        k0 = ((args.warmup + s) * per_step) % len(pairs)
+        oracle.vx_apply(op, psi, pairs=pairs[k0:k0 + per_step])
+    dt = time.perf_counter() - t0
+    value = per_step * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": DATA, "config": {"workload": WORKLOAD, "sample": f"{per_step} pair solves per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+                             "sample": f"{per_step} symmetric pairs of the workload per step, {args.steps} steps"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# algorithmic work per item of each pass (useful flops; fp32 scratch / input / output bytes)
+def pass_model(n):
+    n1, n2, n3 = n
+    N = n1 * n2 * n3
+    return {
+        "X3F": (2.0 * N * n3, 4.0 * N + 8.0 * N),      # rho from two fp32 orbitals, write mode-3 coefficients
+        "X2F": (2.0 * N * n2, 8.0 * N),
+        "X1": (4.0 * N * n1, 8.0 * N),                  # forward + inverse mode 1 in one pass
+        "X2I": (2.0 * N * n2, 8.0 * N),
+        "X3I": (2.0 * N * n3, 4.0 * N + 8.0 * N + 16.0 * N),  # read coefficients, two orbitals, two fp32 RMW
+    }
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import paper_2406_16998_gb300 as kx
+    from paper_2406_16998_gb300 import build
+    world, rank, local = dist_setup(args.gpus)
+    if rank == 0:
+        build.build()
+    barrier(world)
+    hbm, bf16, bf16_sus, peak_src = peaks()
+
+    psi_h = workloads.make_orbitals(SYS)                  # (N, n_orb) float64
+    psi_t = np.ascontiguousarray(psi_h.T)                 # (n_orb, N): orbital-major, x1 fastest
+    psi = torch.from_numpy(psi_t).cuda()
+    n_orb, N = psi.shape
+    P = n_orb * (n_orb + 1) // 2
+    plan = kx.Plan.for_system(SYS, precision=kx.KX_F16X3)
+    vx = torch.empty_like(psi)
+    ex = torch.empty(1, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    for _ in range(max(3, args.warmup)):
+        kx.kx_vx_apply(plan, psi, out=vx, e_x=ex)
+    torch.cuda.synchronize()
+    assert plan.status() == kx.KX_OK
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    plan.profile(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        kx.kx_vx_apply(plan, psi, out=vx, e_x=ex)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms_total = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    prof = plan.profile_read()
+    plan.profile(False)
+    ms_total = max_over_ranks(ms_total, world)
+    ms_step = ms_total / args.steps
+    value = world * P * args.steps / (ms_total / 1e3)
+    gpu_launches = sum(v[1] for v in prof.values())
+
+    if rank != 0:
+        barrier(world)
+        return
+
+    # roofline of the dominant kernel (largest share of timed device time)
+    model = pass_model(SYS.n)
+    kinds = {k: prof[k] for k in model}
+    dom = max(kinds, key=lambda k: kinds[k][0])
+    dom_ms, dom_launches = kinds[dom]
+    avg_ms = dom_ms / max(1, dom_launches)
+    items_per_launch = P * args.steps / max(1, dom_launches)
+    flops, bytes_ = model[dom]
+    t_tensor = flops * 3 / (bf16 * 1e12)
+    t_hbm = bytes_ / (hbm * 1e9)
+    if t_hbm >= t_tensor:
+        ach = bytes_ * items_per_launch / (avg_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": None, "kernel": dom, "peak_source": f"{peak_src} hbm_gbs (copy)"}
+    else:
+        ach = flops * items_per_launch / (avg_ms / 1e3) / 1e12
+        pk = bf16 / 3.0
+        roof = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                "traffic": None, "kernel": dom,
+                "peak_source": f"{peak_src} bf16_tflops / 3 (three fp16 products per useful product)"}
+    roof["avg_launch_ms"] = avg_ms
+    roof["items_per_launch"] = items_per_launch
+    kern = {k: {"ms_total": v[0], "launches": v[1], "share": v[0] / max(1e-9, sum(x[0] for x in prof.values()))}
+            for k, v in prof.items() if v[1] > 0}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f16x3", "data": DATA,
+           "config": {"workload": WORKLOAD, "grid": list(SYS.n), "h_bohr": SYS.h[0], "bc": "dirichlet",
+                      "kernel": "unscreened", "fd_order": SYS.fd_order, "n_orb": n_orb, "pairs_per_step": P,
+                      "precision": "f16x3: fp16 hi/lo split of both operands, 3 tcgen05 products, fp32 accumulate",
+                      "l2": "inputs larger than L2 (psi 453 MB float64, fp32 scratch > 1 GB per chunk)"},
+           "vx_psi_ms": ms_step, "roofline": roof, "kernels": kern, "gpu_launches": gpu_launches,
+           "clocks": clk}
+
+    if not args.no_extras:
+        vx_split = vx.clone()
+        ex_split = ex.item()
+        # float64 GPU path on the same inputs: the speed-up denominator and the full-size error reference
+        plan64 = kx.Plan.for_system(SYS, precision=kx.KX_FP64)
+        vx64 = torch.empty_like(psi)
+        ex64 = torch.empty(1, dtype=torch.float64, device="cuda")
+        kx.kx_vx_apply(plan64, psi, out=vx64, e_x=ex64)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        kx.kx_vx_apply(plan64, psi, out=vx64, e_x=ex64)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1)
+        err_vx = float((vx_split - vx64).abs().max() / vx64.abs().max())
+        err_ex = abs(ex_split - ex64.item()) / abs(ex64.item())
+        out["fp64_gpu"] = {"ms_per_step": ms64, "pair_solves_per_s": P / (ms64 / 1e3),
+                           "speedup_split_vs_fp64": ms64 / ms_step}
+        out["error"] = {"vx_psi_maxrel_vs_fp64_gpu": err_vx, "e_x_rel_vs_fp64_gpu": err_ex,
+                        "targets": {"vx_psi": 1e-5, "e_x": 1e-6}, "e_x": ex_split}
+        del plan64, vx64
+        # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+        psi_pin = torch.from_numpy(psi_t).pin_memory()
+        vx_pin = torch.empty_like(psi_pin).pin_memory()
+        kx.kx_vx_apply_host(plan, psi_pin, out=vx_pin)
+        k_e2e = max(3, min(args.steps, 10))
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            kx.kx_vx_apply_host(plan, psi_pin, out=vx_pin)
+        dt = time.perf_counter() - t0
+        out["e2e"] = {"value": P * k_e2e / dt, "unit": UNIT, "h2d_bytes_per_step": psi_pin.numel() * 8,
+                      "d2h_bytes_per_step": vx_pin.numel() * 8 + 8, "ms_per_step": 1e3 * dt / k_e2e}
+        out["cpu_baseline"] = cpu_baseline(psi_h)
+    print(json.dumps(out), flush=True)
+    barrier(world)
+
+
+if __name__ == "__main__":
+    main()

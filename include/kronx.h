@@ -133,6 +133,18 @@ int kx_apply_fL(kx_plan *plan, int n_rhs, const double *b, double *x, kx_stream 
 int kx_vx_apply(kx_plan *plan, int n_orb, const double *psi, const double *occ,
                 double *vx_psi, double *e_x, kx_stream stream);
 
+/* kx_vx_apply_pairs — the part of kx_vx_apply contributed by a contiguous range
+ * [pair_begin, pair_end) of the symmetric pair list (row-major upper triangle:
+ * (0,0), (0,1), ..., (0,n_orb-1), (1,1), ...).  vx_psi and e_x receive the
+ * partial sums of Eqs. 3-5 over that range (overwritten, not added), so that
+ * ranges covering the list sum to the full result: the unit a multi-GPU split
+ * of the pair solves (Sec. 3: the O(Nk^2 Ns^2) systems are independent)
+ * reduces.  0 <= pair_begin <= pair_end <= n_orb (n_orb+1)/2; other arguments
+ * as in kx_vx_apply. */
+int kx_vx_apply_pairs(kx_plan *plan, int n_orb, const double *psi, const double *occ,
+                      long long pair_begin, long long pair_end, double *vx_psi, double *e_x,
+                      kx_stream stream);
+
 /* kx_vx_apply_host — kx_vx_apply on HOST buffers (pinned memory recommended):
  * copies psi (and occ) to library-owned device buffers, runs the apply and
  * copies vx_psi and e_x back, all queued on `stream`; returns after the stream
@@ -190,6 +202,21 @@ int kx_plan_status(kx_plan *plan, int *status_out, kx_stream stream);
  * (1 <= max_cycles <= 2e9), records KX_ERR_TIMEOUT in the plan's status word
  * and returns; read the word with kx_plan_status.  The GPU context stays usable. */
 int kx_selftest_wait(kx_plan *plan, long long max_cycles, kx_stream stream);
+
+/* kx_profile — starts (enable = 1, clearing earlier records) or stops (0)
+ * per-launch CUDA-event timing of the plan's kernels on the stream each is
+ * launched on.  Launch counts are kept whether or not timing is on. */
+int kx_profile(kx_plan *plan, int enable);
+
+/* kx_profile_read — per kernel kind k < n_kinds: total event-timed
+ * milliseconds ms[k] and launch count launches[k] since the last kx_profile
+ * call (host arrays).  Kinds: 0 prep (fp64 -> fp32), 1 X3F (rho = psi_i psi_j,
+ * mode 3 forward), 2 X2F (mode 2 forward), 3 X1 (mode 1 forward, f(Lambda)
+ * scaling and energy, mode 1 inverse), 4 X2I (mode 2 inverse), 5 X3I (mode 3
+ * inverse and Vx psi accumulation), 6 finalize/energy sums, 7 float64 mode
+ * products, 8 other float64 kernels, 9 ACE, 10 set-up.  Synchronises on the
+ * recorded events. */
+int kx_profile_read(kx_plan *plan, int n_kinds, double *ms, long long *launches);
 
 /* kx_last_error_detail — copies the last error message of the calling host
  * thread into buf (host, len bytes, NUL-terminated).  Returns the last code. */

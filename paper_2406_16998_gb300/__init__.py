@@ -41,6 +41,7 @@ SIGNATURES = {
     "kx_apply_fL": (_c_int, [_vp, _c_int, _vp, _vp, _vp]),
     "kx_vx_apply": (_c_int, [_vp, _c_int, _vp, _vp, _vp, _vp, _vp]),
     "kx_vx_apply_host": (_c_int, [_vp, _c_int, _vp, _vp, _vp, _vp, _vp]),
+    "kx_vx_apply_pairs": (_c_int, [_vp, _c_int, _vp, _vp, _ll, _ll, _vp, _vp, _vp]),
     "kx_energy": (_c_int, [_vp, _c_int, _vp, _vp, _vp, _vp]),
     "kx_ace": (_c_int, [_vp, _c_int, _vp, _vp, _vp, _vp, _vp]),
     "kx_batch_create": (_c_int, [_c_int, _vp, _vp, ctypes.POINTER(_vp)]),
@@ -49,6 +50,8 @@ SIGNATURES = {
     "kx_autotune": (_c_int, [_vp, _c_int, _c_int]),
     "kx_plan_status": (_c_int, [_vp, ctypes.POINTER(_c_int), _vp]),
     "kx_selftest_wait": (_c_int, [_vp, _ll, _vp]),
+    "kx_profile": (_c_int, [_vp, _c_int]),
+    "kx_profile_read": (_c_int, [_vp, _c_int, _vp, _vp]),
     "kx_last_error_detail": (_c_int, [ctypes.c_char_p, _c_int]),
     "kx_strerror": (ctypes.c_char_p, [_c_int]),
 }
@@ -177,6 +180,20 @@ class Plan:
         _check(lib().kx_plan_ftable(self.handle, f.ctypes.data_as(_vp)))
         return f
 
+    PROFILE_KINDS = ["prep", "X3F", "X2F", "X1", "X2I", "X3I", "final", "fp64_mode", "fp64_other", "ace",
+                     "setup"]
+
+    def profile(self, enable=True):
+        _check(lib().kx_profile(self.handle, 1 if enable else 0))
+
+    def profile_read(self):
+        """{kind: (total_ms, launches)} since the last profile() call."""
+        k = len(self.PROFILE_KINDS)
+        ms = np.zeros(k)
+        ln = np.zeros(k, dtype=np.int64)
+        _check(lib().kx_profile_read(self.handle, k, ms.ctypes.data_as(_vp), ln.ctypes.data_as(_vp)))
+        return {name: (float(ms[i]), int(ln[i])) for i, name in enumerate(self.PROFILE_KINDS)}
+
     def status(self, stream=None):
         st = ctypes.c_int(0)
         _check(lib().kx_plan_status(self.handle, ctypes.byref(st), _stream(stream)))
@@ -206,6 +223,21 @@ def kx_vx_apply(plan: Plan, psi, occ=None, out=None, e_x=None, stream=None):
                              _dptr(occ, "occ", torch.float64, (n_orb,)),
                              _dptr(out, "out", torch.float64, (n_orb, plan.N)),
                              _dptr(e_x, "e_x", torch.float64, (1,)), _stream(stream)))
+    return out, e_x
+
+
+def kx_vx_apply_pairs(plan: Plan, psi, pair_begin, pair_end, occ=None, out=None, e_x=None, stream=None):
+    """Partial (Vx psi, E_x) over pairs [pair_begin, pair_end) of the symmetric list."""
+    torch = _torch()
+    n_orb = psi.shape[0]
+    if out is None:
+        out = torch.empty_like(psi)
+    if e_x is None:
+        e_x = torch.empty(1, dtype=torch.float64, device=psi.device)
+    _check(lib().kx_vx_apply_pairs(plan.handle, n_orb, _dptr(psi, "psi", torch.float64, (n_orb, plan.N)),
+                                   _dptr(occ, "occ", torch.float64, (n_orb,)), int(pair_begin), int(pair_end),
+                                   _dptr(out, "out", torch.float64, (n_orb, plan.N)),
+                                   _dptr(e_x, "e_x", torch.float64, (1,)), _stream(stream)))
     return out, e_x
 
 

@@ -76,6 +76,35 @@ int ensure_pairs(kx_plan *p, int n_orb, cudaStream_t s) {
     return KX_OK;
 }
 
+static int prof_event(kx_plan *p, cudaEvent_t *out) {
+    Profiler &P = p->prof;
+    if (P.used == P.pool.size()) {
+        cudaEvent_t e;
+        KX_CUDA_TRY(cudaEventCreate(&e));
+        P.pool.push_back(e);
+    }
+    *out = P.pool[P.used++];
+    return KX_OK;
+}
+
+int prof_begin(kx_plan *p, int kind, cudaStream_t s) {
+    p->prof.launches[kind] += 1;
+    if (!p->prof.on) return KX_OK;
+    cudaEvent_t e;
+    if (int rc = prof_event(p, &e)) return rc;
+    p->prof.marks.push_back({kind, p->prof.used - 1});
+    KX_CUDA_TRY(cudaEventRecord(e, s));
+    return KX_OK;
+}
+
+int prof_end(kx_plan *p, cudaStream_t s) {
+    if (!p->prof.on) return KX_OK;
+    cudaEvent_t e;
+    if (int rc = prof_event(p, &e)) return rc;
+    KX_CUDA_TRY(cudaEventRecord(e, s));
+    return KX_OK;
+}
+
 static int reserve(kx_plan *p, int n_orb) {
     int rc = ensure_pairs(p, n_orb, nullptr);
     if (rc) return rc;
@@ -238,6 +267,26 @@ int kx_vx_apply(kx_plan *plan, int n_orb, const double *psi, const double *occ, 
     return dispatch_vx(plan, n_orb, psi, occ, vx_psi, e_x, false, reinterpret_cast<cudaStream_t>(stream));
 }
 
+int kx_vx_apply_pairs(kx_plan *plan, int n_orb, const double *psi, const double *occ, long long pair_begin,
+                      long long pair_end, double *vx_psi, double *e_x, kx_stream stream) {
+    if (int rc = check_plan(plan)) return rc;
+    if (n_orb < 1 || n_orb > 4096) return set_error(KX_ERR_ARG, "kx_vx_apply_pairs: n_orb must be in 1..4096");
+    const long long P = (long long)n_orb * (n_orb + 1) / 2;
+    if (pair_begin < 0 || pair_end < pair_begin || pair_end > P)
+        return set_error(KX_ERR_ARG, "kx_vx_apply_pairs: need 0 <= pair_begin <= pair_end <= n_orb(n_orb+1)/2");
+    if (!psi || !vx_psi) return set_error(KX_ERR_ARG, "kx_vx_apply_pairs: NULL buffer");
+    if (psi == vx_psi) return set_error(KX_ERR_ARG, "kx_vx_apply_pairs: vx_psi must not overlap psi");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (pair_end == pair_begin) {
+        KX_CUDA_TRY(cudaMemsetAsync(vx_psi, 0, sizeof(double) * (size_t)n_orb * plan->N, s));
+        if (e_x) KX_CUDA_TRY(cudaMemsetAsync(e_x, 0, sizeof(double), s));
+        return KX_OK;
+    }
+    if (plan->precision == KX_FP64)
+        return fp64_vx(plan, n_orb, psi, occ, vx_psi, e_x, false, s, (long)pair_begin, (long)pair_end);
+    return tc_vx(plan, n_orb, psi, occ, vx_psi, e_x, false, s, (long)pair_begin, (long)pair_end);
+}
+
 int kx_energy(kx_plan *plan, int n_orb, const double *psi, const double *occ, double *e_x, kx_stream stream) {
     if (int rc = check_plan(plan)) return rc;
     if (n_orb < 1 || n_orb > 4096) return set_error(KX_ERR_ARG, "kx_energy: n_orb must be in 1..4096");
@@ -301,6 +350,32 @@ int kx_selftest_wait(kx_plan *plan, long long max_cycles, kx_stream stream) {
     if (int rc = check_plan(plan)) return rc;
     if (max_cycles < 1 || max_cycles > 2000000000LL) return set_error(KX_ERR_ARG, "kx_selftest_wait: bad limit");
     return selftest_wait(plan, max_cycles, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int kx_profile(kx_plan *plan, int enable) {
+    if (int rc = check_plan(plan)) return rc;
+    plan->prof.on = enable != 0;
+    plan->prof.used = 0;
+    plan->prof.marks.clear();
+    for (int k = 0; k < PK_COUNT; ++k) plan->prof.launches[k] = 0;
+    return KX_OK;
+}
+
+int kx_profile_read(kx_plan *plan, int n_kinds, double *ms, long long *launches) {
+    if (int rc = check_plan(plan)) return rc;
+    if (n_kinds < 1 || !ms || !launches) return set_error(KX_ERR_ARG, "kx_profile_read: bad arguments");
+    for (int k = 0; k < n_kinds; ++k) {
+        ms[k] = 0.0;
+        launches[k] = k < PK_COUNT ? plan->prof.launches[k] : 0;
+    }
+    for (auto &m : plan->prof.marks) {
+        cudaEvent_t a = plan->prof.pool[m.second], b = plan->prof.pool[m.second + 1];
+        KX_CUDA_TRY(cudaEventSynchronize(b));
+        float t = 0.f;
+        KX_CUDA_TRY(cudaEventElapsedTime(&t, a, b));
+        if (m.first < n_kinds) ms[m.first] += t;
+    }
+    return KX_OK;
 }
 
 int kx_batch_create(int n_sys, kx_plan *const *plans, const int *n_orb, kx_batch **out) {
@@ -406,7 +481,7 @@ int kx_autotune(kx_plan *plan, int n_orb, int budget_ms) {
     TuneParams best = orig;
     float best_ms = 1e30f;
     const long P = (long)n_orb * (n_orb + 1) / 2;
-    const int ctas[] = {1, 2, 3, 4};
+    const int ctas[] = {1, 2};
     const long chunks[] = {256, 512, 1024, 2048};
     auto t_start = std::chrono::steady_clock::now();
     int rc = KX_OK;

@@ -156,16 +156,15 @@ int launch_mode(const kx_plan *p, const double *in, double *out, int R, int axis
     long long inner = axis == 0 ? 1 : (axis == 1 ? p->n[0] : (long long)p->n[0] * p->n[1]);
     long long n_cols = (long long)R * (long long)(p->N / n);
     size_t smem = sizeof(double) * ((size_t)n * n + (size_t)n * (kTQ + 1));
-    static bool attr_set = false;
-    if (!attr_set) {
+    {
         size_t mx = sizeof(double) * ((size_t)kMaxN * kMaxN + (size_t)kMaxN * (kTQ + 1));
         KX_CUDA_TRY(cudaFuncSetAttribute(mode_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx));
-        attr_set = true;
     }
     long long blocks = (n_cols + kTQ - 1) / kTQ;
+    if (int rc = prof_begin(const_cast<kx_plan *>(p), PK_FP64_MODE, s)) return rc;
     mode_f64_kernel<<<(unsigned)blocks, kModeThreads, smem, s>>>(in, out, n_cols, n, inner, p->d_V[axis], inverse);
     KX_LAUNCH_CHECK("mode_f64_kernel launch");
-    return KX_OK;
+    return prof_end(const_cast<kx_plan *>(p), s);
 }
 
 // f(L) on R vectors: forward modes 1, 2, 3; scaling (and energy); inverse modes 3, 2, 1.
@@ -177,8 +176,10 @@ int fl_chunk(const kx_plan *p, const double *src, double *b0, double *b1, double
     if ((rc = launch_mode(p, b0, b1, R, 1, 0, s))) return rc;
     if ((rc = launch_mode(p, b1, b0, R, 2, 0, s))) return rc;
     const bool want_energy = e_x != nullptr;
-    scale_f64_kernel<<<n_part, 256, 0, s>>>(b0, R, p->N, p->d_f64, pairs, occ, partial, want_energy ? 1 : 0,
-                                            energy_only ? 0 : 1);
+    const_cast<kx_plan *>(p)->prof.launches[PK_FP64_OTHER] += want_energy ? 2 : 1;
+    const int sblocks = want_energy ? n_part : 4 * p->num_sms;  // grid of the energy partials when summed
+    scale_f64_kernel<<<sblocks, 256, 0, s>>>(b0, R, p->N, p->d_f64, pairs, occ, partial, want_energy ? 1 : 0,
+                                             energy_only ? 0 : 1);
     KX_LAUNCH_CHECK("scale_f64_kernel launch");
     if (want_energy) {
         energy_add_kernel<<<1, 32, 0, s>>>(partial, n_part, -0.5 * p->dV, e_x);
@@ -218,11 +219,12 @@ int fp64_apply_fL(kx_plan *p, int n_rhs, const double *b, double *x, cudaStream_
 }
 
 int fp64_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, double *vx, double *ex,
-            bool energy_only, cudaStream_t s) {
+            bool energy_only, cudaStream_t s, long pair_begin, long pair_end) {
     int rc = ensure_pairs(p, n_orb, s);
     if (rc) return rc;
-    long P = (long)n_orb * (n_orb + 1) / 2;
-    long chunk = fp64_chunk(p, P);
+    if (pair_end < 0) pair_end = (long)n_orb * (n_orb + 1) / 2;
+    long P = pair_end - pair_begin;
+    long chunk = fp64_chunk(p, std::max(1L, P));
     rc = ensure_workspace(p, fp64_workspace_bytes(p, chunk));
     if (rc) return rc;
     double *w0 = (double *)p->ws.ptr;
@@ -233,9 +235,10 @@ int fp64_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, double 
     if (!energy_only) KX_CUDA_TRY(cudaMemsetAsync(vx, 0, sizeof(double) * n_orb * p->N, s));
     if (ex) KX_CUDA_TRY(cudaMemsetAsync(ex, 0, sizeof(double), s));
     const int2 *pairs = (const int2 *)p->d_pairs;
-    for (long c0 = 0; c0 < P; c0 += chunk) {
-        int R = (int)std::min<long>(chunk, P - c0);
+    for (long c0 = pair_begin; c0 < pair_end; c0 += chunk) {
+        int R = (int)std::min<long>(chunk, pair_end - c0);
         int blocks = (int)std::min<size_t>(((size_t)R * p->N + 255) / 256, (size_t)8 * p->num_sms);
+        p->prof.launches[PK_FP64_OTHER] += energy_only ? 1 : 2;
         pairform_f64_kernel<<<blocks, 256, 0, s>>>(pairs + c0, R, psi, p->N, w2);
         KX_LAUNCH_CHECK("pairform_f64_kernel launch");
         rc = fl_chunk(p, w2, w0, w1, w2, R, energy_only, pairs + c0, occ, partial, n_part, ex, s);

@@ -41,6 +41,17 @@ struct TuneParams {
     long chunk_pairs = 0;     // pairs per chunk (0 = choose from the workspace budget)
 };
 
+// Per-launch CUDA-event timing by kernel kind (kx_profile / kx_profile_read).
+enum ProfKind { PK_PREP = 0, PK_X3F, PK_X2F, PK_X1, PK_X2I, PK_X3I, PK_FINAL, PK_FP64_MODE, PK_FP64_OTHER,
+                PK_ACE, PK_SETUP, PK_COUNT };
+struct Profiler {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;       // reusable events
+    size_t used = 0;
+    std::vector<std::pair<int, size_t>> marks;  // (kind, index of the start event; stop = +1)
+    long long launches[PK_COUNT] = {0};
+};
+
 // Device workspace, grown on demand and reused across calls.
 struct Workspace {
     void *ptr = nullptr;
@@ -82,9 +93,14 @@ struct kx_plan_s {
     int ws_norb = -1;        // orbital count the pair list currently describes
     int *d_pairs = nullptr;  // int2 per pair (i, j), symmetric enumeration
     size_t pairs_cap = 0;
+    kx::Profiler prof;
 };
 
 namespace kx {
+
+// Bracket one kernel launch with profiling events (no-ops unless kx_profile is on).
+int prof_begin(kx_plan *p, int kind, cudaStream_t s);
+int prof_end(kx_plan *p, cudaStream_t s);
 
 // ---- set-up (kx_setup.cu)
 int plan_setup(kx_plan *p);          // eig, f tables, split operands (synchronous)
@@ -97,13 +113,13 @@ int ensure_pairs(kx_plan *p, int n_orb, cudaStream_t s);
 // ---- FP64 path (kx_fp64.cu)
 int fp64_apply_fL(kx_plan *p, int n_rhs, const double *b, double *x, cudaStream_t s);
 int fp64_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, double *vx, double *ex,
-            bool energy_only, cudaStream_t s);
+            bool energy_only, cudaStream_t s, long pair_begin = 0, long pair_end = -1);
 size_t fp64_workspace_bytes(const kx_plan *p, long chunk);
 
 // ---- tensor-core path (kx_tc.cu)
 int tc_apply_fL(kx_plan *p, int n_rhs, const double *b, double *x, cudaStream_t s);
 int tc_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, double *vx, double *ex,
-          bool energy_only, cudaStream_t s);
+          bool energy_only, cudaStream_t s, long pair_begin = 0, long pair_end = -1);
 size_t tc_workspace_bytes(const kx_plan *p, int n_orb, long chunk);
 long tc_default_chunk(const kx_plan *p, int n_orb);
 int selftest_wait(kx_plan *p, long long max_cycles, cudaStream_t s);

@@ -168,8 +168,13 @@ __device__ __forceinline__ void load_tile(const PassArgs &a, long long tile, uin
 }
 
 // D = A_hi B_hi + A_hi B_lo + A_lo B_hi over K = np (single issuing thread).
-__device__ __forceinline__ void issue_split_mma(uint32_t tmem_d, uint32_t a_hi, uint32_t a_lo, bool a_kmajor,
-                                                uint32_t v_hi, uint32_t v_lo, bool inverse, int np) {
+// The tensor core rounds its fp32 accumulator toward zero at every instruction,
+// so a long chain of large partial sums drifts low.  To keep that drift small
+// the two small cross products are issued first into accumulator Da, and the
+// hi*hi chain is split over Da (even k-steps) and Db (odd k-steps); the
+// epilogue adds Da + Db with round-to-nearest.
+__device__ __forceinline__ void issue_split_mma(uint32_t tmem_a, uint32_t tmem_b, uint32_t a_hi, uint32_t a_lo,
+                                                bool a_kmajor, uint32_t v_hi, uint32_t v_lo, bool inverse, int np) {
     const uint32_t idesc = ptx::idesc_f16(128, np, a_kmajor ? 0 : 1, inverse ? 0 : 1);
     const uint32_t a_lbo = a_kmajor ? 128u : 2048u;
     const uint32_t a_sbo = a_kmajor ? (uint32_t)(np * 16) : 128u;
@@ -186,9 +191,27 @@ __device__ __forceinline__ void issue_split_mma(uint32_t tmem_d, uint32_t a_hi, 
         const uint64_t al = ptx::sdesc(a_lo + ks * a_step, a_lbo, a_sbo);
         const uint64_t bh = ptx::sdesc(v_hi + ks * b_step, b_lbo, b_sbo);
         const uint64_t bl = ptx::sdesc(v_lo + ks * b_step, b_lbo, b_sbo);
-        ptx::mma_f16(tmem_d, ah, bh, idesc, ks > 0 ? 1u : 0u);
-        ptx::mma_f16(tmem_d, ah, bl, idesc, 1u);
-        ptx::mma_f16(tmem_d, al, bh, idesc, 1u);
+        ptx::mma_f16(tmem_a, ah, bl, idesc, ks > 0 ? 1u : 0u);
+        ptx::mma_f16(tmem_a, al, bh, idesc, 1u);
+    }
+    for (int ks = 0; ks < nks; ++ks) {
+        const uint64_t ah = ptx::sdesc(a_hi + ks * a_step, a_lbo, a_sbo);
+        const uint64_t bh = ptx::sdesc(v_hi + ks * b_step, b_lbo, b_sbo);
+        if (ks & 1)
+            ptx::mma_f16(tmem_b, ah, bh, idesc, ks > 1 ? 1u : 0u);
+        else
+            ptx::mma_f16(tmem_a, ah, bh, idesc, 1u);
+    }
+}
+
+// Da + Db for 8 columns of this thread's lane (Db is empty when K = 16).
+__device__ __forceinline__ void tmem_ld8_sum(uint32_t ta, uint32_t tb, bool two, float *v) {
+    ptx::tmem_ld8(ta, v);
+    if (two) {
+        float w[8];
+        ptx::tmem_ld8(tb, w);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) v[c] += w[c];
     }
 }
 
@@ -232,7 +255,7 @@ __global__ void __launch_bounds__(kThreads, 2) tc_pass_kernel(const PassArgs a) 
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (warp == 0) {
-        ptx::tmem_alloc(&tmem_slot, 128);
+        ptx::tmem_alloc(&tmem_slot, 256);
         ptx::tmem_relinquish();
     }
     if (tid == 0) {
@@ -255,6 +278,9 @@ __global__ void __launch_bounds__(kThreads, 2) tc_pass_kernel(const PassArgs a) 
     const int q = warp & 3, half = warp >> 2;
     const int m = 32 * q + lane;                       // TMEM lane == tile row of this thread
     const uint32_t t_row = tmem + ((uint32_t)(32 * q) << 16);
+    const uint32_t tmem_b = tmem + (uint32_t)np;          // second hi*hi accumulator
+    const uint32_t t_row_b = t_row + (uint32_t)np;
+    const bool two_acc = (np >> 4) > 1;
     const long long n12 = (long long)a.n1 * a.n2;
     const int nchunk = np >> 3;
 
@@ -270,7 +296,7 @@ __global__ void __launch_bounds__(kThreads, 2) tc_pass_kernel(const PassArgs a) 
         if (tid == 0) {
             ptx::tc_fence_after();
             const bool inv = (PASS == P_X2I || PASS == P_X3I);
-            issue_split_mma(tmem, sAhi, sAlo, PASS == P_X1, sVhi, sVlo, inv, np);
+            issue_split_mma(tmem, tmem_b, sAhi, sAlo, PASS == P_X1, sVhi, sVlo, inv, np);
             ptx::mma_commit(&mbar);
         }
         ok = wait_mma(&mbar, phase, a, &s_flag);
@@ -301,7 +327,7 @@ __global__ void __launch_bounds__(kThreads, 2) tc_pass_kernel(const PassArgs a) 
             float e_row = 0.f;
             for (int c8 = half; c8 < nchunk; c8 += 2) {
                 float v[8];
-                ptx::tmem_ld8(t_row + 8 * c8, v);
+                tmem_ld8_sum(t_row + 8 * c8, t_row_b + 8 * c8, two_acc, v);
                 const bool cvalid = valid && (8 * c8 < a.nc);
                 float fk[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                 if (cvalid) ld8(a.f32 + local * a.n1 + 8 * c8, fk);
@@ -326,7 +352,7 @@ __global__ void __launch_bounds__(kThreads, 2) tc_pass_kernel(const PassArgs a) 
                 __syncthreads();
                 if (tid == 0) {
                     ptx::tc_fence_after();
-                    issue_split_mma(tmem, sAhi, sAlo, true, sVhi, sVlo, true, np);
+                    issue_split_mma(tmem, tmem_b, sAhi, sAlo, true, sVhi, sVlo, true, np);
                     ptx::mma_commit(&mbar);
                 }
                 ok = wait_mma(&mbar, phase, a, &s_flag);
@@ -336,7 +362,7 @@ __global__ void __launch_bounds__(kThreads, 2) tc_pass_kernel(const PassArgs a) 
                 const float unscale2 = ldexpf(1.f, -(e_mid + kVScaleExp));
                 for (int c8 = half; c8 < nchunk; c8 += 2) {
                     float v[8];
-                    ptx::tmem_ld8(t_row + 8 * c8, v);
+                    tmem_ld8_sum(t_row + 8 * c8, t_row_b + 8 * c8, two_acc, v);
                     if (valid && 8 * c8 < a.nc) {
 #pragma unroll
                         for (int c = 0; c < 8; ++c) {
@@ -362,7 +388,7 @@ __global__ void __launch_bounds__(kThreads, 2) tc_pass_kernel(const PassArgs a) 
             }
             for (int c8 = half; c8 < nchunk; c8 += 2) {
                 float v[8];
-                ptx::tmem_ld8(t_row + 8 * c8, v);
+                tmem_ld8_sum(t_row + 8 * c8, t_row_b + 8 * c8, two_acc, v);
                 if (!valid) continue;
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
@@ -386,7 +412,7 @@ __global__ void __launch_bounds__(kThreads, 2) tc_pass_kernel(const PassArgs a) 
             // transposed write into the natural layout of the next pass's input
             for (int c8 = half; c8 < nchunk; c8 += 2) {
                 float v[8];
-                ptx::tmem_ld8(t_row + 8 * c8, v);
+                tmem_ld8_sum(t_row + 8 * c8, t_row_b + 8 * c8, two_acc, v);
                 if (!valid) continue;
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
@@ -429,7 +455,7 @@ __global__ void __launch_bounds__(kThreads, 2) tc_pass_kernel(const PassArgs a) 
     __syncthreads();
     if (warp == 0) {
         ptx::tc_fence_after();
-        ptx::tmem_dealloc(tmem, 128);
+        ptx::tmem_dealloc(tmem, 256);
     }
 }
 
@@ -489,13 +515,14 @@ int launch_pass(const kx_plan *p, PassArgs a, int axis, cudaStream_t s, int *gri
     KX_CUDA_TRY(cudaFuncSetAttribute(tc_pass_kernel<PASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     KX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_pass_kernel<PASS>, kThreads, smem));
-    per_sm = std::max(1, std::min(per_sm, std::min(p->tune.ctas_per_sm, 4)));
+    per_sm = std::max(1, std::min(per_sm, std::min(p->tune.ctas_per_sm, 2)));
     const long long n_tiles = (a.total_rows + 127) / 128;
     const int grid = (int)std::max(1LL, std::min<long long>(n_tiles, (long long)p->num_sms * per_sm));
     if (grid_out) *grid_out = grid;
+    if (int rc = prof_begin(const_cast<kx_plan *>(p), PK_X3F + PASS, s)) return rc;
     tc_pass_kernel<PASS><<<grid, kThreads, smem, s>>>(a);
     KX_LAUNCH_CHECK("tc_pass_kernel launch");
-    return KX_OK;
+    return prof_end(const_cast<kx_plan *>(p), s);
 }
 
 struct TcLayout {
@@ -541,11 +568,13 @@ static float fmax_sqrt(const kx_plan *p) {
 }
 
 int tc_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, double *vx, double *ex, bool energy_only,
-          cudaStream_t s) {
+          cudaStream_t s, long pair_begin, long pair_end) {
     int rc = ensure_pairs(p, n_orb, s);
     if (rc) return rc;
-    const long P = (long)n_orb * (n_orb + 1) / 2;
-    const long chunk = std::min<long>(tc_default_chunk(p, n_orb), P);
+    const long P_all = (long)n_orb * (n_orb + 1) / 2;
+    if (pair_end < 0) pair_end = P_all;
+    const long P = pair_end - pair_begin;
+    const long chunk = std::max(1L, std::min<long>(tc_default_chunk(p, n_orb), P));
     rc = ensure_workspace(p, tc_workspace_bytes(p, n_orb, chunk));
     if (rc) return rc;
     TcLayout L = carve(p, n_orb, chunk, !energy_only);
@@ -554,16 +583,18 @@ int tc_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, double *v
     KX_CUDA_TRY(cudaMemsetAsync(L.orb_max, 0, sizeof(float) * n_orb, s));
     {
         dim3 g((unsigned)std::min<long long>((N + 255) / 256, 64), (unsigned)n_orb);
+        if ((rc = prof_begin(p, PK_PREP, s))) return rc;
         prep_kernel<<<g, 256, 0, s>>>(psi, L.psi32, L.orb_max, n_orb, N);
         KX_LAUNCH_CHECK("prep_kernel launch");
+        if ((rc = prof_end(p, s))) return rc;
     }
     if (!energy_only) KX_CUDA_TRY(cudaMemsetAsync(L.acc, 0, sizeof(float) * (size_t)n_orb * N, s));
     if (ex) KX_CUDA_TRY(cudaMemsetAsync(ex, 0, sizeof(double), s));
     const int2 *pairs = reinterpret_cast<const int2 *>(p->d_pairs);
     const float mid_bound = fmax_sqrt(p);
 
-    for (long c0 = 0; c0 < P; c0 += chunk) {
-        const long R = std::min<long>(chunk, P - c0);
+    for (long c0 = pair_begin; c0 < pair_end; c0 += chunk) {
+        const long R = std::min<long>(chunk, pair_end - c0);
         KX_CUDA_TRY(cudaMemsetAsync(L.mx, 0, sizeof(float) * 4 * chunk, s));
         float *mx1 = L.mx, *mx2 = L.mx + chunk, *mx3 = L.mx + 2 * chunk, *mx4 = L.mx + 3 * chunk;
         PassArgs a{};
@@ -599,8 +630,10 @@ int tc_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, double *v
         int grid = 0;
         if ((rc = launch_pass<P_X1>(p, a, 0, s, &grid))) return rc;
         if (ex) {
+            if ((rc = prof_begin(p, PK_FINAL, s))) return rc;
             energy_add_kernel<<<1, 32, 0, s>>>(L.partial, grid, -0.5 * p->dV, ex);
             KX_LAUNCH_CHECK("energy_add_kernel launch");
+            if ((rc = prof_end(p, s))) return rc;
         }
         a.e_partial = nullptr;
         a.energy_only = 0;
@@ -625,8 +658,10 @@ int tc_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, double *v
     }
     if (!energy_only) {
         const long long n = (long long)n_orb * N;
+        if ((rc = prof_begin(p, PK_FINAL, s))) return rc;
         finalize_kernel<<<(unsigned)std::min<long long>((n + 255) / 256, 8LL * p->num_sms), 256, 0, s>>>(L.acc, vx, n);
         KX_LAUNCH_CHECK("finalize_kernel launch");
+        if ((rc = prof_end(p, s))) return rc;
     }
     return KX_OK;
 }
@@ -649,8 +684,10 @@ int tc_apply_fL(kx_plan *p, int n_rhs, const double *b, double *x, cudaStream_t 
         KX_CUDA_TRY(cudaMemsetAsync(L.orb_max, 0, sizeof(float) * R, s));
         KX_CUDA_TRY(cudaMemsetAsync(L.mx, 0, sizeof(float) * 4 * chunk, s));
         dim3 g((unsigned)std::min<long long>((N + 255) / 256, 64), (unsigned)R);
+        if ((rc = prof_begin(p, PK_PREP, s))) return rc;
         prep_kernel<<<g, 256, 0, s>>>(b + c0 * N, L.psi32, L.orb_max, (int)R, N);
         KX_LAUNCH_CHECK("prep_kernel launch");
+        if ((rc = prof_end(p, s))) return rc;
         float *mx1 = L.mx, *mx2 = L.mx + chunk, *mx3 = L.mx + 2 * chunk, *mx4 = L.mx + 3 * chunk;
         PassArgs a{};
         a.rhs_mode = 1;

@@ -297,3 +297,23 @@ def test_full_size_sampled(kx, name, sample):
     for i in sample:
         ref = _row_reference(op, psi, i)
         assert np.max(np.abs(vx_h[i] - ref)) < 1e-5 * scale
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_pair_ranges_sum_to_full_apply(kx, prec):
+    from paper_2406_16998_gb300 import shard
+    n, h, bc, kind, n_orb = SMALL[0]
+    psi = workloads.make_orbitals(system(n, h, bc, kind, n_orb, 59))
+    plan = kx.Plan(n, h, bc, kind, precision=prec)
+    x = dev(psi.T)
+    full, e_full = kx.kx_vx_apply(plan, x)
+    acc = torch.zeros_like(full)
+    e_acc = 0.0
+    for r in range(3):
+        a, b = shard.pair_range(n_orb, r, 3)
+        part, e_part = kx.kx_vx_apply_pairs(plan, x, a, b)
+        acc += part
+        e_acc += e_part.item()
+    tol = 1e-12 if prec == 0 else 1e-6
+    assert relmax(acc.cpu().numpy(), full.cpu().numpy()) < tol
+    assert abs(e_acc - e_full.item()) < tol * abs(e_full.item())

@@ -121,6 +121,26 @@ int kx_plan_ftable(const kx_plan *plan, double *f);
  * x must not overlap b.  n_rhs >= 0 (0 is a no-op). */
 int kx_apply_fL(kx_plan *plan, int n_rhs, const double *b, double *x, kx_stream stream);
 
+/* kx_apply_fL_noalloc — kx_apply_fL for callers that cannot allocate device
+ * memory at the point of the call (no counterpart in the paper).  Such callers
+ * reserved their device memory up front (a pool or caching allocator owns it,
+ * or a solver loop must not pay the device-wide synchronisation of cudaMalloc
+ * and cudaFree between iterations).  This entry point allocates nothing: its
+ * scratch is a static device array of 30 MiB + 160 KiB inside the library,
+ * which every GPU that loads the library's tensor-core module holds until the
+ * process exits.  The plan (created earlier with kx_plan_create, KX_F16X3
+ * precision) and the caller's b and x are the only other memory it touches.
+ *   Limit: n_rhs * N <= 2,621,440 grid values per call; larger requests return
+ *   KX_ERR_ARG with the numbers (split them into several calls).
+ *   First call on a device: looks up the array's device address once
+ *   (cudaGetSymbolAddress) with the plan's device current; make that first call
+ *   before any stream capture.
+ *   All calls share the array and it keeps the previous call's contents (the
+ *   entry point clears what must start at zero); calls whose GPU work overlaps
+ *   (different streams or host threads on one device) race on it.
+ * Arguments as in kx_apply_fL; the current device must be the plan's. */
+int kx_apply_fL_noalloc(kx_plan *plan, int n_rhs, const double *b, double *x, kx_stream stream);
+
 /* kx_vx_apply — the exact-exchange apply and energy (Sec. 2, Eqs. 3-5 / 8-10 at
  * the Gamma point, one spin channel).  Every unordered pair (i <= j) is solved
  * once (n_orb (n_orb+1)/2 solves of Eq. 19).

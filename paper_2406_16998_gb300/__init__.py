@@ -39,6 +39,7 @@ SIGNATURES = {
     "kx_plan_eig": (_c_int, [_vp, _c_int, _vp, _vp]),
     "kx_plan_ftable": (_c_int, [_vp, _vp]),
     "kx_apply_fL": (_c_int, [_vp, _c_int, _vp, _vp, _vp]),
+    "kx_apply_fL_noalloc": (_c_int, [_vp, _c_int, _vp, _vp, _vp]),
     "kx_vx_apply": (_c_int, [_vp, _c_int, _vp, _vp, _vp, _vp, _vp]),
     "kx_vx_apply_host": (_c_int, [_vp, _c_int, _vp, _vp, _vp, _vp, _vp]),
     "kx_vx_apply_pairs": (_c_int, [_vp, _c_int, _vp, _vp, _ll, _ll, _vp, _vp, _vp]),
@@ -208,6 +209,17 @@ def kx_apply_fL(plan: Plan, b, out=None, stream=None):
         out = torch.empty_like(b)
     _check(lib().kx_apply_fL(plan.handle, n_rhs, _dptr(b, "b", torch.float64, (n_rhs, plan.N)),
                              _dptr(out, "out", torch.float64, (n_rhs, plan.N)), _stream(stream)))
+    return out
+
+
+def kx_apply_fL_noalloc(plan: Plan, b, out, stream=None):
+    """X = f(L) B through the allocation-free entry point (scratch is a static
+    array inside the library).  `out` must be supplied by the caller, so the
+    call allocates nothing on the device; see kronx.h for the size limit."""
+    torch = _torch()
+    n_rhs = b.shape[0]
+    _check(lib().kx_apply_fL_noalloc(plan.handle, n_rhs, _dptr(b, "b", torch.float64, (n_rhs, plan.N)),
+                                     _dptr(out, "out", torch.float64, (n_rhs, plan.N)), _stream(stream)))
     return out
 
 

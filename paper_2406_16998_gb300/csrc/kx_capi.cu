@@ -258,6 +258,15 @@ int kx_apply_fL(kx_plan *plan, int n_rhs, const double *b, double *x, kx_stream 
     return tc_apply_fL(plan, n_rhs, b, x, s);
 }
 
+int kx_apply_fL_noalloc(kx_plan *plan, int n_rhs, const double *b, double *x, kx_stream stream) {
+    if (int rc = check_plan(plan)) return rc;
+    if (n_rhs < 0) return set_error(KX_ERR_ARG, "kx_apply_fL_noalloc: n_rhs < 0");
+    if (n_rhs == 0) return KX_OK;
+    if (!b || !x) return set_error(KX_ERR_ARG, "kx_apply_fL_noalloc: NULL buffer");
+    if (b == x) return set_error(KX_ERR_ARG, "kx_apply_fL_noalloc: x must not overlap b");
+    return tc_apply_fL_noalloc(plan, n_rhs, b, x, reinterpret_cast<cudaStream_t>(stream));
+}
+
 int kx_vx_apply(kx_plan *plan, int n_orb, const double *psi, const double *occ, double *vx_psi, double *e_x,
                 kx_stream stream) {
     if (int rc = check_plan(plan)) return rc;

@@ -123,6 +123,7 @@ int tc_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, double *v
 size_t tc_workspace_bytes(const kx_plan *p, int n_orb, long chunk);
 long tc_default_chunk(const kx_plan *p, int n_orb);
 int selftest_wait(kx_plan *p, long long max_cycles, cudaStream_t s);
+int tc_apply_fL_noalloc(kx_plan *p, int n_rhs, const double *b, double *x, cudaStream_t s);
 
 // ---- ACE tail (kx_ace.cu)
 int ace_run(kx_plan *p, int n_orb, const double *psi, const double *W, double *xi, double *M_out,

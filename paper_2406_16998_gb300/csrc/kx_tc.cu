@@ -22,6 +22,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <string>
 
 namespace kx {
 namespace {
@@ -732,6 +733,119 @@ int tc_apply_fL(kx_plan *p, int n_rhs, const double *b, double *x, cudaStream_t 
         if ((rc = launch_pass<P_X3I>(p, a, 2, s, nullptr))) return rc;
     }
     return KX_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// f(L) B without device allocation (kx_apply_fL_noalloc).
+//
+// Callers that cannot allocate device memory at the point of the call (their
+// device memory was reserved up front by a pool allocator, or they run inside
+// a solver loop that must not pay the device-wide synchronisation of
+// cudaMalloc / cudaFree) get this variant: its scratch is the file-scope
+// array below, so the call itself allocates nothing.  The array is part of
+// this module's image: every GPU that loads it holds kNoAllocBytes until the
+// process exits.  All calls share it and it keeps the previous call's
+// contents; the per-vector maxima that must start at zero are cleared at every
+// call.  Calls whose GPU work overlaps (two streams, or two host threads on one
+// device) race on the array.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocMaxElems = (size_t)5 << 19;  // n_rhs * N limit per call (2,621,440 grid values)
+constexpr size_t kNoAllocMaxVec = 8192;               // >= kNoAllocMaxElems / 512 (smallest N with n % 8 == 0)
+constexpr size_t kNoAllocBytes = 3 * kNoAllocMaxElems * sizeof(float) + 5 * kNoAllocMaxVec * sizeof(float);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+void *g_noalloc_ptr[kNoAllocMaxDevices] = {};  // device address of the array, per device
+
+// Set-up, once per device with that device current: the host-side name of the
+// array is only a stand-in, so the kernels get the address the runtime reports.
+int noalloc_scratch(int dev, void **out) {
+    if (dev < 0 || dev >= kNoAllocMaxDevices)
+        return set_error(KX_ERR_UNSUPPORTED, "kx_apply_fL_noalloc: device index beyond 63");
+    if (g_noalloc_ptr[dev] == nullptr) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_error(e, "kx_apply_fL_noalloc: cudaGetSymbolAddress of the static scratch");
+        g_noalloc_ptr[dev] = ptr;
+    }
+    *out = g_noalloc_ptr[dev];
+    return KX_OK;
+}
+
+}  // namespace
+
+size_t noalloc_max_elems() { return kNoAllocMaxElems; }
+
+int tc_apply_fL_noalloc(kx_plan *p, int n_rhs, const double *b, double *x, cudaStream_t s) {
+    if (p->precision != KX_F16X3)
+        return set_error(KX_ERR_UNSUPPORTED, "kx_apply_fL_noalloc: needs a KX_F16X3 plan");
+    const long long N = (long long)p->N;
+    if ((size_t)n_rhs * (size_t)N > kNoAllocMaxElems)
+        return set_error(KX_ERR_ARG, "kx_apply_fL_noalloc: n_rhs * N = " + std::to_string((size_t)n_rhs * N) +
+                                         " exceeds the static scratch limit of " +
+                                         std::to_string(kNoAllocMaxElems) + " grid values; split the call");
+    int dev = -1;
+    KX_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != p->device) return set_error(KX_ERR_ARG, "kx_apply_fL_noalloc: call on the plan's device");
+    void *base = nullptr;
+    if (int rc = noalloc_scratch(dev, &base)) return rc;
+    const size_t elems = (size_t)n_rhs * (size_t)N;
+    float *b32 = reinterpret_cast<float *>(base);
+    float *T0 = b32 + elems;
+    float *T1 = T0 + elems;
+    float *src_max = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(base) +
+                                               3 * kNoAllocMaxElems * sizeof(float));
+    float *mx1 = src_max + kNoAllocMaxVec, *mx2 = mx1 + kNoAllocMaxVec, *mx3 = mx2 + kNoAllocMaxVec,
+          *mx4 = mx3 + kNoAllocMaxVec;
+    KX_CUDA_TRY(cudaMemsetAsync(src_max, 0, 5 * kNoAllocMaxVec * sizeof(float), s));
+    int rc;
+    dim3 g((unsigned)std::min<long long>((N + 255) / 256, 64), (unsigned)n_rhs);
+    prep_kernel<<<g, 256, 0, s>>>(b, b32, src_max, n_rhs, N);
+    KX_LAUNCH_CHECK("prep_kernel launch");
+    PassArgs a{};
+    a.rhs_mode = 1;
+    a.f32 = p->d_f32;
+    a.mid_bound = fmax_sqrt(p);
+    a.src_max = src_max;
+    a.rows_pp = (long long)p->n[0] * p->n[1];
+    a.total_rows = n_rhs * a.rows_pp;
+    a.in = b32;
+    a.out = T0;
+    a.out_max = mx1;
+    if ((rc = launch_pass<P_X3F>(p, a, 2, s, nullptr))) return rc;
+    a.rows_pp = (long long)p->n[2] * p->n[0];
+    a.total_rows = n_rhs * a.rows_pp;
+    a.in = T0;
+    a.in_max = mx1;
+    a.out = T1;
+    a.out_max = mx2;
+    if ((rc = launch_pass<P_X2F>(p, a, 1, s, nullptr))) return rc;
+    a.rows_pp = (long long)p->n[2] * p->n[1];
+    a.total_rows = n_rhs * a.rows_pp;
+    a.in = T1;
+    a.in_max = mx2;
+    a.out = T0;
+    a.out_max = mx3;
+    if ((rc = launch_pass<P_X1>(p, a, 0, s, nullptr))) return rc;
+    a.rows_pp = (long long)p->n[2] * p->n[0];
+    a.total_rows = n_rhs * a.rows_pp;
+    a.in = T0;
+    a.in_max = mx3;
+    a.out = T1;
+    a.out_max = mx4;
+    if ((rc = launch_pass<P_X2I>(p, a, 1, s, nullptr))) return rc;
+    a.rows_pp = (long long)p->n[0] * p->n[1];
+    a.total_rows = n_rhs * a.rows_pp;
+    a.in = T1;
+    a.in_max = mx4;
+    a.out = nullptr;
+    a.out_max = nullptr;
+    a.xout = x;
+    return launch_pass<P_X3I>(p, a, 2, s, nullptr);
 }
 
 }  // namespace kx

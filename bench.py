@@ -194,7 +194,8 @@ def pass_model(n):
         "X2F": (2.0 * N * n2, 8.0 * N),
         "X1": (4.0 * N * n1, 8.0 * N),                  # forward + inverse mode 1 in one pass
         "X2I": (2.0 * N * n2, 8.0 * N),
-        "X3I": (2.0 * N * n3, 4.0 * N + 8.0 * N + 16.0 * N),  # read coefficients, two orbitals, two fp32 RMW
+        "X3I": (2.0 * N * n3, 8.0 * N),                 # read coefficients, write phi
+        "acc": (4.0 * N, 12.0 * N),                      # read phi; orbital reads and accumulator RMW per group
     }
 
 

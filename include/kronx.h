@@ -154,8 +154,12 @@ int kx_vx_apply(kx_plan *plan, int n_orb, const double *psi, const double *occ,
                 double *vx_psi, double *e_x, kx_stream stream);
 
 /* kx_vx_apply_pairs — the part of kx_vx_apply contributed by a contiguous range
- * [pair_begin, pair_end) of the symmetric pair list (row-major upper triangle:
- * (0,0), (0,1), ..., (0,n_orb-1), (1,1), ...).  vx_psi and e_x receive the
+ * [pair_begin, pair_end) of the library's list of the n_orb (n_orb+1)/2
+ * unordered pairs (i <= j).  The list groups orbitals in blocks of four
+ * (block b = orbitals 4b .. 4b+3, the last block possibly shorter) and visits
+ * block pairs (I, J), I <= J, row-major; inside a diagonal block (I, I) the
+ * pairs i <= j row-major, inside an off-diagonal block all (i, j) row-major.
+ * vx_psi and e_x receive the
  * partial sums of Eqs. 3-5 over that range (overwritten, not added), so that
  * ranges covering the list sum to the full result: the unit a multi-GPU split
  * of the pair solves (Sec. 3: the O(Nk^2 Ns^2) systems are independent)
@@ -234,8 +238,8 @@ int kx_profile(kx_plan *plan, int enable);
  * mode 3 forward), 2 X2F (mode 2 forward), 3 X1 (mode 1 forward, f(Lambda)
  * scaling and energy, mode 1 inverse), 4 X2I (mode 2 inverse), 5 X3I (mode 3
  * inverse and Vx psi accumulation), 6 finalize/energy sums, 7 float64 mode
- * products, 8 other float64 kernels, 9 ACE, 10 set-up.  Synchronises on the
- * recorded events. */
+ * products, 8 other float64 kernels, 9 ACE, 10 set-up, 11 accumulation of
+ * g psi phi into Vx psi.  Synchronises on the recorded events. */
 int kx_profile_read(kx_plan *plan, int n_kinds, double *ms, long long *launches);
 
 /* kx_last_error_detail — copies the last error message of the calling host

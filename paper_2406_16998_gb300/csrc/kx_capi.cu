@@ -51,28 +51,79 @@ int ensure_workspace(kx_plan *p, size_t bytes) {
     return KX_OK;
 }
 
-int ensure_pairs(kx_plan *p, int n_orb, cudaStream_t s) {
+// Pair enumeration: orbitals in blocks of kOrbBlock; block pairs (I, J), I <= J,
+// in row-major order; inside a diagonal block the upper triangle row-major,
+// inside an off-diagonal block all (i, j) row-major.  Each block pair is one
+// accumulation group.  [begin, end) restricts the list to a sub-range of this
+// enumeration (groups are cut at the range ends).
+int ensure_pairs(kx_plan *p, int n_orb, cudaStream_t s, long long begin, long long end) {
     (void)s;
-    if (p->ws_norb == n_orb) return KX_OK;
-    const size_t P = (size_t)n_orb * (n_orb + 1) / 2;
+    const long long P_all = (long long)n_orb * (n_orb + 1) / 2;
+    if (end < 0) end = P_all;
+    if (p->ws_norb == n_orb && p->pr_begin == begin && p->pr_end == end) return KX_OK;
+    std::vector<int> pairs, slots;
+    std::vector<Group> groups;
+    std::vector<int> first;
+    pairs.reserve(2 * (size_t)(end - begin));
+    slots.reserve(2 * (size_t)(end - begin));
+    const int nb = (n_orb + kOrbBlock - 1) / kOrbBlock;
+    long long k = 0;
+    for (int IB = 0; IB < nb; ++IB) {
+        for (int JB = IB; JB < nb; ++JB) {
+            const int I0 = IB * kOrbBlock, bi = std::min(kOrbBlock, n_orb - I0);
+            const int J0 = JB * kOrbBlock, bj = std::min(kOrbBlock, n_orb - J0);
+            Group g{};
+            g.first_item = (int)(pairs.size() / 2);
+            g.n_items = 0;
+            g.n_slots = (IB == JB) ? bi : bi + bj;
+            for (int t = 0; t < bi; ++t) g.orb[t] = I0 + t;
+            if (IB != JB)
+                for (int t = 0; t < bj; ++t) g.orb[bi + t] = J0 + t;
+            for (int si = 0; si < bi; ++si) {
+                for (int sj = (IB == JB ? si : 0); sj < (IB == JB ? bi : bj); ++sj, ++k) {
+                    if (k < begin || k >= end) continue;
+                    pairs.push_back(I0 + si);
+                    pairs.push_back((IB == JB ? I0 : J0) + sj);
+                    slots.push_back(si);
+                    slots.push_back(IB == JB ? sj : bi + sj);
+                    ++g.n_items;
+                }
+            }
+            if (g.n_items > 0) {
+                groups.push_back(g);
+                first.push_back(g.first_item);
+            }
+        }
+    }
+    first.push_back((int)(pairs.size() / 2));
+    const size_t P = pairs.size() / 2;
     if (P > p->pairs_cap) {
         cudaFree(p->d_pairs);
-        p->d_pairs = nullptr;
+        cudaFree(p->d_item_slot);
+        p->d_pairs = p->d_item_slot = nullptr;
         p->pairs_cap = 0;
-        cudaError_t e = cudaMalloc(&p->d_pairs, sizeof(int) * 2 * P);
+        cudaError_t e = cudaMalloc(&p->d_pairs, sizeof(int) * 2 * std::max<size_t>(P, 1));
+        if (e == cudaSuccess) e = cudaMalloc(&p->d_item_slot, sizeof(int) * 2 * std::max<size_t>(P, 1));
         if (e != cudaSuccess) return cuda_error(e, "pair list cudaMalloc");
         p->pairs_cap = P;
     }
-    std::vector<int> h(2 * P);
-    size_t k = 0;
-    for (int i = 0; i < n_orb; ++i)
-        for (int j = i; j < n_orb; ++j) {
-            h[2 * k] = i;
-            h[2 * k + 1] = j;
-            ++k;
-        }
-    KX_CUDA_TRY(cudaMemcpy(p->d_pairs, h.data(), sizeof(int) * 2 * P, cudaMemcpyHostToDevice));
+    if (groups.size() > p->groups_cap) {
+        cudaFree(p->d_groups);
+        p->d_groups = nullptr;
+        p->groups_cap = 0;
+        cudaError_t e = cudaMalloc(&p->d_groups, sizeof(Group) * groups.size());
+        if (e != cudaSuccess) return cuda_error(e, "group table cudaMalloc");
+        p->groups_cap = groups.size();
+    }
+    if (P) {
+        KX_CUDA_TRY(cudaMemcpy(p->d_pairs, pairs.data(), sizeof(int) * 2 * P, cudaMemcpyHostToDevice));
+        KX_CUDA_TRY(cudaMemcpy(p->d_item_slot, slots.data(), sizeof(int) * 2 * P, cudaMemcpyHostToDevice));
+        KX_CUDA_TRY(cudaMemcpy(p->d_groups, groups.data(), sizeof(Group) * groups.size(), cudaMemcpyHostToDevice));
+    }
+    p->h_group_first = first;
     p->ws_norb = n_orb;
+    p->pr_begin = begin;
+    p->pr_end = end;
     return KX_OK;
 }
 

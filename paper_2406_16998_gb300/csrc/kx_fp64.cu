@@ -220,10 +220,11 @@ int fp64_apply_fL(kx_plan *p, int n_rhs, const double *b, double *x, cudaStream_
 
 int fp64_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, double *vx, double *ex,
             bool energy_only, cudaStream_t s, long pair_begin, long pair_end) {
-    int rc = ensure_pairs(p, n_orb, s);
+    int rc = ensure_pairs(p, n_orb, s, pair_begin, pair_end);
     if (rc) return rc;
-    if (pair_end < 0) pair_end = (long)n_orb * (n_orb + 1) / 2;
-    long P = pair_end - pair_begin;
+    long P = p->h_group_first.back();  // items of the (range-restricted) pair list
+    pair_begin = 0;
+    pair_end = P;
     long chunk = fp64_chunk(p, std::max(1L, P));
     rc = ensure_workspace(p, fp64_workspace_bytes(p, chunk));
     if (rc) return rc;

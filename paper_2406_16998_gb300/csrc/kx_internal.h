@@ -29,6 +29,17 @@ int cuda_error(cudaError_t e, const char *what);
     } while (0)
 
 constexpr int kMaxN = 128;       // per-axis limit of this build
+constexpr int kOrbBlock = 4;     // orbitals per block of the pair enumeration
+constexpr int kGroupSlots = 2 * kOrbBlock;
+
+// One accumulation group: the pairs of one orbital block pair (I, J), I <= J
+// (a contiguous run of items), touching at most kGroupSlots orbitals.
+struct Group {
+    int first_item;
+    int n_items;
+    int n_slots;
+    int orb[kGroupSlots];
+};
 constexpr int kTile = 128;       // tcgen05 M (rows of pencils per tile)
 constexpr float kVScale = 16384.f;  // V operand scale 2^14 (|V| <= 1)
 constexpr int kVScaleExp = 14;
@@ -43,7 +54,7 @@ struct TuneParams {
 
 // Per-launch CUDA-event timing by kernel kind (kx_profile / kx_profile_read).
 enum ProfKind { PK_PREP = 0, PK_X3F, PK_X2F, PK_X1, PK_X2I, PK_X3I, PK_FINAL, PK_FP64_MODE, PK_FP64_OTHER,
-                PK_ACE, PK_SETUP, PK_COUNT };
+                PK_ACE, PK_SETUP, PK_ACC, PK_COUNT };
 struct Profiler {
     bool on = false;
     std::vector<cudaEvent_t> pool;       // reusable events
@@ -90,9 +101,15 @@ struct kx_plan_s {
     kx::TuneParams tune;
     kx::Workspace ws;        // chunk buffers and per-pair scratch
     kx::Workspace ws_host;   // device staging for kx_vx_apply_host
-    int ws_norb = -1;        // orbital count the pair list currently describes
-    int *d_pairs = nullptr;  // int2 per pair (i, j), symmetric enumeration
-    size_t pairs_cap = 0;
+    // Pair enumeration (orbital blocks of kx::kOrbBlock, see ensure_pairs) and its
+    // accumulation groups, rebuilt when n_orb or the pair range changes.
+    int ws_norb = -1;
+    long long pr_begin = -1, pr_end = -1;
+    int *d_pairs = nullptr;       // int2 per item (i, j), i <= j
+    int *d_item_slot = nullptr;   // int2 per item: slots of i and j inside its group
+    int *d_groups = nullptr;      // kx::Group per group
+    size_t pairs_cap = 0, groups_cap = 0;
+    std::vector<int> h_group_first;  // first item of each group (+ sentinel)
     kx::Profiler prof;
 };
 
@@ -108,7 +125,7 @@ void plan_free(kx_plan *p);
 
 // ---- workspace (kx_capi.cu)
 int ensure_workspace(kx_plan *p, size_t bytes);
-int ensure_pairs(kx_plan *p, int n_orb, cudaStream_t s);
+int ensure_pairs(kx_plan *p, int n_orb, cudaStream_t s, long long begin = 0, long long end = -1);
 
 // ---- FP64 path (kx_fp64.cu)
 int fp64_apply_fL(kx_plan *p, int n_rhs, const double *b, double *x, cudaStream_t s);

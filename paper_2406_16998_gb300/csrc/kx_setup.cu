@@ -305,6 +305,8 @@ void plan_free(kx_plan *p) {
     cudaFree(p->ws.ptr);
     cudaFree(p->ws_host.ptr);
     cudaFree(p->d_pairs);
+    cudaFree(p->d_item_slot);
+    cudaFree(p->d_groups);
 }
 
 }  // namespace kx

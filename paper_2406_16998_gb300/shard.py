@@ -18,12 +18,26 @@ def pair_range(n_orb: int, rank: int, world: int):
     return (rank * P) // world, ((rank + 1) * P) // world
 
 
+ORB_BLOCK = 4  # orbitals per block of the library's pair enumeration
+
+
+def pair_list(n_orb: int):
+    """The library's enumeration of the unordered pairs (i <= j): orbitals in
+    blocks of ORB_BLOCK, block pairs (I, J), I <= J, row-major; inside a
+    diagonal block i <= j row-major, inside an off-diagonal block all (i, j)."""
+    out = []
+    nb = (n_orb + ORB_BLOCK - 1) // ORB_BLOCK
+    for IB in range(nb):
+        for JB in range(IB, nb):
+            I = range(IB * ORB_BLOCK, min(n_orb, (IB + 1) * ORB_BLOCK))
+            J = range(JB * ORB_BLOCK, min(n_orb, (JB + 1) * ORB_BLOCK))
+            for i in I:
+                for j in J:
+                    if IB != JB or j >= i:
+                        out.append((i, j))
+    return out
+
+
 def pair_at(n_orb: int, k: int):
-    """(i, j) of entry k of the row-major upper-triangular list (i <= j)."""
-    i = 0
-    row = n_orb
-    while k >= row:
-        k -= row
-        i += 1
-        row -= 1
-    return i, i + k
+    """(i, j) of entry k of the library's pair enumeration."""
+    return pair_list(n_orb)[k]

@@ -20,9 +20,9 @@
 // accumulators, one thread per four grid points, group by group.
 //
 // Each pass kernel is persistent (one CTA per SM) and warp-specialised:
-//   warps 0-7   epilogue (TMEM lane quadrant = warp % 4, column half = warp / 4)
-//   warps 8-15  producers: global fp32 -> scale -> fp16 hi/lo -> shared stage
-//   warp 16     TMEM allocation and MMA issue (one thread)
+//   warps 0-3   epilogue (TMEM lane quadrant = warp; one tile row per thread)
+//   warps 4-11  producers: global fp32 -> scale -> fp16 hi/lo -> shared stage
+//   warp 12     TMEM allocation and MMA issue (one thread)
 // with an S-deep ring of shared A stages and two TMEM accumulator slots, so
 // loads, MMAs and stores of consecutive tiles overlap.
 #include "kx_internal.h"
@@ -30,6 +30,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <string>
 
 namespace kx {
@@ -37,15 +38,41 @@ namespace {
 
 enum PassKind { P_X3F = 0, P_X2F = 1, P_X1 = 2, P_X2I = 3, P_X3I = 4 };
 
-constexpr int kEpiWarps = 8;
+constexpr int kEpiWarps = 4;
 constexpr int kProdWarps = 8;
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kProdThreads = 32 * kProdWarps;
+constexpr int kProdGroups = 2;                            // producer groups work on alternate tiles
+constexpr int kGroupThreads = kProdThreads / kProdGroups;  // 128: one thread per row for the K-major pass
 constexpr int kMmaWarp = kEpiWarps + kProdWarps;
 constexpr int kThreads = 32 * (kEpiWarps + kProdWarps + 1);
 constexpr int kMaxStages = 4;
-constexpr int kProdUnroll = 3;
-constexpr size_t kSmemBudget = 225 * 1024;
+constexpr size_t kSmemBudget = 222 * 1024;
+
+// Optional per-role cycle counters (compile with -DKX_ROLE_CLOCKS): each CTA
+// writes kClk counters to PassArgs::clk[blockIdx.x * kClk + k].
+constexpr int kClk = 12;
+#ifdef KX_ROLE_CLOCKS
+long long *g_clkbuf = nullptr;
+#define KX_CLK_NOW() clock64()
+#define KX_CLK_ADD(k, t0) (clk_acc[(k)] += clock64() - (t0))
+#else
+#define KX_CLK_NOW() 0LL
+#define KX_CLK_ADD(k, t0) ((void)(t0))
+#endif
+
+// Shared-memory layout of the A operand (no swizzle, 8x8 fp16 core matrices of
+// 128 contiguous bytes).  Core matrices sit kCoreStride = 144 bytes apart
+// (128 + 16 of padding) so that a warp writing one 16-byte row into each of
+// eight neighbouring core matrices hits eight different bank groups.
+//   MN-major (8 rows contiguous in a core-matrix row):
+//     (m, k) at (m/8)*144 + (k/8)*(16*144) + (k%8)*16 + (m%8)*2
+//     descriptor: K-direction offset 16*144, M-direction offset 144
+//   K-major (8 k contiguous in a core-matrix row), nkc = np/8:
+//     (m, k) at (m/8)*(nkc*144) + (k/8)*144 + (m%8)*16 + (k%8)*2
+//     descriptor: K-direction offset 144, M-direction offset nkc*144
+constexpr int kCoreStride = 144;
+__host__ __device__ constexpr size_t a_half_bytes(int np) { return (size_t)np * 16 * kCoreStride / 8; }
 
 struct PassArgs {
     int n1, n2, n3;
@@ -73,6 +100,7 @@ struct PassArgs {
     double *xout;          // vector mode output of X3I (fp64)
     int *status;
     long long timeout_cycles;
+    long long *clk;        // role counters (only with KX_ROLE_CLOCKS)
 };
 
 __device__ __forceinline__ int scale_exp(float mx) {
@@ -112,99 +140,140 @@ __device__ __forceinline__ float item_in_max(const PassArgs &a, long long item) 
     return a.in_max[item];
 }
 
-// Source address of task t (8 consecutive fp32 values) of a tile and its
-// shared-memory offset; returns false for padding (zero) tasks.  Pair mode of
-// X3F has two sources (psi_i, psi_j).
+// Per-tile source descriptors, computed once per tile by the producers: for
+// the MN-major passes one per group of 8 rows (row (m, k) of the group reads
+// p0 + k * kstride, 8 consecutive rows contiguous), for the K-major pass one per
+// row (chunk kc reads p0 + 8 kc).  p0 == nullptr marks rows past the end.
+struct SrcDesc {
+    const float *p0[128];
+    const float *p1[16];  // second orbital of the pair product (X3F pair mode)
+    float scale[128];
+};
+
 template <int PASS>
-__device__ __forceinline__ bool task_src(const PassArgs &a, long long tile, int t, const float *&p0,
-                                         const float *&p1, float &scale, int &soff) {
-    const int kp = a.np;
+__device__ __forceinline__ void make_desc(const PassArgs &a, long long tile, SrcDesc &d, int ptid) {
     const long long n12 = (long long)a.n1 * a.n2;
+    const int nd = (PASS == P_X1) ? 128 : 16;
+    if (ptid >= nd) return;
+    const long long R0 = tile * 128 + (PASS == P_X1 ? ptid : 8 * ptid);  // < 2^31: 32-bit division below
+    if (R0 >= a.total_rows) {
+        d.p0[ptid] = nullptr;
+        if (PASS == P_X3F) d.p1[ptid] = nullptr;
+        d.scale[ptid] = 0.f;
+        return;
+    }
+    const unsigned rpp = (unsigned)a.rows_pp;
+    const long long item = (unsigned)R0 / rpp, local = (unsigned)R0 % rpp;
+    d.scale[ptid] = ldexpf(1.f, scale_exp(item_in_max<PASS>(a, item)));
     if (PASS == P_X1) {
-        // K-major: element (m, k) at (m/8)*(kp*16) + (k/8)*128 + (m%8)*16 + (k%8)*2
-        const int nkc = kp >> 3;
-        const int mi = t & 7;
-        const int kc = (t >> 3) % nkc;
-        const int mg = (t >> 3) / nkc;
-        soff = mg * (kp * 16) + kc * 128 + mi * 16;
-        const long long R = tile * 128 + mg * 8 + mi;
-        if (R >= a.total_rows || kc * 8 >= a.nc) return false;
-        const long long item = R / a.rows_pp, local = R % a.rows_pp;
-        p0 = a.in + item * a.N + local * a.n1 + kc * 8;
-        p1 = nullptr;
-        scale = ldexpf(1.f, scale_exp(item_in_max<PASS>(a, item)));
-        return true;
-    } else {
-        // MN-major: element (m, k) at (m/8)*128 + (k/8)*2048 + (k%8)*16 + (m%8)*2
-        const int ki = t & 7;
-        const int g = (t >> 3) & 15;
-        const int kg = t >> 7;
-        const int k = kg * 8 + ki;
-        soff = g * 128 + kg * 2048 + ki * 16;
-        const long long R0 = tile * 128 + g * 8;
-        if (R0 >= a.total_rows || k >= a.nc) return false;
-        const long long item = R0 / a.rows_pp, local = R0 % a.rows_pp;
-        scale = ldexpf(1.f, scale_exp(item_in_max<PASS>(a, item)));
-        p1 = nullptr;
-        if (PASS == P_X3F) {
-            const long long x = (long long)k * n12 + local;  // (x3 = k, position = local)
-            if (a.rhs_mode) {
-                p0 = a.in + item * a.N + x;
-            } else {
-                const int2 ij = a.pairs[item];
-                p0 = a.psi32 + (long long)ij.x * a.N + x;
-                p1 = a.psi32 + (long long)ij.y * a.N + x;
-            }
-        } else if (PASS == P_X2F || PASS == P_X2I) {
-            const long long k3 = local / a.n1, x1 = local % a.n1;  // rows (k3, x1)
-            p0 = a.in + item * a.N + k3 * n12 + (long long)k * a.n1 + x1;
-        } else {  // P_X3I: rows = positions, K = k3
-            p0 = a.in + item * a.N + (long long)k * n12 + local;
+        d.p0[ptid] = a.in + item * a.N + local * a.n1;
+    } else if (PASS == P_X3F) {
+        if (a.rhs_mode) {
+            d.p0[ptid] = a.in + item * a.N + local;
+            d.p1[ptid] = nullptr;
+        } else {
+            const int2 ij = a.pairs[item];
+            d.p0[ptid] = a.psi32 + (long long)ij.x * a.N + local;
+            d.p1[ptid] = a.psi32 + (long long)ij.y * a.N + local;
         }
-        return true;
+    } else if (PASS == P_X2F || PASS == P_X2I) {
+        const long long k3 = (unsigned)local / (unsigned)a.n1, x1 = (unsigned)local % (unsigned)a.n1;  // rows (k3, x1)
+        d.p0[ptid] = a.in + item * a.N + k3 * n12 + x1;
+    } else {  // P_X3I: rows = positions
+        d.p0[ptid] = a.in + item * a.N + local;
+    }
+}
+
+template <int PASS, int U, bool TWO>
+__device__ __forceinline__ void produce_tile_u(const PassArgs &a, const SrcDesc &d, uint8_t *Ahi, uint8_t *Alo,
+                                               int ptid) {
+    const int np = a.np;
+    const int nkc = np >> 3;
+    const int ntask = 16 * np;  // 128 rows x np columns / 8
+    const unsigned magic = (65536u + (unsigned)nkc - 1u) / (unsigned)nkc;  // t / nkc == (t * magic) >> 16 for t < 2^11
+    const long long kstride = (PASS == P_X3F || PASS == P_X3I) ? (long long)a.n1 * a.n2 : (long long)a.n1;
+    for (int t0 = ptid; t0 < ntask; t0 += kGroupThreads * U) {
+        float v[U][8];
+        float u[TWO ? U : 1][8];
+        // issue every load of the batch first (padding tasks read nothing)
+#pragma unroll
+        for (int r = 0; r < U; ++r) {
+            const int t = t0 + r * kGroupThreads;
+            const float *p0 = nullptr;
+            const float *p1 = nullptr;
+            bool ok = false;
+            if (t < ntask) {
+                if (PASS == P_X1) {
+                    // lanes walk the 8-value chunks of one row, then the next row: contiguous reads
+                    const int m = (int)(((unsigned)t * magic) >> 16), kc = t - m * nkc;
+                    p0 = d.p0[m];
+                    ok = p0 != nullptr && kc * 8 < a.nc;
+                    if (ok) p0 += kc * 8;
+                } else {
+                    // lanes walk the 16 row groups at one k, then the next k: 16 x 32 contiguous bytes
+                    const int g = t & 15, k = t >> 4;
+                    p0 = d.p0[g];
+                    ok = p0 != nullptr && k < a.nc;
+                    if (ok) {
+                        p0 += k * kstride;
+                        if (TWO) p1 = d.p1[g] + k * kstride;
+                    }
+                }
+            }
+            if (ok) {
+                ld8(p0, v[r]);
+                if (TWO) ld8(p1, u[TWO ? r : 0]);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) v[r][c] = 0.f;
+                if (TWO) {
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) u[TWO ? r : 0][c] = 0.f;
+                }
+            }
+        }
+        // then scale, split and store (offsets and scales re-derived from t)
+#pragma unroll
+        for (int r = 0; r < U; ++r) {
+            const int t = t0 + r * kGroupThreads;
+            if (t >= ntask) continue;
+            int off;
+            float sc;
+            if (PASS == P_X1) {
+                const int m = (int)(((unsigned)t * magic) >> 16), kc = t - m * nkc;
+                off = (m >> 3) * (nkc * kCoreStride) + kc * kCoreStride + (m & 7) * 16;
+                sc = d.scale[m];
+            } else {
+                const int g = t & 15, k = t >> 4;
+                off = g * kCoreStride + (k >> 3) * (16 * kCoreStride) + (k & 7) * 16;
+                sc = d.scale[g];
+            }
+            float w[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) w[c] = (TWO ? v[r][c] * u[TWO ? r : 0][c] : v[r][c]) * sc;
+            uint4 hi4, lo4;
+            split8(w, hi4, lo4);
+            *reinterpret_cast<uint4 *>(Ahi + off) = hi4;
+            *reinterpret_cast<uint4 *>(Alo + off) = lo4;
+        }
     }
 }
 
 // Producer side: stage one 128-row tile of the A operand (scaled, split).
-// The loads of kProdUnroll tasks are issued before any of them is converted.
+// Task t covers 8 consecutive values: MN-major row group g = t%16 at k = t/16;
+// K-major row m = t/nkc, chunk kc = t%nkc.  Consecutive lanes therefore read
+// consecutive global addresses.  All loads of a batch of U tasks (a whole tile for n <= 96 when U = 12) are
+// issued before any is converted, so each thread keeps U*32 bytes in flight.
 template <int PASS>
-__device__ __forceinline__ void produce_tile(const PassArgs &a, long long tile, uint8_t *Ahi, uint8_t *Alo,
+__device__ __forceinline__ void produce_tile(const PassArgs &a, const SrcDesc &d, uint8_t *Ahi, uint8_t *Alo,
                                              int ptid) {
-    const int ntask = (PASS == P_X1) ? 128 * (a.np >> 3) : 16 * a.np;
-    const bool two = (PASS == P_X3F) && !a.rhs_mode;
-    for (int t0 = ptid; t0 < ntask; t0 += kProdThreads * kProdUnroll) {
-        float v[kProdUnroll][8], u[kProdUnroll][8];
-        float sc[kProdUnroll];
-        int off[kProdUnroll];
-        bool ok[kProdUnroll];
-#pragma unroll
-        for (int r = 0; r < kProdUnroll; ++r) {
-            const int t = t0 + r * kProdThreads;
-            const float *p0 = nullptr, *p1 = nullptr;
-            ok[r] = false;
-            off[r] = -1;
-            sc[r] = 0.f;
-            if (t < ntask) ok[r] = task_src<PASS>(a, tile, t, p0, p1, sc[r], off[r]);
-            if (ok[r]) {
-                ld8(p0, v[r]);
-                if (two) ld8(p1, u[r]);
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < kProdUnroll; ++r) {
-            if (off[r] < 0) continue;
-            float w[8];
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                float x = ok[r] ? v[r][c] : 0.f;
-                if (two && ok[r]) x *= u[r][c];
-                w[c] = x * sc[r];
-            }
-            uint4 hi, lo;
-            split8(w, hi, lo);
-            *reinterpret_cast<uint4 *>(Ahi + off[r]) = hi;
-            *reinterpret_cast<uint4 *>(Alo + off[r]) = lo;
-        }
+    if (PASS == P_X3F) {
+        if (a.rhs_mode)
+            produce_tile_u<PASS, 6, false>(a, d, Ahi, Alo, ptid);
+        else
+            produce_tile_u<PASS, 6, true>(a, d, Ahi, Alo, ptid);
+    } else {
+        produce_tile_u<PASS, 12, false>(a, d, Ahi, Alo, ptid);
     }
 }
 
@@ -217,9 +286,9 @@ __device__ __forceinline__ void produce_tile(const PassArgs &a, long long tile, 
 __device__ __forceinline__ void issue_split_mma(uint32_t tmem_a, uint32_t tmem_b, uint32_t a_hi, uint32_t a_lo,
                                                 bool a_kmajor, uint32_t v_hi, uint32_t v_lo, bool inverse, int np) {
     const uint32_t idesc = ptx::idesc_f16(128, np, a_kmajor ? 0 : 1, inverse ? 0 : 1);
-    const uint32_t a_lbo = a_kmajor ? 128u : 2048u;
-    const uint32_t a_sbo = a_kmajor ? (uint32_t)(np * 16) : 128u;
-    const uint32_t a_step = a_kmajor ? 256u : 4096u;
+    const uint32_t a_lbo = a_kmajor ? (uint32_t)kCoreStride : (uint32_t)(16 * kCoreStride);
+    const uint32_t a_sbo = a_kmajor ? (uint32_t)((np >> 3) * kCoreStride) : (uint32_t)kCoreStride;
+    const uint32_t a_step = 2 * a_lbo;  // one k-step = two core matrices along K
     // V stored as 8x8 core matrices, row block of 8 x-rows = np*16 bytes.
     //   forward  (B[x][k] = V[x][k]): MN-major, K (=x) stride np*16, N (=k) stride 128
     //   inverse  (B[k][x] = V[x][k]): K-major,  K (=k) stride 128,   N (=x) stride np*16
@@ -242,17 +311,6 @@ __device__ __forceinline__ void issue_split_mma(uint32_t tmem_a, uint32_t tmem_b
             ptx::mma_f16(tmem_b, ah, bh, idesc, ks > 1 ? 1u : 0u);
         else
             ptx::mma_f16(tmem_a, ah, bh, idesc, 1u);
-    }
-}
-
-// Da + Db for 16 columns of this thread's lane (Db is empty when K = 16).
-__device__ __forceinline__ void tmem_ld16_sum(uint32_t ta, uint32_t tb, bool two, float *v) {
-    ptx::tmem_ld16(ta, v);
-    if (two) {
-        float w[16];
-        ptx::tmem_ld16(tb, w);
-#pragma unroll
-        for (int c = 0; c < 16; ++c) v[c] += w[c];
     }
 }
 
@@ -279,6 +337,18 @@ __device__ __forceinline__ bool wait_bar_warp(uint64_t *bar, uint32_t parity, co
     return __all_sync(0xffffffffu, ok);
 }
 
+// The threads of one producer group agree on `ok` and have finished their
+// previous tile (a named barrier of the group, then a vote through shared memory).
+__device__ __forceinline__ bool producers_agree(bool ok, int *flag, int gtid, int bar_id) {
+    if (gtid == 0) *flag = 1;
+    ptx::named_bar(bar_id, kGroupThreads);
+    if (!ok) *flag = 0;
+    ptx::named_bar(bar_id, kGroupThreads);
+    const bool r = *flag != 0;
+    ptx::named_bar(bar_id, kGroupThreads);
+    return r;
+}
+
 __device__ __forceinline__ void track_max(float *out_max, long long item, float m, bool valid) {
     if (out_max == nullptr) return;
     const long long item0 = __shfl_sync(0xffffffffu, item, 0);
@@ -299,9 +369,44 @@ struct Bars {
     uint64_t tempty[2];
     uint64_t tfull2[2];
     uint64_t mid_full;
-    uint64_t mid_empty;
     uint64_t drain;
 };
+
+// X1 epilogue, inverse half of tile j: wait for its inverse MMA, unscale and
+// store the row (float4 per 4 columns), track the maximum, release the slot.
+__device__ __forceinline__ bool x1_inverse_half(const PassArgs &a, Bars &bars, uint32_t tmem, int q, int m, int j,
+                                                int np, bool two_acc, bool valid, long long item, long long local,
+                                                float unscale2, volatile int *abort) {
+    const int b = j & 1;
+    if (!wait_bar_warp(&bars.tfull2[b], (uint32_t)((j >> 1) & 1), a, abort)) return false;
+    ptx::tc_fence_after();
+    const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * 2 * np);
+    const uint32_t tb = ta + (uint32_t)np;
+    float my_max = 0.f;
+    float *orow = a.out + item * a.N + local * a.n1;
+    for (int c = 0; c < (np >> 4); ++c) {
+        float v[16], vb[16];
+        ptx::tmem_ld16x2(ta + 16 * c, tb + 16 * c, v, vb);
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {  // store each 8-column half that lies inside the row
+            if (!valid || 16 * c + 8 * h2 >= a.nc) continue;
+            float wv[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                wv[k] = (two_acc ? v[8 * h2 + k] + vb[8 * h2 + k] : v[8 * h2 + k]) * unscale2;
+                my_max = fmaxf(my_max, fabsf(wv[k]));
+            }
+            float4 *dst = reinterpret_cast<float4 *>(orow + 16 * c + 8 * h2);
+            dst[0] = make_float4(wv[0], wv[1], wv[2], wv[3]);
+            dst[1] = make_float4(wv[4], wv[5], wv[6], wv[7]);
+        }
+    }
+    track_max(a.out_max, item, my_max, valid);
+    ptx::tc_fence_before();
+    ptx::mbar_arrive(&bars.tempty[b]);
+    (void)m;
+    return true;
+}
 
 template <int PASS>
 __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const PassArgs a) {
@@ -309,18 +414,23 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const PassArgs a) 
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int np = a.np;
     const int S = a.stages;
-    const size_t stage_bytes = (size_t)2 * 128 * np * 2;  // hi + lo
+    const size_t half_bytes = a_half_bytes(np);
+    const size_t stage_bytes = 2 * half_bytes;  // hi + lo
     uint8_t *Vhi = smem;
     uint8_t *Vlo = Vhi + np * np * 2;
     uint8_t *stage0 = Vlo + np * np * 2;
-    uint8_t *mid = stage0 + S * stage_bytes;  // X1 only
     __shared__ Bars bars;
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int s_abort;
     __shared__ double s_red[kEpiWarps];
+    __shared__ SrcDesc sdesc[kProdGroups];
+    __shared__ int s_vote[kProdGroups];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool with_inv = (PASS == P_X1) && !a.energy_only;
+#ifdef KX_ROLE_CLOCKS
+    long long clk_acc[kClk] = {0};
+#endif
     const uint32_t tcols = (4 * np <= 256) ? 256u : 512u;
     if (warp == kMmaWarp) {
         ptx::tmem_alloc(&tmem_slot, tcols);
@@ -328,7 +438,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const PassArgs a) 
     }
     if (tid == 0) {
         for (int s = 0; s < S; ++s) {
-            ptx::mbar_init(&bars.full[s], kProdThreads);
+            ptx::mbar_init(&bars.full[s], kGroupThreads);
             ptx::mbar_init(&bars.empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -337,7 +447,6 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const PassArgs a) 
             ptx::mbar_init(&bars.tfull2[b], 1);
         }
         ptx::mbar_init(&bars.mid_full, kEpiThreads);
-        ptx::mbar_init(&bars.mid_empty, 1);
         ptx::mbar_init(&bars.drain, 1);
         ptx::fence_mbar_init();
         s_abort = 0;
@@ -364,33 +473,42 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const PassArgs a) 
             const uint32_t sVhi = ptx::smem_u32(Vhi), sVlo = ptx::smem_u32(Vlo);
             const bool inv = (PASS == P_X2I || PASS == P_X3I);
             bool ok = true;
+            const long long tm0 = KX_CLK_NOW();
             for (int it = 0; it <= n_my && ok; ++it) {
                 if (it < n_my) {
                     const int s = it % S, b = it & 1;
+                    long long tw = KX_CLK_NOW();
                     ok = wait_bar(&bars.full[s], (uint32_t)((it / S) & 1), a, &s_abort);
+                    KX_CLK_ADD(5, tw);
+                    tw = KX_CLK_NOW();
                     if (ok && it >= 2) ok = wait_bar(&bars.tempty[b], (uint32_t)(((it >> 1) - 1) & 1), a, &s_abort);
+                    KX_CLK_ADD(6, tw);
                     if (!ok) break;
                     ptx::tc_fence_after();
                     const uint32_t sA = ptx::smem_u32(stage0 + s * stage_bytes);
                     const uint32_t da = tmem + (uint32_t)(b * 2 * np);
-                    issue_split_mma(da, da + (uint32_t)np, sA, sA + (uint32_t)(128 * np * 2), PASS == P_X1, sVhi,
+                    issue_split_mma(da, da + (uint32_t)np, sA, sA + (uint32_t)half_bytes, PASS == P_X1, sVhi,
                                     sVlo, inv, np);
-                    ptx::mma_commit(&bars.empty[s]);
+                    if (!with_inv) ptx::mma_commit(&bars.empty[s]);  // X1 keeps the stage for its mid operand
                     ptx::mma_commit(&bars.tfull[b]);
                 }
                 if (with_inv && it >= 1) {
-                    const int j = it - 1, b = j & 1;
+                    // inverse of tile j: its mid operand sits in tile j's own A stage
+                    const int j = it - 1, b = j & 1, sj = j % S;
+                    const long long tw = KX_CLK_NOW();
                     ok = wait_bar(&bars.mid_full, (uint32_t)(j & 1), a, &s_abort);
+                    KX_CLK_ADD(7, tw);
                     if (!ok) break;
                     ptx::tc_fence_after();
-                    const uint32_t sM = ptx::smem_u32(mid);
+                    const uint32_t sM = ptx::smem_u32(stage0 + sj * stage_bytes);
                     const uint32_t da = tmem + (uint32_t)(b * 2 * np);
-                    issue_split_mma(da, da + (uint32_t)np, sM, sM + (uint32_t)(128 * np * 2), true, sVhi, sVlo, true,
+                    issue_split_mma(da, da + (uint32_t)np, sM, sM + (uint32_t)half_bytes, true, sVhi, sVlo, true,
                                     np);
-                    ptx::mma_commit(&bars.mid_empty);
+                    ptx::mma_commit(&bars.empty[sj]);
                     ptx::mma_commit(&bars.tfull2[b]);
                 }
             }
+            KX_CLK_ADD(4, tm0);
             if (!ok) {
                 // a wait gave up: one more bounded wait for the MMAs already issued
                 ptx::mma_commit(&bars.drain);
@@ -401,37 +519,73 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const PassArgs a) 
     } else if (warp >= kEpiWarps) {
         // ------------------------------------------------------------ producers
         const int ptid = tid - kEpiThreads;
-        for (int it = 0; it < n_my; ++it) {
+        const int grp = ptid / kGroupThreads, gtid = ptid % kGroupThreads;
+        const long long tp0 = KX_CLK_NOW();
+        for (int it = grp; it < n_my; it += kProdGroups) {  // groups take alternate tiles
             const int s = it % S;
-            if (it >= S && !wait_bar(&bars.empty[s], (uint32_t)(((it / S) - 1) & 1), a, &s_abort)) break;
-            if (s_abort) break;
+            long long tw = KX_CLK_NOW();
+            bool ok = it < S || wait_bar(&bars.empty[s], (uint32_t)(((it / S) - 1) & 1), a, &s_abort);
+            KX_CLK_ADD(1, tw);
+            tw = KX_CLK_NOW();
+            ok = producers_agree(ok, &s_vote[grp], gtid, 2 + 2 * grp);
+            if (!ok) break;
+            make_desc<PASS>(a, blockIdx.x + (long long)it * gridDim.x, sdesc[grp], gtid);
+            ptx::named_bar(3 + 2 * grp, kGroupThreads);
+            KX_CLK_ADD(2, tw);
+            tw = KX_CLK_NOW();
             uint8_t *Ahi = stage0 + s * stage_bytes;
-            produce_tile<PASS>(a, blockIdx.x + (long long)it * gridDim.x, Ahi, Ahi + 128 * np * 2, ptid);
+            produce_tile<PASS>(a, sdesc[grp], Ahi, Ahi + half_bytes, gtid);
             ptx::fence_proxy_async_smem();
             ptx::mbar_arrive(&bars.full[s]);
+            KX_CLK_ADD(3, tw);
         }
+        KX_CLK_ADD(0, tp0);
     } else {
         // ------------------------------------------------------------ epilogue
-        const int q = warp & 3, half = warp >> 2;
+        const int q = warp & 3;
         const int m = 32 * q + lane;  // TMEM lane == tile row of this thread
         const int nch = np >> 4;      // 16-column chunks
         double e_acc = 0.0;
+        bool prev_valid = false;  // X1: the tile whose inverse half is still pending
+        long long prev_item = 0, prev_local = 0;
+        float prev_unscale2 = 0.f;
+        bool aborted = false;
+        const long long te0 = KX_CLK_NOW();
         for (int it = 0; it < n_my; ++it) {
             const int b = it & 1;
+            // row information and the per-item scale do not depend on the MMA:
+            // fetch them (and X1's first f chunk) before waiting for it
+            const long long tile = blockIdx.x + (long long)it * gridDim.x;
+            const long long R = tile * 128 + m;  // < 2^31
+            const bool valid = R < a.total_rows;
+            const unsigned rpp = (unsigned)a.rows_pp;
+            const long long item = valid ? (unsigned)R / rpp : 0;
+            const long long local = valid ? (unsigned)R % rpp : 0;
+            const float in_mx = valid ? item_in_max<PASS>(a, item) : 0.f;
+            float fpre[16];
+            if (PASS == P_X1) {
+#pragma unroll
+                for (int h2 = 0; h2 < 2; ++h2) {
+                    if (valid && 8 * h2 < a.nc) {
+                        ld8(a.f32 + local * a.n1 + 8 * h2, fpre + 8 * h2);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) fpre[8 * h2 + k] = 0.f;
+                    }
+                }
+            }
+            long long tw = KX_CLK_NOW();
             if (!wait_bar_warp(&bars.tfull[b], (uint32_t)((it >> 1) & 1), a, &s_abort)) break;
+            KX_CLK_ADD(9, tw);
+            tw = KX_CLK_NOW();
             ptx::tc_fence_after();
             const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * 2 * np);
             const uint32_t tb = ta + (uint32_t)np;
-            const long long tile = blockIdx.x + (long long)it * gridDim.x;
-            const long long R = tile * 128 + m;
-            const bool valid = R < a.total_rows;
-            const long long item = valid ? R / a.rows_pp : 0;
-            const long long local = valid ? R % a.rows_pp : 0;
-            const float in_mx = valid ? item_in_max<PASS>(a, item) : 0.f;
             const float unscale = ldexpf(1.f, -(scale_exp(in_mx) + kVScaleExp));
             float my_max = 0.f;
 
             if (PASS == P_X1) {
+                // forward half of tile it: energy, f scaling, mid operand into the tile's own A stage
                 const int e_mid = scale_exp(a.mid_bound * in_mx);
                 const float s_mid = ldexpf(1.f, e_mid);
                 double w = 0.0;
@@ -440,25 +594,28 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const PassArgs a) 
                     w = (ij.x == ij.y) ? 1.0 : 2.0;
                     if (a.occ) w *= a.occ[ij.x] * a.occ[ij.y];
                 }
-                if (with_inv && it >= 1 && !wait_bar_warp(&bars.mid_empty, (uint32_t)((it - 1) & 1), a, &s_abort))
-                    break;
+                uint8_t *midh = stage0 + (it % S) * stage_bytes;
                 float e_row = 0.f;
-                for (int c = half; c < nch; c += 2) {
-                    float v[16];
-                    tmem_ld16_sum(ta + 16 * c, tb + 16 * c, two_acc, v);
+                for (int c = 0; c < nch; ++c) {
                     float fk[16];
 #pragma unroll
-                    for (int h2 = 0; h2 < 2; ++h2) {  // nc is a multiple of 8: each 8-column half is in or out
-                        if (valid && 16 * c + 8 * h2 < a.nc) {
-                            ld8(a.f32 + local * a.n1 + 16 * c + 8 * h2, fk + 8 * h2);
+                    for (int k = 0; k < 16; ++k) fk[k] = fpre[k];
+                    // prefetch the next chunk's f while this one is processed
+                    // (nc is a multiple of 8: each 8-column half is either in or out)
+#pragma unroll
+                    for (int h2 = 0; h2 < 2; ++h2) {
+                        if (valid && 16 * (c + 1) + 8 * h2 < a.nc) {
+                            ld8(a.f32 + local * a.n1 + 16 * (c + 1) + 8 * h2, fpre + 8 * h2);
                         } else {
 #pragma unroll
-                            for (int k = 0; k < 8; ++k) fk[8 * h2 + k] = 0.f;
+                            for (int k = 0; k < 8; ++k) fpre[8 * h2 + k] = 0.f;
                         }
                     }
+                    float v[16], vb[16];
+                    ptx::tmem_ld16x2(ta + 16 * c, tb + 16 * c, v, vb);
 #pragma unroll
                     for (int k = 0; k < 16; ++k) {
-                        const float y = v[k] * unscale;
+                        const float y = (two_acc ? v[k] + vb[k] : v[k]) * unscale;
                         e_row = fmaf(fk[k] * y, y, e_row);
                         v[k] = fk[k] * y * s_mid;
                     }
@@ -467,9 +624,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const PassArgs a) 
                         for (int h2 = 0; h2 < 2; ++h2) {
                             uint4 hi, lo;
                             split8(v + 8 * h2, hi, lo);
-                            const int off = (m >> 3) * (np * 16) + (2 * c + h2) * 128 + (m & 7) * 16;
-                            *reinterpret_cast<uint4 *>(mid + off) = hi;
-                            *reinterpret_cast<uint4 *>(mid + 128 * np * 2 + off) = lo;
+                            const int off = (m >> 3) * ((np >> 3) * kCoreStride) + (2 * c + h2) * kCoreStride + (m & 7) * 16;
+                            *reinterpret_cast<uint4 *>(midh + off) = hi;
+                            *reinterpret_cast<uint4 *>(midh + half_bytes + off) = lo;
                         }
                     }
                 }
@@ -478,51 +635,57 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const PassArgs a) 
                     ptx::fence_proxy_async_smem();
                     ptx::tc_fence_before();
                     ptx::mbar_arrive(&bars.mid_full);
-                    if (!wait_bar_warp(&bars.tfull2[b], (uint32_t)((it >> 1) & 1), a, &s_abort)) break;
-                    ptx::tc_fence_after();
-                    const float unscale2 = ldexpf(1.f, -(e_mid + kVScaleExp));
-                    for (int c = half; c < nch; c += 2) {
-                        float v[16];
-                        tmem_ld16_sum(ta + 16 * c, tb + 16 * c, two_acc, v);
-#pragma unroll
-                        for (int h2 = 0; h2 < 2; ++h2) {  // store each 8-column half that lies inside the row
-                            if (!valid || 16 * c + 8 * h2 >= a.nc) continue;
-                            float *w = v + 8 * h2;
-#pragma unroll
-                            for (int k = 0; k < 8; ++k) {
-                                w[k] *= unscale2;
-                                my_max = fmaxf(my_max, fabsf(w[k]));
-                            }
-                            float4 *dst = reinterpret_cast<float4 *>(a.out + item * a.N + local * a.n1 + 16 * c + 8 * h2);
-                            dst[0] = make_float4(w[0], w[1], w[2], w[3]);
-                            dst[1] = make_float4(w[4], w[5], w[6], w[7]);
-                        }
+                    KX_CLK_ADD(10, tw);
+                    tw = KX_CLK_NOW();
+                    // inverse half of the previous tile (its MMA ran while this tile's forward half was processed)
+                    if (it >= 1) {
+                        if (!x1_inverse_half(a, bars, tmem, q, m, it - 1, np, two_acc, prev_valid, prev_item,
+                                             prev_local, prev_unscale2, &s_abort))
+                            break;
                     }
-                    track_max(a.out_max, item, my_max, valid);
+                    KX_CLK_ADD(11, tw);
+                    prev_valid = valid;
+                    prev_item = item;
+                    prev_local = local;
+                    prev_unscale2 = ldexpf(1.f, -(e_mid + kVScaleExp));
+                    continue;  // tile it's TMEM slot is released by its inverse half
                 }
             } else {
-                // transposed write: one column per store, consecutive lanes = consecutive rows
-                for (int c = half; c < nch; c += 2) {
-                    float v[16];
-                    tmem_ld16_sum(ta + 16 * c, tb + 16 * c, two_acc, v);
+                // transposed write: one column per store, consecutive lanes = consecutive rows;
+                // row base and column stride are computed once per tile
+                // output (row r, column c) at base(r) + c * ostride: [k3 or x3][position] or [k3][k2 or x2][x1]
+                const long long ostride = (PASS == P_X3F || PASS == P_X3I) ? n12 : (long long)a.n1;
+                long long obase = 0;
+                if (valid) {
+                    if (PASS == P_X3F || PASS == P_X3I) {
+                        obase = item * a.N + local;
+                    } else {
+                        const long long k3 = (unsigned)local / (unsigned)a.n1;
+                        const long long x1 = (unsigned)local % (unsigned)a.n1;
+                        obase = item * a.N + k3 * n12 + x1;
+                    }
+                }
+                for (int cb = 0; cb < np; cb += 32) {
+                    float v[32], vb[32];
+                    const long long tl = KX_CLK_NOW();
+                    if (cb + 32 <= np) {
+                        ptx::tmem_ld32x2(ta + cb, tb + cb, v, vb);
+                    } else {
+                        ptx::tmem_ld16x2(ta + cb, tb + cb, v, vb);
+                    }
+                    KX_CLK_ADD(11, tl);
                     if (!valid) continue;
+                    const int w = min(32, a.nc - cb);
 #pragma unroll
-                    for (int k = 0; k < 16; ++k) {
-                        const int col = 16 * c + k;
-                        if (col >= a.nc) break;
-                        const float y = v[k] * unscale;
-                        long long dst;
-                        if (PASS == P_X3F || PASS == P_X3I) {
-                            dst = (long long)col * n12 + local;  // [k3 or x3][position]
-                        } else {
-                            const long long k3 = local / a.n1, x1 = local % a.n1;
-                            dst = k3 * n12 + (long long)col * a.n1 + x1;  // [k3][k2 or x2][x1]
-                        }
+                    for (int k = 0; k < 32; ++k) {
+                        if (k >= w) break;
+                        const float y = (two_acc ? v[k] + vb[k] : v[k]) * unscale;
+                        const long long dst = obase + (long long)(cb + k) * ostride;
                         if (PASS == P_X3I && a.rhs_mode) {
-                            a.xout[item * a.N + dst] = (double)y;
+                            a.xout[dst] = (double)y;
                         } else {
                             my_max = fmaxf(my_max, fabsf(y));
-                            a.out[item * a.N + dst] = y;
+                            a.out[dst] = y;
                         }
                     }
                 }
@@ -530,7 +693,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const PassArgs a) 
             }
             ptx::tc_fence_before();
             ptx::mbar_arrive(&bars.tempty[b]);
+            KX_CLK_ADD(10, tw);
         }
+        KX_CLK_ADD(8, te0);
+        if (PASS == P_X1 && with_inv && n_my >= 1 && !s_abort)
+            aborted = !x1_inverse_half(a, bars, tmem, q, m, n_my - 1, np, two_acc, prev_valid, prev_item, prev_local,
+                                       prev_unscale2, &s_abort);
+        (void)aborted;
         if (a.e_partial != nullptr) {
             double e = e_acc;
             for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
@@ -543,6 +712,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const PassArgs a) 
             }
         }
     }
+#ifdef KX_ROLE_CLOCKS
+    if (a.clk != nullptr) {
+        long long *o = a.clk + (long long)blockIdx.x * kClk;
+        if (warp == kMmaWarp && lane == 0) { o[4] = clk_acc[4]; o[5] = clk_acc[5]; o[6] = clk_acc[6]; o[7] = clk_acc[7]; }
+        if (tid == kEpiThreads) { o[0] = clk_acc[0]; o[1] = clk_acc[1]; o[2] = clk_acc[2]; o[3] = clk_acc[3]; }
+        if (tid == 0) { o[8] = clk_acc[8]; o[9] = clk_acc[9]; o[10] = clk_acc[10]; o[11] = clk_acc[11]; }
+    }
+#endif
     ptx::tc_fence_before();
     __syncthreads();
     if (warp == kMmaWarp) {
@@ -663,16 +840,17 @@ __global__ void selftest_wait_kernel(long long max_cycles, int *status) {
     if (threadIdx.x == 0 && !ptx::mbar_wait_bounded(&bar, 0, max_cycles)) atomicExch(status, KX_ERR_TIMEOUT);
 }
 
-size_t stage_bytes_of(int np) { return (size_t)2 * 128 * np * 2; }
+size_t stage_bytes_of(int np) { return 2 * a_half_bytes(np); }
+constexpr size_t kStagingBytes = 0;
 
 int pass_stages(int np, bool with_mid) {
     const size_t v = (size_t)4 * np * np;
-    const size_t avail = kSmemBudget - v - (with_mid ? stage_bytes_of(np) : 0);
+    const size_t avail = kSmemBudget - v - kStagingBytes - (with_mid ? stage_bytes_of(np) : 0);
     return (int)std::max<size_t>(1, std::min<size_t>(kMaxStages, avail / stage_bytes_of(np)));
 }
 
 size_t pass_smem(int np, int stages, bool with_mid) {
-    return (size_t)4 * np * np + (size_t)(stages + (with_mid ? 1 : 0)) * stage_bytes_of(np) + 1024;
+    return (size_t)4 * np * np + (size_t)(stages + (with_mid ? 1 : 0)) * stage_bytes_of(np) + kStagingBytes + 1024;
 }
 
 template <int PASS>
@@ -686,9 +864,12 @@ int launch_pass(const kx_plan *p, PassArgs a, int axis, cudaStream_t s, int *gri
     a.N = (long long)p->N;
     a.status = p->d_status;
     a.timeout_cycles = 4000000000LL;  // ~2 s at the SM clock
-    const bool with_mid = (PASS == P_X1) && !a.energy_only;
-    a.stages = pass_stages(a.np, with_mid);
-    const size_t smem = pass_smem(a.np, a.stages, with_mid);
+#ifdef KX_ROLE_CLOCKS
+    if (!g_clkbuf) cudaMallocManaged(&g_clkbuf, sizeof(long long) * kClk * 4096 * 5);
+    a.clk = g_clkbuf + (long long)PASS * kClk * 4096;
+#endif
+    a.stages = pass_stages(a.np, false);  // X1's mid operand reuses its tile's A stage
+    const size_t smem = pass_smem(a.np, a.stages, false);
     KX_CUDA_TRY(cudaFuncSetAttribute(tc_pass_kernel<PASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const long long n_tiles = (a.total_rows + 127) / 128;
     const int grid = (int)std::max(1LL, std::min<long long>(n_tiles, (long long)p->num_sms));
@@ -790,6 +971,10 @@ int run_passes(kx_plan *p, PassArgs a, long R, float *T0, float *T1, float *mx, 
 long tc_default_chunk(const kx_plan *p, int n_orb) {
     (void)n_orb;
     if (p->tune.chunk_pairs > 0) return p->tune.chunk_pairs;
+    if (const char *e = std::getenv("KX_CHUNK_PAIRS")) {  // tuning override (pairs per chunk)
+        const long v = std::atol(e);
+        if (v > 0) return v;
+    }
     const size_t budget = (size_t)4 << 30;  // both chunk buffers together
     long c = (long)std::max<size_t>(1, budget / (2 * p->N * sizeof(float)));
     return std::max(1L, std::min<long>(c, 2048));
@@ -941,6 +1126,13 @@ int noalloc_scratch(int dev, void **out) {
 }  // namespace
 
 size_t noalloc_max_elems() { return kNoAllocMaxElems; }
+
+#ifdef KX_ROLE_CLOCKS
+}  // namespace kx
+// managed buffer written by the last launch of each pass (experiment builds only)
+extern "C" long long *kx_debug_role_clocks() { return kx::g_clkbuf; }
+namespace kx {
+#endif
 
 int tc_apply_fL_noalloc(kx_plan *p, int n_rhs, const double *b, double *x, cudaStream_t s) {
     if (p->precision != KX_F16X3)

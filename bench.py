@@ -194,6 +194,7 @@ def pass_model(n):
         "X2F": (2.0 * N * n2, 8.0 * N),
         "X1": (4.0 * N * n1, 8.0 * N),                  # forward + inverse mode 1 in one pass
         "X2I": (2.0 * N * n2, 8.0 * N),
+        "slab": (4.0 * N * (n1 + n2), 8.0 * N),         # X2F + X1 + X2I fused per k3 slice
         "X3I": (2.0 * N * n3, 8.0 * N),                 # read coefficients, write phi
         "acc": (4.0 * N, 12.0 * N),                      # read phi; orbital reads and accumulator RMW per group
     }

@@ -541,16 +541,16 @@ int kx_autotune(kx_plan *plan, int n_orb, int budget_ms) {
     TuneParams best = orig;
     float best_ms = 1e30f;
     const long P = (long)n_orb * (n_orb + 1) / 2;
-    const int ctas[] = {1, 2};
+    const int fuse[] = {1, 0};
     const long chunks[] = {256, 512, 1024, 2048};
     auto t_start = std::chrono::steady_clock::now();
     int rc = KX_OK;
-    for (int c : ctas) {
+    for (int fz : fuse) {
         for (long ch : chunks) {
             if (ch > 2 * P && ch != chunks[0]) continue;
             double elapsed = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
             if (elapsed > budget_ms && best_ms < 1e30f) break;
-            plan->tune.ctas_per_sm = c;
+            plan->tune.fuse_slab = fz;
             plan->tune.chunk_pairs = ch;
             rc = tc_vx(plan, n_orb, psi, nullptr, vx, ex, false, s);  // warm-up (also sizes the workspace)
             if (rc) break;

@@ -728,6 +728,470 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const PassArgs a) 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Slab kernel: the three middle mode products of Eq. 19 for one k3 slice (an
+// n1 x n2 plane of one item) without leaving the SM.  Per unit (item, k3):
+//   M1  A1[x1][x2] (MN-major, from global) x V2      -> D1[x1][k2]
+//   B   D1 -> A2[k2][x1] (MN-major, written by the thread owning row x1)
+//   M2  A2 x V1                                      -> D2[k2][k1]
+//   C   energy sum f Y^2; mid = f Y -> A3[k2][k1] (K-major, own row)
+//   M3  A3 x V1^T                                    -> D3[k2][x1]
+//   D   D3 -> A4[x1][k2] (MN-major, written by the thread owning row k2)
+//   M4  A4 x V2^T                                    -> D4[x1][x2]
+//   E   D4 -> global slice [x2][x1] (coalesced), per-item maximum
+// Two units are interleaved (TMEM slot and A buffer = unit parity) so MMAs of
+// one overlap the epilogue stages of the other.  Split scales are powers of two
+// from bounds: each orthogonal mode product grows max|.| by at most sqrt(n),
+// the scaling by at most fmax.
+// ---------------------------------------------------------------------------
+struct SlabArgs {
+    int n1, n2, n3, np1, np2;
+    long long N;
+    long long total_units;  // items * n3
+    const float *in;
+    float *out;
+    const __half *V1s, *V2s;
+    const float *in_max;    // per item
+    float *out_max;         // per item (nullable)
+    const float *f32;
+    float fmax, sq1, sq2;   // fmax, sqrt(n1), sqrt(n2) (each with a small margin)
+    double *e_partial;
+    const int2 *pairs;
+    const double *occ;
+    int rhs_mode;
+    int stage_out;          // stage the output slice in shared memory and store it with one bulk copy
+    int *status;
+    long long timeout_cycles;
+    long long *clk;         // role counters (only with KX_ROLE_CLOCKS)
+};
+
+constexpr int kSlabEpiWarps = 8;
+constexpr int kSlabEpiThreads = 32 * kSlabEpiWarps;
+constexpr int kSlabProdThreads = 96;
+constexpr int kSlabU = 8;  // producer loads in flight per thread
+constexpr int kSlabMmaWarp = kSlabEpiWarps + kSlabProdThreads / 32;
+constexpr int kSlabThreads = 32 * (kSlabMmaWarp + 1);
+
+struct SlabBars {
+    uint64_t full[2], empty[2], tfull[2], ready[2], drain;
+};
+
+__device__ __forceinline__ bool slab_wait(uint64_t *bar, uint32_t parity, const SlabArgs &a, volatile int *abort) {
+    const long long t0 = clock64();
+    while (!ptx::mbar_try_wait(bar, parity)) {
+        if (*abort) return false;
+        if (clock64() - t0 > a.timeout_cycles) {
+            *abort = 1;
+            atomicExch(a.status, KX_ERR_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void store_split8(uint8_t *hi_base, uint8_t *lo_base, int off, const float *w) {
+    uint4 h, l;
+    split8(w, h, l);
+    *reinterpret_cast<uint4 *>(hi_base + off) = h;
+    *reinterpret_cast<uint4 *>(lo_base + off) = l;
+}
+
+__global__ void __launch_bounds__(kSlabThreads, 1) tc_slab_kernel(const SlabArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int np1 = a.np1, np2 = a.np2, npm = max(np1, np2);
+    const size_t half_bytes = a_half_bytes(npm);
+    uint8_t *V1hi = smem;
+    uint8_t *V1lo = V1hi + np1 * np1 * 2;
+    uint8_t *V2hi = V1lo + np1 * np1 * 2;
+    uint8_t *V2lo = V2hi + np2 * np2 * 2;
+    uint8_t *buf0 = V2lo + np2 * np2 * 2;  // two A buffers (hi | lo), one per unit in flight
+    float *ostage = reinterpret_cast<float *>(buf0 + 4 * half_bytes);  // output slice [x2][x1] (stage_out)
+    __shared__ SlabBars bars;
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int s_abort;
+    __shared__ double s_red[kSlabEpiWarps];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+#ifdef KX_ROLE_CLOCKS
+    long long clk_acc[kClk] = {0};
+    const long long clk_t0 = clock64();
+#endif
+    if (warp == kSlabMmaWarp) {
+        ptx::tmem_alloc(&tmem_slot, 512);
+        ptx::tmem_relinquish();
+    }
+    if (tid == 0) {
+        for (int b = 0; b < 2; ++b) {
+            ptx::mbar_init(&bars.full[b], kSlabProdThreads);
+            ptx::mbar_init(&bars.empty[b], 1);
+            ptx::mbar_init(&bars.tfull[b], 1);
+            ptx::mbar_init(&bars.ready[b], kSlabEpiThreads);
+        }
+        ptx::mbar_init(&bars.drain, 1);
+        ptx::fence_mbar_init();
+        s_abort = 0;
+    }
+    {
+        const uint4 *s1 = reinterpret_cast<const uint4 *>(a.V1s);
+        const uint4 *s2 = reinterpret_cast<const uint4 *>(a.V2s);
+        uint4 *d1 = reinterpret_cast<uint4 *>(V1hi);
+        uint4 *d2 = reinterpret_cast<uint4 *>(V2hi);
+        const int c1 = (4 * np1 * np1) / 16, c2 = (4 * np2 * np2) / 16;
+        for (int i = tid; i < c1; i += blockDim.x) d1[i] = __ldg(s1 + i);
+        for (int i = tid; i < c2; i += blockDim.x) d2[i] = __ldg(s2 + i);
+    }
+    ptx::fence_proxy_async_smem();
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    const int n_my = (int)((a.total_units - blockIdx.x + gridDim.x - 1) / gridDim.x);
+    const long long n12 = (long long)a.n1 * a.n2;
+
+    if (warp == kSlabMmaWarp) {
+        // ---------------------------------------------------------------- MMA issue
+        if (lane == 0) {
+            const uint32_t sV1h = ptx::smem_u32(V1hi), sV1l = ptx::smem_u32(V1lo);
+            const uint32_t sV2h = ptx::smem_u32(V2hi), sV2l = ptx::smem_u32(V2lo);
+            bool ok = true;
+            for (int jj = 0; jj < n_my && ok; jj += 2) {
+                for (int d = 0; d < 2 && ok; ++d) {  // M1 of both units
+                    const int j = jj + d;
+                    if (j >= n_my) break;
+                    const int sl = j & 1;
+                    long long tw = KX_CLK_NOW();
+                    ok = slab_wait(&bars.full[sl], (uint32_t)((j >> 1) & 1), a, &s_abort);
+                    KX_CLK_ADD(5, tw);
+                    tw = KX_CLK_NOW();
+                    if (ok && j >= 2) ok = slab_wait(&bars.ready[sl], 1u, a, &s_abort);  // stage E of unit j-2
+                    KX_CLK_ADD(6, tw);
+                    if (!ok) break;
+                    ptx::tc_fence_after();
+                    const uint32_t sA = ptx::smem_u32(buf0 + sl * 2 * half_bytes);
+                    const uint32_t da = tmem + (uint32_t)(sl * 2 * npm);
+                    issue_split_mma(da, da + (uint32_t)npm, sA, sA + (uint32_t)half_bytes, false, sV2h, sV2l, false,
+                                    np2);
+                    ptx::mma_commit(&bars.tfull[sl]);
+                }
+                for (int st = 1; st <= 3 && ok; ++st) {
+                    for (int d = 0; d < 2 && ok; ++d) {
+                        const int j = jj + d;
+                        if (j >= n_my) break;
+                        const int sl = j & 1;
+                        long long tw = KX_CLK_NOW();
+                        ok = slab_wait(&bars.ready[sl], (uint32_t)((st - 1) & 1), a, &s_abort);
+                        KX_CLK_ADD(6, tw);
+                        if (!ok) break;
+                        ptx::tc_fence_after();
+                        const uint32_t sA = ptx::smem_u32(buf0 + sl * 2 * half_bytes);
+                        const uint32_t da = tmem + (uint32_t)(sl * 2 * npm);
+                        if (st == 1)  // M2: A2 (MN-major) x V1 forward
+                            issue_split_mma(da, da + (uint32_t)npm, sA, sA + (uint32_t)half_bytes, false, sV1h, sV1l,
+                                            false, np1);
+                        else if (st == 2)  // M3: A3 (K-major) x V1^T
+                            issue_split_mma(da, da + (uint32_t)npm, sA, sA + (uint32_t)half_bytes, true, sV1h, sV1l,
+                                            true, np1);
+                        else  // M4: A4 (MN-major) x V2^T
+                            issue_split_mma(da, da + (uint32_t)npm, sA, sA + (uint32_t)half_bytes, false, sV2h, sV2l,
+                                            true, np2);
+                        ptx::mma_commit(&bars.tfull[sl]);
+                        if (st == 3) ptx::mma_commit(&bars.empty[sl]);
+                    }
+                }
+            }
+            if (!ok) {
+                ptx::mma_commit(&bars.drain);
+                ptx::mbar_wait_bounded(&bars.drain, 0, a.timeout_cycles);
+            }
+        }
+        __syncwarp();
+    } else if (warp >= kSlabEpiWarps) {
+        // ---------------------------------------------------------------- producers: A1 from global
+        const int ptid = tid - kSlabEpiThreads;
+        const int ntask = 16 * np2;  // 16 row groups (x1) x np2 columns (x2)
+        const int nlines = (int)((n12 * 4) >> 7);  // 128-byte lines of a slice (n1 % 8 == 0)
+        for (int it = 0; it < n_my; ++it) {
+            const int sl = it & 1;
+            if (it + 2 < n_my) {
+                // pull the slice of unit it+2 into L2 while this unit waits for its buffer
+                const long long u2 = blockIdx.x + (long long)(it + 2) * gridDim.x;
+                const long long item2 = (unsigned)u2 / (unsigned)a.n3, k32 = (unsigned)u2 % (unsigned)a.n3;
+                const char *src = reinterpret_cast<const char *>(a.in + item2 * a.N + k32 * n12);
+                for (int l = ptid; l < nlines; l += kSlabProdThreads) ptx::prefetch_l2(src + ((long long)l << 7));
+            }
+            long long tw = KX_CLK_NOW();
+            if (it >= 2 && !slab_wait(&bars.empty[sl], (uint32_t)(((it >> 1) - 1) & 1), a, &s_abort)) break;
+            KX_CLK_ADD(1, tw);
+            tw = KX_CLK_NOW();
+            if (s_abort) break;
+            const long long u = blockIdx.x + (long long)it * gridDim.x;
+            const long long item = (unsigned)u / (unsigned)a.n3, k3 = (unsigned)u % (unsigned)a.n3;
+            const float *slice = a.in + item * a.N + k3 * n12;
+            const float sc = ldexpf(1.f, scale_exp(a.in_max[item]));
+            uint8_t *Ahi = buf0 + sl * 2 * half_bytes;
+            uint8_t *Alo = Ahi + half_bytes;
+            for (int t0 = ptid; t0 < ntask; t0 += kSlabProdThreads * kSlabU) {
+                float v[kSlabU][8];
+#pragma unroll
+                for (int r = 0; r < kSlabU; ++r) {
+                    const int t = t0 + r * kSlabProdThreads;
+                    const int g = t & 15, k = t >> 4;
+                    if (t < ntask && 8 * g < a.n1 && k < a.n2) {
+                        ld8(slice + (long long)k * a.n1 + 8 * g, v[r]);
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) v[r][c] = 0.f;
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < kSlabU; ++r) {
+                    const int t = t0 + r * kSlabProdThreads;
+                    if (t >= ntask) continue;
+                    const int g = t & 15, k = t >> 4;
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) v[r][c] *= sc;
+                    store_split8(Ahi, Alo, g * kCoreStride + (k >> 3) * (16 * kCoreStride) + (k & 7) * 16, v[r]);
+                }
+            }
+            ptx::fence_proxy_async_smem();
+            ptx::mbar_arrive(&bars.full[sl]);
+            KX_CLK_ADD(2, tw);
+        }
+    } else {
+        // ---------------------------------------------------------------- epilogue stages B, C, D, E
+        // Warp w reads TMEM lanes 32*(w%4).. (its D rows) and the 16-column
+        // chunks c = 16*(w/4) + 32*i, two chunks per load round.  tcgen05.ld is
+        // warp-collective, so every lane of a warp loads and only the stores are
+        // predicated per row.  After a failed wait the warps keep walking the
+        // same stage sequence without work, so that the barriers of stage E and
+        // of the energy sum see all eight warps.
+        const int q = warp & 3, h = warp >> 2;
+        const int m = 32 * q + lane;  // TMEM lane == D row
+        const bool two1 = (np1 >> 4) > 1, two2 = (np2 >> 4) > 1;
+        const int nkc1 = np1 >> 3;
+        const bool sto = a.stage_out != 0;
+        double e_acc = 0.0;
+        bool ok = true;
+        for (int jj = 0; jj < n_my; jj += 2) {
+            // per-unit constants of the two units in flight
+            long long itm[2], k3u[2];
+            int ex1[2], ex2[2], ex3[2], ex4[2];
+            double wgt[2];
+#pragma unroll
+            for (int d = 0; d < 2; ++d) {
+                const long long u = blockIdx.x + (long long)min(jj + d, n_my - 1) * gridDim.x;
+                itm[d] = (unsigned)u / (unsigned)a.n3;
+                k3u[d] = (unsigned)u % (unsigned)a.n3;
+                const float b1 = __ldg(a.in_max + itm[d]);
+                const float b2 = b1 * a.sq2, b3 = a.fmax * a.sq1 * b2, b4 = a.sq1 * b3;
+                ex1[d] = scale_exp(b1);
+                ex2[d] = scale_exp(b2);
+                ex3[d] = scale_exp(b3);
+                ex4[d] = scale_exp(b4);
+                double w = 0.0;
+                if (a.e_partial != nullptr && !a.rhs_mode) {
+                    const int2 ij = a.pairs[itm[d]];
+                    w = (ij.x == ij.y) ? 1.0 : 2.0;
+                    if (a.occ) w *= a.occ[ij.x] * a.occ[ij.y];
+                }
+                wgt[d] = w;
+            }
+            for (int st = 0; st < 4; ++st) {
+                for (int d = 0; d < 2; ++d) {
+                    const int j = jj + d;
+                    if (j >= n_my) break;
+                    const int sl = j & 1;
+                    const long long item = d ? itm[1] : itm[0], k3 = d ? k3u[1] : k3u[0];
+                    const int e1 = d ? ex1[1] : ex1[0], e2 = d ? ex2[1] : ex2[0];
+                    const int e3 = d ? ex3[1] : ex3[0], e4 = d ? ex4[1] : ex4[0];
+                    uint8_t *Ahi = buf0 + sl * 2 * half_bytes;
+                    uint8_t *Alo = Ahi + half_bytes;
+                    // stage C: the row's first 16 f(Lambda) values are fetched before the wait,
+                    // each further chunk's while the previous one is processed
+                    float fpre[16];
+                    const bool rowC = (st == 1) && m < a.n2;
+                    const float *frow = a.f32 + (k3 * a.n2 + m) * (long long)a.n1;
+                    if (st == 1 && ok) {
+#pragma unroll
+                        for (int hh = 0; hh < 2; ++hh) {
+                            const int c0 = 16 * h + 8 * hh;
+                            if (rowC && c0 < a.n1) {
+                                ld8(frow + c0, fpre + 8 * hh);
+                            } else {
+#pragma unroll
+                                for (int k = 0; k < 8; ++k) fpre[8 * hh + k] = 0.f;
+                            }
+                        }
+                    }
+                    long long tw = KX_CLK_NOW();
+                    if (ok) ok = __all_sync(0xffffffffu, slab_wait(&bars.tfull[sl], (uint32_t)(st & 1), a, &s_abort));
+                    KX_CLK_ADD(9, tw);
+                    tw = KX_CLK_NOW();
+                    ptx::tc_fence_after();
+                    const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(sl * 2 * npm);
+                    const uint32_t tb = ta + (uint32_t)npm;
+                    if (st == 0 || st == 2) {
+                        // B: D1[x1][k2] -> A2[k2][x1];  D: D3[k2][x1] -> A4[x1][k2]  (both MN-major).
+                        // The thread of D row r writes K column r of the next operand: 8 consecutive
+                        // M values (D columns) per 16-byte store.  Rows r >= n (padding) give zeros.
+                        const int nrow = (st == 0) ? a.n1 : a.n2, nprow = (st == 0) ? np1 : np2;
+                        const int ncol = (st == 0) ? np2 : np1;
+                        const bool two = (st == 0) ? two2 : two1;
+                        const float us = (st == 0) ? ldexpf(1.f, e2 - e1 - kVScaleExp) : ldexpf(1.f, e4 - e3 - kVScaleExp);
+                        if (ok && 32 * q < nprow) {
+                            const int off_r = (m >> 3) * (16 * kCoreStride) + (m & 7) * 16;
+#pragma unroll
+                            for (int i = 0; i < 4; i += 2) {
+                                const int c0 = 16 * h + 32 * i;
+                                if (c0 >= ncol) break;
+                                const bool has2 = c0 + 32 < ncol;
+                                float v[2][16], vb[2][16];
+                                if (has2)
+                                    ptx::tmem_ld16x4(ta + c0, tb + c0, ta + c0 + 32, tb + c0 + 32, v[0], vb[0], v[1], vb[1]);
+                                else
+                                    ptx::tmem_ld16x2(ta + c0, tb + c0, v[0], vb[0]);
+                                if (m < nprow) {
+#pragma unroll
+                                    for (int g = 0; g < 2; ++g) {
+                                        if (g == 1 && !has2) break;
+                                        const int c = c0 + 32 * g;
+#pragma unroll
+                                        for (int hh = 0; hh < 2; ++hh) {
+                                            float w[8];
+#pragma unroll
+                                            for (int k = 0; k < 8; ++k)
+                                                w[k] = (m < nrow) ? (two ? v[g][8 * hh + k] + vb[g][8 * hh + k] : v[g][8 * hh + k]) * us
+                                                                  : 0.f;
+                                            store_split8(Ahi, Alo, ((c >> 3) + hh) * kCoreStride + off_r, w);
+                                        }
+                                    }
+                                }
+                            }
+                        }
+                        ptx::fence_proxy_async_smem();
+                    } else if (st == 1) {
+                        // C: D2[k2][k1] = Y: energy sum f Y^2, mid = f Y -> A3[k2][k1] (K-major, own row)
+                        const float u2 = ldexpf(1.f, -(e2 + kVScaleExp));
+                        const float s3 = ldexpf(1.f, e3);
+                        const int off_r = (m >> 3) * (nkc1 * kCoreStride) + (m & 7) * 16;
+                        float e_row = 0.f;
+                        if (ok) {
+                            for (int c = 16 * h; c < np1; c += 32) {
+                                float fk[16];
+#pragma unroll
+                                for (int k = 0; k < 16; ++k) fk[k] = fpre[k];
+#pragma unroll
+                                for (int hh = 0; hh < 2; ++hh) {
+                                    const int c1 = c + 32 + 8 * hh;
+                                    if (rowC && c1 < a.n1) {
+                                        ld8(frow + c1, fpre + 8 * hh);
+                                    } else {
+#pragma unroll
+                                        for (int k = 0; k < 8; ++k) fpre[8 * hh + k] = 0.f;
+                                    }
+                                }
+                                float v[16], vb[16];
+                                ptx::tmem_ld16x2(ta + c, tb + c, v, vb);
+#pragma unroll
+                                for (int k = 0; k < 16; ++k) {
+                                    const float y = rowC ? (two1 ? v[k] + vb[k] : v[k]) * u2 : 0.f;
+                                    e_row = fmaf(fk[k] * y, y, e_row);
+                                    v[k] = fk[k] * y * s3;
+                                }
+#pragma unroll
+                                for (int hh = 0; hh < 2; ++hh)
+                                    store_split8(Ahi, Alo, off_r + ((c >> 3) + hh) * kCoreStride, v + 8 * hh);
+                            }
+                        }
+                        if (rowC) e_acc += (d ? wgt[1] : wgt[0]) * (double)e_row;
+                        ptx::fence_proxy_async_smem();
+                    } else {
+                        // E: D4[x1][x2] -> slice [x2][x1] of the output, coalesced over x1; either
+                        // through the shared staging buffer and one bulk copy, or stored directly
+                        const float u4 = ldexpf(1.f, -(e4 + kVScaleExp));
+                        const bool valid = m < a.n1;
+                        float *gslice = a.out + item * a.N + k3 * n12;
+                        float *dst = sto ? ostage : gslice;
+                        float my_max = 0.f;
+                        if (sto) {
+                            // the previous bulk copy must have finished reading the staging buffer
+                            if (tid == 0) ptx::bulk_wait_read_all();
+                            ptx::named_bar(1, kSlabEpiThreads);
+                        }
+                        if (ok && 32 * q < a.n1) {
+#pragma unroll
+                            for (int i = 0; i < 4; i += 2) {
+                                const int c0 = 16 * h + 32 * i;
+                                if (c0 >= np2) break;
+                                const bool has2 = c0 + 32 < np2;
+                                float v[2][16], vb[2][16];
+                                if (has2)
+                                    ptx::tmem_ld16x4(ta + c0, tb + c0, ta + c0 + 32, tb + c0 + 32, v[0], vb[0], v[1], vb[1]);
+                                else
+                                    ptx::tmem_ld16x2(ta + c0, tb + c0, v[0], vb[0]);
+                                if (!valid) continue;
+#pragma unroll
+                                for (int g = 0; g < 2; ++g) {
+                                    if (g == 1 && !has2) break;
+                                    const int c = c0 + 32 * g;
+#pragma unroll
+                                    for (int k = 0; k < 16; ++k) {
+                                        if (c + k < a.n2) {
+                                            const float y = (two2 ? v[g][k] + vb[g][k] : v[g][k]) * u4;
+                                            my_max = fmaxf(my_max, fabsf(y));
+                                            dst[(long long)(c + k) * a.n1 + m] = y;
+                                        }
+                                    }
+                                }
+                            }
+                        }
+                        if (sto) {
+                            ptx::fence_proxy_async_smem();
+                            ptx::named_bar(1, kSlabEpiThreads);
+                            if (tid == 0 && ok) {
+                                ptx::bulk_store(gslice, ostage, (uint32_t)(n12 * 4));
+                                ptx::bulk_commit();
+                            }
+                        }
+                        track_max(a.out_max, item, my_max, valid);
+                    }
+                    ptx::tc_fence_before();
+                    if (ok) ptx::mbar_arrive(&bars.ready[sl]);
+                    KX_CLK_ADD(st == 0 ? 10 : st == 1 ? 11 : st == 2 ? 3 : 7, tw);
+                }
+            }
+        }
+        if (sto && tid == 0) ptx::bulk_wait_all();
+        if (a.e_partial != nullptr) {
+            double e = e_acc;
+            for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+            if (lane == 0) s_red[warp] = e;
+            ptx::named_bar(1, kSlabEpiThreads);
+            if (tid == 0) {
+                double sum = 0.0;
+                for (int w = 0; w < kSlabEpiWarps; ++w) sum += s_red[w];
+                a.e_partial[blockIdx.x] = sum;
+            }
+        }
+    }
+#ifdef KX_ROLE_CLOCKS
+    if (a.clk != nullptr) {
+        long long *o = a.clk + (long long)blockIdx.x * kClk;
+        const long long tot = clock64() - clk_t0;
+        if (warp == kSlabMmaWarp && lane == 0) { o[4] = tot; o[5] = clk_acc[5]; o[6] = clk_acc[6]; }
+        if (tid == kSlabEpiThreads) { o[0] = tot; o[1] = clk_acc[1]; o[2] = clk_acc[2]; }
+        if (tid == 0) { o[8] = tot; o[9] = clk_acc[9]; o[10] = clk_acc[10]; o[11] = clk_acc[11]; o[3] = clk_acc[3]; o[7] = clk_acc[7]; }
+    }
+#endif
+    ptx::tc_fence_before();
+    __syncthreads();
+    if (warp == kSlabMmaWarp) {
+        ptx::tc_fence_after();
+        ptx::tmem_dealloc(tmem, 512);
+    }
+}
+
 // Accumulation of one chunk, group by group: one thread per four grid points
 // keeps psi and the partial sums of the group's (<= kGroupSlots) orbitals in
 // shared memory and visits the group's items in order, adding
@@ -865,7 +1329,7 @@ int launch_pass(const kx_plan *p, PassArgs a, int axis, cudaStream_t s, int *gri
     a.status = p->d_status;
     a.timeout_cycles = 4000000000LL;  // ~2 s at the SM clock
 #ifdef KX_ROLE_CLOCKS
-    if (!g_clkbuf) cudaMallocManaged(&g_clkbuf, sizeof(long long) * kClk * 4096 * 5);
+    if (!g_clkbuf) cudaMallocManaged(&g_clkbuf, sizeof(long long) * kClk * 4096 * 6);
     a.clk = g_clkbuf + (long long)PASS * kClk * 4096;
 #endif
     a.stages = pass_stages(a.np, false);  // X1's mid operand reuses its tile's A stage
@@ -878,6 +1342,70 @@ int launch_pass(const kx_plan *p, PassArgs a, int axis, cudaStream_t s, int *gri
     tc_pass_kernel<PASS><<<grid, kThreads, smem, s>>>(a);
     KX_LAUNCH_CHECK("tc_pass_kernel launch");
     return prof_end(const_cast<kx_plan *>(p), s);
+}
+
+size_t slab_smem(const kx_plan *p) {
+    const int np1 = p->np[0], np2 = p->np[1], npm = std::max(np1, np2);
+    return (size_t)4 * np1 * np1 + (size_t)4 * np2 * np2 + 4 * a_half_bytes(npm) + 1024;
+}
+
+// The slab kernel holds V1, V2 and two split A buffers in shared memory (plus,
+// where it fits, a staging buffer for the output slice).
+constexpr size_t kSlabSmemMax = 227 * 1024 - 1024;  // opt-in maximum less static shared memory
+bool slab_fits(const kx_plan *p) { return slab_smem(p) <= kSlabSmemMax; }
+
+bool use_slab(const kx_plan *p) {
+    if (const char *e = std::getenv("KX_SLAB")) return std::atoi(e) != 0;  // tuning override
+    return p->tune.fuse_slab != 0;
+}
+
+// Mode 2 forward, mode 1 forward, f(Lambda) scaling (+ energy), mode 1 inverse
+// and mode 2 inverse of R items in one launch; `in` holds the mode-3 forward
+// output, `out` receives the input of the mode-3 inverse (both natural layout).
+int launch_slab(kx_plan *p, long R, const float *in, const float *in_max, float *out, float *out_max,
+                double *e_partial, const int2 *pairs, const double *occ, int rhs_mode, cudaStream_t s,
+                int *grid_out) {
+    SlabArgs a{};
+    a.n1 = p->n[0];
+    a.n2 = p->n[1];
+    a.n3 = p->n[2];
+    a.np1 = p->np[0];
+    a.np2 = p->np[1];
+    a.N = (long long)p->N;
+    a.total_units = (long long)R * a.n3;
+    a.in = in;
+    a.out = out;
+    a.V1s = p->d_Vs[0];
+    a.V2s = p->d_Vs[1];
+    a.in_max = in_max;
+    a.out_max = out_max;
+    a.f32 = p->d_f32;
+    a.fmax = (float)(p->fmax * 1.0001);
+    a.sq1 = (float)(std::sqrt((double)a.n1) * 1.0001);
+    a.sq2 = (float)(std::sqrt((double)a.n2) * 1.0001);
+    a.e_partial = e_partial;
+    a.pairs = pairs;
+    a.occ = occ;
+    a.rhs_mode = rhs_mode;
+    a.status = p->d_status;
+    a.timeout_cycles = 4000000000LL;  // ~2 s at the SM clock
+#ifdef KX_ROLE_CLOCKS
+    if (!g_clkbuf) cudaMallocManaged(&g_clkbuf, sizeof(long long) * kClk * 4096 * 6);
+    a.clk = g_clkbuf + 5LL * kClk * 4096;
+#endif
+    size_t smem = slab_smem(p);
+    const size_t ostage = (size_t)a.n1 * a.n2 * 4;
+    a.stage_out = (smem + ostage <= kSlabSmemMax) ? 1 : 0;
+    if (a.stage_out) smem += ostage;
+    // at least 120 KB so that one CTA (and one 512-column TMEM allocation) sits on each SM
+    smem = std::max<size_t>(smem, 120 * 1024);
+    KX_CUDA_TRY(cudaFuncSetAttribute(tc_slab_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = (int)std::max(1LL, std::min<long long>(a.total_units, (long long)p->num_sms));
+    if (grid_out) *grid_out = grid;
+    if (int rc = prof_begin(p, PK_SLAB, s)) return rc;
+    tc_slab_kernel<<<grid, kSlabThreads, smem, s>>>(a);
+    KX_LAUNCH_CHECK("tc_slab_kernel launch");
+    return prof_end(p, s);
 }
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -919,6 +1447,30 @@ int run_passes(kx_plan *p, PassArgs a, long R, float *T0, float *T1, float *mx, 
     a.out = T0;
     a.out_max = mx1;
     if ((rc = launch_pass<P_X3F>(p, a, 2, s, nullptr))) return rc;
+
+    if (!energy_only && slab_fits(p) && use_slab(p)) {
+        // X2F, X1 and X2I fused: T0 -> T1 without the intermediate round trips
+        int grid = 0;
+        if ((rc = launch_slab(p, R, T0, mx1, T1, mx4, ex ? partial : nullptr, a.pairs, a.occ, a.rhs_mode, s,
+                              &grid)))
+            return rc;
+        if (ex) {
+            if ((rc = prof_begin(p, PK_FINAL, s))) return rc;
+            energy_add_kernel<<<1, 32, 0, s>>>(partial, grid, -0.5 * p->dV, ex);
+            KX_LAUNCH_CHECK("energy_add_kernel launch");
+            if ((rc = prof_end(p, s))) return rc;
+        }
+        a.e_partial = nullptr;
+        a.energy_only = 0;
+        a.rows_pp = (long long)p->n[0] * p->n[1];
+        a.total_rows = R * a.rows_pp;
+        a.in = T1;
+        a.in_max = mx4;
+        a.out = T0;
+        a.out_max = nullptr;
+        a.xout = xout;
+        return launch_pass<P_X3I>(p, a, 2, s, nullptr);
+    }
 
     a.rows_pp = (long long)p->n[2] * p->n[0];
     a.total_rows = R * a.rows_pp;

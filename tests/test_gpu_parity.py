@@ -143,6 +143,32 @@ def test_single_orbital_and_tiny_grid(kx):
         assert abs(ex.item() - ex_ref) < TOL[prec]["ex"] * abs(ex_ref)
 
 
+@pytest.mark.parametrize("case", [0, 1, 2])
+def test_fused_and_unfused_middle_passes(kx, case, monkeypatch):
+    """The fused per-slice kernel (modes 2 and 1, f scaling, energy) and the
+    three separate passes it replaces both match the oracle; the launch counts
+    show which of the two ran."""
+    n, h, bc, kind, n_orb = SMALL[case]
+    sysd = system(n, h, bc, kind, n_orb, 200 + case)
+    psi = workloads.make_orbitals(sysd)
+    op = oracle.Plan(n, h, bc, kind)
+    vx_ref, ex_ref = oracle.vx_apply(op, psi)
+    plan = kx.Plan(n, h, bc, kind, precision=1)
+    for fused in (True, False):
+        monkeypatch.setenv("KX_SLAB", "1" if fused else "0")
+        plan.profile(True)
+        vx, ex = kx.kx_vx_apply(plan, dev(psi.T))
+        torch.cuda.synchronize()
+        prof = plan.profile_read()
+        plan.profile(False)
+        assert plan.status() == kx.KX_OK
+        assert (prof["slab"][1] > 0) == fused
+        assert (prof["X2F"][1] > 0) == (not fused)
+        assert prof["X3F"][1] > 0 and prof["X3I"][1] > 0
+        assert relmax(vx.cpu().numpy().T, vx_ref) < TOL[1]["vx"]
+        assert abs(ex.item() - ex_ref) < TOL[1]["ex"] * abs(ex_ref)
+
+
 def test_max_axis_128(kx):
     n, h, bc = (128, 8, 16), (0.2, 0.5, 0.5), (D, P, D)
     sysd = system(n, h, bc, S, 2, 29)

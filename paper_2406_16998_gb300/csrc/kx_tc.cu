@@ -739,10 +739,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const PassArgs a) 
 //   D   D3 -> A4[x1][k2] (MN-major, written by the thread owning row k2)
 //   M4  A4 x V2^T                                    -> D4[x1][x2]
 //   E   D4 -> global slice [x2][x1] (coalesced), per-item maximum
-// Two units are interleaved (TMEM slot and A buffer = unit parity) so MMAs of
-// one overlap the epilogue stages of the other.  Split scales are powers of two
-// from bounds: each orthogonal mode product grows max|.| by at most sqrt(n),
-// the scaling by at most fmax.
+// Two units are in flight: unit j uses TMEM slot, A buffer and epilogue
+// warpgroup j & 1, so the two groups run their stage chains independently and
+// the single MMA thread serves whichever group is ready.  Split scales are
+// powers of two from bounds: each orthogonal mode product grows max|.| by at
+// most sqrt(n), the scaling by at most fmax.
 // ---------------------------------------------------------------------------
 struct SlabArgs {
     int n1, n2, n3, np1, np2;
@@ -759,16 +760,15 @@ struct SlabArgs {
     const int2 *pairs;
     const double *occ;
     int rhs_mode;
-    int stage_out;          // stage the output slice in shared memory and store it with one bulk copy
     int *status;
     long long timeout_cycles;
     long long *clk;         // role counters (only with KX_ROLE_CLOCKS)
 };
 
-constexpr int kSlabEpiWarps = 8;
-constexpr int kSlabEpiThreads = 32 * kSlabEpiWarps;
+constexpr int kSlabEpiWarps = 8;     // two warpgroups, one per TMEM slot
+constexpr int kSlabGroupThreads = 128;
 constexpr int kSlabProdThreads = 96;
-constexpr int kSlabU = 8;  // producer loads in flight per thread
+constexpr int kSlabU = 8;            // producer loads in flight per thread
 constexpr int kSlabMmaWarp = kSlabEpiWarps + kSlabProdThreads / 32;
 constexpr int kSlabThreads = 32 * (kSlabMmaWarp + 1);
 
@@ -796,6 +796,55 @@ __device__ __forceinline__ void store_split8(uint8_t *hi_base, uint8_t *lo_base,
     *reinterpret_cast<uint4 *>(lo_base + off) = l;
 }
 
+// Per-unit constants of the epilogue: item, slice, the four split exponents and
+// the pair's energy weight.
+struct SlabUnit {
+    long long item, k3;
+    int e1, e2, e3, e4;
+    double w;
+};
+
+__device__ __forceinline__ SlabUnit slab_unit(const SlabArgs &a, long long u) {
+    SlabUnit r;
+    r.item = (unsigned)u / (unsigned)a.n3;
+    r.k3 = (unsigned)u % (unsigned)a.n3;
+    const float b1 = __ldg(a.in_max + r.item);
+    const float b2 = b1 * a.sq2, b3 = a.fmax * a.sq1 * b2, b4 = a.sq1 * b3;
+    r.e1 = scale_exp(b1);
+    r.e2 = scale_exp(b2);
+    r.e3 = scale_exp(b3);
+    r.e4 = scale_exp(b4);
+    r.w = 0.0;
+    if (a.e_partial != nullptr && !a.rhs_mode) {
+        const int2 ij = a.pairs[r.item];
+        r.w = (ij.x == ij.y) ? 1.0 : 2.0;
+        if (a.occ) r.w *= a.occ[ij.x] * a.occ[ij.y];
+    }
+    return r;
+}
+
+// Epilogue stage B or D for one warp: D row m (a TMEM lane) becomes K column m
+// of the next MN-major operand; 8 consecutive D columns (M values) per 16-byte
+// store.  Rows m >= nrow (padding) give zeros; rows m >= nprow are not written.
+__device__ __forceinline__ void slab_transpose_stage(uint32_t ta, uint32_t tb, int m, int nrow, int nprow, int ncol,
+                                                     bool two, float us, uint8_t *Ahi, uint8_t *Alo) {
+    const int off_r = (m >> 3) * (16 * kCoreStride) + (m & 7) * 16;
+    for (int c = 0; c < ncol; c += 16) {
+        float v[16], vb[16];
+        ptx::tmem_ld16x2(ta + c, tb + c, v, vb);
+        if (m < nprow) {
+#pragma unroll
+            for (int g8 = 0; g8 < 2; ++g8) {
+                float w[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    w[k] = (m < nrow) ? (two ? v[8 * g8 + k] + vb[8 * g8 + k] : v[8 * g8 + k]) * us : 0.f;
+                store_split8(Ahi, Alo, ((c >> 3) + g8) * kCoreStride + off_r, w);
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kSlabThreads, 1) tc_slab_kernel(const SlabArgs a) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -805,8 +854,7 @@ __global__ void __launch_bounds__(kSlabThreads, 1) tc_slab_kernel(const SlabArgs
     uint8_t *V1lo = V1hi + np1 * np1 * 2;
     uint8_t *V2hi = V1lo + np1 * np1 * 2;
     uint8_t *V2lo = V2hi + np2 * np2 * 2;
-    uint8_t *buf0 = V2lo + np2 * np2 * 2;  // two A buffers (hi | lo), one per unit in flight
-    float *ostage = reinterpret_cast<float *>(buf0 + 4 * half_bytes);  // output slice [x2][x1] (stage_out)
+    uint8_t *buf0 = V2lo + np2 * np2 * 2;  // two A buffers (hi | lo), one per TMEM slot
     __shared__ SlabBars bars;
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int s_abort;
@@ -826,7 +874,7 @@ __global__ void __launch_bounds__(kSlabThreads, 1) tc_slab_kernel(const SlabArgs
             ptx::mbar_init(&bars.full[b], kSlabProdThreads);
             ptx::mbar_init(&bars.empty[b], 1);
             ptx::mbar_init(&bars.tfull[b], 1);
-            ptx::mbar_init(&bars.ready[b], kSlabEpiThreads);
+            ptx::mbar_init(&bars.ready[b], kSlabGroupThreads);
         }
         ptx::mbar_init(&bars.drain, 1);
         ptx::fence_mbar_init();
@@ -851,55 +899,65 @@ __global__ void __launch_bounds__(kSlabThreads, 1) tc_slab_kernel(const SlabArgs
 
     if (warp == kSlabMmaWarp) {
         // ---------------------------------------------------------------- MMA issue
+        // Polls both slots and issues the next product of whichever is ready:
+        // M1 of unit j needs its A1 (full) and the slot's previous unit through
+        // stage E; M2..M4 need the group's previous stage (ready).
         if (lane == 0) {
             const uint32_t sV1h = ptx::smem_u32(V1hi), sV1l = ptx::smem_u32(V1lo);
             const uint32_t sV2h = ptx::smem_u32(V2hi), sV2l = ptx::smem_u32(V2lo);
+            int jn[2] = {0, 1}, sn[2] = {0, 0};
             bool ok = true;
-            for (int jj = 0; jj < n_my && ok; jj += 2) {
-                for (int d = 0; d < 2 && ok; ++d) {  // M1 of both units
-                    const int j = jj + d;
-                    if (j >= n_my) break;
-                    const int sl = j & 1;
-                    long long tw = KX_CLK_NOW();
-                    ok = slab_wait(&bars.full[sl], (uint32_t)((j >> 1) & 1), a, &s_abort);
-                    KX_CLK_ADD(5, tw);
-                    tw = KX_CLK_NOW();
-                    if (ok && j >= 2) ok = slab_wait(&bars.ready[sl], 1u, a, &s_abort);  // stage E of unit j-2
-                    KX_CLK_ADD(6, tw);
-                    if (!ok) break;
+            long long last = clock64();
+            while (ok && (jn[0] < n_my || jn[1] < n_my)) {
+                bool progressed = false;
+#pragma unroll
+                for (int g = 0; g < 2; ++g) {
+                    const int j = jn[g], st = sn[g];
+                    if (j >= n_my) continue;
+                    bool go;
+                    if (st == 0)
+                        go = ptx::mbar_test_wait(&bars.full[g], (uint32_t)((j >> 1) & 1)) &&
+                             (j < 2 || ptx::mbar_test_wait(&bars.ready[g], 1u));
+                    else
+                        go = ptx::mbar_test_wait(&bars.ready[g], (uint32_t)((st - 1) & 1));
+                    if (!go) continue;
                     ptx::tc_fence_after();
-                    const uint32_t sA = ptx::smem_u32(buf0 + sl * 2 * half_bytes);
-                    const uint32_t da = tmem + (uint32_t)(sl * 2 * npm);
-                    issue_split_mma(da, da + (uint32_t)npm, sA, sA + (uint32_t)half_bytes, false, sV2h, sV2l, false,
-                                    np2);
-                    ptx::mma_commit(&bars.tfull[sl]);
-                }
-                for (int st = 1; st <= 3 && ok; ++st) {
-                    for (int d = 0; d < 2 && ok; ++d) {
-                        const int j = jj + d;
-                        if (j >= n_my) break;
-                        const int sl = j & 1;
-                        long long tw = KX_CLK_NOW();
-                        ok = slab_wait(&bars.ready[sl], (uint32_t)((st - 1) & 1), a, &s_abort);
-                        KX_CLK_ADD(6, tw);
-                        if (!ok) break;
-                        ptx::tc_fence_after();
-                        const uint32_t sA = ptx::smem_u32(buf0 + sl * 2 * half_bytes);
-                        const uint32_t da = tmem + (uint32_t)(sl * 2 * npm);
-                        if (st == 1)  // M2: A2 (MN-major) x V1 forward
-                            issue_split_mma(da, da + (uint32_t)npm, sA, sA + (uint32_t)half_bytes, false, sV1h, sV1l,
-                                            false, np1);
-                        else if (st == 2)  // M3: A3 (K-major) x V1^T
-                            issue_split_mma(da, da + (uint32_t)npm, sA, sA + (uint32_t)half_bytes, true, sV1h, sV1l,
-                                            true, np1);
-                        else  // M4: A4 (MN-major) x V2^T
-                            issue_split_mma(da, da + (uint32_t)npm, sA, sA + (uint32_t)half_bytes, false, sV2h, sV2l,
-                                            true, np2);
-                        ptx::mma_commit(&bars.tfull[sl]);
-                        if (st == 3) ptx::mma_commit(&bars.empty[sl]);
+                    const uint32_t sA = ptx::smem_u32(buf0 + g * 2 * half_bytes);
+                    const uint32_t da = tmem + (uint32_t)(g * 2 * npm);
+                    if (st == 0)  // M1: A1 (MN-major) x V2 forward
+                        issue_split_mma(da, da + (uint32_t)npm, sA, sA + (uint32_t)half_bytes, false, sV2h, sV2l,
+                                        false, np2);
+                    else if (st == 1)  // M2: A2 (MN-major) x V1 forward
+                        issue_split_mma(da, da + (uint32_t)npm, sA, sA + (uint32_t)half_bytes, false, sV1h, sV1l,
+                                        false, np1);
+                    else if (st == 2)  // M3: A3 (K-major) x V1^T
+                        issue_split_mma(da, da + (uint32_t)npm, sA, sA + (uint32_t)half_bytes, true, sV1h, sV1l,
+                                        true, np1);
+                    else  // M4: A4 (MN-major) x V2^T
+                        issue_split_mma(da, da + (uint32_t)npm, sA, sA + (uint32_t)half_bytes, false, sV2h, sV2l,
+                                        true, np2);
+                    ptx::mma_commit(&bars.tfull[g]);
+                    if (st == 3) ptx::mma_commit(&bars.empty[g]);
+                    if (++sn[g] == 4) {
+                        sn[g] = 0;
+                        jn[g] += 2;
                     }
+                    progressed = true;
+                }
+                const long long now = clock64();
+                if (progressed) {
+                    last = now;
+                } else if (s_abort) {
+                    ok = false;
+                } else if (now - last > a.timeout_cycles) {
+                    s_abort = 1;
+                    atomicExch(a.status, KX_ERR_TIMEOUT);
+                    ok = false;
                 }
             }
+#ifdef KX_ROLE_CLOCKS
+            clk_acc[5] = 0;
+#endif
             if (!ok) {
                 ptx::mma_commit(&bars.drain);
                 ptx::mbar_wait_bounded(&bars.drain, 0, a.timeout_cycles);
@@ -908,7 +966,7 @@ __global__ void __launch_bounds__(kSlabThreads, 1) tc_slab_kernel(const SlabArgs
         __syncwarp();
     } else if (warp >= kSlabEpiWarps) {
         // ---------------------------------------------------------------- producers: A1 from global
-        const int ptid = tid - kSlabEpiThreads;
+        const int ptid = tid - kSlabEpiWarps * 32;
         const int ntask = 16 * np2;  // 16 row groups (x1) x np2 columns (x2)
         const int nlines = (int)((n12 * 4) >> 7);  // 128-byte lines of a slice (n1 % 8 == 0)
         for (int it = 0; it < n_my; ++it) {
@@ -959,215 +1017,166 @@ __global__ void __launch_bounds__(kSlabThreads, 1) tc_slab_kernel(const SlabArgs
             KX_CLK_ADD(2, tw);
         }
     } else {
-        // ---------------------------------------------------------------- epilogue stages B, C, D, E
-        // Warp w reads TMEM lanes 32*(w%4).. (its D rows) and the 16-column
-        // chunks c = 16*(w/4) + 32*i, two chunks per load round.  tcgen05.ld is
-        // warp-collective, so every lane of a warp loads and only the stores are
-        // predicated per row.  After a failed wait the warps keep walking the
-        // same stage sequence without work, so that the barriers of stage E and
-        // of the energy sum see all eight warps.
-        const int q = warp & 3, h = warp >> 2;
+        // ---------------------------------------------------------------- epilogue: group g = warp / 4
+        // Warp w of a group reads TMEM lanes 32*(w%4).. (its D rows), all columns,
+        // 32 at a time.  tcgen05.ld is warp-collective: every lane loads, only
+        // the stores are predicated per row.
+        const int g = warp >> 2, q = warp & 3;
         const int m = 32 * q + lane;  // TMEM lane == D row
         const bool two1 = (np1 >> 4) > 1, two2 = (np2 >> 4) > 1;
         const int nkc1 = np1 >> 3;
-        const bool sto = a.stage_out != 0;
+        const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(g * 2 * npm);
+        const uint32_t tb = ta + (uint32_t)npm;
+        uint8_t *Ahi = buf0 + g * 2 * half_bytes;
+        uint8_t *Alo = Ahi + half_bytes;
         double e_acc = 0.0;
         bool ok = true;
-        for (int jj = 0; jj < n_my; jj += 2) {
-            // per-unit constants of the two units in flight
-            long long itm[2], k3u[2];
-            int ex1[2], ex2[2], ex3[2], ex4[2];
-            double wgt[2];
+        for (int j = g; j < n_my && ok; j += 2) {
+            long long tw = KX_CLK_NOW();
+            const SlabUnit U = slab_unit(a, blockIdx.x + (long long)j * gridDim.x);
+            KX_CLK_ADD(0, tw);
+            // ---- B: D1[x1][k2] -> A2[k2][x1]
+            tw = KX_CLK_NOW();
+            ok = __all_sync(0xffffffffu, slab_wait(&bars.tfull[g], 0u, a, &s_abort));
+            KX_CLK_ADD(9, tw);
+            if (!ok) break;
+            tw = KX_CLK_NOW();
+            ptx::tc_fence_after();
+            if (32 * q < np1)
+                slab_transpose_stage(ta, tb, m, a.n1, np1, np2, two2, ldexpf(1.f, U.e2 - U.e1 - kVScaleExp), Ahi,
+                                     Alo);
+            ptx::fence_proxy_async_smem();
+            ptx::tc_fence_before();
+            ptx::mbar_arrive(&bars.ready[g]);
+            KX_CLK_ADD(10, tw);
+            // ---- C: D2[k2][k1] = Y: energy sum f Y^2, mid = f Y -> A3[k2][k1] (K-major, own row)
+            {
+                const bool rowC = m < a.n2;
+                const float *frow = a.f32 + (U.k3 * a.n2 + m) * (long long)a.n1;
+                // f(Lambda) of the row, three 16-column chunks ahead (ring of registers)
+                float fr[3][16];
 #pragma unroll
-            for (int d = 0; d < 2; ++d) {
-                const long long u = blockIdx.x + (long long)min(jj + d, n_my - 1) * gridDim.x;
-                itm[d] = (unsigned)u / (unsigned)a.n3;
-                k3u[d] = (unsigned)u % (unsigned)a.n3;
-                const float b1 = __ldg(a.in_max + itm[d]);
-                const float b2 = b1 * a.sq2, b3 = a.fmax * a.sq1 * b2, b4 = a.sq1 * b3;
-                ex1[d] = scale_exp(b1);
-                ex2[d] = scale_exp(b2);
-                ex3[d] = scale_exp(b3);
-                ex4[d] = scale_exp(b4);
-                double w = 0.0;
-                if (a.e_partial != nullptr && !a.rhs_mode) {
-                    const int2 ij = a.pairs[itm[d]];
-                    w = (ij.x == ij.y) ? 1.0 : 2.0;
-                    if (a.occ) w *= a.occ[ij.x] * a.occ[ij.y];
+                for (int r = 0; r < 3; ++r) {
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh) {
+                        const int c0 = 16 * r + 8 * hh;
+                        if (rowC && c0 < a.n1) {
+                            ld8(frow + c0, fr[r] + 8 * hh);
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) fr[r][8 * hh + k] = 0.f;
+                        }
+                    }
                 }
-                wgt[d] = w;
+                tw = KX_CLK_NOW();
+                ok = __all_sync(0xffffffffu, slab_wait(&bars.tfull[g], 1u, a, &s_abort));
+                KX_CLK_ADD(9, tw);
+                if (!ok) break;
+                tw = KX_CLK_NOW();
+                ptx::tc_fence_after();
+                const float u2 = ldexpf(1.f, -(U.e2 + kVScaleExp));
+                const float s3 = ldexpf(1.f, U.e3);
+                const int off_r = (m >> 3) * (nkc1 * kCoreStride) + (m & 7) * 16;
+                float e_row = 0.f;
+#pragma unroll
+                for (int r = 0; r < kMaxN / 16; ++r) {
+                    const int c = 16 * r;
+                    if (c >= np1) break;
+                    float v[16], vb[16];
+                    ptx::tmem_ld16x2(ta + c, tb + c, v, vb);
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        const float y = rowC ? (two1 ? v[k] + vb[k] : v[k]) * u2 : 0.f;
+                        e_row = fmaf(fr[r % 3][k] * y, y, e_row);
+                        v[k] = fr[r % 3][k] * y * s3;
+                    }
+                    // refill this ring slot with the chunk three ahead
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh) {
+                        const int c0 = c + 48 + 8 * hh;
+                        if (rowC && c0 < a.n1) {
+                            const float4 *src = reinterpret_cast<const float4 *>(frow + c0);
+                            const float4 x0 = __ldg(src), x1 = __ldg(src + 1);
+                            fr[r % 3][8 * hh + 0] = x0.x;
+                            fr[r % 3][8 * hh + 1] = x0.y;
+                            fr[r % 3][8 * hh + 2] = x0.z;
+                            fr[r % 3][8 * hh + 3] = x0.w;
+                            fr[r % 3][8 * hh + 4] = x1.x;
+                            fr[r % 3][8 * hh + 5] = x1.y;
+                            fr[r % 3][8 * hh + 6] = x1.z;
+                            fr[r % 3][8 * hh + 7] = x1.w;
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) fr[r % 3][8 * hh + k] = 0.f;
+                        }
+                    }
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh)
+                        store_split8(Ahi, Alo, off_r + ((c >> 3) + hh) * kCoreStride, v + 8 * hh);
+                }
+                if (rowC) e_acc += U.w * (double)e_row;
+                ptx::fence_proxy_async_smem();
+                ptx::tc_fence_before();
+                ptx::mbar_arrive(&bars.ready[g]);
+                KX_CLK_ADD(11, tw);
             }
-            for (int st = 0; st < 4; ++st) {
-                for (int d = 0; d < 2; ++d) {
-                    const int j = jj + d;
-                    if (j >= n_my) break;
-                    const int sl = j & 1;
-                    const long long item = d ? itm[1] : itm[0], k3 = d ? k3u[1] : k3u[0];
-                    const int e1 = d ? ex1[1] : ex1[0], e2 = d ? ex2[1] : ex2[0];
-                    const int e3 = d ? ex3[1] : ex3[0], e4 = d ? ex4[1] : ex4[0];
-                    uint8_t *Ahi = buf0 + sl * 2 * half_bytes;
-                    uint8_t *Alo = Ahi + half_bytes;
-                    // stage C: the row's first 16 f(Lambda) values are fetched before the wait,
-                    // each further chunk's while the previous one is processed
-                    float fpre[16];
-                    const bool rowC = (st == 1) && m < a.n2;
-                    const float *frow = a.f32 + (k3 * a.n2 + m) * (long long)a.n1;
-                    if (st == 1 && ok) {
+            // ---- D: D3[k2][x1] -> A4[x1][k2]
+            tw = KX_CLK_NOW();
+            ok = __all_sync(0xffffffffu, slab_wait(&bars.tfull[g], 0u, a, &s_abort));
+            KX_CLK_ADD(9, tw);
+            if (!ok) break;
+            tw = KX_CLK_NOW();
+            ptx::tc_fence_after();
+            if (32 * q < np2)
+                slab_transpose_stage(ta, tb, m, a.n2, np2, np1, two1, ldexpf(1.f, U.e4 - U.e3 - kVScaleExp), Ahi,
+                                     Alo);
+            ptx::fence_proxy_async_smem();
+            ptx::tc_fence_before();
+            ptx::mbar_arrive(&bars.ready[g]);
+            KX_CLK_ADD(3, tw);
+            // ---- E: D4[x1][x2] -> slice [x2][x1] of the output, coalesced over x1
+            tw = KX_CLK_NOW();
+            ok = __all_sync(0xffffffffu, slab_wait(&bars.tfull[g], 1u, a, &s_abort));
+            KX_CLK_ADD(9, tw);
+            if (!ok) break;
+            tw = KX_CLK_NOW();
+            ptx::tc_fence_after();
+            {
+                const float u4 = ldexpf(1.f, -(U.e4 + kVScaleExp));
+                const bool valid = m < a.n1;
+                float *orow = a.out + U.item * a.N + U.k3 * n12 + m;
+                float my_max = 0.f;
+                if (32 * q < a.n1) {
+                    for (int c = 0; c < np2; c += 32) {
+                        float v[32], vb[32];
+                        const bool wide = c + 32 <= np2;
+                        if (wide)
+                            ptx::tmem_ld32x2(ta + c, tb + c, v, vb);
+                        else
+                            ptx::tmem_ld16x2(ta + c, tb + c, v, vb);
+                        if (!valid) continue;
 #pragma unroll
-                        for (int hh = 0; hh < 2; ++hh) {
-                            const int c0 = 16 * h + 8 * hh;
-                            if (rowC && c0 < a.n1) {
-                                ld8(frow + c0, fpre + 8 * hh);
-                            } else {
-#pragma unroll
-                                for (int k = 0; k < 8; ++k) fpre[8 * hh + k] = 0.f;
+                        for (int k = 0; k < 32; ++k) {
+                            if (k >= 16 && !wide) break;
+                            if (c + k < a.n2) {
+                                const float y = (two2 ? v[k] + vb[k] : v[k]) * u4;
+                                my_max = fmaxf(my_max, fabsf(y));
+                                orow[(long long)(c + k) * a.n1] = y;
                             }
                         }
                     }
-                    long long tw = KX_CLK_NOW();
-                    if (ok) ok = __all_sync(0xffffffffu, slab_wait(&bars.tfull[sl], (uint32_t)(st & 1), a, &s_abort));
-                    KX_CLK_ADD(9, tw);
-                    tw = KX_CLK_NOW();
-                    ptx::tc_fence_after();
-                    const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(sl * 2 * npm);
-                    const uint32_t tb = ta + (uint32_t)npm;
-                    if (st == 0 || st == 2) {
-                        // B: D1[x1][k2] -> A2[k2][x1];  D: D3[k2][x1] -> A4[x1][k2]  (both MN-major).
-                        // The thread of D row r writes K column r of the next operand: 8 consecutive
-                        // M values (D columns) per 16-byte store.  Rows r >= n (padding) give zeros.
-                        const int nrow = (st == 0) ? a.n1 : a.n2, nprow = (st == 0) ? np1 : np2;
-                        const int ncol = (st == 0) ? np2 : np1;
-                        const bool two = (st == 0) ? two2 : two1;
-                        const float us = (st == 0) ? ldexpf(1.f, e2 - e1 - kVScaleExp) : ldexpf(1.f, e4 - e3 - kVScaleExp);
-                        if (ok && 32 * q < nprow) {
-                            const int off_r = (m >> 3) * (16 * kCoreStride) + (m & 7) * 16;
-#pragma unroll
-                            for (int i = 0; i < 4; i += 2) {
-                                const int c0 = 16 * h + 32 * i;
-                                if (c0 >= ncol) break;
-                                const bool has2 = c0 + 32 < ncol;
-                                float v[2][16], vb[2][16];
-                                if (has2)
-                                    ptx::tmem_ld16x4(ta + c0, tb + c0, ta + c0 + 32, tb + c0 + 32, v[0], vb[0], v[1], vb[1]);
-                                else
-                                    ptx::tmem_ld16x2(ta + c0, tb + c0, v[0], vb[0]);
-                                if (m < nprow) {
-#pragma unroll
-                                    for (int g = 0; g < 2; ++g) {
-                                        if (g == 1 && !has2) break;
-                                        const int c = c0 + 32 * g;
-#pragma unroll
-                                        for (int hh = 0; hh < 2; ++hh) {
-                                            float w[8];
-#pragma unroll
-                                            for (int k = 0; k < 8; ++k)
-                                                w[k] = (m < nrow) ? (two ? v[g][8 * hh + k] + vb[g][8 * hh + k] : v[g][8 * hh + k]) * us
-                                                                  : 0.f;
-                                            store_split8(Ahi, Alo, ((c >> 3) + hh) * kCoreStride + off_r, w);
-                                        }
-                                    }
-                                }
-                            }
-                        }
-                        ptx::fence_proxy_async_smem();
-                    } else if (st == 1) {
-                        // C: D2[k2][k1] = Y: energy sum f Y^2, mid = f Y -> A3[k2][k1] (K-major, own row)
-                        const float u2 = ldexpf(1.f, -(e2 + kVScaleExp));
-                        const float s3 = ldexpf(1.f, e3);
-                        const int off_r = (m >> 3) * (nkc1 * kCoreStride) + (m & 7) * 16;
-                        float e_row = 0.f;
-                        if (ok) {
-                            for (int c = 16 * h; c < np1; c += 32) {
-                                float fk[16];
-#pragma unroll
-                                for (int k = 0; k < 16; ++k) fk[k] = fpre[k];
-#pragma unroll
-                                for (int hh = 0; hh < 2; ++hh) {
-                                    const int c1 = c + 32 + 8 * hh;
-                                    if (rowC && c1 < a.n1) {
-                                        ld8(frow + c1, fpre + 8 * hh);
-                                    } else {
-#pragma unroll
-                                        for (int k = 0; k < 8; ++k) fpre[8 * hh + k] = 0.f;
-                                    }
-                                }
-                                float v[16], vb[16];
-                                ptx::tmem_ld16x2(ta + c, tb + c, v, vb);
-#pragma unroll
-                                for (int k = 0; k < 16; ++k) {
-                                    const float y = rowC ? (two1 ? v[k] + vb[k] : v[k]) * u2 : 0.f;
-                                    e_row = fmaf(fk[k] * y, y, e_row);
-                                    v[k] = fk[k] * y * s3;
-                                }
-#pragma unroll
-                                for (int hh = 0; hh < 2; ++hh)
-                                    store_split8(Ahi, Alo, off_r + ((c >> 3) + hh) * kCoreStride, v + 8 * hh);
-                            }
-                        }
-                        if (rowC) e_acc += (d ? wgt[1] : wgt[0]) * (double)e_row;
-                        ptx::fence_proxy_async_smem();
-                    } else {
-                        // E: D4[x1][x2] -> slice [x2][x1] of the output, coalesced over x1; either
-                        // through the shared staging buffer and one bulk copy, or stored directly
-                        const float u4 = ldexpf(1.f, -(e4 + kVScaleExp));
-                        const bool valid = m < a.n1;
-                        float *gslice = a.out + item * a.N + k3 * n12;
-                        float *dst = sto ? ostage : gslice;
-                        float my_max = 0.f;
-                        if (sto) {
-                            // the previous bulk copy must have finished reading the staging buffer
-                            if (tid == 0) ptx::bulk_wait_read_all();
-                            ptx::named_bar(1, kSlabEpiThreads);
-                        }
-                        if (ok && 32 * q < a.n1) {
-#pragma unroll
-                            for (int i = 0; i < 4; i += 2) {
-                                const int c0 = 16 * h + 32 * i;
-                                if (c0 >= np2) break;
-                                const bool has2 = c0 + 32 < np2;
-                                float v[2][16], vb[2][16];
-                                if (has2)
-                                    ptx::tmem_ld16x4(ta + c0, tb + c0, ta + c0 + 32, tb + c0 + 32, v[0], vb[0], v[1], vb[1]);
-                                else
-                                    ptx::tmem_ld16x2(ta + c0, tb + c0, v[0], vb[0]);
-                                if (!valid) continue;
-#pragma unroll
-                                for (int g = 0; g < 2; ++g) {
-                                    if (g == 1 && !has2) break;
-                                    const int c = c0 + 32 * g;
-#pragma unroll
-                                    for (int k = 0; k < 16; ++k) {
-                                        if (c + k < a.n2) {
-                                            const float y = (two2 ? v[g][k] + vb[g][k] : v[g][k]) * u4;
-                                            my_max = fmaxf(my_max, fabsf(y));
-                                            dst[(long long)(c + k) * a.n1 + m] = y;
-                                        }
-                                    }
-                                }
-                            }
-                        }
-                        if (sto) {
-                            ptx::fence_proxy_async_smem();
-                            ptx::named_bar(1, kSlabEpiThreads);
-                            if (tid == 0 && ok) {
-                                ptx::bulk_store(gslice, ostage, (uint32_t)(n12 * 4));
-                                ptx::bulk_commit();
-                            }
-                        }
-                        track_max(a.out_max, item, my_max, valid);
-                    }
-                    ptx::tc_fence_before();
-                    if (ok) ptx::mbar_arrive(&bars.ready[sl]);
-                    KX_CLK_ADD(st == 0 ? 10 : st == 1 ? 11 : st == 2 ? 3 : 7, tw);
                 }
+                track_max(a.out_max, U.item, my_max, valid);
             }
+            ptx::tc_fence_before();
+            ptx::mbar_arrive(&bars.ready[g]);
+            KX_CLK_ADD(7, tw);
         }
-        if (sto && tid == 0) ptx::bulk_wait_all();
         if (a.e_partial != nullptr) {
             double e = e_acc;
             for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
             if (lane == 0) s_red[warp] = e;
-            ptx::named_bar(1, kSlabEpiThreads);
+            ptx::named_bar(1, kSlabEpiWarps * 32);
             if (tid == 0) {
                 double sum = 0.0;
                 for (int w = 0; w < kSlabEpiWarps; ++w) sum += s_red[w];
@@ -1179,9 +1188,9 @@ __global__ void __launch_bounds__(kSlabThreads, 1) tc_slab_kernel(const SlabArgs
     if (a.clk != nullptr) {
         long long *o = a.clk + (long long)blockIdx.x * kClk;
         const long long tot = clock64() - clk_t0;
-        if (warp == kSlabMmaWarp && lane == 0) { o[4] = tot; o[5] = clk_acc[5]; o[6] = clk_acc[6]; }
-        if (tid == kSlabEpiThreads) { o[0] = tot; o[1] = clk_acc[1]; o[2] = clk_acc[2]; }
-        if (tid == 0) { o[8] = tot; o[9] = clk_acc[9]; o[10] = clk_acc[10]; o[11] = clk_acc[11]; o[3] = clk_acc[3]; o[7] = clk_acc[7]; }
+        if (warp == kSlabMmaWarp && lane == 0) { o[4] = tot; }
+        if (tid == kSlabEpiWarps * 32) { o[5] = tot; o[1] = clk_acc[1]; o[2] = clk_acc[2]; }
+        if (tid == 0) { o[8] = tot; o[0] = clk_acc[0]; o[9] = clk_acc[9]; o[10] = clk_acc[10]; o[11] = clk_acc[11]; o[3] = clk_acc[3]; o[7] = clk_acc[7]; }
     }
 #endif
     ptx::tc_fence_before();
@@ -1349,8 +1358,7 @@ size_t slab_smem(const kx_plan *p) {
     return (size_t)4 * np1 * np1 + (size_t)4 * np2 * np2 + 4 * a_half_bytes(npm) + 1024;
 }
 
-// The slab kernel holds V1, V2 and two split A buffers in shared memory (plus,
-// where it fits, a staging buffer for the output slice).
+// The slab kernel holds V1, V2 and two split A buffers in shared memory.
 constexpr size_t kSlabSmemMax = 227 * 1024 - 1024;  // opt-in maximum less static shared memory
 bool slab_fits(const kx_plan *p) { return slab_smem(p) <= kSlabSmemMax; }
 
@@ -1393,12 +1401,8 @@ int launch_slab(kx_plan *p, long R, const float *in, const float *in_max, float 
     if (!g_clkbuf) cudaMallocManaged(&g_clkbuf, sizeof(long long) * kClk * 4096 * 6);
     a.clk = g_clkbuf + 5LL * kClk * 4096;
 #endif
-    size_t smem = slab_smem(p);
-    const size_t ostage = (size_t)a.n1 * a.n2 * 4;
-    a.stage_out = (smem + ostage <= kSlabSmemMax) ? 1 : 0;
-    if (a.stage_out) smem += ostage;
     // at least 120 KB so that one CTA (and one 512-column TMEM allocation) sits on each SM
-    smem = std::max<size_t>(smem, 120 * 1024);
+    const size_t smem = std::max<size_t>(slab_smem(p), 120 * 1024);
     KX_CUDA_TRY(cudaFuncSetAttribute(tc_slab_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = (int)std::max(1LL, std::min<long long>(a.total_units, (long long)p->num_sms));
     if (grid_out) *grid_out = grid;

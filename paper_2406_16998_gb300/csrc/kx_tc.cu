@@ -296,21 +296,33 @@ __device__ __forceinline__ void issue_split_mma(uint32_t tmem_a, uint32_t tmem_b
     const uint32_t b_sbo = inverse ? (uint32_t)(np * 16) : 128u;
     const uint32_t b_step = inverse ? 256u : (uint32_t)(np * 32);
     const int nks = np >> 4;
-    for (int ks = 0; ks < nks; ++ks) {
-        const uint64_t ah = ptx::sdesc(a_hi + ks * a_step, a_lbo, a_sbo);
-        const uint64_t al = ptx::sdesc(a_lo + ks * a_step, a_lbo, a_sbo);
-        const uint64_t bh = ptx::sdesc(v_hi + ks * b_step, b_lbo, b_sbo);
-        const uint64_t bl = ptx::sdesc(v_lo + ks * b_step, b_lbo, b_sbo);
-        ptx::mma_f16(tmem_a, ah, bl, idesc, ks > 0 ? 1u : 0u);
+    // descriptors built once; a k-step advances the start-address field (16-byte units)
+    const uint64_t ah0 = ptx::sdesc(a_hi, a_lbo, a_sbo), al0 = ptx::sdesc(a_lo, a_lbo, a_sbo);
+    const uint64_t bh0 = ptx::sdesc(v_hi, b_lbo, b_sbo), bl0 = ptx::sdesc(v_lo, b_lbo, b_sbo);
+    const uint64_t a_inc = a_step >> 4, b_inc = b_step >> 4;
+    {
+        uint64_t ah = ah0, al = al0, bh = bh0, bl = bl0;
+        ptx::mma_f16(tmem_a, ah, bl, idesc, 0u);
         ptx::mma_f16(tmem_a, al, bh, idesc, 1u);
+        for (int ks = 1; ks < nks; ++ks) {
+            ah += a_inc;
+            al += a_inc;
+            bh += b_inc;
+            bl += b_inc;
+            ptx::mma_f16(tmem_a, ah, bl, idesc, 1u);
+            ptx::mma_f16(tmem_a, al, bh, idesc, 1u);
+        }
     }
-    for (int ks = 0; ks < nks; ++ks) {
-        const uint64_t ah = ptx::sdesc(a_hi + ks * a_step, a_lbo, a_sbo);
-        const uint64_t bh = ptx::sdesc(v_hi + ks * b_step, b_lbo, b_sbo);
-        if (ks & 1)
-            ptx::mma_f16(tmem_b, ah, bh, idesc, ks > 1 ? 1u : 0u);
-        else
-            ptx::mma_f16(tmem_a, ah, bh, idesc, 1u);
+    {
+        uint64_t ah = ah0, bh = bh0;
+        for (int ks = 0; ks < nks; ++ks) {
+            if (ks & 1)
+                ptx::mma_f16(tmem_b, ah, bh, idesc, ks > 1 ? 1u : 0u);
+            else
+                ptx::mma_f16(tmem_a, ah, bh, idesc, 1u);
+            ah += a_inc;
+            bh += b_inc;
+        }
     }
 }
 
@@ -760,20 +772,24 @@ struct SlabArgs {
     const int2 *pairs;
     const double *occ;
     int rhs_mode;
+    int stage_in;           // the input plane is bulk-copied into shared memory before it is split
     int *status;
     long long timeout_cycles;
     long long *clk;         // role counters (only with KX_ROLE_CLOCKS)
 };
 
-constexpr int kSlabEpiWarps = 8;     // two warpgroups, one per TMEM slot
-constexpr int kSlabGroupThreads = 128;
 constexpr int kSlabProdThreads = 96;
 constexpr int kSlabU = 8;            // producer loads in flight per thread
+// Warp roles: 16 epilogue warps (warp w reads TMEM lane quadrant w % 4, the
+// TMEM access rule; column half (w / 4) % 2; group w / 8), then 3 producer
+// warps, then the MMA warp.
+constexpr int kSlabEpiWarps = 16;
+constexpr int kSlabGroupThreads = 256;
 constexpr int kSlabMmaWarp = kSlabEpiWarps + kSlabProdThreads / 32;
 constexpr int kSlabThreads = 32 * (kSlabMmaWarp + 1);
 
 struct SlabBars {
-    uint64_t full[2], empty[2], tfull[2], ready[2], drain;
+    uint64_t full[2], empty[2], tfull[2], ready[2], in_full, drain;
 };
 
 __device__ __forceinline__ bool slab_wait(uint64_t *bar, uint32_t parity, const SlabArgs &a, volatile int *abort) {
@@ -826,10 +842,10 @@ __device__ __forceinline__ SlabUnit slab_unit(const SlabArgs &a, long long u) {
 // Epilogue stage B or D for one warp: D row m (a TMEM lane) becomes K column m
 // of the next MN-major operand; 8 consecutive D columns (M values) per 16-byte
 // store.  Rows m >= nrow (padding) give zeros; rows m >= nprow are not written.
-__device__ __forceinline__ void slab_transpose_stage(uint32_t ta, uint32_t tb, int m, int nrow, int nprow, int ncol,
-                                                     bool two, float us, uint8_t *Ahi, uint8_t *Alo) {
+__device__ __forceinline__ void slab_transpose_stage(uint32_t ta, uint32_t tb, int m, int h, int nrow, int nprow,
+                                                     int ncol, bool two, float us, uint8_t *Ahi, uint8_t *Alo) {
     const int off_r = (m >> 3) * (16 * kCoreStride) + (m & 7) * 16;
-    for (int c = 0; c < ncol; c += 16) {
+    for (int c = 16 * h; c < ncol; c += 32) {
         float v[16], vb[16];
         ptx::tmem_ld16x2(ta + c, tb + c, v, vb);
         if (m < nprow) {
@@ -855,6 +871,7 @@ __global__ void __launch_bounds__(kSlabThreads, 1) tc_slab_kernel(const SlabArgs
     uint8_t *V2hi = V1lo + np1 * np1 * 2;
     uint8_t *V2lo = V2hi + np2 * np2 * 2;
     uint8_t *buf0 = V2lo + np2 * np2 * 2;  // two A buffers (hi | lo), one per TMEM slot
+    float *sin = reinterpret_cast<float *>(buf0 + 4 * half_bytes);  // input plane [x2][x1] (stage_in)
     __shared__ SlabBars bars;
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int s_abort;
@@ -876,6 +893,7 @@ __global__ void __launch_bounds__(kSlabThreads, 1) tc_slab_kernel(const SlabArgs
             ptx::mbar_init(&bars.tfull[b], 1);
             ptx::mbar_init(&bars.ready[b], kSlabGroupThreads);
         }
+        ptx::mbar_init(&bars.in_full, 1);
         ptx::mbar_init(&bars.drain, 1);
         ptx::fence_mbar_init();
         s_abort = 0;
@@ -969,59 +987,111 @@ __global__ void __launch_bounds__(kSlabThreads, 1) tc_slab_kernel(const SlabArgs
         const int ptid = tid - kSlabEpiWarps * 32;
         const int ntask = 16 * np2;  // 16 row groups (x1) x np2 columns (x2)
         const int nlines = (int)((n12 * 4) >> 7);  // 128-byte lines of a slice (n1 % 8 == 0)
+        const uint32_t plane_bytes = (uint32_t)(n12 * 4);
+        auto plane = [&](int it) {
+            const long long u = blockIdx.x + (long long)it * gridDim.x;
+            const long long item = (unsigned)u / (unsigned)a.n3, k3 = (unsigned)u % (unsigned)a.n3;
+            return a.in + item * a.N + k3 * n12;
+        };
+        // stage_in: one thread copies the plane of the next unit into shared memory
+        // (pieces of at most 16 KB) as soon as the previous plane has been split
+        auto issue_plane = [&](int it) {
+            ptx::fence_proxy_async_smem();
+            ptx::mbar_arrive_expect_tx(&bars.in_full, plane_bytes);
+            const char *src = reinterpret_cast<const char *>(plane(it));
+            char *dst = reinterpret_cast<char *>(sin);
+            for (uint32_t o = 0; o < plane_bytes; o += 16384u)
+                ptx::bulk_load(dst + o, src + o, min(16384u, plane_bytes - o), &bars.in_full);
+        };
+        int inflight = -1;  // unit whose plane copy thread 0 issued and has not yet waited for
+        if (a.stage_in && ptid == 0 && n_my > 0) {
+            issue_plane(0);
+            inflight = 0;
+        }
         for (int it = 0; it < n_my; ++it) {
             const int sl = it & 1;
             if (it + 2 < n_my) {
-                // pull the slice of unit it+2 into L2 while this unit waits for its buffer
-                const long long u2 = blockIdx.x + (long long)(it + 2) * gridDim.x;
-                const long long item2 = (unsigned)u2 / (unsigned)a.n3, k32 = (unsigned)u2 % (unsigned)a.n3;
-                const char *src = reinterpret_cast<const char *>(a.in + item2 * a.N + k32 * n12);
+                // pull the plane of unit it+2 into L2 while this unit waits for its buffer
+                const char *src = reinterpret_cast<const char *>(plane(it + 2));
                 for (int l = ptid; l < nlines; l += kSlabProdThreads) ptx::prefetch_l2(src + ((long long)l << 7));
             }
             long long tw = KX_CLK_NOW();
-            if (it >= 2 && !slab_wait(&bars.empty[sl], (uint32_t)(((it >> 1) - 1) & 1), a, &s_abort)) break;
+            bool ok = it < 2 || slab_wait(&bars.empty[sl], (uint32_t)(((it >> 1) - 1) & 1), a, &s_abort);
             KX_CLK_ADD(1, tw);
             tw = KX_CLK_NOW();
-            if (s_abort) break;
+            if (ok && a.stage_in) ok = slab_wait(&bars.in_full, (uint32_t)(it & 1), a, &s_abort);
+            if (ok && ptid == 0) inflight = -1;
+            ok = ok && !s_abort;
+            // with stage_in the producers meet at a named barrier below, so they leave together
+            if (a.stage_in) ok = ptx::named_bar_and(2, kSlabProdThreads, ok);
+            if (!ok) break;
             const long long u = blockIdx.x + (long long)it * gridDim.x;
-            const long long item = (unsigned)u / (unsigned)a.n3, k3 = (unsigned)u % (unsigned)a.n3;
-            const float *slice = a.in + item * a.N + k3 * n12;
+            const long long item = (unsigned)u / (unsigned)a.n3;
             const float sc = ldexpf(1.f, scale_exp(a.in_max[item]));
             uint8_t *Ahi = buf0 + sl * 2 * half_bytes;
             uint8_t *Alo = Ahi + half_bytes;
-            for (int t0 = ptid; t0 < ntask; t0 += kSlabProdThreads * kSlabU) {
-                float v[kSlabU][8];
-#pragma unroll
-                for (int r = 0; r < kSlabU; ++r) {
-                    const int t = t0 + r * kSlabProdThreads;
+            if (a.stage_in) {
+#pragma unroll 4
+                for (int t = ptid; t < ntask; t += kSlabProdThreads) {
                     const int g = t & 15, k = t >> 4;
-                    if (t < ntask && 8 * g < a.n1 && k < a.n2) {
-                        ld8(slice + (long long)k * a.n1 + 8 * g, v[r]);
+                    float v[8];
+                    if (8 * g < a.n1 && k < a.n2) {
+                        const float4 *src = reinterpret_cast<const float4 *>(sin + k * a.n1 + 8 * g);
+                        const float4 x0 = src[0], x1 = src[1];
+                        v[0] = x0.x * sc; v[1] = x0.y * sc; v[2] = x0.z * sc; v[3] = x0.w * sc;
+                        v[4] = x1.x * sc; v[5] = x1.y * sc; v[6] = x1.z * sc; v[7] = x1.w * sc;
                     } else {
 #pragma unroll
-                        for (int c = 0; c < 8; ++c) v[r][c] = 0.f;
+                        for (int c = 0; c < 8; ++c) v[c] = 0.f;
+                    }
+                    store_split8(Ahi, Alo, g * kCoreStride + (k >> 3) * (16 * kCoreStride) + (k & 7) * 16, v);
+                }
+                ptx::fence_proxy_async_smem();
+                ptx::mbar_arrive(&bars.full[sl]);
+                // every producer has finished reading the plane: it may be overwritten
+                ptx::named_bar(2, kSlabProdThreads);
+                if (ptid == 0 && it + 1 < n_my) {
+                    issue_plane(it + 1);
+                    inflight = it + 1;
+                }
+            } else {
+                const float *slice = plane(it);
+                for (int t0 = ptid; t0 < ntask; t0 += kSlabProdThreads * kSlabU) {
+                    float v[kSlabU][8];
+#pragma unroll
+                    for (int r = 0; r < kSlabU; ++r) {
+                        const int t = t0 + r * kSlabProdThreads;
+                        const int g = t & 15, k = t >> 4;
+                        if (t < ntask && 8 * g < a.n1 && k < a.n2) {
+                            ld8(slice + (long long)k * a.n1 + 8 * g, v[r]);
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < 8; ++c) v[r][c] = 0.f;
+                        }
+                    }
+#pragma unroll
+                    for (int r = 0; r < kSlabU; ++r) {
+                        const int t = t0 + r * kSlabProdThreads;
+                        if (t >= ntask) continue;
+                        const int g = t & 15, k = t >> 4;
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) v[r][c] *= sc;
+                        store_split8(Ahi, Alo, g * kCoreStride + (k >> 3) * (16 * kCoreStride) + (k & 7) * 16, v[r]);
                     }
                 }
-#pragma unroll
-                for (int r = 0; r < kSlabU; ++r) {
-                    const int t = t0 + r * kSlabProdThreads;
-                    if (t >= ntask) continue;
-                    const int g = t & 15, k = t >> 4;
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) v[r][c] *= sc;
-                    store_split8(Ahi, Alo, g * kCoreStride + (k >> 3) * (16 * kCoreStride) + (k & 7) * 16, v[r]);
-                }
+                ptx::fence_proxy_async_smem();
+                ptx::mbar_arrive(&bars.full[sl]);
             }
-            ptx::fence_proxy_async_smem();
-            ptx::mbar_arrive(&bars.full[sl]);
             KX_CLK_ADD(2, tw);
         }
+        // a plane copy still in flight after an early exit must land before the CTA leaves
+        if (inflight >= 0) ptx::mbar_wait_bounded(&bars.in_full, (uint32_t)(inflight & 1), a.timeout_cycles);
     } else {
-        // ---------------------------------------------------------------- epilogue: group g = warp / 4
-        // Warp w of a group reads TMEM lanes 32*(w%4).. (its D rows), all columns,
-        // 32 at a time.  tcgen05.ld is warp-collective: every lane loads, only
-        // the stores are predicated per row.
-        const int g = warp >> 2, q = warp & 3;
+        // ---------------------------------------------------------------- epilogue: group g = warp / 8
+        // Warp w of a group reads TMEM lanes 32*(w%4).. (its D rows) and the
+        // 16-column chunks c = 16*h + 32*i, h = (w/4)%2.  tcgen05.ld is
+        // warp-collective: every lane loads, only the stores are predicated per row.
+        const int g = warp >> 3, q = warp & 3, h = (warp >> 2) & 1;
         const int m = 32 * q + lane;  // TMEM lane == D row
         const bool two1 = (np1 >> 4) > 1, two2 = (np2 >> 4) > 1;
         const int nkc1 = np1 >> 3;
@@ -1043,7 +1113,7 @@ __global__ void __launch_bounds__(kSlabThreads, 1) tc_slab_kernel(const SlabArgs
             tw = KX_CLK_NOW();
             ptx::tc_fence_after();
             if (32 * q < np1)
-                slab_transpose_stage(ta, tb, m, a.n1, np1, np2, two2, ldexpf(1.f, U.e2 - U.e1 - kVScaleExp), Ahi,
+                slab_transpose_stage(ta, tb, m, h, a.n1, np1, np2, two2, ldexpf(1.f, U.e2 - U.e1 - kVScaleExp), Ahi,
                                      Alo);
             ptx::fence_proxy_async_smem();
             ptx::tc_fence_before();
@@ -1053,19 +1123,17 @@ __global__ void __launch_bounds__(kSlabThreads, 1) tc_slab_kernel(const SlabArgs
             {
                 const bool rowC = m < a.n2;
                 const float *frow = a.f32 + (U.k3 * a.n2 + m) * (long long)a.n1;
-                // f(Lambda) of the row, three 16-column chunks ahead (ring of registers)
-                float fr[3][16];
+                // f(Lambda) of this warp's first chunk; each further chunk's is fetched
+                // while the previous one is processed
+                float fr[2][16];
 #pragma unroll
-                for (int r = 0; r < 3; ++r) {
+                for (int hh = 0; hh < 2; ++hh) {
+                    const int c0 = 16 * h + 8 * hh;
+                    if (rowC && c0 < a.n1) {
+                        ld8(frow + c0, fr[0] + 8 * hh);
+                    } else {
 #pragma unroll
-                    for (int hh = 0; hh < 2; ++hh) {
-                        const int c0 = 16 * r + 8 * hh;
-                        if (rowC && c0 < a.n1) {
-                            ld8(frow + c0, fr[r] + 8 * hh);
-                        } else {
-#pragma unroll
-                            for (int k = 0; k < 8; ++k) fr[r][8 * hh + k] = 0.f;
-                        }
+                        for (int k = 0; k < 8; ++k) fr[0][8 * hh + k] = 0.f;
                     }
                 }
                 tw = KX_CLK_NOW();
@@ -1079,36 +1147,35 @@ __global__ void __launch_bounds__(kSlabThreads, 1) tc_slab_kernel(const SlabArgs
                 const int off_r = (m >> 3) * (nkc1 * kCoreStride) + (m & 7) * 16;
                 float e_row = 0.f;
 #pragma unroll
-                for (int r = 0; r < kMaxN / 16; ++r) {
-                    const int c = 16 * r;
+                for (int r = 0; r < kMaxN / 32; ++r) {
+                    const int c = 16 * h + 32 * r;
                     if (c >= np1) break;
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh) {
+                        const int c0 = c + 32 + 8 * hh;
+                        if (rowC && c0 < a.n1) {
+                            const float4 *src = reinterpret_cast<const float4 *>(frow + c0);
+                            const float4 x0 = __ldg(src), x1 = __ldg(src + 1);
+                            fr[(r + 1) & 1][8 * hh + 0] = x0.x;
+                            fr[(r + 1) & 1][8 * hh + 1] = x0.y;
+                            fr[(r + 1) & 1][8 * hh + 2] = x0.z;
+                            fr[(r + 1) & 1][8 * hh + 3] = x0.w;
+                            fr[(r + 1) & 1][8 * hh + 4] = x1.x;
+                            fr[(r + 1) & 1][8 * hh + 5] = x1.y;
+                            fr[(r + 1) & 1][8 * hh + 6] = x1.z;
+                            fr[(r + 1) & 1][8 * hh + 7] = x1.w;
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) fr[(r + 1) & 1][8 * hh + k] = 0.f;
+                        }
+                    }
                     float v[16], vb[16];
                     ptx::tmem_ld16x2(ta + c, tb + c, v, vb);
 #pragma unroll
                     for (int k = 0; k < 16; ++k) {
                         const float y = rowC ? (two1 ? v[k] + vb[k] : v[k]) * u2 : 0.f;
-                        e_row = fmaf(fr[r % 3][k] * y, y, e_row);
-                        v[k] = fr[r % 3][k] * y * s3;
-                    }
-                    // refill this ring slot with the chunk three ahead
-#pragma unroll
-                    for (int hh = 0; hh < 2; ++hh) {
-                        const int c0 = c + 48 + 8 * hh;
-                        if (rowC && c0 < a.n1) {
-                            const float4 *src = reinterpret_cast<const float4 *>(frow + c0);
-                            const float4 x0 = __ldg(src), x1 = __ldg(src + 1);
-                            fr[r % 3][8 * hh + 0] = x0.x;
-                            fr[r % 3][8 * hh + 1] = x0.y;
-                            fr[r % 3][8 * hh + 2] = x0.z;
-                            fr[r % 3][8 * hh + 3] = x0.w;
-                            fr[r % 3][8 * hh + 4] = x1.x;
-                            fr[r % 3][8 * hh + 5] = x1.y;
-                            fr[r % 3][8 * hh + 6] = x1.z;
-                            fr[r % 3][8 * hh + 7] = x1.w;
-                        } else {
-#pragma unroll
-                            for (int k = 0; k < 8; ++k) fr[r % 3][8 * hh + k] = 0.f;
-                        }
+                        e_row = fmaf(fr[r & 1][k] * y, y, e_row);
+                        v[k] = fr[r & 1][k] * y * s3;
                     }
 #pragma unroll
                     for (int hh = 0; hh < 2; ++hh)
@@ -1128,7 +1195,7 @@ __global__ void __launch_bounds__(kSlabThreads, 1) tc_slab_kernel(const SlabArgs
             tw = KX_CLK_NOW();
             ptx::tc_fence_after();
             if (32 * q < np2)
-                slab_transpose_stage(ta, tb, m, a.n2, np2, np1, two1, ldexpf(1.f, U.e4 - U.e3 - kVScaleExp), Ahi,
+                slab_transpose_stage(ta, tb, m, h, a.n2, np2, np1, two1, ldexpf(1.f, U.e4 - U.e3 - kVScaleExp), Ahi,
                                      Alo);
             ptx::fence_proxy_async_smem();
             ptx::tc_fence_before();
@@ -1147,17 +1214,12 @@ __global__ void __launch_bounds__(kSlabThreads, 1) tc_slab_kernel(const SlabArgs
                 float *orow = a.out + U.item * a.N + U.k3 * n12 + m;
                 float my_max = 0.f;
                 if (32 * q < a.n1) {
-                    for (int c = 0; c < np2; c += 32) {
-                        float v[32], vb[32];
-                        const bool wide = c + 32 <= np2;
-                        if (wide)
-                            ptx::tmem_ld32x2(ta + c, tb + c, v, vb);
-                        else
-                            ptx::tmem_ld16x2(ta + c, tb + c, v, vb);
+                    for (int c = 16 * h; c < np2; c += 32) {
+                        float v[16], vb[16];
+                        ptx::tmem_ld16x2(ta + c, tb + c, v, vb);
                         if (!valid) continue;
 #pragma unroll
-                        for (int k = 0; k < 32; ++k) {
-                            if (k >= 16 && !wide) break;
+                        for (int k = 0; k < 16; ++k) {
                             if (c + k < a.n2) {
                                 const float y = (two2 ? v[k] + vb[k] : v[k]) * u4;
                                 my_max = fmaxf(my_max, fabsf(y));
@@ -1202,13 +1264,15 @@ __global__ void __launch_bounds__(kSlabThreads, 1) tc_slab_kernel(const SlabArgs
 }
 
 // Accumulation of one chunk, group by group: one thread per four grid points
-// keeps psi and the partial sums of the group's (<= kGroupSlots) orbitals in
-// shared memory and visits the group's items in order, adding
-// g_j psi_j phi_ij to orbital i and g_i psi_i phi_ij to orbital j; at the end
-// of the group it adds the partial sums into the fp32 accumulators.  Every
+// visits the group's items in order, adding g_j psi_j phi_ij to orbital i and
+// g_i psi_i phi_ij to orbital j in shared-memory partial sums (one per orbital
+// slot of the group, <= kGroupSlots), then adds the partial sums into the fp32
+// accumulators.  All of a group's global loads (phi of every item, psi and the
+// old accumulator of every slot) are issued before the first is used.  Every
 // accumulator element is owned by one thread per launch and chunks run in a
 // fixed order, so the result is deterministic.
 constexpr int kAccThreads = 128;
+constexpr int kGroupItems = kOrbBlock * kOrbBlock;
 
 __global__ void __launch_bounds__(kAccThreads) acc_kernel(const float *__restrict__ phi, const Group *__restrict__ groups,
                                                          int g0, int g1, int item0, const int2 *__restrict__ item_slot,
@@ -1218,6 +1282,7 @@ __global__ void __launch_bounds__(kAccThreads) acc_kernel(const float *__restric
     __shared__ float4 as[kGroupSlots][kAccThreads];
     __shared__ Group G;
     __shared__ float gs[kGroupSlots];
+    __shared__ int2 sl_s[kGroupItems];
     const int tid = threadIdx.x;
     const long long N4 = N >> 2;
     const long long x4 = (long long)blockIdx.x * kAccThreads + tid;
@@ -1225,50 +1290,59 @@ __global__ void __launch_bounds__(kAccThreads) acc_kernel(const float *__restric
     const float4 *phi4 = reinterpret_cast<const float4 *>(phi);
     const float4 *psi4 = reinterpret_cast<const float4 *>(psi32);
     float4 *acc4 = reinterpret_cast<float4 *>(acc);
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int g = g0; g < g1; ++g) {
         __syncthreads();
         if (tid == 0) G = groups[g];
         __syncthreads();
-        if (tid < G.n_slots) gs[tid] = occ ? (float)occ[G.orb[tid]] : 1.f;
-        for (int s = 0; s < G.n_slots; ++s) {
-            ps[s][tid] = valid ? __ldg(psi4 + (long long)G.orb[s] * N4 + x4) : make_float4(0.f, 0.f, 0.f, 0.f);
-            as[s][tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int ns = G.n_slots, ni = G.n_items, fi = G.first_item;
+        if (tid < ns) gs[tid] = occ ? (float)occ[G.orb[tid]] : 1.f;
+        if (tid < ni) sl_s[tid] = item_slot[fi + tid];
+        float4 f[kGroupItems], o[kGroupSlots];
+#pragma unroll
+        for (int k = 0; k < kGroupItems; ++k)
+            f[k] = (valid && k < ni) ? __ldg(phi4 + (long long)(fi + k - item0) * N4 + x4) : z;
+#pragma unroll
+        for (int s = 0; s < kGroupSlots; ++s) {
+            if (s < ns) {
+                const long long off = (long long)G.orb[s] * N4 + x4;
+                ps[s][tid] = valid ? __ldg(psi4 + off) : z;
+                o[s] = valid ? acc4[off] : z;
+                as[s][tid] = z;
+            }
         }
         __syncthreads();
-        if (valid) {
-#pragma unroll 4
-            for (int k = 0; k < G.n_items; ++k) {
-                const int item = G.first_item + k;
-                const int2 sl = __ldg(item_slot + item);
-                const float4 f = __ldg(phi4 + (long long)(item - item0) * N4 + x4);
-                const float4 pj = ps[sl.y][tid];
-                const float gj = gs[sl.y];
-                float4 ai = as[sl.x][tid];
-                ai.x = fmaf(gj * pj.x, f.x, ai.x);
-                ai.y = fmaf(gj * pj.y, f.y, ai.y);
-                ai.z = fmaf(gj * pj.z, f.z, ai.z);
-                ai.w = fmaf(gj * pj.w, f.w, ai.w);
-                as[sl.x][tid] = ai;
-                if (sl.x != sl.y) {
-                    const float4 pi = ps[sl.x][tid];
-                    const float gi = gs[sl.x];
-                    float4 aj = as[sl.y][tid];
-                    aj.x = fmaf(gi * pi.x, f.x, aj.x);
-                    aj.y = fmaf(gi * pi.y, f.y, aj.y);
-                    aj.z = fmaf(gi * pi.z, f.z, aj.z);
-                    aj.w = fmaf(gi * pi.w, f.w, aj.w);
-                    as[sl.y][tid] = aj;
-                }
+#pragma unroll
+        for (int k = 0; k < kGroupItems; ++k) {
+            if (k >= ni) break;
+            const int2 sl = sl_s[k];
+            const float4 pj = ps[sl.y][tid];
+            const float gj = gs[sl.y];
+            float4 ai = as[sl.x][tid];
+            ai.x = fmaf(gj * pj.x, f[k].x, ai.x);
+            ai.y = fmaf(gj * pj.y, f[k].y, ai.y);
+            ai.z = fmaf(gj * pj.z, f[k].z, ai.z);
+            ai.w = fmaf(gj * pj.w, f[k].w, ai.w);
+            as[sl.x][tid] = ai;
+            if (sl.x != sl.y) {
+                const float4 pi = ps[sl.x][tid];
+                const float gi = gs[sl.x];
+                float4 aj = as[sl.y][tid];
+                aj.x = fmaf(gi * pi.x, f[k].x, aj.x);
+                aj.y = fmaf(gi * pi.y, f[k].y, aj.y);
+                aj.z = fmaf(gi * pi.z, f[k].z, aj.z);
+                aj.w = fmaf(gi * pi.w, f[k].w, aj.w);
+                as[sl.y][tid] = aj;
             }
-            for (int s = 0; s < G.n_slots; ++s) {
-                float4 *dst = acc4 + (long long)G.orb[s] * N4 + x4;
-                float4 o = *dst;
-                const float4 d = as[s][tid];
-                o.x += d.x;
-                o.y += d.y;
-                o.z += d.z;
-                o.w += d.w;
-                *dst = o;
+        }
+        if (valid) {
+#pragma unroll
+            for (int s = 0; s < kGroupSlots; ++s) {
+                if (s < ns) {
+                    const float4 d = as[s][tid];
+                    acc4[(long long)G.orb[s] * N4 + x4] =
+                        make_float4(o[s].x + d.x, o[s].y + d.y, o[s].z + d.z, o[s].w + d.w);
+                }
             }
         }
     }
@@ -1401,8 +1475,12 @@ int launch_slab(kx_plan *p, long R, const float *in, const float *in_max, float 
     if (!g_clkbuf) cudaMallocManaged(&g_clkbuf, sizeof(long long) * kClk * 4096 * 6);
     a.clk = g_clkbuf + 5LL * kClk * 4096;
 #endif
+    size_t smem = slab_smem(p);
+    const size_t plane = (size_t)a.n1 * a.n2 * 4;
+    a.stage_in = (smem + plane <= kSlabSmemMax) ? 1 : 0;
+    if (a.stage_in) smem += plane;
     // at least 120 KB so that one CTA (and one 512-column TMEM allocation) sits on each SM
-    const size_t smem = std::max<size_t>(slab_smem(p), 120 * 1024);
+    smem = std::max<size_t>(smem, 120 * 1024);
     KX_CUDA_TRY(cudaFuncSetAttribute(tc_slab_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = (int)std::max(1LL, std::min<long long>(a.total_units, (long long)p->num_sms));
     if (grid_out) *grid_out = grid;

@@ -221,6 +221,20 @@ __device__ __forceinline__ void tmem_ld16x4(uint32_t ta0, uint32_t tb0, uint32_t
 }
 
 // ---- bulk (non-tensor) asynchronous copies and L2 prefetch
+// Global -> shared copy of `bytes` (multiple of 16, both addresses 16-byte
+// aligned) that signals completion on `bar` as transaction bytes.
+__device__ __forceinline__ void bulk_load(void *sdst, const void *gsrc, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(sdst)),
+        "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+// Arrive on `bar` and announce `bytes` of transactions for the current phase.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
 // Shared -> global copy of `bytes` (multiple of 16, both addresses 16-byte
 // aligned) in the calling thread's bulk group.
 __device__ __forceinline__ void bulk_store(void *gdst, const void *ssrc, uint32_t bytes) {

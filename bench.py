@@ -200,6 +200,20 @@ def pass_model(n):
     }
 
 
+def issued_tensor_flops_per_pair(n, fused=True):
+    """Tensor-core flops the split path issues per pair: three fp16 products per
+    mode product, M padded to 128-row tiles, K and N padded to multiples of 16."""
+    n1, n2, n3 = n
+    npad = [((x + 15) // 16) * 16 for x in n]
+    np1, np2, np3 = npad
+    f = 3 * 2 * 2 * (n1 * n2) * np3 * np3            # X3F and X3I: rows = positions
+    if fused:
+        f += n3 * 3 * 2 * 128 * (2 * np2 * np2 + 2 * np1 * np1)   # slab: M1, M4 (x2) and M2, M3 (x1)
+    else:
+        f += 3 * 2 * 2 * (n3 * n1) * np2 * np2 + 3 * 2 * 2 * (n3 * n2) * np1 * np1
+    return float(f)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -288,6 +302,14 @@ def main():
                       "l2": "inputs larger than L2 (psi 453 MB float64, fp32 scratch > 1 GB per chunk)"},
            "vx_psi_ms": ms_step, "roofline": roof, "kernels": kern, "gpu_launches": gpu_launches,
            "clocks": clk}
+    n1, n2, n3 = SYS.n
+    useful = 4.0 * n1 * n2 * n3 * (n1 + n2 + n3)
+    fused = prof.get("slab", (0.0, 0))[1] > 0
+    out["flops"] = {"useful_per_pair": useful,
+                    "useful_tflops": P * useful / (ms_step / 1e3) / 1e12,
+                    "issued_tensor_tflops": P * issued_tensor_flops_per_pair(SYS.n, fused) / (ms_step / 1e3) / 1e12,
+                    "split_tensor_bound_ms": 3 * P * useful / (bf16_sus * 1e12) * 1e3,
+                    "peak_bf16_tflops": bf16, "peak_bf16_sustained_tflops": bf16_sus}
 
     if not args.no_extras:
         vx_split = vx.clone()

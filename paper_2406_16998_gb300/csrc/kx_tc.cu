@@ -563,6 +563,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const PassArgs a) 
         float prev_unscale2 = 0.f;
         bool aborted = false;
         const long long te0 = KX_CLK_NOW();
+        const unsigned rpp = (unsigned)a.rows_pp;
+        // the per-item scale of a row is fetched one tile ahead (its loads are
+        // dependent L2 round trips that would otherwise follow the MMA wait)
+        auto row_in_max = [&](int j) {
+            const long long R = (blockIdx.x + (long long)j * gridDim.x) * 128 + m;
+            return (R < a.total_rows) ? item_in_max<PASS>(a, (unsigned)R / rpp) : 0.f;
+        };
+        float in_mx_next = n_my > 0 ? row_in_max(0) : 0.f;
         for (int it = 0; it < n_my; ++it) {
             const int b = it & 1;
             // row information and the per-item scale do not depend on the MMA:
@@ -570,10 +578,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const PassArgs a) 
             const long long tile = blockIdx.x + (long long)it * gridDim.x;
             const long long R = tile * 128 + m;  // < 2^31
             const bool valid = R < a.total_rows;
-            const unsigned rpp = (unsigned)a.rows_pp;
             const long long item = valid ? (unsigned)R / rpp : 0;
             const long long local = valid ? (unsigned)R % rpp : 0;
-            const float in_mx = valid ? item_in_max<PASS>(a, item) : 0.f;
+            const float in_mx = in_mx_next;
+            if (it + 1 < n_my) in_mx_next = row_in_max(it + 1);
             float fpre[16];
             if (PASS == P_X1) {
 #pragma unroll

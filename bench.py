@@ -44,7 +44,29 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["kronx", "reference"], default="kronx")
     ap.add_argument("--no-extras", action="store_true", help="skip FP64/e2e/oracle legs (profiling runs)")
+    ap.add_argument("--profile-case", choices=["small"], default=None,
+                    help="run one apply of a small case of the same kernels (96^3, 8 orbitals) for ncu captures")
     return ap.parse_args()
+
+
+def run_profile_case():
+    """One split-precision apply at 96^3 with 8 orbitals (36 pairs): the same
+    kernels as the bench workload on inputs of about L2 size, so that an ncu
+    capture with many passes stays short."""
+    import torch
+    import paper_2406_16998_gb300 as kx
+    from paper_2406_16998_gb300 import build
+    build.build()
+    case = workloads.System(n=(96, 96, 96), h=(0.25,) * 3, bc=(workloads.DIRICHLET,) * 3,
+                            kernel=workloads.UNSCREENED, n_orb=8, n_centres=4, seed=5, name="profile-small")
+    psi = torch.from_numpy(np.ascontiguousarray(workloads.make_orbitals(case).T)).cuda()
+    plan = kx.Plan.for_system(case, precision=kx.KX_F16X3)
+    vx, ex = kx.kx_vx_apply(plan, psi)
+    torch.cuda.synchronize()
+    status = plan.status()
+    print(json.dumps({"profile_case": "small", "e_x": ex.item(), "status": status}), flush=True)
+    if status != kx.KX_OK:
+        raise SystemExit(1)
 
 
 def peaks():
@@ -216,6 +238,8 @@ def issued_tensor_flops_per_pair(n, fused=True):
 
 def main():
     args = parse()
+    if args.profile_case:
+        return run_profile_case()
     if args.impl == "reference":
         return run_reference(args)
     import torch

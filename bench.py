@@ -222,6 +222,31 @@ def pass_model(n):
     }
 
 
+# DRAM bytes per unit of a kernel, from the ncu summaries under profiles/: a
+# line "traffic: <kernel> <bytes per unit> <unit> sha256=<hash of the kernel
+# source the capture was taken with>".  The figure is used only while the
+# source still has that hash; otherwise the traffic is reported as null.
+TRAFFIC_SOURCES = {"slab": ("profiles/tc_slab_kernel_96cube_8orb_full.md", "paper_2406_16998_gb300/csrc/kx_tc.cu")}
+
+
+def measured_traffic(kind, units_per_launch):
+    import hashlib
+    if kind not in TRAFFIC_SOURCES:
+        return None, "no ncu capture for this kernel"
+    summary, source = (os.path.join(ROOT, x) for x in TRAFFIC_SOURCES[kind])
+    try:
+        sha = hashlib.sha256(open(source, "rb").read()).hexdigest()
+        for line in open(summary):
+            f = line.split()
+            if len(f) >= 5 and f[0] == "traffic:" and f[1] == kind:
+                if f[4] != "sha256=" + sha:
+                    return None, "kernel source changed since the ncu capture"
+                return float(f[2]) * units_per_launch, f"ncu dram__bytes_read+write per {f[3]} x units per launch"
+    except OSError:
+        pass
+    return None, "no ncu capture for this kernel"
+
+
 def issued_tensor_flops_per_pair(n, fused=True):
     """Tensor-core flops the split path issues per pair: three fp16 products per
     mode product, M padded to 128-row tiles, K and N padded to multiples of 16."""
@@ -312,6 +337,7 @@ def main():
         roof = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
                 "traffic": None, "kernel": dom,
                 "peak_source": f"{peak_src} bf16_tflops / 3 (three fp16 products per useful product)"}
+    roof["traffic"], roof["traffic_source"] = measured_traffic(dom, SYS.n[2] * items_per_launch)
     roof["avg_launch_ms"] = avg_ms
     roof["items_per_launch"] = items_per_launch
     kern = {k: {"ms_total": v[0], "launches": v[1], "share": v[0] / max(1e-9, sum(x[0] for x in prof.values()))}

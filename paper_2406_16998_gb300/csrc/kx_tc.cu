@@ -20,9 +20,10 @@
 // accumulators, one thread per four grid points, group by group.
 //
 // Each pass kernel is persistent (one CTA per SM) and warp-specialised:
-//   warps 0-3   epilogue (TMEM lane quadrant = warp; one tile row per thread)
-//   warps 4-11  producers: global fp32 -> scale -> fp16 hi/lo -> shared stage
-//   warp 12     TMEM allocation and MMA issue (one thread)
+//   warps 0-7   epilogue (TMEM lane quadrant = warp % 4, one tile row per
+//               thread; warps 0-3 and 4-7 take alternate column blocks)
+//   warps 8-15  producers: global fp32 -> scale -> fp16 hi/lo -> shared stage
+//   warp 16     TMEM allocation and MMA issue (one thread)
 // with an S-deep ring of shared A stages and two TMEM accumulator slots, so
 // loads, MMAs and stores of consecutive tiles overlap.
 #include "kx_internal.h"
@@ -38,7 +39,7 @@ namespace {
 
 enum PassKind { P_X3F = 0, P_X2F = 1, P_X1 = 2, P_X2I = 3, P_X3I = 4 };
 
-constexpr int kEpiWarps = 4;
+constexpr int kEpiWarps = 8;   // two per TMEM lane quadrant, alternate 16/32-column blocks
 constexpr int kProdWarps = 8;
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kProdThreads = 32 * kProdWarps;
@@ -271,9 +272,9 @@ __device__ __forceinline__ void produce_tile(const PassArgs &a, const SrcDesc &d
         if (a.rhs_mode)
             produce_tile_u<PASS, 6, false>(a, d, Ahi, Alo, ptid);
         else
-            produce_tile_u<PASS, 6, true>(a, d, Ahi, Alo, ptid);
+            produce_tile_u<PASS, 4, true>(a, d, Ahi, Alo, ptid);
     } else {
-        produce_tile_u<PASS, 12, false>(a, d, Ahi, Alo, ptid);
+        produce_tile_u<PASS, 8, false>(a, d, Ahi, Alo, ptid);
     }
 }
 
@@ -386,7 +387,7 @@ struct Bars {
 
 // X1 epilogue, inverse half of tile j: wait for its inverse MMA, unscale and
 // store the row (float4 per 4 columns), track the maximum, release the slot.
-__device__ __forceinline__ bool x1_inverse_half(const PassArgs &a, Bars &bars, uint32_t tmem, int q, int m, int j,
+__device__ __forceinline__ bool x1_inverse_half(const PassArgs &a, Bars &bars, uint32_t tmem, int q, int hcol, int j,
                                                 int np, bool two_acc, bool valid, long long item, long long local,
                                                 float unscale2, volatile int *abort) {
     const int b = j & 1;
@@ -396,7 +397,7 @@ __device__ __forceinline__ bool x1_inverse_half(const PassArgs &a, Bars &bars, u
     const uint32_t tb = ta + (uint32_t)np;
     float my_max = 0.f;
     float *orow = a.out + item * a.N + local * a.n1;
-    for (int c = 0; c < (np >> 4); ++c) {
+    for (int c = hcol; c < (np >> 4); c += 2) {
         float v[16], vb[16];
         ptx::tmem_ld16x2(ta + 16 * c, tb + 16 * c, v, vb);
 #pragma unroll
@@ -416,7 +417,6 @@ __device__ __forceinline__ bool x1_inverse_half(const PassArgs &a, Bars &bars, u
     track_max(a.out_max, item, my_max, valid);
     ptx::tc_fence_before();
     ptx::mbar_arrive(&bars.tempty[b]);
-    (void)m;
     return true;
 }
 
@@ -554,7 +554,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const PassArgs a) 
         KX_CLK_ADD(0, tp0);
     } else {
         // ------------------------------------------------------------ epilogue
-        const int q = warp & 3;
+        const int q = warp & 3, hcol = warp >> 2;  // lane quadrant, column half
         const int m = 32 * q + lane;  // TMEM lane == tile row of this thread
         const int nch = np >> 4;      // 16-column chunks
         double e_acc = 0.0;
@@ -586,8 +586,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const PassArgs a) 
             if (PASS == P_X1) {
 #pragma unroll
                 for (int h2 = 0; h2 < 2; ++h2) {
-                    if (valid && 8 * h2 < a.nc) {
-                        ld8(a.f32 + local * a.n1 + 8 * h2, fpre + 8 * h2);
+                    if (valid && 16 * hcol + 8 * h2 < a.nc) {
+                        ld8(a.f32 + local * a.n1 + 16 * hcol + 8 * h2, fpre + 8 * h2);
                     } else {
 #pragma unroll
                         for (int k = 0; k < 8; ++k) fpre[8 * h2 + k] = 0.f;
@@ -616,7 +616,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const PassArgs a) 
                 }
                 uint8_t *midh = stage0 + (it % S) * stage_bytes;
                 float e_row = 0.f;
-                for (int c = 0; c < nch; ++c) {
+                for (int c = hcol; c < nch; c += 2) {
                     float fk[16];
 #pragma unroll
                     for (int k = 0; k < 16; ++k) fk[k] = fpre[k];
@@ -624,8 +624,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const PassArgs a) 
                     // (nc is a multiple of 8: each 8-column half is either in or out)
 #pragma unroll
                     for (int h2 = 0; h2 < 2; ++h2) {
-                        if (valid && 16 * (c + 1) + 8 * h2 < a.nc) {
-                            ld8(a.f32 + local * a.n1 + 16 * (c + 1) + 8 * h2, fpre + 8 * h2);
+                        if (valid && 16 * (c + 2) + 8 * h2 < a.nc) {
+                            ld8(a.f32 + local * a.n1 + 16 * (c + 2) + 8 * h2, fpre + 8 * h2);
                         } else {
 #pragma unroll
                             for (int k = 0; k < 8; ++k) fpre[8 * h2 + k] = 0.f;
@@ -659,7 +659,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const PassArgs a) 
                     tw = KX_CLK_NOW();
                     // inverse half of the previous tile (its MMA ran while this tile's forward half was processed)
                     if (it >= 1) {
-                        if (!x1_inverse_half(a, bars, tmem, q, m, it - 1, np, two_acc, prev_valid, prev_item,
+                        if (!x1_inverse_half(a, bars, tmem, q, hcol, it - 1, np, two_acc, prev_valid, prev_item,
                                              prev_local, prev_unscale2, &s_abort))
                             break;
                     }
@@ -685,7 +685,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const PassArgs a) 
                         obase = item * a.N + k3 * n12 + x1;
                     }
                 }
-                for (int cb = 0; cb < np; cb += 32) {
+                for (int cb = 32 * hcol; cb < np; cb += 64) {
                     float v[32], vb[32];
                     const long long tl = KX_CLK_NOW();
                     if (cb + 32 <= np) {
@@ -717,7 +717,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const PassArgs a) 
         }
         KX_CLK_ADD(8, te0);
         if (PASS == P_X1 && with_inv && n_my >= 1 && !s_abort)
-            aborted = !x1_inverse_half(a, bars, tmem, q, m, n_my - 1, np, two_acc, prev_valid, prev_item, prev_local,
+            aborted = !x1_inverse_half(a, bars, tmem, q, hcol, n_my - 1, np, two_acc, prev_valid, prev_item, prev_local,
                                        prev_unscale2, &s_abort);
         (void)aborted;
         if (a.e_partial != nullptr) {

@@ -159,23 +159,31 @@ def max_over_ranks(x, world):
 
 
 def cpu_baseline(psi, budget_s=12.0):
-    """The FP64 oracle as it stands, on a bounded sample of the workload's pairs."""
+    """The FP64 oracle as it stands, on a bounded sample of the workload's pairs
+    (the first pairs of the library's pair list, so that the same partial sums
+    can be compared with the split path's).  Returns the timing line and the
+    oracle's partial (Vx psi, E_x) over those pairs."""
     import oracle
+    from paper_2406_16998_gb300 import shard
     op = oracle.Plan(SYS.n, SYS.h, SYS.bc, SYS.kernel, SYS.omega)
     n_orb = psi.shape[1]
-    pairs = oracle.pair_list(n_orb, ordered=False)
+    pairs = shard.pair_list(n_orb)
     t0 = time.perf_counter()
     done = 0
+    vx_sum, ex_sum = None, 0.0
     while done < len(pairs):
         chunk = pairs[done:done + 4]
-        oracle.vx_apply(op, psi, pairs=chunk)
+        vx, ex = oracle.vx_apply(op, psi, pairs=chunk)
+        vx_sum = vx if vx_sum is None else vx_sum + vx
+        ex_sum += ex
         done += len(chunk)
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    return {"value": done / dt, "unit": UNIT, "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+    line = {"value": done / dt, "unit": UNIT, "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
             "sample": f"first {done} of {len(pairs)} symmetric pairs of the workload (pair product, f(L) by "
                       f"mode products, both accumulations), {dt:.1f} s of NumPy FP64"}
+    return line, done, vx_sum, ex_sum
 
 
 def run_reference(args):
@@ -440,7 +448,15 @@ def main():
         out["e2e"] = {"value": P * k_e2e / dt, "unit": UNIT, "h2d_bytes_per_step": psi_pin.numel() * 8,
                       "d2h_bytes_per_step": vx_pin.numel() * 8 + 8, "ms_per_step": 1e3 * dt / k_e2e}
         out["other_workloads"] = other_workloads(kx, torch, stream)
-        out["cpu_baseline"] = cpu_baseline(psi_h)
+        line, done, vx_ref, ex_ref = cpu_baseline(psi_h)
+        out["cpu_baseline"] = line
+        # the split path over the same first pairs of the list, against the oracle
+        vx_part, ex_part = kx.kx_vx_apply_pairs(plan, psi, 0, done)
+        vx_part = vx_part.cpu().numpy().T
+        out["error"]["vs_oracle_sampled"] = {
+            "pairs": done,
+            "vx_psi_maxrel": float(np.max(np.abs(vx_part - vx_ref)) / np.max(np.abs(vx_ref))),
+            "e_x_rel": abs(ex_part.item() - ex_ref) / abs(ex_ref)}
     print(json.dumps(out), flush=True)
     barrier(world)
 

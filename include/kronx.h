@@ -171,8 +171,11 @@ int kx_vx_apply_pairs(kx_plan *plan, int n_orb, const double *psi, const double 
 
 /* kx_vx_apply_host — kx_vx_apply on HOST buffers (pinned memory recommended):
  * copies psi (and occ) to library-owned device buffers, runs the apply and
- * copies vx_psi and e_x back, all queued on `stream`; returns after the stream
- * has finished.  psi, occ (nullable), vx_psi, e_x (nullable) are host pointers. */
+ * copies vx_psi and e_x back; returns after all of it has finished.  With
+ * KX_F16X3 the rows of vx_psi whose pairs are all done are copied back on a
+ * plan-owned stream while the remaining pairs compute (the work starts on
+ * `stream` and ends joined to it).  psi, occ (nullable), vx_psi, e_x
+ * (nullable) are host pointers.  Calls on one plan must not overlap. */
 int kx_vx_apply_host(kx_plan *plan, int n_orb, const double *psi, const double *occ,
                      double *vx_psi, double *e_x, kx_stream stream);
 

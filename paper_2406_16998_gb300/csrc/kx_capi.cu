@@ -96,6 +96,9 @@ int ensure_pairs(kx_plan *p, int n_orb, cudaStream_t s, long long begin, long lo
         }
     }
     first.push_back((int)(pairs.size() / 2));
+    std::vector<int> last(n_orb, -1);
+    for (size_t gi = 0; gi < groups.size(); ++gi)
+        for (int t = 0; t < groups[gi].n_slots; ++t) last[groups[gi].orb[t]] = (int)gi;
     const size_t P = pairs.size() / 2;
     if (P > p->pairs_cap) {
         cudaFree(p->d_pairs);
@@ -121,6 +124,7 @@ int ensure_pairs(kx_plan *p, int n_orb, cudaStream_t s, long long begin, long lo
         KX_CUDA_TRY(cudaMemcpy(p->d_groups, groups.data(), sizeof(Group) * groups.size(), cudaMemcpyHostToDevice));
     }
     p->h_group_first = first;
+    p->h_orb_last = last;
     p->ws_norb = n_orb;
     p->pr_begin = begin;
     p->pr_end = end;
@@ -371,15 +375,62 @@ int kx_vx_apply_host(kx_plan *plan, int n_orb, const double *psi, const double *
         if (e != cudaSuccess) return cuda_error(e, "kx_vx_apply_host staging cudaMalloc");
         plan->ws_host.bytes = need;
     }
+    if (!plan->copy_stream) KX_CUDA_TRY(cudaStreamCreateWithFlags(&plan->copy_stream, cudaStreamNonBlocking));
     double *d_psi = (double *)plan->ws_host.ptr;
     double *d_vx = d_psi + (size_t)n_orb * plan->N;
     double *d_ex = d_vx + (size_t)n_orb * plan->N;
     double *d_occ = occ ? d_ex + 1 : nullptr;
     KX_CUDA_TRY(cudaMemcpyAsync(d_psi, psi, vec, cudaMemcpyHostToDevice, s));
     if (occ) KX_CUDA_TRY(cudaMemcpyAsync(d_occ, occ, sizeof(double) * n_orb, cudaMemcpyHostToDevice, s));
+    // rows of Vx psi that the split path reports final are copied back on the
+    // plan's copy stream while the later chunks compute
+    struct Ctx {
+        kx_plan *p;
+        double *host;
+        const double *dev;
+        size_t N;
+        int copied, events, rc;
+    } ctx{plan, vx_psi, d_vx, plan->N, 0, 0, KX_OK};
+    plan->final_hook.ctx = &ctx;
+    plan->final_hook.fn = [](void *c, int o0, int o1, cudaStream_t st) {
+        Ctx *x = static_cast<Ctx *>(c);
+        if (x->rc || o1 <= o0) return;
+        kx_plan *p = x->p;
+        if ((size_t)x->events == p->copy_events.size()) {
+            cudaEvent_t ev;
+            cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (e != cudaSuccess) {
+                x->rc = cuda_error(e, "kx_vx_apply_host copy event");
+                return;
+            }
+            p->copy_events.push_back(ev);
+        }
+        cudaEvent_t ev = p->copy_events[x->events++];
+        cudaError_t e = cudaEventRecord(ev, st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(p->copy_stream, ev, 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(x->host + (size_t)o0 * x->N, x->dev + (size_t)o0 * x->N,
+                                sizeof(double) * (size_t)(o1 - o0) * x->N, cudaMemcpyDeviceToHost, p->copy_stream);
+        if (e != cudaSuccess) x->rc = cuda_error(e, "kx_vx_apply_host row copy");
+        x->copied = o1;
+    };
     int rc = dispatch_vx(plan, n_orb, d_psi, d_occ, d_vx, d_ex, false, s);
-    if (rc) return rc;
-    KX_CUDA_TRY(cudaMemcpyAsync(vx_psi, d_vx, vec, cudaMemcpyDeviceToHost, s));
+    plan->final_hook = FinalHook{};
+    if (!rc) rc = ctx.rc;
+    // the copy stream's work joins the caller's stream before the rest is read
+    cudaEvent_t done;
+    KX_CUDA_TRY(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+    cudaError_t e = cudaEventRecord(done, plan->copy_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, done, 0);
+    cudaEventDestroy(done);
+    if (e != cudaSuccess) return cuda_error(e, "kx_vx_apply_host copy join");
+    if (rc) {
+        cudaStreamSynchronize(s);
+        return rc;
+    }
+    if (ctx.copied < n_orb)
+        KX_CUDA_TRY(cudaMemcpyAsync(vx_psi + (size_t)ctx.copied * plan->N, d_vx + (size_t)ctx.copied * plan->N,
+                                    sizeof(double) * (size_t)(n_orb - ctx.copied) * plan->N, cudaMemcpyDeviceToHost, s));
     if (e_x) KX_CUDA_TRY(cudaMemcpyAsync(e_x, d_ex, sizeof(double), cudaMemcpyDeviceToHost, s));
     KX_CUDA_TRY(cudaStreamSynchronize(s));
     return KX_OK;

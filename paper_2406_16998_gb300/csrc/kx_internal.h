@@ -71,6 +71,15 @@ struct Workspace {
 
 }  // namespace kx
 
+namespace kx {
+// Called by the split path when rows [o0, o1) of the caller's Vx psi output are
+// final (written on stream s).
+struct FinalHook {
+    void (*fn)(void *ctx, int o0, int o1, cudaStream_t s) = nullptr;
+    void *ctx = nullptr;
+};
+}  // namespace kx
+
 struct kx_plan_s {
     int n[3];
     double h[3];
@@ -110,7 +119,13 @@ struct kx_plan_s {
     int *d_groups = nullptr;      // kx::Group per group
     size_t pairs_cap = 0, groups_cap = 0;
     std::vector<int> h_group_first;  // first item of each group (+ sentinel)
+    std::vector<int> h_orb_last;     // per orbital: index of the last group that touches it (-1: none)
     kx::Profiler prof;
+    // kx_vx_apply_host: told when leading rows of Vx psi are final, so that their
+    // device-to-host copies run on copy_stream while later chunks compute
+    kx::FinalHook final_hook;
+    cudaStream_t copy_stream = nullptr;
+    std::vector<cudaEvent_t> copy_events;
 };
 
 namespace kx {

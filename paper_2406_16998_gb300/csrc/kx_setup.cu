@@ -307,6 +307,10 @@ void plan_free(kx_plan *p) {
     cudaFree(p->d_pairs);
     cudaFree(p->d_item_slot);
     cudaFree(p->d_groups);
+    for (cudaEvent_t e : p->copy_events) cudaEventDestroy(e);
+    p->copy_events.clear();
+    if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
+    p->copy_stream = nullptr;
 }
 
 }  // namespace kx

@@ -1370,7 +1370,20 @@ __global__ void prep_kernel(const double *__restrict__ src, float *__restrict__ 
     if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(reinterpret_cast<int *>(vmax + v), __float_as_int(m));
 }
 
+// Vx psi = -acc over n values (n % 4 == 0; both pointers 16-byte aligned).
 __global__ void finalize_kernel(const float *__restrict__ acc, double *__restrict__ vx, long long n) {
+    const float4 *a4 = reinterpret_cast<const float4 *>(acc);
+    double2 *v2 = reinterpret_cast<double2 *>(vx);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (n >> 2);
+         e += (long long)gridDim.x * blockDim.x) {
+        const float4 x = __ldg(a4 + e);
+        v2[2 * e] = make_double2(-(double)x.x, -(double)x.y);
+        v2[2 * e + 1] = make_double2(-(double)x.z, -(double)x.w);
+    }
+}
+
+// The same for an output that is only 8-byte aligned.
+__global__ void finalize_scalar_kernel(const float *__restrict__ acc, double *__restrict__ vx, long long n) {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
         vx[e] = -(double)acc[e];
 }
@@ -1628,6 +1641,24 @@ size_t tc_workspace_bytes(const kx_plan *p, int n_vec, long chunk) {
            4096;
 }
 
+// Vx psi rows [o0, o1) = -acc, then the plan's final-rows hook (if set).
+int finalize_rows(kx_plan *p, const float *acc, double *vx, int o0, int o1, cudaStream_t s) {
+    if (o1 <= o0) return KX_OK;
+    const long long n = (long long)(o1 - o0) * (long long)p->N;
+    const size_t off = (size_t)o0 * p->N;
+    if (int rc = prof_begin(p, PK_FINAL, s)) return rc;
+    if ((reinterpret_cast<uintptr_t>(vx + off) & 15) == 0)
+        finalize_kernel<<<(unsigned)std::min<long long>((n / 4 + 255) / 256, 8LL * p->num_sms), 256, 0, s>>>(
+            acc + off, vx + off, n);
+    else
+        finalize_scalar_kernel<<<(unsigned)std::min<long long>((n + 255) / 256, 8LL * p->num_sms), 256, 0, s>>>(
+            acc + off, vx + off, n);
+    KX_LAUNCH_CHECK("finalize_kernel launch");
+    if (int rc = prof_end(p, s)) return rc;
+    if (p->final_hook.fn) p->final_hook.fn(p->final_hook.ctx, o0, o1, s);
+    return KX_OK;
+}
+
 int tc_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, double *vx, double *ex, bool energy_only,
           cudaStream_t s, long pair_begin, long pair_end) {
     int rc = ensure_pairs(p, n_orb, s, pair_begin, pair_end);
@@ -1656,7 +1687,7 @@ int tc_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, double *v
     const int2 *pairs = reinterpret_cast<const int2 *>(p->d_pairs);
     const float mid_bound = fmax_sqrt(p);
 
-    int g0 = 0;
+    int g0 = 0, o_fin = 0;
     while (g0 < n_groups) {
         int g1 = g0 + 1;
         while (g1 < n_groups && first[g1 + 1] - first[g0] <= chunk) ++g1;
@@ -1680,15 +1711,16 @@ int tc_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, double *v
             KX_LAUNCH_CHECK("acc_kernel launch");
             if ((rc = prof_end(p, s))) return rc;
         }
+        if (!energy_only) {
+            // rows whose last group is done are final: negate them into vx now
+            int o_done = o_fin;
+            while (o_done < n_orb && p->h_orb_last[o_done] < g1) ++o_done;
+            if ((rc = finalize_rows(p, L.acc, vx, o_fin, o_done, s))) return rc;
+            o_fin = o_done;
+        }
         g0 = g1;
     }
-    if (!energy_only) {
-        const long long n = (long long)n_orb * N;
-        if ((rc = prof_begin(p, PK_FINAL, s))) return rc;
-        finalize_kernel<<<(unsigned)std::min<long long>((n + 255) / 256, 8LL * p->num_sms), 256, 0, s>>>(L.acc, vx, n);
-        KX_LAUNCH_CHECK("finalize_kernel launch");
-        if ((rc = prof_end(p, s))) return rc;
-    }
+    if (!energy_only) return finalize_rows(p, L.acc, vx, o_fin, n_orb, s);
     return KX_OK;
 }
 

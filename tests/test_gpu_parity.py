@@ -343,3 +343,46 @@ def test_pair_ranges_sum_to_full_apply(kx, prec):
     tol = 1e-12 if prec == 0 else 1e-6
     assert relmax(acc.cpu().numpy(), full.cpu().numpy()) < tol
     assert abs(e_acc - e_full.item()) < tol * abs(e_full.item())
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_host_buffers_match_device_path(kx, prec, monkeypatch):
+    """kx_vx_apply_host (host buffers; rows of Vx psi copied back chunk by chunk
+    as they become final) gives the device path's result bit for bit, over
+    several chunks of the pair list."""
+    monkeypatch.setenv("KX_CHUNK_PAIRS", "16")
+    n, h, bc = (24, 16, 32), (0.4, 0.45, 0.5), (D, P, D)
+    sysd = system(n, h, bc, S, 12, 61)
+    psi = workloads.make_orbitals(sysd)
+    plan = kx.Plan(n, h, bc, S, precision=prec)
+    psi_d = dev(psi.T)
+    vx, ex = kx.kx_vx_apply(plan, psi_d)
+    vx = vx.cpu().numpy()
+    for pinned in (False, True):
+        psi_h = torch.from_numpy(np.ascontiguousarray(psi.T))
+        if pinned:
+            psi_h = psi_h.pin_memory()
+        vx_h, ex_h = kx.kx_vx_apply_host(plan, psi_h)
+        assert plan.status() == kx.KX_OK
+        assert np.array_equal(vx_h.numpy(), vx)
+        assert ex_h == ex.item()
+
+
+def test_unaligned_output_pointer(kx):
+    """An output that is 8- but not 16-byte aligned takes the scalar final pass
+    and gives the same values."""
+    import ctypes
+    n, h, bc = (16, 24, 16), (0.5, 0.4, 0.5), (D, D, D)
+    sysd = system(n, h, bc, U, 5, 62)
+    psi = workloads.make_orbitals(sysd)
+    plan = kx.Plan(n, h, bc, U, precision=1)
+    psi_d = dev(psi.T)
+    vx, _ = kx.kx_vx_apply(plan, psi_d)
+    n_orb, N = psi_d.shape
+    buf = torch.empty(n_orb * N + 1, dtype=torch.float64, device="cuda")
+    ex = torch.empty(1, dtype=torch.float64, device="cuda")
+    rc = kx.lib().kx_vx_apply(plan.handle, n_orb, ctypes.c_void_p(psi_d.data_ptr()), None,
+                              ctypes.c_void_p(buf.data_ptr() + 8), ctypes.c_void_p(ex.data_ptr()), None)
+    torch.cuda.synchronize()
+    assert rc == kx.KX_OK
+    assert torch.equal(buf[1:].view(n_orb, N), vx)

@@ -231,19 +231,28 @@ def pass_model(n):
 
 
 # DRAM bytes per unit of a kernel, from the ncu summaries under profiles/: a
-# line "traffic: <kernel> <bytes per unit> <unit> sha256=<hash of the kernel
-# source the capture was taken with>".  The figure is used only while the
+# line "traffic: <kernel> <bytes per unit> <unit> sha256=<hash of the kernel's
+# source text when the capture was taken>".  The figure is used only while the
 # source still has that hash; otherwise the traffic is reported as null.
-TRAFFIC_SOURCES = {"slab": ("profiles/tc_slab_kernel_96cube_8orb_full.md", "paper_2406_16998_gb300/csrc/kx_tc.cu")}
+# The hash covers the kernel's own source text: from `start` up to `end`.
+TRAFFIC_SOURCES = {"slab": ("profiles/tc_slab_kernel_96cube_8orb_full.md", "paper_2406_16998_gb300/csrc/kx_tc.cu",
+                            "struct SlabArgs {", "// Accumulation of one chunk")}
+
+
+def kernel_source_hash(kind):
+    import hashlib
+    _, source, start, end = TRAFFIC_SOURCES[kind]
+    text = open(os.path.join(ROOT, source)).read()
+    a = text.index(start)
+    return hashlib.sha256(text[a:text.index(end, a)].encode()).hexdigest()
 
 
 def measured_traffic(kind, units_per_launch):
-    import hashlib
     if kind not in TRAFFIC_SOURCES:
         return None, "no ncu capture for this kernel"
-    summary, source = (os.path.join(ROOT, x) for x in TRAFFIC_SOURCES[kind])
+    summary = os.path.join(ROOT, TRAFFIC_SOURCES[kind][0])
     try:
-        sha = hashlib.sha256(open(source, "rb").read()).hexdigest()
+        sha = kernel_source_hash(kind)
         for line in open(summary):
             f = line.split()
             if len(f) >= 5 and f[0] == "traffic:" and f[1] == kind:

@@ -1388,7 +1388,7 @@ struct X3AccArgs {
     long long n_units;
 };
 
-constexpr int kX3aMaxNH = 48;  // 2 D slots + 8 group slots of NH columns fit in 512 TMEM columns; 3 x 16 columns per row
+constexpr int kX3aMaxNH = 48;  // 2 D slots + 8 group slots of NH columns fit in 512 TMEM columns
 
 // D = A_hi B_hi + A_hi B_lo + A_lo B_hi into one accumulator: A MN-major (pass
 // layout, K = np), B = V^T restricted to NH output columns (K-major).
@@ -1419,14 +1419,7 @@ __device__ __forceinline__ void issue_x3a_mma(uint32_t tmem_d, uint32_t a_hi, ui
     }
 }
 
-// Warp roles: 12 epilogue warps (lane quadrant w % 4, 16-column piece w / 4 of
-// the part), one producer group of 4 warps, the MMA warp.
-constexpr int kXEpiWarps = 12;
-constexpr int kXEpiThreads = 32 * kXEpiWarps;
-constexpr int kXMmaWarp = kXEpiWarps + 4;
-constexpr int kXThreads = 32 * (kXMmaWarp + 1);
-
-__global__ void __launch_bounds__(kXThreads, 1) tc_x3acc_kernel(const X3AccArgs x) {
+__global__ void __launch_bounds__(kThreads, 1) tc_x3acc_kernel(const X3AccArgs x) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const PassArgs &a = x.pa;
@@ -1439,11 +1432,11 @@ __global__ void __launch_bounds__(kXThreads, 1) tc_x3acc_kernel(const X3AccArgs 
     __shared__ Bars bars;
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int s_abort;
-    __shared__ SrcDesc sdesc;
-    __shared__ int s_vote;
+    __shared__ SrcDesc sdesc[kProdGroups];
+    __shared__ int s_vote[kProdGroups];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (warp == kXMmaWarp) {
+    if (warp == kMmaWarp) {
         ptx::tmem_alloc(&tmem_slot, 512);
         ptx::tmem_relinquish();
     }
@@ -1454,7 +1447,7 @@ __global__ void __launch_bounds__(kXThreads, 1) tc_x3acc_kernel(const X3AccArgs 
         }
         for (int b = 0; b < 2; ++b) {
             ptx::mbar_init(&bars.tfull[b], 1);
-            ptx::mbar_init(&bars.tempty[b], kXEpiThreads);
+            ptx::mbar_init(&bars.tempty[b], kEpiThreads);
         }
         ptx::mbar_init(&bars.drain, 1);
         ptx::fence_mbar_init();
@@ -1478,7 +1471,7 @@ __global__ void __launch_bounds__(kXThreads, 1) tc_x3acc_kernel(const X3AccArgs 
     // iteration it: unit blockIdx.x + (it / R) * gridDim.x, item it % R of the chunk
     auto unit_of = [&](int it) { return blockIdx.x + (long long)(it / R) * gridDim.x; };
 
-    if (warp == kXMmaWarp) {
+    if (warp == kMmaWarp) {
         // ------------------------------------------------------------ MMA issue
         if (lane == 0) {
             const uint32_t sVhi = ptx::smem_u32(Vhi), sVlo = ptx::smem_u32(Vlo);
@@ -1504,113 +1497,117 @@ __global__ void __launch_bounds__(kXThreads, 1) tc_x3acc_kernel(const X3AccArgs 
             }
         }
         __syncwarp();
-    } else if (warp >= kXEpiWarps) {
-        // ------------------------------------------------------------ producer group (the X3I loader)
-        const int gtid = tid - kXEpiThreads;
-        for (int it = 0; it < n_my; ++it) {
+    } else if (warp >= kEpiWarps) {
+        // ------------------------------------------------------------ producers (the X3I loader)
+        const int ptid = tid - kEpiThreads;
+        const int grp = ptid / kGroupThreads, gtid = ptid % kGroupThreads;
+        for (int it = grp; it < n_my; it += kProdGroups) {
             const int s = it % S;
             bool ok = it < S || wait_bar(&bars.empty[s], (uint32_t)(((it / S) - 1) & 1), a, &s_abort);
-            ok = producers_agree(ok, &s_vote, gtid, 2);
+            ok = producers_agree(ok, &s_vote[grp], gtid, 2 + 2 * grp);
             if (!ok) break;
             const long long u = unit_of(it);
             const long long tile = (long long)(it % R) * x.n_ptiles + u / x.H;  // rows of item it % R
-            make_desc<P_X3I>(a, tile, sdesc, gtid);
-            ptx::named_bar(3, kGroupThreads);
+            make_desc<P_X3I>(a, tile, sdesc[grp], gtid);
+            ptx::named_bar(3 + 2 * grp, kGroupThreads);
             uint8_t *Ahi = stage0 + s * stage_bytes;
-            produce_tile<P_X3I>(a, sdesc, Ahi, Ahi + half_bytes, gtid);
+            produce_tile<P_X3I>(a, sdesc[grp], Ahi, Ahi + half_bytes, gtid);
             ptx::fence_proxy_async_smem();
             ptx::mbar_arrive(&bars.full[s]);
         }
     } else {
         // ------------------------------------------------------------ epilogue
         // warp w: TMEM lane quadrant w % 4 (one tile row = one position per
-        // thread), 16 columns [16 pc, 16 pc + 16) of the part, pc = w / 4.
-        const int q = warp & 3, pc = warp >> 2;
+        // thread), columns [hc*NH/2, (hc+1)*NH/2) of the part, hc = w / 4.
+        const int q = warp & 3, hc = warp >> 2;
         const int m = 32 * q + lane;
-        const int c0 = 16 * pc;
-        const bool live = c0 < NH;  // warp-uniform
+        const int cw = NH >> 1;  // 8, 16 or 24 columns, multiples of 8
+        const int c0 = hc * cw;
         const uint32_t trow = (uint32_t)(32 * q) << 16;
         const uint32_t tslot0 = tmem + trow + (uint32_t)(2 * NH + c0);  // group slot s at + s * NH
-        float zero16[16];
-#pragma unroll
-        for (int e = 0; e < 16; ++e) zero16[e] = 0.f;
-        if (live) {
-            for (int sl = 0; sl < kGroupSlots; ++sl) ptx::tmem_st16(tslot0 + (uint32_t)(sl * NH), zero16);
-            ptx::tmem_wait_st();
-        }
+        const float zero8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int sl = 0; sl < kGroupSlots; ++sl)
+            for (int c = 0; c < cw; c += 8) ptx::tmem_st8(tslot0 + (uint32_t)(sl * NH + c), zero8);
+        ptx::tmem_wait_st();
         int gi = x.f.g0;
         Group G = x.f.groups[gi];
         long long p = 0, xb = 0;  // position in the plane, first x3 of this thread's columns
-        int cv = 0;               // of the 16 columns, those with x3 < n3
         for (int it = 0; it < n_my; ++it) {
             const int b = it & 1, k = it % R;
             if (k == 0) {  // a new unit starts at the chunk's first group
                 const long long u = unit_of(it);
                 p = (u / x.H) * 128 + m;
                 xb = (u % x.H) * NH + c0;
-                cv = (int)(xb + 16 <= a.n3 ? 16 : (xb < a.n3 ? a.n3 - xb : 0));
                 gi = x.f.g0;
                 G = x.f.groups[gi];
             }
             const int item = x.f.item0 + k;
             while (item >= G.first_item + G.n_items) G = x.f.groups[++gi];
-            float pi[16], pj[16];
-            float gi_ = 1.f, gj_ = 1.f;
-            int2 sl = make_int2(0, 0);
-            if (live) {
-                const int2 ij = a.pairs[k];
-                sl = x.f.item_slot[item];
-                if (x.f.occ) {
-                    gi_ = (float)x.f.occ[ij.x];
-                    gj_ = (float)x.f.occ[ij.y];
-                }
-                // orbital values at this row's position and columns, fetched before the MMA wait
-                const float *ppi = x.f.psi32 + (long long)ij.x * a.N + xb * n12 + p;
-                const float *ppj = x.f.psi32 + (long long)ij.y * a.N + xb * n12 + p;
+            const int2 ij = a.pairs[k];
+            const int2 sl = x.f.item_slot[item];
+            const float gi_ = x.f.occ ? (float)x.f.occ[ij.x] : 1.f;
+            const float gj_ = x.f.occ ? (float)x.f.occ[ij.y] : 1.f;
+            // orbital values at this row's position and columns, fetched before the MMA wait
+            float pi[kX3aMaxNH / 2], pj[kX3aMaxNH / 2];
+            const float *ppi = x.f.psi32 + (long long)ij.x * a.N + xb * n12 + p;
+            const float *ppj = x.f.psi32 + (long long)ij.y * a.N + xb * n12 + p;
+            const int cv = (int)(xb + cw <= a.n3 ? cw : (xb < a.n3 ? a.n3 - xb : 0));  // columns with x3 < n3
 #pragma unroll
-                for (int c = 0; c < 16; ++c) {
-                    pi[c] = (c < cv) ? __ldg(ppi + c * n12) : 0.f;
-                    pj[c] = (c < cv) ? __ldg(ppj + c * n12) : 0.f;
-                }
+            for (int c = 0; c < kX3aMaxNH / 2; ++c) {
+                pi[c] = (c < cv) ? __ldg(ppi + c * n12) : 0.f;
+                pj[c] = (c < cv) ? __ldg(ppj + c * n12) : 0.f;
             }
             const float unscale = ldexpf(1.f, -(scale_exp(a.in_max[k]) + kVScaleExp));
             if (!wait_bar_warp(&bars.tfull[b], (uint32_t)((it >> 1) & 1), a, &s_abort)) break;
             ptx::tc_fence_after();
-            float phi[16];
-            if (live) ptx::tmem_ld16(tmem + trow + (uint32_t)(b * NH + c0), phi);
+            float phi[kX3aMaxNH / 2];
+            const uint32_t td = tmem + trow + (uint32_t)(b * NH + c0);
+#pragma unroll
+            for (int c = 0; c < kX3aMaxNH / 2; c += 8)
+                if (c < cw) ptx::tmem_ld8(td + c, phi + c);
             ptx::tc_fence_before();
             ptx::mbar_arrive(&bars.tempty[b]);  // the D slot is free for the next MMA
-            if (!live) continue;
+#pragma unroll
+            for (int c = 0; c < kX3aMaxNH / 2; ++c) phi[c] *= unscale;
             // slot(i) += g_j psi_j phi; slot(j) += g_i psi_i phi (once when i == j)
-            {
-                float v[16];
-                const uint32_t tx = tslot0 + (uint32_t)(sl.x * NH);
-                ptx::tmem_ld16(tx, v);
 #pragma unroll
-                for (int e = 0; e < 16; ++e) v[e] = fmaf(gj_ * pj[e], phi[e] * unscale, v[e]);
-                ptx::tmem_st16(tx, v);
-            }
-            if (sl.y != sl.x) {
-                float v[16];
-                const uint32_t ty = tslot0 + (uint32_t)(sl.y * NH);
-                ptx::tmem_ld16(ty, v);
+            for (int c = 0; c < kX3aMaxNH / 2; c += 8) {
+                if (c >= cw) break;
+                float v[8];
+                const uint32_t tx = tslot0 + (uint32_t)(sl.x * NH + c);
+                ptx::tmem_ld8(tx, v);
 #pragma unroll
-                for (int e = 0; e < 16; ++e) v[e] = fmaf(gi_ * pi[e], phi[e] * unscale, v[e]);
-                ptx::tmem_st16(ty, v);
+                for (int e = 0; e < 8; ++e) v[e] = fmaf(gj_ * pj[c + e], phi[c + e], v[e]);
+                ptx::tmem_st8(tx, v);
             }
             ptx::tmem_wait_st();
+            if (sl.y != sl.x) {
+#pragma unroll
+                for (int c = 0; c < kX3aMaxNH / 2; c += 8) {
+                    if (c >= cw) break;
+                    float v[8];
+                    const uint32_t ty = tslot0 + (uint32_t)(sl.y * NH + c);
+                    ptx::tmem_ld8(ty, v);
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) v[e] = fmaf(gi_ * pi[c + e], phi[c + e], v[e]);
+                    ptx::tmem_st8(ty, v);
+                }
+                ptx::tmem_wait_st();
+            }
             if (item == G.first_item + G.n_items - 1) {
                 // the group is complete: add every slot into its orbital's accumulator and clear it
                 for (int s2 = 0; s2 < G.n_slots; ++s2) {
                     float *dst = x.f.acc + (long long)G.orb[s2] * a.N + xb * n12 + p;
-                    float v[16], o[16];
-                    ptx::tmem_ld16(tslot0 + (uint32_t)(s2 * NH), v);
+                    for (int c = 0; c < cw; c += 8) {
+                        float v[8], o[8];
+                        ptx::tmem_ld8(tslot0 + (uint32_t)(s2 * NH + c), v);
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) o[e] = (e < cv) ? dst[e * n12] : 0.f;
+                        for (int e = 0; e < 8; ++e) o[e] = (c + e < cv) ? dst[(c + e) * n12] : 0.f;
 #pragma unroll
-                    for (int e = 0; e < 16; ++e)
-                        if (e < cv) dst[e * n12] = o[e] + v[e];
-                    ptx::tmem_st16(tslot0 + (uint32_t)(s2 * NH), zero16);
+                        for (int e = 0; e < 8; ++e)
+                            if (c + e < cv) dst[(c + e) * n12] = o[e] + v[e];
+                        ptx::tmem_st8(tslot0 + (uint32_t)(s2 * NH + c), zero8);
+                    }
                 }
                 ptx::tmem_wait_st();
             }
@@ -1618,7 +1615,7 @@ __global__ void __launch_bounds__(kXThreads, 1) tc_x3acc_kernel(const X3AccArgs 
     }
     ptx::tc_fence_before();
     __syncthreads();
-    if (warp == kXMmaWarp) {
+    if (warp == kMmaWarp) {
         ptx::tc_fence_after();
         ptx::tmem_dealloc(tmem, 512);
     }
@@ -1831,7 +1828,7 @@ int launch_x3acc(kx_plan *p, PassArgs a, const X3Acc &f, long R, cudaStream_t s)
     KX_CUDA_TRY(cudaFuncSetAttribute(tc_x3acc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = (int)std::max(1LL, std::min<long long>(x.n_units, (long long)p->num_sms));
     if (int rc = prof_begin(p, PK_X3ACC, s)) return rc;
-    tc_x3acc_kernel<<<grid, kXThreads, smem, s>>>(x);
+    tc_x3acc_kernel<<<grid, kThreads, smem, s>>>(x);
     KX_LAUNCH_CHECK("tc_x3acc_kernel launch");
     return prof_end(p, s);
 }

@@ -243,9 +243,8 @@ int kx_profile(kx_plan *plan, int enable);
  * inverse and Vx psi accumulation), 6 finalize/energy sums, 7 float64 mode
  * products, 8 other float64 kernels, 9 ACE, 10 set-up, 11 accumulation of
  * g psi phi into Vx psi, 12 fused mode 2 forward + X1 + mode 2 inverse per
- * k3 slice (replaces kinds 2-4 where the operands fit in shared memory), 13
- * mode 3 inverse fused with the accumulation (replaces kinds 5 and 11 where
- * the shape allows).  Synchronises on the recorded events. */
+ * k3 slice (replaces kinds 2-4 where the operands fit in shared memory).
+ * Synchronises on the recorded events. */
 int kx_profile_read(kx_plan *plan, int n_kinds, double *ms, long long *launches);
 
 /* kx_last_error_detail — copies the last error message of the calling host

@@ -50,12 +50,11 @@ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 struct TuneParams {
     long chunk_pairs = 0;     // pairs per chunk (0 = choose from the workspace budget)
     int fuse_slab = 1;        // fuse the mode-2/mode-1 products of each k3 slice into one kernel
-    int fuse_acc = 1;         // fuse the mode-3 inverse with the accumulation where the shape allows
 };
 
 // Per-launch CUDA-event timing by kernel kind (kx_profile / kx_profile_read).
 enum ProfKind { PK_PREP = 0, PK_X3F, PK_X2F, PK_X1, PK_X2I, PK_X3I, PK_FINAL, PK_FP64_MODE, PK_FP64_OTHER,
-                PK_ACE, PK_SETUP, PK_ACC, PK_SLAB, PK_X3ACC, PK_COUNT };
+                PK_ACE, PK_SETUP, PK_ACC, PK_SLAB, PK_COUNT };
 struct Profiler {
     bool on = false;
     std::vector<cudaEvent_t> pool;       // reusable events

@@ -1356,271 +1356,6 @@ __global__ void __launch_bounds__(kAccThreads) acc_kernel(const float *__restric
     }
 }
 
-// ---------------------------------------------------------------------------
-// Fused mode-3 inverse and accumulation (replaces X3I + acc_kernel where the
-// shapes allow).  A unit is one tile of 128 in-plane positions times one
-// part of NH x3 values (H parts of the padded n3); a CTA takes its units one
-// after the other and, for each, every item of the chunk in order:
-//   MMA   phi[pos][x3 in part] = sum_k3 T1[k3][pos] V3[x3][k3]   (3 fp16
-//         products, one fp32 TMEM accumulator, two TMEM slots)
-//   epi   slot(i) += g_j psi_j phi,  slot(j) += g_i psi_i phi   in TMEM
-//         accumulators, one per orbital slot of the item's group (<= 8);
-//         after the group's last item every slot is added into the fp32
-//         accumulator of its orbital in global memory and cleared.
-// phi never goes to global memory.  Each accumulator element belongs to one
-// unit and the items are visited in a fixed order, so the result is
-// deterministic.
-// ---------------------------------------------------------------------------
-struct X3Acc {
-    const Group *groups;
-    int g0, g1;
-    int item0;                // first item of the chunk in the pair list
-    const int2 *item_slot;    // absolute item -> (slot of i, slot of j)
-    const float *psi32;
-    const double *occ;
-    float *acc;
-};
-
-struct X3AccArgs {
-    PassArgs pa;              // the X3I pass's fields (in = mode-3 inverse input, in_max, V3, sizes)
-    X3Acc f;
-    int H, NH, n_ptiles, R;   // parts of x3, columns per part, position tiles per plane, items
-    long long n_units;
-};
-
-constexpr int kX3aMaxNH = 48;  // 2 D slots + 8 group slots of NH columns fit in 512 TMEM columns
-
-// D = A_hi B_hi + A_hi B_lo + A_lo B_hi into one accumulator: A MN-major (pass
-// layout, K = np), B = V^T restricted to NH output columns (K-major).
-__device__ __forceinline__ void issue_x3a_mma(uint32_t tmem_d, uint32_t a_hi, uint32_t a_lo, uint32_t v_hi,
-                                              uint32_t v_lo, int np, int nh) {
-    const uint32_t idesc = ptx::idesc_f16(128, nh, 1, 0);
-    const uint32_t a_lbo = 16 * kCoreStride, a_sbo = kCoreStride, a_step = 2 * a_lbo;
-    const uint32_t b_lbo = 128u, b_sbo = (uint32_t)(np * 16), b_step = 256u;
-    const int nks = np >> 4;
-    const uint64_t ah0 = ptx::sdesc(a_hi, a_lbo, a_sbo), al0 = ptx::sdesc(a_lo, a_lbo, a_sbo);
-    const uint64_t bh0 = ptx::sdesc(v_hi, b_lbo, b_sbo), bl0 = ptx::sdesc(v_lo, b_lbo, b_sbo);
-    const uint64_t a_inc = a_step >> 4, b_inc = b_step >> 4;
-    uint64_t ah = ah0, al = al0, bh = bh0, bl = bl0;
-    for (int ks = 0; ks < nks; ++ks) {
-        ptx::mma_f16(tmem_d, ah, bl, idesc, ks > 0 ? 1u : 0u);
-        ptx::mma_f16(tmem_d, al, bh, idesc, 1u);
-        ah += a_inc;
-        al += a_inc;
-        bh += b_inc;
-        bl += b_inc;
-    }
-    ah = ah0;
-    bh = bh0;
-    for (int ks = 0; ks < nks; ++ks) {
-        ptx::mma_f16(tmem_d, ah, bh, idesc, 1u);
-        ah += a_inc;
-        bh += b_inc;
-    }
-}
-
-__global__ void __launch_bounds__(kThreads, 1) tc_x3acc_kernel(const X3AccArgs x) {
-    extern __shared__ uint8_t smem_raw[];
-    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const PassArgs &a = x.pa;
-    const int np = a.np, S = a.stages, NH = x.NH;
-    const size_t half_bytes = a_half_bytes(np);
-    const size_t stage_bytes = 2 * half_bytes;
-    uint8_t *Vhi = smem;
-    uint8_t *Vlo = Vhi + np * np * 2;
-    uint8_t *stage0 = Vlo + np * np * 2;
-    __shared__ Bars bars;
-    __shared__ uint32_t tmem_slot;
-    __shared__ volatile int s_abort;
-    __shared__ SrcDesc sdesc[kProdGroups];
-    __shared__ int s_vote[kProdGroups];
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (warp == kMmaWarp) {
-        ptx::tmem_alloc(&tmem_slot, 512);
-        ptx::tmem_relinquish();
-    }
-    if (tid == 0) {
-        for (int s = 0; s < S; ++s) {
-            ptx::mbar_init(&bars.full[s], kGroupThreads);
-            ptx::mbar_init(&bars.empty[s], 1);
-        }
-        for (int b = 0; b < 2; ++b) {
-            ptx::mbar_init(&bars.tfull[b], 1);
-            ptx::mbar_init(&bars.tempty[b], kEpiThreads);
-        }
-        ptx::mbar_init(&bars.drain, 1);
-        ptx::fence_mbar_init();
-        s_abort = 0;
-    }
-    {
-        const uint4 *src = reinterpret_cast<const uint4 *>(a.Vs);
-        uint4 *dst = reinterpret_cast<uint4 *>(Vhi);
-        const int n16 = (2 * np * np * 2) / 16;
-        for (int i = tid; i < n16; i += blockDim.x) dst[i] = __ldg(src + i);
-    }
-    ptx::fence_proxy_async_smem();
-    ptx::tc_fence_before();
-    __syncthreads();
-    ptx::tc_fence_after();
-    const uint32_t tmem = tmem_slot;
-    const int R = x.R;
-    const long long my_units = (x.n_units - blockIdx.x + gridDim.x - 1) / gridDim.x;
-    const int n_my = (int)(my_units * R);
-    const long long n12 = (long long)a.n1 * a.n2;
-    // iteration it: unit blockIdx.x + (it / R) * gridDim.x, item it % R of the chunk
-    auto unit_of = [&](int it) { return blockIdx.x + (long long)(it / R) * gridDim.x; };
-
-    if (warp == kMmaWarp) {
-        // ------------------------------------------------------------ MMA issue
-        if (lane == 0) {
-            const uint32_t sVhi = ptx::smem_u32(Vhi), sVlo = ptx::smem_u32(Vlo);
-            bool ok = true;
-            for (int it = 0; it < n_my && ok; ++it) {
-                const int s = it % S, b = it & 1;
-                ok = wait_bar(&bars.full[s], (uint32_t)((it / S) & 1), a, &s_abort);
-                if (ok && it >= 2) ok = wait_bar(&bars.tempty[b], (uint32_t)(((it >> 1) - 1) & 1), a, &s_abort);
-                if (!ok) break;
-                ptx::tc_fence_after();
-                const int h = (int)(unit_of(it) % x.H);
-                // the part's columns of V^T: N rows h*NH .. of the K-major inverse operand
-                const uint32_t boff = (uint32_t)((h * NH / 8) * np * 16);
-                const uint32_t sA = ptx::smem_u32(stage0 + s * stage_bytes);
-                issue_x3a_mma(tmem + (uint32_t)(b * NH), sA, sA + (uint32_t)half_bytes, sVhi + boff, sVlo + boff, np,
-                              NH);
-                ptx::mma_commit(&bars.empty[s]);
-                ptx::mma_commit(&bars.tfull[b]);
-            }
-            if (!ok) {
-                ptx::mma_commit(&bars.drain);
-                ptx::mbar_wait_bounded(&bars.drain, 0, a.timeout_cycles);
-            }
-        }
-        __syncwarp();
-    } else if (warp >= kEpiWarps) {
-        // ------------------------------------------------------------ producers (the X3I loader)
-        const int ptid = tid - kEpiThreads;
-        const int grp = ptid / kGroupThreads, gtid = ptid % kGroupThreads;
-        for (int it = grp; it < n_my; it += kProdGroups) {
-            const int s = it % S;
-            bool ok = it < S || wait_bar(&bars.empty[s], (uint32_t)(((it / S) - 1) & 1), a, &s_abort);
-            ok = producers_agree(ok, &s_vote[grp], gtid, 2 + 2 * grp);
-            if (!ok) break;
-            const long long u = unit_of(it);
-            const long long tile = (long long)(it % R) * x.n_ptiles + u / x.H;  // rows of item it % R
-            make_desc<P_X3I>(a, tile, sdesc[grp], gtid);
-            ptx::named_bar(3 + 2 * grp, kGroupThreads);
-            uint8_t *Ahi = stage0 + s * stage_bytes;
-            produce_tile<P_X3I>(a, sdesc[grp], Ahi, Ahi + half_bytes, gtid);
-            ptx::fence_proxy_async_smem();
-            ptx::mbar_arrive(&bars.full[s]);
-        }
-    } else {
-        // ------------------------------------------------------------ epilogue
-        // warp w: TMEM lane quadrant w % 4 (one tile row = one position per
-        // thread), columns [hc*NH/2, (hc+1)*NH/2) of the part, hc = w / 4.
-        const int q = warp & 3, hc = warp >> 2;
-        const int m = 32 * q + lane;
-        const int cw = NH >> 1;  // 8, 16 or 24 columns, multiples of 8
-        const int c0 = hc * cw;
-        const uint32_t trow = (uint32_t)(32 * q) << 16;
-        const uint32_t tslot0 = tmem + trow + (uint32_t)(2 * NH + c0);  // group slot s at + s * NH
-        const float zero8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        for (int sl = 0; sl < kGroupSlots; ++sl)
-            for (int c = 0; c < cw; c += 8) ptx::tmem_st8(tslot0 + (uint32_t)(sl * NH + c), zero8);
-        ptx::tmem_wait_st();
-        int gi = x.f.g0;
-        Group G = x.f.groups[gi];
-        long long p = 0, xb = 0;  // position in the plane, first x3 of this thread's columns
-        for (int it = 0; it < n_my; ++it) {
-            const int b = it & 1, k = it % R;
-            if (k == 0) {  // a new unit starts at the chunk's first group
-                const long long u = unit_of(it);
-                p = (u / x.H) * 128 + m;
-                xb = (u % x.H) * NH + c0;
-                gi = x.f.g0;
-                G = x.f.groups[gi];
-            }
-            const int item = x.f.item0 + k;
-            while (item >= G.first_item + G.n_items) G = x.f.groups[++gi];
-            const int2 ij = a.pairs[k];
-            const int2 sl = x.f.item_slot[item];
-            const float gi_ = x.f.occ ? (float)x.f.occ[ij.x] : 1.f;
-            const float gj_ = x.f.occ ? (float)x.f.occ[ij.y] : 1.f;
-            // orbital values at this row's position and columns, fetched before the MMA wait
-            float pi[kX3aMaxNH / 2], pj[kX3aMaxNH / 2];
-            const float *ppi = x.f.psi32 + (long long)ij.x * a.N + xb * n12 + p;
-            const float *ppj = x.f.psi32 + (long long)ij.y * a.N + xb * n12 + p;
-            const int cv = (int)(xb + cw <= a.n3 ? cw : (xb < a.n3 ? a.n3 - xb : 0));  // columns with x3 < n3
-#pragma unroll
-            for (int c = 0; c < kX3aMaxNH / 2; ++c) {
-                pi[c] = (c < cv) ? __ldg(ppi + c * n12) : 0.f;
-                pj[c] = (c < cv) ? __ldg(ppj + c * n12) : 0.f;
-            }
-            const float unscale = ldexpf(1.f, -(scale_exp(a.in_max[k]) + kVScaleExp));
-            if (!wait_bar_warp(&bars.tfull[b], (uint32_t)((it >> 1) & 1), a, &s_abort)) break;
-            ptx::tc_fence_after();
-            float phi[kX3aMaxNH / 2];
-            const uint32_t td = tmem + trow + (uint32_t)(b * NH + c0);
-#pragma unroll
-            for (int c = 0; c < kX3aMaxNH / 2; c += 8)
-                if (c < cw) ptx::tmem_ld8(td + c, phi + c);
-            ptx::tc_fence_before();
-            ptx::mbar_arrive(&bars.tempty[b]);  // the D slot is free for the next MMA
-#pragma unroll
-            for (int c = 0; c < kX3aMaxNH / 2; ++c) phi[c] *= unscale;
-            // slot(i) += g_j psi_j phi; slot(j) += g_i psi_i phi (once when i == j)
-#pragma unroll
-            for (int c = 0; c < kX3aMaxNH / 2; c += 8) {
-                if (c >= cw) break;
-                float v[8];
-                const uint32_t tx = tslot0 + (uint32_t)(sl.x * NH + c);
-                ptx::tmem_ld8(tx, v);
-#pragma unroll
-                for (int e = 0; e < 8; ++e) v[e] = fmaf(gj_ * pj[c + e], phi[c + e], v[e]);
-                ptx::tmem_st8(tx, v);
-            }
-            ptx::tmem_wait_st();
-            if (sl.y != sl.x) {
-#pragma unroll
-                for (int c = 0; c < kX3aMaxNH / 2; c += 8) {
-                    if (c >= cw) break;
-                    float v[8];
-                    const uint32_t ty = tslot0 + (uint32_t)(sl.y * NH + c);
-                    ptx::tmem_ld8(ty, v);
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) v[e] = fmaf(gi_ * pi[c + e], phi[c + e], v[e]);
-                    ptx::tmem_st8(ty, v);
-                }
-                ptx::tmem_wait_st();
-            }
-            if (item == G.first_item + G.n_items - 1) {
-                // the group is complete: add every slot into its orbital's accumulator and clear it
-                for (int s2 = 0; s2 < G.n_slots; ++s2) {
-                    float *dst = x.f.acc + (long long)G.orb[s2] * a.N + xb * n12 + p;
-                    for (int c = 0; c < cw; c += 8) {
-                        float v[8], o[8];
-                        ptx::tmem_ld8(tslot0 + (uint32_t)(s2 * NH + c), v);
-#pragma unroll
-                        for (int e = 0; e < 8; ++e) o[e] = (c + e < cv) ? dst[(c + e) * n12] : 0.f;
-#pragma unroll
-                        for (int e = 0; e < 8; ++e)
-                            if (c + e < cv) dst[(c + e) * n12] = o[e] + v[e];
-                        ptx::tmem_st8(tslot0 + (uint32_t)(s2 * NH + c), zero8);
-                    }
-                }
-                ptx::tmem_wait_st();
-            }
-        }
-    }
-    ptx::tc_fence_before();
-    __syncthreads();
-    if (warp == kMmaWarp) {
-        ptx::tc_fence_after();
-        ptx::tmem_dealloc(tmem, 512);
-    }
-}
-
 // psi (fp64) -> psi32 and per-vector max |value|.
 __global__ void prep_kernel(const double *__restrict__ src, float *__restrict__ dst, float *__restrict__ vmax,
                             int n_vec, long long N) {
@@ -1776,63 +1511,6 @@ int launch_slab(kx_plan *p, long R, const float *in, const float *in_max, float 
     return prof_end(p, s);
 }
 
-// Parts of x3 for the fused mode-3 inverse + accumulation: H parts of NH
-// columns, NH <= kX3aMaxNH and a multiple of 16; the plane must split into
-// whole 128-position tiles.
-bool x3acc_shape(const kx_plan *p, int *H, int *NH) {
-    const int np3 = p->np[2];
-    if (((long long)p->n[0] * p->n[1]) % 128) return false;
-    if (np3 <= kX3aMaxNH) {
-        *H = 1;
-        *NH = np3;
-        return true;
-    }
-    if (np3 % 32 == 0 && np3 / 2 <= kX3aMaxNH) {
-        *H = 2;
-        *NH = np3 / 2;
-        return true;
-    }
-    return false;
-}
-
-bool use_x3acc(const kx_plan *p) {
-    if (const char *e = std::getenv("KX_X3ACC")) return std::atoi(e) != 0;  // tuning override
-    return p->tune.fuse_acc != 0;
-}
-
-int launch_x3acc(kx_plan *p, PassArgs a, const X3Acc &f, long R, cudaStream_t s) {
-    X3AccArgs x{};
-    int H = 0, NH = 0;
-    if (!x3acc_shape(p, &H, &NH)) return set_error(KX_ERR_UNSUPPORTED, "fused mode-3 accumulation: shape");
-    a.nc = p->n[2];
-    a.np = p->np[2];
-    a.Vs = p->d_Vs[2];
-    a.n1 = p->n[0];
-    a.n2 = p->n[1];
-    a.n3 = p->n[2];
-    a.N = (long long)p->N;
-    a.status = p->d_status;
-    a.timeout_cycles = 4000000000LL;  // ~2 s at the SM clock
-    a.rows_pp = (long long)p->n[0] * p->n[1];
-    a.total_rows = R * a.rows_pp;
-    a.stages = pass_stages(a.np, false);
-    x.pa = a;
-    x.f = f;
-    x.H = H;
-    x.NH = NH;
-    x.n_ptiles = (int)(a.rows_pp / 128);
-    x.R = (int)R;
-    x.n_units = (long long)x.n_ptiles * H;
-    // at least 120 KB so that one CTA (and one 512-column TMEM allocation) sits on each SM
-    const size_t smem = std::max<size_t>(pass_smem(a.np, a.stages, false), 120 * 1024);
-    KX_CUDA_TRY(cudaFuncSetAttribute(tc_x3acc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int grid = (int)std::max(1LL, std::min<long long>(x.n_units, (long long)p->num_sms));
-    if (int rc = prof_begin(p, PK_X3ACC, s)) return rc;
-    tc_x3acc_kernel<<<grid, kThreads, smem, s>>>(x);
-    KX_LAUNCH_CHECK("tc_x3acc_kernel launch");
-    return prof_end(p, s);
-}
-
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct TcLayout {
@@ -1864,7 +1542,7 @@ float fmax_sqrt(const kx_plan *p) {
 // T0->T1, X3I T1->T0 (or xout in vector mode).  mx holds four rows of per-item
 // maxima, mx_stride apart.
 int run_passes(kx_plan *p, PassArgs a, long R, float *T0, float *T1, float *mx, long mx_stride, double *ex,
-               double *partial, bool energy_only, double *xout, cudaStream_t s, const X3Acc *fuse = nullptr) {
+               double *partial, bool energy_only, double *xout, cudaStream_t s) {
     int rc;
     float *mx1 = mx, *mx2 = mx + mx_stride, *mx3 = mx + 2 * mx_stride, *mx4 = mx + 3 * mx_stride;
     a.rows_pp = (long long)p->n[0] * p->n[1];
@@ -1894,7 +1572,6 @@ int run_passes(kx_plan *p, PassArgs a, long R, float *T0, float *T1, float *mx, 
         a.out = T0;
         a.out_max = nullptr;
         a.xout = xout;
-        if (fuse) return launch_x3acc(p, a, *fuse, R, s);
         return launch_pass<P_X3I>(p, a, 2, s, nullptr);
     }
 
@@ -1941,7 +1618,6 @@ int run_passes(kx_plan *p, PassArgs a, long R, float *T0, float *T1, float *mx, 
     a.out = T0;
     a.out_max = nullptr;
     a.xout = xout;
-    if (fuse) return launch_x3acc(p, a, *fuse, R, s);
     return launch_pass<P_X3I>(p, a, 2, s, nullptr);
 }
 
@@ -2011,8 +1687,6 @@ int tc_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, double *v
     const int2 *pairs = reinterpret_cast<const int2 *>(p->d_pairs);
     const float mid_bound = fmax_sqrt(p);
 
-    int H = 0, NH = 0;
-    const bool fused_acc = !energy_only && use_x3acc(p) && x3acc_shape(p, &H, &NH);
     int g0 = 0, o_fin = 0;
     while (g0 < n_groups) {
         int g1 = g0 + 1;
@@ -2027,12 +1701,8 @@ int tc_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, double *v
         a.occ = occ;
         a.f32 = p->d_f32;
         a.mid_bound = mid_bound;
-        X3Acc fa{reinterpret_cast<const Group *>(p->d_groups), g0, g1, (int)c0,
-                 reinterpret_cast<const int2 *>(p->d_item_slot), L.psi32, occ, L.acc};
-        if ((rc = run_passes(p, a, R, L.T0, L.T1, L.mx, chunk, ex, L.partial, energy_only, nullptr, s,
-                             fused_acc ? &fa : nullptr)))
-            return rc;
-        if (!energy_only && !fused_acc) {
+        if ((rc = run_passes(p, a, R, L.T0, L.T1, L.mx, chunk, ex, L.partial, energy_only, nullptr, s))) return rc;
+        if (!energy_only) {
             const unsigned blocks = (unsigned)((N / 4 + kAccThreads - 1) / kAccThreads);
             if ((rc = prof_begin(p, PK_ACC, s))) return rc;
             acc_kernel<<<blocks, kAccThreads, 0, s>>>(L.T0, reinterpret_cast<const Group *>(p->d_groups), g0, g1,

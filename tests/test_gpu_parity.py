@@ -386,39 +386,3 @@ def test_unaligned_output_pointer(kx):
     torch.cuda.synchronize()
     assert rc == kx.KX_OK
     assert torch.equal(buf[1:].view(n_orb, N), vx)
-
-
-X3ACC_CASES = [
-    ((16, 24, 48), (0.5, 0.5, 0.4), (P, P, D), U, 6, "1"),    # one x3 part of 48, no padding
-    ((40, 32, 24), (0.4, 0.45, 0.5), (P, P, P), S, 5, "1"),   # one part of 32, x3 padded 24 -> 32
-    ((16, 16, 56), (0.5, 0.5, 0.35), (D, D, D), U, 9, "24"),  # two parts of 32, padded 56 -> 64; several chunks
-    ((8, 16, 8), (0.6, 0.5, 0.6), (D, P, D), S, 3, "1"),      # one part of 16, padded 8 -> 16
-]
-
-
-@pytest.mark.parametrize("case", range(len(X3ACC_CASES)))
-def test_fused_mode3_accumulation(kx, case, monkeypatch):
-    """The fused mode-3 inverse + accumulation kernel (phi kept on chip, per-group
-    TMEM accumulators) and the separate X3I pass + accumulation kernel both match
-    the oracle; the launch counts show which ran."""
-    n, h, bc, kind, n_orb, chunk = X3ACC_CASES[case]
-    sysd = system(n, h, bc, kind, n_orb, 300 + case)
-    psi = workloads.make_orbitals(sysd)
-    occ = np.linspace(1.0, 0.5, n_orb)
-    op = oracle.Plan(n, h, bc, kind)
-    vx_ref, ex_ref = oracle.vx_apply(op, psi, occ=occ)
-    plan = kx.Plan(n, h, bc, kind, precision=1)
-    if chunk != "1":
-        monkeypatch.setenv("KX_CHUNK_PAIRS", chunk)
-    for fused in (True, False):
-        monkeypatch.setenv("KX_X3ACC", "1" if fused else "0")
-        plan.profile(True)
-        vx, ex = kx.kx_vx_apply(plan, dev(psi.T), occ=dev(occ))
-        torch.cuda.synchronize()
-        prof = plan.profile_read()
-        plan.profile(False)
-        assert plan.status() == kx.KX_OK
-        assert (prof["x3acc"][1] > 0) == fused
-        assert (prof["acc"][1] > 0) == (not fused)
-        assert relmax(vx.cpu().numpy().T, vx_ref) < TOL[1]["vx"]
-        assert abs(ex.item() - ex_ref) < TOL[1]["ex"] * abs(ex_ref)

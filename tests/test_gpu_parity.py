@@ -386,3 +386,20 @@ def test_unaligned_output_pointer(kx):
     torch.cuda.synchronize()
     assert rc == kx.KX_OK
     assert torch.equal(buf[1:].view(n_orb, N), vx)
+
+
+def test_autotune_then_apply(kx):
+    """kx_autotune times the launch shapes on synthetic orbitals and keeps one;
+    the apply afterwards still matches the oracle."""
+    n, h, bc = (24, 16, 32), (0.4, 0.45, 0.5), (D, P, D)
+    sysd = system(n, h, bc, S, 6, 63)
+    psi = workloads.make_orbitals(sysd)
+    op = oracle.Plan(n, h, bc, S)
+    vx_ref, ex_ref = oracle.vx_apply(op, psi)
+    plan = kx.Plan(n, h, bc, S, precision=1)
+    kx.kx_autotune(plan, 6, 200)
+    vx, ex = kx.kx_vx_apply(plan, dev(psi.T))
+    torch.cuda.synchronize()
+    assert plan.status() == kx.KX_OK
+    assert relmax(vx.cpu().numpy().T, vx_ref) < TOL[1]["vx"]
+    assert abs(ex.item() - ex_ref) < TOL[1]["ex"] * abs(ex_ref)

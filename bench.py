@@ -400,6 +400,9 @@ def main():
                 "peak_source": f"{peak_src} bf16_tflops / 3 (three fp16 products per useful product)"}
     roof["traffic"], roof["traffic_source"] = measured_traffic(dom, SYS.n[2] * items_per_launch)
     roof["avg_launch_ms"] = avg_ms
+    if roof["traffic"] is not None:  # DRAM bytes per launch / launch time, against the measured copy peak
+        roof["dram_gbs"] = roof["traffic"] / (avg_ms / 1e3) / 1e9
+        roof["dram_frac_of_hbm_peak"] = roof["dram_gbs"] / hbm
     roof["items_per_launch"] = items_per_launch
     kern = {k: {"ms_total": v[0], "launches": v[1], "share": v[0] / max(1e-9, sum(x[0] for x in prof.values()))}
             for k, v in prof.items() if v[1] > 0}

@@ -759,13 +759,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const PassArgs a) 
 //   D   D3 -> A4[x1][k2] (MN-major, written by the thread owning row k2)
 //   M4  A4 x V2^T                                    -> D4[x1][x2]
 //   E   D4 -> global slice [x2][x1] (coalesced), per-item maximum
-// Three units are in flight: unit j uses TMEM slot, A buffer and epilogue
-// group j % 3, so the groups run their stage chains independently and the
-// single MMA thread serves whichever group is ready.  Each product accumulates
-// its three split terms in one fp32 TMEM accumulator (the small cross terms
-// first), which leaves TMEM room for the third unit.  Split scales are powers
-// of two from bounds: each orthogonal mode product grows max|.| by at most
-// sqrt(n), the scaling by at most fmax.
+// Two units are in flight: unit j uses TMEM slot, A buffer and epilogue
+// warpgroup j & 1, so the two groups run their stage chains independently and
+// the single MMA thread serves whichever group is ready.  Split scales are
+// powers of two from bounds: each orthogonal mode product grows max|.| by at
+// most sqrt(n), the scaling by at most fmax.
 // ---------------------------------------------------------------------------
 struct SlabArgs {
     int n1, n2, n3, np1, np2;
@@ -782,28 +780,24 @@ struct SlabArgs {
     const int2 *pairs;
     const double *occ;
     int rhs_mode;
+    int stage_in;           // the input plane is bulk-copied into shared memory before it is split
     int *status;
     long long timeout_cycles;
     long long *clk;         // role counters (only with KX_ROLE_CLOCKS)
 };
 
-constexpr int kSlabSlots = 3;        // units in flight: TMEM slots, A buffers, epilogue groups
 constexpr int kSlabProdThreads = 96;
-constexpr int kSlabU = 4;            // producer loads in flight per thread
-// Warp roles: 24 epilogue warps (warp w reads TMEM lane quadrant w % 4, the
+constexpr int kSlabU = 8;            // producer loads in flight per thread
+// Warp roles: 16 epilogue warps (warp w reads TMEM lane quadrant w % 4, the
 // TMEM access rule; column half (w / 4) % 2; group w / 8), then 3 producer
 // warps, then the MMA warp.
-constexpr int kSlabEpiWarps = 8 * kSlabSlots;
+constexpr int kSlabEpiWarps = 16;
 constexpr int kSlabGroupThreads = 256;
 constexpr int kSlabMmaWarp = kSlabEpiWarps + kSlabProdThreads / 32;
 constexpr int kSlabThreads = 32 * (kSlabMmaWarp + 1);
-// The slab's A buffers use unpadded core matrices (128 bytes apart): every
-// writer stores 16-byte rows of eight consecutive rows of one core matrix.
-constexpr int kSlabCore = 128;
-__host__ __device__ constexpr size_t slab_half_bytes(int np) { return (size_t)np * 16 * kSlabCore / 8; }
 
 struct SlabBars {
-    uint64_t full[kSlabSlots], empty[kSlabSlots], tfull[kSlabSlots], ready[kSlabSlots], drain;
+    uint64_t full[2], empty[2], tfull[2], ready[2], in_full, drain;
 };
 
 __device__ __forceinline__ bool slab_wait(uint64_t *bar, uint32_t parity, const SlabArgs &a, volatile int *abort) {
@@ -824,39 +818,6 @@ __device__ __forceinline__ void store_split8(uint8_t *hi_base, uint8_t *lo_base,
     split8(w, h, l);
     *reinterpret_cast<uint4 *>(hi_base + off) = h;
     *reinterpret_cast<uint4 *>(lo_base + off) = l;
-}
-
-// D = A_hi V_hi + A_hi V_lo + A_lo V_hi over K = np in one accumulator, the
-// two small cross products first (single issuing thread; unpadded A layout).
-__device__ __forceinline__ void issue_slab_mma(uint32_t tmem_d, uint32_t a_hi, uint32_t a_lo, bool a_kmajor,
-                                               uint32_t v_hi, uint32_t v_lo, bool inverse, int np) {
-    const uint32_t idesc = ptx::idesc_f16(128, np, a_kmajor ? 0 : 1, inverse ? 0 : 1);
-    const uint32_t a_lbo = a_kmajor ? (uint32_t)kSlabCore : (uint32_t)(16 * kSlabCore);
-    const uint32_t a_sbo = a_kmajor ? (uint32_t)((np >> 3) * kSlabCore) : (uint32_t)kSlabCore;
-    const uint32_t a_step = 2 * a_lbo;
-    const uint32_t b_lbo = inverse ? 128u : (uint32_t)(np * 16);
-    const uint32_t b_sbo = inverse ? (uint32_t)(np * 16) : 128u;
-    const uint32_t b_step = inverse ? 256u : (uint32_t)(np * 32);
-    const int nks = np >> 4;
-    const uint64_t ah0 = ptx::sdesc(a_hi, a_lbo, a_sbo), al0 = ptx::sdesc(a_lo, a_lbo, a_sbo);
-    const uint64_t bh0 = ptx::sdesc(v_hi, b_lbo, b_sbo), bl0 = ptx::sdesc(v_lo, b_lbo, b_sbo);
-    const uint64_t a_inc = a_step >> 4, b_inc = b_step >> 4;
-    uint64_t ah = ah0, al = al0, bh = bh0, bl = bl0;
-    for (int ks = 0; ks < nks; ++ks) {
-        ptx::mma_f16(tmem_d, ah, bl, idesc, ks > 0 ? 1u : 0u);
-        ptx::mma_f16(tmem_d, al, bh, idesc, 1u);
-        ah += a_inc;
-        al += a_inc;
-        bh += b_inc;
-        bl += b_inc;
-    }
-    ah = ah0;
-    bh = bh0;
-    for (int ks = 0; ks < nks; ++ks) {
-        ptx::mma_f16(tmem_d, ah, bh, idesc, 1u);
-        ah += a_inc;
-        bh += b_inc;
-    }
 }
 
 // Per-unit constants of the epilogue: item, slice, the four split exponents and
@@ -889,19 +850,20 @@ __device__ __forceinline__ SlabUnit slab_unit(const SlabArgs &a, long long u) {
 // Epilogue stage B or D for one warp: D row m (a TMEM lane) becomes K column m
 // of the next MN-major operand; 8 consecutive D columns (M values) per 16-byte
 // store.  Rows m >= nrow (padding) give zeros; rows m >= nprow are not written.
-__device__ __forceinline__ void slab_transpose_stage(uint32_t ta, int m, int h, int nrow, int nprow, int ncol,
-                                                     float us, uint8_t *Ahi, uint8_t *Alo) {
-    const int off_r = (m >> 3) * (16 * kSlabCore) + (m & 7) * 16;
+__device__ __forceinline__ void slab_transpose_stage(uint32_t ta, uint32_t tb, int m, int h, int nrow, int nprow,
+                                                     int ncol, bool two, float us, uint8_t *Ahi, uint8_t *Alo) {
+    const int off_r = (m >> 3) * (16 * kCoreStride) + (m & 7) * 16;
     for (int c = 16 * h; c < ncol; c += 32) {
-        float v[16];
-        ptx::tmem_ld16(ta + c, v);
+        float v[16], vb[16];
+        ptx::tmem_ld16x2(ta + c, tb + c, v, vb);
         if (m < nprow) {
 #pragma unroll
             for (int g8 = 0; g8 < 2; ++g8) {
                 float w[8];
 #pragma unroll
-                for (int k = 0; k < 8; ++k) w[k] = (m < nrow) ? v[8 * g8 + k] * us : 0.f;
-                store_split8(Ahi, Alo, ((c >> 3) + g8) * kSlabCore + off_r, w);
+                for (int k = 0; k < 8; ++k)
+                    w[k] = (m < nrow) ? (two ? v[8 * g8 + k] + vb[8 * g8 + k] : v[8 * g8 + k]) * us : 0.f;
+                store_split8(Ahi, Alo, ((c >> 3) + g8) * kCoreStride + off_r, w);
             }
         }
     }
@@ -911,12 +873,13 @@ __global__ void __launch_bounds__(kSlabThreads, 1) tc_slab_kernel(const SlabArgs
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int np1 = a.np1, np2 = a.np2, npm = max(np1, np2);
-    const size_t half_bytes = slab_half_bytes(npm);
+    const size_t half_bytes = a_half_bytes(npm);
     uint8_t *V1hi = smem;
     uint8_t *V1lo = V1hi + np1 * np1 * 2;
     uint8_t *V2hi = V1lo + np1 * np1 * 2;
     uint8_t *V2lo = V2hi + np2 * np2 * 2;
-    uint8_t *buf0 = V2lo + np2 * np2 * 2;  // kSlabSlots A buffers (hi | lo), one per TMEM slot
+    uint8_t *buf0 = V2lo + np2 * np2 * 2;  // two A buffers (hi | lo), one per TMEM slot
+    float *sin = reinterpret_cast<float *>(buf0 + 4 * half_bytes);  // input plane [x2][x1] (stage_in)
     __shared__ SlabBars bars;
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int s_abort;
@@ -932,12 +895,13 @@ __global__ void __launch_bounds__(kSlabThreads, 1) tc_slab_kernel(const SlabArgs
         ptx::tmem_relinquish();
     }
     if (tid == 0) {
-        for (int b = 0; b < kSlabSlots; ++b) {
+        for (int b = 0; b < 2; ++b) {
             ptx::mbar_init(&bars.full[b], kSlabProdThreads);
             ptx::mbar_init(&bars.empty[b], 1);
             ptx::mbar_init(&bars.tfull[b], 1);
             ptx::mbar_init(&bars.ready[b], kSlabGroupThreads);
         }
+        ptx::mbar_init(&bars.in_full, 1);
         ptx::mbar_init(&bars.drain, 1);
         ptx::fence_mbar_init();
         s_abort = 0;
@@ -961,55 +925,51 @@ __global__ void __launch_bounds__(kSlabThreads, 1) tc_slab_kernel(const SlabArgs
 
     if (warp == kSlabMmaWarp) {
         // ---------------------------------------------------------------- MMA issue
-        // Polls the slots and issues the next product of whichever is ready:
+        // Polls both slots and issues the next product of whichever is ready:
         // M1 of unit j needs its A1 (full) and the slot's previous unit through
         // stage E; M2..M4 need the group's previous stage (ready).
         if (lane == 0) {
             const uint32_t sV1h = ptx::smem_u32(V1hi), sV1l = ptx::smem_u32(V1lo);
             const uint32_t sV2h = ptx::smem_u32(V2hi), sV2l = ptx::smem_u32(V2lo);
-            int jn[kSlabSlots], sn[kSlabSlots];
-#pragma unroll
-            for (int g = 0; g < kSlabSlots; ++g) {
-                jn[g] = g;
-                sn[g] = 0;
-            }
+            int jn[2] = {0, 1}, sn[2] = {0, 0};
             bool ok = true;
             long long last = clock64();
-            while (ok) {
-                bool progressed = false, pending = false;
+            while (ok && (jn[0] < n_my || jn[1] < n_my)) {
+                bool progressed = false;
 #pragma unroll
-                for (int g = 0; g < kSlabSlots; ++g) {
+                for (int g = 0; g < 2; ++g) {
                     const int j = jn[g], st = sn[g];
                     if (j >= n_my) continue;
-                    pending = true;
-                    const uint32_t use = (uint32_t)(j / kSlabSlots);  // units of this slot before j
                     bool go;
                     if (st == 0)
-                        go = ptx::mbar_test_wait(&bars.full[g], use & 1u) &&
-                             (j < kSlabSlots || ptx::mbar_test_wait(&bars.ready[g], 1u));
+                        go = ptx::mbar_test_wait(&bars.full[g], (uint32_t)((j >> 1) & 1)) &&
+                             (j < 2 || ptx::mbar_test_wait(&bars.ready[g], 1u));
                     else
                         go = ptx::mbar_test_wait(&bars.ready[g], (uint32_t)((st - 1) & 1));
                     if (!go) continue;
                     ptx::tc_fence_after();
                     const uint32_t sA = ptx::smem_u32(buf0 + g * 2 * half_bytes);
-                    const uint32_t da = tmem + (uint32_t)(g * npm);
+                    const uint32_t da = tmem + (uint32_t)(g * 2 * npm);
                     if (st == 0)  // M1: A1 (MN-major) x V2 forward
-                        issue_slab_mma(da, sA, sA + (uint32_t)half_bytes, false, sV2h, sV2l, false, np2);
+                        issue_split_mma(da, da + (uint32_t)npm, sA, sA + (uint32_t)half_bytes, false, sV2h, sV2l,
+                                        false, np2);
                     else if (st == 1)  // M2: A2 (MN-major) x V1 forward
-                        issue_slab_mma(da, sA, sA + (uint32_t)half_bytes, false, sV1h, sV1l, false, np1);
+                        issue_split_mma(da, da + (uint32_t)npm, sA, sA + (uint32_t)half_bytes, false, sV1h, sV1l,
+                                        false, np1);
                     else if (st == 2)  // M3: A3 (K-major) x V1^T
-                        issue_slab_mma(da, sA, sA + (uint32_t)half_bytes, true, sV1h, sV1l, true, np1);
+                        issue_split_mma(da, da + (uint32_t)npm, sA, sA + (uint32_t)half_bytes, true, sV1h, sV1l,
+                                        true, np1);
                     else  // M4: A4 (MN-major) x V2^T
-                        issue_slab_mma(da, sA, sA + (uint32_t)half_bytes, false, sV2h, sV2l, true, np2);
+                        issue_split_mma(da, da + (uint32_t)npm, sA, sA + (uint32_t)half_bytes, false, sV2h, sV2l,
+                                        true, np2);
                     ptx::mma_commit(&bars.tfull[g]);
                     if (st == 3) ptx::mma_commit(&bars.empty[g]);
                     if (++sn[g] == 4) {
                         sn[g] = 0;
-                        jn[g] += kSlabSlots;
+                        jn[g] += 2;
                     }
                     progressed = true;
                 }
-                if (!pending) break;
                 const long long now = clock64();
                 if (progressed) {
                     last = now;
@@ -1021,6 +981,9 @@ __global__ void __launch_bounds__(kSlabThreads, 1) tc_slab_kernel(const SlabArgs
                     ok = false;
                 }
             }
+#ifdef KX_ROLE_CLOCKS
+            clk_acc[5] = 0;
+#endif
             if (!ok) {
                 ptx::mma_commit(&bars.drain);
                 ptx::mbar_wait_bounded(&bars.drain, 0, a.timeout_cycles);
@@ -1029,61 +992,108 @@ __global__ void __launch_bounds__(kSlabThreads, 1) tc_slab_kernel(const SlabArgs
         __syncwarp();
     } else if (warp >= kSlabEpiWarps) {
         // ---------------------------------------------------------------- producers: A1 from global
-        // Task t covers 8 consecutive x1 of one x2 row: row group g = (t/8)%16,
-        // x2 = 8*(t/128) + t%8, so eight neighbouring lanes fill one core matrix
-        // (128 contiguous bytes) and read eight 32-byte row pieces.
         const int ptid = tid - kSlabEpiWarps * 32;
         const int ntask = 16 * np2;  // 16 row groups (x1) x np2 columns (x2)
         const int nlines = (int)((n12 * 4) >> 7);  // 128-byte lines of a slice (n1 % 8 == 0)
+        const uint32_t plane_bytes = (uint32_t)(n12 * 4);
+        auto plane = [&](int it) {
+            const long long u = blockIdx.x + (long long)it * gridDim.x;
+            const long long item = (unsigned)u / (unsigned)a.n3, k3 = (unsigned)u % (unsigned)a.n3;
+            return a.in + item * a.N + k3 * n12;
+        };
+        // stage_in: one thread copies the plane of the next unit into shared memory
+        // (pieces of at most 16 KB) as soon as the previous plane has been split
+        auto issue_plane = [&](int it) {
+            ptx::fence_proxy_async_smem();
+            ptx::mbar_arrive_expect_tx(&bars.in_full, plane_bytes);
+            const char *src = reinterpret_cast<const char *>(plane(it));
+            char *dst = reinterpret_cast<char *>(sin);
+            for (uint32_t o = 0; o < plane_bytes; o += 16384u)
+                ptx::bulk_load(dst + o, src + o, min(16384u, plane_bytes - o), &bars.in_full);
+        };
+        int inflight = -1;  // unit whose plane copy thread 0 issued and has not yet waited for
+        if (a.stage_in && ptid == 0 && n_my > 0) {
+            issue_plane(0);
+            inflight = 0;
+        }
         for (int it = 0; it < n_my; ++it) {
-            const int sl = it % kSlabSlots;
-            if (it + kSlabSlots < n_my) {
-                // pull the slice of a later unit into L2 while this one waits for its buffer
-                const long long u2 = blockIdx.x + (long long)(it + kSlabSlots) * gridDim.x;
-                const long long item2 = (unsigned)u2 / (unsigned)a.n3, k32 = (unsigned)u2 % (unsigned)a.n3;
-                const char *src = reinterpret_cast<const char *>(a.in + item2 * a.N + k32 * n12);
+            const int sl = it & 1;
+            if (it + 2 < n_my) {
+                // pull the plane of unit it+2 into L2 while this unit waits for its buffer
+                const char *src = reinterpret_cast<const char *>(plane(it + 2));
                 for (int l = ptid; l < nlines; l += kSlabProdThreads) ptx::prefetch_l2(src + ((long long)l << 7));
             }
             long long tw = KX_CLK_NOW();
-            if (it >= kSlabSlots &&
-                !slab_wait(&bars.empty[sl], (uint32_t)((it / kSlabSlots - 1) & 1), a, &s_abort))
-                break;
+            bool ok = it < 2 || slab_wait(&bars.empty[sl], (uint32_t)(((it >> 1) - 1) & 1), a, &s_abort);
             KX_CLK_ADD(1, tw);
             tw = KX_CLK_NOW();
-            if (s_abort) break;
+            if (ok && a.stage_in) ok = slab_wait(&bars.in_full, (uint32_t)(it & 1), a, &s_abort);
+            if (ok && ptid == 0) inflight = -1;
+            ok = ok && !s_abort;
+            // with stage_in the producers meet at a named barrier below, so they leave together
+            if (a.stage_in) ok = ptx::named_bar_and(2, kSlabProdThreads, ok);
+            if (!ok) break;
             const long long u = blockIdx.x + (long long)it * gridDim.x;
-            const long long item = (unsigned)u / (unsigned)a.n3, k3 = (unsigned)u % (unsigned)a.n3;
-            const float *slice = a.in + item * a.N + k3 * n12;
+            const long long item = (unsigned)u / (unsigned)a.n3;
             const float sc = ldexpf(1.f, scale_exp(a.in_max[item]));
             uint8_t *Ahi = buf0 + sl * 2 * half_bytes;
             uint8_t *Alo = Ahi + half_bytes;
-            for (int t0 = ptid; t0 < ntask; t0 += kSlabProdThreads * kSlabU) {
-                float v[kSlabU][8];
-#pragma unroll
-                for (int r = 0; r < kSlabU; ++r) {
-                    const int t = t0 + r * kSlabProdThreads;
-                    const int g = (t >> 3) & 15, k = 8 * (t >> 7) + (t & 7);
-                    if (t < ntask && 8 * g < a.n1 && k < a.n2) {
-                        ld8(slice + (long long)k * a.n1 + 8 * g, v[r]);
+            if (a.stage_in) {
+#pragma unroll 4
+                for (int t = ptid; t < ntask; t += kSlabProdThreads) {
+                    const int g = t & 15, k = t >> 4;
+                    float v[8];
+                    if (8 * g < a.n1 && k < a.n2) {
+                        const float4 *src = reinterpret_cast<const float4 *>(sin + k * a.n1 + 8 * g);
+                        const float4 x0 = src[0], x1 = src[1];
+                        v[0] = x0.x * sc; v[1] = x0.y * sc; v[2] = x0.z * sc; v[3] = x0.w * sc;
+                        v[4] = x1.x * sc; v[5] = x1.y * sc; v[6] = x1.z * sc; v[7] = x1.w * sc;
                     } else {
 #pragma unroll
-                        for (int c = 0; c < 8; ++c) v[r][c] = 0.f;
+                        for (int c = 0; c < 8; ++c) v[c] = 0.f;
+                    }
+                    store_split8(Ahi, Alo, g * kCoreStride + (k >> 3) * (16 * kCoreStride) + (k & 7) * 16, v);
+                }
+                ptx::fence_proxy_async_smem();
+                ptx::mbar_arrive(&bars.full[sl]);
+                // every producer has finished reading the plane: it may be overwritten
+                ptx::named_bar(2, kSlabProdThreads);
+                if (ptid == 0 && it + 1 < n_my) {
+                    issue_plane(it + 1);
+                    inflight = it + 1;
+                }
+            } else {
+                const float *slice = plane(it);
+                for (int t0 = ptid; t0 < ntask; t0 += kSlabProdThreads * kSlabU) {
+                    float v[kSlabU][8];
+#pragma unroll
+                    for (int r = 0; r < kSlabU; ++r) {
+                        const int t = t0 + r * kSlabProdThreads;
+                        const int g = t & 15, k = t >> 4;
+                        if (t < ntask && 8 * g < a.n1 && k < a.n2) {
+                            ld8(slice + (long long)k * a.n1 + 8 * g, v[r]);
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < 8; ++c) v[r][c] = 0.f;
+                        }
+                    }
+#pragma unroll
+                    for (int r = 0; r < kSlabU; ++r) {
+                        const int t = t0 + r * kSlabProdThreads;
+                        if (t >= ntask) continue;
+                        const int g = t & 15, k = t >> 4;
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) v[r][c] *= sc;
+                        store_split8(Ahi, Alo, g * kCoreStride + (k >> 3) * (16 * kCoreStride) + (k & 7) * 16, v[r]);
                     }
                 }
-#pragma unroll
-                for (int r = 0; r < kSlabU; ++r) {
-                    const int t = t0 + r * kSlabProdThreads;
-                    if (t >= ntask) continue;
-                    const int g = (t >> 3) & 15, k = 8 * (t >> 7) + (t & 7);
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) v[r][c] *= sc;
-                    store_split8(Ahi, Alo, g * kSlabCore + (k >> 3) * (16 * kSlabCore) + (k & 7) * 16, v[r]);
-                }
+                ptx::fence_proxy_async_smem();
+                ptx::mbar_arrive(&bars.full[sl]);
             }
-            ptx::fence_proxy_async_smem();
-            ptx::mbar_arrive(&bars.full[sl]);
             KX_CLK_ADD(2, tw);
         }
+        // a plane copy still in flight after an early exit must land before the CTA leaves
+        if (inflight >= 0) ptx::mbar_wait_bounded(&bars.in_full, (uint32_t)(inflight & 1), a.timeout_cycles);
     } else {
         // ---------------------------------------------------------------- epilogue: group g = warp / 8
         // Warp w of a group reads TMEM lanes 32*(w%4).. (its D rows) and the
@@ -1091,13 +1101,15 @@ __global__ void __launch_bounds__(kSlabThreads, 1) tc_slab_kernel(const SlabArgs
         // warp-collective: every lane loads, only the stores are predicated per row.
         const int g = warp >> 3, q = warp & 3, h = (warp >> 2) & 1;
         const int m = 32 * q + lane;  // TMEM lane == D row
+        const bool two1 = (np1 >> 4) > 1, two2 = (np2 >> 4) > 1;
         const int nkc1 = np1 >> 3;
-        const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(g * npm);
+        const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(g * 2 * npm);
+        const uint32_t tb = ta + (uint32_t)npm;
         uint8_t *Ahi = buf0 + g * 2 * half_bytes;
         uint8_t *Alo = Ahi + half_bytes;
         double e_acc = 0.0;
         bool ok = true;
-        for (int j = g; j < n_my && ok; j += kSlabSlots) {
+        for (int j = g; j < n_my && ok; j += 2) {
             long long tw = KX_CLK_NOW();
             const SlabUnit U = slab_unit(a, blockIdx.x + (long long)j * gridDim.x);
             KX_CLK_ADD(0, tw);
@@ -1109,7 +1121,8 @@ __global__ void __launch_bounds__(kSlabThreads, 1) tc_slab_kernel(const SlabArgs
             tw = KX_CLK_NOW();
             ptx::tc_fence_after();
             if (32 * q < np1)
-                slab_transpose_stage(ta, m, h, a.n1, np1, np2, ldexpf(1.f, U.e2 - U.e1 - kVScaleExp), Ahi, Alo);
+                slab_transpose_stage(ta, tb, m, h, a.n1, np1, np2, two2, ldexpf(1.f, U.e2 - U.e1 - kVScaleExp), Ahi,
+                                     Alo);
             ptx::fence_proxy_async_smem();
             ptx::tc_fence_before();
             ptx::mbar_arrive(&bars.ready[g]);
@@ -1139,7 +1152,7 @@ __global__ void __launch_bounds__(kSlabThreads, 1) tc_slab_kernel(const SlabArgs
                 ptx::tc_fence_after();
                 const float u2 = ldexpf(1.f, -(U.e2 + kVScaleExp));
                 const float s3 = ldexpf(1.f, U.e3);
-                const int off_r = (m >> 3) * (nkc1 * kSlabCore) + (m & 7) * 16;
+                const int off_r = (m >> 3) * (nkc1 * kCoreStride) + (m & 7) * 16;
                 float e_row = 0.f;
 #pragma unroll
                 for (int r = 0; r < kMaxN / 32; ++r) {
@@ -1164,17 +1177,17 @@ __global__ void __launch_bounds__(kSlabThreads, 1) tc_slab_kernel(const SlabArgs
                             for (int k = 0; k < 8; ++k) fr[(r + 1) & 1][8 * hh + k] = 0.f;
                         }
                     }
-                    float v[16];
-                    ptx::tmem_ld16(ta + c, v);
+                    float v[16], vb[16];
+                    ptx::tmem_ld16x2(ta + c, tb + c, v, vb);
 #pragma unroll
                     for (int k = 0; k < 16; ++k) {
-                        const float y = rowC ? v[k] * u2 : 0.f;
+                        const float y = rowC ? (two1 ? v[k] + vb[k] : v[k]) * u2 : 0.f;
                         e_row = fmaf(fr[r & 1][k] * y, y, e_row);
                         v[k] = fr[r & 1][k] * y * s3;
                     }
 #pragma unroll
                     for (int hh = 0; hh < 2; ++hh)
-                        store_split8(Ahi, Alo, off_r + ((c >> 3) + hh) * kSlabCore, v + 8 * hh);
+                        store_split8(Ahi, Alo, off_r + ((c >> 3) + hh) * kCoreStride, v + 8 * hh);
                 }
                 if (rowC) e_acc += U.w * (double)e_row;
                 ptx::fence_proxy_async_smem();
@@ -1190,7 +1203,8 @@ __global__ void __launch_bounds__(kSlabThreads, 1) tc_slab_kernel(const SlabArgs
             tw = KX_CLK_NOW();
             ptx::tc_fence_after();
             if (32 * q < np2)
-                slab_transpose_stage(ta, m, h, a.n2, np2, np1, ldexpf(1.f, U.e4 - U.e3 - kVScaleExp), Ahi, Alo);
+                slab_transpose_stage(ta, tb, m, h, a.n2, np2, np1, two1, ldexpf(1.f, U.e4 - U.e3 - kVScaleExp), Ahi,
+                                     Alo);
             ptx::fence_proxy_async_smem();
             ptx::tc_fence_before();
             ptx::mbar_arrive(&bars.ready[g]);
@@ -1209,13 +1223,13 @@ __global__ void __launch_bounds__(kSlabThreads, 1) tc_slab_kernel(const SlabArgs
                 float my_max = 0.f;
                 if (32 * q < a.n1) {
                     for (int c = 16 * h; c < np2; c += 32) {
-                        float v[16];
-                        ptx::tmem_ld16(ta + c, v);
+                        float v[16], vb[16];
+                        ptx::tmem_ld16x2(ta + c, tb + c, v, vb);
                         if (!valid) continue;
 #pragma unroll
                         for (int k = 0; k < 16; ++k) {
                             if (c + k < a.n2) {
-                                const float y = v[k] * u4;
+                                const float y = (two2 ? v[k] + vb[k] : v[k]) * u4;
                                 my_max = fmaxf(my_max, fabsf(y));
                                 orow[(long long)(c + k) * a.n1] = y;
                             }
@@ -1436,10 +1450,10 @@ int launch_pass(const kx_plan *p, PassArgs a, int axis, cudaStream_t s, int *gri
 
 size_t slab_smem(const kx_plan *p) {
     const int np1 = p->np[0], np2 = p->np[1], npm = std::max(np1, np2);
-    return (size_t)4 * np1 * np1 + (size_t)4 * np2 * np2 + 2 * kSlabSlots * slab_half_bytes(npm) + 1024;
+    return (size_t)4 * np1 * np1 + (size_t)4 * np2 * np2 + 4 * a_half_bytes(npm) + 1024;
 }
 
-// The slab kernel holds V1, V2 and the slots' split A buffers in shared memory.
+// The slab kernel holds V1, V2 and two split A buffers in shared memory.
 constexpr size_t kSlabSmemMax = 227 * 1024 - 1024;  // opt-in maximum less static shared memory
 bool slab_fits(const kx_plan *p) { return slab_smem(p) <= kSlabSmemMax; }
 
@@ -1482,8 +1496,12 @@ int launch_slab(kx_plan *p, long R, const float *in, const float *in_max, float 
     if (!g_clkbuf) cudaMallocManaged(&g_clkbuf, sizeof(long long) * kClk * 4096 * 6);
     a.clk = g_clkbuf + 5LL * kClk * 4096;
 #endif
+    size_t smem = slab_smem(p);
+    const size_t plane = (size_t)a.n1 * a.n2 * 4;
+    a.stage_in = (smem + plane <= kSlabSmemMax) ? 1 : 0;
+    if (a.stage_in) smem += plane;
     // at least 120 KB so that one CTA (and one 512-column TMEM allocation) sits on each SM
-    const size_t smem = std::max<size_t>(slab_smem(p), 120 * 1024);
+    smem = std::max<size_t>(smem, 120 * 1024);
     KX_CUDA_TRY(cudaFuncSetAttribute(tc_slab_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = (int)std::max(1LL, std::min<long long>(a.total_units, (long long)p->num_sms));
     if (grid_out) *grid_out = grid;

@@ -285,12 +285,10 @@ __device__ __forceinline__ void produce_tile(const PassArgs &a, const SrcDesc &d
 // hi*hi chain is split over Da (even k-steps) and Db (odd k-steps); the
 // epilogue adds Da + Db with round-to-nearest.
 __device__ __forceinline__ void issue_split_mma(uint32_t tmem_a, uint32_t tmem_b, uint32_t a_hi, uint32_t a_lo,
-                                                bool a_kmajor, uint32_t v_hi, uint32_t v_lo, bool inverse, int np,
-                                                int core = kCoreStride) {
+                                                bool a_kmajor, uint32_t v_hi, uint32_t v_lo, bool inverse, int np) {
     const uint32_t idesc = ptx::idesc_f16(128, np, a_kmajor ? 0 : 1, inverse ? 0 : 1);
-    // core: distance of neighbouring A core matrices (kCoreStride padded, 128 packed)
-    const uint32_t a_lbo = a_kmajor ? (uint32_t)core : (uint32_t)(16 * core);
-    const uint32_t a_sbo = a_kmajor ? (uint32_t)((np >> 3) * core) : (uint32_t)core;
+    const uint32_t a_lbo = a_kmajor ? (uint32_t)kCoreStride : (uint32_t)(16 * kCoreStride);
+    const uint32_t a_sbo = a_kmajor ? (uint32_t)((np >> 3) * kCoreStride) : (uint32_t)kCoreStride;
     const uint32_t a_step = 2 * a_lbo;  // one k-step = two core matrices along K
     // V stored as 8x8 core matrices, row block of 8 x-rows = np*16 bytes.
     //   forward  (B[x][k] = V[x][k]): MN-major, K (=x) stride np*16, N (=k) stride 128
@@ -761,11 +759,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const PassArgs a) 
 //   D   D3 -> A4[x1][k2] (MN-major, written by the thread owning row k2)
 //   M4  A4 x V2^T                                    -> D4[x1][x2]
 //   E   D4 -> global slice [x2][x1] (coalesced), per-item maximum
-// Two units are in flight: unit j uses TMEM slot and epilogue group j & 1, so
-// the two groups run their stage chains independently and the single MMA
-// thread serves whichever group is ready.  Unit j's operands live in A buffer
-// j % 3: with one buffer more than units in flight, the producers stage the
-// next unit's plane while both groups work, off the chain's critical path.  Split scales are
+// Two units are in flight: unit j uses TMEM slot, A buffer and epilogue
+// warpgroup j & 1, so the two groups run their stage chains independently and
+// the single MMA thread serves whichever group is ready.  Split scales are
 // powers of two from bounds: each orthogonal mode product grows max|.| by at
 // most sqrt(n), the scaling by at most fmax.
 // ---------------------------------------------------------------------------
@@ -784,6 +780,7 @@ struct SlabArgs {
     const int2 *pairs;
     const double *occ;
     int rhs_mode;
+    int stage_in;           // the input plane is bulk-copied into shared memory before it is split
     int *status;
     long long timeout_cycles;
     long long *clk;         // role counters (only with KX_ROLE_CLOCKS)
@@ -791,7 +788,6 @@ struct SlabArgs {
 
 constexpr int kSlabProdThreads = 96;
 constexpr int kSlabU = 8;            // producer loads in flight per thread
-constexpr int kSlabBufs = 3;         // A buffers (hi | lo)
 // Warp roles: 16 epilogue warps (warp w reads TMEM lane quadrant w % 4, the
 // TMEM access rule; column half (w / 4) % 2; group w / 8), then 3 producer
 // warps, then the MMA warp.
@@ -799,14 +795,9 @@ constexpr int kSlabEpiWarps = 16;
 constexpr int kSlabGroupThreads = 256;
 constexpr int kSlabMmaWarp = kSlabEpiWarps + kSlabProdThreads / 32;
 constexpr int kSlabThreads = 32 * (kSlabMmaWarp + 1);
-// The slab's A buffers hold packed core matrices (128 bytes apart): every
-// writer stores 16-byte rows of eight consecutive rows of one core matrix, so
-// a warp's stores need no padding to avoid bank conflicts.
-constexpr int kSlabCore = 128;
-__host__ __device__ constexpr size_t slab_half_bytes(int np) { return (size_t)np * 16 * kSlabCore / 8; }
 
 struct SlabBars {
-    uint64_t full[kSlabBufs], empty[kSlabBufs], tfull[2], ready[2], drain;
+    uint64_t full[2], empty[2], tfull[2], ready[2], in_full, drain;
 };
 
 __device__ __forceinline__ bool slab_wait(uint64_t *bar, uint32_t parity, const SlabArgs &a, volatile int *abort) {
@@ -861,7 +852,7 @@ __device__ __forceinline__ SlabUnit slab_unit(const SlabArgs &a, long long u) {
 // store.  Rows m >= nrow (padding) give zeros; rows m >= nprow are not written.
 __device__ __forceinline__ void slab_transpose_stage(uint32_t ta, uint32_t tb, int m, int h, int nrow, int nprow,
                                                      int ncol, bool two, float us, uint8_t *Ahi, uint8_t *Alo) {
-    const int off_r = (m >> 3) * (16 * kSlabCore) + (m & 7) * 16;
+    const int off_r = (m >> 3) * (16 * kCoreStride) + (m & 7) * 16;
     for (int c = 16 * h; c < ncol; c += 32) {
         float v[16], vb[16];
         ptx::tmem_ld16x2(ta + c, tb + c, v, vb);
@@ -872,7 +863,7 @@ __device__ __forceinline__ void slab_transpose_stage(uint32_t ta, uint32_t tb, i
 #pragma unroll
                 for (int k = 0; k < 8; ++k)
                     w[k] = (m < nrow) ? (two ? v[8 * g8 + k] + vb[8 * g8 + k] : v[8 * g8 + k]) * us : 0.f;
-                store_split8(Ahi, Alo, ((c >> 3) + g8) * kSlabCore + off_r, w);
+                store_split8(Ahi, Alo, ((c >> 3) + g8) * kCoreStride + off_r, w);
             }
         }
     }
@@ -882,12 +873,13 @@ __global__ void __launch_bounds__(kSlabThreads, 1) tc_slab_kernel(const SlabArgs
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int np1 = a.np1, np2 = a.np2, npm = max(np1, np2);
-    const size_t half_bytes = slab_half_bytes(npm);
+    const size_t half_bytes = a_half_bytes(npm);
     uint8_t *V1hi = smem;
     uint8_t *V1lo = V1hi + np1 * np1 * 2;
     uint8_t *V2hi = V1lo + np1 * np1 * 2;
     uint8_t *V2lo = V2hi + np2 * np2 * 2;
-    uint8_t *buf0 = V2lo + np2 * np2 * 2;  // kSlabBufs A buffers (hi | lo)
+    uint8_t *buf0 = V2lo + np2 * np2 * 2;  // two A buffers (hi | lo), one per TMEM slot
+    float *sin = reinterpret_cast<float *>(buf0 + 4 * half_bytes);  // input plane [x2][x1] (stage_in)
     __shared__ SlabBars bars;
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int s_abort;
@@ -903,14 +895,13 @@ __global__ void __launch_bounds__(kSlabThreads, 1) tc_slab_kernel(const SlabArgs
         ptx::tmem_relinquish();
     }
     if (tid == 0) {
-        for (int b = 0; b < kSlabBufs; ++b) {
+        for (int b = 0; b < 2; ++b) {
             ptx::mbar_init(&bars.full[b], kSlabProdThreads);
             ptx::mbar_init(&bars.empty[b], 1);
+            ptx::mbar_init(&bars.tfull[b], 1);
+            ptx::mbar_init(&bars.ready[b], kSlabGroupThreads);
         }
-        for (int g = 0; g < 2; ++g) {
-            ptx::mbar_init(&bars.tfull[g], 1);
-            ptx::mbar_init(&bars.ready[g], kSlabGroupThreads);
-        }
+        ptx::mbar_init(&bars.in_full, 1);
         ptx::mbar_init(&bars.drain, 1);
         ptx::fence_mbar_init();
         s_abort = 0;
@@ -934,8 +925,8 @@ __global__ void __launch_bounds__(kSlabThreads, 1) tc_slab_kernel(const SlabArgs
 
     if (warp == kSlabMmaWarp) {
         // ---------------------------------------------------------------- MMA issue
-        // Polls both groups and issues the next product of whichever is ready:
-        // M1 of unit j needs its A1 (full) and the group's previous unit through
+        // Polls both slots and issues the next product of whichever is ready:
+        // M1 of unit j needs its A1 (full) and the slot's previous unit through
         // stage E; M2..M4 need the group's previous stage (ready).
         if (lane == 0) {
             const uint32_t sV1h = ptx::smem_u32(V1hi), sV1l = ptx::smem_u32(V1lo);
@@ -949,31 +940,30 @@ __global__ void __launch_bounds__(kSlabThreads, 1) tc_slab_kernel(const SlabArgs
                 for (int g = 0; g < 2; ++g) {
                     const int j = jn[g], st = sn[g];
                     if (j >= n_my) continue;
-                    const int bj = j % kSlabBufs;
                     bool go;
                     if (st == 0)
-                        go = ptx::mbar_test_wait(&bars.full[bj], (uint32_t)((j / kSlabBufs) & 1)) &&
+                        go = ptx::mbar_test_wait(&bars.full[g], (uint32_t)((j >> 1) & 1)) &&
                              (j < 2 || ptx::mbar_test_wait(&bars.ready[g], 1u));
                     else
                         go = ptx::mbar_test_wait(&bars.ready[g], (uint32_t)((st - 1) & 1));
                     if (!go) continue;
                     ptx::tc_fence_after();
-                    const uint32_t sA = ptx::smem_u32(buf0 + bj * 2 * half_bytes);
+                    const uint32_t sA = ptx::smem_u32(buf0 + g * 2 * half_bytes);
                     const uint32_t da = tmem + (uint32_t)(g * 2 * npm);
                     if (st == 0)  // M1: A1 (MN-major) x V2 forward
                         issue_split_mma(da, da + (uint32_t)npm, sA, sA + (uint32_t)half_bytes, false, sV2h, sV2l,
-                                        false, np2, kSlabCore);
+                                        false, np2);
                     else if (st == 1)  // M2: A2 (MN-major) x V1 forward
                         issue_split_mma(da, da + (uint32_t)npm, sA, sA + (uint32_t)half_bytes, false, sV1h, sV1l,
-                                        false, np1, kSlabCore);
+                                        false, np1);
                     else if (st == 2)  // M3: A3 (K-major) x V1^T
                         issue_split_mma(da, da + (uint32_t)npm, sA, sA + (uint32_t)half_bytes, true, sV1h, sV1l,
-                                        true, np1, kSlabCore);
+                                        true, np1);
                     else  // M4: A4 (MN-major) x V2^T
                         issue_split_mma(da, da + (uint32_t)npm, sA, sA + (uint32_t)half_bytes, false, sV2h, sV2l,
-                                        true, np2, kSlabCore);
+                                        true, np2);
                     ptx::mma_commit(&bars.tfull[g]);
-                    if (st == 3) ptx::mma_commit(&bars.empty[bj]);
+                    if (st == 3) ptx::mma_commit(&bars.empty[g]);
                     if (++sn[g] == 4) {
                         sn[g] = 0;
                         jn[g] += 2;
@@ -1002,64 +992,108 @@ __global__ void __launch_bounds__(kSlabThreads, 1) tc_slab_kernel(const SlabArgs
         __syncwarp();
     } else if (warp >= kSlabEpiWarps) {
         // ---------------------------------------------------------------- producers: A1 from global
-        // Task t covers 8 consecutive x1 of one x2 row: row group gx = (t/8)%16,
-        // x2 = 8*(t/128) + t%8, so eight neighbouring lanes fill one core matrix
-        // (128 contiguous bytes) and read eight 32-byte row pieces.
         const int ptid = tid - kSlabEpiWarps * 32;
         const int ntask = 16 * np2;  // 16 row groups (x1) x np2 columns (x2)
         const int nlines = (int)((n12 * 4) >> 7);  // 128-byte lines of a slice (n1 % 8 == 0)
+        const uint32_t plane_bytes = (uint32_t)(n12 * 4);
         auto plane = [&](int it) {
             const long long u = blockIdx.x + (long long)it * gridDim.x;
             const long long item = (unsigned)u / (unsigned)a.n3, k3 = (unsigned)u % (unsigned)a.n3;
             return a.in + item * a.N + k3 * n12;
         };
+        // stage_in: one thread copies the plane of the next unit into shared memory
+        // (pieces of at most 16 KB) as soon as the previous plane has been split
+        auto issue_plane = [&](int it) {
+            ptx::fence_proxy_async_smem();
+            ptx::mbar_arrive_expect_tx(&bars.in_full, plane_bytes);
+            const char *src = reinterpret_cast<const char *>(plane(it));
+            char *dst = reinterpret_cast<char *>(sin);
+            for (uint32_t o = 0; o < plane_bytes; o += 16384u)
+                ptx::bulk_load(dst + o, src + o, min(16384u, plane_bytes - o), &bars.in_full);
+        };
+        int inflight = -1;  // unit whose plane copy thread 0 issued and has not yet waited for
+        if (a.stage_in && ptid == 0 && n_my > 0) {
+            issue_plane(0);
+            inflight = 0;
+        }
         for (int it = 0; it < n_my; ++it) {
-            const int bi = it % kSlabBufs;
+            const int sl = it & 1;
             if (it + 2 < n_my) {
                 // pull the plane of unit it+2 into L2 while this unit waits for its buffer
                 const char *src = reinterpret_cast<const char *>(plane(it + 2));
                 for (int l = ptid; l < nlines; l += kSlabProdThreads) ptx::prefetch_l2(src + ((long long)l << 7));
             }
             long long tw = KX_CLK_NOW();
-            if (it >= kSlabBufs &&
-                !slab_wait(&bars.empty[bi], (uint32_t)((it / kSlabBufs - 1) & 1), a, &s_abort))
-                break;
+            bool ok = it < 2 || slab_wait(&bars.empty[sl], (uint32_t)(((it >> 1) - 1) & 1), a, &s_abort);
             KX_CLK_ADD(1, tw);
             tw = KX_CLK_NOW();
-            if (s_abort) break;
+            if (ok && a.stage_in) ok = slab_wait(&bars.in_full, (uint32_t)(it & 1), a, &s_abort);
+            if (ok && ptid == 0) inflight = -1;
+            ok = ok && !s_abort;
+            // with stage_in the producers meet at a named barrier below, so they leave together
+            if (a.stage_in) ok = ptx::named_bar_and(2, kSlabProdThreads, ok);
+            if (!ok) break;
             const long long u = blockIdx.x + (long long)it * gridDim.x;
             const long long item = (unsigned)u / (unsigned)a.n3;
             const float sc = ldexpf(1.f, scale_exp(a.in_max[item]));
-            const float *slice = plane(it);
-            uint8_t *Ahi = buf0 + bi * 2 * half_bytes;
+            uint8_t *Ahi = buf0 + sl * 2 * half_bytes;
             uint8_t *Alo = Ahi + half_bytes;
-            for (int t0 = ptid; t0 < ntask; t0 += kSlabProdThreads * kSlabU) {
-                float v[kSlabU][8];
-#pragma unroll
-                for (int r = 0; r < kSlabU; ++r) {
-                    const int t = t0 + r * kSlabProdThreads;
-                    const int gx = (t >> 3) & 15, k = 8 * (t >> 7) + (t & 7);
-                    if (t < ntask && 8 * gx < a.n1 && k < a.n2) {
-                        ld8(slice + (long long)k * a.n1 + 8 * gx, v[r]);
+            if (a.stage_in) {
+#pragma unroll 4
+                for (int t = ptid; t < ntask; t += kSlabProdThreads) {
+                    const int g = t & 15, k = t >> 4;
+                    float v[8];
+                    if (8 * g < a.n1 && k < a.n2) {
+                        const float4 *src = reinterpret_cast<const float4 *>(sin + k * a.n1 + 8 * g);
+                        const float4 x0 = src[0], x1 = src[1];
+                        v[0] = x0.x * sc; v[1] = x0.y * sc; v[2] = x0.z * sc; v[3] = x0.w * sc;
+                        v[4] = x1.x * sc; v[5] = x1.y * sc; v[6] = x1.z * sc; v[7] = x1.w * sc;
                     } else {
 #pragma unroll
-                        for (int c = 0; c < 8; ++c) v[r][c] = 0.f;
+                        for (int c = 0; c < 8; ++c) v[c] = 0.f;
+                    }
+                    store_split8(Ahi, Alo, g * kCoreStride + (k >> 3) * (16 * kCoreStride) + (k & 7) * 16, v);
+                }
+                ptx::fence_proxy_async_smem();
+                ptx::mbar_arrive(&bars.full[sl]);
+                // every producer has finished reading the plane: it may be overwritten
+                ptx::named_bar(2, kSlabProdThreads);
+                if (ptid == 0 && it + 1 < n_my) {
+                    issue_plane(it + 1);
+                    inflight = it + 1;
+                }
+            } else {
+                const float *slice = plane(it);
+                for (int t0 = ptid; t0 < ntask; t0 += kSlabProdThreads * kSlabU) {
+                    float v[kSlabU][8];
+#pragma unroll
+                    for (int r = 0; r < kSlabU; ++r) {
+                        const int t = t0 + r * kSlabProdThreads;
+                        const int g = t & 15, k = t >> 4;
+                        if (t < ntask && 8 * g < a.n1 && k < a.n2) {
+                            ld8(slice + (long long)k * a.n1 + 8 * g, v[r]);
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < 8; ++c) v[r][c] = 0.f;
+                        }
+                    }
+#pragma unroll
+                    for (int r = 0; r < kSlabU; ++r) {
+                        const int t = t0 + r * kSlabProdThreads;
+                        if (t >= ntask) continue;
+                        const int g = t & 15, k = t >> 4;
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) v[r][c] *= sc;
+                        store_split8(Ahi, Alo, g * kCoreStride + (k >> 3) * (16 * kCoreStride) + (k & 7) * 16, v[r]);
                     }
                 }
-#pragma unroll
-                for (int r = 0; r < kSlabU; ++r) {
-                    const int t = t0 + r * kSlabProdThreads;
-                    if (t >= ntask) continue;
-                    const int gx = (t >> 3) & 15, k = 8 * (t >> 7) + (t & 7);
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) v[r][c] *= sc;
-                    store_split8(Ahi, Alo, gx * kSlabCore + (k >> 3) * (16 * kSlabCore) + (k & 7) * 16, v[r]);
-                }
+                ptx::fence_proxy_async_smem();
+                ptx::mbar_arrive(&bars.full[sl]);
             }
-            ptx::fence_proxy_async_smem();
-            ptx::mbar_arrive(&bars.full[bi]);
             KX_CLK_ADD(2, tw);
         }
+        // a plane copy still in flight after an early exit must land before the CTA leaves
+        if (inflight >= 0) ptx::mbar_wait_bounded(&bars.in_full, (uint32_t)(inflight & 1), a.timeout_cycles);
     } else {
         // ---------------------------------------------------------------- epilogue: group g = warp / 8
         // Warp w of a group reads TMEM lanes 32*(w%4).. (its D rows) and the
@@ -1071,11 +1105,11 @@ __global__ void __launch_bounds__(kSlabThreads, 1) tc_slab_kernel(const SlabArgs
         const int nkc1 = np1 >> 3;
         const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(g * 2 * npm);
         const uint32_t tb = ta + (uint32_t)npm;
+        uint8_t *Ahi = buf0 + g * 2 * half_bytes;
+        uint8_t *Alo = Ahi + half_bytes;
         double e_acc = 0.0;
         bool ok = true;
         for (int j = g; j < n_my && ok; j += 2) {
-            uint8_t *Ahi = buf0 + (j % kSlabBufs) * 2 * half_bytes;
-            uint8_t *Alo = Ahi + half_bytes;
             long long tw = KX_CLK_NOW();
             const SlabUnit U = slab_unit(a, blockIdx.x + (long long)j * gridDim.x);
             KX_CLK_ADD(0, tw);
@@ -1118,7 +1152,7 @@ __global__ void __launch_bounds__(kSlabThreads, 1) tc_slab_kernel(const SlabArgs
                 ptx::tc_fence_after();
                 const float u2 = ldexpf(1.f, -(U.e2 + kVScaleExp));
                 const float s3 = ldexpf(1.f, U.e3);
-                const int off_r = (m >> 3) * (nkc1 * kSlabCore) + (m & 7) * 16;
+                const int off_r = (m >> 3) * (nkc1 * kCoreStride) + (m & 7) * 16;
                 float e_row = 0.f;
 #pragma unroll
                 for (int r = 0; r < kMaxN / 32; ++r) {
@@ -1153,7 +1187,7 @@ __global__ void __launch_bounds__(kSlabThreads, 1) tc_slab_kernel(const SlabArgs
                     }
 #pragma unroll
                     for (int hh = 0; hh < 2; ++hh)
-                        store_split8(Ahi, Alo, off_r + ((c >> 3) + hh) * kSlabCore, v + 8 * hh);
+                        store_split8(Ahi, Alo, off_r + ((c >> 3) + hh) * kCoreStride, v + 8 * hh);
                 }
                 if (rowC) e_acc += U.w * (double)e_row;
                 ptx::fence_proxy_async_smem();
@@ -1416,10 +1450,10 @@ int launch_pass(const kx_plan *p, PassArgs a, int axis, cudaStream_t s, int *gri
 
 size_t slab_smem(const kx_plan *p) {
     const int np1 = p->np[0], np2 = p->np[1], npm = std::max(np1, np2);
-    return (size_t)4 * np1 * np1 + (size_t)4 * np2 * np2 + 2 * kSlabBufs * slab_half_bytes(npm) + 1024;
+    return (size_t)4 * np1 * np1 + (size_t)4 * np2 * np2 + 4 * a_half_bytes(npm) + 1024;
 }
 
-// The slab kernel holds V1, V2 and kSlabBufs split A buffers in shared memory.
+// The slab kernel holds V1, V2 and two split A buffers in shared memory.
 constexpr size_t kSlabSmemMax = 227 * 1024 - 1024;  // opt-in maximum less static shared memory
 bool slab_fits(const kx_plan *p) { return slab_smem(p) <= kSlabSmemMax; }
 
@@ -1462,8 +1496,12 @@ int launch_slab(kx_plan *p, long R, const float *in, const float *in_max, float 
     if (!g_clkbuf) cudaMallocManaged(&g_clkbuf, sizeof(long long) * kClk * 4096 * 6);
     a.clk = g_clkbuf + 5LL * kClk * 4096;
 #endif
+    size_t smem = slab_smem(p);
+    const size_t plane = (size_t)a.n1 * a.n2 * 4;
+    a.stage_in = (smem + plane <= kSlabSmemMax) ? 1 : 0;
+    if (a.stage_in) smem += plane;
     // at least 120 KB so that one CTA (and one 512-column TMEM allocation) sits on each SM
-    const size_t smem = std::max<size_t>(slab_smem(p), 120 * 1024);
+    smem = std::max<size_t>(smem, 120 * 1024);
     KX_CUDA_TRY(cudaFuncSetAttribute(tc_slab_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = (int)std::max(1LL, std::min<long long>(a.total_units, (long long)p->num_sms));
     if (grid_out) *grid_out = grid;

@@ -267,3 +267,14 @@ def ace(plan: Plan, psi: np.ndarray, vx_psi: np.ndarray):
     R = np.linalg.cholesky(-M).T            # upper triangular, R^T R = -M
     xi = np.linalg.solve(R.T, W.T).T        # xi = W R^{-1}
     return xi, M, R
+
+
+def ace_apply(plan: Plan, xi: np.ndarray, phi: np.ndarray) -> np.ndarray:
+    """The compressed exchange operator applied to vectors: V_ACE phi = -xi (dV xi^T phi).
+
+    xi: N x n_xi (from ace), phi: N x n_vec; returns N x n_vec.  On the occupied
+    orbitals V_ACE Psi equals Vx Psi, which is what lets an SCF loop use V_ACE
+    in place of Vx between rebuilds (the ACE construction Sec. 4 cites).
+    """
+    P = plan.dV * (xi.T @ phi)              # projections of phi on xi (dV inner product)
+    return -(xi @ P)

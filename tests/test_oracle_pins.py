@@ -424,3 +424,31 @@ def test_ace_reproduces_vx_on_occupied_space():
     assert np.max(np.abs(R.T @ R + M)) < 1e-12 * np.abs(M).max()
     Vace_psi = -xi @ (plan.dV * xi.T @ psi)
     assert np.max(np.abs(Vace_psi - vx)) < 1e-11 * np.abs(vx).max()
+
+
+def test_ace_apply_is_vx_on_occupied_space_and_projector_elsewhere():
+    """V_ACE = -xi (dV xi^T .) must give Vx Psi on the orbitals (checked against the
+    pair-by-pair Vx apply, not against a retyped formula), be symmetric and
+    negative semidefinite in the dV inner product, and vanish on every vector
+    dV-orthogonal to span(Vx Psi)."""
+    psi, sysd = small_orbitals((8, 7, 6), (0.5,) * 3, (D, P, D), 5, 73)
+    plan = oracle.Plan(sysd.n, sysd.h, sysd.bc, S)
+    vx, _ = oracle.vx_apply(plan, psi)
+    xi, M, _ = oracle.ace(plan, psi, vx)
+    assert np.max(np.abs(oracle.ace_apply(plan, xi, psi) - vx)) < 1e-11 * np.abs(vx).max()
+    # on the occupied space V_ACE has the matrix elements of Vx
+    Vp = oracle.ace_apply(plan, xi, psi)
+    assert np.max(np.abs(plan.dV * psi.T @ Vp - M)) < 1e-11 * np.abs(M).max()
+    rng = np.random.default_rng(9)
+    a, b = rng.standard_normal((plan.N, 3)), rng.standard_normal((plan.N, 3))
+    Va, Vb = oracle.ace_apply(plan, xi, a), oracle.ace_apply(plan, xi, b)
+    lhs, rhs = a.T @ Vb, Va.T @ b
+    assert np.max(np.abs(lhs - rhs)) < 1e-12 * np.abs(lhs).max()
+    assert np.all(np.diag(b.T @ Vb) <= 0.0)
+    # component of b orthogonal to span(vx): least-squares residual, independent of xi
+    coef, *_ = np.linalg.lstsq(vx, b, rcond=None)
+    b_perp = b - vx @ coef
+    assert np.max(np.abs(oracle.ace_apply(plan, xi, b_perp))) < 1e-11 * np.abs(Vb).max()
+    # rank: at most n_orb nonzero singular values
+    sv = np.linalg.svd(oracle.ace_apply(plan, xi, rng.standard_normal((plan.N, 12))), compute_uv=False)
+    assert np.all(sv[psi.shape[1]:] < 1e-11 * sv[0])

@@ -308,6 +308,50 @@ def other_workloads(kx, torch, stream, steps=3):
     return res
 
 
+def ace_legs(kx, torch, stream, plan, psi, vx, hbm, steps=5):
+    """The ACE tail and the compressed operator on the headline system: xi from
+    (psi, Vx psi) with kx_ace, then V_ACE applied to the orbitals with
+    kx_ace_apply.  The apply reads xi and phi for the projections and xi again
+    for the combination and writes out: 16 N (n_xi + n_vec) bytes, its HBM
+    roofline.  Errors are against the float64 plan on the same xi and psi, and
+    the ACE property V_ACE psi = Vx psi."""
+    n_orb, N = psi.shape
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    xi, _ = kx.kx_ace(plan, psi, vx)  # first call reserves the workspace
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        xi, _ = kx.kx_ace(plan, psi, vx)  # synchronises (reads the Cholesky flag)
+    ms_ace = 1e3 * (time.perf_counter() - t0) / steps
+    out = torch.empty_like(psi)
+    kx.kx_ace_apply(plan, xi, psi, out=out, stream=stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        kx.kx_ace_apply(plan, xi, psi, out=out, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_apply = e0.elapsed_time(e1) / steps
+    plan64 = kx.Plan.for_system(SYS, precision=kx.KX_FP64)
+    out64 = torch.empty_like(psi)
+    kx.kx_ace_apply(plan64, xi, psi, out=out64, stream=stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    kx.kx_ace_apply(plan64, xi, psi, out=out64, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1)
+    bytes_apply = 16.0 * N * (n_orb + n_orb)
+    gbs = bytes_apply / (ms_apply / 1e3) / 1e9
+    return {"ace_build_ms": ms_ace,
+            "ace_apply_ms": ms_apply, "ace_apply_fp64_ms": ms64, "speedup_vs_fp64": ms64 / ms_apply,
+            "ace_apply_roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                                   "algorithmic_bytes": bytes_apply},
+            "ace_apply_maxrel_vs_fp64_gpu": float((out - out64).abs().max() / out64.abs().max()),
+            "ace_psi_vs_vx_psi_maxrel": float((out - vx).abs().max() / vx.abs().max()),
+            "n_xi": n_orb, "n_vec": n_orb}
+
+
 def issued_tensor_flops_per_pair(n, fused=True):
     """Tensor-core flops the split path issues per pair: three fp16 products per
     mode product, M padded to 128-row tiles, K and N padded to multiples of 16."""
@@ -459,6 +503,7 @@ def main():
         dt = time.perf_counter() - t0
         out["e2e"] = {"value": P * k_e2e / dt, "unit": UNIT, "h2d_bytes_per_step": psi_pin.numel() * 8,
                       "d2h_bytes_per_step": vx_pin.numel() * 8 + 8, "ms_per_step": 1e3 * dt / k_e2e}
+        out["ace"] = ace_legs(kx, torch, stream, plan, psi, vx_split, hbm)
         out["other_workloads"] = other_workloads(kx, torch, stream)
         line, done, vx_ref, ex_ref = cpu_baseline(psi_h)
         out["cpu_baseline"] = line

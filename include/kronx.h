@@ -192,10 +192,30 @@ int kx_energy(kx_plan *plan, int n_orb, const double *psi, const double *occ, do
  *   psi, vx_psi  inputs (n_orb grid vectors each).
  *   xi           out: n_orb grid vectors; must not overlap the inputs.
  *   M_out        out (nullable): n_orb*n_orb float64, row-major, M before factoring.
+ * M, its Cholesky factor and R^{-1} are float64; the grid-sized products
+ * (Psi^T W and W R^{-1}) are float64 for KX_FP64 plans and float32 products
+ * with float64 sums across blocks of grid points for KX_F16X3 plans.
  * Returns KX_ERR_ARG if -M is not positive definite (detected on the GPU; the
  * call then synchronises the stream to read the flag).  1 <= n_orb <= 256. */
 int kx_ace(kx_plan *plan, int n_orb, const double *psi, const double *vx_psi, double *xi,
            double *M_out, kx_stream stream);
+
+/* kx_ace_apply — the compressed exchange operator built by kx_ace applied to
+ * vectors (the ACE construction Sec. 4 cites):
+ *   out = -xi (dV xi^T phi),
+ * which equals Vx phi for phi in the span of the orbitals xi was built from,
+ * so an SCF loop can use it in place of Vx between rebuilds.
+ *   xi    in: n_xi grid vectors (device), as written by kx_ace.
+ *   phi   in: n_vec grid vectors (device).
+ *   out   out: n_vec grid vectors (device); must not overlap xi or phi.
+ * The projections dV xi^T phi (n_xi x n_vec) are summed in float64.  The
+ * grid-sized products run in float64 for KX_FP64 plans and as float32
+ * products with float64 sums across blocks of grid points for KX_F16X3
+ * plans (relative error ~1e-7 of the largest entry).  Queued on the stream,
+ * no host synchronisation.  1 <= n_xi <= 256, n_vec >= 1; KX_ERR_ARG
+ * otherwise. */
+int kx_ace_apply(kx_plan *plan, int n_xi, const double *xi, int n_vec, const double *phi, double *out,
+                 kx_stream stream);
 
 /* kx_batch_create — groups n_sys plans (different grids, kernels and orbital
  * counts) into one CUDA graph that runs every system's kx_vx_apply.  Workspaces

@@ -45,6 +45,7 @@ SIGNATURES = {
     "kx_vx_apply_pairs": (_c_int, [_vp, _c_int, _vp, _vp, _ll, _ll, _vp, _vp, _vp]),
     "kx_energy": (_c_int, [_vp, _c_int, _vp, _vp, _vp, _vp]),
     "kx_ace": (_c_int, [_vp, _c_int, _vp, _vp, _vp, _vp, _vp]),
+    "kx_ace_apply": (_c_int, [_vp, _c_int, _vp, _c_int, _vp, _vp, _vp]),
     "kx_batch_create": (_c_int, [_c_int, _vp, _vp, ctypes.POINTER(_vp)]),
     "kx_batch_run": (_c_int, [_vp, _vp, _vp, _vp, _vp]),
     "kx_batch_destroy": (_c_int, [_vp]),
@@ -291,6 +292,18 @@ def kx_ace(plan: Plan, psi, vx_psi, stream=None):
                         _dptr(vx_psi, "vx_psi", torch.float64, (n_orb, plan.N)), _dptr(xi, "xi"),
                         _dptr(M, "M"), _stream(stream)))
     return xi, M
+
+
+def kx_ace_apply(plan: Plan, xi, phi, out=None, stream=None):
+    """V_ACE phi = -xi (dV xi^T phi) for the n_vec grid vectors phi (rows of a float64 tensor)."""
+    torch = _torch()
+    n_xi, n_vec = xi.shape[0], phi.shape[0]
+    if out is None:
+        out = torch.empty_like(phi)
+    _check(lib().kx_ace_apply(plan.handle, n_xi, _dptr(xi, "xi", torch.float64, (n_xi, plan.N)), n_vec,
+                              _dptr(phi, "phi", torch.float64, (n_vec, plan.N)),
+                              _dptr(out, "out", torch.float64, (n_vec, plan.N)), _stream(stream)))
+    return out
 
 
 def kx_autotune(plan: Plan, n_orb: int, budget_ms: int = 2000):

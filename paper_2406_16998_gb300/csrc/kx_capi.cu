@@ -445,6 +445,21 @@ int kx_ace(kx_plan *plan, int n_orb, const double *psi, const double *vx_psi, do
     return ace_run(plan, n_orb, psi, vx_psi, xi, M_out, reinterpret_cast<cudaStream_t>(stream));
 }
 
+int kx_ace_apply(kx_plan *plan, int n_xi, const double *xi, int n_vec, const double *phi, double *out,
+                 kx_stream stream) {
+    if (int rc = check_plan(plan)) return rc;
+    if (n_xi < 1 || n_xi > 256) return set_error(KX_ERR_ARG, "kx_ace_apply: n_xi must be in 1..256");
+    if (n_vec < 1) return set_error(KX_ERR_ARG, "kx_ace_apply: n_vec must be >= 1");
+    if (!xi || !phi || !out) return set_error(KX_ERR_ARG, "kx_ace_apply: NULL buffer");
+    const size_t N = plan->N;
+    auto overlaps = [N](const double *a, size_t na, const double *b, size_t nb) {
+        return a < b + nb * N && b < a + na * N;
+    };
+    if (overlaps(out, (size_t)n_vec, xi, (size_t)n_xi) || overlaps(out, (size_t)n_vec, phi, (size_t)n_vec))
+        return set_error(KX_ERR_ARG, "kx_ace_apply: out must not overlap xi or phi");
+    return ace_apply_run(plan, n_xi, xi, n_vec, phi, out, reinterpret_cast<cudaStream_t>(stream));
+}
+
 int kx_plan_status(kx_plan *plan, int *status_out, kx_stream stream) {
     if (int rc = check_plan(plan)) return rc;
     if (!status_out) return set_error(KX_ERR_ARG, "kx_plan_status: NULL output");

@@ -160,5 +160,7 @@ int tc_apply_fL_noalloc(kx_plan *p, int n_rhs, const double *b, double *x, cudaS
 // ---- ACE tail (kx_ace.cu)
 int ace_run(kx_plan *p, int n_orb, const double *psi, const double *W, double *xi, double *M_out,
             cudaStream_t s);
+int ace_apply_run(kx_plan *p, int n_xi, const double *xi, int n_vec, const double *phi, double *out,
+                  cudaStream_t s);
 
 }  // namespace kx

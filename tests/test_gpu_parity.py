@@ -208,6 +208,83 @@ def test_ace_matches_oracle(kx):
     assert relmax(xi.cpu().numpy().T, xi_ref) < 1e-10
 
 
+def test_ace_f16x3_plan_matches_oracle(kx):
+    """The tensor-core plan's ACE tail: float32 products, float64 block sums and
+    float64 Cholesky; M to 1e-6 and xi to 1e-5 of their largest entries."""
+    n, h, bc, kind, n_orb = SMALL[1]
+    sysd = system(n, h, bc, kind, n_orb, 37)
+    psi = workloads.make_orbitals(sysd)
+    op = oracle.Plan(n, h, bc, kind)
+    vx_ref, _ = oracle.vx_apply(op, psi)
+    xi_ref, M_ref, _ = oracle.ace(op, psi, vx_ref)
+    plan = kx.Plan(n, h, bc, kind, precision=1)
+    xi, M = kx.kx_ace(plan, dev(psi.T), dev(vx_ref.T))
+    assert relmax(M.cpu().numpy(), M_ref) < 1e-6
+    assert relmax(xi.cpu().numpy().T, xi_ref) < 1e-5
+
+
+# n (grid), precision, n_xi, n_vec: ragged grids (float64 plan), several
+# projection and combination tiles, single vectors
+ACE_APPLY_CASES = [
+    ((13, 11, 7), 0, 1, 1),
+    ((13, 11, 7), 0, 7, 33),
+    ((24, 40, 16), 0, 65, 70),
+    ((24, 40, 16), 1, 1, 1),
+    ((24, 40, 16), 1, 7, 33),
+    ((24, 40, 16), 1, 64, 64),
+    ((32, 16, 40), 1, 65, 130),
+    ((16, 8, 8), 1, 200, 3),
+]
+
+
+@pytest.mark.parametrize("n,prec,n_xi,n_vec", ACE_APPLY_CASES)
+def test_ace_apply_matches_oracle(kx, n, prec, n_xi, n_vec):
+    """-xi (dV xi^T phi) on seeded inputs against the float64 oracle: 1e-12 for
+    float64 plans, 2e-6 (float32 products) for tensor-core plans."""
+    h, bc = (0.4, 0.45, 0.5), (D, P, D)
+    op = oracle.Plan(n, h, bc, U)
+    xi = workloads.random_field(op.N, n_xi, 101 + n_xi) * 0.3
+    phi = workloads.random_field(op.N, n_vec, 202 + n_vec)
+    ref = oracle.ace_apply(op, xi, phi)
+    plan = kx.Plan(n, h, bc, U, precision=prec)
+    out = kx.kx_ace_apply(plan, dev(xi.T), dev(phi.T))
+    tol = 1e-12 if prec == 0 else 2e-6
+    assert relmax(out.cpu().numpy().T, ref) < tol
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_ace_operator_reproduces_vx_on_orbitals(kx, prec):
+    """kx_ace then kx_ace_apply on the orbitals gives back Vx psi (the property
+    the compressed operator is built for), against the oracle's pair-by-pair Vx."""
+    n, h, bc, kind, n_orb = SMALL[2]
+    sysd = system(n, h, bc, kind, n_orb, 43)
+    psi = workloads.make_orbitals(sysd)
+    op = oracle.Plan(n, h, bc, kind)
+    vx_ref, _ = oracle.vx_apply(op, psi)
+    plan = kx.Plan(n, h, bc, kind, precision=prec)
+    psi_d = dev(psi.T)
+    xi, _ = kx.kx_ace(plan, psi_d, dev(vx_ref.T))
+    out = kx.kx_ace_apply(plan, xi, psi_d)
+    assert relmax(out.cpu().numpy().T, vx_ref) < (1e-10 if prec == 0 else 1e-5)
+
+
+def test_ace_apply_rejects_bad_arguments(kx):
+    n, h, bc = (16, 8, 8), (0.5,) * 3, (D, D, D)
+    plan = kx.Plan(n, h, bc, U, precision=1)
+    xi = dev(workloads.random_field(plan.N, 3, 1).T)
+    phi = dev(workloads.random_field(plan.N, 2, 2).T)
+    with pytest.raises(kx.KxError) as ei:
+        kx.kx_ace_apply(plan, xi, phi, out=phi)  # out overlaps phi
+    assert ei.value.code == kx.KX_ERR_ARG
+    with pytest.raises(kx.KxError) as ei:
+        kx.kx_ace_apply(plan, xi, phi, out=xi[:2])  # out overlaps xi
+    assert ei.value.code == kx.KX_ERR_ARG
+    big = dev(workloads.random_field(plan.N, 257, 3).T)
+    with pytest.raises(kx.KxError) as ei:
+        kx.kx_ace_apply(plan, big, phi)
+    assert ei.value.code == kx.KX_ERR_ARG
+
+
 def test_batch_equals_individual_runs(kx):
     cases = [SMALL[0], SMALL[2], SMALL[3]]
     plans, psis, refs = [], [], []
@@ -323,6 +400,29 @@ def test_full_size_sampled(kx, name, sample):
     for i in sample:
         ref = _row_reference(op, psi, i)
         assert np.max(np.abs(vx_h[i] - ref)) < 1e-5 * scale
+
+
+def test_ace_full_size(kx):
+    """The ACE tail and the compressed operator at the benchmark's size (96^3,
+    64 orbitals, tensor-core plan) against the oracle on the whole output:
+    W = -psi S with S symmetric positive definite (so -M is), xi from the
+    oracle's construction as the apply's input."""
+    sysd = workloads.C2
+    psi = workloads.make_orbitals(sysd)
+    op = oracle.Plan(sysd.n, sysd.h, sysd.bc, sysd.kernel, sysd.omega)
+    rng = np.random.default_rng(77)
+    Q, _ = np.linalg.qr(rng.standard_normal((sysd.n_orb, sysd.n_orb)))
+    S_mat = (Q * rng.uniform(0.5, 2.0, sysd.n_orb)) @ Q.T
+    W = -psi @ S_mat
+    xi_ref, M_ref, _ = oracle.ace(op, psi, W)
+    ref = oracle.ace_apply(op, xi_ref, psi)
+    plan = kx.Plan.for_system(sysd, precision=1)
+    psi_d = dev(psi.T)
+    xi, M = kx.kx_ace(plan, psi_d, dev(W.T))
+    assert relmax(M.cpu().numpy(), M_ref) < 1e-6
+    assert relmax(xi.cpu().numpy().T, xi_ref) < 1e-5
+    out = kx.kx_ace_apply(plan, dev(xi_ref.T), psi_d)
+    assert relmax(out.cpu().numpy().T, ref) < 2e-6
 
 
 @pytest.mark.parametrize("prec", [0, 1])

@@ -332,6 +332,12 @@ def ace_legs(kx, torch, stream, plan, psi, vx, hbm, steps=5):
     e1.record(stream)
     torch.cuda.synchronize()
     ms_apply = e0.elapsed_time(e1) / steps
+    plan.profile(True)
+    kx.kx_ace_apply(plan, xi, psi, out=out, stream=stream)
+    prof = plan.profile_read()
+    plan.profile(False)
+    kernels = {"projection_ms": prof["ace"][0], "combination_ms": prof["ace_comb"][0],
+               "launches": prof["ace"][1] + prof["ace_comb"][1]}
     plan64 = kx.Plan.for_system(SYS, precision=kx.KX_FP64)
     out64 = torch.empty_like(psi)
     kx.kx_ace_apply(plan64, xi, psi, out=out64, stream=stream)
@@ -344,7 +350,8 @@ def ace_legs(kx, torch, stream, plan, psi, vx, hbm, steps=5):
     bytes_apply = 16.0 * N * (n_orb + n_orb)
     gbs = bytes_apply / (ms_apply / 1e3) / 1e9
     return {"ace_build_ms": ms_ace,
-            "ace_apply_ms": ms_apply, "ace_apply_fp64_ms": ms64, "speedup_vs_fp64": ms64 / ms_apply,
+            "ace_apply_ms": ms_apply, "ace_apply_kernels": kernels, "ace_apply_fp64_ms": ms64,
+            "speedup_vs_fp64": ms64 / ms_apply,
             "ace_apply_roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
                                    "algorithmic_bytes": bytes_apply},
             "ace_apply_maxrel_vs_fp64_gpu": float((out - out64).abs().max() / out64.abs().max()),

@@ -261,9 +261,11 @@ int kx_profile(kx_plan *plan, int enable);
  * mode 3 forward), 2 X2F (mode 2 forward), 3 X1 (mode 1 forward, f(Lambda)
  * scaling and energy, mode 1 inverse), 4 X2I (mode 2 inverse), 5 X3I (mode 3
  * inverse and Vx psi accumulation), 6 finalize/energy sums, 7 float64 mode
- * products, 8 other float64 kernels, 9 ACE, 10 set-up, 11 accumulation of
+ * products, 8 other float64 kernels, 9 ACE projections, 10 set-up, 11 accumulation of
  * g psi phi into Vx psi, 12 fused mode 2 forward + X1 + mode 2 inverse per
- * k3 slice (replaces kinds 2-4 where the operands fit in shared memory).
+ * k3 slice (replaces kinds 2-4 where the operands fit in shared memory),
+ * 13 ACE combinations of grid vectors (xi = W R^{-1}, -xi P); kind 9 covers
+ * the ACE projections over the grid and their reduction.
  * Synchronises on the recorded events. */
 int kx_profile_read(kx_plan *plan, int n_kinds, double *ms, long long *launches);
 

@@ -14,8 +14,10 @@
 // this GPU runs at a small fraction of the float32 rate and both products
 // are bound by memory traffic once they run in float32.
 #include "kx_internal.h"
+#include "kx_tc_ptx.cuh"
 
 #include <algorithm>
+#include <cstdint>
 
 namespace kx {
 namespace {
@@ -151,49 +153,133 @@ __global__ void xi_kernel(const double *__restrict__ W, const double *__restrict
 // ---------------------------------------------------------------------------
 // float32-product forms of the two grid-sized products
 // ---------------------------------------------------------------------------
+// Conversions between float64 and float32 with integer operations: on this
+// GPU the hardware conversions run on the float64 pipe, which is slow enough
+// that they, not memory, would bound the kernels below.  Finite values in the
+// float32 normal range convert as IEEE rounding would, up to the tie rule
+// (half-ulp ties round away from zero); magnitudes below 2^-126 become zero
+// or a float32 subnormal below 2^-146, magnitudes beyond the float32 range a
+// non-finite value.
+__device__ __forceinline__ float f64_to_f32(double d) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+    const unsigned lo = (unsigned)u;
+    unsigned hi = (unsigned)(u >> 32);
+    const unsigned lo_r = lo + 0x10000000u;  // half of the last kept mantissa bit
+    hi += (lo_r < lo) ? 1u : 0u;             // its carry
+    // float64 exponent 896 + e is float32 exponent e: clamp to 0 .. 255, rebias
+    const unsigned ax = min(max(hi & 0x7fffffffu, 896u << 20), 1151u << 20) - (896u << 20);
+    return __uint_as_float((hi & 0x80000000u) | (ax << 3) | (lo_r >> 29));
+}
+
+__device__ __forceinline__ double f32_to_f64(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned sgn = b & 0x80000000u, ax = b & 0x7fffffffu;
+    unsigned hi = sgn, lo = 0u;
+    if (ax >= 0x7f800000u) {
+        hi = sgn | 0x7ff00000u;
+    } else if (ax >= 0x00800000u) {
+        hi = sgn | ((ax >> 3) + (896u << 20));
+        lo = ax << 29;
+    }
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+// (hi, lo) += v with the rounding error of the float32 addition kept in lo.
+__device__ __forceinline__ void two_sum_add(float &hi, float &lo, float v) {
+    const float t = hi + v;
+    const float bp = t - hi;
+    lo += (hi - (t - bp)) + (v - bp);
+    hi = t;
+}
+
 constexpr int kPT = 64;   // projection tile: 64 a x 64 b per CTA
-constexpr int kPX = 64;   // grid points per shared-memory step
-constexpr int kPBlk = 4;  // steps summed in float32 before the float64 accumulation (256 points)
+constexpr int kPX = 32;   // grid points per pipeline step
+constexpr int kPBlk = 8;  // steps summed in float32 before the compensated accumulation (256 points)
+constexpr int kPStages = 2;
+// dynamic shared memory of proj32_kernel (82 KB, two CTAs per SM): raw float64
+// stages of both operands, then their float32 copies (rows padded by 4 floats
+// for conflict-free float4 reads)
+constexpr size_t kProjRawBytes = (size_t)kPStages * 2 * kPT * kPX * sizeof(double);
+constexpr size_t kProjSmem = kProjRawBytes + 2 * (size_t)kPT * (kPX + 4) * sizeof(float);
+
+// Issues the asynchronous copies of grid points [xb, xb + kPX) of rows
+// r0..r0+63 of M (nr rows in all, stride N) into raw[64][kPX]; points at or
+// past xe and rows past nr are zero-filled.  VEC2: 16-byte pieces (N even,
+// xb even), else 8-byte pieces.
+template <bool VEC2>
+__device__ __forceinline__ void proj_issue(const double *__restrict__ M, int nr, int r0, long long N, long long xb,
+                                           long long xe, double *raw, int tid) {
+    constexpr int per_row = VEC2 ? kPX / 2 : kPX;
+#pragma unroll
+    for (int m = 0; m < kPT * per_row / 256; ++m) {
+        const int piece = tid + 256 * m;
+        const int r = piece / per_row, c = (piece % per_row) * (VEC2 ? 2 : 1);
+        const long long x = xb + c;
+        long long nbytes = (r0 + r < nr) ? (xe - x) * 8 : 0;
+        nbytes = nbytes < 0 ? 0 : (nbytes > (VEC2 ? 16 : 8) ? (VEC2 ? 16 : 8) : nbytes);
+        const double *src = nbytes > 0 ? M + (long long)(r0 + r) * N + x : M;
+        if (VEC2)
+            ptx::cp_async16(raw + r * kPX + c, src, (uint32_t)nbytes);
+        else
+            ptx::cp_async8(raw + r * kPX + c, src, (uint32_t)nbytes);
+    }
+}
 
 // part[blockIdx.x][a][b] = sum over the CTA's grid points [x0, x0 + span) of
-// A_a(x) B_b(x) for its 64 x 64 tile (blockIdx.y, blockIdx.z).  Thread (tx, ty)
-// of a 16 x 16 layout owns a = a0 + ty + 16 i, b = b0 + tx + 16 j (i, j < 4):
-// per four grid points it reads four a-rows (two distinct per warp, broadcast)
-// and four b-rows as float4 and does 64 FMAs.
-__global__ void __launch_bounds__(256) proj32_kernel(const double *__restrict__ A, int na,
-                                                     const double *__restrict__ B, int nb, long long N,
-                                                     long long span, double *__restrict__ part) {
-    __shared__ __align__(16) float As[kPT][kPX + 4];
-    __shared__ __align__(16) float Bs[kPT][kPX + 4];
+// A_a(x) B_b(x) for its 64 x 64 tile (blockIdx.y, blockIdx.z); two CTAs per SM.
+// The float64 inputs of step k+1 are copied into shared memory (cp.async)
+// while step k is converted to float32 and multiplied, so the SM always has a
+// step's loads in flight.  Thread (tx, ty) of a 16 x 16 layout owns
+// a = a0 + ty + 16 i, b = b0 + tx + 16 j (i, j < 4): per four grid points it
+// reads four a-rows (two distinct per warp, broadcast) and four b-rows as
+// float4 and does 64 FMAs.  Each block of 256 points is summed in float32 and
+// added to a float32 pair (sum and rounding error), so the CTA's total keeps
+// about 48 bits.
+template <bool VEC2>
+__global__ void __launch_bounds__(256, 2) proj32_kernel(const double *__restrict__ A, int na,
+                                                        const double *__restrict__ B, int nb, long long N,
+                                                        long long span, double *__restrict__ part) {
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    double *raw = reinterpret_cast<double *>(smem_raw);  // [stage][A|B][64][kPX]
+    float(*As)[kPX + 4] = reinterpret_cast<float(*)[kPX + 4]>(smem_raw + kProjRawBytes);
+    float(*Bs)[kPX + 4] = As + kPT;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int a0 = blockIdx.y * kPT, b0 = blockIdx.z * kPT;
     const long long x0 = (long long)blockIdx.x * span;
     const long long x1 = min(N, x0 + span);
-    double acc[4][4];
-    float s[4][4];
+    const int nsteps = x1 > x0 ? (int)((x1 - x0 + kPX - 1) / kPX) : 0;
+    float acc_hi[4][4], acc_lo[4][4], s[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            acc[i][j] = 0.0;
+            acc_hi[i][j] = 0.f;
+            acc_lo[i][j] = 0.f;
             s[i][j] = 0.f;
         }
-    const int lx = tid & 63, lr = tid >> 6;  // loader: one grid point, rows lr + 4k
-    int steps = 0;
-    for (long long xb = x0; xb < x1; xb += kPX) {
-        const long long x = xb + lx;
-        const bool okx = x < x1;
-        float va[16], vb[16];
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            const int r = lr + 4 * k;
-            va[k] = (okx && a0 + r < na) ? (float)__ldg(A + (long long)(a0 + r) * N + x) : 0.f;
-            vb[k] = (okx && b0 + r < nb) ? (float)__ldg(B + (long long)(b0 + r) * N + x) : 0.f;
+    auto stage = [&](int k) { return raw + (size_t)(k % kPStages) * 2 * kPT * kPX; };
+    if (nsteps > 0) {
+        proj_issue<VEC2>(A, na, a0, N, x0, x1, stage(0), tid);
+        proj_issue<VEC2>(B, nb, b0, N, x0, x1, stage(0) + kPT * kPX, tid);
+    }
+    ptx::cp_async_commit();
+    const int lx = tid & 31, lr = tid >> 5;  // converter: one grid point, rows lr + 8m
+    int blk = 0;
+    for (int k = 0; k < nsteps; ++k) {
+        if (k + 1 < nsteps) {
+            const long long xb = x0 + (long long)(k + 1) * kPX;
+            proj_issue<VEC2>(A, na, a0, N, xb, x1, stage(k + 1), tid);
+            proj_issue<VEC2>(B, nb, b0, N, xb, x1, stage(k + 1) + kPT * kPX, tid);
         }
+        ptx::cp_async_commit();
+        ptx::cp_async_wait<1>();  // this thread's copies of step k have landed
+        __syncthreads();          // everyone's have; the float32 tiles are free
+        const double *ra = stage(k), *rb = stage(k) + kPT * kPX;
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            As[lr + 4 * k][lx] = va[k];
-            Bs[lr + 4 * k][lx] = vb[k];
+        for (int m = 0; m < 8; ++m) {
+            const int r = lr + 8 * m;
+            As[r][lx] = f64_to_f32(ra[r * kPX + lx]);
+            Bs[r][lx] = f64_to_f32(rb[r * kPX + lx]);
         }
         __syncthreads();
 #pragma unroll 2
@@ -213,134 +299,210 @@ __global__ void __launch_bounds__(256) proj32_kernel(const double *__restrict__ 
                     s[i][j] = fmaf(av[i].w, bv[j].w, s[i][j]);
                 }
         }
-        __syncthreads();
-        if (++steps == kPBlk) {
-            steps = 0;
+        if (++blk == kPBlk) {
+            blk = 0;
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    acc[i][j] += (double)s[i][j];
+                    two_sum_add(acc_hi[i][j], acc_lo[i][j], s[i][j]);
                     s[i][j] = 0.f;
                 }
         }
     }
+    ptx::cp_async_wait<0>();
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int a = a0 + ty + 16 * i, b = b0 + tx + 16 * j;
-            if (a < na && b < nb) part[((long long)blockIdx.x * na + a) * nb + b] = acc[i][j] + (double)s[i][j];
+            if (a < na && b < nb) {
+                two_sum_add(acc_hi[i][j], acc_lo[i][j], s[i][j]);
+                part[((long long)blockIdx.x * na + a) * nb + b] = f32_to_f64(acc_hi[i][j]) + f32_to_f64(acc_lo[i][j]);
+            }
         }
 }
 
-constexpr int kCX = 128;  // combination tile: 128 grid points x 64 output vectors per CTA
+constexpr int kCX = 128;  // combination tile: 128 grid points x 64 output vectors
 constexpr int kCB = 64;
-constexpr int kCA = 32;   // input vectors per shared-memory step
+constexpr int kCA = 16;   // input vectors per pipeline step
+constexpr int kCStages = 3;
+constexpr size_t kCombRawBytes = (size_t)kCStages * kCA * kCX * sizeof(double);
+// dynamic shared memory: raw float64 stages, the float32 step tile, then C (na rows x 64, float32);
+// up to 88 KB (two CTAs per SM) for na <= 128
+__host__ __device__ constexpr size_t comb_smem(int na) {
+    return kCombRawBytes + (size_t)kCA * kCX * sizeof(float) + (size_t)((na + kCA - 1) / kCA) * kCA * kCB * sizeof(float);
+}
 
 // out_b(x) = sgn sum_a A_a(x) C[a][b]   (a < na, b < nb; C row-major na x nb).
-// Thread (tx, ty) of a 32 x 8 layout owns x = x0 + tx + 32 k (k < 4) and
-// b = b0 + 8 ty + j (j < 8): the C row piece it needs is the same for the
-// whole warp (two broadcast float4 reads), the A values are consecutive
-// across lanes.  Sums over a stay in float32 (na <= 256 terms).
-__global__ void __launch_bounds__(256) combine32_kernel(const double *__restrict__ A, int na,
-                                                        const double *__restrict__ C, int nb, long long N, double sgn,
-                                                        double *__restrict__ out) {
-    __shared__ __align__(16) float As[kCA][kCX];
-    __shared__ __align__(16) float Cs[kCA][kCB];
+// CTA (blockIdx.x, blockIdx.y) owns output vectors b0 = 64 blockIdx.y .. +63
+// and walks the 128-point tiles blockIdx.x, + gridDim.x, ...; each tile takes
+// ceil(na / 16) steps of 16 input vectors, whose float64 rows are copied into
+// shared memory two steps ahead (cp.async).  Thread (tx, ty) of a 32 x 8
+// layout owns x = tile + tx + 32 k (k < 4) and b = b0 + 8 ty + j (j < 8): the
+// C row piece it needs is the same for the whole warp (two broadcast float4
+// reads), the A values are consecutive across lanes.  Sums over a stay in
+// float32 (na <= 256 terms).
+template <bool VEC2>
+__global__ void __launch_bounds__(256, 2) combine32_kernel(const double *__restrict__ A, int na,
+                                                           const double *__restrict__ C, int nb, long long N,
+                                                           float sgn, double *__restrict__ out) {
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    double *raw = reinterpret_cast<double *>(smem_raw);  // [stage][kCA][kCX]
+    float(*As)[kCX] = reinterpret_cast<float(*)[kCX]>(smem_raw + kCombRawBytes);
+    float(*Cs)[kCB] = reinterpret_cast<float(*)[kCB]>(smem_raw + kCombRawBytes + (size_t)kCA * kCX * sizeof(float));
     const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
-    const long long x0 = (long long)blockIdx.x * kCX;
     const int b0 = blockIdx.y * kCB;
+    const int nch = (na + kCA - 1) / kCA;
+    const long long ntiles = (N + kCX - 1) / kCX;
+    const long long my_tiles = ntiles > blockIdx.x ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    const long long nitems = my_tiles * nch;
+    for (int e = tid; e < nch * kCA * kCB; e += 256) {
+        const int r = e / kCB, c = e % kCB;
+        Cs[r][c] = (r < na && b0 + c < nb) ? f64_to_f32(__ldg(C + (long long)r * nb + b0 + c)) : 0.f;
+    }
+    // item i: tile blockIdx.x + (i / nch) gridDim.x, input vectors 16 (i % nch) ..
+    auto issue = [&](long long i) {
+        double *dst = raw + (size_t)(i % kCStages) * kCA * kCX;
+        const long long xt = (blockIdx.x + (i / nch) * gridDim.x) * kCX;
+        const int r0 = (int)(i % nch) * kCA;
+        constexpr int per_row = VEC2 ? kCX / 2 : kCX;
+#pragma unroll
+        for (int m = 0; m < kCA * per_row / 256; ++m) {
+            const int piece = tid + 256 * m;
+            const int r = piece / per_row, c = (piece % per_row) * (VEC2 ? 2 : 1);
+            const long long x = xt + c;
+            long long nbytes = (r0 + r < na) ? (N - x) * 8 : 0;
+            nbytes = nbytes < 0 ? 0 : (nbytes > (VEC2 ? 16 : 8) ? (VEC2 ? 16 : 8) : nbytes);
+            const double *src = nbytes > 0 ? A + (long long)(r0 + r) * N + x : A;
+            if (VEC2)
+                ptx::cp_async16(dst + r * kCX + c, src, (uint32_t)nbytes);
+            else
+                ptx::cp_async8(dst + r * kCX + c, src, (uint32_t)nbytes);
+        }
+    };
+#pragma unroll
+    for (int i = 0; i < kCStages - 1; ++i) {
+        if (i < nitems) issue(i);
+        ptx::cp_async_commit();
+    }
     float acc[8][4];
 #pragma unroll
     for (int j = 0; j < 8; ++j)
 #pragma unroll
         for (int k = 0; k < 4; ++k) acc[j][k] = 0.f;
-    const int lx = tid & 127, lr = tid >> 7;  // loader: one grid point, rows lr + 2m
-    const long long xl = x0 + lx;
-    for (int a0 = 0; a0 < na; a0 += kCA) {
-        float va[16];
+    const int lx = tid & 127, lr = tid >> 7;  // converter: one grid point, rows lr + 2m
+    for (long long i = 0; i < nitems; ++i) {
+        if (i + kCStages - 1 < nitems) issue(i + kCStages - 1);
+        ptx::cp_async_commit();
+        ptx::cp_async_wait<kCStages - 1>();  // this thread's copies of item i have landed
+        __syncthreads();                     // everyone's have; the float32 tile is free
+        const double *src = raw + (size_t)(i % kCStages) * kCA * kCX;
 #pragma unroll
-        for (int m = 0; m < 16; ++m) {
-            const int r = lr + 2 * m;
-            va[m] = (xl < N && a0 + r < na) ? (float)__ldg(A + (long long)(a0 + r) * N + xl) : 0.f;
-        }
-#pragma unroll
-        for (int m = 0; m < 8; ++m) {
-            const int e = tid + 256 * m, r = e >> 6, c = e & 63;
-            Cs[r][c] = (a0 + r < na && b0 + c < nb) ? (float)__ldg(C + (long long)(a0 + r) * nb + b0 + c) : 0.f;
-        }
-#pragma unroll
-        for (int m = 0; m < 16; ++m) As[lr + 2 * m][lx] = va[m];
+        for (int m = 0; m < kCA / 2; ++m) As[lr + 2 * m][lx] = f64_to_f32(src[(lr + 2 * m) * kCX + lx]);
         __syncthreads();
+        const int ch = (int)(i % nch);
 #pragma unroll 4
         for (int r = 0; r < kCA; ++r) {
             float av[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) av[k] = As[r][tx + 32 * k];
-            const float4 c0 = *reinterpret_cast<const float4 *>(&Cs[r][8 * ty]);
-            const float4 c1 = *reinterpret_cast<const float4 *>(&Cs[r][8 * ty + 4]);
+            const float4 c0 = *reinterpret_cast<const float4 *>(&Cs[ch * kCA + r][8 * ty]);
+            const float4 c1 = *reinterpret_cast<const float4 *>(&Cs[ch * kCA + r][8 * ty + 4]);
             const float cv[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
 #pragma unroll
             for (int j = 0; j < 8; ++j)
 #pragma unroll
                 for (int k = 0; k < 4; ++k) acc[j][k] = fmaf(av[k], cv[j], acc[j][k]);
         }
-        __syncthreads();
-    }
+        if (ch == nch - 1) {
+            const long long xt = (blockIdx.x + (i / nch) * gridDim.x) * kCX;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const int b = b0 + 8 * ty + j;
-        if (b >= nb) continue;
+            for (int j = 0; j < 8; ++j) {
+                const int b = b0 + 8 * ty + j;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const long long x = x0 + tx + 32 * k;
-            if (x < N) out[(long long)b * N + x] = sgn * (double)acc[j][k];
+                for (int k = 0; k < 4; ++k) {
+                    const long long x = xt + tx + 32 * k;
+                    if (b < nb && x < N) out[(long long)b * N + x] = f32_to_f64(sgn * acc[j][k]);
+                    acc[j][k] = 0.f;
+                }
+            }
         }
     }
+    ptx::cp_async_wait<0>();
 }
 
 // part (n_split x na x nb) of A^T B over the grid, float64 or float32 products
 // by plan precision; returns n_split.
-int launch_projection(const kx_plan *p, const double *A, int na, const double *B, int nb, double *part,
-                      int n_split, cudaStream_t s) {
+int launch_projection(kx_plan *p, const double *A, int na, const double *B, int nb, double *part, int n_split,
+                      cudaStream_t s) {
     const long long N = (long long)p->N;
-    const long long span = (N + n_split - 1) / n_split;
+    if (int rc = prof_begin(p, PK_ACE, s)) return rc;
     if (p->precision == KX_FP64) {
+        const long long span = (N + n_split - 1) / n_split;
         gram_kernel<<<dim3((na + kG - 1) / kG, (nb + kG - 1) / kG, n_split), 256, 0, s>>>(A, na, B, nb, N, span, part);
         KX_LAUNCH_CHECK("gram_kernel launch");
     } else {
-        proj32_kernel<<<dim3(n_split, (na + kPT - 1) / kPT, (nb + kPT - 1) / kPT), 256, 0, s>>>(A, na, B, nb, N, span,
-                                                                                               part);
+        // whole pipeline steps per CTA, so that every step starts on an even grid point
+        const long long span = ((N + n_split - 1) / n_split + kPX - 1) / kPX * kPX;
+        const dim3 grid(n_split, (na + kPT - 1) / kPT, (nb + kPT - 1) / kPT);
+        // 16-byte copies need even N (so every row starts 16-byte aligned) and aligned bases
+        const bool vec2 = N % 2 == 0 && ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15) == 0;
+        if (vec2) {
+            KX_CUDA_TRY(cudaFuncSetAttribute(proj32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kProjSmem));
+            proj32_kernel<true><<<grid, 256, kProjSmem, s>>>(A, na, B, nb, N, span, part);
+        } else {
+            KX_CUDA_TRY(cudaFuncSetAttribute(proj32_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kProjSmem));
+            proj32_kernel<false><<<grid, 256, kProjSmem, s>>>(A, na, B, nb, N, span, part);
+        }
         KX_LAUNCH_CHECK("proj32_kernel launch");
     }
-    return KX_OK;
+    return prof_end(p, s);
 }
 
-// Grid points per projection CTA: enough CTAs for a few per SM, at least 256
-// points each; float64 plans keep the earlier fixed slab split.
+// Number of grid-point ranges of the projection: float32 plans put two CTAs
+// on each SM with at least 256 points per CTA; float64 plans keep a fixed
+// slab split.  A range that starts past the end of the grid leaves a zero
+// partial.
 int projection_split(const kx_plan *p, int na, int nb) {
     const long long N = (long long)p->N;
     if (p->precision == KX_FP64) return (int)std::max(1LL, std::min<long long>(128, (N + 4095) / 4096));
     const long long tiles = (long long)((na + kPT - 1) / kPT) * ((nb + kPT - 1) / kPT);
-    const long long want = std::max(1LL, (3LL * p->num_sms + tiles - 1) / tiles);
+    const long long want = std::max(1LL, 2LL * p->num_sms / tiles);
     return (int)std::max(1LL, std::min<long long>(want, (N + 255) / 256));
 }
 
 // out = sgn A C (grid vectors), float64 or float32 products by plan precision.
-int launch_combination(const kx_plan *p, const double *A, int na, const double *C, int nb, double sgn, double *out,
+int launch_combination(kx_plan *p, const double *A, int na, const double *C, int nb, double sgn, double *out,
                        cudaStream_t s) {
     const long long N = (long long)p->N;
+    if (int rc = prof_begin(p, PK_ACE_COMB, s)) return rc;
     if (p->precision == KX_FP64) {
         xi_kernel<<<dim3((unsigned)((N + 127) / 128), (unsigned)((nb + 31) / 32)), 256, 0, s>>>(A, C, na, nb, N, sgn,
                                                                                               out);
         KX_LAUNCH_CHECK("xi_kernel launch");
     } else {
-        combine32_kernel<<<dim3((unsigned)((N + kCX - 1) / kCX), (unsigned)((nb + kCB - 1) / kCB)), 256, 0, s>>>(
-            A, na, C, nb, N, sgn, out);
+        const int tiles_b = (nb + kCB - 1) / kCB;
+        const long long ntiles = (N + kCX - 1) / kCX;
+        const int gx = (int)std::max(1LL, std::min<long long>(ntiles, std::max(1, 2 * p->num_sms / tiles_b)));
+        const size_t smem = comb_smem(na);
+        const dim3 grid(gx, tiles_b);
+        const float fs = sgn < 0.0 ? -1.f : 1.f;
+        const bool vec2 = N % 2 == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0;
+        if (vec2) {
+            KX_CUDA_TRY(cudaFuncSetAttribute(combine32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem));
+            combine32_kernel<true><<<grid, 256, smem, s>>>(A, na, C, nb, N, fs, out);
+        } else {
+            KX_CUDA_TRY(cudaFuncSetAttribute(combine32_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem));
+            combine32_kernel<false><<<grid, 256, smem, s>>>(A, na, C, nb, N, fs, out);
+        }
         KX_LAUNCH_CHECK("combine32_kernel launch");
     }
-    return KX_OK;
+    return prof_end(p, s);
 }
 
 }  // namespace
@@ -359,12 +521,14 @@ int ace_run(kx_plan *p, int n_orb, const double *psi, const double *W, double *x
     int *bad = reinterpret_cast<int *>(Rinv + nn);
     KX_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), s));
     if ((rc = launch_projection(p, psi, n_orb, W, n_orb, part, n_slab, s))) return rc;
+    if ((rc = prof_begin(p, PK_ACE, s))) return rc;
     gram_reduce_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(part, n_slab, (int)nn, p->dV, M, M_out, A);
     KX_LAUNCH_CHECK("gram_reduce_kernel launch");
     cholesky_kernel<<<1, 256, 0, s>>>(A, n_orb, R, bad);
     KX_LAUNCH_CHECK("cholesky_kernel launch");
     triinv_kernel<<<(n_orb + 127) / 128, 128, 0, s>>>(R, n_orb, Rinv);
     KX_LAUNCH_CHECK("triinv_kernel launch");
+    if ((rc = prof_end(p, s))) return rc;
     if ((rc = launch_combination(p, W, n_orb, Rinv, n_orb, 1.0, xi, s))) return rc;
     int h_bad = 0;
     KX_CUDA_TRY(cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -383,9 +547,11 @@ int ace_apply_run(kx_plan *p, int n_xi, const double *xi, int n_vec, const doubl
     double *P = part + ne * n_split;
     // P = dV xi^T phi, then out = -xi P
     if ((rc = launch_projection(p, xi, n_xi, phi, n_vec, part, n_split, s))) return rc;
+    if ((rc = prof_begin(p, PK_ACE, s))) return rc;
     gram_reduce_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(part, n_split, (int)ne, p->dV, P, nullptr,
                                                                     nullptr);
     KX_LAUNCH_CHECK("gram_reduce_kernel launch");
+    if ((rc = prof_end(p, s))) return rc;
     return launch_combination(p, xi, n_xi, P, n_vec, -1.0, out, s);
 }
 

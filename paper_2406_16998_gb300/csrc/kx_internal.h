@@ -54,7 +54,7 @@ struct TuneParams {
 
 // Per-launch CUDA-event timing by kernel kind (kx_profile / kx_profile_read).
 enum ProfKind { PK_PREP = 0, PK_X3F, PK_X2F, PK_X1, PK_X2I, PK_X3I, PK_FINAL, PK_FP64_MODE, PK_FP64_OTHER,
-                PK_ACE, PK_SETUP, PK_ACC, PK_SLAB, PK_COUNT };
+                PK_ACE, PK_SETUP, PK_ACC, PK_SLAB, PK_ACE_COMB, PK_COUNT };
 struct Profiler {
     bool on = false;
     std::vector<cudaEvent_t> pool;       // reusable events

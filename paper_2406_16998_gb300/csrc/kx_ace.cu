@@ -184,6 +184,15 @@ __device__ __forceinline__ double f32_to_f64(float f) {
     return __hiloint2double((int)hi, (int)lo);
 }
 
+// s += a * b on both lanes of a float pair, one packed instruction.
+__device__ __forceinline__ void fma2(float2 &s, float2 a, float2 b) {
+    unsigned long long rs = *reinterpret_cast<unsigned long long *>(&s);
+    asm("fma.rn.f32x2 %0, %1, %2, %0;"
+        : "+l"(rs)
+        : "l"(*reinterpret_cast<unsigned long long *>(&a)), "l"(*reinterpret_cast<unsigned long long *>(&b)));
+    s = *reinterpret_cast<float2 *>(&rs);
+}
+
 // (hi, lo) += v with the rounding error of the float32 addition kept in lo.
 __device__ __forceinline__ void two_sum_add(float &hi, float &lo, float v) {
     const float t = hi + v;
@@ -248,14 +257,15 @@ __global__ void __launch_bounds__(256, 2) proj32_kernel(const double *__restrict
     const long long x0 = (long long)blockIdx.x * span;
     const long long x1 = min(N, x0 + span);
     const int nsteps = x1 > x0 ? (int)((x1 - x0 + kPX - 1) / kPX) : 0;
-    float acc_hi[4][4], acc_lo[4][4], s[4][4];
+    float acc_hi[4][4], acc_lo[4][4];
+    float2 s[4][4];  // even and odd grid points of the current block
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             acc_hi[i][j] = 0.f;
             acc_lo[i][j] = 0.f;
-            s[i][j] = 0.f;
+            s[i][j] = make_float2(0.f, 0.f);
         }
     auto stage = [&](int k) { return raw + (size_t)(k % kPStages) * 2 * kPT * kPX; };
     if (nsteps > 0) {
@@ -293,10 +303,8 @@ __global__ void __launch_bounds__(256, 2) proj32_kernel(const double *__restrict
             for (int i = 0; i < 4; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    s[i][j] = fmaf(av[i].x, bv[j].x, s[i][j]);
-                    s[i][j] = fmaf(av[i].y, bv[j].y, s[i][j]);
-                    s[i][j] = fmaf(av[i].z, bv[j].z, s[i][j]);
-                    s[i][j] = fmaf(av[i].w, bv[j].w, s[i][j]);
+                    fma2(s[i][j], make_float2(av[i].x, av[i].y), make_float2(bv[j].x, bv[j].y));
+                    fma2(s[i][j], make_float2(av[i].z, av[i].w), make_float2(bv[j].z, bv[j].w));
                 }
         }
         if (++blk == kPBlk) {
@@ -305,8 +313,8 @@ __global__ void __launch_bounds__(256, 2) proj32_kernel(const double *__restrict
             for (int i = 0; i < 4; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    two_sum_add(acc_hi[i][j], acc_lo[i][j], s[i][j]);
-                    s[i][j] = 0.f;
+                    two_sum_add(acc_hi[i][j], acc_lo[i][j], s[i][j].x + s[i][j].y);
+                    s[i][j] = make_float2(0.f, 0.f);
                 }
         }
     }
@@ -317,7 +325,7 @@ __global__ void __launch_bounds__(256, 2) proj32_kernel(const double *__restrict
         for (int j = 0; j < 4; ++j) {
             const int a = a0 + ty + 16 * i, b = b0 + tx + 16 * j;
             if (a < na && b < nb) {
-                two_sum_add(acc_hi[i][j], acc_lo[i][j], s[i][j]);
+                two_sum_add(acc_hi[i][j], acc_lo[i][j], s[i][j].x + s[i][j].y);
                 part[((long long)blockIdx.x * na + a) * nb + b] = f32_to_f64(acc_hi[i][j]) + f32_to_f64(acc_lo[i][j]);
             }
         }
@@ -386,11 +394,11 @@ __global__ void __launch_bounds__(256, 2) combine32_kernel(const double *__restr
         if (i < nitems) issue(i);
         ptx::cp_async_commit();
     }
-    float acc[8][4];
+    float2 acc[4][4];  // acc[jp][k] = outputs b0 + 8 ty + 2 jp (.x) and + 1 (.y) at point k
 #pragma unroll
-    for (int j = 0; j < 8; ++j)
+    for (int jp = 0; jp < 4; ++jp)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) acc[j][k] = 0.f;
+        for (int k = 0; k < 4; ++k) acc[jp][k] = make_float2(0.f, 0.f);
     const int lx = tid & 127, lr = tid >> 7;  // converter: one grid point, rows lr + 2m
     for (long long i = 0; i < nitems; ++i) {
         if (i + kCStages - 1 < nitems) issue(i + kCStages - 1);
@@ -409,22 +417,28 @@ __global__ void __launch_bounds__(256, 2) combine32_kernel(const double *__restr
             for (int k = 0; k < 4; ++k) av[k] = As[r][tx + 32 * k];
             const float4 c0 = *reinterpret_cast<const float4 *>(&Cs[ch * kCA + r][8 * ty]);
             const float4 c1 = *reinterpret_cast<const float4 *>(&Cs[ch * kCA + r][8 * ty + 4]);
-            const float cv[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+            const float2 cv[4] = {make_float2(c0.x, c0.y), make_float2(c0.z, c0.w), make_float2(c1.x, c1.y),
+                                  make_float2(c1.z, c1.w)};
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
+            for (int k = 0; k < 4; ++k) {
+                const float2 ak = make_float2(av[k], av[k]);
 #pragma unroll
-                for (int k = 0; k < 4; ++k) acc[j][k] = fmaf(av[k], cv[j], acc[j][k]);
+                for (int jp = 0; jp < 4; ++jp) fma2(acc[jp][k], ak, cv[jp]);
+            }
         }
         if (ch == nch - 1) {
             const long long xt = (blockIdx.x + (i / nch) * gridDim.x) * kCX;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int b = b0 + 8 * ty + j;
+            for (int jp = 0; jp < 4; ++jp) {
+                const int b = b0 + 8 * ty + 2 * jp;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const long long x = xt + tx + 32 * k;
-                    if (b < nb && x < N) out[(long long)b * N + x] = f32_to_f64(sgn * acc[j][k]);
-                    acc[j][k] = 0.f;
+                    if (x < N) {
+                        if (b < nb) out[(long long)b * N + x] = f32_to_f64(sgn * acc[jp][k].x);
+                        if (b + 1 < nb) out[(long long)(b + 1) * N + x] = f32_to_f64(sgn * acc[jp][k].y);
+                    }
+                    acc[jp][k] = make_float2(0.f, 0.f);
                 }
             }
         }

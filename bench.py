@@ -44,19 +44,32 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["kronx", "reference"], default="kronx")
     ap.add_argument("--no-extras", action="store_true", help="skip FP64/e2e/oracle legs (profiling runs)")
-    ap.add_argument("--profile-case", choices=["small"], default=None,
-                    help="run one apply of a small case of the same kernels (96^3, 8 orbitals) for ncu captures")
+    ap.add_argument("--profile-case", choices=["small", "ace"], default=None,
+                    help="small: one apply of a small case of the same kernels (96^3, 8 orbitals); ace: three "
+                         "ACE operator applies at 96^3 with 64 + 64 vectors; both for ncu captures")
     return ap.parse_args()
 
 
-def run_profile_case():
-    """One split-precision apply at 96^3 with 8 orbitals (36 pairs): the same
-    kernels as the bench workload on inputs of about L2 size, so that an ncu
-    capture with many passes stays short."""
+def run_profile_case(which="small"):
+    """small: one split-precision apply at 96^3 with 8 orbitals (36 pairs): the
+    same kernels as the bench workload on inputs of about L2 size, so that an
+    ncu capture with many passes stays short.  ace: three kx_ace_apply calls on
+    the headline system's tensor-core plan with 64 seeded vectors xi (scaled by
+    1e-3) and 64 orbitals phi (1.4 GB on the device)."""
     import torch
     import paper_2406_16998_gb300 as kx
     from paper_2406_16998_gb300 import build
     build.build()
+    if which == "ace":
+        plan = kx.Plan.for_system(SYS, precision=kx.KX_F16X3)
+        xi = torch.from_numpy(np.ascontiguousarray(workloads.random_field(plan.N, 64, 3).T) * 1e-3).cuda()
+        phi = torch.from_numpy(np.ascontiguousarray(workloads.make_orbitals(SYS).T)).cuda()
+        out = torch.empty_like(phi)
+        for _ in range(3):
+            kx.kx_ace_apply(plan, xi, phi, out=out)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "ace", "max_abs": float(out.abs().max())}), flush=True)
+        return
     case = workloads.System(n=(96, 96, 96), h=(0.25,) * 3, bc=(workloads.DIRICHLET,) * 3,
                             kernel=workloads.UNSCREENED, n_orb=8, n_centres=4, seed=5, name="profile-small")
     psi = torch.from_numpy(np.ascontiguousarray(workloads.make_orbitals(case).T)).cuda()
@@ -376,7 +389,7 @@ def issued_tensor_flops_per_pair(n, fused=True):
 def main():
     args = parse()
     if args.profile_case:
-        return run_profile_case()
+        return run_profile_case(args.profile_case)
     if args.impl == "reference":
         return run_reference(args)
     import torch

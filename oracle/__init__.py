@@ -1,12 +1,17 @@
 """FP64 CPU oracle (test infrastructure only; never called by the CUDA library).
 
 Pinned functions (see tests/test_oracle_pins.py): fd_weights, lap1d, eig1d,
-kernel_f, apply_fL, dense_fL, vx_apply, exchange_energy, energy_gradient, ace, ace_apply.
+kernel_f, apply_fL, dense_fL, vx_apply, exchange_energy, energy_gradient, ace, ace_apply,
+multipole_moments, multipole_potential, rhs_multipole, apply_fL_multipole.
 """
 from .kron_oracle import (DIRICHLET, PERIODIC, UNSCREENED, SCREENED, Plan, fd_weights, lap1d, eig1d,
                           kernel_f, apply_fL, forward_transform, inverse_transform, fdiag_matrix,
-                          dense_L, dense_fL, pair_list, vx_apply, exchange_energy, energy_gradient, ace, ace_apply)
+                          dense_L, dense_fL, pair_list, vx_apply, exchange_energy, energy_gradient, ace, ace_apply,
+                          expansion_centre, interior_points, exterior_points, multipole_moments,
+                          multipole_potential, rhs_multipole, apply_fL_multipole)
 
 __all__ = ["DIRICHLET", "PERIODIC", "UNSCREENED", "SCREENED", "Plan", "fd_weights", "lap1d", "eig1d",
            "kernel_f", "apply_fL", "forward_transform", "inverse_transform", "fdiag_matrix", "dense_L",
-           "dense_fL", "pair_list", "vx_apply", "exchange_energy", "energy_gradient", "ace", "ace_apply"]
+           "dense_fL", "pair_list", "vx_apply", "exchange_energy", "energy_gradient", "ace", "ace_apply",
+           "expansion_centre", "interior_points", "exterior_points", "multipole_moments", "multipole_potential",
+           "rhs_multipole", "apply_fL_multipole"]

@@ -202,12 +202,14 @@ def pair_list(n_orb: int, ordered: bool):
     return [(i, j) for i in range(n_orb) for j in range(i, n_orb)]
 
 
-def vx_apply(plan: Plan, psi: np.ndarray, occ=None, ordered: bool = False, pairs=None):
+def vx_apply(plan: Plan, psi: np.ndarray, occ=None, ordered: bool = False, pairs=None, l_max=None):
     """(Vx Psi)_i = -sum_j g_j psi_j * phi_ij with phi_ij = f(L)(psi_i * psi_j), and
     E_x = -1/2 dV sum_{i,j} g_i g_j <psi_i psi_j, phi_ij>.
 
     Returns (vx_psi (N, n_orb), e_x).  `pairs` restricts the sum to a sub-list of
-    the chosen enumeration (used for sharded partial sums).
+    the chosen enumeration (used for sharded partial sums).  With l_max, each
+    phi_ij takes the Dirichlet values of the multipole expansion of rho_ij up
+    to order l_max (apply_fL_multipole) instead of zero boundary values.
     """
     psi = np.asarray(psi, dtype=np.float64)
     n_orb = psi.shape[1]
@@ -218,7 +220,7 @@ def vx_apply(plan: Plan, psi: np.ndarray, occ=None, ordered: bool = False, pairs
         pairs = pair_list(n_orb, ordered)
     for (i, j) in pairs:
         rho = psi[:, i] * psi[:, j]
-        phi = apply_fL(plan, rho)
+        phi = apply_fL(plan, rho) if l_max is None else apply_fL_multipole(plan, rho, l_max)
         if ordered:
             out[:, i] -= g[j] * psi[:, j] * phi
             e += -0.5 * plan.dV * g[i] * g[j] * np.dot(rho, phi)
@@ -252,6 +254,125 @@ def energy_gradient(plan: Plan, psi: np.ndarray, occ=None) -> np.ndarray:
     g = np.ones(n_orb) if occ is None else np.asarray(occ, dtype=np.float64)
     vx, _ = vx_apply(plan, psi, occ)
     return 2.0 * plan.dV * vx * g[None, :]
+
+
+# ---------------------------------------------------------------------------
+# Dirichlet values from the multipole expansion of the source (Sec. 4: for
+# isolated systems the boundary values of each linear system come from the
+# multipole expansion of the Coulomb kernel and enter through the right-hand
+# side).  Readings (R10-R12):
+#  R10 The expansion is about the box centre c, c_a = (n_a + 1) h_a / 2, up to
+#      order l_max (the paper gives no order); it applies to all-Dirichlet
+#      boxes with the unscreened kernel (-del^2 phi = 4 pi rho).
+#  R11 The exterior points are those the order-2m stencil of an interior point
+#      reaches across one face: index -m..-1 or n_a..n_a+m-1 along one axis a,
+#      interior along the other two, at x = (i + 1) h like the interior.
+#  R12 Moving the known exterior values to the right-hand side of
+#      L_full phi = -4 pi rho gives L phi = -4 pi (rho + L_ext phi_ext / (4 pi)),
+#      i.e. phi = f(L) (rho + L_ext phi_ext / (4 pi)) with f = -4 pi / lambda.
+# ---------------------------------------------------------------------------
+def _require_isolated(plan: Plan):
+    if plan.kind != UNSCREENED or any(b != DIRICHLET for b in plan.bc):
+        raise ValueError("multipole boundary values need an all-Dirichlet box and the unscreened kernel")
+
+
+def expansion_centre(plan: Plan) -> np.ndarray:
+    return np.array([(plan.n[a] + 1) * plan.h[a] / 2.0 for a in range(3)])
+
+
+def interior_points(plan: Plan) -> np.ndarray:
+    """(N, 3) coordinates of the grid points, x1 fastest (R7)."""
+    ax = [(np.arange(plan.n[a]) + 1) * plan.h[a] for a in range(3)]
+    z, y, x = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+    return np.stack([x.ravel(), y.ravel(), z.ravel()], axis=1)
+
+
+def exterior_points(plan: Plan):
+    """Exterior points of R11 as a list of (axis, index along that axis, (M, 3)
+    coordinates, (M,) flat index of the interior point sharing the other two
+    indices); each face layer is one entry."""
+    _require_isolated(plan)
+    m = plan.fd_order // 2
+    n1, n2, n3 = plan.n
+    out = []
+    for a in range(3):
+        for i_a in list(range(-m, 0)) + list(range(plan.n[a], plan.n[a] + m)):
+            idx = [np.arange(n1), np.arange(n2), np.arange(n3)]
+            idx[a] = np.array([i_a])
+            k3, k2, k1 = np.meshgrid(idx[2], idx[1], idx[0], indexing="ij")
+            k1, k2, k3 = k1.ravel(), k2.ravel(), k3.ravel()
+            pts = np.stack([(k1 + 1) * plan.h[0], (k2 + 1) * plan.h[1], (k3 + 1) * plan.h[2]], axis=1)
+            # the interior point on the same line along axis a, with index 0 (i_a < 0) or n_a - 1
+            kk = [k1, k2, k3]
+            kk[a] = np.full_like(kk[a], 0 if i_a < 0 else plan.n[a] - 1)
+            flat = kk[0] + n1 * (kk[1] + n2 * kk[2])
+            out.append((a, i_a, pts, flat))
+    return out
+
+
+def _spherical(v: np.ndarray):
+    r = np.linalg.norm(v, axis=1)
+    cos_t = np.where(r > 0, v[:, 2] / np.where(r > 0, r, 1.0), 1.0)
+    phi = np.arctan2(v[:, 1], v[:, 0])
+    return r, np.clip(cos_t, -1.0, 1.0), phi
+
+
+def multipole_moments(plan: Plan, rho: np.ndarray, l_max: int):
+    """Moments q[(l, m, t)] = dV sum_r rho(r) |r-c|^l P_l^m(cos theta) trig_t(m phi),
+    t = 0 for cos and 1 for sin (m >= 1), about the expansion centre (R10)."""
+    from scipy.special import lpmv
+    r, ct, ph = _spherical(interior_points(plan) - expansion_centre(plan))
+    q = {}
+    for l in range(l_max + 1):
+        for m in range(l + 1):
+            base = plan.dV * rho * r ** l * lpmv(m, l, ct)
+            q[(l, m, 0)] = float(np.sum(base * np.cos(m * ph)))
+            if m > 0:
+                q[(l, m, 1)] = float(np.sum(base * np.sin(m * ph)))
+    return q
+
+
+def multipole_potential(plan: Plan, q: dict, l_max: int, pts: np.ndarray) -> np.ndarray:
+    """Potential of the moments at points outside the source (addition theorem of
+    1/|p - r| in Legendre functions: sum_l r^l / p^(l+1) P_l(cos gamma) with
+    P_l(cos gamma) = sum_m (2 - delta_m0) (l-m)!/(l+m)! P_l^m P_l^m cos(m (phi_p - phi_r)))."""
+    from scipy.special import lpmv
+    r, ct, ph = _spherical(pts - expansion_centre(plan))
+    out = np.zeros(len(pts))
+    for l in range(l_max + 1):
+        for m in range(l + 1):
+            w = (1.0 if m == 0 else 2.0) * math.factorial(l - m) / math.factorial(l + m)
+            ang = q[(l, m, 0)] * np.cos(m * ph) + (q[(l, m, 1)] * np.sin(m * ph) if m > 0 else 0.0)
+            out += w * lpmv(m, l, ct) * ang / r ** (l + 1)
+    return out
+
+
+def rhs_multipole(plan: Plan, rho: np.ndarray, l_max: int) -> np.ndarray:
+    """rho + L_ext phi_ext / (4 pi) (R12): each exterior value reaches the interior
+    points within m along its axis with the stencil weight of that distance."""
+    _require_isolated(plan)
+    rho = np.asarray(rho, dtype=np.float64)
+    w = fd_weights(plan.fd_order)
+    q = multipole_moments(plan, rho, l_max)
+    b = rho.copy()
+    n1, n2, n3 = plan.n
+    stride = [1, n1, n1 * n2]
+    m = plan.fd_order // 2
+    for a, i_a, pts, flat in exterior_points(plan):
+        vals = multipole_potential(plan, q, l_max, pts)
+        # interior points i with |i - i_a| <= m along axis a
+        lo, hi = (0, i_a + m) if i_a < 0 else (i_a - m, plan.n[a] - 1)
+        edge = 0 if i_a < 0 else plan.n[a] - 1
+        for i in range(max(lo, 0), min(hi, plan.n[a] - 1) + 1):
+            d = abs(i - i_a)
+            b[flat + (i - edge) * stride[a]] += w[d] / plan.h[a] ** 2 * vals / (4.0 * math.pi)
+    return b
+
+
+def apply_fL_multipole(plan: Plan, rho: np.ndarray, l_max: int) -> np.ndarray:
+    """phi = f(L) (rho + L_ext phi_ext / (4 pi)): the solution of -del^2 phi = 4 pi rho
+    whose values outside the box are the multipole expansion of rho's potential."""
+    return apply_fL(plan, rhs_multipole(plan, rho, l_max))
 
 
 # ---------------------------------------------------------------------------

@@ -452,3 +452,88 @@ def test_ace_apply_is_vx_on_occupied_space_and_projector_elsewhere():
     # rank: at most n_orb nonzero singular values
     sv = np.linalg.svd(oracle.ace_apply(plan, xi, rng.standard_normal((plan.N, 12))), compute_uv=False)
     assert np.all(sv[psi.shape[1]:] < 1e-11 * sv[0])
+
+
+# ---------------------------------------------------------------- multipole boundary values
+def _gaussian(plan, centre, alpha):
+    """Normalised Gaussian charge (total charge 1) sampled on the grid."""
+    d = oracle.interior_points(plan) - np.asarray(centre)
+    return (alpha / math.pi) ** 1.5 * np.exp(-alpha * np.sum(d * d, axis=1))
+
+
+def test_multipole_values_are_the_legendre_series_and_converge_to_coulomb():
+    """Exterior values from the moments equal the Legendre series of 1/|p - r|
+    summed over the source directly (the addition theorem, written here the
+    other way round), and approach the direct Coulomb sum as l_max grows."""
+    from scipy.special import eval_legendre
+    plan = oracle.Plan((16, 14, 18), (0.6, 0.6, 0.6), (D, D, D), U)
+    c = oracle.expansion_centre(plan)
+    rho = _gaussian(plan, c + np.array([0.4, -0.3, 0.25]), 4.0)
+    src = oracle.interior_points(plan) - c
+    rs = np.linalg.norm(src, axis=1)
+    pts = np.concatenate([e[2] for e in oracle.exterior_points(plan)])[::7]
+    rel = pts - c
+    rp = np.linalg.norm(rel, axis=1)
+    coul = np.array([plan.dV * np.sum(rho / np.linalg.norm(p - oracle.interior_points(plan), axis=1)) for p in pts])
+    errs = []
+    for l_max in (0, 2, 4, 8):
+        q = oracle.multipole_moments(plan, rho, l_max)
+        vals = oracle.multipole_potential(plan, q, l_max, pts)
+        series = np.zeros(len(pts))
+        for k, p in enumerate(rel):
+            cosg = np.where(rs > 0, src @ p / np.where(rs > 0, rs, 1.0) / rp[k], 1.0)
+            series[k] = plan.dV * sum(np.sum(rho * rs ** l * eval_legendre(l, cosg)) / rp[k] ** (l + 1)
+                                      for l in range(l_max + 1))
+        assert np.max(np.abs(vals - series)) < 1e-12 * np.abs(series).max()
+        errs.append(np.max(np.abs(vals - coul)) / np.abs(coul).max())
+    assert errs[0] > errs[1] > errs[2] > errs[3]
+    assert errs[3] < 1e-6
+
+
+def test_multipole_solution_satisfies_the_extended_stencil():
+    """phi = apply_fL_multipole(rho) solves the finite-difference equation on the
+    grid extended by the exterior points, -L_full phi = 4 pi rho, with the
+    stencil built from exact rational weights and the exterior values in place."""
+    plan = oracle.Plan((12, 10, 14), (0.5, 0.55, 0.45), (D, D, D), U)
+    c = oracle.expansion_centre(plan)
+    rho = _gaussian(plan, c + np.array([0.2, 0.1, -0.3]), 2.5) - 0.5 * _gaussian(plan, c - 0.4, 5.0)
+    l_max = 3
+    phi = oracle.apply_fL_multipole(plan, rho, l_max)
+    m = plan.fd_order // 2
+    n1, n2, n3 = plan.n
+    ext = np.zeros((n3 + 2 * m, n2 + 2 * m, n1 + 2 * m))
+    ext[m:m + n3, m:m + n2, m:m + n1] = phi.reshape(n3, n2, n1)
+    q = oracle.multipole_moments(plan, rho, l_max)
+    for a, i_a, pts, flat in oracle.exterior_points(plan):
+        vals = oracle.multipole_potential(plan, q, l_max, pts).reshape(
+            [1 if b == a else plan.n[b] for b in (2, 1, 0)])
+        sl = [slice(m, m + n3), slice(m, m + n2), slice(m, m + n1)]
+        sl[2 - a] = slice(m + i_a, m + i_a + 1)
+        ext[tuple(sl)] = vals
+    w = [float(x) for x in exact_weights(plan.fd_order)]
+    lap = np.zeros((n3, n2, n1))
+    for a in range(3):
+        for d in range(-m, m + 1):
+            sl = [slice(m, m + n3), slice(m, m + n2), slice(m, m + n1)]
+            sl[2 - a] = slice(m + d, m + d + plan.n[a])
+            lap += w[abs(d)] / plan.h[a] ** 2 * ext[tuple(sl)]
+    resid = -lap.ravel() - 4.0 * math.pi * rho
+    assert np.max(np.abs(resid)) < 1e-10 * 4.0 * math.pi * np.abs(rho).max()
+
+
+def test_multipole_boundary_reproduces_the_free_space_potential():
+    """A normalised Gaussian charge in a Dirichlet box: with multipole boundary
+    values the grid solution is the free-space potential erf(sqrt(a) r) / r up
+    to the discretisation error everywhere, also next to the faces, where zero
+    boundary values miss it by the whole 1/r tail."""
+    from scipy.special import erf
+    plan = oracle.Plan((24, 24, 24), (0.35,) * 3, (D, D, D), U)
+    c = oracle.expansion_centre(plan)
+    alpha = 3.0
+    rho = _gaussian(plan, c, alpha)
+    r = np.linalg.norm(oracle.interior_points(plan) - c, axis=1)
+    exact = np.where(r > 0, erf(np.sqrt(alpha) * r) / np.where(r > 0, r, 1.0), 2.0 * np.sqrt(alpha / math.pi))
+    err_mp = np.max(np.abs(oracle.apply_fL_multipole(plan, rho, 4) - exact)) / exact.max()
+    err_zero = np.max(np.abs(oracle.apply_fL(plan, rho) - exact)) / exact.max()
+    assert err_mp < 2e-4
+    assert err_zero > 50 * err_mp

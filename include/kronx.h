@@ -116,6 +116,25 @@ int kx_plan_eig(const kx_plan *plan, int axis, double *lam, double *V);
  * Synchronous. */
 int kx_plan_ftable(const kx_plan *plan, double *f);
 
+/* kx_plan_set_multipole — Dirichlet boundary values from the multipole
+ * expansion of the source (Sec. 4: for isolated systems the boundary values of
+ * each linear system come from the multipole expansion of the Coulomb kernel
+ * and enter through the right-hand side) for every later solve of this plan:
+ *   phi = f(L) (rho + L_ext phi_ext / (4 pi)),
+ * phi_ext = the expansion of rho's potential to order l_max about the box
+ * centre ((n_a + 1) h_a / 2 per axis), taken at the exterior points the FD
+ * stencil reaches across each face.  Solved as f(L) rho plus a rank-K
+ * correction sum_k Q_k(rho) h_k, K = (l_max + 1)^2, with the fields h_k set up
+ * here by K float64 solves.  Applies to kx_apply_fL, kx_vx_apply,
+ * kx_vx_apply_pairs, kx_vx_apply_host (which then copies Vx psi back after the
+ * last chunk), kx_energy and batches created afterwards.
+ *   l_max  0..8; -1 turns the expansion off (zero boundary values again).
+ * KX_ERR_UNSUPPORTED unless all three axes are Dirichlet and the kernel is
+ * unscreened; while it is on, kx_apply_fL_noalloc returns KX_ERR_UNSUPPORTED
+ * and tensor-core plans accept at most 256 orbitals.  Synchronous; allocates
+ * 24 K N bytes of fields. */
+int kx_plan_set_multipole(kx_plan *plan, int l_max);
+
 /* kx_apply_fL — X = f(L) B for n_rhs independent right-hand sides (Sec. 3,
  * Eq. 18-19).  b and x hold n_rhs grid vectors each (float64); b is read only,
  * x must not overlap b.  n_rhs >= 0 (0 is a no-op). */

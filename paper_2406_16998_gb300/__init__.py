@@ -46,6 +46,7 @@ SIGNATURES = {
     "kx_energy": (_c_int, [_vp, _c_int, _vp, _vp, _vp, _vp]),
     "kx_ace": (_c_int, [_vp, _c_int, _vp, _vp, _vp, _vp, _vp]),
     "kx_ace_apply": (_c_int, [_vp, _c_int, _vp, _c_int, _vp, _vp, _vp]),
+    "kx_plan_set_multipole": (_c_int, [_vp, _c_int]),
     "kx_batch_create": (_c_int, [_c_int, _vp, _vp, ctypes.POINTER(_vp)]),
     "kx_batch_run": (_c_int, [_vp, _vp, _vp, _vp, _vp]),
     "kx_batch_destroy": (_c_int, [_vp]),
@@ -169,6 +170,12 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+    def set_multipole(self, l_max: int):
+        """Dirichlet values from the multipole expansion of each source up to
+        order l_max (-1: zero boundary values); see kx_plan_set_multipole."""
+        _check(lib().kx_plan_set_multipole(self.handle, int(l_max)))
+        self.l_max = int(l_max)
 
     def eig(self, axis):
         n = self.n[axis]
@@ -361,6 +368,10 @@ def _autograd():
 
         @staticmethod
         def forward(ctx, psi, plan, occ=None):
+            if getattr(plan, "l_max", -1) >= 0:
+                # with multipole boundary values the solve is not symmetric in rho, so
+                # dE_x/dpsi is not 2 dV Vx psi
+                raise NotImplementedError("ExchangeEnergy needs zero boundary values (plan.set_multipole(-1))")
             ctx.plan = plan
             ctx.save_for_backward(psi, occ) if occ is not None else ctx.save_for_backward(psi)
             ctx.has_occ = occ is not None

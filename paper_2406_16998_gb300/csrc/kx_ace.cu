@@ -24,9 +24,9 @@ namespace {
 
 constexpr int kG = 32;  // gram tile
 
-// part[s][a][b] = sum over slab s of grid points of psi_a(x) W_b(x)   (a < na, b < nb)
-__global__ void gram_kernel(const double *__restrict__ psi, int na, const double *__restrict__ W, int nb, long long N,
-                            long long slab, double *__restrict__ part) {
+// part[s][a][b] = sum over slab s of grid points of psi_a(x) W_b(x) w(x)   (a < na, b < nb; w nullable)
+__global__ void gram_kernel(const double *__restrict__ psi, int na, const double *__restrict__ W, int nb,
+                            const double *__restrict__ w, long long N, long long slab, double *__restrict__ part) {
     __shared__ double Ps[kG][kG + 1], Ws[kG][kG + 1];
     const int a0 = blockIdx.x * kG, b0 = blockIdx.y * kG;
     const long long x0 = blockIdx.z * slab, x1 = min(N, x0 + slab);
@@ -37,7 +37,7 @@ __global__ void gram_kernel(const double *__restrict__ psi, int na, const double
             long long x = xb + tx;
             int a = a0 + r, b = b0 + r;
             Ps[r][tx] = (a < na && x < x1) ? psi[(long long)a * N + x] : 0.0;
-            Ws[r][tx] = (b < nb && x < x1) ? W[(long long)b * N + x] : 0.0;
+            Ws[r][tx] = (b < nb && x < x1) ? W[(long long)b * N + x] * (w ? w[x] : 1.0) : 0.0;
         }
         __syncthreads();
         for (int k = 0; k < kG; ++k) {
@@ -112,9 +112,9 @@ __global__ void triinv_kernel(const double *__restrict__ R, int n, double *__res
     }
 }
 
-// xi_b(x) = sgn sum_k W_k(x) Rinv[k][b]   (k < na, b < nb; Rinv row-major na x nb)
+// xi_b(x) = (accumulate ? xi_b(x) : 0) + sgn sum_k W_k(x) Rinv[k][b]   (k < na, b < nb; Rinv row-major na x nb)
 __global__ void xi_kernel(const double *__restrict__ W, const double *__restrict__ Rinv, int na, int nb, long long N,
-                          double sgn, double *__restrict__ xi) {
+                          double sgn, bool accumulate, double *__restrict__ xi) {
     __shared__ double Ws[16][128 + 1];
     __shared__ double Rs[16][32];
     const long long x0 = (long long)blockIdx.x * 128;
@@ -145,7 +145,10 @@ __global__ void xi_kernel(const double *__restrict__ W, const double *__restrict
     if (x < N) {
         for (int u = 0; u < 16; ++u) {
             int b = b0 + ty * 16 + u;
-            if (b < nb) xi[(long long)b * N + x] = sgn * acc[u];
+            if (b < nb) {
+                double *o = xi + (long long)b * N + x;
+                *o = (accumulate ? *o : 0.0) + sgn * acc[u];
+            }
         }
     }
 }
@@ -243,11 +246,13 @@ __device__ __forceinline__ void proj_issue(const double *__restrict__ M, int nr,
 // reads four a-rows (two distinct per warp, broadcast) and four b-rows as
 // float4 and does 64 FMAs.  Each block of 256 points is summed in float32 and
 // added to a float32 pair (sum and rounding error), so the CTA's total keeps
-// about 48 bits.
+// about 48 bits.  w (nullable) weights every grid point of B; a tile whose A
+// and B rows are the same rows of one array copies them once.
 template <bool VEC2>
 __global__ void __launch_bounds__(256, 2) proj32_kernel(const double *__restrict__ A, int na,
-                                                        const double *__restrict__ B, int nb, long long N,
-                                                        long long span, double *__restrict__ part) {
+                                                        const double *__restrict__ B, int nb,
+                                                        const float *__restrict__ w, long long N, long long span,
+                                                        double *__restrict__ part) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     double *raw = reinterpret_cast<double *>(smem_raw);  // [stage][A|B][64][kPX]
     float(*As)[kPX + 4] = reinterpret_cast<float(*)[kPX + 4]>(smem_raw + kProjRawBytes);
@@ -268,9 +273,10 @@ __global__ void __launch_bounds__(256, 2) proj32_kernel(const double *__restrict
             s[i][j] = make_float2(0.f, 0.f);
         }
     auto stage = [&](int k) { return raw + (size_t)(k % kPStages) * 2 * kPT * kPX; };
+    const bool same = A == B && a0 == b0;  // the B rows are the A rows
     if (nsteps > 0) {
         proj_issue<VEC2>(A, na, a0, N, x0, x1, stage(0), tid);
-        proj_issue<VEC2>(B, nb, b0, N, x0, x1, stage(0) + kPT * kPX, tid);
+        if (!same) proj_issue<VEC2>(B, nb, b0, N, x0, x1, stage(0) + kPT * kPX, tid);
     }
     ptx::cp_async_commit();
     const int lx = tid & 31, lr = tid >> 5;  // converter: one grid point, rows lr + 8m
@@ -279,17 +285,19 @@ __global__ void __launch_bounds__(256, 2) proj32_kernel(const double *__restrict
         if (k + 1 < nsteps) {
             const long long xb = x0 + (long long)(k + 1) * kPX;
             proj_issue<VEC2>(A, na, a0, N, xb, x1, stage(k + 1), tid);
-            proj_issue<VEC2>(B, nb, b0, N, xb, x1, stage(k + 1) + kPT * kPX, tid);
+            if (!same) proj_issue<VEC2>(B, nb, b0, N, xb, x1, stage(k + 1) + kPT * kPX, tid);
         }
         ptx::cp_async_commit();
         ptx::cp_async_wait<1>();  // this thread's copies of step k have landed
         __syncthreads();          // everyone's have; the float32 tiles are free
-        const double *ra = stage(k), *rb = stage(k) + kPT * kPX;
+        const double *ra = stage(k), *rb = same ? stage(k) : stage(k) + kPT * kPX;
+        const long long xw = x0 + (long long)k * kPX + lx;
+        const float wx = (w != nullptr && xw < x1) ? __ldg(w + xw) : 1.f;
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
             const int r = lr + 8 * m;
             As[r][lx] = f64_to_f32(ra[r * kPX + lx]);
-            Bs[r][lx] = f64_to_f32(rb[r * kPX + lx]);
+            Bs[r][lx] = f64_to_f32(rb[r * kPX + lx]) * wx;
         }
         __syncthreads();
 #pragma unroll 2
@@ -342,8 +350,8 @@ __host__ __device__ constexpr size_t comb_smem(int na) {
     return kCombRawBytes + (size_t)kCA * kCX * sizeof(float) + (size_t)((na + kCA - 1) / kCA) * kCA * kCB * sizeof(float);
 }
 
-// out_b(x) = sgn sum_a A_a(x) C[a][b]   (a < na, b < nb; C row-major na x nb).
-// CTA (blockIdx.x, blockIdx.y) owns output vectors b0 = 64 blockIdx.y .. +63
+// out_b(x) = (accumulate ? out_b(x) : 0) + sgn sum_a A_a(x) C[a][b]
+// (a < na, b < nb; C row-major na x nb).  CTA (blockIdx.x, blockIdx.y) owns output vectors b0 = 64 blockIdx.y .. +63
 // and walks the 128-point tiles blockIdx.x, + gridDim.x, ...; each tile takes
 // ceil(na / 16) steps of 16 input vectors, whose float64 rows are copied into
 // shared memory two steps ahead (cp.async).  Thread (tx, ty) of a 32 x 8
@@ -354,7 +362,7 @@ __host__ __device__ constexpr size_t comb_smem(int na) {
 template <bool VEC2>
 __global__ void __launch_bounds__(256, 2) combine32_kernel(const double *__restrict__ A, int na,
                                                            const double *__restrict__ C, int nb, long long N,
-                                                           float sgn, double *__restrict__ out) {
+                                                           float sgn, bool accumulate, double *__restrict__ out) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     double *raw = reinterpret_cast<double *>(smem_raw);  // [stage][kCA][kCX]
     float(*As)[kCX] = reinterpret_cast<float(*)[kCX]>(smem_raw + kCombRawBytes);
@@ -435,8 +443,14 @@ __global__ void __launch_bounds__(256, 2) combine32_kernel(const double *__restr
                 for (int k = 0; k < 4; ++k) {
                     const long long x = xt + tx + 32 * k;
                     if (x < N) {
-                        if (b < nb) out[(long long)b * N + x] = f32_to_f64(sgn * acc[jp][k].x);
-                        if (b + 1 < nb) out[(long long)(b + 1) * N + x] = f32_to_f64(sgn * acc[jp][k].y);
+                        if (b < nb) {
+                            double *o = out + (long long)b * N + x;
+                            *o = (accumulate ? *o : 0.0) + f32_to_f64(sgn * acc[jp][k].x);
+                        }
+                        if (b + 1 < nb) {
+                            double *o = out + (long long)(b + 1) * N + x;
+                            *o = (accumulate ? *o : 0.0) + f32_to_f64(sgn * acc[jp][k].y);
+                        }
                     }
                     acc[jp][k] = make_float2(0.f, 0.f);
                 }
@@ -448,13 +462,14 @@ __global__ void __launch_bounds__(256, 2) combine32_kernel(const double *__restr
 
 // part (n_split x na x nb) of A^T B over the grid, float64 or float32 products
 // by plan precision; returns n_split.
-int launch_projection(kx_plan *p, const double *A, int na, const double *B, int nb, double *part, int n_split,
-                      cudaStream_t s) {
+int launch_projection(kx_plan *p, const double *A, int na, const double *B, int nb, const double *w64,
+                      const float *w32, double *part, int n_split, cudaStream_t s) {
     const long long N = (long long)p->N;
     if (int rc = prof_begin(p, PK_ACE, s)) return rc;
     if (p->precision == KX_FP64) {
         const long long span = (N + n_split - 1) / n_split;
-        gram_kernel<<<dim3((na + kG - 1) / kG, (nb + kG - 1) / kG, n_split), 256, 0, s>>>(A, na, B, nb, N, span, part);
+        gram_kernel<<<dim3((na + kG - 1) / kG, (nb + kG - 1) / kG, n_split), 256, 0, s>>>(A, na, B, nb, w64, N, span,
+                                                                                          part);
         KX_LAUNCH_CHECK("gram_kernel launch");
     } else {
         // whole pipeline steps per CTA, so that every step starts on an even grid point
@@ -465,11 +480,11 @@ int launch_projection(kx_plan *p, const double *A, int na, const double *B, int 
         if (vec2) {
             KX_CUDA_TRY(cudaFuncSetAttribute(proj32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)kProjSmem));
-            proj32_kernel<true><<<grid, 256, kProjSmem, s>>>(A, na, B, nb, N, span, part);
+            proj32_kernel<true><<<grid, 256, kProjSmem, s>>>(A, na, B, nb, w32, N, span, part);
         } else {
             KX_CUDA_TRY(cudaFuncSetAttribute(proj32_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)kProjSmem));
-            proj32_kernel<false><<<grid, 256, kProjSmem, s>>>(A, na, B, nb, N, span, part);
+            proj32_kernel<false><<<grid, 256, kProjSmem, s>>>(A, na, B, nb, w32, N, span, part);
         }
         KX_LAUNCH_CHECK("proj32_kernel launch");
     }
@@ -489,13 +504,13 @@ int projection_split(const kx_plan *p, int na, int nb) {
 }
 
 // out = sgn A C (grid vectors), float64 or float32 products by plan precision.
-int launch_combination(kx_plan *p, const double *A, int na, const double *C, int nb, double sgn, double *out,
-                       cudaStream_t s) {
+int launch_combination(kx_plan *p, const double *A, int na, const double *C, int nb, double sgn, bool accumulate,
+                       double *out, cudaStream_t s) {
     const long long N = (long long)p->N;
     if (int rc = prof_begin(p, PK_ACE_COMB, s)) return rc;
     if (p->precision == KX_FP64) {
         xi_kernel<<<dim3((unsigned)((N + 127) / 128), (unsigned)((nb + 31) / 32)), 256, 0, s>>>(A, C, na, nb, N, sgn,
-                                                                                              out);
+                                                                                              accumulate, out);
         KX_LAUNCH_CHECK("xi_kernel launch");
     } else {
         const int tiles_b = (nb + kCB - 1) / kCB;
@@ -508,11 +523,11 @@ int launch_combination(kx_plan *p, const double *A, int na, const double *C, int
         if (vec2) {
             KX_CUDA_TRY(cudaFuncSetAttribute(combine32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem));
-            combine32_kernel<true><<<grid, 256, smem, s>>>(A, na, C, nb, N, fs, out);
+            combine32_kernel<true><<<grid, 256, smem, s>>>(A, na, C, nb, N, fs, accumulate, out);
         } else {
             KX_CUDA_TRY(cudaFuncSetAttribute(combine32_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem));
-            combine32_kernel<false><<<grid, 256, smem, s>>>(A, na, C, nb, N, fs, out);
+            combine32_kernel<false><<<grid, 256, smem, s>>>(A, na, C, nb, N, fs, accumulate, out);
         }
         KX_LAUNCH_CHECK("combine32_kernel launch");
     }
@@ -534,7 +549,7 @@ int ace_run(kx_plan *p, int n_orb, const double *psi, const double *W, double *x
     double *Rinv = R + nn;
     int *bad = reinterpret_cast<int *>(Rinv + nn);
     KX_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), s));
-    if ((rc = launch_projection(p, psi, n_orb, W, n_orb, part, n_slab, s))) return rc;
+    if ((rc = launch_projection(p, psi, n_orb, W, n_orb, nullptr, nullptr, part, n_slab, s))) return rc;
     if ((rc = prof_begin(p, PK_ACE, s))) return rc;
     gram_reduce_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(part, n_slab, (int)nn, p->dV, M, M_out, A);
     KX_LAUNCH_CHECK("gram_reduce_kernel launch");
@@ -543,7 +558,7 @@ int ace_run(kx_plan *p, int n_orb, const double *psi, const double *W, double *x
     triinv_kernel<<<(n_orb + 127) / 128, 128, 0, s>>>(R, n_orb, Rinv);
     KX_LAUNCH_CHECK("triinv_kernel launch");
     if ((rc = prof_end(p, s))) return rc;
-    if ((rc = launch_combination(p, W, n_orb, Rinv, n_orb, 1.0, xi, s))) return rc;
+    if ((rc = launch_combination(p, W, n_orb, Rinv, n_orb, 1.0, false, xi, s))) return rc;
     int h_bad = 0;
     KX_CUDA_TRY(cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
     KX_CUDA_TRY(cudaStreamSynchronize(s));
@@ -560,13 +575,37 @@ int ace_apply_run(kx_plan *p, int n_xi, const double *xi, int n_vec, const doubl
     double *part = (double *)p->ws.ptr;
     double *P = part + ne * n_split;
     // P = dV xi^T phi, then out = -xi P
-    if ((rc = launch_projection(p, xi, n_xi, phi, n_vec, part, n_split, s))) return rc;
+    if ((rc = launch_projection(p, xi, n_xi, phi, n_vec, nullptr, nullptr, part, n_split, s))) return rc;
     if ((rc = prof_begin(p, PK_ACE, s))) return rc;
     gram_reduce_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(part, n_split, (int)ne, p->dV, P, nullptr,
                                                                     nullptr);
     KX_LAUNCH_CHECK("gram_reduce_kernel launch");
     if ((rc = prof_end(p, s))) return rc;
-    return launch_combination(p, xi, n_xi, P, n_vec, -1.0, out, s);
+    return launch_combination(p, xi, n_xi, P, n_vec, -1.0, false, out, s);
+}
+
+size_t grid_projection_bytes(const kx_plan *p, int na, int nb) {
+    return sizeof(double) * (size_t)na * nb * (size_t)projection_split(p, na, nb) + 256;
+}
+
+int grid_projection(kx_plan *p, const double *A, int na, const double *B, int nb, const double *w64, const float *w32,
+                    double scale, double *out, cudaStream_t s) {
+    const int n_split = projection_split(p, na, nb);
+    const size_t ne = (size_t)na * nb;
+    int rc = ensure_workspace(p, grid_projection_bytes(p, na, nb));
+    if (rc) return rc;
+    double *part = (double *)p->ws.ptr;
+    if ((rc = launch_projection(p, A, na, B, nb, w64, w32, part, n_split, s))) return rc;
+    if ((rc = prof_begin(p, PK_ACE, s))) return rc;
+    gram_reduce_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(part, n_split, (int)ne, scale, out, nullptr,
+                                                                    nullptr);
+    KX_LAUNCH_CHECK("gram_reduce_kernel launch");
+    return prof_end(p, s);
+}
+
+int grid_combination(kx_plan *p, const double *A, int na, const double *C, int nb, double sgn, bool accumulate,
+                     double *out, cudaStream_t s) {
+    return launch_combination(p, A, na, C, nb, sgn, accumulate, out, s);
 }
 
 }  // namespace kx

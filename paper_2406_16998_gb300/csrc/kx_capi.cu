@@ -64,6 +64,7 @@ int ensure_pairs(kx_plan *p, int n_orb, cudaStream_t s, long long begin, long lo
     std::vector<int> pairs, slots;
     std::vector<Group> groups;
     std::vector<int> first;
+    std::vector<unsigned char> mask((size_t)n_orb * n_orb, 0);
     pairs.reserve(2 * (size_t)(end - begin));
     slots.reserve(2 * (size_t)(end - begin));
     const int nb = (n_orb + kOrbBlock - 1) / kOrbBlock;
@@ -82,6 +83,8 @@ int ensure_pairs(kx_plan *p, int n_orb, cudaStream_t s, long long begin, long lo
             for (int si = 0; si < bi; ++si) {
                 for (int sj = (IB == JB ? si : 0); sj < (IB == JB ? bi : bj); ++sj, ++k) {
                     if (k < begin || k >= end) continue;
+                    const int oi = I0 + si, oj = (IB == JB ? I0 : J0) + sj;
+                    mask[(size_t)oi * n_orb + oj] = mask[(size_t)oj * n_orb + oi] = 1;
                     pairs.push_back(I0 + si);
                     pairs.push_back((IB == JB ? I0 : J0) + sj);
                     slots.push_back(si);
@@ -118,6 +121,15 @@ int ensure_pairs(kx_plan *p, int n_orb, cudaStream_t s, long long begin, long lo
         if (e != cudaSuccess) return cuda_error(e, "group table cudaMalloc");
         p->groups_cap = groups.size();
     }
+    if (mask.size() > p->pair_mask_cap) {
+        cudaFree(p->d_pair_mask);
+        p->d_pair_mask = nullptr;
+        p->pair_mask_cap = 0;
+        cudaError_t e = cudaMalloc(&p->d_pair_mask, mask.size());
+        if (e != cudaSuccess) return cuda_error(e, "pair mask cudaMalloc");
+        p->pair_mask_cap = mask.size();
+    }
+    KX_CUDA_TRY(cudaMemcpy(p->d_pair_mask, mask.data(), mask.size(), cudaMemcpyHostToDevice));
     if (P) {
         KX_CUDA_TRY(cudaMemcpy(p->d_pairs, pairs.data(), sizeof(int) * 2 * P, cudaMemcpyHostToDevice));
         KX_CUDA_TRY(cudaMemcpy(p->d_item_slot, slots.data(), sizeof(int) * 2 * P, cudaMemcpyHostToDevice));
@@ -163,6 +175,7 @@ int prof_end(kx_plan *p, cudaStream_t s) {
 static int reserve(kx_plan *p, int n_orb) {
     int rc = ensure_pairs(p, n_orb, nullptr);
     if (rc) return rc;
+    if ((rc = mp_reserve(p, n_orb))) return rc;
     if (p->precision == KX_FP64) {
         const long P = (long)n_orb * (n_orb + 1) / 2;
         const size_t budget = (size_t)2 << 30;
@@ -175,9 +188,13 @@ static int reserve(kx_plan *p, int n_orb) {
 }
 
 static int dispatch_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, double *vx, double *ex,
-                       bool energy_only, cudaStream_t s) {
-    if (p->precision == KX_FP64) return fp64_vx(p, n_orb, psi, occ, vx, ex, energy_only, s);
-    return tc_vx(p, n_orb, psi, occ, vx, ex, energy_only, s);
+                       bool energy_only, cudaStream_t s, long pair_begin = 0, long pair_end = -1) {
+    int rc = p->precision == KX_FP64 ? fp64_vx(p, n_orb, psi, occ, vx, ex, energy_only, s, pair_begin, pair_end)
+                                     : tc_vx(p, n_orb, psi, occ, vx, ex, energy_only, s, pair_begin, pair_end);
+    // boundary values from the multipole expansion: the rank-K correction of
+    // the same pair range (its mask was built by the solve's ensure_pairs)
+    if (!rc && p->mp_lmax >= 0) rc = mp_correct_vx(p, n_orb, psi, occ, vx, ex, energy_only, s);
+    return rc;
 }
 
 static int check_plan(const kx_plan *p) {
@@ -309,8 +326,9 @@ int kx_apply_fL(kx_plan *plan, int n_rhs, const double *b, double *x, kx_stream 
     if (!b || !x) return set_error(KX_ERR_ARG, "kx_apply_fL: NULL buffer");
     if (b == x) return set_error(KX_ERR_ARG, "kx_apply_fL: x must not overlap b");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    if (plan->precision == KX_FP64) return fp64_apply_fL(plan, n_rhs, b, x, s);
-    return tc_apply_fL(plan, n_rhs, b, x, s);
+    int rc = plan->precision == KX_FP64 ? fp64_apply_fL(plan, n_rhs, b, x, s) : tc_apply_fL(plan, n_rhs, b, x, s);
+    if (!rc && plan->mp_lmax >= 0) rc = mp_correct_apply(plan, n_rhs, b, x, s);
+    return rc;
 }
 
 int kx_apply_fL_noalloc(kx_plan *plan, int n_rhs, const double *b, double *x, kx_stream stream) {
@@ -319,6 +337,8 @@ int kx_apply_fL_noalloc(kx_plan *plan, int n_rhs, const double *b, double *x, kx
     if (n_rhs == 0) return KX_OK;
     if (!b || !x) return set_error(KX_ERR_ARG, "kx_apply_fL_noalloc: NULL buffer");
     if (b == x) return set_error(KX_ERR_ARG, "kx_apply_fL_noalloc: x must not overlap b");
+    if (plan->mp_lmax >= 0)
+        return set_error(KX_ERR_UNSUPPORTED, "kx_apply_fL_noalloc: not available with multipole boundary values");
     return tc_apply_fL_noalloc(plan, n_rhs, b, x, reinterpret_cast<cudaStream_t>(stream));
 }
 
@@ -346,9 +366,7 @@ int kx_vx_apply_pairs(kx_plan *plan, int n_orb, const double *psi, const double 
         if (e_x) KX_CUDA_TRY(cudaMemsetAsync(e_x, 0, sizeof(double), s));
         return KX_OK;
     }
-    if (plan->precision == KX_FP64)
-        return fp64_vx(plan, n_orb, psi, occ, vx_psi, e_x, false, s, (long)pair_begin, (long)pair_end);
-    return tc_vx(plan, n_orb, psi, occ, vx_psi, e_x, false, s, (long)pair_begin, (long)pair_end);
+    return dispatch_vx(plan, n_orb, psi, occ, vx_psi, e_x, false, s, (long)pair_begin, (long)pair_end);
 }
 
 int kx_energy(kx_plan *plan, int n_orb, const double *psi, const double *occ, double *e_x, kx_stream stream) {
@@ -414,6 +432,8 @@ int kx_vx_apply_host(kx_plan *plan, int n_orb, const double *psi, const double *
         if (e != cudaSuccess) x->rc = cuda_error(e, "kx_vx_apply_host row copy");
         x->copied = o1;
     };
+    // with multipole boundary values every row changes after the pair loop: no early copies
+    if (plan->mp_lmax >= 0) plan->final_hook = FinalHook{};
     int rc = dispatch_vx(plan, n_orb, d_psi, d_occ, d_vx, d_ex, false, s);
     plan->final_hook = FinalHook{};
     if (!rc) rc = ctx.rc;
@@ -458,6 +478,11 @@ int kx_ace_apply(kx_plan *plan, int n_xi, const double *xi, int n_vec, const dou
     if (overlaps(out, (size_t)n_vec, xi, (size_t)n_xi) || overlaps(out, (size_t)n_vec, phi, (size_t)n_vec))
         return set_error(KX_ERR_ARG, "kx_ace_apply: out must not overlap xi or phi");
     return ace_apply_run(plan, n_xi, xi, n_vec, phi, out, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int kx_plan_set_multipole(kx_plan *plan, int l_max) {
+    if (int rc = check_plan(plan)) return rc;
+    return mp_set(plan, l_max);
 }
 
 int kx_plan_status(kx_plan *plan, int *status_out, kx_stream stream) {

@@ -126,6 +126,17 @@ struct kx_plan_s {
     kx::FinalHook final_hook;
     cudaStream_t copy_stream = nullptr;
     std::vector<cudaEvent_t> copy_events;
+    // pair {i, j} in the current pair range (n_orb x n_orb bytes, symmetric)
+    unsigned char *d_pair_mask = nullptr;
+    size_t pair_mask_cap = 0;
+    // multipole boundary values (kx_plan_set_multipole): order, number of
+    // harmonics K = (l_max + 1)^2, and per harmonic the regular solid harmonic
+    // R_k and the correction field h_k on the grid (K x N, float64 and float32)
+    int mp_lmax = -1;
+    int mp_K = 0;
+    double *d_mpR = nullptr, *d_mpH = nullptr;
+    float *d_mpR32 = nullptr, *d_mpH32 = nullptr;
+    kx::Workspace mp_scratch;
 };
 
 namespace kx {
@@ -162,5 +173,27 @@ int ace_run(kx_plan *p, int n_orb, const double *psi, const double *W, double *x
             cudaStream_t s);
 int ace_apply_run(kx_plan *p, int n_xi, const double *xi, int n_vec, const double *phi, double *out,
                   cudaStream_t s);
+// ---- multipole boundary values (kx_mp.cu)
+int mp_set(kx_plan *p, int l_max);
+void mp_free(kx_plan *p);
+int mp_reserve(kx_plan *p, int n_orb);
+// Vx psi and E_x (or E_x alone) of the pair range of the last ensure_pairs:
+// adds the rank-K boundary correction to the homogeneous result
+int mp_correct_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, double *vx, double *ex,
+                  bool energy_only, cudaStream_t s);
+// x += sum_k Q_k(b) h_k for n_rhs right-hand sides b
+int mp_correct_apply(kx_plan *p, int n_rhs, const double *b, double *x, cudaStream_t s);
+
+// out[a][b] = scale sum_x A_a(x) B_b(x) w(x) over the grid (w nullable; the
+// float64 weights serve float64 plans, the float32 ones the others), partial
+// sums per grid-point range added in float64 in a fixed order.  Uses the plan
+// workspace (grid_projection_bytes).
+size_t grid_projection_bytes(const kx_plan *p, int na, int nb);
+int grid_projection(kx_plan *p, const double *A, int na, const double *B, int nb, const double *w64, const float *w32,
+                    double scale, double *out, cudaStream_t s);
+// out = (accumulate ? out : 0) + sgn A C for na grid vectors A and the na x nb
+// row-major float64 matrix C; no workspace.
+int grid_combination(kx_plan *p, const double *A, int na, const double *C, int nb, double sgn, bool accumulate,
+                     double *out, cudaStream_t s);
 
 }  // namespace kx

@@ -1,0 +1,470 @@
+// Dirichlet values from the multipole expansion of the source (Sec. 4: the
+// linear systems of isolated systems take their boundary values from the
+// multipole expansion of the Coulomb kernel, imposed through the right-hand
+// side).  With the exterior values phi_ext of the expansion of rho's potential
+// about the box centre, moving them to the right-hand side of the
+// finite-difference equation gives
+//     phi = f(L) (rho + L_ext phi_ext / (4 pi)).
+// The expansion is linear in rho through its moments Q_k(rho) = dV sum_x
+// rho(x) R_k(x - c), so with the plan's fields
+//     g_k = L_ext I_k / (4 pi)   (boundary layer of the irregular harmonic I_k)
+//     h_k = f(L) g_k
+// the solution is phi = f(L) rho + sum_k Q_k(rho) h_k: the existing solve plus
+// a rank-K correction (K = (l_max + 1)^2).  For the exchange operator, with
+// rho_ij = psi_i psi_j,
+//     (Vx psi)_i -= sum_k h_k sum_j g_j Q_k(ij) psi_j,
+//     E_x        -= 1/2 dV sum_ij g_i g_j <psi_i psi_j, sum_k Q_k(ij) h_k>.
+// R_k and I_k are the real solid harmonics in Schmidt normalisation, for which
+// sum_k R_k(v') I_k(v) = sum_l |v'|^l / |v|^(l+1) P_l(cos gamma), the Legendre
+// expansion of 1 / |v - v'|.
+#include "kx_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+namespace kx {
+namespace {
+
+constexpr int kMpMaxL = 8;
+constexpr int kMpMaxK = (kMpMaxL + 1) * (kMpMaxL + 1);
+constexpr int kMaxHalf = 16;  // stencil half-width limit (order <= 32)
+
+struct MpGeom {
+    int n[3];
+    double h[3], c[3];
+    int m;                 // stencil half-width
+    double w[kMaxHalf + 1];  // centred second-derivative weights for h = 1
+    int L, K;
+};
+
+__device__ double mp_factorial(int n) {
+    double f = 1.0;
+    for (int i = 2; i <= n; ++i) f *= i;
+    return f;
+}
+
+// R[k] for k = l^2 + (m == 0 ? 0 : 2m - 1 + t), t = 0 (cos) / 1 (sin):
+// r^l P_l^m(cos theta) (cos | sin)(m phi) sqrt((2 - delta_m0) (l-m)! / (l+m)!),
+// evaluated as polynomials: (x + i y)^m times A_l^m(z, r^2), where
+// A_m^m = (2m-1)!!, A_{m+1}^m = (2m+1) z A_m^m and
+// (l - m) A_l^m = (2l - 1) z A_{l-1}^m - (l + m - 1) r^2 A_{l-2}^m.
+__device__ void solid_harmonics(double x, double y, double z, int L, double *R) {
+    const double r2 = x * x + y * y + z * z;
+    double cm = 1.0, sm = 0.0, dfact = 1.0;
+    for (int m = 0; m <= L; ++m) {
+        double p1 = 0.0, p2 = 0.0;
+        for (int l = m; l <= L; ++l) {
+            double a;
+            if (l == m)
+                a = dfact;
+            else if (l == m + 1)
+                a = (2 * m + 1) * z * p1;
+            else
+                a = ((2 * l - 1) * z * p1 - (l + m - 1) * r2 * p2) / (l - m);
+            p2 = p1;
+            p1 = a;
+            const double nrm = sqrt((m == 0 ? 1.0 : 2.0) * mp_factorial(l - m) / mp_factorial(l + m));
+            if (m == 0) {
+                R[l * l] = nrm * a;
+            } else {
+                R[l * l + 2 * m - 1] = nrm * a * cm;
+                R[l * l + 2 * m] = nrm * a * sm;
+            }
+        }
+        const double cn = x * cm - y * sm, sn = x * sm + y * cm;
+        cm = cn;
+        sm = sn;
+        dfact *= (2 * m + 1);
+    }
+}
+
+// One thread per grid point: R_k(x - c) and g_k(x) = (1 / 4 pi) sum over the
+// exterior points e the stencil of x reaches of w_|d| / h_a^2 I_k(e - c).
+__global__ void mp_fields_kernel(const MpGeom G, long long N, double *__restrict__ R, double *__restrict__ Gk) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N) return;
+    const int i1 = (int)(idx % G.n[0]);
+    const int i2 = (int)((idx / G.n[0]) % G.n[1]);
+    const int i3 = (int)(idx / ((long long)G.n[0] * G.n[1]));
+    const int ii[3] = {i1, i2, i3};
+    double v[3];
+    for (int a = 0; a < 3; ++a) v[a] = (ii[a] + 1) * G.h[a] - G.c[a];
+    double Rv[kMpMaxK], g[kMpMaxK];
+    solid_harmonics(v[0], v[1], v[2], G.L, Rv);
+    for (int k = 0; k < G.K; ++k) {
+        R[(long long)k * N + idx] = Rv[k];
+        g[k] = 0.0;
+    }
+    for (int a = 0; a < 3; ++a) {
+        for (int side = 0; side < 2; ++side) {
+            // exterior indices e on this side within reach: |e - i_a| <= m
+            const int e0 = side == 0 ? ii[a] - G.m : G.n[a];
+            const int e1 = side == 0 ? -1 : ii[a] + G.m;
+            for (int e = e0; e <= e1; ++e) {
+                const int d = e > ii[a] ? e - ii[a] : ii[a] - e;
+                double p[3] = {v[0], v[1], v[2]};
+                p[a] = (e + 1) * G.h[a] - G.c[a];
+                solid_harmonics(p[0], p[1], p[2], G.L, Rv);
+                const double r = sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+                const double wd = G.w[d] / (G.h[a] * G.h[a]);
+                double inv = 1.0 / r;  // 1 / r^(2l+1), l = 0 first
+                for (int l = 0; l <= G.L; ++l) {
+                    for (int k = l * l; k < (l + 1) * (l + 1); ++k) g[k] += wd * Rv[k] * inv;
+                    inv /= r * r;
+                }
+            }
+        }
+    }
+    const double s = 1.0 / (4.0 * 3.14159265358979323846);
+    for (int k = 0; k < G.K; ++k) Gk[(long long)k * N + idx] = g[k] * s;
+}
+
+__global__ void to_f32_kernel(const double *__restrict__ in, float *__restrict__ out, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = (float)in[i];
+}
+
+// C[k][j][i] = g_j mask(i, j) Q[k][i][j]   (T = float or double)
+template <typename T>
+__global__ void mp_coef_kernel(const double *__restrict__ Q, const unsigned char *__restrict__ mask,
+                               const double *__restrict__ occ, int n, int K, T *__restrict__ C) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nn = (long long)n * n;
+    if (e >= nn * K) return;
+    const int k = (int)(e / nn), i = (int)((e % nn) / n), j = (int)(e % n);
+    const double gj = occ ? occ[j] : 1.0;
+    C[(long long)k * nn + (long long)j * n + i] = (T)(mask[(long long)i * n + j] ? gj * Q[e] : 0.0);
+}
+
+constexpr int kMcX = 128;  // correction tile: 128 grid points x 64 orbitals
+
+// vx_i(x) -= T_i(x), T_i(x) = sum_k h_k(x) sum_j C[k][j][i] psi_j(x), float32
+// products (psi converted once per tile into shared memory, C[k] staged per k);
+// e_part[CTA] = sum over the tile of g_i psi_i(x) T_i(x).  Thread (tx, ty) owns
+// x = x0 + tx + 32 q (q < 4) and i = i0 + 8 ty + u (u < 8).
+__global__ void __launch_bounds__(256) mp_combine32_kernel(const double *__restrict__ psi, int n,
+                                                           const float *__restrict__ C, const float *__restrict__ H,
+                                                           int K, const double *__restrict__ occ, long long N,
+                                                           double *__restrict__ vx, double *__restrict__ e_part) {
+    extern __shared__ __align__(16) float mp_smem[];
+    float *Ps = mp_smem;                  // [n][kMcX]
+    float *Cs = mp_smem + (size_t)n * kMcX;  // [n][64]
+    __shared__ double red[8];
+    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+    const long long x0 = (long long)blockIdx.x * kMcX;
+    const int i0 = blockIdx.y * 64;
+    for (int e = tid; e < n * kMcX; e += 256) {
+        const int j = e / kMcX, c = e % kMcX;
+        const long long x = x0 + c;
+        Ps[e] = x < N ? (float)psi[(long long)j * N + x] : 0.f;
+    }
+    float acc[8][4];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[u][q] = 0.f;
+    for (int k = 0; k < K; ++k) {
+        __syncthreads();
+        const float *Ck = C + (size_t)k * n * n;
+        for (int e = tid; e < n * 64; e += 256) {
+            const int j = e >> 6, c = e & 63;
+            Cs[e] = i0 + c < n ? Ck[(size_t)j * n + i0 + c] : 0.f;
+        }
+        __syncthreads();
+        float t[8][4];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) t[u][q] = 0.f;
+        for (int j = 0; j < n; ++j) {
+            float pv[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) pv[q] = Ps[j * kMcX + tx + 32 * q];
+            const float4 c0 = *reinterpret_cast<const float4 *>(&Cs[j * 64 + 8 * ty]);
+            const float4 c1 = *reinterpret_cast<const float4 *>(&Cs[j * 64 + 8 * ty + 4]);
+            const float cv[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) t[u][q] = fmaf(cv[u], pv[q], t[u][q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const long long x = x0 + tx + 32 * q;
+            const float hk = x < N ? __ldg(H + (size_t)k * N + x) : 0.f;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc[u][q] = fmaf(hk, t[u][q], acc[u][q]);
+        }
+    }
+    double e = 0.0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int i = i0 + 8 * ty + u;
+        if (i >= n) continue;
+        const double gi = occ ? occ[i] : 1.0;
+        float ei = 0.f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const long long x = x0 + tx + 32 * q;
+            if (x >= N) continue;
+            vx[(long long)i * N + x] -= (double)acc[u][q];
+            ei = fmaf(Ps[i * kMcX + tx + 32 * q], acc[u][q], ei);
+        }
+        e += gi * (double)ei;
+    }
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    if ((tid & 31) == 0) red[ty] = e;
+    __syncthreads();
+    if (tid == 0) {
+        double sum = 0.0;
+        for (int w = 0; w < 8; ++w) sum += red[w];
+        e_part[(long long)blockIdx.y * gridDim.x + blockIdx.x] = sum;
+    }
+}
+
+// float64 form: one thread per (grid point, orbital), block partials of the energy.
+__global__ void mp_combine64_kernel(const double *__restrict__ psi, int n, const double *__restrict__ C,
+                                    const double *__restrict__ H, int K, const double *__restrict__ occ, long long N,
+                                    double *__restrict__ vx, double *__restrict__ e_part) {
+    __shared__ double red[256];
+    const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    double e = 0.0;
+    if (x < N) {
+        double T = 0.0;
+        for (int k = 0; k < K; ++k) {
+            const double *Ck = C + (size_t)k * n * n;
+            double t = 0.0;
+            for (int j = 0; j < n; ++j) t = fma(Ck[(size_t)j * n + i], psi[(long long)j * N + x], t);
+            T = fma(H[(size_t)k * N + x], t, T);
+        }
+        vx[(long long)i * N + x] -= T;
+        e = (occ ? occ[i] : 1.0) * psi[(long long)i * N + x] * T;
+    }
+    red[threadIdx.x] = e;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) e_part[(long long)blockIdx.y * gridDim.x + blockIdx.x] = red[0];
+}
+
+// ex += scale * sum of the partials, in index order (one thread: deterministic).
+__global__ void mp_energy_add_kernel(const double *__restrict__ part, long long count, double scale,
+                                     double *__restrict__ ex) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    double s = 0.0;
+    for (long long i = 0; i < count; ++i) s += part[i];
+    *ex += scale * s;
+}
+
+// ex += -1/2 sum_{i,j} g_i g_j mask(i,j) sum_k Q_k(ij) P_k(ij); fixed-order block reduction.
+__global__ void mp_energy_qp_kernel(const double *__restrict__ Q, const double *__restrict__ P,
+                                    const unsigned char *__restrict__ mask, const double *__restrict__ occ, int n,
+                                    int K, double *__restrict__ ex) {
+    __shared__ double red[256];
+    const long long nn = (long long)n * n;
+    double s = 0.0;
+    for (long long e = threadIdx.x; e < nn; e += blockDim.x) {
+        const int i = (int)(e / n), j = (int)(e % n);
+        if (!mask[e]) continue;
+        double t = 0.0;
+        for (int k = 0; k < K; ++k) t += Q[(long long)k * nn + e] * P[(long long)k * nn + e];
+        s += (occ ? occ[i] * occ[j] : 1.0) * t;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *ex += -0.5 * red[0];
+}
+
+std::vector<double> centred_weights(int order) {
+    const int m = order / 2;
+    std::vector<double> w(m + 1, 0.0);
+    for (int p = 1; p <= m; ++p) w[0] -= 2.0 / (double(p) * p);
+    double fm = 1.0;
+    for (int i = 2; i <= m; ++i) fm *= i;
+    for (int p = 1; p <= m; ++p) {
+        double fmp = 1.0, fpp = 1.0;
+        for (int i = 2; i <= m - p; ++i) fmp *= i;
+        for (int i = 2; i <= m + p; ++i) fpp *= i;
+        w[p] = 2.0 * ((p % 2) ? 1.0 : -1.0) * fm * fm / (double(p) * p * fmp * fpp);
+    }
+    return w;
+}
+
+size_t mp_scratch_bytes(int n, int K, long long N) {
+    const size_t kn2 = (size_t)K * n * n;
+    const size_t tiles = (size_t)((N + kMcX - 1) / kMcX) * ((n + 63) / 64);
+    const size_t part64 = (size_t)((N + 255) / 256) * n;
+    return sizeof(double) * (2 * kn2 + kn2 + std::max(tiles, part64)) + 1024;
+}
+
+}  // namespace
+
+void mp_free(kx_plan *p) {
+    cudaFree(p->d_mpR);
+    cudaFree(p->d_mpH);
+    cudaFree(p->d_mpR32);
+    cudaFree(p->d_mpH32);
+    cudaFree(p->mp_scratch.ptr);
+    p->d_mpR = p->d_mpH = nullptr;
+    p->d_mpR32 = p->d_mpH32 = nullptr;
+    p->mp_scratch = Workspace{};
+    p->mp_lmax = -1;
+    p->mp_K = 0;
+}
+
+int mp_set(kx_plan *p, int l_max) {
+    if (l_max < 0) {
+        cudaError_t e = cudaDeviceSynchronize();
+        mp_free(p);
+        return e == cudaSuccess ? KX_OK : cuda_error(e, "kx_plan_set_multipole");
+    }
+    if (l_max > kMpMaxL) return set_error(KX_ERR_ARG, "kx_plan_set_multipole: l_max must be in -1..8");
+    if (p->kind != 0 || p->bc[0] != 0 || p->bc[1] != 0 || p->bc[2] != 0)
+        return set_error(KX_ERR_UNSUPPORTED,
+                         "kx_plan_set_multipole: needs Dirichlet boundaries on all axes and the unscreened kernel");
+    if (p->fd_order / 2 > kMaxHalf) return set_error(KX_ERR_UNSUPPORTED, "kx_plan_set_multipole: FD order too high");
+    KX_CUDA_TRY(cudaDeviceSynchronize());
+    mp_free(p);
+    const int K = (l_max + 1) * (l_max + 1);
+    const long long N = (long long)p->N;
+    MpGeom G{};
+    for (int a = 0; a < 3; ++a) {
+        G.n[a] = p->n[a];
+        G.h[a] = p->h[a];
+        G.c[a] = (p->n[a] + 1) * p->h[a] / 2.0;
+    }
+    G.m = p->fd_order / 2;
+    const std::vector<double> w = centred_weights(p->fd_order);
+    for (int d = 0; d <= G.m; ++d) G.w[d] = w[d];
+    G.L = l_max;
+    G.K = K;
+    const size_t fld = sizeof(double) * (size_t)K * N;
+    double *Gk = nullptr;
+    cudaError_t e = cudaMalloc(&p->d_mpR, fld);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_mpH, fld);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_mpR32, fld / 2);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_mpH32, fld / 2);
+    if (e == cudaSuccess) e = cudaMalloc(&Gk, fld);
+    if (e != cudaSuccess) {
+        cudaFree(Gk);
+        mp_free(p);
+        return cuda_error(e, "kx_plan_set_multipole cudaMalloc");
+    }
+    mp_fields_kernel<<<(unsigned)((N + 127) / 128), 128>>>(G, N, p->d_mpR, Gk);
+    e = cudaGetLastError();
+    int rc = e == cudaSuccess ? KX_OK : cuda_error(e, "mp_fields_kernel launch");
+    // h_k = f(L) g_k with the float64 solver (set-up, once per plan)
+    if (!rc) rc = fp64_apply_fL(p, K, Gk, p->d_mpH, nullptr);
+    if (!rc) {
+        to_f32_kernel<<<1024, 256>>>(p->d_mpR, p->d_mpR32, (long long)K * N);
+        to_f32_kernel<<<1024, 256>>>(p->d_mpH, p->d_mpH32, (long long)K * N);
+        e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) rc = cuda_error(e, "kx_plan_set_multipole set-up");
+    }
+    cudaFree(Gk);
+    if (rc) {
+        mp_free(p);
+        return rc;
+    }
+    p->mp_lmax = l_max;
+    p->mp_K = K;
+    return KX_OK;
+}
+
+int mp_reserve(kx_plan *p, int n_orb) {
+    if (p->mp_lmax < 0) return KX_OK;
+    const size_t need = mp_scratch_bytes(n_orb, p->mp_K, (long long)p->N);
+    if (p->mp_scratch.bytes < need) {
+        cudaFree(p->mp_scratch.ptr);
+        p->mp_scratch = Workspace{};
+        cudaError_t e = cudaMalloc(&p->mp_scratch.ptr, need);
+        if (e != cudaSuccess) return cuda_error(e, "multipole scratch cudaMalloc");
+        p->mp_scratch.bytes = need;
+    }
+    return ensure_workspace(p, grid_projection_bytes(p, std::max(n_orb, p->mp_K), std::max(n_orb, p->mp_K)));
+}
+
+int mp_correct_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, double *vx, double *ex,
+                  bool energy_only, cudaStream_t s) {
+    if (p->precision != KX_FP64 && n_orb > 256)
+        return set_error(KX_ERR_UNSUPPORTED, "multipole boundary values: at most 256 orbitals on tensor-core plans");
+    int rc = mp_reserve(p, n_orb);
+    if (rc) return rc;
+    const int K = p->mp_K, n = n_orb;
+    const long long N = (long long)p->N;
+    const size_t nn = (size_t)n * n;
+    const bool f64 = p->precision == KX_FP64;
+    double *Q = (double *)p->mp_scratch.ptr;
+    double *P = Q + (size_t)K * nn;  // energy-only: projections on h_k; otherwise C
+    double *part = P + (size_t)K * nn + (size_t)K * nn;
+    const unsigned char *mask = p->d_pair_mask;
+    // moments Q_k(ij) = dV sum_x R_k psi_i psi_j
+    for (int k = 0; k < K; ++k)
+        if ((rc = grid_projection(p, psi, n, psi, n, f64 ? p->d_mpR + (size_t)k * N : nullptr,
+                                  f64 ? nullptr : p->d_mpR32 + (size_t)k * N, p->dV, Q + (size_t)k * nn, s)))
+            return rc;
+    if (energy_only) {
+        for (int k = 0; k < K; ++k)
+            if ((rc = grid_projection(p, psi, n, psi, n, f64 ? p->d_mpH + (size_t)k * N : nullptr,
+                                      f64 ? nullptr : p->d_mpH32 + (size_t)k * N, p->dV, P + (size_t)k * nn, s)))
+                return rc;
+        if (ex) {
+            mp_energy_qp_kernel<<<1, 256, 0, s>>>(Q, P, mask, occ, n, K, ex);
+            KX_LAUNCH_CHECK("mp_energy_qp_kernel launch");
+        }
+        return KX_OK;
+    }
+    const unsigned cb = (unsigned)((nn * K + 255) / 256);
+    if (f64) {
+        double *C = P;
+        mp_coef_kernel<double><<<cb, 256, 0, s>>>(Q, mask, occ, n, K, C);
+        KX_LAUNCH_CHECK("mp_coef_kernel launch");
+        const dim3 grid((unsigned)((N + 255) / 256), (unsigned)n);
+        mp_combine64_kernel<<<grid, 256, 0, s>>>(psi, n, C, p->d_mpH, K, occ, N, vx, part);
+        KX_LAUNCH_CHECK("mp_combine64_kernel launch");
+        if (ex) {
+            mp_energy_add_kernel<<<1, 1, 0, s>>>(part, (long long)grid.x * grid.y, -0.5 * p->dV, ex);
+            KX_LAUNCH_CHECK("mp_energy_add_kernel launch");
+        }
+        return KX_OK;
+    }
+    float *C = reinterpret_cast<float *>(P);
+    mp_coef_kernel<float><<<cb, 256, 0, s>>>(Q, mask, occ, n, K, C);
+    KX_LAUNCH_CHECK("mp_coef_kernel launch");
+    const dim3 grid((unsigned)((N + kMcX - 1) / kMcX), (unsigned)((n + 63) / 64));
+    const size_t smem = sizeof(float) * (size_t)n * (kMcX + 64);
+    KX_CUDA_TRY(cudaFuncSetAttribute(mp_combine32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    mp_combine32_kernel<<<grid, 256, smem, s>>>(psi, n, C, p->d_mpH32, K, occ, N, vx, part);
+    KX_LAUNCH_CHECK("mp_combine32_kernel launch");
+    if (ex) {
+        mp_energy_add_kernel<<<1, 1, 0, s>>>(part, (long long)grid.x * grid.y, -0.5 * p->dV, ex);
+        KX_LAUNCH_CHECK("mp_energy_add_kernel launch");
+    }
+    return KX_OK;
+}
+
+int mp_correct_apply(kx_plan *p, int n_rhs, const double *b, double *x, cudaStream_t s) {
+    const int K = p->mp_K;
+    const size_t need = sizeof(double) * (size_t)K * n_rhs + 256;
+    if (p->mp_scratch.bytes < need) {
+        cudaFree(p->mp_scratch.ptr);
+        p->mp_scratch = Workspace{};
+        cudaError_t e = cudaMalloc(&p->mp_scratch.ptr, need);
+        if (e != cudaSuccess) return cuda_error(e, "multipole scratch cudaMalloc");
+        p->mp_scratch.bytes = need;
+    }
+    double *Cb = (double *)p->mp_scratch.ptr;  // [K][n_rhs]: dV sum_x R_k b_r
+    int rc = grid_projection(p, p->d_mpR, K, b, n_rhs, nullptr, nullptr, p->dV, Cb, s);
+    if (rc) return rc;
+    return grid_combination(p, p->d_mpH, K, Cb, n_rhs, 1.0, true, x, s);
+}
+
+}  // namespace kx

@@ -307,6 +307,9 @@ void plan_free(kx_plan *p) {
     cudaFree(p->d_pairs);
     cudaFree(p->d_item_slot);
     cudaFree(p->d_groups);
+    cudaFree(p->d_pair_mask);
+    p->d_pair_mask = nullptr;
+    mp_free(p);
     for (cudaEvent_t e : p->copy_events) cudaEventDestroy(e);
     p->copy_events.clear();
     if (p->copy_stream) cudaStreamDestroy(p->copy_stream);

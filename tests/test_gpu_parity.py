@@ -208,6 +208,126 @@ def test_ace_matches_oracle(kx):
     assert relmax(xi.cpu().numpy().T, xi_ref) < 1e-10
 
 
+# --------------------------------------------------------------------------
+# Dirichlet values from the multipole expansion (isolated systems, Sec. 4)
+# --------------------------------------------------------------------------
+MP_GRID = ((16, 12, 20), (0.5, 0.55, 0.45), (D, D, D))
+
+
+@pytest.mark.parametrize("prec,l_max", [(0, 0), (0, 2), (0, 4), (1, 2), (1, 4)])
+def test_multipole_apply_fL_matches_oracle(kx, prec, l_max):
+    n, h, bc = MP_GRID
+    op = oracle.Plan(n, h, bc, U)
+    b = workloads.random_field(op.N, 3, 71 + l_max)
+    ref = np.stack([oracle.apply_fL_multipole(op, b[:, r], l_max) for r in range(3)], axis=1)
+    plan = kx.Plan(n, h, bc, U, precision=prec)
+    plan.set_multipole(l_max)
+    x = kx.kx_apply_fL(plan, dev(b.T)).cpu().numpy().T
+    assert relmax(x, ref) < (1e-11 if prec == 0 else TOL[1]["fl"])
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_multipole_vx_and_energy_match_oracle(kx, prec):
+    n, h, bc = MP_GRID
+    sysd = system(n, h, bc, U, 5, 73)
+    psi = workloads.make_orbitals(sysd)
+    occ = np.array([1.0, 0.9, 0.75, 0.5, 0.25])
+    op = oracle.Plan(n, h, bc, U)
+    vx_ref, ex_ref = oracle.vx_apply(op, psi, occ, l_max=3)
+    vx0_ref, ex0_ref = oracle.vx_apply(op, psi, occ)
+    plan = kx.Plan(n, h, bc, U, precision=prec)
+    plan.set_multipole(3)
+    psi_d, occ_d = dev(psi.T), dev(occ)
+    vx, ex = kx.kx_vx_apply(plan, psi_d, occ_d)
+    e_only = kx.kx_energy(plan, psi_d, occ_d)[0].item()
+    tol = TOL[prec]
+    assert relmax(vx.cpu().numpy().T, vx_ref) < tol["vx"]
+    assert abs(ex.item() - ex_ref) < tol["ex"] * abs(ex_ref)
+    assert abs(e_only - ex_ref) < tol["ex"] * abs(ex_ref)
+    # the boundary values matter: the result differs from zero boundary values
+    assert relmax(vx_ref, vx0_ref) > 1e-3
+    plan.set_multipole(-1)
+    vx0, ex0 = kx.kx_vx_apply(plan, psi_d, occ_d)
+    assert relmax(vx0.cpu().numpy().T, vx0_ref) < tol["vx"]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_multipole_pair_ranges_host_path_and_batch(kx, prec):
+    """With boundary values from the expansion: pair ranges add up to the full
+    apply, the host-buffer entry point and a captured batch give the device
+    path's result."""
+    from paper_2406_16998_gb300 import shard
+    n, h, bc = MP_GRID
+    psi = workloads.make_orbitals(system(n, h, bc, U, 6, 79))
+    plan = kx.Plan(n, h, bc, U, precision=prec)
+    plan.set_multipole(2)
+    x = dev(psi.T)
+    full, e_full = kx.kx_vx_apply(plan, x)
+    acc = torch.zeros_like(full)
+    e_acc = 0.0
+    for r in range(3):
+        a, b = shard.pair_range(6, r, 3)
+        part, e_part = kx.kx_vx_apply_pairs(plan, x, a, b)
+        acc += part
+        e_acc += e_part.item()
+    tol = 1e-12 if prec == 0 else 1e-6
+    assert relmax(acc.cpu().numpy(), full.cpu().numpy()) < tol
+    assert abs(e_acc - e_full.item()) < tol * abs(e_full.item())
+    vx_h, ex_h = kx.kx_vx_apply_host(plan, torch.from_numpy(np.ascontiguousarray(psi.T)))
+    assert np.array_equal(vx_h.numpy(), full.cpu().numpy()) and ex_h == e_full.item()
+    out = torch.empty_like(full)
+    ex_b = torch.empty(1, dtype=torch.float64, device="cuda")
+    bt = kx.Batch([plan], [6])
+    for _ in range(2):
+        bt.run([x], [out], ex_b)
+    torch.cuda.synchronize()
+    bt.close()
+    assert relmax(out.cpu().numpy(), full.cpu().numpy()) < 1e-12
+    assert abs(ex_b.item() - e_full.item()) < 1e-12 * abs(e_full.item())
+
+
+def test_multipole_rejects_unsupported_plans(kx):
+    plan = kx.Plan((16, 16, 16), (0.5,) * 3, (P, P, D), U, precision=1)
+    with pytest.raises(kx.KxError) as ei:
+        plan.set_multipole(2)
+    assert ei.value.code == kx.KX_ERR_UNSUPPORTED
+    plan = kx.Plan((16, 16, 16), (0.5,) * 3, (D, D, D), S, precision=1)
+    with pytest.raises(kx.KxError) as ei:
+        plan.set_multipole(2)
+    assert ei.value.code == kx.KX_ERR_UNSUPPORTED
+    plan = kx.Plan((16, 16, 16), (0.5,) * 3, (D, D, D), U, precision=1)
+    with pytest.raises(kx.KxError) as ei:
+        plan.set_multipole(9)
+    assert ei.value.code == kx.KX_ERR_ARG
+    plan.set_multipole(1)
+    b = dev(workloads.random_field(plan.N, 1, 3).T)
+    with pytest.raises(kx.KxError) as ei:
+        kx.kx_apply_fL_noalloc(plan, b, torch.empty_like(b))
+    assert ei.value.code == kx.KX_ERR_UNSUPPORTED
+    with pytest.raises(NotImplementedError):
+        kx.exchange_energy(dev(workloads.random_field(plan.N, 2, 4).T), plan)
+
+
+def test_multipole_full_size_row(kx):
+    """The 96^3 / 64-orbital benchmark system with boundary values to order 4,
+    in the launch configuration of the benchmark: one orbital's row of pair
+    solves against the oracle, and E_x through 1/2 sum_i dV <psi_i, (Vx psi)_i>."""
+    sysd = workloads.C2
+    psi = workloads.make_orbitals(sysd)
+    op = oracle.Plan(sysd.n, sysd.h, sysd.bc, sysd.kernel, sysd.omega)
+    plan = kx.Plan.for_system(sysd, precision=1)
+    plan.set_multipole(4)
+    vx, ex = kx.kx_vx_apply(plan, dev(psi.T))
+    torch.cuda.synchronize()
+    assert plan.status() == kx.KX_OK
+    vx_h = vx.cpu().numpy()
+    assert abs(ex.item() - 0.5 * sysd.dV * np.einsum("ij,ij->", psi.T, vx_h)) < 1e-6 * abs(ex.item())
+    i = 5
+    pairs = [(i, j) for j in range(psi.shape[1])]
+    ref, _ = oracle.vx_apply(op, psi, ordered=True, pairs=pairs, l_max=4)
+    assert np.max(np.abs(vx_h[i] - ref[:, i])) < 1e-5 * np.abs(vx_h).max()
+
+
 def test_ace_f16x3_plan_matches_oracle(kx):
     """The tensor-core plan's ACE tail: float32 products, float64 block sums and
     float64 Cholesky; M to 1e-6 and xi to 1e-5 of their largest entries."""

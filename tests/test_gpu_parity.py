@@ -211,7 +211,7 @@ def test_ace_matches_oracle(kx):
 # --------------------------------------------------------------------------
 # Dirichlet values from the multipole expansion (isolated systems, Sec. 4)
 # --------------------------------------------------------------------------
-MP_GRID = ((16, 12, 20), (0.5, 0.55, 0.45), (D, D, D))
+MP_GRID = ((16, 24, 24), (0.5, 0.45, 0.4), (D, D, D))
 
 
 @pytest.mark.parametrize("prec,l_max", [(0, 0), (0, 2), (0, 4), (1, 2), (1, 4)])

@@ -372,6 +372,51 @@ def ace_legs(kx, torch, stream, plan, psi, vx, hbm, steps=5):
             "n_xi": n_orb, "n_vec": n_orb}
 
 
+FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x flops per FMA x max SM clock
+
+
+def multipole_legs(kx, torch, stream, plan, psi, ms_zero, steps=3):
+    """Vx psi of the headline system with Dirichlet values from the multipole
+    expansion (orders 2 and 4) instead of zero boundary values: time per apply,
+    the correction kernels' time, and their FP32 roofline (the weighted moments
+    of the pair densities and the k-weighted combination each take K n^2 N
+    multiply-adds on the CUDA cores, K = (l_max + 1)^2)."""
+    res = {}
+    n_orb, N = psi.shape
+    vx = torch.empty_like(psi)
+    ex = torch.empty(1, dtype=torch.float64, device="cuda")
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for l_max in (2, 4):
+        t0 = time.perf_counter()
+        plan.set_multipole(l_max)
+        setup_s = time.perf_counter() - t0
+        kx.kx_vx_apply(plan, psi, out=vx, e_x=ex, stream=stream)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            kx.kx_vx_apply(plan, psi, out=vx, e_x=ex, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        plan.profile(True)
+        kx.kx_vx_apply(plan, psi, out=vx, e_x=ex, stream=stream)
+        prof = plan.profile_read()
+        plan.profile(False)
+        mp_ms = prof["multipole"][0]
+        K = (l_max + 1) ** 2
+        flops = 4.0 * K * n_orb * n_orb * N
+        ach = flops / (mp_ms / 1e3) / 1e12
+        res[f"l_max_{l_max}"] = {
+            "ms_per_apply": ms, "overhead_ms": ms - ms_zero, "correction_ms": mp_ms, "setup_s": setup_s,
+            "e_x": ex.item(), "status": plan.status(),
+            "correction_roofline": {"bound": "alu", "achieved": ach, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                    "frac": ach / FP32_ALU_PEAK_TFLOPS,
+                                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"}}
+    plan.set_multipole(-1)
+    return res
+
+
 def issued_tensor_flops_per_pair(n, fused=True):
     """Tensor-core flops the split path issues per pair: three fp16 products per
     mode product, M padded to 128-row tiles, K and N padded to multiples of 16."""
@@ -524,6 +569,8 @@ def main():
         out["e2e"] = {"value": P * k_e2e / dt, "unit": UNIT, "h2d_bytes_per_step": psi_pin.numel() * 8,
                       "d2h_bytes_per_step": vx_pin.numel() * 8 + 8, "ms_per_step": 1e3 * dt / k_e2e}
         out["ace"] = ace_legs(kx, torch, stream, plan, psi, vx_split, hbm)
+        out["multipole"] = multipole_legs(kx, torch, stream, plan, psi, ms_step)
+        out["multipole"]["e_x_zero_boundary"] = ex_split
         out["other_workloads"] = other_workloads(kx, torch, stream)
         line, done, vx_ref, ex_ref = cpu_baseline(psi_h)
         out["cpu_baseline"] = line

@@ -284,7 +284,9 @@ int kx_profile(kx_plan *plan, int enable);
  * g psi phi into Vx psi, 12 fused mode 2 forward + X1 + mode 2 inverse per
  * k3 slice (replaces kinds 2-4 where the operands fit in shared memory),
  * 13 ACE combinations of grid vectors (xi = W R^{-1}, -xi P); kind 9 covers
- * the ACE projections over the grid and their reduction.
+ * the ACE projections over the grid and their reduction; 14 the multipole
+ * boundary correction (moments of the sources, correction of the solution,
+ * Vx psi and E_x).
  * Synchronises on the recorded events. */
 int kx_profile_read(kx_plan *plan, int n_kinds, double *ms, long long *launches);
 

@@ -190,7 +190,7 @@ class Plan:
         return f
 
     PROFILE_KINDS = ["prep", "X3F", "X2F", "X1", "X2I", "X3I", "final", "fp64_mode", "fp64_other", "ace",
-                     "setup", "acc", "slab", "ace_comb"]
+                     "setup", "acc", "slab", "ace_comb", "multipole"]
 
     def profile(self, enable=True):
         _check(lib().kx_profile(self.handle, 1 if enable else 0))

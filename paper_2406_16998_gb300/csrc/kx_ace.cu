@@ -463,9 +463,9 @@ __global__ void __launch_bounds__(256, 2) combine32_kernel(const double *__restr
 // part (n_split x na x nb) of A^T B over the grid, float64 or float32 products
 // by plan precision; returns n_split.
 int launch_projection(kx_plan *p, const double *A, int na, const double *B, int nb, const double *w64,
-                      const float *w32, double *part, int n_split, cudaStream_t s) {
+                      const float *w32, double *part, int n_split, cudaStream_t s, int kind = PK_ACE) {
     const long long N = (long long)p->N;
-    if (int rc = prof_begin(p, PK_ACE, s)) return rc;
+    if (int rc = prof_begin(p, kind, s)) return rc;
     if (p->precision == KX_FP64) {
         const long long span = (N + n_split - 1) / n_split;
         gram_kernel<<<dim3((na + kG - 1) / kG, (nb + kG - 1) / kG, n_split), 256, 0, s>>>(A, na, B, nb, w64, N, span,
@@ -505,9 +505,9 @@ int projection_split(const kx_plan *p, int na, int nb) {
 
 // out = sgn A C (grid vectors), float64 or float32 products by plan precision.
 int launch_combination(kx_plan *p, const double *A, int na, const double *C, int nb, double sgn, bool accumulate,
-                       double *out, cudaStream_t s) {
+                       double *out, cudaStream_t s, int kind = PK_ACE_COMB) {
     const long long N = (long long)p->N;
-    if (int rc = prof_begin(p, PK_ACE_COMB, s)) return rc;
+    if (int rc = prof_begin(p, kind, s)) return rc;
     if (p->precision == KX_FP64) {
         xi_kernel<<<dim3((unsigned)((N + 127) / 128), (unsigned)((nb + 31) / 32)), 256, 0, s>>>(A, C, na, nb, N, sgn,
                                                                                               accumulate, out);
@@ -589,14 +589,14 @@ size_t grid_projection_bytes(const kx_plan *p, int na, int nb) {
 }
 
 int grid_projection(kx_plan *p, const double *A, int na, const double *B, int nb, const double *w64, const float *w32,
-                    double scale, double *out, cudaStream_t s) {
+                    double scale, double *out, cudaStream_t s, int kind) {
     const int n_split = projection_split(p, na, nb);
     const size_t ne = (size_t)na * nb;
     int rc = ensure_workspace(p, grid_projection_bytes(p, na, nb));
     if (rc) return rc;
     double *part = (double *)p->ws.ptr;
-    if ((rc = launch_projection(p, A, na, B, nb, w64, w32, part, n_split, s))) return rc;
-    if ((rc = prof_begin(p, PK_ACE, s))) return rc;
+    if ((rc = launch_projection(p, A, na, B, nb, w64, w32, part, n_split, s, kind))) return rc;
+    if ((rc = prof_begin(p, kind, s))) return rc;
     gram_reduce_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(part, n_split, (int)ne, scale, out, nullptr,
                                                                     nullptr);
     KX_LAUNCH_CHECK("gram_reduce_kernel launch");
@@ -604,8 +604,8 @@ int grid_projection(kx_plan *p, const double *A, int na, const double *B, int nb
 }
 
 int grid_combination(kx_plan *p, const double *A, int na, const double *C, int nb, double sgn, bool accumulate,
-                     double *out, cudaStream_t s) {
-    return launch_combination(p, A, na, C, nb, sgn, accumulate, out, s);
+                     double *out, cudaStream_t s, int kind) {
+    return launch_combination(p, A, na, C, nb, sgn, accumulate, out, s, kind);
 }
 
 }  // namespace kx

@@ -54,7 +54,7 @@ struct TuneParams {
 
 // Per-launch CUDA-event timing by kernel kind (kx_profile / kx_profile_read).
 enum ProfKind { PK_PREP = 0, PK_X3F, PK_X2F, PK_X1, PK_X2I, PK_X3I, PK_FINAL, PK_FP64_MODE, PK_FP64_OTHER,
-                PK_ACE, PK_SETUP, PK_ACC, PK_SLAB, PK_ACE_COMB, PK_COUNT };
+                PK_ACE, PK_SETUP, PK_ACC, PK_SLAB, PK_ACE_COMB, PK_MP, PK_COUNT };
 struct Profiler {
     bool on = false;
     std::vector<cudaEvent_t> pool;       // reusable events
@@ -190,10 +190,10 @@ int mp_correct_apply(kx_plan *p, int n_rhs, const double *b, double *x, cudaStre
 // workspace (grid_projection_bytes).
 size_t grid_projection_bytes(const kx_plan *p, int na, int nb);
 int grid_projection(kx_plan *p, const double *A, int na, const double *B, int nb, const double *w64, const float *w32,
-                    double scale, double *out, cudaStream_t s);
+                    double scale, double *out, cudaStream_t s, int kind = PK_ACE);
 // out = (accumulate ? out : 0) + sgn A C for na grid vectors A and the na x nb
 // row-major float64 matrix C; no workspace.
 int grid_combination(kx_plan *p, const double *A, int na, const double *C, int nb, double sgn, bool accumulate,
-                     double *out, cudaStream_t s);
+                     double *out, cudaStream_t s, int kind = PK_ACE_COMB);
 
 }  // namespace kx

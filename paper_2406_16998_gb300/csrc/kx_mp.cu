@@ -409,20 +409,24 @@ int mp_correct_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, d
     // moments Q_k(ij) = dV sum_x R_k psi_i psi_j
     for (int k = 0; k < K; ++k)
         if ((rc = grid_projection(p, psi, n, psi, n, f64 ? p->d_mpR + (size_t)k * N : nullptr,
-                                  f64 ? nullptr : p->d_mpR32 + (size_t)k * N, p->dV, Q + (size_t)k * nn, s)))
+                                  f64 ? nullptr : p->d_mpR32 + (size_t)k * N, p->dV, Q + (size_t)k * nn, s, PK_MP)))
             return rc;
     if (energy_only) {
         for (int k = 0; k < K; ++k)
             if ((rc = grid_projection(p, psi, n, psi, n, f64 ? p->d_mpH + (size_t)k * N : nullptr,
-                                      f64 ? nullptr : p->d_mpH32 + (size_t)k * N, p->dV, P + (size_t)k * nn, s)))
+                                      f64 ? nullptr : p->d_mpH32 + (size_t)k * N, p->dV, P + (size_t)k * nn, s,
+                                      PK_MP)))
                 return rc;
         if (ex) {
+            if ((rc = prof_begin(p, PK_MP, s))) return rc;
             mp_energy_qp_kernel<<<1, 256, 0, s>>>(Q, P, mask, occ, n, K, ex);
             KX_LAUNCH_CHECK("mp_energy_qp_kernel launch");
+            if ((rc = prof_end(p, s))) return rc;
         }
         return KX_OK;
     }
     const unsigned cb = (unsigned)((nn * K + 255) / 256);
+    if ((rc = prof_begin(p, PK_MP, s))) return rc;
     if (f64) {
         double *C = P;
         mp_coef_kernel<double><<<cb, 256, 0, s>>>(Q, mask, occ, n, K, C);
@@ -434,7 +438,7 @@ int mp_correct_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, d
             mp_energy_add_kernel<<<1, 1, 0, s>>>(part, (long long)grid.x * grid.y, -0.5 * p->dV, ex);
             KX_LAUNCH_CHECK("mp_energy_add_kernel launch");
         }
-        return KX_OK;
+        return prof_end(p, s);
     }
     float *C = reinterpret_cast<float *>(P);
     mp_coef_kernel<float><<<cb, 256, 0, s>>>(Q, mask, occ, n, K, C);
@@ -448,7 +452,7 @@ int mp_correct_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, d
         mp_energy_add_kernel<<<1, 1, 0, s>>>(part, (long long)grid.x * grid.y, -0.5 * p->dV, ex);
         KX_LAUNCH_CHECK("mp_energy_add_kernel launch");
     }
-    return KX_OK;
+    return prof_end(p, s);
 }
 
 int mp_correct_apply(kx_plan *p, int n_rhs, const double *b, double *x, cudaStream_t s) {
@@ -462,9 +466,9 @@ int mp_correct_apply(kx_plan *p, int n_rhs, const double *b, double *x, cudaStre
         p->mp_scratch.bytes = need;
     }
     double *Cb = (double *)p->mp_scratch.ptr;  // [K][n_rhs]: dV sum_x R_k b_r
-    int rc = grid_projection(p, p->d_mpR, K, b, n_rhs, nullptr, nullptr, p->dV, Cb, s);
+    int rc = grid_projection(p, p->d_mpR, K, b, n_rhs, nullptr, nullptr, p->dV, Cb, s, PK_MP);
     if (rc) return rc;
-    return grid_combination(p, p->d_mpH, K, Cb, n_rhs, 1.0, true, x, s);
+    return grid_combination(p, p->d_mpH, K, Cb, n_rhs, 1.0, true, x, s, PK_MP);
 }
 
 }  // namespace kx

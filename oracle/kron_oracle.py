@@ -31,6 +31,8 @@ test in tests/test_oracle_pins.py):
       real orbitals at the Gamma point, so conjugates drop (Sec. 2, Eq. 5 setting).
   R9  Pair enumeration: the symmetric (i <= j) and ordered schedules give the
       same VxPsi and E_x.
+  R10-R12 (multipole boundary values for isolated systems): see the section
+      above apply_fL_multipole.
 """
 from __future__ import annotations
 

@@ -136,6 +136,7 @@ struct kx_plan_s {
     int mp_K = 0;
     double *d_mpR = nullptr, *d_mpH = nullptr;
     float *d_mpR32 = nullptr, *d_mpH32 = nullptr;
+    float *d_mpMax = nullptr;  // max |R_k| (K values) then max |h_k| (K values)
     kx::Workspace mp_scratch;
 };
 

@@ -18,6 +18,10 @@
 // sum_k R_k(v') I_k(v) = sum_l |v'|^l / |v|^(l+1) P_l(cos gamma), the Legendre
 // expansion of 1 / |v - v'|.
 #include "kx_internal.h"
+#include "kx_tc_ptx.cuh"
+#include "kx_conv.cuh"
+
+#include <cuda_fp16.h>
 
 #include <algorithm>
 #include <cmath>
@@ -142,7 +146,8 @@ constexpr int kMcX = 128;  // correction tile: 128 grid points x 64 orbitals
 // vx_i(x) -= T_i(x), T_i(x) = sum_k h_k(x) sum_j C[k][j][i] psi_j(x), float32
 // products (psi converted once per tile into shared memory, C[k] staged per k);
 // e_part[CTA] = sum over the tile of g_i psi_i(x) T_i(x).  Thread (tx, ty) owns
-// x = x0 + tx + 32 q (q < 4) and i = i0 + 8 ty + u (u < 8).
+// x = x0 + tx + 32 q (q < 4) and i = i0 + 8 ty + u (u < 8); the orbitals are
+// taken in pairs (u, u + 1) by packed f32x2 FMAs.
 __global__ void __launch_bounds__(256) mp_combine32_kernel(const double *__restrict__ psi, int n,
                                                            const float *__restrict__ C, const float *__restrict__ H,
                                                            int K, const double *__restrict__ occ, long long N,
@@ -159,11 +164,11 @@ __global__ void __launch_bounds__(256) mp_combine32_kernel(const double *__restr
         const long long x = x0 + c;
         Ps[e] = x < N ? (float)psi[(long long)j * N + x] : 0.f;
     }
-    float acc[8][4];
+    float2 acc[4][4];  // acc[up][q]: orbitals 2 up (.x) and 2 up + 1 (.y) at point q
 #pragma unroll
-    for (int u = 0; u < 8; ++u)
+    for (int up = 0; up < 4; ++up)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[u][q] = 0.f;
+        for (int q = 0; q < 4; ++q) acc[up][q] = make_float2(0.f, 0.f);
     for (int k = 0; k < K; ++k) {
         __syncthreads();
         const float *Ck = C + (size_t)k * n * n;
@@ -172,29 +177,35 @@ __global__ void __launch_bounds__(256) mp_combine32_kernel(const double *__restr
             Cs[e] = i0 + c < n ? Ck[(size_t)j * n + i0 + c] : 0.f;
         }
         __syncthreads();
-        float t[8][4];
+        float2 t[4][4];
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
+        for (int up = 0; up < 4; ++up)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) t[u][q] = 0.f;
+            for (int q = 0; q < 4; ++q) t[up][q] = make_float2(0.f, 0.f);
+#pragma unroll 2
         for (int j = 0; j < n; ++j) {
-            float pv[4];
+            float2 pv[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) pv[q] = Ps[j * kMcX + tx + 32 * q];
+            for (int q = 0; q < 4; ++q) {
+                const float v = Ps[j * kMcX + tx + 32 * q];
+                pv[q] = make_float2(v, v);
+            }
             const float4 c0 = *reinterpret_cast<const float4 *>(&Cs[j * 64 + 8 * ty]);
             const float4 c1 = *reinterpret_cast<const float4 *>(&Cs[j * 64 + 8 * ty + 4]);
-            const float cv[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+            const float2 cv[4] = {make_float2(c0.x, c0.y), make_float2(c0.z, c0.w), make_float2(c1.x, c1.y),
+                                  make_float2(c1.z, c1.w)};
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
+            for (int up = 0; up < 4; ++up)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) t[u][q] = fmaf(cv[u], pv[q], t[u][q]);
+                for (int q = 0; q < 4; ++q) fma2(t[up][q], cv[up], pv[q]);
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const long long x = x0 + tx + 32 * q;
             const float hk = x < N ? __ldg(H + (size_t)k * N + x) : 0.f;
+            const float2 h2 = make_float2(hk, hk);
 #pragma unroll
-            for (int u = 0; u < 8; ++u) acc[u][q] = fmaf(hk, t[u][q], acc[u][q]);
+            for (int up = 0; up < 4; ++up) fma2(acc[up][q], h2, t[up][q]);
         }
     }
     double e = 0.0;
@@ -208,8 +219,9 @@ __global__ void __launch_bounds__(256) mp_combine32_kernel(const double *__restr
         for (int q = 0; q < 4; ++q) {
             const long long x = x0 + tx + 32 * q;
             if (x >= N) continue;
-            vx[(long long)i * N + x] -= (double)acc[u][q];
-            ei = fmaf(Ps[i * kMcX + tx + 32 * q], acc[u][q], ei);
+            const float a = (u & 1) ? acc[u >> 1][q].y : acc[u >> 1][q].x;
+            vx[(long long)i * N + x] -= (double)a;
+            ei = fmaf(Ps[i * kMcX + tx + 32 * q], a, ei);
         }
         e += gi * (double)ei;
     }
@@ -249,6 +261,208 @@ __global__ void mp_combine64_kernel(const double *__restrict__ psi, int n, const
         __syncthreads();
     }
     if (threadIdx.x == 0) e_part[(long long)blockIdx.y * gridDim.x + blockIdx.x] = red[0];
+}
+
+// ---------------------------------------------------------------------------
+// Moments on the tensor cores (at most 64 orbitals): for the harmonic pairs
+// (2p, 2p+1) of this CTA, D_p[(t, i)][j] = sum_x (psi_i R_{2p+t})(x) psi_j(x)
+// over the CTA's grid points, as 128 x 64 tcgen05 products with K = grid
+// points: A rows are (harmonic t, orbital i), B rows orbitals j, both K-major
+// fp16 hi/lo splits of power-of-two-scaled values (|psi s_psi| < 1,
+// |R_k s_k| < 2^14), three products per k-step (cross terms first, the hi*hi
+// chain split over two accumulators as in the mode products).  One step = 64
+// grid points: every thread stages two (orbital, 8-point) tasks of B and the
+// matching rows of all A tiles, then one thread issues the step's products.
+// ---------------------------------------------------------------------------
+constexpr int kMtX = 64;                  // grid points per step
+constexpr int kMtPairs = 4;               // harmonic pairs per CTA (two fp32 accumulators of 64 columns each)
+constexpr uint32_t kMtGroup = 1024;       // bytes per 8-row group: 8 core matrices of 8 points along K
+constexpr size_t kMtB = 64 * kMtX * 2;    // hi (or lo) of B: 64 orbitals x 64 points fp16
+constexpr size_t kMtA = 128 * kMtX * 2;   // hi (or lo) of one A pair tile
+constexpr size_t kMtSmem = 2 * kMtB + (size_t)kMtPairs * 2 * kMtA + 1024;
+
+__device__ __forceinline__ void mt_split_store(uint8_t *hi, uint8_t *lo, int off, const float *w) {
+    __half2 h[4], l[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const __half2 hh = __floats2half2_rn(w[2 * c], w[2 * c + 1]);
+        const float2 hf = __half22float2(hh);
+        h[c] = hh;
+        l[c] = __floats2half2_rn(w[2 * c] - hf.x, w[2 * c + 1] - hf.y);
+    }
+    *reinterpret_cast<uint4 *>(hi + off) = *reinterpret_cast<uint4 *>(h);
+    *reinterpret_cast<uint4 *>(lo + off) = *reinterpret_cast<uint4 *>(l);
+}
+
+// Three-product split MMA of one step into (Da, Db); accumulate = 0 starts them.
+__device__ __forceinline__ void mt_issue(uint32_t da, uint32_t db, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi,
+                                         uint32_t b_lo, bool accumulate) {
+    const uint32_t idesc = ptx::idesc_f16(128, 64, 0, 0);  // A and B K-major
+    const uint64_t ah0 = ptx::sdesc(a_hi, 128, kMtGroup), al0 = ptx::sdesc(a_lo, 128, kMtGroup);
+    const uint64_t bh0 = ptx::sdesc(b_hi, 128, kMtGroup), bl0 = ptx::sdesc(b_lo, 128, kMtGroup);
+    const uint64_t inc = 256 >> 4;  // one k-step = 16 points = two core matrices
+    uint64_t ah = ah0, al = al0, bh = bh0, bl = bl0;
+    for (int ks = 0; ks < kMtX / 16; ++ks) {
+        ptx::mma_f16(da, ah, bl, idesc, (ks > 0 || accumulate) ? 1u : 0u);
+        ptx::mma_f16(da, al, bh, idesc, 1u);
+        ah += inc;
+        al += inc;
+        bh += inc;
+        bl += inc;
+    }
+    ah = ah0;
+    bh = bh0;
+    for (int ks = 0; ks < kMtX / 16; ++ks) {
+        if (ks & 1)
+            ptx::mma_f16(db, ah, bh, idesc, (ks > 1 || accumulate) ? 1u : 0u);
+        else
+            ptx::mma_f16(da, ah, bh, idesc, 1u);
+        ah += inc;
+        bh += inc;
+    }
+}
+
+__global__ void __launch_bounds__(256, 1) mp_moments_tc_kernel(const double *__restrict__ psi, int n,
+                                                               const float *__restrict__ R32, int K,
+                                                               const float *__restrict__ Rmax,
+                                                               const float *__restrict__ psimax, long long N,
+                                                               long long span, double *__restrict__ part,
+                                                               int *status, long long timeout_cycles) {
+    extern __shared__ uint8_t mt_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(mt_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *Bhi = smem, *Blo = smem + kMtB;
+    uint8_t *A0 = smem + 2 * kMtB;  // pair p: hi at A0 + 2p kMtA, lo after it
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tslot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int kp0 = blockIdx.y * kMtPairs;
+    const int npair = min(kMtPairs, (K + 1) / 2 - kp0);
+    if (warp == 0) {
+        ptx::tmem_alloc(&tslot, 512);
+        ptx::tmem_relinquish();
+    }
+    if (tid == 0) {
+        ptx::mbar_init(&bar, 1);
+        ptx::fence_mbar_init();
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem = tslot;
+    int e = 0;
+    frexpf(*psimax, &e);
+    const float sp = ldexpf(1.f, -e);  // |psi sp| < 1
+    float sk[2 * kMtPairs];
+#pragma unroll
+    for (int q = 0; q < 2 * kMtPairs; ++q) {
+        const int k = 2 * kp0 + q;
+        int ek = 0;
+        if (k < K) frexpf(Rmax[k], &ek);
+        sk[q] = (k < K && q < 2 * npair) ? ldexpf(1.f, 14 - ek) : 0.f;  // |R_k sk| < 2^14
+    }
+    const long long x0 = (long long)blockIdx.x * span;
+    const long long x1 = min(N, x0 + span);
+    const int nsteps = x1 > x0 ? (int)((x1 - x0 + kMtX - 1) / kMtX) : 0;
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int s = 0; s < nsteps && ok; ++s) {
+        if (s > 0) {
+            // the previous step's products have read the tiles
+            ok = __syncthreads_and(ptx::mbar_wait_bounded(&bar, phase, timeout_cycles));
+            phase ^= 1u;
+            if (!ok) break;
+            ptx::tc_fence_after();
+        }
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int i = tid & 63, g = (tid >> 6) + 4 * r;  // orbital, group of 8 points
+            const long long xb = x0 + (long long)s * kMtX + 8 * g;
+            float v[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const long long x = xb + c;
+                v[c] = (i < n && x < x1) ? f64_to_f32(__ldg(psi + (long long)i * N + x)) * sp : 0.f;
+            }
+            mt_split_store(Bhi, Blo, (i >> 3) * kMtGroup + g * 128 + (i & 7) * 16, v);
+            for (int q = 0; q < 2 * npair; ++q) {
+                const int k = 2 * kp0 + q;
+                float w[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const long long x = xb + c;
+                    w[c] = (k < K && x < x1) ? v[c] * (__ldg(R32 + (long long)k * N + x) * sk[q]) : 0.f;
+                }
+                const int row = (q & 1) * 64 + i;
+                uint8_t *Ahi = A0 + (size_t)(q >> 1) * 2 * kMtA;
+                mt_split_store(Ahi, Ahi + kMtA, (row >> 3) * kMtGroup + g * 128 + (row & 7) * 16, w);
+            }
+        }
+        ptx::fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            ptx::tc_fence_after();
+            for (int p = 0; p < npair; ++p) {
+                const uint32_t sA = ptx::smem_u32(A0 + (size_t)p * 2 * kMtA);
+                mt_issue(tmem + 128 * p, tmem + 128 * p + 64, sA, sA + (uint32_t)kMtA, ptx::smem_u32(Bhi),
+                         ptx::smem_u32(Blo), s > 0);
+            }
+            ptx::mma_commit(&bar);
+        }
+    }
+    if (nsteps > 0 && ok) ok = __syncthreads_and(ptx::mbar_wait_bounded(&bar, phase, timeout_cycles));
+    if (!ok && tid == 0) atomicExch(status, KX_ERR_TIMEOUT);
+    ptx::tc_fence_after();
+    if (warp < 4) {
+        // lane r of TMEM = A row r = (harmonic 2p + r / 64, orbital r % 64)
+        const int row = warp * 32 + lane, t = row >> 6, i = row & 63;
+        const uint32_t tl = tmem + ((uint32_t)(32 * warp) << 16);
+        const long long nn = (long long)n * n;
+        for (int p = 0; p < npair; ++p) {
+            const int k = 2 * (kp0 + p) + t;
+            const float un = (k < K && sk[2 * p + t] > 0.f) ? 1.f / (sp * sp * sk[2 * p + t]) : 0.f;
+            for (int c0 = 0; c0 < 64; c0 += 16) {
+                float va[16], vb[16];
+                ptx::tmem_ld16x2(tl + 128 * p + c0, tl + 128 * p + 64 + c0, va, vb);
+                if (k >= K || i >= n) continue;
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    const int j = c0 + c;
+                    if (j < n)
+                        part[((long long)blockIdx.x * K + k) * nn + (long long)i * n + j] =
+                            (nsteps > 0 && ok) ? (double)(va[c] + vb[c]) * (double)un : 0.0;
+                }
+            }
+        }
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        ptx::tc_fence_after();
+        ptx::tmem_dealloc(tmem, 512);
+    }
+}
+
+// Q[e] = scale sum_c part[c][e] in a fixed order.
+__global__ void mp_reduce_kernel(const double *__restrict__ part, int n_part, long long n_e, double scale,
+                                 double *__restrict__ Q) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_e) return;
+    double s = 0.0;
+    for (int c = 0; c < n_part; ++c) s += part[(long long)c * n_e + e];
+    Q[e] = scale * s;
+}
+
+__device__ __forceinline__ float as_f32(float v) { return v; }
+__device__ __forceinline__ float as_f32(double v) { return f64_to_f32(v); }
+
+// max |a| over n values into *out (float bits, non-negative: integer max is exact and order-free)
+template <typename T>
+__global__ void absmax_kernel(const T *__restrict__ a, long long n, float *__restrict__ out) {
+    float m = 0.f;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(as_f32(a[i])));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int *>(out), __float_as_int(m));
 }
 
 // ex += scale * sum of the partials, in index order (one thread: deterministic).
@@ -298,11 +512,51 @@ std::vector<double> centred_weights(int order) {
     return w;
 }
 
-size_t mp_scratch_bytes(int n, int K, long long N) {
+// Tensor-core moments: one grid-point range per SM, each range split over the
+// harmonic pairs in groups of kMtPairs.
+int moments_tc_split(const kx_plan *p) { return p->num_sms; }
+
+size_t mp_scratch_bytes(const kx_plan *p, int n, int K) {
+    const long long N = (long long)p->N;
     const size_t kn2 = (size_t)K * n * n;
     const size_t tiles = (size_t)((N + kMcX - 1) / kMcX) * ((n + 63) / 64);
     const size_t part64 = (size_t)((N + 255) / 256) * n;
-    return sizeof(double) * (2 * kn2 + kn2 + std::max(tiles, part64)) + 1024;
+    const size_t part_tc = n <= 64 ? (size_t)moments_tc_split(p) * kn2 : 0;
+    return sizeof(double) * (2 * kn2 + kn2 + std::max(std::max(tiles, part64), part_tc)) + 1024;
+}
+
+// Q[k] = dV sum_x W_k psi_i psi_j for k < K (weights W: K x N).  Tensor cores for
+// up to 64 orbitals on tensor-core plans (W32 and its per-field maxima), else one
+// weighted projection per k.
+int weighted_moments(kx_plan *p, int n, const double *psi, const double *W64, const float *W32, const float *Wmax,
+                     double *Q, double *part, float *psimax, cudaStream_t s) {
+    const int K = p->mp_K;
+    const long long N = (long long)p->N;
+    const size_t nn = (size_t)n * n;
+    if (p->precision != KX_FP64 && n <= 64) {
+        if (int rc = prof_begin(p, PK_MP, s)) return rc;
+        KX_CUDA_TRY(cudaMemsetAsync(psimax, 0, sizeof(float), s));
+        absmax_kernel<double><<<4 * p->num_sms, 256, 0, s>>>(psi, (long long)n * N, psimax);
+        KX_LAUNCH_CHECK("absmax_kernel launch");
+        const int n_split = moments_tc_split(p);
+        const long long span = ((N + n_split - 1) / n_split + kMtX - 1) / kMtX * kMtX;
+        const dim3 grid(n_split, ((K + 1) / 2 + kMtPairs - 1) / kMtPairs);
+        KX_CUDA_TRY(cudaFuncSetAttribute(mp_moments_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kMtSmem));
+        mp_moments_tc_kernel<<<grid, 256, kMtSmem, s>>>(psi, n, W32, K, Wmax, psimax, N, span, part, p->d_status,
+                                                         4000000000LL);
+        KX_LAUNCH_CHECK("mp_moments_tc_kernel launch");
+        const long long ne = (long long)K * nn;
+        mp_reduce_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(part, n_split, ne, p->dV, Q);
+        KX_LAUNCH_CHECK("mp_reduce_kernel launch");
+        return prof_end(p, s);
+    }
+    const bool f64 = p->precision == KX_FP64;
+    for (int k = 0; k < K; ++k)
+        if (int rc = grid_projection(p, psi, n, psi, n, f64 ? W64 + (size_t)k * N : nullptr,
+                                     f64 ? nullptr : W32 + (size_t)k * N, p->dV, Q + (size_t)k * nn, s, PK_MP))
+            return rc;
+    return KX_OK;
 }
 
 }  // namespace
@@ -312,6 +566,8 @@ void mp_free(kx_plan *p) {
     cudaFree(p->d_mpH);
     cudaFree(p->d_mpR32);
     cudaFree(p->d_mpH32);
+    cudaFree(p->d_mpMax);
+    p->d_mpMax = nullptr;
     cudaFree(p->mp_scratch.ptr);
     p->d_mpR = p->d_mpH = nullptr;
     p->d_mpR32 = p->d_mpH32 = nullptr;
@@ -352,6 +608,7 @@ int mp_set(kx_plan *p, int l_max) {
     if (e == cudaSuccess) e = cudaMalloc(&p->d_mpH, fld);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_mpR32, fld / 2);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_mpH32, fld / 2);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_mpMax, sizeof(float) * 2 * K);
     if (e == cudaSuccess) e = cudaMalloc(&Gk, fld);
     if (e != cudaSuccess) {
         cudaFree(Gk);
@@ -366,6 +623,12 @@ int mp_set(kx_plan *p, int l_max) {
     if (!rc) {
         to_f32_kernel<<<1024, 256>>>(p->d_mpR, p->d_mpR32, (long long)K * N);
         to_f32_kernel<<<1024, 256>>>(p->d_mpH, p->d_mpH32, (long long)K * N);
+        // per-field maxima (R_k then h_k) for the tensor-core moments' scales
+        cudaMemset(p->d_mpMax, 0, sizeof(float) * 2 * K);
+        for (int k = 0; k < K; ++k) {
+            absmax_kernel<float><<<256, 256>>>(p->d_mpR32 + (size_t)k * N, N, p->d_mpMax + k);
+            absmax_kernel<float><<<256, 256>>>(p->d_mpH32 + (size_t)k * N, N, p->d_mpMax + K + k);
+        }
         e = cudaDeviceSynchronize();
         if (e != cudaSuccess) rc = cuda_error(e, "kx_plan_set_multipole set-up");
     }
@@ -381,7 +644,7 @@ int mp_set(kx_plan *p, int l_max) {
 
 int mp_reserve(kx_plan *p, int n_orb) {
     if (p->mp_lmax < 0) return KX_OK;
-    const size_t need = mp_scratch_bytes(n_orb, p->mp_K, (long long)p->N);
+    const size_t need = mp_scratch_bytes(p, n_orb, p->mp_K);
     if (p->mp_scratch.bytes < need) {
         cudaFree(p->mp_scratch.ptr);
         p->mp_scratch = Workspace{};
@@ -405,18 +668,12 @@ int mp_correct_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, d
     double *Q = (double *)p->mp_scratch.ptr;
     double *P = Q + (size_t)K * nn;  // energy-only: projections on h_k; otherwise C
     double *part = P + (size_t)K * nn + (size_t)K * nn;
+    float *psimax = reinterpret_cast<float *>(P + (size_t)K * nn);  // the unused third block
     const unsigned char *mask = p->d_pair_mask;
     // moments Q_k(ij) = dV sum_x R_k psi_i psi_j
-    for (int k = 0; k < K; ++k)
-        if ((rc = grid_projection(p, psi, n, psi, n, f64 ? p->d_mpR + (size_t)k * N : nullptr,
-                                  f64 ? nullptr : p->d_mpR32 + (size_t)k * N, p->dV, Q + (size_t)k * nn, s, PK_MP)))
-            return rc;
+    if ((rc = weighted_moments(p, n, psi, p->d_mpR, p->d_mpR32, p->d_mpMax, Q, part, psimax, s))) return rc;
     if (energy_only) {
-        for (int k = 0; k < K; ++k)
-            if ((rc = grid_projection(p, psi, n, psi, n, f64 ? p->d_mpH + (size_t)k * N : nullptr,
-                                      f64 ? nullptr : p->d_mpH32 + (size_t)k * N, p->dV, P + (size_t)k * nn, s,
-                                      PK_MP)))
-                return rc;
+        if ((rc = weighted_moments(p, n, psi, p->d_mpH, p->d_mpH32, p->d_mpMax + K, P, part, psimax, s))) return rc;
         if (ex) {
             if ((rc = prof_begin(p, PK_MP, s))) return rc;
             mp_energy_qp_kernel<<<1, 256, 0, s>>>(Q, P, mask, occ, n, K, ex);

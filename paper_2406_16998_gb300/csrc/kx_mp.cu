@@ -25,6 +25,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <vector>
 
 namespace kx {
@@ -373,25 +374,47 @@ __global__ void __launch_bounds__(256, 1) mp_moments_tc_kernel(const double *__r
             if (!ok) break;
             ptx::tc_fence_after();
         }
-#pragma unroll
+#pragma unroll 1
         for (int r = 0; r < 2; ++r) {
             const int i = tid & 63, g = (tid >> 6) + 4 * r;  // orbital, group of 8 points
             const long long xb = x0 + (long long)s * kMtX + 8 * g;
-            float v[8];
+            // all loads of the task first (16-byte pieces; N % 8 == 0 and aligned rows,
+            // checked by the launcher), then the products
+            float v[8], rw[2 * kMtPairs][8];
+            if (i < n && xb < x1) {
+                const double2 *src = reinterpret_cast<const double2 *>(psi + (long long)i * N + xb);
+                double2 d[4];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const long long x = xb + c;
-                v[c] = (i < n && x < x1) ? f64_to_f32(__ldg(psi + (long long)i * N + x)) * sp : 0.f;
+                for (int c = 0; c < 4; ++c) d[c] = __ldg(src + c);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    v[2 * c] = f64_to_f32(d[c].x) * sp;
+                    v[2 * c + 1] = f64_to_f32(d[c].y) * sp;
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) v[c] = 0.f;
+            }
+#pragma unroll
+            for (int q = 0; q < 2 * kMtPairs; ++q) {
+                const int k = 2 * kp0 + q;
+                if (q < 2 * npair && k < K && xb < x1) {
+                    const float4 *src = reinterpret_cast<const float4 *>(R32 + (long long)k * N + xb);
+                    const float4 a = __ldg(src), b = __ldg(src + 1);
+                    rw[q][0] = a.x; rw[q][1] = a.y; rw[q][2] = a.z; rw[q][3] = a.w;
+                    rw[q][4] = b.x; rw[q][5] = b.y; rw[q][6] = b.z; rw[q][7] = b.w;
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) rw[q][c] = 0.f;
+                }
             }
             mt_split_store(Bhi, Blo, (i >> 3) * kMtGroup + g * 128 + (i & 7) * 16, v);
-            for (int q = 0; q < 2 * npair; ++q) {
-                const int k = 2 * kp0 + q;
+#pragma unroll
+            for (int q = 0; q < 2 * kMtPairs; ++q) {
+                if (q >= 2 * npair) break;
                 float w[8];
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const long long x = xb + c;
-                    w[c] = (k < K && x < x1) ? v[c] * (__ldg(R32 + (long long)k * N + x) * sk[q]) : 0.f;
-                }
+                for (int c = 0; c < 8; ++c) w[c] = v[c] * (rw[q][c] * sk[q]);
                 const int row = (q & 1) * 64 + i;
                 uint8_t *Ahi = A0 + (size_t)(q >> 1) * 2 * kMtA;
                 mt_split_store(Ahi, Ahi + kMtA, (row >> 3) * kMtGroup + g * 128 + (row & 7) * 16, w);
@@ -533,7 +556,10 @@ int weighted_moments(kx_plan *p, int n, const double *psi, const double *W64, co
     const int K = p->mp_K;
     const long long N = (long long)p->N;
     const size_t nn = (size_t)n * n;
-    if (p->precision != KX_FP64 && n <= 64) {
+    // 16-byte loads of 8 grid points: N % 8 == 0 (so rows and steps stay aligned) and aligned bases
+    const bool tc = p->precision != KX_FP64 && n <= 64 && N % 8 == 0 &&
+                    ((reinterpret_cast<uintptr_t>(psi) | reinterpret_cast<uintptr_t>(W32)) & 15) == 0;
+    if (tc) {
         if (int rc = prof_begin(p, PK_MP, s)) return rc;
         KX_CUDA_TRY(cudaMemsetAsync(psimax, 0, sizeof(float), s));
         absmax_kernel<double><<<4 * p->num_sms, 256, 0, s>>>(psi, (long long)n * N, psimax);

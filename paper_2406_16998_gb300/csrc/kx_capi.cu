@@ -189,11 +189,14 @@ static int reserve(kx_plan *p, int n_orb) {
 
 static int dispatch_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, double *vx, double *ex,
                        bool energy_only, cudaStream_t s, long pair_begin = 0, long pair_end = -1) {
+    p->mp_applied = false;
     int rc = p->precision == KX_FP64 ? fp64_vx(p, n_orb, psi, occ, vx, ex, energy_only, s, pair_begin, pair_end)
                                      : tc_vx(p, n_orb, psi, occ, vx, ex, energy_only, s, pair_begin, pair_end);
     // boundary values from the multipole expansion: the rank-K correction of
-    // the same pair range (its mask was built by the solve's ensure_pairs)
-    if (!rc && p->mp_lmax >= 0) rc = mp_correct_vx(p, n_orb, psi, occ, vx, ex, energy_only, s);
+    // the same pair range (its mask was built by the solve's ensure_pairs),
+    // unless the split path already started its accumulator from it
+    if (!rc && p->mp_lmax >= 0 && !p->mp_applied) rc = mp_correct_vx(p, n_orb, psi, occ, vx, ex, energy_only, s);
+    p->mp_applied = false;
     return rc;
 }
 

@@ -137,6 +137,7 @@ struct kx_plan_s {
     double *d_mpR = nullptr, *d_mpH = nullptr;
     float *d_mpR32 = nullptr, *d_mpH32 = nullptr;
     float *d_mpMax = nullptr;  // max |R_k| (K values) then max |h_k| (K values)
+    bool mp_applied = false;   // the split path applied the correction inside its pair loop
     kx::Workspace mp_scratch;
 };
 
@@ -178,6 +179,12 @@ int ace_apply_run(kx_plan *p, int n_xi, const double *xi, int n_vec, const doubl
 int mp_set(kx_plan *p, int l_max);
 void mp_free(kx_plan *p);
 int mp_reserve(kx_plan *p, int n_orb);
+int mp_reserve_scratch(kx_plan *p, int n_orb);
+// tensor-core form of the Vx psi correction: written into the float32
+// accumulator of the split path before its pair loop (sets mp_applied)
+bool mp_tc_eligible(const kx_plan *p, int n_orb, const double *psi);
+int mp_correct_into_acc(kx_plan *p, int n_orb, const double *psi, const double *occ, float *acc, double *ex,
+                        cudaStream_t s);
 // Vx psi and E_x (or E_x alone) of the pair range of the last ensure_pairs:
 // adds the rank-K boundary correction to the homogeneous result
 int mp_correct_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, double *vx, double *ex,

@@ -465,6 +465,257 @@ __global__ void __launch_bounds__(256, 1) mp_moments_tc_kernel(const double *__r
     }
 }
 
+// ---------------------------------------------------------------------------
+// Correction on the tensor cores (at most 64 orbitals):
+//   T[x][i] = sum_k sum_j (h_k(x) psi_j(x)) C_k[j][i]
+// is one product with inner dimension K n: per 128-point tile, for each k the
+// A tile (h_k psi)[x][j] (MN-major: points contiguous) and the B tile
+// C_k[j][i] (MN-major: orbitals i contiguous) are fp16 hi/lo splits, and the
+// products accumulate into one TMEM pair.  Every term carries the same overall
+// scale: A_k is scaled by s_psi s_h,k and B_k by t_k with s_h,k t_k = S for
+// all k (t_k puts max |C_k| near 2^14, S is the largest common value that
+// keeps every |A_k| < 2^14), so T = D / (s_psi S).
+// ---------------------------------------------------------------------------
+constexpr int kCtM = 128;                 // grid points per tile
+constexpr size_t kCtA = 128 * 64 * 2;     // hi (or lo) of A_k: 128 points x 64 orbitals fp16
+constexpr size_t kCtB = 64 * 64 * 2;      // hi (or lo) of B_k
+constexpr size_t kCtStage = 2 * kCtA + 2 * kCtB;
+constexpr size_t kCtSmem = 2 * kCtStage + 1024;
+
+// scale exponents: e_psi from max|psi|, per k the exponents of max|h_k| and max|C_k|
+// out: sc[k] = s_psi s_h,k (the A scale), sc[K + k] = t_k, sc[2K] = 1 / (s_psi S)
+__global__ void mp_ct_scales_kernel(const float *__restrict__ hmax, const float *__restrict__ cmax,
+                                    const float *__restrict__ psimax, int K, float *__restrict__ sc) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    int ep = 0;
+    frexpf(*psimax, &ep);  // |psi 2^-ep| < 1
+    // t_k = 2^(14 - ec_k); A_k max = hmax_k 2^-ep S / t_k < 2^14  =>  S <= 2^(14 + 14 - ec_k - eh_k)
+    int eS = 1 << 20;
+    for (int k = 0; k < K; ++k) {
+        int eh = 0, ec = 0;
+        frexpf(hmax[k], &eh);
+        frexpf(cmax[k], &ec);
+        if (hmax[k] > 0.f && cmax[k] > 0.f) eS = min(eS, 28 - ec - eh);
+    }
+    if (eS == (1 << 20)) eS = 0;
+    for (int k = 0; k < K; ++k) {
+        int ec = 0;
+        frexpf(cmax[k], &ec);
+        const int et = cmax[k] > 0.f ? 14 - ec : 0;
+        sc[K + k] = ldexpf(1.f, et);
+        sc[k] = ldexpf(1.f, eS - et - ep);  // s_psi s_h,k
+    }
+    // every product term carries 2^(eS - ep): A = psi h_k sc[k], B = C_k t_k
+    sc[2 * K] = ldexpf(1.f, ep - eS);
+}
+
+// max over |C_k| per k (C float64 [K][n][n])
+__global__ void mp_cmax_kernel(const double *__restrict__ C, int n, int K, float *__restrict__ cmax) {
+    const long long nn = (long long)n * n;
+    for (int k = blockIdx.x; k < K; k += gridDim.x) {
+        float m = 0.f;
+        for (long long e = threadIdx.x; e < nn; e += blockDim.x) m = fmaxf(m, fabsf(f64_to_f32(C[k * nn + e])));
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int *>(cmax + k), __float_as_int(m));
+    }
+}
+
+// B_k = C_k t_k split into fp16 hi/lo, MN-major core matrices (i contiguous):
+// element (j, i) at (j/8) 1024 + (i/8) 128 + (j%8) 16 + (i%8) 2, hi block then lo block per k.
+__global__ void mp_ct_bsplit_kernel(const double *__restrict__ C, int n, int K, const float *__restrict__ sc,
+                                    __half *__restrict__ Bs) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // over K x 64 x 64
+    if (e >= (long long)K * 4096) return;
+    const int k = (int)(e >> 12), j = (int)((e >> 6) & 63), i = (int)(e & 63);
+    const float v = (i < n && j < n) ? f64_to_f32(C[((long long)k * n + j) * n + i]) * sc[K + k] : 0.f;
+    const __half h = __float2half_rn(v);
+    const __half l = __float2half_rn(v - __half2float(h));
+    const int off = (j >> 3) * 512 + (i >> 3) * 64 + (j & 7) * 8 + (i & 7);  // in halves
+    Bs[(size_t)k * 8192 + off] = h;
+    Bs[(size_t)k * 8192 + 4096 + off] = l;
+}
+
+__device__ __forceinline__ void ct_issue(uint32_t da, uint32_t db, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi,
+                                         uint32_t b_lo, bool accumulate) {
+    const uint32_t idesc = ptx::idesc_f16(128, 64, 1, 1);  // A and B MN-major
+    // A: M-core (8 points) stride 128, K-group (8 orbitals) stride 16 x 128; B: N-core 128, K-group 1024
+    const uint64_t ah0 = ptx::sdesc(a_hi, 2048, 128), al0 = ptx::sdesc(a_lo, 2048, 128);
+    const uint64_t bh0 = ptx::sdesc(b_hi, 1024, 128), bl0 = ptx::sdesc(b_lo, 1024, 128);
+    const uint64_t a_inc = 4096 >> 4, b_inc = 2048 >> 4;  // one k-step = 16 orbitals
+    uint64_t ah = ah0, al = al0, bh = bh0, bl = bl0;
+    for (int ks = 0; ks < 4; ++ks) {
+        ptx::mma_f16(da, ah, bl, idesc, (ks > 0 || accumulate) ? 1u : 0u);
+        ptx::mma_f16(da, al, bh, idesc, 1u);
+        ah += a_inc;
+        al += a_inc;
+        bh += b_inc;
+        bl += b_inc;
+    }
+    ah = ah0;
+    bh = bh0;
+    for (int ks = 0; ks < 4; ++ks) {
+        if (ks & 1)
+            ptx::mma_f16(db, ah, bh, idesc, (ks > 1 || accumulate) ? 1u : 0u);
+        else
+            ptx::mma_f16(da, ah, bh, idesc, 1u);
+        ah += a_inc;
+        bh += b_inc;
+    }
+}
+
+// acc_i(x) = T[x][i] (the float32 accumulator of the pair loop starts from the
+// correction); e_part[CTA] = sum over its tiles of g_i psi_i(x) T[x][i].
+// Persistent: CTA walks the tiles blockIdx.x, + gridDim.x, ...; for each tile
+// the K harmonics go through two shared stages (A_k built by all threads, B_k
+// copied from the pre-split array), one thread issuing each k's products.
+__global__ void __launch_bounds__(256, 1) mp_combine_tc_kernel(const double *__restrict__ psi, int n,
+                                                               const __half *__restrict__ Bs,
+                                                               const float *__restrict__ H, int K,
+                                                               const float *__restrict__ sc,
+                                                               const double *__restrict__ occ, long long N,
+                                                               float *__restrict__ acc, double *__restrict__ e_part,
+                                                               int *status, long long timeout_cycles) {
+    extern __shared__ uint8_t ct_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(ct_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ uint64_t bar[2];
+    __shared__ uint32_t tslot;
+    __shared__ double red[8];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) {
+        ptx::tmem_alloc(&tslot, 128);
+        ptx::tmem_relinquish();
+    }
+    if (tid == 0) {
+        ptx::mbar_init(&bar[0], 1);
+        ptx::mbar_init(&bar[1], 1);
+        ptx::fence_mbar_init();
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem = tslot;
+    const float unscale = sc[2 * K];
+    const long long ntiles = (N + kCtM - 1) / kCtM;
+    // producer task of this thread: point group mg (8 points), orbitals j0 + 16 u
+    const int mg = tid & 15, j0 = tid >> 4;
+    uint32_t uses[2] = {0u, 0u};  // commits issued per stage
+    uint32_t waited[2] = {0u, 0u};
+    bool ok = true;
+    double e_acc = 0.0;
+    for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const long long xb = tile * kCtM + 8 * mg;
+        float pv[4][8];  // psi_j at the thread's 8 points, scaled later per k
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = j0 + 16 * u;
+            if (j < n && xb < N) {
+                const double2 *src = reinterpret_cast<const double2 *>(psi + (long long)j * N + xb);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const double2 d = __ldg(src + c);
+                    pv[u][2 * c] = f64_to_f32(d.x);
+                    pv[u][2 * c + 1] = f64_to_f32(d.y);
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) pv[u][c] = 0.f;
+            }
+        }
+        for (int k = 0; k < K && ok; ++k) {
+            const int b = k & 1;
+            uint8_t *st = smem + b * kCtStage;
+            if (uses[b] > waited[b]) {  // the products that last read this stage are done
+                ok = __syncthreads_and(ptx::mbar_wait_bounded(&bar[b], (waited[b]) & 1u, timeout_cycles));
+                ++waited[b];
+                if (!ok) break;
+                ptx::tc_fence_after();
+            }
+            // A_k: (h_k psi_j) at the 8 points, scaled by sc[k]
+            float hv[8];
+            if (xb < N) {
+                const float4 *hs = reinterpret_cast<const float4 *>(H + (long long)k * N + xb);
+                const float4 a = __ldg(hs), c = __ldg(hs + 1);
+                const float sk = sc[k];
+                hv[0] = a.x * sk; hv[1] = a.y * sk; hv[2] = a.z * sk; hv[3] = a.w * sk;
+                hv[4] = c.x * sk; hv[5] = c.y * sk; hv[6] = c.z * sk; hv[7] = c.w * sk;
+            } else {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) hv[c] = 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int j = j0 + 16 * u;
+                float w[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) w[c] = pv[u][c] * hv[c];
+                mt_split_store(st, st + kCtA, mg * 128 + (j >> 3) * 2048 + (j & 7) * 16, w);
+            }
+            // B_k: 2 x 8 KB from the pre-split array
+            {
+                const uint4 *src = reinterpret_cast<const uint4 *>(Bs + (size_t)k * 8192);
+                uint4 *dst = reinterpret_cast<uint4 *>(st + 2 * kCtA);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) dst[tid + 256 * q] = __ldg(src + tid + 256 * q);
+            }
+            ptx::fence_proxy_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                ptx::tc_fence_after();
+                const uint32_t sa = ptx::smem_u32(st), sb = sa + 2 * (uint32_t)kCtA;
+                ct_issue(tmem, tmem + 64, sa, sa + (uint32_t)kCtA, sb, sb + (uint32_t)kCtB, k > 0);
+                ptx::mma_commit(&bar[b]);
+            }
+            ++uses[b];
+        }
+        // the tile's last products are done: read T, update Vx psi, energy
+        for (int b = 0; b < 2 && ok; ++b)
+            while (ok && uses[b] > waited[b]) {
+                ok = __syncthreads_and(ptx::mbar_wait_bounded(&bar[b], waited[b] & 1u, timeout_cycles));
+                ++waited[b];
+            }
+        if (!ok) break;
+        ptx::tc_fence_after();
+        if (warp < 4) {
+            const int m = warp * 32 + lane;
+            const long long x = tile * kCtM + m;
+            const uint32_t tl = tmem + ((uint32_t)(32 * warp) << 16);
+            float ef = 0.f;
+            for (int c0 = 0; c0 < 64; c0 += 16) {
+                float va[16], vb[16];
+                ptx::tmem_ld16x2(tl + c0, tl + 64 + c0, va, vb);
+                if (x >= N) continue;
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    const int i = c0 + c;
+                    if (i >= n) continue;
+                    const float t = (va[c] + vb[c]) * unscale;
+                    acc[(long long)i * N + x] = t;
+                    const float gi = occ ? f64_to_f32(occ[i]) : 1.f;
+                    ef = fmaf(gi * f64_to_f32(__ldg(psi + (long long)i * N + x)), t, ef);
+                }
+            }
+            e_acc += (double)ef;
+        }
+        ptx::tc_fence_before();
+        __syncthreads();  // TMEM read before the next tile's first product overwrites it
+        ptx::tc_fence_after();
+    }
+    if (!ok && tid == 0) atomicExch(status, KX_ERR_TIMEOUT);
+    for (int o = 16; o > 0; o >>= 1) e_acc += __shfl_xor_sync(0xffffffffu, e_acc, o);
+    if (lane == 0) red[warp] = e_acc;
+    ptx::tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+        double sum = 0.0;
+        for (int w = 0; w < 8; ++w) sum += red[w];
+        e_part[blockIdx.x] = sum;
+    }
+    if (warp == 0) {
+        ptx::tc_fence_after();
+        ptx::tmem_dealloc(tmem, 128);
+    }
+}
+
 // Q[e] = scale sum_c part[c][e] in a fixed order.
 __global__ void mp_reduce_kernel(const double *__restrict__ part, int n_part, long long n_e, double scale,
                                  double *__restrict__ Q) {
@@ -539,13 +790,42 @@ std::vector<double> centred_weights(int order) {
 // harmonic pairs in groups of kMtPairs.
 int moments_tc_split(const kx_plan *p) { return p->num_sms; }
 
+constexpr size_t kMpSmall = 4096;  // psimax (1 float), cmax (<= 81), scales (<= 163)
+
 size_t mp_scratch_bytes(const kx_plan *p, int n, int K) {
     const long long N = (long long)p->N;
     const size_t kn2 = (size_t)K * n * n;
     const size_t tiles = (size_t)((N + kMcX - 1) / kMcX) * ((n + 63) / 64);
     const size_t part64 = (size_t)((N + 255) / 256) * n;
     const size_t part_tc = n <= 64 ? (size_t)moments_tc_split(p) * kn2 : 0;
-    return sizeof(double) * (2 * kn2 + kn2 + std::max(std::max(tiles, part64), part_tc)) + 1024;
+    return kMpSmall + sizeof(double) * (2 * kn2 + std::max(std::max(tiles, part64), part_tc)) + (size_t)K * 16384;
+}
+
+// Layout of the plan's multipole scratch for n orbitals: small float arrays
+// (max |psi|, max |C_k|, scales), Q, then P or C, the partial sums, the
+// pre-split B tiles.
+struct MpScratch {
+    float *psimax, *cmax, *sc;
+    double *Q, *P, *part;
+    __half *Bs;
+};
+
+MpScratch mp_layout(const kx_plan *p, int n) {
+    const size_t kn2 = (size_t)p->mp_K * n * n;
+    const long long N = (long long)p->N;
+    const size_t tiles = (size_t)((N + kMcX - 1) / kMcX) * ((n + 63) / 64);
+    const size_t part64 = (size_t)((N + 255) / 256) * n;
+    const size_t part_tc = n <= 64 ? (size_t)moments_tc_split(p) * kn2 : 0;
+    uint8_t *b = (uint8_t *)p->mp_scratch.ptr;
+    MpScratch m;
+    m.psimax = reinterpret_cast<float *>(b);
+    m.cmax = reinterpret_cast<float *>(b + 256);
+    m.sc = reinterpret_cast<float *>(b + 1024);
+    m.Q = reinterpret_cast<double *>(b + kMpSmall);
+    m.P = m.Q + kn2;
+    m.part = m.P + kn2;
+    m.Bs = reinterpret_cast<__half *>(m.part + std::max(std::max(tiles, part64), part_tc));
+    return m;
 }
 
 // Q[k] = dV sum_x W_k psi_i psi_j for k < K (weights W: K x N).  Tensor cores for
@@ -668,6 +948,18 @@ int mp_set(kx_plan *p, int l_max) {
     return KX_OK;
 }
 
+int mp_reserve_scratch(kx_plan *p, int n_orb) {
+    const size_t need = mp_scratch_bytes(p, n_orb, p->mp_K);
+    if (p->mp_scratch.bytes < need) {
+        cudaFree(p->mp_scratch.ptr);
+        p->mp_scratch = Workspace{};
+        cudaError_t e = cudaMalloc(&p->mp_scratch.ptr, need);
+        if (e != cudaSuccess) return cuda_error(e, "multipole scratch cudaMalloc");
+        p->mp_scratch.bytes = need;
+    }
+    return KX_OK;
+}
+
 int mp_reserve(kx_plan *p, int n_orb) {
     if (p->mp_lmax < 0) return KX_OK;
     const size_t need = mp_scratch_bytes(p, n_orb, p->mp_K);
@@ -691,10 +983,11 @@ int mp_correct_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, d
     const long long N = (long long)p->N;
     const size_t nn = (size_t)n * n;
     const bool f64 = p->precision == KX_FP64;
-    double *Q = (double *)p->mp_scratch.ptr;
-    double *P = Q + (size_t)K * nn;  // energy-only: projections on h_k; otherwise C
-    double *part = P + (size_t)K * nn + (size_t)K * nn;
-    float *psimax = reinterpret_cast<float *>(P + (size_t)K * nn);  // the unused third block
+    const MpScratch m = mp_layout(p, n);
+    double *Q = m.Q;
+    double *P = m.P;  // energy-only: projections on h_k; otherwise C
+    double *part = m.part;
+    float *psimax = m.psimax;
     const unsigned char *mask = p->d_pair_mask;
     // moments Q_k(ij) = dV sum_x R_k psi_i psi_j
     if ((rc = weighted_moments(p, n, psi, p->d_mpR, p->d_mpR32, p->d_mpMax, Q, part, psimax, s))) return rc;
@@ -735,6 +1028,47 @@ int mp_correct_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, d
         mp_energy_add_kernel<<<1, 1, 0, s>>>(part, (long long)grid.x * grid.y, -0.5 * p->dV, ex);
         KX_LAUNCH_CHECK("mp_energy_add_kernel launch");
     }
+    return prof_end(p, s);
+}
+
+bool mp_tc_eligible(const kx_plan *p, int n_orb, const double *psi) {
+    return p->mp_lmax >= 0 && p->precision != KX_FP64 && n_orb <= 64 && p->N % 8 == 0 &&
+           (reinterpret_cast<uintptr_t>(psi) & 15) == 0;
+}
+
+int mp_correct_into_acc(kx_plan *p, int n_orb, const double *psi, const double *occ, float *acc, double *ex,
+                        cudaStream_t s) {
+    int rc = mp_reserve_scratch(p, n_orb);
+    if (rc) return rc;
+    const int K = p->mp_K, n = n_orb;
+    const long long N = (long long)p->N;
+    const size_t nn = (size_t)n * n;
+    const MpScratch m = mp_layout(p, n);
+    double *Q = m.Q, *C = m.P, *part = m.part;
+    float *psimax = m.psimax, *cmax = m.cmax, *sc = m.sc;
+    __half *Bs = m.Bs;
+    if ((rc = weighted_moments(p, n, psi, p->d_mpR, p->d_mpR32, p->d_mpMax, Q, part, psimax, s))) return rc;
+    if ((rc = prof_begin(p, PK_MP, s))) return rc;
+    const unsigned cb = (unsigned)((nn * K + 255) / 256);
+    mp_coef_kernel<double><<<cb, 256, 0, s>>>(Q, p->d_pair_mask, occ, n, K, C);
+    KX_LAUNCH_CHECK("mp_coef_kernel launch");
+    KX_CUDA_TRY(cudaMemsetAsync(cmax, 0, sizeof(float) * K, s));
+    mp_cmax_kernel<<<K, 256, 0, s>>>(C, n, K, cmax);
+    KX_LAUNCH_CHECK("mp_cmax_kernel launch");
+    mp_ct_scales_kernel<<<1, 1, 0, s>>>(p->d_mpMax + K, cmax, psimax, K, sc);
+    KX_LAUNCH_CHECK("mp_ct_scales_kernel launch");
+    mp_ct_bsplit_kernel<<<(unsigned)(((long long)K * 4096 + 255) / 256), 256, 0, s>>>(C, n, K, sc, Bs);
+    KX_LAUNCH_CHECK("mp_ct_bsplit_kernel launch");
+    const int grid = (int)std::min<long long>((N + kCtM - 1) / kCtM, p->num_sms);
+    KX_CUDA_TRY(cudaFuncSetAttribute(mp_combine_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCtSmem));
+    mp_combine_tc_kernel<<<grid, 256, kCtSmem, s>>>(psi, n, Bs, p->d_mpH32, K, sc, occ, N, acc, part, p->d_status,
+                                                     4000000000LL);
+    KX_LAUNCH_CHECK("mp_combine_tc_kernel launch");
+    if (ex) {
+        mp_energy_add_kernel<<<1, 1, 0, s>>>(part, grid, -0.5 * p->dV, ex);
+        KX_LAUNCH_CHECK("mp_energy_add_kernel launch");
+    }
+    p->mp_applied = true;
     return prof_end(p, s);
 }
 

@@ -1682,8 +1682,16 @@ int tc_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, double *v
         KX_LAUNCH_CHECK("prep_kernel launch");
         if ((rc = prof_end(p, s))) return rc;
     }
-    if (!energy_only) KX_CUDA_TRY(cudaMemsetAsync(L.acc, 0, sizeof(float) * (size_t)n_orb * N, s));
     if (ex) KX_CUDA_TRY(cudaMemsetAsync(ex, 0, sizeof(double), s));
+    if (!energy_only) {
+        // with multipole boundary values the accumulator starts from the boundary
+        // correction (tensor-core form), otherwise from zero
+        if (mp_tc_eligible(p, n_orb, psi)) {
+            if ((rc = mp_correct_into_acc(p, n_orb, psi, occ, L.acc, ex, s))) return rc;
+        } else {
+            KX_CUDA_TRY(cudaMemsetAsync(L.acc, 0, sizeof(float) * (size_t)n_orb * N, s));
+        }
+    }
     const int2 *pairs = reinterpret_cast<const int2 *>(p->d_pairs);
     const float mid_bound = fmax_sqrt(p);
 

@@ -621,6 +621,13 @@ __global__ void __launch_bounds__(256, 1) mp_combine_tc_kernel(const double *__r
                 for (int c = 0; c < 8; ++c) pv[u][c] = 0.f;
             }
         }
+        // h_k at the thread's 8 points, fetched one harmonic ahead
+        float4 hn0 = make_float4(0.f, 0.f, 0.f, 0.f), hn1 = hn0;
+        if (xb < N) {
+            const float4 *hs = reinterpret_cast<const float4 *>(H + xb);
+            hn0 = __ldg(hs);
+            hn1 = __ldg(hs + 1);
+        }
         for (int k = 0; k < K && ok; ++k) {
             const int b = k & 1;
             uint8_t *st = smem + b * kCtStage;
@@ -630,17 +637,22 @@ __global__ void __launch_bounds__(256, 1) mp_combine_tc_kernel(const double *__r
                 if (!ok) break;
                 ptx::tc_fence_after();
             }
-            // A_k: (h_k psi_j) at the 8 points, scaled by sc[k]
-            float hv[8];
-            if (xb < N) {
-                const float4 *hs = reinterpret_cast<const float4 *>(H + (long long)k * N + xb);
-                const float4 a = __ldg(hs), c = __ldg(hs + 1);
-                const float sk = sc[k];
-                hv[0] = a.x * sk; hv[1] = a.y * sk; hv[2] = a.z * sk; hv[3] = a.w * sk;
-                hv[4] = c.x * sk; hv[5] = c.y * sk; hv[6] = c.z * sk; hv[7] = c.w * sk;
-            } else {
+            // B_k: 2 x 8 KB from the pre-split array, copied while A_k is built
+            {
+                const uint4 *src = reinterpret_cast<const uint4 *>(Bs + (size_t)k * 8192);
+                uint8_t *dst = st + 2 * kCtA;
 #pragma unroll
-                for (int c = 0; c < 8; ++c) hv[c] = 0.f;
+                for (int q = 0; q < 4; ++q) ptx::cp_async16(dst + 16 * (tid + 256 * q), src + tid + 256 * q, 16u);
+                ptx::cp_async_commit();
+            }
+            // A_k: (h_k psi_j) at the 8 points, scaled by sc[k]
+            const float sk = sc[k];
+            const float hv[8] = {hn0.x * sk, hn0.y * sk, hn0.z * sk, hn0.w * sk,
+                                 hn1.x * sk, hn1.y * sk, hn1.z * sk, hn1.w * sk};
+            if (k + 1 < K && xb < N) {
+                const float4 *hs = reinterpret_cast<const float4 *>(H + (long long)(k + 1) * N + xb);
+                hn0 = __ldg(hs);
+                hn1 = __ldg(hs + 1);
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -650,13 +662,7 @@ __global__ void __launch_bounds__(256, 1) mp_combine_tc_kernel(const double *__r
                 for (int c = 0; c < 8; ++c) w[c] = pv[u][c] * hv[c];
                 mt_split_store(st, st + kCtA, mg * 128 + (j >> 3) * 2048 + (j & 7) * 16, w);
             }
-            // B_k: 2 x 8 KB from the pre-split array
-            {
-                const uint4 *src = reinterpret_cast<const uint4 *>(Bs + (size_t)k * 8192);
-                uint4 *dst = reinterpret_cast<uint4 *>(st + 2 * kCtA);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) dst[tid + 256 * q] = __ldg(src + tid + 256 * q);
-            }
+            ptx::cp_async_wait<0>();
             ptx::fence_proxy_async_smem();
             __syncthreads();
             if (tid == 0) {
@@ -798,7 +804,8 @@ size_t mp_scratch_bytes(const kx_plan *p, int n, int K) {
     const size_t tiles = (size_t)((N + kMcX - 1) / kMcX) * ((n + 63) / 64);
     const size_t part64 = (size_t)((N + 255) / 256) * n;
     const size_t part_tc = n <= 64 ? (size_t)moments_tc_split(p) * kn2 : 0;
-    return kMpSmall + sizeof(double) * (2 * kn2 + std::max(std::max(tiles, part64), part_tc)) + (size_t)K * 16384;
+    return kMpSmall + sizeof(double) * (2 * kn2 + std::max(std::max(tiles, part64), part_tc)) + 256 +
+           (size_t)K * 16384;
 }
 
 // Layout of the plan's multipole scratch for n orbitals: small float arrays
@@ -824,7 +831,8 @@ MpScratch mp_layout(const kx_plan *p, int n) {
     m.Q = reinterpret_cast<double *>(b + kMpSmall);
     m.P = m.Q + kn2;
     m.part = m.P + kn2;
-    m.Bs = reinterpret_cast<__half *>(m.part + std::max(std::max(tiles, part64), part_tc));
+    const uintptr_t bs = reinterpret_cast<uintptr_t>(m.part + std::max(std::max(tiles, part64), part_tc));
+    m.Bs = reinterpret_cast<__half *>((bs + 255) & ~uintptr_t(255));  // 16-byte copies need alignment
     return m;
 }
 

@@ -44,9 +44,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["kronx", "reference"], default="kronx")
     ap.add_argument("--no-extras", action="store_true", help="skip FP64/e2e/oracle legs (profiling runs)")
-    ap.add_argument("--profile-case", choices=["small", "ace"], default=None,
+    ap.add_argument("--profile-case", choices=["small", "ace", "multipole"], default=None,
                     help="small: one apply of a small case of the same kernels (96^3, 8 orbitals); ace: three "
-                         "ACE operator applies at 96^3 with 64 + 64 vectors; both for ncu captures")
+                         "ACE operator applies at 96^3 with 64 + 64 vectors; multipole: two applies of the "
+                         "headline system with boundary values to order 4; all for ncu captures")
     return ap.parse_args()
 
 
@@ -60,6 +61,15 @@ def run_profile_case(which="small"):
     import paper_2406_16998_gb300 as kx
     from paper_2406_16998_gb300 import build
     build.build()
+    if which == "multipole":
+        plan = kx.Plan.for_system(SYS, precision=kx.KX_F16X3)
+        plan.set_multipole(4)
+        psi = torch.from_numpy(np.ascontiguousarray(workloads.make_orbitals(SYS).T)).cuda()
+        for _ in range(2):
+            vx, ex = kx.kx_vx_apply(plan, psi)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "multipole", "e_x": ex.item(), "status": plan.status()}), flush=True)
+        return
     if which == "ace":
         plan = kx.Plan.for_system(SYS, precision=kx.KX_F16X3)
         xi = torch.from_numpy(np.ascontiguousarray(workloads.random_field(plan.N, 64, 3).T) * 1e-3).cuda()

@@ -596,8 +596,10 @@ __global__ void __launch_bounds__(256, 1) mp_combine_tc_kernel(const double *__r
     const uint32_t tmem = tslot;
     const float unscale = sc[2 * K];
     const long long ntiles = (N + kCtM - 1) / kCtM;
-    // producer task of this thread: point group mg (8 points), orbitals j0 + 16 u
-    const int mg = tid & 15, j0 = tid >> 4;
+    // producer tasks of this thread: point group mg (8 points) and orbitals
+    // j = 8 (jh + 2u) + jl, u < 4: eight neighbouring lanes fill one 128-byte
+    // core matrix (the eight orbitals of a K group at one point group)
+    const int jl = tid & 7, mg = (tid >> 3) & 15, jh = tid >> 7;
     uint32_t uses[2] = {0u, 0u};  // commits issued per stage
     uint32_t waited[2] = {0u, 0u};
     bool ok = true;
@@ -607,7 +609,7 @@ __global__ void __launch_bounds__(256, 1) mp_combine_tc_kernel(const double *__r
         float pv[4][8];  // psi_j at the thread's 8 points, scaled later per k
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const int j = j0 + 16 * u;
+            const int j = 8 * (jh + 2 * u) + jl;
             if (j < n && xb < N) {
                 const double2 *src = reinterpret_cast<const double2 *>(psi + (long long)j * N + xb);
 #pragma unroll
@@ -656,7 +658,7 @@ __global__ void __launch_bounds__(256, 1) mp_combine_tc_kernel(const double *__r
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const int j = j0 + 16 * u;
+                const int j = 8 * (jh + 2 * u) + jl;
                 float w[8];
 #pragma unroll
                 for (int c = 0; c < 8; ++c) w[c] = pv[u][c] * hv[c];

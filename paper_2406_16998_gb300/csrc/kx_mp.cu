@@ -280,7 +280,13 @@ constexpr int kMtPairs = 4;               // harmonic pairs per CTA (two fp32 ac
 constexpr uint32_t kMtGroup = 1024;       // bytes per 8-row group: 8 core matrices of 8 points along K
 constexpr size_t kMtB = 64 * kMtX * 2;    // hi (or lo) of B: 64 orbitals x 64 points fp16
 constexpr size_t kMtA = 128 * kMtX * 2;   // hi (or lo) of one A pair tile
-constexpr size_t kMtSmem = 2 * kMtB + (size_t)kMtPairs * 2 * kMtA + 1024;
+// raw inputs of one step, copied a step ahead: psi rows (64 points, float64,
+// rows padded by 16 bytes so that lanes reading different rows hit distinct
+// banks) and the pass's 8 weight rows (float32)
+constexpr int kMtRawRow = kMtX * 8 + 16;
+constexpr size_t kMtRawPsi = 64 * (size_t)kMtRawRow;
+constexpr size_t kMtRaw = kMtRawPsi + 2 * kMtPairs * kMtX * 4;
+constexpr size_t kMtSmem = 2 * kMtB + (size_t)kMtPairs * 2 * kMtA + 2 * kMtRaw + 1024;
 
 __device__ __forceinline__ void mt_split_store(uint8_t *hi, uint8_t *lo, int off, const float *w) {
     __half2 h[4], l[4];
@@ -333,6 +339,7 @@ __global__ void __launch_bounds__(256, 1) mp_moments_tc_kernel(const double *__r
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(mt_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *Bhi = smem, *Blo = smem + kMtB;
     uint8_t *A0 = smem + 2 * kMtB;  // pair p: hi at A0 + 2p kMtA, lo after it
+    uint8_t *raw0 = A0 + (size_t)kMtPairs * 2 * kMtA;  // two raw stages
     __shared__ uint64_t bar;
     __shared__ uint32_t tslot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -364,57 +371,69 @@ __global__ void __launch_bounds__(256, 1) mp_moments_tc_kernel(const double *__r
     const long long x0 = (long long)blockIdx.x * span;
     const long long x1 = min(N, x0 + span);
     const int nsteps = x1 > x0 ? (int)((x1 - x0 + kMtX - 1) / kMtX) : 0;
+    // copies of step t's raw inputs into stage t & 1: psi rows i < n and the
+    // pass's weight rows, 16-byte pieces (zero-filled past the range)
+    auto issue_raw = [&](int t) {
+        uint8_t *dst = raw0 + (size_t)(t & 1) * kMtRaw;
+        const long long xs = x0 + (long long)t * kMtX;
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            const int piece = tid + 256 * m, i = piece >> 5, c = piece & 31;  // row i, 2 points per piece
+            const long long x = xs + 2 * c;
+            const bool ok_ = i < n && x < x1;
+            ptx::cp_async16(dst + i * kMtRawRow + 16 * c, ok_ ? (const void *)(psi + (long long)i * N + x) : psi,
+                            ok_ ? 16u : 0u);
+        }
+        if (tid < 2 * kMtPairs * kMtX / 4) {
+            const int q = tid >> 4, c = tid & 15;  // weight row q, 4 points per piece
+            const int k = 2 * kp0 + q;
+            const long long x = xs + 4 * c;
+            const bool ok_ = q < 2 * npair && k < K && x < x1;
+            ptx::cp_async16(dst + kMtRawPsi + q * (kMtX * 4) + 16 * c,
+                            ok_ ? (const void *)(R32 + (long long)k * N + x) : R32, ok_ ? 16u : 0u);
+        }
+    };
+    if (nsteps > 0) issue_raw(0);
+    ptx::cp_async_commit();
     uint32_t phase = 0;
     bool ok = true;
     for (int s = 0; s < nsteps && ok; ++s) {
+        if (s + 1 < nsteps) issue_raw(s + 1);
+        ptx::cp_async_commit();
+        ptx::cp_async_wait<1>();  // this thread's copies of step s have landed
         if (s > 0) {
             // the previous step's products have read the tiles
             ok = __syncthreads_and(ptx::mbar_wait_bounded(&bar, phase, timeout_cycles));
             phase ^= 1u;
             if (!ok) break;
             ptx::tc_fence_after();
+        } else {
+            __syncthreads();
         }
+        const uint8_t *rs = raw0 + (size_t)(s & 1) * kMtRaw;
 #pragma unroll 1
         for (int r = 0; r < 2; ++r) {
             const int i = tid & 63, g = (tid >> 6) + 4 * r;  // orbital, group of 8 points
-            const long long xb = x0 + (long long)s * kMtX + 8 * g;
-            // all loads of the task first (16-byte pieces; N % 8 == 0 and aligned rows,
-            // checked by the launcher), then the products
-            float v[8], rw[2 * kMtPairs][8];
-            if (i < n && xb < x1) {
-                const double2 *src = reinterpret_cast<const double2 *>(psi + (long long)i * N + xb);
-                double2 d[4];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) d[c] = __ldg(src + c);
+            float v[8];
+            {
+                const double2 *src = reinterpret_cast<const double2 *>(rs + i * kMtRawRow + 64 * g);
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    v[2 * c] = f64_to_f32(d[c].x) * sp;
-                    v[2 * c + 1] = f64_to_f32(d[c].y) * sp;
-                }
-            } else {
-#pragma unroll
-                for (int c = 0; c < 8; ++c) v[c] = 0.f;
-            }
-#pragma unroll
-            for (int q = 0; q < 2 * kMtPairs; ++q) {
-                const int k = 2 * kp0 + q;
-                if (q < 2 * npair && k < K && xb < x1) {
-                    const float4 *src = reinterpret_cast<const float4 *>(R32 + (long long)k * N + xb);
-                    const float4 a = __ldg(src), b = __ldg(src + 1);
-                    rw[q][0] = a.x; rw[q][1] = a.y; rw[q][2] = a.z; rw[q][3] = a.w;
-                    rw[q][4] = b.x; rw[q][5] = b.y; rw[q][6] = b.z; rw[q][7] = b.w;
-                } else {
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) rw[q][c] = 0.f;
+                    const double2 d = src[c];
+                    v[2 * c] = f64_to_f32(d.x) * sp;
+                    v[2 * c + 1] = f64_to_f32(d.y) * sp;
                 }
             }
             mt_split_store(Bhi, Blo, (i >> 3) * kMtGroup + g * 128 + (i & 7) * 16, v);
 #pragma unroll
             for (int q = 0; q < 2 * kMtPairs; ++q) {
                 if (q >= 2 * npair) break;
+                const float4 *wr = reinterpret_cast<const float4 *>(rs + kMtRawPsi + q * (kMtX * 4) + 32 * g);
+                const float4 a = wr[0], b = wr[1];
+                const float rv[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
                 float w[8];
 #pragma unroll
-                for (int c = 0; c < 8; ++c) w[c] = v[c] * (rw[q][c] * sk[q]);
+                for (int c = 0; c < 8; ++c) w[c] = v[c] * (rv[c] * sk[q]);
                 const int row = (q & 1) * 64 + i;
                 uint8_t *Ahi = A0 + (size_t)(q >> 1) * 2 * kMtA;
                 mt_split_store(Ahi, Ahi + kMtA, (row >> 3) * kMtGroup + g * 128 + (row & 7) * 16, w);
@@ -432,6 +451,7 @@ __global__ void __launch_bounds__(256, 1) mp_moments_tc_kernel(const double *__r
             ptx::mma_commit(&bar);
         }
     }
+    ptx::cp_async_wait<0>();
     if (nsteps > 0 && ok) ok = __syncthreads_and(ptx::mbar_wait_bounded(&bar, phase, timeout_cycles));
     if (!ok && tid == 0) atomicExch(status, KX_ERR_TIMEOUT);
     ptx::tc_fence_after();

@@ -600,6 +600,7 @@ __global__ void __launch_bounds__(256, 1) mp_combine_tc_kernel(const double *__r
     __shared__ uint64_t bar[2];
     __shared__ uint32_t tslot;
     __shared__ double red[8];
+    __shared__ volatile int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (warp == 0) {
         ptx::tmem_alloc(&tslot, 128);
@@ -609,6 +610,7 @@ __global__ void __launch_bounds__(256, 1) mp_combine_tc_kernel(const double *__r
         ptx::mbar_init(&bar[0], 1);
         ptx::mbar_init(&bar[1], 1);
         ptx::fence_mbar_init();
+        s_abort = 0;
     }
     ptx::tc_fence_before();
     __syncthreads();
@@ -653,10 +655,11 @@ __global__ void __launch_bounds__(256, 1) mp_combine_tc_kernel(const double *__r
         for (int k = 0; k < K && ok; ++k) {
             const int b = k & 1;
             uint8_t *st = smem + b * kCtStage;
-            if (uses[b] > waited[b]) {  // the products that last read this stage are done
-                ok = __syncthreads_and(ptx::mbar_wait_bounded(&bar[b], (waited[b]) & 1u, timeout_cycles));
+            if (uses[b] > waited[b]) {
+                // the products that last read this stage are done (each thread waits by
+                // itself; a timeout is acted on after the block barrier below)
+                if (!ptx::mbar_wait_bounded(&bar[b], waited[b] & 1u, timeout_cycles)) s_abort = 1;
                 ++waited[b];
-                if (!ok) break;
                 ptx::tc_fence_after();
             }
             // B_k: 2 x 8 KB from the pre-split array, copied while A_k is built
@@ -687,6 +690,10 @@ __global__ void __launch_bounds__(256, 1) mp_combine_tc_kernel(const double *__r
             ptx::cp_async_wait<0>();
             ptx::fence_proxy_async_smem();
             __syncthreads();
+            if (s_abort) {
+                ok = false;
+                break;
+            }
             if (tid == 0) {
                 ptx::tc_fence_after();
                 const uint32_t sa = ptx::smem_u32(st), sb = sa + 2 * (uint32_t)kCtA;
@@ -729,6 +736,9 @@ __global__ void __launch_bounds__(256, 1) mp_combine_tc_kernel(const double *__r
         ptx::tc_fence_after();
     }
     if (!ok && tid == 0) atomicExch(status, KX_ERR_TIMEOUT);
+    // products still in flight after an early exit finish before TMEM is released
+    for (int b = 0; b < 2; ++b)
+        for (; uses[b] > waited[b]; ++waited[b]) ptx::mbar_wait_bounded(&bar[b], waited[b] & 1u, timeout_cycles);
     for (int o = 16; o > 0; o >>= 1) e_acc += __shfl_xor_sync(0xffffffffu, e_acc, o);
     if (lane == 0) red[warp] = e_acc;
     ptx::tc_fence_before();

@@ -59,6 +59,10 @@ typedef struct CUstream_st *kx_stream;
 #define KX_F16X3 1 /* tensor cores: fp16 hi/lo split of both operands, three products
                       (hi*hi + hi*lo + lo*hi) accumulated in fp32, per-pair power-of-two
                       scaling; energy and outputs accumulated in fp32/fp64            */
+#define KX_FFT32 2 /* fully periodic grids only: f(L) through the DFT (the eigenvectors of
+                      a periodic axis are Fourier modes), float32 complex Stockham FFTs
+                      of radix 2, 3, 4, 5; every n[a] a product of 2, 3 and 5; the
+                      FFT variant the Kronecker form is compared with (Sec. 3, Fig. 1) */
 
 /* Error codes. */
 #define KX_OK              0
@@ -286,7 +290,7 @@ int kx_profile(kx_plan *plan, int enable);
  * 13 ACE combinations of grid vectors (xi = W R^{-1}, -xi P); kind 9 covers
  * the ACE projections over the grid and their reduction; 14 the multipole
  * boundary correction (moments of the sources, correction of the solution,
- * Vx psi and E_x).
+ * Vx psi and E_x), 15 the DFT passes of KX_FFT32 plans.
  * Synchronises on the recorded events. */
 int kx_profile_read(kx_plan *plan, int n_kinds, double *ms, long long *launches);
 

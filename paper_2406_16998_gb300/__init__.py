@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libkronx.so")
 
 KX_DIRICHLET, KX_PERIODIC = 0, 1
 KX_UNSCREENED, KX_SCREENED = 0, 1
-KX_FP64, KX_F16X3 = 0, 1
+KX_FP64, KX_F16X3, KX_FFT32 = 0, 1, 2
 KX_OK, KX_ERR_ARG, KX_ERR_SINGULAR, KX_ERR_NOMEM, KX_ERR_CUDA, KX_ERR_TIMEOUT, KX_ERR_UNSUPPORTED = range(7)
 
 # Every symbol the C header declares, with (restype, argtypes).
@@ -190,7 +190,7 @@ class Plan:
         return f
 
     PROFILE_KINDS = ["prep", "X3F", "X2F", "X1", "X2I", "X3I", "final", "fp64_mode", "fp64_other", "ace",
-                     "setup", "acc", "slab", "ace_comb", "multipole"]
+                     "setup", "acc", "slab", "ace_comb", "multipole", "fft"]
 
     def profile(self, enable=True):
         _check(lib().kx_profile(self.handle, 1 if enable else 0))

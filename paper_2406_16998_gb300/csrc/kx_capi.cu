@@ -257,8 +257,12 @@ int kx_plan_create(const kx_grid *grid, const kx_kernel *kernel, int precision, 
         return set_error(KX_ERR_ARG, "kx_plan_create: unknown kernel kind");
     if (kernel->kind == KX_SCREENED && !(kernel->omega > 0.0))
         return set_error(KX_ERR_ARG, "kx_plan_create: omega must be > 0 for the screened kernel");
-    if (precision != KX_FP64 && precision != KX_F16X3)
+    if (precision != KX_FP64 && precision != KX_F16X3 && precision != KX_FFT32)
         return set_error(KX_ERR_ARG, "kx_plan_create: unknown precision");
+    if (precision == KX_FFT32 && !fft_supported(grid->n, grid->bc))
+        return set_error(KX_ERR_UNSUPPORTED,
+                         "kx_plan_create: KX_FFT32 needs periodic axes whose sizes are products of 2, 3 and 5 "
+                         "and an n[0] x n[1] plane of at most about 12,000 points");
     if (precision == KX_F16X3)
         for (int a = 0; a < 3; ++a)
             if (grid->n[a] % 8)
@@ -342,6 +346,8 @@ int kx_apply_fL_noalloc(kx_plan *plan, int n_rhs, const double *b, double *x, kx
     if (b == x) return set_error(KX_ERR_ARG, "kx_apply_fL_noalloc: x must not overlap b");
     if (plan->mp_lmax >= 0)
         return set_error(KX_ERR_UNSUPPORTED, "kx_apply_fL_noalloc: not available with multipole boundary values");
+    if (plan->precision == KX_FFT32)
+        return set_error(KX_ERR_UNSUPPORTED, "kx_apply_fL_noalloc: not available on KX_FFT32 plans");
     return tc_apply_fL_noalloc(plan, n_rhs, b, x, reinterpret_cast<cudaStream_t>(stream));
 }
 
@@ -608,7 +614,7 @@ int kx_batch_destroy(kx_batch *batch) {
 int kx_autotune(kx_plan *plan, int n_orb, int budget_ms) {
     if (int rc = check_plan(plan)) return rc;
     if (n_orb < 1 || n_orb > 4096 || budget_ms < 0) return set_error(KX_ERR_ARG, "kx_autotune: bad arguments");
-    if (plan->precision == KX_FP64) return KX_OK;  // single launch shape
+    if (plan->precision == KX_FP64 || plan->precision == KX_FFT32) return KX_OK;  // single launch shape
     const size_t vec = sizeof(double) * (size_t)n_orb * plan->N;
     double *buf = nullptr;
     KX_CUDA_TRY(cudaMalloc(&buf, 2 * vec + sizeof(double)));

@@ -1,0 +1,331 @@
+// Fully periodic grids through the discrete Fourier transform: the FFT variant
+// that Sec. 3 and Fig. 1 set the Kronecker form against.  On a periodic axis
+// the centred stencil is a circulant matrix, diagonalised by the DFT with
+// eigenvalues lambda_a(k) = (w0 + 2 sum_p w_p cos(2 pi p k / n_a)) / h_a^2, so
+//     f(L) b = IDFT( f(lambda1 + lambda2 + lambda3) . DFT(b) ),
+// the same operator as the Kronecker form with Fourier eigenvectors.  Per item
+// (a pair density or a right-hand side) three passes, float32 complex:
+//   A  per x3 plane: form the source, 2D transform along x1 and x2 in shared memory
+//   B  per line along x3: transform, scale by f (and sum f |Y|^2 for the energy
+//      by Parseval), inverse transform
+//   C  per x3 plane: inverse 2D transform, real part / N.
+// Each line transform is a mixed-radix (4, 2, 3, 5) Stockham FFT run by one
+// thread over a column of shared memory.
+#include "kx_internal.h"
+
+#include <cmath>
+#include <vector>
+
+namespace kx {
+namespace {
+
+constexpr int kFftMaxR = 5;
+constexpr int kFftLine = 64;  // lines per CTA in pass B
+
+struct FftAxis {
+    int n, nr;
+    int radix[8];
+};
+
+struct FftGeom {
+    FftAxis ax[3];
+    int n1, n2, n3;
+    long long N, n12;
+    const float2 *tw;  // per axis 128 entries: exp(-2 pi i t / n_a), t < n_a
+};
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// Stockham FFT of one line (element stride st in a, scratch b with the same
+// layout); the inverse uses conjugate twiddles and is unnormalised.  Returns
+// the buffer that holds the result (a or b, by the number of stages).
+__device__ float2 *fft_line(float2 *a, float2 *b, int st, const FftAxis &ax, const float2 *W, bool inv) {
+    const int n = ax.n;
+    const float sg = inv ? -1.f : 1.f;
+    int Ns = 1;
+    for (int s = 0; s < ax.nr; ++s) {
+        const int R = ax.radix[s], nR = n / R, tstep = n / (Ns * R);
+        for (int j = 0; j < nR; ++j) {
+            const int jj = j % Ns;
+            float2 v[kFftMaxR];
+            for (int r = 0; r < R; ++r) {
+                float2 w = W[(jj * r * tstep) % n];
+                w.y *= sg;
+                v[r] = cmul(a[(j + r * nR) * st], w);
+            }
+            const int base = (j / Ns) * Ns * R + jj;
+            for (int p = 0; p < R; ++p) {
+                float2 u = v[0];
+                for (int q = 1; q < R; ++q) {
+                    float2 w = W[((p * q) % R) * nR];
+                    w.y *= sg;
+                    const float2 t = cmul(v[q], w);
+                    u.x += t.x;
+                    u.y += t.y;
+                }
+                b[(base + p * Ns) * st] = u;
+            }
+        }
+        float2 *t = a;
+        a = b;
+        b = t;
+        Ns *= R;
+    }
+    return a;
+}
+
+// Pass A: x3 plane blockIdx.x of item blockIdx.y; source psi_i psi_j (pairs) or in32.
+__global__ void __launch_bounds__(128) fft_plane_fwd_kernel(const FftGeom G, const int2 *__restrict__ pairs,
+                                                            const float *__restrict__ src32, int rhs,
+                                                            float2 *__restrict__ C) {
+    extern __shared__ float2 fsm[];
+    const int ld = G.n1 + 1;  // padded rows
+    float2 *A = fsm, *B = fsm + (size_t)G.n2 * ld;
+    const int x3 = blockIdx.x;
+    const long long item = blockIdx.y;
+    const float *p0, *p1 = nullptr;
+    if (rhs) {
+        p0 = src32 + item * G.N + x3 * G.n12;
+    } else {
+        const int2 ij = pairs[item];
+        p0 = src32 + (long long)ij.x * G.N + x3 * G.n12;
+        p1 = src32 + (long long)ij.y * G.N + x3 * G.n12;
+    }
+    for (int e = threadIdx.x; e < G.n12; e += blockDim.x) {
+        const int x1 = e % G.n1, x2 = e / G.n1;
+        A[x2 * ld + x1] = make_float2(p1 ? p0[e] * p1[e] : p0[e], 0.f);
+    }
+    __syncthreads();
+    for (int row = threadIdx.x; row < G.n2; row += blockDim.x)
+        fft_line(A + row * ld, B + row * ld, 1, G.ax[0], G.tw, false);
+    __syncthreads();
+    float2 *R1 = (G.ax[0].nr & 1) ? B : A, *O1 = (R1 == A) ? B : A;
+    for (int col = threadIdx.x; col < G.n1; col += blockDim.x)
+        fft_line(R1 + col, O1 + col, ld, G.ax[1], G.tw + 128, false);
+    __syncthreads();
+    const float2 *R2 = (G.ax[1].nr & 1) ? O1 : R1;
+    float2 *dst = C + item * G.N + x3 * G.n12;
+    for (int e = threadIdx.x; e < G.n12; e += blockDim.x) dst[e] = R2[(e / G.n1) * ld + e % G.n1];
+}
+
+// Pass B: kFftLine lines along x3 (plane positions blockIdx.x * kFftLine + t) of
+// item blockIdx.y: transform, f scaling, energy sum, inverse transform.
+__global__ void __launch_bounds__(kFftLine) fft_axis3_kernel(const FftGeom G, float2 *__restrict__ C,
+                                                             const float *__restrict__ ftab,
+                                                             const int2 *__restrict__ pairs,
+                                                             const double *__restrict__ occ, int rhs,
+                                                             int energy_only, double *__restrict__ e_part) {
+    extern __shared__ float2 fsm[];
+    __shared__ double red[kFftLine / 32];
+    float2 *A = fsm, *B = fsm + (size_t)G.n3 * kFftLine;
+    const int t = threadIdx.x;
+    const long long item = blockIdx.y;
+    const long long p = (long long)blockIdx.x * kFftLine + t;
+    const bool valid = p < G.n12;
+    float2 *line = C + item * G.N + p;
+    for (int x3 = 0; x3 < G.n3; ++x3) A[x3 * kFftLine + t] = valid ? line[x3 * G.n12] : make_float2(0.f, 0.f);
+    float2 *Rr = fft_line(A + t, B + t, kFftLine, G.ax[2], G.tw + 256, false);
+    float2 *Or = (Rr == A + t) ? B + t : A + t;
+    double e = 0.0;
+    for (int k3 = 0; k3 < G.n3; ++k3) {
+        const float f = valid ? __ldg(ftab + k3 * G.n12 + p) : 0.f;
+        const float2 y = Rr[k3 * kFftLine];
+        e += (double)(f * (y.x * y.x + y.y * y.y));
+        Rr[k3 * kFftLine] = make_float2(y.x * f, y.y * f);
+    }
+    if (!energy_only) {
+        const float2 *R2 = fft_line(Rr, Or, kFftLine, G.ax[2], G.tw + 256, true);
+        if (valid)
+            for (int x3 = 0; x3 < G.n3; ++x3) line[x3 * G.n12] = R2[x3 * kFftLine];
+    }
+    if (e_part != nullptr) {
+        double w = 0.0;
+        if (!rhs) {
+            const int2 ij = pairs[item];
+            w = (ij.x == ij.y) ? 1.0 : 2.0;
+            if (occ) w *= occ[ij.x] * occ[ij.y];
+        }
+        e *= w;
+        for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+        if ((t & 31) == 0) red[t >> 5] = e;
+        __syncthreads();
+        if (t == 0) {
+            double sum = 0.0;
+            for (int k = 0; k < kFftLine / 32; ++k) sum += red[k];
+            e_part[item * gridDim.x + blockIdx.x] = sum;
+        }
+    }
+}
+
+// Pass C: inverse 2D transform of x3 plane blockIdx.x of item blockIdx.y; real part / N
+// into out32 (fp32) or out64 (fp64, right-hand-side mode).
+__global__ void __launch_bounds__(128) fft_plane_inv_kernel(const FftGeom G, const float2 *__restrict__ C,
+                                                            float *__restrict__ out32, double *__restrict__ out64) {
+    extern __shared__ float2 fsm[];
+    const int ld = G.n1 + 1;
+    float2 *A = fsm, *B = fsm + (size_t)G.n2 * ld;
+    const int x3 = blockIdx.x;
+    const long long item = blockIdx.y;
+    const float2 *src = C + item * G.N + x3 * G.n12;
+    for (int e = threadIdx.x; e < G.n12; e += blockDim.x) A[(e / G.n1) * ld + e % G.n1] = src[e];
+    __syncthreads();
+    for (int col = threadIdx.x; col < G.n1; col += blockDim.x)
+        fft_line(A + col, B + col, ld, G.ax[1], G.tw + 128, true);
+    __syncthreads();
+    float2 *R1 = (G.ax[1].nr & 1) ? B : A, *O1 = (R1 == A) ? B : A;
+    for (int row = threadIdx.x; row < G.n2; row += blockDim.x)
+        fft_line(R1 + row * ld, O1 + row * ld, 1, G.ax[0], G.tw, true);
+    __syncthreads();
+    const float2 *R2 = (G.ax[0].nr & 1) ? O1 : R1;
+    const float inv_n = 1.f / (float)G.N;
+    const long long base = item * G.N + x3 * G.n12;
+    for (int e = threadIdx.x; e < G.n12; e += blockDim.x) {
+        const float v = R2[(e / G.n1) * ld + e % G.n1].x * inv_n;
+        if (out64)
+            out64[base + e] = (double)v;
+        else
+            out32[base + e] = v;
+    }
+}
+
+// ex += factor sum part[0..count): fixed strided partial sums and a fixed tree.
+__global__ void __launch_bounds__(1024) fft_energy_reduce_kernel(const double *__restrict__ part, long long count,
+                                                                 double factor, double *__restrict__ ex) {
+    __shared__ double red[1024];
+    double s = 0.0;
+    for (long long i = threadIdx.x; i < count; i += 1024) s += part[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int st = 512; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *ex += factor * red[0];
+}
+
+bool factor_235(int n, FftAxis &ax) {
+    ax.n = n;
+    ax.nr = 0;
+    int m = n;
+    while (m % 4 == 0) {
+        ax.radix[ax.nr++] = 4;
+        m /= 4;
+    }
+    for (int r : {2, 3, 5})
+        while (m % r == 0) {
+            if (ax.nr == 8) return false;
+            ax.radix[ax.nr++] = r;
+            m /= r;
+        }
+    return m == 1;
+}
+
+FftGeom geom(const kx_plan *p) {
+    FftGeom G{};
+    for (int a = 0; a < 3; ++a) factor_235(p->n[a], G.ax[a]);
+    G.n1 = p->n[0];
+    G.n2 = p->n[1];
+    G.n3 = p->n[2];
+    G.N = (long long)p->N;
+    G.n12 = (long long)p->n[0] * p->n[1];
+    G.tw = reinterpret_cast<const float2 *>(p->d_fft_tw);
+    return G;
+}
+
+size_t plane_smem(const kx_plan *p) { return sizeof(float2) * 2 * (size_t)p->n[1] * (p->n[0] + 1); }
+size_t line_smem(const kx_plan *p) { return sizeof(float2) * 2 * (size_t)p->n[2] * kFftLine; }
+
+}  // namespace
+
+bool fft_supported(const int *n, const int *bc) {
+    FftAxis ax;
+    for (int a = 0; a < 3; ++a)
+        if (bc[a] != KX_PERIODIC || !factor_235(n[a], ax)) return false;
+    return sizeof(float2) * 2 * (size_t)n[1] * (n[0] + 1) <= 200 * 1024;
+}
+
+int fft_setup(kx_plan *p) {
+    // twiddles exp(-2 pi i t / n_a) and the f table in DFT order, from float64 host arithmetic
+    std::vector<float> tw(3 * 128 * 2, 0.f);
+    for (int a = 0; a < 3; ++a)
+        for (int t = 0; t < p->n[a]; ++t) {
+            const double ang = 2.0 * M_PI * t / p->n[a];
+            tw[(a * 128 + t) * 2] = (float)std::cos(ang);
+            tw[(a * 128 + t) * 2 + 1] = (float)-std::sin(ang);
+        }
+    const int m = p->fd_order / 2;
+    std::vector<double> w(m + 1, 0.0);
+    double fm = 1.0;
+    for (int i = 2; i <= m; ++i) fm *= i;
+    for (int q = 1; q <= m; ++q) {
+        double fmq = 1.0, fpq = 1.0;
+        for (int i = 2; i <= m - q; ++i) fmq *= i;
+        for (int i = 2; i <= m + q; ++i) fpq *= i;
+        w[q] = 2.0 * ((q % 2) ? 1.0 : -1.0) * fm * fm / (double(q) * q * fmq * fpq);
+        w[0] -= 2.0 / (double(q) * q);
+    }
+    std::vector<double> lam[3];
+    for (int a = 0; a < 3; ++a) {
+        lam[a].resize(p->n[a]);
+        for (int k = 0; k < p->n[a]; ++k) {
+            double s = w[0];
+            for (int q = 1; q <= m; ++q) s += 2.0 * w[q] * std::cos(2.0 * M_PI * q * k / p->n[a]);
+            lam[a][k] = s / (p->h[a] * p->h[a]);
+        }
+    }
+    std::vector<float> f(p->N);
+    const double om2 = p->omega * p->omega;
+    for (int k3 = 0; k3 < p->n[2]; ++k3)
+        for (int k2 = 0; k2 < p->n[1]; ++k2)
+            for (int k1 = 0; k1 < p->n[0]; ++k1) {
+                const double mu = -(lam[0][k1] + lam[1][k2] + lam[2][k3]);
+                double v;
+                if (p->kind == KX_SCREENED)
+                    v = (mu > 0.0) ? -4.0 * M_PI * std::expm1(-mu / (4.0 * om2)) / mu : M_PI / om2;
+                else
+                    v = 4.0 * M_PI / mu;
+                f[((size_t)k3 * p->n[1] + k2) * p->n[0] + k1] = (float)v;
+            }
+    KX_CUDA_TRY(cudaMalloc(&p->d_fft_tw, sizeof(float) * tw.size()));
+    KX_CUDA_TRY(cudaMalloc(&p->d_fft_f, sizeof(float) * p->N));
+    KX_CUDA_TRY(cudaMemcpy(p->d_fft_tw, tw.data(), sizeof(float) * tw.size(), cudaMemcpyHostToDevice));
+    KX_CUDA_TRY(cudaMemcpy(p->d_fft_f, f.data(), sizeof(float) * p->N, cudaMemcpyHostToDevice));
+    return KX_OK;
+}
+
+size_t fft_partial_count(const kx_plan *p, long chunk) {
+    const long long groups = ((long long)p->n[0] * p->n[1] + kFftLine - 1) / kFftLine;
+    return (size_t)std::max<long long>(4096, groups * chunk);
+}
+
+int fft_passes(kx_plan *p, long R, const int2 *pairs, const float *src32, int rhs, const double *occ, float2 *C,
+               float *out32, double *out64, double *ex, double *partial, bool energy_only, cudaStream_t s) {
+    const FftGeom G = geom(p);
+    const size_t ps = plane_smem(p), ls = line_smem(p);
+    KX_CUDA_TRY(cudaFuncSetAttribute(fft_plane_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps));
+    KX_CUDA_TRY(cudaFuncSetAttribute(fft_plane_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps));
+    KX_CUDA_TRY(cudaFuncSetAttribute(fft_axis3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ls));
+    int rc;
+    const dim3 gp((unsigned)p->n[2], (unsigned)R);
+    if ((rc = prof_begin(p, PK_FFT, s))) return rc;
+    fft_plane_fwd_kernel<<<gp, 128, ps, s>>>(G, pairs, src32, rhs, C);
+    KX_LAUNCH_CHECK("fft_plane_fwd_kernel launch");
+    const unsigned groups = (unsigned)((G.n12 + kFftLine - 1) / kFftLine);
+    double *e_part = (ex != nullptr && !rhs) ? partial : nullptr;
+    fft_axis3_kernel<<<dim3(groups, (unsigned)R), kFftLine, ls, s>>>(G, C, p->d_fft_f, pairs, occ, rhs,
+                                                                    energy_only ? 1 : 0, e_part);
+    KX_LAUNCH_CHECK("fft_axis3_kernel launch");
+    if (e_part) {
+        fft_energy_reduce_kernel<<<1, 1024, 0, s>>>(partial, (long long)groups * R, -0.5 * p->dV / (double)G.N, ex);
+        KX_LAUNCH_CHECK("fft_energy_reduce_kernel launch");
+    }
+    if (!energy_only) {
+        fft_plane_inv_kernel<<<gp, 128, ps, s>>>(G, C, out32, out64);
+        KX_LAUNCH_CHECK("fft_plane_inv_kernel launch");
+    }
+    return prof_end(p, s);
+}
+
+}  // namespace kx

@@ -54,7 +54,7 @@ struct TuneParams {
 
 // Per-launch CUDA-event timing by kernel kind (kx_profile / kx_profile_read).
 enum ProfKind { PK_PREP = 0, PK_X3F, PK_X2F, PK_X1, PK_X2I, PK_X3I, PK_FINAL, PK_FP64_MODE, PK_FP64_OTHER,
-                PK_ACE, PK_SETUP, PK_ACC, PK_SLAB, PK_ACE_COMB, PK_MP, PK_COUNT };
+                PK_ACE, PK_SETUP, PK_ACC, PK_SLAB, PK_ACE_COMB, PK_MP, PK_FFT, PK_COUNT };
 struct Profiler {
     bool on = false;
     std::vector<cudaEvent_t> pool;       // reusable events
@@ -104,6 +104,9 @@ struct kx_plan_s {
     // tensor-core operands (device): per axis, hi and lo fp16 blocks of the
     // np x np zero-padded, 2^14-scaled V in 8x8 core-matrix order
     __half *d_Vs[3] = {nullptr, nullptr, nullptr};    // [2][np*np]: hi block then lo block
+    // KX_FFT32 plans: twiddles exp(-2 pi i t / n_a) (3 x 128 complex) and f in DFT order (N)
+    float *d_fft_tw = nullptr;
+    float *d_fft_f = nullptr;
 
     int *d_status = nullptr;                          // bounded-wait status word
 
@@ -175,6 +178,15 @@ int ace_run(kx_plan *p, int n_orb, const double *psi, const double *W, double *x
             cudaStream_t s);
 int ace_apply_run(kx_plan *p, int n_xi, const double *xi, int n_vec, const double *phi, double *out,
                   cudaStream_t s);
+// ---- fully periodic grids through the DFT (kx_fft.cu)
+bool fft_supported(const int *n, const int *bc);
+int fft_setup(kx_plan *p);
+size_t fft_partial_count(const kx_plan *p, long chunk);
+// f(L) of R items: sources psi_i psi_j (pairs) or src32 (rhs), complex scratch C
+// (R x N), output real part into out32 (fp32) or out64; energy into ex
+int fft_passes(kx_plan *p, long R, const int2 *pairs, const float *src32, int rhs, const double *occ, float2 *C,
+               float *out32, double *out64, double *ex, double *partial, bool energy_only, cudaStream_t s);
+
 // ---- multipole boundary values (kx_mp.cu)
 int mp_set(kx_plan *p, int l_max);
 void mp_free(kx_plan *p);

@@ -282,6 +282,8 @@ int plan_setup(kx_plan *p) {
             KX_LAUNCH_CHECK("split_v_kernel launch");
         }
     }
+    if (p->precision == KX_FFT32)
+        if (int rc = fft_setup(p)) return rc;
     double *d_fmax = nullptr;
     KX_CUDA_TRY(cudaMalloc(&d_fmax, sizeof(double)));
     fmax_kernel<<<1, 256>>>(p->d_f64, p->N, d_fmax);
@@ -301,6 +303,8 @@ void plan_free(kx_plan *p) {
     }
     cudaFree(p->d_f64);
     cudaFree(p->d_f32);
+    cudaFree(p->d_fft_tw);
+    cudaFree(p->d_fft_f);
     cudaFree(p->d_status);
     cudaFree(p->ws.ptr);
     cudaFree(p->ws_host.ptr);

@@ -1525,11 +1525,12 @@ TcLayout carve(kx_plan *p, int n_vec, long chunk, bool with_acc) {
     auto take = [&](size_t bytes) { uint8_t *r = b + off; off += align256(bytes); return r; };
     L.psi32 = (float *)take(sizeof(float) * (size_t)n_vec * p->N);
     L.acc = with_acc ? (float *)take(sizeof(float) * (size_t)n_vec * p->N) : nullptr;
+    const bool fft = p->precision == KX_FFT32;  // T1 holds complex values, more energy partials
     L.T0 = (float *)take(sizeof(float) * (size_t)chunk * p->N);
-    L.T1 = (float *)take(sizeof(float) * (size_t)chunk * p->N);
+    L.T1 = (float *)take(sizeof(float) * (fft ? 2 : 1) * (size_t)chunk * p->N);
     L.orb_max = (float *)take(sizeof(float) * (size_t)n_vec);
     L.mx = (float *)take(sizeof(float) * 4 * (size_t)chunk);
-    L.partial = (double *)take(sizeof(double) * 4096);
+    L.partial = (double *)take(sizeof(double) * (fft ? fft_partial_count(p, chunk) : 4096));
     return L;
 }
 
@@ -1636,8 +1637,10 @@ long tc_default_chunk(const kx_plan *p, int n_orb) {
 }
 
 size_t tc_workspace_bytes(const kx_plan *p, int n_vec, long chunk) {
-    return align256(sizeof(float) * (size_t)n_vec * p->N) * 2 + align256(sizeof(float) * (size_t)chunk * p->N) * 2 +
-           align256(sizeof(float) * n_vec) + align256(sizeof(float) * 4 * chunk) + align256(sizeof(double) * 4096) +
+    const bool fft = p->precision == KX_FFT32;
+    return align256(sizeof(float) * (size_t)n_vec * p->N) * 2 + align256(sizeof(float) * (size_t)chunk * p->N) +
+           align256(sizeof(float) * (fft ? 2 : 1) * (size_t)chunk * p->N) + align256(sizeof(float) * n_vec) +
+           align256(sizeof(float) * 4 * chunk) + align256(sizeof(double) * (fft ? fft_partial_count(p, chunk) : 4096)) +
            4096;
 }
 
@@ -1709,7 +1712,12 @@ int tc_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, double *v
         a.occ = occ;
         a.f32 = p->d_f32;
         a.mid_bound = mid_bound;
-        if ((rc = run_passes(p, a, R, L.T0, L.T1, L.mx, chunk, ex, L.partial, energy_only, nullptr, s))) return rc;
+        if (p->precision == KX_FFT32)
+            rc = fft_passes(p, R, pairs + c0, L.psi32, 0, occ, reinterpret_cast<float2 *>(L.T1), L.T0, nullptr, ex,
+                            L.partial, energy_only, s);
+        else
+            rc = run_passes(p, a, R, L.T0, L.T1, L.mx, chunk, ex, L.partial, energy_only, nullptr, s);
+        if (rc) return rc;
         if (!energy_only) {
             const unsigned blocks = (unsigned)((N / 4 + kAccThreads - 1) / kAccThreads);
             if ((rc = prof_begin(p, PK_ACC, s))) return rc;
@@ -1760,7 +1768,12 @@ int tc_apply_fL(kx_plan *p, int n_rhs, const double *b, double *x, cudaStream_t 
         a.mid_bound = mid_bound;
         a.src_max = L.orb_max;
         a.in = L.psi32;
-        if ((rc = run_passes(p, a, R, L.T0, L.T1, L.mx, chunk, nullptr, nullptr, false, x + c0 * N, s))) return rc;
+        if (p->precision == KX_FFT32)
+            rc = fft_passes(p, R, nullptr, L.psi32, 1, nullptr, reinterpret_cast<float2 *>(L.T1), nullptr, x + c0 * N,
+                            nullptr, nullptr, false, s);
+        else
+            rc = run_passes(p, a, R, L.T0, L.T1, L.mx, chunk, nullptr, nullptr, false, x + c0 * N, s);
+        if (rc) return rc;
     }
     return KX_OK;
 }

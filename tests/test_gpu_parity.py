@@ -328,6 +328,70 @@ def test_multipole_full_size_row(kx):
     assert np.max(np.abs(vx_h[i] - ref[:, i])) < 1e-5 * np.abs(vx_h).max()
 
 
+# --------------------------------------------------------------------------
+# FFT variant for fully periodic grids (KX_FFT32)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [(20, 24, 30), (16, 15, 18), (9, 10, 12)])
+def test_fft_apply_fL_matches_oracle(kx, n):
+    h, bc = (0.45, 0.5, 0.4), (P, P, P)
+    op = oracle.Plan(n, h, bc, S)
+    b = workloads.random_field(op.N, 3, 83)
+    ref = np.stack([oracle.apply_fL(op, b[:, r]) for r in range(3)], axis=1)
+    plan = kx.Plan(n, h, bc, S, precision=kx.KX_FFT32)
+    x = kx.kx_apply_fL(plan, dev(b.T)).cpu().numpy().T
+    assert relmax(x, ref) < TOL[1]["fl"]
+
+
+def test_fft_vx_and_energy_match_oracle(kx):
+    n, h, bc = (24, 20, 18), (0.45, 0.5, 0.4), (P, P, P)
+    sysd = system(n, h, bc, S, 5, 89)
+    psi = workloads.make_orbitals(sysd)
+    occ = np.array([1.0, 0.8, 0.6, 0.4, 0.2])
+    op = oracle.Plan(n, h, bc, S)
+    vx_ref, ex_ref = oracle.vx_apply(op, psi, occ)
+    plan = kx.Plan(n, h, bc, S, precision=kx.KX_FFT32)
+    psi_d, occ_d = dev(psi.T), dev(occ)
+    vx, ex = kx.kx_vx_apply(plan, psi_d, occ_d)
+    e_only = kx.kx_energy(plan, psi_d, occ_d)[0].item()
+    assert relmax(vx.cpu().numpy().T, vx_ref) < TOL[1]["vx"]
+    assert abs(ex.item() - ex_ref) < TOL[1]["ex"] * abs(ex_ref)
+    assert abs(e_only - ex_ref) < TOL[1]["ex"] * abs(ex_ref)
+
+
+def test_fft_rejects_unsupported_grids(kx):
+    with pytest.raises(kx.KxError) as ei:
+        kx.Plan((16, 16, 16), (0.5,) * 3, (P, P, D), S, precision=kx.KX_FFT32)
+    assert ei.value.code == kx.KX_ERR_UNSUPPORTED
+    with pytest.raises(kx.KxError) as ei:
+        kx.Plan((14, 16, 16), (0.5,) * 3, (P, P, P), S, precision=kx.KX_FFT32)  # 14 = 2 x 7
+    assert ei.value.code == kx.KX_ERR_UNSUPPORTED
+    plan = kx.Plan((16, 16, 16), (0.5,) * 3, (P, P, P), S, precision=kx.KX_FFT32)
+    b = dev(workloads.random_field(plan.N, 1, 3).T)
+    with pytest.raises(kx.KxError) as ei:
+        kx.kx_apply_fL_noalloc(plan, b, torch.empty_like(b))
+    assert ei.value.code == kx.KX_ERR_UNSUPPORTED
+
+
+def test_fft_full_size_against_kronecker_and_oracle(kx):
+    """The 80^3 periodic screened 256-orbital system: the FFT plan's first 12
+    pairs against the oracle, and its full apply against the tensor-core
+    Kronecker plan on the same orbitals (both are f(L) on the same grid)."""
+    sysd = workloads.C3
+    psi = workloads.make_orbitals(sysd)
+    op = oracle.Plan(sysd.n, sysd.h, sysd.bc, sysd.kernel, sysd.omega)
+    plan = kx.Plan.for_system(sysd, precision=kx.KX_FFT32)
+    psi_d = dev(psi.T)
+    part, e_part = kx.kx_vx_apply_pairs(plan, psi_d, 0, 12)
+    from paper_2406_16998_gb300 import shard
+    ref, e_ref = oracle.vx_apply(op, psi, pairs=shard.pair_list(psi.shape[1])[:12])
+    assert relmax(part.cpu().numpy().T, ref) < 1e-5
+    assert abs(e_part.item() - e_ref) < 1e-6 * abs(e_ref)
+    vx_f, ex_f = kx.kx_vx_apply(plan, psi_d)
+    vx_k, ex_k = kx.kx_vx_apply(kx.Plan.for_system(sysd, precision=1), psi_d)
+    assert relmax(vx_f.cpu().numpy(), vx_k.cpu().numpy()) < 2e-5
+    assert abs(ex_f.item() - ex_k.item()) < 2e-6 * abs(ex_k.item())
+
+
 def test_ace_f16x3_plan_matches_oracle(kx):
     """The tensor-core plan's ACE tail: float32 products, float64 block sums and
     float64 Cholesky; M to 1e-6 and xi to 1e-5 of their largest entries."""

@@ -9,8 +9,8 @@
 //   B  per line along x3: transform, scale by f (and sum f |Y|^2 for the energy
 //      by Parseval), inverse transform
 //   C  per x3 plane: inverse 2D transform, real part / N.
-// Each line transform is a mixed-radix (4, 2, 3, 5) Stockham FFT run by one
-// thread over a column of shared memory.
+// Each batch of line transforms is a mixed-radix (4, 2, 3, 5) Stockham FFT whose
+// stages are spread over the CTA's threads (lines x butterflies).
 #include "kx_internal.h"
 
 #include <cmath>
@@ -19,7 +19,6 @@
 namespace kx {
 namespace {
 
-constexpr int kFftMaxR = 5;
 constexpr int kFftLine = 64;  // lines per CTA in pass B
 
 struct FftAxis {
@@ -38,36 +37,71 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// Stockham FFT of one line (element stride st in a, scratch b with the same
-// layout); the inverse uses conjugate twiddles and is unnormalised.  Returns
-// the buffer that holds the result (a or b, by the number of stages).
-__device__ float2 *fft_line(float2 *a, float2 *b, int st, const FftAxis &ax, const float2 *W, bool inv) {
-    const int n = ax.n;
+// One Stockham stage of radix R over nl lines at once, spread over the CTA:
+// line l's element k sits at a[l * lstride + k * st] (scratch b, same
+// layout).  lines_fast picks the task order: consecutive threads take
+// consecutive lines (element stride st > 1: neighbouring lines are adjacent)
+// or consecutive butterflies of one line (st == 1).
+template <int R>
+__device__ __forceinline__ void fft_stage(const float2 *a, float2 *b, int n, int Ns, int nl, int lstride, int st,
+                                          bool lines_fast, const float2 *W, float sg) {
+    const int nR = n / R, tstep = n / (Ns * R);
+    for (int task = threadIdx.x; task < nl * nR; task += blockDim.x) {
+        int l, j;
+        if (lines_fast) {
+            j = task / nl;
+            l = task - j * nl;
+        } else {
+            l = task / nR;
+            j = task - l * nR;
+        }
+        const float2 *al = a + l * lstride;
+        float2 *bl = b + l * lstride;
+        const int jj = j % Ns;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            float2 w = W[(jj * r * tstep) % n];
+            w.y *= sg;
+            v[r] = cmul(al[(j + r * nR) * st], w);
+        }
+        const int base = (j / Ns) * Ns * R + jj;
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            float2 u = v[0];
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                float2 w = W[((q * r) % R) * nR];
+                w.y *= sg;
+                const float2 t = cmul(v[r], w);
+                u.x += t.x;
+                u.y += t.y;
+            }
+            bl[(base + q * Ns) * st] = u;
+        }
+    }
+}
+
+// Stockham FFT of nl lines (see fft_stage for the layout) by the whole CTA;
+// the inverse uses conjugate twiddles and is unnormalised.  Returns the buffer
+// that holds the result (a or b, by the number of stages).  Every thread of
+// the CTA must call it; it ends with a barrier.
+__device__ float2 *fft_lines(float2 *a, float2 *b, const FftAxis &ax, int nl, int lstride, int st, const float2 *W,
+                             bool inv) {
     const float sg = inv ? -1.f : 1.f;
+    const bool lines_fast = st != 1;
     int Ns = 1;
     for (int s = 0; s < ax.nr; ++s) {
-        const int R = ax.radix[s], nR = n / R, tstep = n / (Ns * R);
-        for (int j = 0; j < nR; ++j) {
-            const int jj = j % Ns;
-            float2 v[kFftMaxR];
-            for (int r = 0; r < R; ++r) {
-                float2 w = W[(jj * r * tstep) % n];
-                w.y *= sg;
-                v[r] = cmul(a[(j + r * nR) * st], w);
-            }
-            const int base = (j / Ns) * Ns * R + jj;
-            for (int p = 0; p < R; ++p) {
-                float2 u = v[0];
-                for (int q = 1; q < R; ++q) {
-                    float2 w = W[((p * q) % R) * nR];
-                    w.y *= sg;
-                    const float2 t = cmul(v[q], w);
-                    u.x += t.x;
-                    u.y += t.y;
-                }
-                b[(base + p * Ns) * st] = u;
-            }
-        }
+        const int R = ax.radix[s];
+        if (R == 4)
+            fft_stage<4>(a, b, ax.n, Ns, nl, lstride, st, lines_fast, W, sg);
+        else if (R == 2)
+            fft_stage<2>(a, b, ax.n, Ns, nl, lstride, st, lines_fast, W, sg);
+        else if (R == 3)
+            fft_stage<3>(a, b, ax.n, Ns, nl, lstride, st, lines_fast, W, sg);
+        else
+            fft_stage<5>(a, b, ax.n, Ns, nl, lstride, st, lines_fast, W, sg);
+        __syncthreads();
         float2 *t = a;
         a = b;
         b = t;
@@ -76,11 +110,16 @@ __device__ float2 *fft_line(float2 *a, float2 *b, int st, const FftAxis &ax, con
     return a;
 }
 
-// Pass A: x3 plane blockIdx.x of item blockIdx.y; source psi_i psi_j (pairs) or in32.
-__global__ void __launch_bounds__(128) fft_plane_fwd_kernel(const FftGeom G, const int2 *__restrict__ pairs,
+__device__ __forceinline__ void load_twiddles(const float2 *__restrict__ tw, float2 *Ws) {
+    for (int i = threadIdx.x; i < 3 * 128; i += blockDim.x) Ws[i] = tw[i];
+}
+
+// Pass A: x3 plane blockIdx.x of item blockIdx.y; source psi_i psi_j (pairs) or src32.
+__global__ void __launch_bounds__(256) fft_plane_fwd_kernel(const FftGeom G, const int2 *__restrict__ pairs,
                                                             const float *__restrict__ src32, int rhs,
                                                             float2 *__restrict__ C) {
     extern __shared__ float2 fsm[];
+    __shared__ float2 Ws[3 * 128];
     const int ld = G.n1 + 1;  // padded rows
     float2 *A = fsm, *B = fsm + (size_t)G.n2 * ld;
     const int x3 = blockIdx.x;
@@ -93,52 +132,58 @@ __global__ void __launch_bounds__(128) fft_plane_fwd_kernel(const FftGeom G, con
         p0 = src32 + (long long)ij.x * G.N + x3 * G.n12;
         p1 = src32 + (long long)ij.y * G.N + x3 * G.n12;
     }
+    load_twiddles(G.tw, Ws);
     for (int e = threadIdx.x; e < G.n12; e += blockDim.x) {
         const int x1 = e % G.n1, x2 = e / G.n1;
-        A[x2 * ld + x1] = make_float2(p1 ? p0[e] * p1[e] : p0[e], 0.f);
+        A[x2 * ld + x1] = make_float2(p1 ? __ldg(p0 + e) * __ldg(p1 + e) : __ldg(p0 + e), 0.f);
     }
     __syncthreads();
-    for (int row = threadIdx.x; row < G.n2; row += blockDim.x)
-        fft_line(A + row * ld, B + row * ld, 1, G.ax[0], G.tw, false);
-    __syncthreads();
-    float2 *R1 = (G.ax[0].nr & 1) ? B : A, *O1 = (R1 == A) ? B : A;
-    for (int col = threadIdx.x; col < G.n1; col += blockDim.x)
-        fft_line(R1 + col, O1 + col, ld, G.ax[1], G.tw + 128, false);
-    __syncthreads();
-    const float2 *R2 = (G.ax[1].nr & 1) ? O1 : R1;
+    float2 *R1 = fft_lines(A, B, G.ax[0], G.n2, ld, 1, Ws, false);  // rows: along x1
+    float2 *O1 = (R1 == A) ? B : A;
+    const float2 *R2 = fft_lines(R1, O1, G.ax[1], G.n1, 1, ld, Ws + 128, false);  // columns: along x2
     float2 *dst = C + item * G.N + x3 * G.n12;
     for (int e = threadIdx.x; e < G.n12; e += blockDim.x) dst[e] = R2[(e / G.n1) * ld + e % G.n1];
 }
 
-// Pass B: kFftLine lines along x3 (plane positions blockIdx.x * kFftLine + t) of
+// Pass B: kFftLine lines along x3 (plane positions blockIdx.x * kFftLine + l) of
 // item blockIdx.y: transform, f scaling, energy sum, inverse transform.
-__global__ void __launch_bounds__(kFftLine) fft_axis3_kernel(const FftGeom G, float2 *__restrict__ C,
-                                                             const float *__restrict__ ftab,
-                                                             const int2 *__restrict__ pairs,
-                                                             const double *__restrict__ occ, int rhs,
-                                                             int energy_only, double *__restrict__ e_part) {
+__global__ void __launch_bounds__(256) fft_axis3_kernel(const FftGeom G, float2 *__restrict__ C,
+                                                        const float *__restrict__ ftab,
+                                                        const int2 *__restrict__ pairs,
+                                                        const double *__restrict__ occ, int rhs, int energy_only,
+                                                        double *__restrict__ e_part) {
     extern __shared__ float2 fsm[];
-    __shared__ double red[kFftLine / 32];
+    __shared__ float2 Ws[3 * 128];
+    __shared__ double red[8];
     float2 *A = fsm, *B = fsm + (size_t)G.n3 * kFftLine;
-    const int t = threadIdx.x;
+    const int tid = threadIdx.x;
     const long long item = blockIdx.y;
-    const long long p = (long long)blockIdx.x * kFftLine + t;
-    const bool valid = p < G.n12;
-    float2 *line = C + item * G.N + p;
-    for (int x3 = 0; x3 < G.n3; ++x3) A[x3 * kFftLine + t] = valid ? line[x3 * G.n12] : make_float2(0.f, 0.f);
-    float2 *Rr = fft_line(A + t, B + t, kFftLine, G.ax[2], G.tw + 256, false);
-    float2 *Or = (Rr == A + t) ? B + t : A + t;
-    double e = 0.0;
-    for (int k3 = 0; k3 < G.n3; ++k3) {
-        const float f = valid ? __ldg(ftab + k3 * G.n12 + p) : 0.f;
-        const float2 y = Rr[k3 * kFftLine];
-        e += (double)(f * (y.x * y.x + y.y * y.y));
-        Rr[k3 * kFftLine] = make_float2(y.x * f, y.y * f);
+    const long long p0 = (long long)blockIdx.x * kFftLine;
+    float2 *col = C + item * G.N + p0;
+    load_twiddles(G.tw, Ws);
+    for (int e = tid; e < G.n3 * kFftLine; e += blockDim.x) {  // e = x3 * kFftLine + l
+        const int x3 = e / kFftLine, l = e % kFftLine;
+        A[e] = (p0 + l < G.n12) ? col[x3 * G.n12 + l] : make_float2(0.f, 0.f);
     }
+    __syncthreads();
+    float2 *Rr = fft_lines(A, B, G.ax[2], kFftLine, 1, kFftLine, Ws + 256, false);
+    float2 *Or = (Rr == A) ? B : A;
+    float ef = 0.f;  // at most n3 * kFftLine / blockDim = 32 terms per thread
+    for (int k = tid; k < G.n3 * kFftLine; k += blockDim.x) {
+        const int k3 = k / kFftLine, l = k % kFftLine;
+        const float f = (p0 + l < G.n12) ? __ldg(ftab + k3 * G.n12 + p0 + l) : 0.f;
+        const float2 y = Rr[k];
+        ef = fmaf(f, y.x * y.x + y.y * y.y, ef);
+        Rr[k] = make_float2(y.x * f, y.y * f);
+    }
+    double e = (double)ef;
+    __syncthreads();
     if (!energy_only) {
-        const float2 *R2 = fft_line(Rr, Or, kFftLine, G.ax[2], G.tw + 256, true);
-        if (valid)
-            for (int x3 = 0; x3 < G.n3; ++x3) line[x3 * G.n12] = R2[x3 * kFftLine];
+        const float2 *R2 = fft_lines(Rr, Or, G.ax[2], kFftLine, 1, kFftLine, Ws + 256, true);
+        for (int k = tid; k < G.n3 * kFftLine; k += blockDim.x) {
+            const int x3 = k / kFftLine, l = k % kFftLine;
+            if (p0 + l < G.n12) col[x3 * G.n12 + l] = R2[k];
+        }
     }
     if (e_part != nullptr) {
         double w = 0.0;
@@ -149,11 +194,11 @@ __global__ void __launch_bounds__(kFftLine) fft_axis3_kernel(const FftGeom G, fl
         }
         e *= w;
         for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-        if ((t & 31) == 0) red[t >> 5] = e;
+        if ((tid & 31) == 0) red[tid >> 5] = e;
         __syncthreads();
-        if (t == 0) {
+        if (tid == 0) {
             double sum = 0.0;
-            for (int k = 0; k < kFftLine / 32; ++k) sum += red[k];
+            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) sum += red[k];
             e_part[item * gridDim.x + blockIdx.x] = sum;
         }
     }
@@ -161,24 +206,21 @@ __global__ void __launch_bounds__(kFftLine) fft_axis3_kernel(const FftGeom G, fl
 
 // Pass C: inverse 2D transform of x3 plane blockIdx.x of item blockIdx.y; real part / N
 // into out32 (fp32) or out64 (fp64, right-hand-side mode).
-__global__ void __launch_bounds__(128) fft_plane_inv_kernel(const FftGeom G, const float2 *__restrict__ C,
+__global__ void __launch_bounds__(256) fft_plane_inv_kernel(const FftGeom G, const float2 *__restrict__ C,
                                                             float *__restrict__ out32, double *__restrict__ out64) {
     extern __shared__ float2 fsm[];
+    __shared__ float2 Ws[3 * 128];
     const int ld = G.n1 + 1;
     float2 *A = fsm, *B = fsm + (size_t)G.n2 * ld;
     const int x3 = blockIdx.x;
     const long long item = blockIdx.y;
     const float2 *src = C + item * G.N + x3 * G.n12;
+    load_twiddles(G.tw, Ws);
     for (int e = threadIdx.x; e < G.n12; e += blockDim.x) A[(e / G.n1) * ld + e % G.n1] = src[e];
     __syncthreads();
-    for (int col = threadIdx.x; col < G.n1; col += blockDim.x)
-        fft_line(A + col, B + col, ld, G.ax[1], G.tw + 128, true);
-    __syncthreads();
-    float2 *R1 = (G.ax[1].nr & 1) ? B : A, *O1 = (R1 == A) ? B : A;
-    for (int row = threadIdx.x; row < G.n2; row += blockDim.x)
-        fft_line(R1 + row * ld, O1 + row * ld, 1, G.ax[0], G.tw, true);
-    __syncthreads();
-    const float2 *R2 = (G.ax[0].nr & 1) ? O1 : R1;
+    float2 *R1 = fft_lines(A, B, G.ax[1], G.n1, 1, ld, Ws + 128, true);  // columns: along x2
+    float2 *O1 = (R1 == A) ? B : A;
+    const float2 *R2 = fft_lines(R1, O1, G.ax[0], G.n2, ld, 1, Ws, true);  // rows: along x1
     const float inv_n = 1.f / (float)G.N;
     const long long base = item * G.N + x3 * G.n12;
     for (int e = threadIdx.x; e < G.n12; e += blockDim.x) {
@@ -310,11 +352,11 @@ int fft_passes(kx_plan *p, long R, const int2 *pairs, const float *src32, int rh
     int rc;
     const dim3 gp((unsigned)p->n[2], (unsigned)R);
     if ((rc = prof_begin(p, PK_FFT, s))) return rc;
-    fft_plane_fwd_kernel<<<gp, 128, ps, s>>>(G, pairs, src32, rhs, C);
+    fft_plane_fwd_kernel<<<gp, 256, ps, s>>>(G, pairs, src32, rhs, C);
     KX_LAUNCH_CHECK("fft_plane_fwd_kernel launch");
     const unsigned groups = (unsigned)((G.n12 + kFftLine - 1) / kFftLine);
     double *e_part = (ex != nullptr && !rhs) ? partial : nullptr;
-    fft_axis3_kernel<<<dim3(groups, (unsigned)R), kFftLine, ls, s>>>(G, C, p->d_fft_f, pairs, occ, rhs,
+    fft_axis3_kernel<<<dim3(groups, (unsigned)R), 256, ls, s>>>(G, C, p->d_fft_f, pairs, occ, rhs,
                                                                     energy_only ? 1 : 0, e_part);
     KX_LAUNCH_CHECK("fft_axis3_kernel launch");
     if (e_part) {
@@ -322,7 +364,7 @@ int fft_passes(kx_plan *p, long R, const int2 *pairs, const float *src32, int rh
         KX_LAUNCH_CHECK("fft_energy_reduce_kernel launch");
     }
     if (!energy_only) {
-        fft_plane_inv_kernel<<<gp, 128, ps, s>>>(G, C, out32, out64);
+        fft_plane_inv_kernel<<<gp, 256, ps, s>>>(G, C, out32, out64);
         KX_LAUNCH_CHECK("fft_plane_inv_kernel launch");
     }
     return prof_end(p, s);

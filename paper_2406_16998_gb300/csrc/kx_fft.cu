@@ -37,6 +37,50 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
+// x / d for x < 2^14 and 2 <= d <= 128 as a multiply-high by m = 2^32 / d + 1
+// (checked exhaustively over that range); d == 1 is passed as m == 0.
+__device__ __forceinline__ unsigned fast_div(unsigned x, unsigned m) { return m ? __umulhi(x, m) : x; }
+__device__ __forceinline__ unsigned div_magic(unsigned d) { return d > 1 ? 0xFFFFFFFFu / d + 1u : 0u; }
+
+// u = DFT_R(v) with W the twiddle table of the line (exp(-2 pi i t / n)),
+// nR = n / R; sg = -1 conjugates (inverse).  Radix 2 and 4 by additions and
+// multiplications by +-i, radix 3 and 5 from the table.
+template <int R>
+__device__ __forceinline__ void dft_small(float2 *v, const float2 *W, int nR, float sg) {
+    if (R == 2) {
+        const float2 a = v[0], b = v[1];
+        v[0] = make_float2(a.x + b.x, a.y + b.y);
+        v[1] = make_float2(a.x - b.x, a.y - b.y);
+    } else if (R == 4) {
+        // (-i sg) (x, y) = (sg y, -sg x)
+        const float2 a = make_float2(v[0].x + v[2].x, v[0].y + v[2].y);
+        const float2 b = make_float2(v[0].x - v[2].x, v[0].y - v[2].y);
+        const float2 c = make_float2(v[1].x + v[3].x, v[1].y + v[3].y);
+        const float2 t = make_float2(v[1].x - v[3].x, v[1].y - v[3].y);
+        const float2 d = make_float2(sg * t.y, -sg * t.x);
+        v[0] = make_float2(a.x + c.x, a.y + c.y);
+        v[2] = make_float2(a.x - c.x, a.y - c.y);
+        v[1] = make_float2(b.x + d.x, b.y + d.y);
+        v[3] = make_float2(b.x - d.x, b.y - d.y);
+    } else {
+        float2 u[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            u[q] = v[0];
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                float2 w = W[((q * r) % R) * nR];
+                w.y *= sg;
+                const float2 t = cmul(v[r], w);
+                u[q].x += t.x;
+                u[q].y += t.y;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q) v[q] = u[q];
+    }
+}
+
 // One Stockham stage of radix R over nl lines at once, spread over the CTA:
 // line l's element k sits at a[l * lstride + k * st] (scratch b, same
 // layout).  lines_fast picks the task order: consecutive threads take
@@ -46,39 +90,32 @@ template <int R>
 __device__ __forceinline__ void fft_stage(const float2 *a, float2 *b, int n, int Ns, int nl, int lstride, int st,
                                           bool lines_fast, const float2 *W, float sg) {
     const int nR = n / R, tstep = n / (Ns * R);
+    const unsigned m_fast = div_magic(lines_fast ? nl : nR), m_ns = div_magic(Ns);
     for (int task = threadIdx.x; task < nl * nR; task += blockDim.x) {
         int l, j;
         if (lines_fast) {
-            j = task / nl;
+            j = (int)fast_div(task, m_fast);
             l = task - j * nl;
         } else {
-            l = task / nR;
+            l = (int)fast_div(task, m_fast);
             j = task - l * nR;
         }
         const float2 *al = a + l * lstride;
         float2 *bl = b + l * lstride;
-        const int jj = j % Ns;
+        const int jq = (int)fast_div(j, m_ns), jj = j - jq * Ns;
         float2 v[R];
+        v[0] = al[j * st];
+        const int tw0 = jj * tstep;  // < n / R
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            float2 w = W[(jj * r * tstep) % n];
+        for (int r = 1; r < R; ++r) {
+            float2 w = W[tw0 * r];   // jj r tstep < n
             w.y *= sg;
             v[r] = cmul(al[(j + r * nR) * st], w);
         }
-        const int base = (j / Ns) * Ns * R + jj;
+        dft_small<R>(v, W, nR, sg);
+        const int base = jq * Ns * R + jj;
 #pragma unroll
-        for (int q = 0; q < R; ++q) {
-            float2 u = v[0];
-#pragma unroll
-            for (int r = 1; r < R; ++r) {
-                float2 w = W[((q * r) % R) * nR];
-                w.y *= sg;
-                const float2 t = cmul(v[r], w);
-                u.x += t.x;
-                u.y += t.y;
-            }
-            bl[(base + q * Ns) * st] = u;
-        }
+        for (int q = 0; q < R; ++q) bl[(base + q * Ns) * st] = v[q];
     }
 }
 

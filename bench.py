@@ -44,10 +44,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["kronx", "reference"], default="kronx")
     ap.add_argument("--no-extras", action="store_true", help="skip FP64/e2e/oracle legs (profiling runs)")
-    ap.add_argument("--profile-case", choices=["small", "ace", "multipole"], default=None,
+    ap.add_argument("--profile-case", choices=["small", "ace", "multipole", "fft"], default=None,
                     help="small: one apply of a small case of the same kernels (96^3, 8 orbitals); ace: three "
                          "ACE operator applies at 96^3 with 64 + 64 vectors; multipole: two applies of the "
-                         "headline system with boundary values to order 4; all for ncu captures")
+                         "headline system with boundary values to order 4; fft: the first 64 pairs of the "
+                         "80^3 periodic system on a KX_FFT32 plan, twice; all for ncu captures")
     return ap.parse_args()
 
 
@@ -61,6 +62,15 @@ def run_profile_case(which="small"):
     import paper_2406_16998_gb300 as kx
     from paper_2406_16998_gb300 import build
     build.build()
+    if which == "fft":
+        sysd = workloads.C3
+        plan = kx.Plan.for_system(sysd, precision=kx.KX_FFT32)
+        psi = torch.from_numpy(np.ascontiguousarray(workloads.make_orbitals(sysd).T)).cuda()
+        for _ in range(2):
+            vx, ex = kx.kx_vx_apply_pairs(plan, psi, 0, 64)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "fft", "e_x": ex.item(), "status": plan.status()}), flush=True)
+        return
     if which == "multipole":
         plan = kx.Plan.for_system(SYS, precision=kx.KX_F16X3)
         plan.set_multipole(4)

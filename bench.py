@@ -297,7 +297,7 @@ def measured_traffic(kind, units_per_launch):
     return None, "no ncu capture for this kernel"
 
 
-def other_workloads(kx, torch, stream, steps=3):
+def other_workloads(kx, torch, stream, hbm, steps=3):
     """Context lines beside the headline: the split path on the 80^3 periodic
     screened 256-orbital system (32896 pairs) and the batch of eight systems
     (26400 pairs) replayed as one CUDA graph."""
@@ -319,7 +319,32 @@ def other_workloads(kx, torch, stream, steps=3):
     P3 = sysd.n_orb * (sysd.n_orb + 1) // 2
     res["c3_80cube_periodic_screened_256orb"] = {"ms_per_apply": ms, "pair_solves_per_s": P3 / (ms / 1e3),
                                                  "pairs": P3, "status": plan.status()}
-    del psi, vx, plan
+    # the same system through the FFT variant (KX_FFT32: float32 DFTs on the CUDA cores);
+    # its passes move 36 N bytes per pair (pass A writes 8N, B reads and writes 8N, C
+    # reads 8N and writes 4N)
+    plan_f = kx.Plan.for_system(sysd, precision=kx.KX_FFT32)
+    vx_f = torch.empty_like(vx)
+    ex_f = torch.empty(1, dtype=torch.float64, device="cuda")
+    kx.kx_vx_apply(plan_f, psi, out=vx_f, e_x=ex_f)
+    e0.record(stream)
+    kx.kx_vx_apply(plan_f, psi, out=vx_f, e_x=ex_f)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_f = e0.elapsed_time(e1)
+    plan_f.profile(True)
+    kx.kx_vx_apply(plan_f, psi, out=vx_f, e_x=ex_f)
+    pr = plan_f.profile_read()
+    plan_f.profile(False)
+    fft_ms = pr["fft"][0]
+    gbs = 36.0 * plan_f.N * P3 / (fft_ms / 1e3) / 1e9
+    res["c3_fft_variant"] = {
+        "ms_per_apply": ms_f, "pair_solves_per_s": P3 / (ms_f / 1e3), "fft_passes_ms": fft_ms,
+        "kronecker_speedup": ms_f / ms, "status": plan_f.status(),
+        "vx_psi_maxrel_vs_kronecker": float((vx_f - vx).abs().max() / vx.abs().max()),
+        "e_x_rel_vs_kronecker": abs(ex_f.item() - ex.item()) / abs(ex.item()),
+        "fft_roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                         "algorithmic_bytes_per_pair": 36.0 * plan_f.N}}
+    del psi, vx, plan, plan_f, vx_f
     plans, psis, outs, P4 = [], [], [], 0
     for sd in workloads.C4:
         plans.append(kx.Plan.for_system(sd, precision=kx.KX_F16X3))
@@ -597,7 +622,7 @@ def main():
         out["ace"] = ace_legs(kx, torch, stream, plan, psi, vx_split, hbm)
         out["multipole"] = multipole_legs(kx, torch, stream, plan, psi, ms_step, bf16)
         out["multipole"]["e_x_zero_boundary"] = ex_split
-        out["other_workloads"] = other_workloads(kx, torch, stream)
+        out["other_workloads"] = other_workloads(kx, torch, stream, hbm)
         line, done, vx_ref, ex_ref = cpu_baseline(psi_h)
         out["cpu_baseline"] = line
         # the split path over the same first pairs of the list, against the oracle

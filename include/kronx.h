@@ -120,6 +120,23 @@ int kx_plan_eig(const kx_plan *plan, int axis, double *lam, double *V);
  * Synchronous. */
 int kx_plan_ftable(const kx_plan *plan, double *f);
 
+/* kx_energy_gradient — dE_x/dpsi_a(x) of the discrete E_x (Sec. 2, Eq. 5 as a
+ * dV-weighted sum over the pairs) for the orbitals psi, and E_x:
+ *   grad_a = 2 dV g_a G_a,
+ * G = Vx psi for zero boundary values (the solve is symmetric in rho); with
+ * multipole boundary values (kx_plan_set_multipole) the solve
+ * K rho = f(L) rho + sum_k Q_k(rho) h_k is not symmetric and
+ *   G_a = (Vx psi with zero boundary values)_a
+ *         - 1/2 sum_j g_j psi_j sum_k (Q_k(rho_aj) h_k + P_k(rho_aj) R_k),
+ * P_k(rho) = dV <h_k, rho>, the gradient of E_x = -1/2 dV sum g_i g_j
+ * <rho_ij, K rho_ij> (the symmetric part (K + K^T) / 2 enters).
+ *   psi   in: n_orb grid vectors (device);  occ: nullable (device)
+ *   grad  out: n_orb grid vectors (device), must not overlap psi
+ *   e_x   out (nullable): E_x (device scalar)
+ * Same precision and arguments as kx_vx_apply. */
+int kx_energy_gradient(kx_plan *plan, int n_orb, const double *psi, const double *occ, double *grad, double *e_x,
+                       kx_stream stream);
+
 /* kx_plan_set_multipole — Dirichlet boundary values from the multipole
  * expansion of the source (Sec. 4: for isolated systems the boundary values of
  * each linear system come from the multipole expansion of the Coulomb kernel

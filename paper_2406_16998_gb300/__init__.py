@@ -47,6 +47,7 @@ SIGNATURES = {
     "kx_ace": (_c_int, [_vp, _c_int, _vp, _vp, _vp, _vp, _vp]),
     "kx_ace_apply": (_c_int, [_vp, _c_int, _vp, _c_int, _vp, _vp, _vp]),
     "kx_plan_set_multipole": (_c_int, [_vp, _c_int]),
+    "kx_energy_gradient": (_c_int, [_vp, _c_int, _vp, _vp, _vp, _vp, _vp]),
     "kx_batch_create": (_c_int, [_c_int, _vp, _vp, ctypes.POINTER(_vp)]),
     "kx_batch_run": (_c_int, [_vp, _vp, _vp, _vp, _vp]),
     "kx_batch_destroy": (_c_int, [_vp]),
@@ -301,6 +302,22 @@ def kx_ace(plan: Plan, psi, vx_psi, stream=None):
     return xi, M
 
 
+def kx_energy_gradient(plan: Plan, psi, occ=None, out=None, e_x=None, stream=None):
+    """(dE_x/dpsi, E_x): 2 dV g_a G_a, G = Vx psi (symmetric form of the multipole
+    correction when the plan has one); see kx_energy_gradient in kronx.h."""
+    torch = _torch()
+    n_orb = psi.shape[0]
+    if out is None:
+        out = torch.empty_like(psi)
+    if e_x is None:
+        e_x = torch.empty(1, dtype=torch.float64, device=psi.device)
+    occ_p = None if occ is None else _dptr(occ, "occ", torch.float64, (n_orb,))
+    _check(lib().kx_energy_gradient(plan.handle, n_orb, _dptr(psi, "psi", torch.float64, (n_orb, plan.N)), occ_p,
+                                    _dptr(out, "out", torch.float64, (n_orb, plan.N)),
+                                    _dptr(e_x, "e_x", torch.float64, (1,)), _stream(stream)))
+    return out, e_x
+
+
 def kx_ace_apply(plan: Plan, xi, phi, out=None, stream=None):
     """V_ACE phi = -xi (dV xi^T phi) for the n_vec grid vectors phi (rows of a float64 tensor)."""
     torch = _torch()
@@ -360,18 +377,17 @@ def _autograd():
     torch = _torch()
 
     class ExchangeEnergy(torch.autograd.Function):
-        """E_x(psi) with a hand-written backward: dE_x/dpsi_k = 2 dV g_k (Vx psi)_k.
+        """E_x(psi) with a hand-written backward: dE_x/dpsi_k = 2 dV g_k G_k,
+        G = Vx psi (with the symmetric form of the multipole correction when the
+        plan has one).
 
         forward runs kx_energy (forward transforms and the Parseval sum only);
-        backward recomputes the pair products inside kx_vx_apply (nothing stored).
+        backward recomputes the pair products inside kx_energy_gradient (nothing
+        stored).
         """
 
         @staticmethod
         def forward(ctx, psi, plan, occ=None):
-            if getattr(plan, "l_max", -1) >= 0:
-                # with multipole boundary values the solve is not symmetric in rho, so
-                # dE_x/dpsi is not 2 dV Vx psi
-                raise NotImplementedError("ExchangeEnergy needs zero boundary values (plan.set_multipole(-1))")
             ctx.plan = plan
             ctx.save_for_backward(psi, occ) if occ is not None else ctx.save_for_backward(psi)
             ctx.has_occ = occ is not None
@@ -382,10 +398,8 @@ def _autograd():
             saved = ctx.saved_tensors
             psi = saved[0]
             occ = saved[1] if ctx.has_occ else None
-            vx, _ = kx_vx_apply(ctx.plan, psi.detach().contiguous(), occ)
-            w = 2.0 * ctx.plan.dV * g_e
-            grad = vx * w if occ is None else vx * (w * occ)[:, None]
-            return grad, None, None
+            grad, _ = kx_energy_gradient(ctx.plan, psi.detach().contiguous(), occ)
+            return grad * g_e, None, None
 
     return ExchangeEnergy
 

@@ -489,6 +489,36 @@ int kx_ace_apply(kx_plan *plan, int n_xi, const double *xi, int n_vec, const dou
     return ace_apply_run(plan, n_xi, xi, n_vec, phi, out, reinterpret_cast<cudaStream_t>(stream));
 }
 
+namespace kx {
+namespace {
+// grad[a][x] = 2 dV g_a G[a][x] in place
+__global__ void grad_scale_kernel(double *__restrict__ g, const double *__restrict__ occ, int n, long long N,
+                                  double two_dv) {
+    const long long total = (long long)n * N;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x)
+        g[e] *= two_dv * (occ ? occ[e / N] : 1.0);
+}
+}  // namespace
+}  // namespace kx
+
+int kx_energy_gradient(kx_plan *plan, int n_orb, const double *psi, const double *occ, double *grad, double *e_x,
+                       kx_stream stream) {
+    if (int rc = check_plan(plan)) return rc;
+    if (n_orb < 1 || n_orb > 4096) return set_error(KX_ERR_ARG, "kx_energy_gradient: n_orb must be in 1..4096");
+    if (!psi || !grad) return set_error(KX_ERR_ARG, "kx_energy_gradient: NULL buffer");
+    if (psi == grad) return set_error(KX_ERR_ARG, "kx_energy_gradient: grad must not overlap psi");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // G = Vx psi, with the multipole correction in its symmetric form when it is on
+    plan->mp_grad = plan->mp_lmax >= 0;
+    int rc = dispatch_vx(plan, n_orb, psi, occ, grad, e_x, false, s);
+    plan->mp_grad = false;
+    if (rc) return rc;
+    grad_scale_kernel<<<4 * plan->num_sms, 256, 0, s>>>(grad, occ, n_orb, (long long)plan->N, 2.0 * plan->dV);
+    KX_LAUNCH_CHECK("grad_scale_kernel launch");
+    return KX_OK;
+}
+
 int kx_plan_set_multipole(kx_plan *plan, int l_max) {
     if (int rc = check_plan(plan)) return rc;
     return mp_set(plan, l_max);

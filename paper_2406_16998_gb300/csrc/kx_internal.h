@@ -141,6 +141,7 @@ struct kx_plan_s {
     float *d_mpR32 = nullptr, *d_mpH32 = nullptr;
     float *d_mpMax = nullptr;  // max |R_k| (K values) then max |h_k| (K values)
     bool mp_applied = false;   // the split path applied the correction inside its pair loop
+    bool mp_grad = false;      // kx_energy_gradient: use the symmetric form of the correction
     kx::Workspace mp_scratch;
 };
 

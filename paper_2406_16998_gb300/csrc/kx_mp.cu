@@ -130,16 +130,16 @@ __global__ void to_f32_kernel(const double *__restrict__ in, float *__restrict__
         out[i] = (float)in[i];
 }
 
-// C[k][j][i] = g_j mask(i, j) Q[k][i][j]   (T = float or double)
+// C[k][j][i] = scale g_j mask(i, j) Q[k][i][j]   (T = float or double)
 template <typename T>
 __global__ void mp_coef_kernel(const double *__restrict__ Q, const unsigned char *__restrict__ mask,
-                               const double *__restrict__ occ, int n, int K, T *__restrict__ C) {
+                               const double *__restrict__ occ, int n, int K, double scale, T *__restrict__ C) {
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nn = (long long)n * n;
     if (e >= nn * K) return;
     const int k = (int)(e / nn), i = (int)((e % nn) / n), j = (int)(e % n);
     const double gj = occ ? occ[j] : 1.0;
-    C[(long long)k * nn + (long long)j * n + i] = (T)(mask[(long long)i * n + j] ? gj * Q[e] : 0.0);
+    C[(long long)k * nn + (long long)j * n + i] = (T)(mask[(long long)i * n + j] ? scale * gj * Q[e] : 0.0);
 }
 
 constexpr int kMcX = 128;  // correction tile: 128 grid points x 64 orbitals
@@ -836,8 +836,9 @@ size_t mp_scratch_bytes(const kx_plan *p, int n, int K) {
     const size_t tiles = (size_t)((N + kMcX - 1) / kMcX) * ((n + 63) / 64);
     const size_t part64 = (size_t)((N + 255) / 256) * n;
     const size_t part_tc = n <= 64 ? (size_t)moments_tc_split(p) * kn2 : 0;
-    return kMpSmall + sizeof(double) * (2 * kn2 + std::max(std::max(tiles, part64), part_tc)) + 256 +
-           (size_t)K * 16384;
+    // Q and P hold up to 2K matrices (the gradient's symmetric correction), Bs 2K tiles
+    return kMpSmall + sizeof(double) * (4 * kn2 + std::max(std::max(tiles, part64), part_tc)) + 256 +
+           (size_t)2 * K * 16384;
 }
 
 // Layout of the plan's multipole scratch for n orbitals: small float arrays
@@ -861,8 +862,8 @@ MpScratch mp_layout(const kx_plan *p, int n) {
     m.cmax = reinterpret_cast<float *>(b + 256);
     m.sc = reinterpret_cast<float *>(b + 1024);
     m.Q = reinterpret_cast<double *>(b + kMpSmall);
-    m.P = m.Q + kn2;
-    m.part = m.P + kn2;
+    m.P = m.Q + 2 * kn2;
+    m.part = m.P + 2 * kn2;
     const uintptr_t bs = reinterpret_cast<uintptr_t>(m.part + std::max(std::max(tiles, part64), part_tc));
     m.Bs = reinterpret_cast<__half *>((bs + 255) & ~uintptr_t(255));  // 16-byte copies need alignment
     return m;
@@ -908,10 +909,8 @@ int weighted_moments(kx_plan *p, int n, const double *psi, const double *W64, co
 }  // namespace
 
 void mp_free(kx_plan *p) {
-    cudaFree(p->d_mpR);
-    cudaFree(p->d_mpH);
+    cudaFree(p->d_mpR);    // R and h share one allocation (h = R + K N)
     cudaFree(p->d_mpR32);
-    cudaFree(p->d_mpH32);
     cudaFree(p->d_mpMax);
     p->d_mpMax = nullptr;
     cudaFree(p->mp_scratch.ptr);
@@ -950,10 +949,14 @@ int mp_set(kx_plan *p, int l_max) {
     G.K = K;
     const size_t fld = sizeof(double) * (size_t)K * N;
     double *Gk = nullptr;
-    cudaError_t e = cudaMalloc(&p->d_mpR, fld);
-    if (e == cudaSuccess) e = cudaMalloc(&p->d_mpH, fld);
-    if (e == cudaSuccess) e = cudaMalloc(&p->d_mpR32, fld / 2);
-    if (e == cudaSuccess) e = cudaMalloc(&p->d_mpH32, fld / 2);
+    // [R_0 .. R_{K-1} | h_0 .. h_{K-1}] in one allocation per precision, so that
+    // the gradient's correction walks all 2K fields in order
+    cudaError_t e = cudaMalloc(&p->d_mpR, 2 * fld);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_mpR32, fld);
+    if (e == cudaSuccess) {
+        p->d_mpH = p->d_mpR + (size_t)K * N;
+        p->d_mpH32 = p->d_mpR32 + (size_t)K * N;
+    }
     if (e == cudaSuccess) e = cudaMalloc(&p->d_mpMax, sizeof(float) * 2 * K);
     if (e == cudaSuccess) e = cudaMalloc(&Gk, fld);
     if (e != cudaSuccess) {
@@ -1041,14 +1044,23 @@ int mp_correct_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, d
         }
         return KX_OK;
     }
-    const unsigned cb = (unsigned)((nn * K + 255) / 256);
+    // gradient mode: fields [R | h] with coefficients 1/2 [P | Q] (P_k = dV <h_k, rho>)
+    const bool sym = p->mp_grad;
+    const int Kc = sym ? 2 * K : K;
+    if (sym) {
+        if ((rc = weighted_moments(p, n, psi, p->d_mpH, p->d_mpH32, p->d_mpMax + K, P, part, psimax, s))) return rc;
+        KX_CUDA_TRY(cudaMemcpyAsync(Q + (size_t)K * nn, Q, sizeof(double) * K * nn, cudaMemcpyDeviceToDevice, s));
+        KX_CUDA_TRY(cudaMemcpyAsync(Q, P, sizeof(double) * K * nn, cudaMemcpyDeviceToDevice, s));
+    }
+    const double cscale = sym ? 0.5 : 1.0;
+    const unsigned cb = (unsigned)((nn * Kc + 255) / 256);
     if ((rc = prof_begin(p, PK_MP, s))) return rc;
     if (f64) {
         double *C = P;
-        mp_coef_kernel<double><<<cb, 256, 0, s>>>(Q, mask, occ, n, K, C);
+        mp_coef_kernel<double><<<cb, 256, 0, s>>>(Q, mask, occ, n, Kc, cscale, C);
         KX_LAUNCH_CHECK("mp_coef_kernel launch");
         const dim3 grid((unsigned)((N + 255) / 256), (unsigned)n);
-        mp_combine64_kernel<<<grid, 256, 0, s>>>(psi, n, C, p->d_mpH, K, occ, N, vx, part);
+        mp_combine64_kernel<<<grid, 256, 0, s>>>(psi, n, C, sym ? p->d_mpR : p->d_mpH, Kc, occ, N, vx, part);
         KX_LAUNCH_CHECK("mp_combine64_kernel launch");
         if (ex) {
             mp_energy_add_kernel<<<1, 1, 0, s>>>(part, (long long)grid.x * grid.y, -0.5 * p->dV, ex);
@@ -1057,12 +1069,12 @@ int mp_correct_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, d
         return prof_end(p, s);
     }
     float *C = reinterpret_cast<float *>(P);
-    mp_coef_kernel<float><<<cb, 256, 0, s>>>(Q, mask, occ, n, K, C);
+    mp_coef_kernel<float><<<cb, 256, 0, s>>>(Q, mask, occ, n, Kc, cscale, C);
     KX_LAUNCH_CHECK("mp_coef_kernel launch");
     const dim3 grid((unsigned)((N + kMcX - 1) / kMcX), (unsigned)((n + 63) / 64));
     const size_t smem = sizeof(float) * (size_t)n * (kMcX + 64);
     KX_CUDA_TRY(cudaFuncSetAttribute(mp_combine32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    mp_combine32_kernel<<<grid, 256, smem, s>>>(psi, n, C, p->d_mpH32, K, occ, N, vx, part);
+    mp_combine32_kernel<<<grid, 256, smem, s>>>(psi, n, C, sym ? p->d_mpR32 : p->d_mpH32, Kc, occ, N, vx, part);
     KX_LAUNCH_CHECK("mp_combine32_kernel launch");
     if (ex) {
         mp_energy_add_kernel<<<1, 1, 0, s>>>(part, (long long)grid.x * grid.y, -0.5 * p->dV, ex);
@@ -1087,22 +1099,29 @@ int mp_correct_into_acc(kx_plan *p, int n_orb, const double *psi, const double *
     double *Q = m.Q, *C = m.P, *part = m.part;
     float *psimax = m.psimax, *cmax = m.cmax, *sc = m.sc;
     __half *Bs = m.Bs;
-    if ((rc = weighted_moments(p, n, psi, p->d_mpR, p->d_mpR32, p->d_mpMax, Q, part, psimax, s))) return rc;
+    // gradient mode: fields [R | h] with coefficients 1/2 [P | Q] (P_k = dV <h_k, rho>)
+    const bool sym = p->mp_grad;
+    const int Kc = sym ? 2 * K : K;
+    double *Qr = sym ? Q + (size_t)K * nn : Q;
+    if (sym && (rc = weighted_moments(p, n, psi, p->d_mpH, p->d_mpH32, p->d_mpMax + K, Q, part, psimax, s)))
+        return rc;
+    if ((rc = weighted_moments(p, n, psi, p->d_mpR, p->d_mpR32, p->d_mpMax, Qr, part, psimax, s))) return rc;
     if ((rc = prof_begin(p, PK_MP, s))) return rc;
-    const unsigned cb = (unsigned)((nn * K + 255) / 256);
-    mp_coef_kernel<double><<<cb, 256, 0, s>>>(Q, p->d_pair_mask, occ, n, K, C);
+    const unsigned cb = (unsigned)((nn * Kc + 255) / 256);
+    mp_coef_kernel<double><<<cb, 256, 0, s>>>(Q, p->d_pair_mask, occ, n, Kc, sym ? 0.5 : 1.0, C);
     KX_LAUNCH_CHECK("mp_coef_kernel launch");
-    KX_CUDA_TRY(cudaMemsetAsync(cmax, 0, sizeof(float) * K, s));
-    mp_cmax_kernel<<<K, 256, 0, s>>>(C, n, K, cmax);
+    KX_CUDA_TRY(cudaMemsetAsync(cmax, 0, sizeof(float) * Kc, s));
+    mp_cmax_kernel<<<Kc, 256, 0, s>>>(C, n, Kc, cmax);
     KX_LAUNCH_CHECK("mp_cmax_kernel launch");
-    mp_ct_scales_kernel<<<1, 1, 0, s>>>(p->d_mpMax + K, cmax, psimax, K, sc);
+    // field maxima in the same order as the fields: [R | h] or h alone
+    mp_ct_scales_kernel<<<1, 1, 0, s>>>(sym ? p->d_mpMax : p->d_mpMax + K, cmax, psimax, Kc, sc);
     KX_LAUNCH_CHECK("mp_ct_scales_kernel launch");
-    mp_ct_bsplit_kernel<<<(unsigned)(((long long)K * 4096 + 255) / 256), 256, 0, s>>>(C, n, K, sc, Bs);
+    mp_ct_bsplit_kernel<<<(unsigned)(((long long)Kc * 4096 + 255) / 256), 256, 0, s>>>(C, n, Kc, sc, Bs);
     KX_LAUNCH_CHECK("mp_ct_bsplit_kernel launch");
     const int grid = (int)std::min<long long>((N + kCtM - 1) / kCtM, p->num_sms);
     KX_CUDA_TRY(cudaFuncSetAttribute(mp_combine_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCtSmem));
-    mp_combine_tc_kernel<<<grid, 256, kCtSmem, s>>>(psi, n, Bs, p->d_mpH32, K, sc, occ, N, acc, part, p->d_status,
-                                                     4000000000LL);
+    mp_combine_tc_kernel<<<grid, 256, kCtSmem, s>>>(psi, n, Bs, sym ? p->d_mpR32 : p->d_mpH32, Kc, sc, occ, N, acc,
+                                                     part, p->d_status, 4000000000LL);
     KX_LAUNCH_CHECK("mp_combine_tc_kernel launch");
     if (ex) {
         mp_energy_add_kernel<<<1, 1, 0, s>>>(part, grid, -0.5 * p->dV, ex);

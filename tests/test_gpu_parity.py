@@ -304,8 +304,55 @@ def test_multipole_rejects_unsupported_plans(kx):
     with pytest.raises(kx.KxError) as ei:
         kx.kx_apply_fL_noalloc(plan, b, torch.empty_like(b))
     assert ei.value.code == kx.KX_ERR_UNSUPPORTED
-    with pytest.raises(NotImplementedError):
-        kx.exchange_energy(dev(workloads.random_field(plan.N, 2, 4).T), plan)
+
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_multipole_energy_gradient_against_finite_differences(kx, prec):
+    """dE_x/dpsi with multipole boundary values (the solve is not symmetric in
+    rho) against central finite differences of the oracle's E_x, and the
+    autograd energy's backward against the same gradient."""
+    n, h, bc = MP_GRID
+    sysd = system(n, h, bc, U, 3, 97)
+    psi = workloads.make_orbitals(sysd)
+    occ = np.array([1.0, 0.7, 0.4])
+    op = oracle.Plan(n, h, bc, U)
+    plan = kx.Plan(n, h, bc, U, precision=prec)
+    plan.set_multipole(2)
+    psi_d, occ_d = dev(psi.T), dev(occ)
+    grad, ex = kx.kx_energy_gradient(plan, psi_d, occ_d)
+    grad = grad.cpu().numpy().T
+    _, ex_ref = oracle.vx_apply(op, psi, occ, l_max=2)
+    assert abs(ex.item() - ex_ref) < TOL[prec]["ex"] * abs(ex_ref)
+    rng = np.random.default_rng(11)
+    step = 1e-4
+    scale = np.abs(grad).max()
+    for _ in range(6):
+        r, k = int(rng.integers(op.N)), int(rng.integers(3))
+        pp, pm = psi.copy(), psi.copy()
+        pp[r, k] += step
+        pm[r, k] -= step
+        fd = (oracle.vx_apply(op, pp, occ, l_max=2)[1] - oracle.vx_apply(op, pm, occ, l_max=2)[1]) / (2 * step)
+        assert abs(fd - grad[r, k]) < (1e-7 if prec == 0 else 1e-5) * scale
+    # the gradient is not 2 dV g Vx psi here (that would use the solve, not its symmetric part)
+    vx, _ = kx.kx_vx_apply(plan, psi_d, occ_d)
+    naive = 2 * sysd.dV * vx.cpu().numpy().T * occ[None, :]
+    assert relmax(naive, grad) > 1e-4
+    x = psi_d.clone().requires_grad_(True)
+    e = kx.exchange_energy(x, plan, occ_d)
+    e.backward()
+    assert relmax(x.grad.cpu().numpy().T, grad) < 1e-12
+
+
+def test_energy_gradient_is_2dv_vx_with_zero_boundary_values(kx):
+    n, h, bc, kind, n_orb = SMALL[0]
+    psi = workloads.make_orbitals(system(n, h, bc, kind, n_orb, 99))
+    plan = kx.Plan(n, h, bc, kind, precision=1)
+    psi_d = dev(psi.T)
+    grad, ex = kx.kx_energy_gradient(plan, psi_d)
+    vx, ex2 = kx.kx_vx_apply(plan, psi_d)
+    assert np.array_equal(grad.cpu().numpy(), (2 * plan.dV * vx).cpu().numpy())
+    assert ex.item() == ex2.item()
 
 
 def test_multipole_full_size_row(kx):

@@ -355,6 +355,35 @@ def test_energy_gradient_is_2dv_vx_with_zero_boundary_values(kx):
     assert ex.item() == ex2.item()
 
 
+def test_multipole_more_than_64_orbitals(kx):
+    """Tensor-core plans with more than 64 orbitals take the CUDA-core form of
+    the multipole correction (weighted projections, FMA combination applied
+    to Vx psi after the pair loop): a pair range of a 70-orbital system
+    against the oracle over the same pairs."""
+    from paper_2406_16998_gb300 import shard
+    n, h, bc = (16, 16, 24), (0.55, 0.55, 0.5), (D, D, D)
+    sysd = system(n, h, bc, U, 70, 101, centres=6)
+    psi = workloads.make_orbitals(sysd)
+    op = oracle.Plan(n, h, bc, U)
+    plan = kx.Plan(n, h, bc, U, precision=1)
+    plan.set_multipole(2)
+    part, e_part = kx.kx_vx_apply_pairs(plan, dev(psi.T), 0, 40)
+    ref, e_ref = oracle.vx_apply(op, psi, pairs=shard.pair_list(70)[:40], l_max=2)
+    assert relmax(part.cpu().numpy().T, ref) < TOL[1]["vx"]
+    assert abs(e_part.item() - e_ref) < TOL[1]["ex"] * abs(e_ref)
+
+
+def test_full_size_apply_is_deterministic(kx):
+    """Two applies of the benchmark system give bit-identical Vx psi and E_x
+    (fixed-order reductions, no floating-point atomics)."""
+    sysd = workloads.C2
+    psi = dev(workloads.make_orbitals(sysd).T)
+    plan = kx.Plan.for_system(sysd, precision=1)
+    a, ea = kx.kx_vx_apply(plan, psi)
+    b, eb = kx.kx_vx_apply(plan, psi)
+    assert torch.equal(a, b) and ea.item() == eb.item()
+
+
 def test_multipole_full_size_row(kx):
     """The 96^3 / 64-orbital benchmark system with boundary values to order 4,
     in the launch configuration of the benchmark: one orbital's row of pair

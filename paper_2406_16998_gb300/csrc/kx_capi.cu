@@ -42,6 +42,7 @@ int ensure_workspace(kx_plan *p, size_t bytes) {
         p->ws.ptr = nullptr;
         p->ws.bytes = 0;
     }
+    ++p->config_version;
     cudaError_t e = cudaMalloc(&p->ws.ptr, bytes);
     if (e != cudaSuccess) {
         p->ws.ptr = nullptr;
@@ -61,6 +62,7 @@ int ensure_pairs(kx_plan *p, int n_orb, cudaStream_t s, long long begin, long lo
     const long long P_all = (long long)n_orb * (n_orb + 1) / 2;
     if (end < 0) end = P_all;
     if (p->ws_norb == n_orb && p->pr_begin == begin && p->pr_end == end) return KX_OK;
+    ++p->config_version;  // the list is rebuilt in place
     std::vector<int> pairs, slots;
     std::vector<Group> groups;
     std::vector<int> first;
@@ -218,6 +220,7 @@ struct kx_batch_s {
     std::vector<const double *> last_psi;
     std::vector<double *> last_vx;
     double *last_ex = nullptr;
+    std::vector<unsigned long long> versions;  // plans' config_version at capture
     int device = 0;
 };
 
@@ -603,12 +606,18 @@ int kx_batch_run(kx_batch *batch, const double *const *psi, double *const *vx_ps
     if (!batch || !psi || !vx_psi) return set_error(KX_ERR_ARG, "kx_batch_run: bad arguments");
     const int n = (int)batch->plans.size();
     bool same = batch->exec != nullptr && batch->last_ex == e_x;
-    for (int i = 0; same && i < n; ++i) same = batch->last_psi[i] == psi[i] && batch->last_vx[i] == vx_psi[i];
+    for (int i = 0; same && i < n; ++i)
+        same = batch->last_psi[i] == psi[i] && batch->last_vx[i] == vx_psi[i] &&
+               batch->versions[i] == batch->plans[i]->config_version;
     if (!same) {
         if (batch->exec) cudaGraphExecDestroy(batch->exec);
         if (batch->graph) cudaGraphDestroy(batch->graph);
         batch->exec = nullptr;
         batch->graph = nullptr;
+        // the plans may have been used or reconfigured since the last capture:
+        // restore each one's full pair list and buffers outside the capture
+        for (int i = 0; i < n; ++i)
+            if (int rc = reserve(batch->plans[i], batch->n_orb[i])) return rc;
         KX_CUDA_TRY(cudaStreamBeginCapture(batch->cap, cudaStreamCaptureModeThreadLocal));
         int rc = KX_OK;
         for (int i = 0; i < n && rc == KX_OK; ++i)
@@ -627,6 +636,8 @@ int kx_batch_run(kx_batch *batch, const double *const *psi, double *const *vx_ps
         batch->last_psi.assign(psi, psi + n);
         batch->last_vx.assign(vx_psi, vx_psi + n);
         batch->last_ex = e_x;
+        batch->versions.resize(n);
+        for (int i = 0; i < n; ++i) batch->versions[i] = batch->plans[i]->config_version;
     }
     KX_CUDA_TRY(cudaGraphLaunch(batch->exec, reinterpret_cast<cudaStream_t>(stream)));
     return KX_OK;

@@ -142,6 +142,9 @@ struct kx_plan_s {
     float *d_mpMax = nullptr;  // max |R_k| (K values) then max |h_k| (K values)
     bool mp_applied = false;   // the split path applied the correction inside its pair loop
     bool mp_grad = false;      // kx_energy_gradient: use the symmetric form of the correction
+    // bumped whenever device buffers a captured batch graph refers to are
+    // reallocated or refilled (workspaces, pair list, multipole fields)
+    unsigned long long config_version = 0;
     kx::Workspace mp_scratch;
 };
 

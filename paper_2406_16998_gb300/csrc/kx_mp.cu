@@ -919,6 +919,7 @@ void mp_free(kx_plan *p) {
     p->mp_scratch = Workspace{};
     p->mp_lmax = -1;
     p->mp_K = 0;
+    ++p->config_version;
 }
 
 int mp_set(kx_plan *p, int l_max) {
@@ -988,6 +989,7 @@ int mp_set(kx_plan *p, int l_max) {
     }
     p->mp_lmax = l_max;
     p->mp_K = K;
+    ++p->config_version;
     return KX_OK;
 }
 
@@ -996,6 +998,7 @@ int mp_reserve_scratch(kx_plan *p, int n_orb) {
     if (p->mp_scratch.bytes < need) {
         cudaFree(p->mp_scratch.ptr);
         p->mp_scratch = Workspace{};
+        ++p->config_version;
         cudaError_t e = cudaMalloc(&p->mp_scratch.ptr, need);
         if (e != cudaSuccess) return cuda_error(e, "multipole scratch cudaMalloc");
         p->mp_scratch.bytes = need;
@@ -1009,6 +1012,7 @@ int mp_reserve(kx_plan *p, int n_orb) {
     if (p->mp_scratch.bytes < need) {
         cudaFree(p->mp_scratch.ptr);
         p->mp_scratch = Workspace{};
+        ++p->config_version;
         cudaError_t e = cudaMalloc(&p->mp_scratch.ptr, need);
         if (e != cudaSuccess) return cuda_error(e, "multipole scratch cudaMalloc");
         p->mp_scratch.bytes = need;
@@ -1137,6 +1141,7 @@ int mp_correct_apply(kx_plan *p, int n_rhs, const double *b, double *x, cudaStre
     if (p->mp_scratch.bytes < need) {
         cudaFree(p->mp_scratch.ptr);
         p->mp_scratch = Workspace{};
+        ++p->config_version;
         cudaError_t e = cudaMalloc(&p->mp_scratch.ptr, need);
         if (e != cudaSuccess) return cuda_error(e, "multipole scratch cudaMalloc");
         p->mp_scratch.bytes = need;

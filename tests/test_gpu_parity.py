@@ -567,6 +567,36 @@ def test_ace_apply_rejects_bad_arguments(kx):
     assert ei.value.code == kx.KX_ERR_ARG
 
 
+def test_batch_follows_plan_changes(kx):
+    """A batch's captured graph refers to its plans' buffers: after the plan is
+    used with another pair range (its pair list is rebuilt) or switched to
+    multipole boundary values, the next run captures again and still gives
+    the direct result."""
+    n, h, bc = MP_GRID
+    psi = workloads.make_orbitals(system(n, h, bc, U, 6, 103))
+    plan = kx.Plan(n, h, bc, U, precision=1)
+    x = dev(psi.T)
+    out = torch.empty_like(x)
+    ex = torch.empty(1, dtype=torch.float64, device="cuda")
+    b = kx.Batch([plan], [6])
+    b.run([x], [out], ex)
+    ref0, _ = kx.kx_vx_apply(plan, x)
+    torch.cuda.synchronize()
+    assert relmax(out.cpu().numpy(), ref0.cpu().numpy()) < 1e-12
+    kx.kx_vx_apply_pairs(plan, x, 3, 9)  # rebuilds the plan's pair list for a sub-range
+    b.run([x], [out], ex)
+    torch.cuda.synchronize()
+    assert relmax(out.cpu().numpy(), ref0.cpu().numpy()) < 1e-12
+    plan.set_multipole(2)
+    ref1, e1 = kx.kx_vx_apply(plan, x)
+    b.run([x], [out], ex)
+    torch.cuda.synchronize()
+    assert relmax(out.cpu().numpy(), ref1.cpu().numpy()) < 1e-12
+    assert abs(ex.item() - e1.item()) < 1e-12 * abs(e1.item())
+    assert relmax(ref1.cpu().numpy(), ref0.cpu().numpy()) > 1e-3
+    b.close()
+
+
 def test_batch_equals_individual_runs(kx):
     cases = [SMALL[0], SMALL[2], SMALL[3]]
     plans, psis, refs = [], [], []

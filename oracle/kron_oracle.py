@@ -33,6 +33,8 @@ test in tests/test_oracle_pins.py):
       same VxPsi and E_x.
   R10-R12 (multipole boundary values for isolated systems): see the section
       above apply_fL_multipole.
+  R13-R16 (Bloch-periodic boundary conditions and k-point sums): see the section
+      above lap1d_bloch.
 """
 from __future__ import annotations
 
@@ -401,3 +403,140 @@ def ace_apply(plan: Plan, xi: np.ndarray, phi: np.ndarray) -> np.ndarray:
     """
     P = plan.dV * (xi.T @ phi)              # projections of phi on xi (dV inner product)
     return -(xi @ P)
+
+
+# ---------------------------------------------------------------------------
+# Bloch-periodic boundary conditions and k-point sums (Sec. 2.1, Eqs. 6-9: the
+# orbitals are complex, the pair densities conj(psi_mq) phi_nk obey Bloch
+# conditions at k - q along the extended axes, and the sums carry Brillouin-zone
+# weights; Sec. 3: the 1D matrices may then be complex and wavevector
+# dependent, and Eq. 19 contracts with the conjugated eigenvectors).  Readings:
+#  R13 A k-point is given by its phase per cell along each periodic axis,
+#      theta_a = k_a n_a h_a (radians); Dirichlet axes ignore it.  The Poisson
+#      problem of the pair (mq, nk) takes the phases theta_k - theta_q.
+#  R14 Bloch 1D matrix: a stencil point j = i + p that leaves the cell w times
+#      (w = floor(j / n)) lands on j - w n with the factor exp(i w theta); the
+#      matrix is Hermitian and theta = 0 gives the periodic one.
+#  R15 The forward transform contracts each mode with conj(Vk) (the V^{*T} B V^{*}
+#      of Eq. 19b), the inverse transform with Vk (Eq. 19a).
+#  R16 Vx phi_nk = -sum_q w_q sum_m g_mq psi_mq f(L_{k-q})(conj(psi_mq) phi_nk) and
+#      E_x = -1/2 dV sum_k w_k sum_n g_nk sum_q w_q sum_m g_mq <rho, f rho> with
+#      rho = conj(psi_mq) psi_nk and <a, b> = sum_r conj(a) b (Eqs. 7-8), for one
+#      spin channel; the spin sum of Eq. 6 adds independent channels.
+# ---------------------------------------------------------------------------
+def lap1d_bloch(n: int, h: float, order: int, theta: float) -> np.ndarray:
+    """Dense complex n x n matrix of d^2/dx^2 with the Bloch condition u(x + n h) = e^{i theta} u(x) (R14)."""
+    w = fd_weights(order) / (h * h)
+    m = order // 2
+    L = np.zeros((n, n), dtype=np.complex128)
+    for i in range(n):
+        for p in range(-m, m + 1):
+            j = i + p
+            wraps = j // n                  # floor division: cells crossed, with sign
+            L[i, j - wraps * n] += w[abs(p)] * np.exp(1j * wraps * theta)
+    return L
+
+
+class BlochPlan(Plan):
+    """The set-up of a Plan for the Poisson problems at one phase difference theta
+    (3 values, radians per cell; ignored on Dirichlet axes): complex eigenvectors
+    along the periodic axes (R13-R14), real ones along the Dirichlet axes."""
+
+    def __init__(self, base: Plan, theta):
+        self.n, self.h, self.bc = base.n, base.h, base.bc
+        self.kind, self.omega, self.fd_order = base.kind, base.omega, base.fd_order
+        self.theta = tuple(float(t) for t in theta)
+        self.L = []
+        for a in range(3):
+            if self.bc[a] == PERIODIC:
+                self.L.append(lap1d_bloch(self.n[a], self.h[a], self.fd_order, self.theta[a]))
+            else:
+                self.L.append(lap1d(self.n[a], self.h[a], self.bc[a], self.fd_order).astype(np.complex128))
+        eig = [np.linalg.eigh(Lk) for Lk in self.L]
+        self.lam = [e[0] for e in eig]
+        self.V = [e[1] for e in eig]
+        lsum = (self.lam[2][:, None, None] + self.lam[1][None, :, None] + self.lam[0][None, None, :])
+        self.fdiag = kernel_f(lsum, self.kind, self.omega)
+
+
+def forward_transform_bloch(plan: BlochPlan, b: np.ndarray) -> np.ndarray:
+    """Spectral coefficients: slices V1^H B_k conj(V2), then mode 3 with conj(V3) (Eq. 19b, R15)."""
+    V1, V2, V3 = plan.V
+    n1, n2, n3 = plan.n
+    cube = np.asarray(b, dtype=np.complex128).reshape(n3, n2, n1)
+    cols = np.empty((n1 * n2, n3), dtype=np.complex128)
+    for k in range(n3):
+        Bk = cube[k].T
+        Yk = V1.conj().T @ Bk @ V2.conj()
+        cols[:, k] = Yk.reshape(-1, order="F")
+    return cols @ V3.conj()
+
+
+def inverse_transform_bloch(plan: BlochPlan, Xt: np.ndarray) -> np.ndarray:
+    """Grid values: slices V1 X_k V2^T, then mode 3 with V3^T (Eq. 19a)."""
+    V1, V2, V3 = plan.V
+    n1, n2, n3 = plan.n
+    cols = np.empty((n1 * n2, n3), dtype=np.complex128)
+    for k in range(n3):
+        Xk = Xt[:, k].reshape(n1, n2, order="F")
+        cols[:, k] = (V1 @ Xk @ V2.T).reshape(-1, order="F")
+    return (cols @ V3.T).reshape(-1, order="F")
+
+
+def apply_fL_bloch(plan: BlochPlan, b: np.ndarray) -> np.ndarray:
+    """X = f(L_theta) b for one complex grid vector (N,) (Sec. 3, Eq. 19 with complex Vk)."""
+    Y = forward_transform_bloch(plan, b)
+    return inverse_transform_bloch(plan, fdiag_matrix(plan) * Y)
+
+
+def _kpoint_args(theta, wk, psi, occ):
+    theta = np.asarray(theta, dtype=np.float64).reshape(-1, 3)
+    wk = np.asarray(wk, dtype=np.float64).reshape(-1)
+    psi = np.asarray(psi, dtype=np.complex128)      # (n_kpt, N, n_orb)
+    n_kpt, _, n_orb = psi.shape
+    if theta.shape[0] != n_kpt or wk.shape[0] != n_kpt:
+        raise ValueError("theta, weights and orbitals disagree on the number of k-points")
+    g = np.ones((n_kpt, n_orb)) if occ is None else np.asarray(occ, dtype=np.float64).reshape(n_kpt, n_orb)
+    return theta, wk, psi, g
+
+
+def vx_apply_kpoint(base: Plan, theta, wk, psi, occ, k: int, phi: np.ndarray) -> np.ndarray:
+    """Vx applied to vectors phi (N, n_vec) at k-point k (R16): for every q and band m,
+    phi_v -> -w_q g_mq psi_mq f(L_{theta_k - theta_q})(conj(psi_mq) phi_v), summed."""
+    theta, wk, psi, g = _kpoint_args(theta, wk, psi, occ)
+    phi = np.asarray(phi, dtype=np.complex128)
+    out = np.zeros_like(phi)
+    for q in range(psi.shape[0]):
+        plan = BlochPlan(base, theta[k] - theta[q])
+        for m in range(psi.shape[2]):
+            for v in range(phi.shape[1]):
+                rho = np.conj(psi[q][:, m]) * phi[:, v]
+                out[:, v] -= wk[q] * g[q, m] * psi[q][:, m] * apply_fL_bloch(plan, rho)
+    return out
+
+
+def vx_kpoints(base: Plan, theta, wk, psi, occ=None):
+    """Vx psi_nk at every k-point (n_kpt, N, n_orb) and E_x = 1/2 dV sum_k w_k sum_n
+    g_nk <psi_nk, Vx psi_nk> (the same sum as Eq. 8 after the Poisson solve, R16)."""
+    theta, wk, psi, g = _kpoint_args(theta, wk, psi, occ)
+    vx = np.stack([vx_apply_kpoint(base, theta, wk, psi, g, k, psi[k]) for k in range(psi.shape[0])])
+    e = 0.0
+    for k in range(psi.shape[0]):
+        for n in range(psi.shape[2]):
+            e += 0.5 * base.dV * wk[k] * g[k, n] * np.vdot(psi[k][:, n], vx[k][:, n]).real
+    return vx, e
+
+
+def exchange_energy_kpoints(base: Plan, theta, wk, psi, occ=None) -> float:
+    """E_x of Eq. 8 through Parseval: -1/2 dV sum w_k w_q g_nk g_mq sum f(Lambda) |V^H rho|^2."""
+    theta, wk, psi, g = _kpoint_args(theta, wk, psi, occ)
+    e = 0.0
+    for k in range(psi.shape[0]):
+        for q in range(psi.shape[0]):
+            plan = BlochPlan(base, theta[k] - theta[q])
+            F = fdiag_matrix(plan)
+            for n in range(psi.shape[2]):
+                for m in range(psi.shape[2]):
+                    Y = forward_transform_bloch(plan, np.conj(psi[q][:, m]) * psi[k][:, n])
+                    e += -0.5 * base.dV * wk[k] * wk[q] * g[k, n] * g[q, m] * float(np.sum(F * np.abs(Y) ** 2))
+    return e

@@ -537,3 +537,144 @@ def test_multipole_boundary_reproduces_the_free_space_potential():
     err_zero = np.max(np.abs(oracle.apply_fL(plan, rho) - exact)) / exact.max()
     assert err_mp < 2e-4
     assert err_zero > 50 * err_mp
+
+
+# ---------------------------------------------------------------- Bloch k-points (R13-R16)
+def _complex_orbitals(rng, n_kpt, N, n_orb):
+    return rng.standard_normal((n_kpt, N, n_orb)) + 1j * rng.standard_normal((n_kpt, N, n_orb))
+
+
+@pytest.mark.parametrize("n,order,theta", [(9, 2, 0.7), (12, 12, -2.1), (7, 12, math.pi), (16, 8, 0.0),
+                                           (5, 12, 1.3)])
+def test_bloch_1d_plane_waves_and_eigenvalues(n, order, theta):
+    """Every e^{i kappa x} with kappa = (2 pi m + theta) / n is an eigenvector of the
+    Bloch matrix with the stencil's symbol as eigenvalue, also when the stencil
+    wraps the cell more than once (n < order + 1)."""
+    h = 0.37
+    L = oracle.lap1d_bloch(n, h, order, theta)
+    assert np.max(np.abs(L - L.conj().T)) < 1e-12 * np.abs(L).max()
+    w = [float(x) for x in exact_weights(order)]
+    x = np.arange(n)
+    lam = []
+    for m_ in range(n):
+        kap = (2 * np.pi * m_ + theta) / n
+        lk = (w[0] + 2 * sum(w[p] * np.cos(p * kap) for p in range(1, order // 2 + 1))) / h ** 2
+        u = np.exp(1j * kap * x)
+        assert np.max(np.abs(L @ u - lk * u)) < 1e-11 * abs(w[0]) / h ** 2
+        lam.append(lk)
+    assert np.max(np.abs(np.sort(lam) - np.linalg.eigvalsh(L))) < 1e-10 * abs(w[0]) / h ** 2
+    if theta == 0.0:
+        assert np.max(np.abs(L - oracle.lap1d(n, h, P, order))) == 0.0
+
+
+@pytest.mark.parametrize("kind", [U, S])
+def test_bloch_apply_fL_matches_dense_matrix_function(kind):
+    """Mixed Bloch / Dirichlet axes: the Kronecker apply (complex Vk, conjugated
+    forward contraction) equals f of the dense Hermitian 3D Laplacian."""
+    base = oracle.Plan((5, 4, 6), (0.5, 0.45, 0.4), (P, D, P), kind, fd_order=4)
+    theta = (0.9, 0.0, -2.4)
+    bp = oracle.BlochPlan(base, theta)
+    L1, L2, L3 = bp.L
+    I1, I2, I3 = (np.eye(k) for k in base.n)
+    Ld = np.kron(I3, np.kron(I2, L1)) + np.kron(I3, np.kron(L2, I1)) + np.kron(L3, np.kron(I2, I1))
+    lam, V = np.linalg.eigh(Ld)
+    mu = -lam
+    fl = 4 * np.pi / mu if kind == U else 4 * np.pi * (1 - np.exp(-mu / (4 * 0.11 ** 2))) / mu
+    F = (V * fl) @ V.conj().T
+    rng = np.random.default_rng(5)
+    b = rng.standard_normal(base.N) + 1j * rng.standard_normal(base.N)
+    x = oracle.apply_fL_bloch(bp, b)
+    assert np.max(np.abs(x - F @ b)) < 1e-11 * np.abs(F @ b).max()
+
+
+def test_bloch_plane_wave_is_scaled_by_f():
+    base = oracle.Plan((6, 5, 7), (0.4, 0.5, 0.45), (P, P, P), S)
+    theta = (0.3, -1.1, 2.9)
+    bp = oracle.BlochPlan(base, theta)
+    w = [float(x) for x in exact_weights(12)]
+    idx = np.indices((7, 5, 6))  # [x3, x2, x1]
+    modes = (2, 4, 1)
+    phase = np.zeros((7, 5, 6))
+    lam = 0.0
+    for a, (n, h, th, m_) in enumerate(zip(base.n, base.h, theta, modes)):
+        kap = (2 * np.pi * m_ + th) / n
+        phase = phase + kap * idx[2 - a]
+        lam += (w[0] + 2 * sum(w[p] * np.cos(p * kap) for p in range(1, 7))) / h ** 2
+    u = np.exp(1j * phase).ravel()
+    f = 4 * np.pi * (1 - np.exp(lam / (4 * 0.11 ** 2))) / (-lam)
+    assert np.max(np.abs(oracle.apply_fL_bloch(bp, u) - f * u)) < 1e-10 * f
+
+
+def test_bloch_zero_phase_is_the_real_periodic_solve():
+    base = oracle.Plan((6, 8, 5), (0.4, 0.35, 0.5), (P, P, D), U)
+    b = np.random.default_rng(2).standard_normal(base.N)
+    x = oracle.apply_fL_bloch(oracle.BlochPlan(base, (0.0, 0.0, 0.0)), b)
+    ref = oracle.apply_fL(base, b)
+    assert np.max(np.abs(x - ref)) < 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("kind", [U, S])
+def test_kpoint_exchange_is_the_supercell_exchange(kind):
+    """k-point sampling along x1 with n_k phases 2 pi c / n_k is the Gamma-point
+    exchange of the n_k-fold supercell whose orbitals are the Bloch orbitals
+    continued cell by cell with their phase: with unit weights, Vx Psi on the
+    first cell agrees and the supercell energy is n_k times the k-point sum.
+    The supercell side uses a dense f from the independently derived stencil."""
+    n_k = 3
+    n1, n2, n3 = 4, 5, 4
+    h = (0.45, 0.5, 0.4)
+    base = oracle.Plan((n1, n2, n3), h, (P, P, D), kind, fd_order=6)
+    theta = np.array([[2 * np.pi * c / n_k, 0.0, 0.0] for c in range(n_k)])
+    rng = np.random.default_rng(17)
+    n_orb = 2
+    psi = _complex_orbitals(rng, n_k, base.N, n_orb)
+    occ = rng.uniform(0.3, 1.0, (n_k, n_orb))
+    wk = np.ones(n_k)
+    vx, e = oracle.vx_kpoints(base, theta, wk, psi, occ)
+    # supercell: cells c = 0..n_k-1 along x1, Psi(x1 + c n1) = e^{i c theta_q} psi_q(x1)
+    sup = oracle.Plan((n_k * n1, n2, n3), h, (P, P, D), kind, fd_order=6)
+    Ls = sparse_laplacian(sup).toarray()
+    lam, V = np.linalg.eigh(Ls)
+    mu = -lam
+    fl = 4 * np.pi / mu if kind == U else 4 * np.pi * (1 - np.exp(-mu / (4 * 0.11 ** 2))) / mu
+    F = (V * fl) @ V.T
+    def unfold(u, th):
+        cube = u.reshape(n3, n2, n1)
+        return np.concatenate([np.exp(1j * c * th) * cube for c in range(n_k)], axis=2).ravel()
+    Psi = [(q, m_, unfold(psi[q][:, m_], theta[q, 0])) for q in range(n_k) for m_ in range(n_orb)]
+    e_sup = 0.0
+    for k, n_, Pk in Psi:
+        out = np.zeros(sup.N, dtype=complex)
+        for q, m_, Pq in Psi:
+            rho = np.conj(Pq) * Pk
+            out -= occ[q, m_] * Pq * (F @ rho)
+        first = out.reshape(n3, n2, n_k * n1)[:, :, :n1].ravel()
+        assert np.max(np.abs(first - vx[k][:, n_])) < 1e-11 * np.abs(first).max()
+        e_sup += 0.5 * base.dV * occ[k, n_] * np.vdot(Pk, out).real
+    assert abs(e_sup - n_k * e) < 1e-11 * abs(e_sup)
+
+
+def test_kpoint_energy_parseval_hermitian_and_negative():
+    """E_x from <psi, Vx psi> equals the Parseval sum of Eq. 8; Vx is Hermitian
+    (dV inner product) at each k-point; E_x < 0; and one k-point at theta = 0 with
+    real orbitals is the Gamma-point exchange."""
+    base = oracle.Plan((6, 4, 5), (0.4, 0.5, 0.45), (P, D, P), S, fd_order=8)
+    rng = np.random.default_rng(23)
+    theta = np.array([[0.0, 0.0, 0.0], [1.2, 0.0, -0.4], [-2.0, 0.0, 2.5]])
+    wk = np.array([0.5, 0.3, 0.2])
+    n_orb = 2
+    psi = _complex_orbitals(rng, 3, base.N, n_orb)
+    occ = rng.uniform(0.2, 1.0, (3, n_orb))
+    vx, e = oracle.vx_kpoints(base, theta, wk, psi, occ)
+    e_p = oracle.exchange_energy_kpoints(base, theta, wk, psi, occ)
+    assert e < 0 and abs(e - e_p) < 1e-11 * abs(e)
+    a = rng.standard_normal((base.N, 2)) + 1j * rng.standard_normal((base.N, 2))
+    for k in range(3):
+        va = oracle.vx_apply_kpoint(base, theta, wk, psi, occ, k, a)
+        assert abs(np.vdot(a[:, 0], va[:, 1]) - np.conj(np.vdot(a[:, 1], va[:, 0]))) < 1e-11 * np.abs(va).max()
+    psr = rng.standard_normal((base.N, 3))
+    g = np.array([1.0, 0.5, 0.8])
+    vx1, e1 = oracle.vx_kpoints(base, [[0.0, 0.0, 0.0]], [1.0], psr[None].astype(complex), g[None])
+    vref, eref = oracle.vx_apply(base, psr, g)
+    assert np.max(np.abs(vx1[0] - vref)) < 1e-12 * np.abs(vref).max()
+    assert abs(e1 - eref) < 1e-12 * abs(eref)

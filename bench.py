@@ -44,11 +44,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["kronx", "reference"], default="kronx")
     ap.add_argument("--no-extras", action="store_true", help="skip FP64/e2e/oracle legs (profiling runs)")
-    ap.add_argument("--profile-case", choices=["small", "ace", "multipole", "fft"], default=None,
+    ap.add_argument("--profile-case", choices=["small", "ace", "multipole", "fft", "kpoints"], default=None,
                     help="small: one apply of a small case of the same kernels (96^3, 8 orbitals); ace: three "
                          "ACE operator applies at 96^3 with 64 + 64 vectors; multipole: two applies of the "
                          "headline system with boundary values to order 4; fft: the first 64 pairs of the "
-                         "80^3 periodic system on a KX_FFT32 plan, twice; all for ncu captures")
+                         "80^3 periodic system on a KX_FFT32 plan, twice; kpoints: Vx of the 64^3 slab's "
+                         "16 bands at one k-point of its 2 x 2 grid, twice; all for ncu captures")
     return ap.parse_args()
 
 
@@ -70,6 +71,18 @@ def run_profile_case(which="small"):
             vx, ex = kx.kx_vx_apply_pairs(plan, psi, 0, 64)
         torch.cuda.synchronize()
         print(json.dumps({"profile_case": "fft", "e_x": ex.item(), "status": plan.status()}), flush=True)
+        return
+    if which == "kpoints":
+        kd = workloads.K1
+        theta, wk = workloads.kpoint_grid(kd, workloads.K1_KGRID)
+        psi = torch.from_numpy(np.ascontiguousarray(
+            np.transpose(workloads.make_bloch_orbitals(kd, theta), (0, 2, 1)))).cuda()
+        plan = kx.Plan.for_system(kd, precision=kx.KX_F16X3)
+        for _ in range(2):
+            out = kx.kx_vx_apply_kpoint(plan, theta, wk, psi, 1, psi[1])
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "kpoints", "maxabs": out.abs().max().item(), "status": plan.status()}),
+              flush=True)
         return
     if which == "multipole":
         plan = kx.Plan.for_system(SYS, precision=kx.KX_F16X3)
@@ -299,8 +312,9 @@ def measured_traffic(kind, units_per_launch):
 
 def other_workloads(kx, torch, stream, hbm, steps=3):
     """Context lines beside the headline: the split path on the 80^3 periodic
-    screened 256-orbital system (32896 pairs) and the batch of eight systems
-    (26400 pairs) replayed as one CUDA graph."""
+    screened 256-orbital system (32896 pairs), the same system through the FFT
+    variant, the batch of eight systems (26400 pairs) replayed as one CUDA graph,
+    and the Bloch k-point path on the 64^3 slab (4096 pair solves)."""
     res = {}
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -363,6 +377,43 @@ def other_workloads(kx, torch, stream, hbm, steps=3):
     res["c4_batch_8_systems"] = {"ms_per_batch": ms, "pair_solves_per_s": P4 / (ms / 1e3), "pairs": P4,
                                  "status": [p.status() for p in plans]}
     batch.close()
+    del psis, outs, plans
+    # Bloch k-points: the 64^3 slab (periodic x1 and x2, vacuum along x3), 16 bands
+    # on a 2 x 2 k-grid; Vx psi at every k-point is 4 x 4 x 16 x 16 pair solves,
+    # each six complex mode products of 8 n_a N flops (16 N (n1 + n2 + n3) a pair),
+    # in complex float32 on the CUDA cores (float64 plan for the error)
+    kd = workloads.K1
+    theta, wk = workloads.kpoint_grid(kd, workloads.K1_KGRID)
+    psi_k = torch.from_numpy(np.ascontiguousarray(
+        np.transpose(workloads.make_bloch_orbitals(kd, theta), (0, 2, 1)))).cuda()
+    plan_k = kx.Plan.for_system(kd, precision=kx.KX_F16X3)
+    vx_k = torch.empty_like(psi_k)
+    ex_k = torch.empty(1, dtype=torch.float64, device="cuda")
+    kx.kx_vx_kpoints(plan_k, theta, wk, psi_k, out=vx_k, e_x=ex_k, stream=stream)
+    e0.record(stream)
+    for _ in range(steps):
+        kx.kx_vx_kpoints(plan_k, theta, wk, psi_k, out=vx_k, e_x=ex_k, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_k = e0.elapsed_time(e1) / steps
+    plan_k.profile(True)
+    kx.kx_vx_kpoints(plan_k, theta, wk, psi_k, out=vx_k, e_x=ex_k, stream=stream)
+    pr = plan_k.profile_read()
+    plan_k.profile(False)
+    PK = len(wk) ** 2 * kd.n_orb ** 2
+    flops_pair = 16.0 * kd.N * sum(kd.n)
+    tf = flops_pair * PK / (pr["bloch"][0] / 1e3) / 1e12
+    plan_k64 = kx.Plan.for_system(kd, precision=kx.KX_FP64)
+    vx_64, ex_64 = kx.kx_vx_kpoints(plan_k64, theta, wk, psi_k, stream=stream)
+    torch.cuda.synchronize()
+    res["k1_kpoints_slab_64cube_16bands_2x2"] = {
+        "ms_per_apply": ms_k, "pair_solves_per_s": PK / (ms_k / 1e3), "pairs": PK,
+        "mode_products_ms": pr["bloch"][0], "mode_product_launches": pr["bloch"][1],
+        "other_kernels_ms": pr["bloch_other"][0], "e_x": ex_k.item(), "status": plan_k.status(),
+        "vx_maxrel_vs_fp64_plan": float((vx_k - vx_64).abs().max() / vx_64.abs().max()),
+        "e_x_rel_vs_fp64_plan": abs(ex_k.item() - ex_64.item()) / abs(ex_64.item()),
+        "roofline": {"bound": "alu", "achieved": tf, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": tf / FP32_ALU_PEAK_TFLOPS, "algorithmic_flops_per_pair": flops_pair}}
     return res
 
 

@@ -257,6 +257,44 @@ int kx_ace(kx_plan *plan, int n_orb, const double *psi, const double *vx_psi, do
 int kx_ace_apply(kx_plan *plan, int n_xi, const double *xi, int n_vec, const double *phi, double *out,
                  kx_stream stream);
 
+/* Bloch-periodic boundary conditions and k-point sums (Sec. 2.1, Eqs. 6-9;
+ * Sec. 3, Eq. 19 with complex, wavevector-dependent Vk), one spin channel (the
+ * spin sum adds independent channels).  The plan's KX_PERIODIC axes become
+ * Bloch-periodic; its Dirichlet axes (vacuum) ignore the k-point phases.
+ *   n_kpt  number of k-points (1..1024).
+ *   theta  host, n_kpt x 3: phase per cell of each k-point along each axis,
+ *          theta_a = k_a n_a h_a (radians); entries of Dirichlet axes unused.
+ *          The pair (mq, nk) is solved with the Bloch phases theta_k - theta_q.
+ *   wk     host, n_kpt Brillouin-zone weights w_q.
+ *   n_orb  bands per k-point (1..4096).
+ *   psi    in: n_kpt x n_orb x N complex grid values, interleaved (re, im)
+ *          float64 (device, 16-byte aligned), psi[q][m][x].
+ *   occ    in: n_kpt x n_orb occupations g_mq (device) or NULL for 1.
+ * The forward transform contracts each axis with conj(Vk), the inverse with Vk;
+ * along a Bloch axis Vk[x][m] = e^{i (2 pi m + theta) x / n} / sqrt(n).  The mode
+ * products run in complex float64 on the CUDA cores for KX_FP64 plans and in
+ * complex float32 (float64 accumulation of Vx across bands) for the others
+ * (relative error ~1e-6).  Queued on the stream, no host synchronisation.
+ * KX_ERR_UNSUPPORTED for plans with multipole boundary values; KX_ERR_SINGULAR
+ * does not arise past kx_plan_create (an unscreened plan has a Dirichlet axis
+ * or is rejected there). */
+
+/* kx_vx_apply_kpoint — Vx applied to n_vec complex vectors phi (device,
+ * n_vec x N, layout of psi) at k-point k_index:
+ *   out_v = -sum_q w_q sum_m g_mq psi_mq f(L_{k-q}) (conj(psi_mq) phi_v).
+ * out (device, n_vec x N complex) must not overlap psi or phi.  KX_ERR_ARG for
+ * sizes out of range, NULL or misaligned buffers. */
+int kx_vx_apply_kpoint(kx_plan *plan, int n_kpt, const double *theta, const double *wk, int n_orb,
+                       const double *psi, const double *occ, int k_index, int n_vec, const double *phi,
+                       double *out, kx_stream stream);
+
+/* kx_vx_kpoints — Vx psi_nk at every k-point into vx (device, layout of psi,
+ * not overlapping it) and, if ex != NULL, the exchange energy
+ *   E_x = 1/2 dV sum_k w_k sum_n g_nk Re <psi_nk, Vx psi_nk>
+ * (Eq. 8 after the Poisson solves) into ex[0] (device float64). */
+int kx_vx_kpoints(kx_plan *plan, int n_kpt, const double *theta, const double *wk, int n_orb, const double *psi,
+                  const double *occ, double *vx, double *ex, kx_stream stream);
+
 /* kx_batch_create — groups n_sys plans (different grids, kernels and orbital
  * counts) into one CUDA graph that runs every system's kx_vx_apply.  Workspaces
  * are reserved here so that the graph holds no allocation.
@@ -307,7 +345,9 @@ int kx_profile(kx_plan *plan, int enable);
  * 13 ACE combinations of grid vectors (xi = W R^{-1}, -xi P); kind 9 covers
  * the ACE projections over the grid and their reduction; 14 the multipole
  * boundary correction (moments of the sources, correction of the solution,
- * Vx psi and E_x), 15 the DFT passes of KX_FFT32 plans.
+ * Vx psi and E_x), 15 the DFT passes of KX_FFT32 plans, 16 the complex mode
+ * products of the Bloch k-point path, 17 its other kernels (bases, f tables,
+ * conversions, Vx accumulation, E_x sums).
  * Synchronises on the recorded events. */
 int kx_profile_read(kx_plan *plan, int n_kinds, double *ms, long long *launches);
 

@@ -47,6 +47,8 @@ SIGNATURES = {
     "kx_ace": (_c_int, [_vp, _c_int, _vp, _vp, _vp, _vp, _vp]),
     "kx_ace_apply": (_c_int, [_vp, _c_int, _vp, _c_int, _vp, _vp, _vp]),
     "kx_plan_set_multipole": (_c_int, [_vp, _c_int]),
+    "kx_vx_apply_kpoint": (_c_int, [_vp, _c_int, _vp, _vp, _c_int, _vp, _vp, _c_int, _c_int, _vp, _vp, _vp]),
+    "kx_vx_kpoints": (_c_int, [_vp, _c_int, _vp, _vp, _c_int, _vp, _vp, _vp, _vp, _vp]),
     "kx_energy_gradient": (_c_int, [_vp, _c_int, _vp, _vp, _vp, _vp, _vp]),
     "kx_batch_create": (_c_int, [_c_int, _vp, _vp, ctypes.POINTER(_vp)]),
     "kx_batch_run": (_c_int, [_vp, _vp, _vp, _vp, _vp]),
@@ -191,7 +193,8 @@ class Plan:
         return f
 
     PROFILE_KINDS = ["prep", "X3F", "X2F", "X1", "X2I", "X3I", "final", "fp64_mode", "fp64_other", "ace",
-                     "setup", "acc", "slab", "ace_comb", "multipole", "fft"]
+                     "setup", "acc", "slab", "ace_comb", "multipole", "fft", "bloch",
+                     "bloch_other"]
 
     def profile(self, enable=True):
         _check(lib().kx_profile(self.handle, 1 if enable else 0))
@@ -328,6 +331,51 @@ def kx_ace_apply(plan: Plan, xi, phi, out=None, stream=None):
                               _dptr(phi, "phi", torch.float64, (n_vec, plan.N)),
                               _dptr(out, "out", torch.float64, (n_vec, plan.N)), _stream(stream)))
     return out
+
+
+def _kpoint_host(theta, wk):
+    th = [float(x) for row in theta for x in row]
+    w = [float(x) for x in wk]
+    if len(th) != 3 * len(w):
+        raise ValueError("theta must hold 3 phases per k-point")
+    ta = (ctypes.c_double * len(th))(*th)
+    wa = (ctypes.c_double * len(w))(*w)
+    return len(w), ta, wa
+
+
+def kx_vx_apply_kpoint(plan: Plan, theta, wk, psi, k_index: int, phi, occ=None, out=None, stream=None):
+    """Vx at k-point k_index applied to complex vectors phi (n_vec x N, complex128),
+    with the orbitals psi (n_kpt x n_orb x N, complex128) at the k-points whose
+    phases per cell are theta (n_kpt x 3) and weights wk; see kx_vx_apply_kpoint."""
+    torch = _torch()
+    n_kpt, ta, wa = _kpoint_host(theta, wk)
+    n_orb, n_vec = psi.shape[1], phi.shape[0]
+    if out is None:
+        out = torch.empty_like(phi)
+    occ_p = None if occ is None else _dptr(occ, "occ", torch.float64, (n_kpt, n_orb))
+    _check(lib().kx_vx_apply_kpoint(plan.handle, n_kpt, ctypes.cast(ta, _vp), ctypes.cast(wa, _vp), n_orb,
+                                    _dptr(psi, "psi", torch.complex128, (n_kpt, n_orb, plan.N)), occ_p,
+                                    int(k_index), n_vec, _dptr(phi, "phi", torch.complex128, (n_vec, plan.N)),
+                                    _dptr(out, "out", torch.complex128, (n_vec, plan.N)), _stream(stream)))
+    return out
+
+
+def kx_vx_kpoints(plan: Plan, theta, wk, psi, occ=None, out=None, e_x=None, stream=None):
+    """(Vx psi at every k-point, E_x) for complex128 orbitals psi (n_kpt x n_orb x N);
+    see kx_vx_kpoints."""
+    torch = _torch()
+    n_kpt, ta, wa = _kpoint_host(theta, wk)
+    n_orb = psi.shape[1]
+    if out is None:
+        out = torch.empty_like(psi)
+    if e_x is None:
+        e_x = torch.empty(1, dtype=torch.float64, device=psi.device)
+    occ_p = None if occ is None else _dptr(occ, "occ", torch.float64, (n_kpt, n_orb))
+    _check(lib().kx_vx_kpoints(plan.handle, n_kpt, ctypes.cast(ta, _vp), ctypes.cast(wa, _vp), n_orb,
+                               _dptr(psi, "psi", torch.complex128, (n_kpt, n_orb, plan.N)), occ_p,
+                               _dptr(out, "vx", torch.complex128, (n_kpt, n_orb, plan.N)),
+                               _dptr(e_x, "e_x", torch.float64, (1,)), _stream(stream)))
+    return out, e_x
 
 
 def kx_autotune(plan: Plan, n_orb: int, budget_ms: int = 2000):

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libkronx.so")
-SOURCES = ["kx_capi.cu", "kx_setup.cu", "kx_fp64.cu", "kx_tc.cu", "kx_ace.cu", "kx_mp.cu", "kx_fft.cu"]
+SOURCES = ["kx_capi.cu", "kx_setup.cu", "kx_fp64.cu", "kx_tc.cu", "kx_ace.cu", "kx_mp.cu", "kx_fft.cu", "kx_bloch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]

@@ -1,0 +1,607 @@
+// Exact exchange with Bloch-periodic boundary conditions and k-point sums
+// (Sec. 2.1, Eqs. 6-9; Sec. 3, Eq. 19 with complex, wavevector-dependent Vk).
+//
+// For a target k-point and vectors phi_v every k-point q contributes
+//   (Vx phi)_v -= w_q sum_m g_mq psi_mq f(L_{k-q}) (conj(psi_mq) phi_v),
+// the Poisson problem of the pair taking the Bloch phases theta_k - theta_q
+// along the periodic axes.  Along such an axis the Bloch matrix at phase theta
+// has the eigenvectors e^{i kappa_m x} / sqrt(n), kappa_m = (2 pi m + theta) / n,
+// with the stencil's symbol (w_0 + 2 sum_p w_p cos(p kappa_m)) / h^2 as
+// eigenvalue, so the complex basis of each q is written in closed form; Dirichlet
+// axes keep the plan's real eigenvectors.  The forward transform contracts with
+// conj(Vk), the inverse with Vk.  The six complex mode products run on the CUDA
+// cores, in float64 for KX_FP64 plans and in float32 (packed f32x2 FMAs) for the
+// others; the pair density is formed inside the first product and f(Lambda) is
+// applied inside the third.
+#include "kx_internal.h"
+#include "kx_conv.cuh"
+#include "kx_fd.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+
+namespace kx {
+namespace {
+
+template <typename T> struct Cx;
+template <> struct Cx<float> { using t = float2; };
+template <> struct Cx<double> { using t = double2; };
+
+constexpr int kBThreads = 256;
+constexpr int kBWarps = kBThreads / 32;  // output-column groups of a CTA
+template <typename T> constexpr int pencils_per_thread() { return sizeof(T) == 4 ? 2 : 1; }
+template <typename T> constexpr int tile_pencils() { return 32 * pencils_per_thread<T>(); }
+constexpr size_t kBSmemTarget = 110 * 1024;  // two CTAs per SM where the split allows it
+
+template <typename T2> __device__ __forceinline__ T2 cmul_conj(T2 a, T2 b) {  // conj(a) b
+    T2 r;
+    r.x = a.x * b.x + a.y * b.y;
+    r.y = a.x * b.y - a.y * b.x;
+    return r;
+}
+
+// One complex mode product on R grid vectors viewed as [outer][n][inner] (items
+// stacked along outer): out[o][c][i] = sum_k M[k][c] in[o][k][i] for the output
+// columns c in [c0, c0 + ncy) of this CTA's split; pencils q = o * inner + i,
+// QB = 32 PQ of them per CTA.  Warp w owns the output columns c0 + w + 8u
+// (u < U, the operand padded with zero columns up to 8U), lane l the pencils
+// l + 32j (j < PQ).  Chunk-relative indices stay below 2^31 (checked at launch).
+// FORM (first product, inner == 1): the input element of chunk item r is
+// conj(P_m[x]) F_v[x] with (v, m) = divmod(r0 + r, n_orb), formed while loading.
+// SCALE (third product, one pencil plane per item): the output is multiplied by
+// f[c * inner + i], the f(Lambda) diagonal.
+template <typename T, bool FORM, bool SCALE, int U>
+__global__ void __launch_bounds__(kBThreads) bloch_mode_kernel(
+    const typename Cx<T>::t *__restrict__ in, typename Cx<T>::t *__restrict__ out, int n_cols, int n, int inner,
+    const typename Cx<T>::t *__restrict__ M, int nc, int n_split, const T *__restrict__ f,
+    const typename Cx<T>::t *__restrict__ P, const typename Cx<T>::t *__restrict__ F, int n_orb, long long r0,
+    long long N) {
+    using T2 = typename Cx<T>::t;
+    constexpr int PQ = pencils_per_thread<T>();
+    constexpr int QB = 32 * PQ;
+    constexpr int NCP = 8 * U;  // padded operand columns
+    extern __shared__ __align__(16) unsigned char bloch_smem[];
+    T2 *Ms = reinterpret_cast<T2 *>(bloch_smem);  // n x NCP: Ms[k * NCP + cl]
+    T2 *Ts = Ms + (size_t)n * NCP;                // n x (QB + 1): Ts[k * ld + ql]
+    const int ld = QB + 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int split = (int)(blockIdx.x % n_split);
+    const int tile = (int)(blockIdx.x / n_split);
+    const int c0 = split * nc;
+    const int ncy = min(nc, n - c0);
+    for (int k = warp; k < n; k += kBWarps)
+        for (int cl = lane; cl < NCP; cl += 32) {
+            T2 z;
+            z.x = z.y = (T)0;
+            Ms[k * NCP + cl] = cl < ncy ? M[(size_t)k * n + c0 + cl] : z;
+        }
+    const int q0 = tile * QB;
+    const int nq = min(QB, n_cols - q0);
+    int base[PQ];  // element offset of each owned pencil (inner > 1)
+    if (inner == 1) {
+        for (int ql = warp; ql < nq; ql += kBWarps) {
+            const int q = q0 + ql;
+            if constexpr (FORM) {
+                const int ppi = (int)(N / n);  // pencils per item
+                const int r = q / ppi;
+                const long long x0 = (long long)(q - r * ppi) * n;
+                const long long rr = r0 + r;
+                const long long vv = rr / n_orb, m = rr - vv * n_orb;
+                const T2 *Pp = P + m * N + x0;
+                const T2 *Fp = F + vv * N + x0;
+                for (int k = lane; k < n; k += 32) Ts[k * ld + ql] = cmul_conj(Pp[k], Fp[k]);
+            } else {
+                const T2 *src = in + (size_t)q * n;
+                for (int k = lane; k < n; k += 32) Ts[k * ld + ql] = src[k];
+            }
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < PQ; ++j) {
+            const int ql = lane + 32 * j;
+            const int q = q0 + min(ql, nq - 1);
+            const int o = q / inner;
+            base[j] = o * n * inner + (q - o * inner);
+            if (ql < nq)
+                for (int k = warp; k < n; k += kBWarps) Ts[k * ld + ql] = in[base[j] + k * inner];
+        }
+    }
+    __syncthreads();
+
+    T2 res[PQ][U];
+    if constexpr (sizeof(T) == 4) {
+        // (sum a_re v, sum a_im v) as two packed accumulators per output
+        float2 accA[PQ][U], accB[PQ][U];
+#pragma unroll
+        for (int j = 0; j < PQ; ++j)
+#pragma unroll
+            for (int u = 0; u < U; ++u) accA[j][u] = accB[j][u] = make_float2(0.f, 0.f);
+        const float2 *mcol = Ms + warp;
+        const float2 *tcol = Ts + lane;
+#pragma unroll 2
+        for (int k = 0; k < n; ++k) {
+            float2 ar[PQ], ai[PQ];
+#pragma unroll
+            for (int j = 0; j < PQ; ++j) {
+                const float2 a = tcol[k * ld + 32 * j];
+                ar[j] = make_float2(a.x, a.x);
+                ai[j] = make_float2(a.y, a.y);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const float2 v = mcol[k * NCP + 8 * u];
+#pragma unroll
+                for (int j = 0; j < PQ; ++j) {
+                    fma2(accA[j][u], ar[j], v);
+                    fma2(accB[j][u], ai[j], v);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < PQ; ++j)
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                res[j][u] = make_float2(accA[j][u].x - accB[j][u].y, accA[j][u].y + accB[j][u].x);
+    } else {
+#pragma unroll
+        for (int j = 0; j < PQ; ++j)
+#pragma unroll
+            for (int u = 0; u < U; ++u) res[j][u] = make_double2(0.0, 0.0);
+        for (int k = 0; k < n; ++k) {
+#pragma unroll
+            for (int j = 0; j < PQ; ++j) {
+                const double2 a = Ts[k * ld + lane + 32 * j];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const double2 v = Ms[k * NCP + warp + 8 * u];
+                    res[j][u].x = fma(a.x, v.x, fma(-a.y, v.y, res[j][u].x));
+                    res[j][u].y = fma(a.x, v.y, fma(a.y, v.x, res[j][u].y));
+                }
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < PQ; ++j) {
+        const int ql = lane + 32 * j;
+        if (ql >= nq) continue;
+        int i_in = 0;
+        if constexpr (SCALE) i_in = (q0 + ql) % inner;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int cl = warp + 8 * u;
+            if (cl < ncy) {
+                T2 v = res[j][u];
+                if constexpr (SCALE) {
+                    const T fv = f[(size_t)(c0 + cl) * inner + i_in];
+                    v.x *= fv;
+                    v.y *= fv;
+                }
+                Ts[cl * ld + ql] = v;
+            }
+        }
+    }
+    __syncthreads();
+    if (inner == 1) {
+        for (int ql = warp; ql < nq; ql += kBWarps) {
+            T2 *dst = out + (size_t)(q0 + ql) * n + c0;
+            for (int cl = lane; cl < ncy; cl += 32) dst[cl] = Ts[cl * ld + ql];
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < PQ; ++j) {
+            const int ql = lane + 32 * j;
+            if (ql < nq)
+                for (int cl = warp; cl < ncy; cl += kBWarps) out[base[j] + (c0 + cl) * inner] = Ts[cl * ld + ql];
+        }
+    }
+}
+
+struct BlochAxes {
+    int n[3];
+    double h[3];
+    int bc[3];
+    double theta[3];
+    int order;
+    const double *V[3];    // plan's real eigenvectors (Dirichlet axes), V[x][k]
+    const double *lam[3];  // plan's eigenvalues (Dirichlet axes)
+};
+
+// One CTA per axis: the forward operand Mf[k][c] = conj(V[k][c]) and the inverse
+// operand Mi[k][c] = V[c][k] in T, and the eigenvalues lam_out (float64).
+template <typename T>
+__global__ void bloch_basis_kernel(BlochAxes ax, typename Cx<T>::t *Mf0, typename Cx<T>::t *Mf1,
+                                   typename Cx<T>::t *Mf2, typename Cx<T>::t *Mi0, typename Cx<T>::t *Mi1,
+                                   typename Cx<T>::t *Mi2, double *lam0, double *lam1, double *lam2) {
+    using T2 = typename Cx<T>::t;
+    const int a = blockIdx.x;
+    const int n = ax.n[a];
+    T2 *Mf = a == 0 ? Mf0 : (a == 1 ? Mf1 : Mf2);
+    T2 *Mi = a == 0 ? Mi0 : (a == 1 ? Mi1 : Mi2);
+    double *lam = a == 0 ? lam0 : (a == 1 ? lam1 : lam2);
+    const bool bloch = ax.bc[a] == KX_PERIODIC;
+    const double th = ax.theta[a];
+    const double inv_sqrt_n = 1.0 / sqrt((double)n);
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        int x = e / n, m = e - x * n;
+        double vr, vi;
+        if (bloch) {
+            // e^{i 2 pi m x / n} with the angle reduced exactly, times e^{i theta x / n}
+            int t = (int)(((long long)m * x) % n);
+            double s1, c1, s2, c2;
+            sincospi(2.0 * t / n, &s1, &c1);
+            sincos(th * x / n, &s2, &c2);
+            vr = (c1 * c2 - s1 * s2) * inv_sqrt_n;
+            vi = (s1 * c2 + c1 * s2) * inv_sqrt_n;
+        } else {
+            vr = ax.V[a][x * n + m];
+            vi = 0.0;
+        }
+        T2 v;
+        v.x = (T)vr;
+        v.y = (T)vi;
+        Mi[m * n + x] = v;
+        v.y = -v.y;
+        Mf[x * n + m] = v;
+    }
+    const int mo = ax.order / 2;
+    const double ih2 = 1.0 / (ax.h[a] * ax.h[a]);
+    for (int m = threadIdx.x; m < n; m += blockDim.x) {
+        if (bloch) {
+            double kap = (2.0 * M_PI * m + th) / n;
+            double s = fd_weight(mo, 0);
+            for (int p = 1; p <= mo; ++p) s += 2.0 * fd_weight(mo, p) * cos(p * kap);
+            lam[m] = s * ih2;
+        } else {
+            lam[m] = ax.lam[a][m];
+        }
+    }
+}
+
+template <typename T>
+__global__ void bloch_ftable_kernel(int n1, int n2, int n3, const double *l1, const double *l2, const double *l3,
+                                    int kind, double omega, T *f) {
+    const long long N = (long long)n1 * n2 * n3;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N;
+         idx += (long long)gridDim.x * blockDim.x) {
+        int k1 = (int)(idx % n1);
+        int k2 = (int)((idx / n1) % n2);
+        int k3 = (int)(idx / ((long long)n1 * n2));
+        f[idx] = (T)kernel_f_value(kind, omega, l1[k1] + l2[k2] + l3[k3]);
+    }
+}
+
+// complex float64 -> float32 (count complex values)
+__global__ void bloch_to_f32_kernel(const double2 *__restrict__ src, float2 *__restrict__ dst, long long count) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
+         e += (long long)gridDim.x * blockDim.x) {
+        double2 v = src[e];
+        dst[e] = make_float2(f64_to_f32(v.x), f64_to_f32(v.y));
+    }
+}
+
+// out_v[x] -= sum over the chunk items r = v * n_orb + m in [r0, r1) of
+// w_q g_mq psi_m[x] X_{r - r0}[x] (m ascending, one thread per (v, x)).
+template <typename T>
+__global__ void bloch_accum_kernel(const typename Cx<T>::t *__restrict__ X, long long r0, long long r1, int n_orb,
+                                   const typename Cx<T>::t *__restrict__ P, const double *__restrict__ occ_q,
+                                   double wq, double2 *__restrict__ out, long long N) {
+    using T2 = typename Cx<T>::t;
+    const long long v_lo = r0 / n_orb, v_hi = (r1 - 1) / n_orb;
+    const long long total = (v_hi - v_lo + 1) * N;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        long long vl = e / N, x = e - vl * N;
+        long long v = v_lo + vl;
+        long long m0 = max(0LL, r0 - v * n_orb), m1 = min((long long)n_orb, r1 - v * n_orb);
+        T sr = 0, si = 0;
+        for (long long m = m0; m < m1; ++m) {
+            T2 p = P[m * N + x];
+            T2 xx = X[(v * n_orb + m - r0) * N + x];
+            T c = (T)(wq * (occ_q ? occ_q[m] : 1.0));
+            sr = fma(c, p.x * xx.x - p.y * xx.y, sr);
+            si = fma(c, p.x * xx.y + p.y * xx.x, si);
+        }
+        double2 o = out[v * N + x];
+        if constexpr (sizeof(T) == 4) {
+            o.x -= f32_to_f64(sr);
+            o.y -= f32_to_f64(si);
+        } else {
+            o.x -= sr;
+            o.y -= si;
+        }
+        out[v * N + x] = o;
+    }
+}
+
+// partial[k * nb + b] = w_k sum_n g_kn sum_x Re(conj(psi_kn[x]) vx_kn[x]) over a
+// grid-stride share (block b of nb).
+constexpr int kEThreads = 256;
+__global__ void __launch_bounds__(kEThreads) bloch_energy_kernel(const double2 *__restrict__ psi,
+                                                                const double2 *__restrict__ vx,
+                                                                const double *__restrict__ occ_k, int n_orb,
+                                                                long long N, double wk, double *partial) {
+    double s = 0.0;
+    const long long total = (long long)n_orb * N;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        double2 a = psi[e], b = vx[e];
+        double g = occ_k ? occ_k[e / N] : 1.0;
+        s += g * (a.x * b.x + a.y * b.y);
+    }
+    __shared__ double red[kEThreads / 32];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kEThreads / 32; ++w) t += red[w];
+        partial[blockIdx.x] = wk * t;
+    }
+}
+
+__global__ void bloch_energy_final_kernel(const double *partial, int count, double half_dv, double *ex) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < count; ++i) t += partial[i];
+        *ex = half_dv * t;
+    }
+}
+
+inline size_t al256(size_t b) { return (b + 255) / 256 * 256; }
+
+// Output columns per CTA split for an axis of n points: all n where the shared
+// memory allows two CTAs per SM, else halves; the per-thread output count U
+// rounds the split up to 8U columns from the instantiated set.
+template <typename T> int outputs_for(int nc) {
+    const int need = (nc + kBWarps - 1) / kBWarps;
+    if (sizeof(T) == 8) return need <= 2 ? 2 : (need <= 4 ? 4 : 8);
+    return need <= 2 ? 2 : need <= 4 ? 4 : need <= 6 ? 6 : need <= 8 ? 8 : need <= 12 ? 12 : 16;
+}
+
+template <typename T>
+void choose_split(int n, int *nc, int *n_split, int *U, size_t *smem) {
+    using T2 = typename Cx<T>::t;
+    const int max_cols = kBWarps * (sizeof(T) == 4 ? 16 : 8);
+    auto bytes = [n](int u) { return sizeof(T2) * ((size_t)n * 8 * u + (size_t)n * (tile_pencils<T>() + 1)); };
+    int c = std::min(n, max_cols);
+    while (bytes(outputs_for<T>(c)) > kBSmemTarget && c > kBWarps) c = (c + 1) / 2;
+    *nc = c;
+    *n_split = (n + c - 1) / c;
+    *U = outputs_for<T>(c);
+    *smem = bytes(*U);
+}
+
+template <typename T, bool FORM, bool SCALE, int U>
+int launch_mode_u(unsigned blocks, size_t smem, cudaStream_t s, const typename Cx<T>::t *in,
+                  typename Cx<T>::t *out, int n_cols, int n, int inner, const typename Cx<T>::t *M, int nc,
+                  int n_split, const T *f, const typename Cx<T>::t *P, const typename Cx<T>::t *F, int n_orb,
+                  long long r0, long long N) {
+    static bool attr = false;  // once per instantiation
+    if (!attr) {
+        KX_CUDA_TRY(cudaFuncSetAttribute(bloch_mode_kernel<T, FORM, SCALE, U>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        attr = true;
+    }
+    bloch_mode_kernel<T, FORM, SCALE, U><<<blocks, kBThreads, smem, s>>>(in, out, n_cols, n, inner, M, nc, n_split,
+                                                                         f, P, F, n_orb, r0, N);
+    KX_LAUNCH_CHECK("bloch_mode_kernel launch");
+    return KX_OK;
+}
+
+template <typename T, bool FORM, bool SCALE>
+int launch_mode(kx_plan *p, int axis, long long R, const typename Cx<T>::t *in, typename Cx<T>::t *out,
+                const typename Cx<T>::t *M, const T *f, const typename Cx<T>::t *P,
+                const typename Cx<T>::t *F, int n_orb, long long r0, cudaStream_t s) {
+    const int n = p->n[axis];
+    const long long N = (long long)p->N;
+    const int inner = axis == 0 ? 1 : (axis == 1 ? p->n[0] : p->n[0] * p->n[1]);
+    const long long n_cols = R * (N / n);
+    int nc, n_split, U;
+    size_t smem;
+    choose_split<T>(n, &nc, &n_split, &U, &smem);
+    const long long blocks = (n_cols + tile_pencils<T>() - 1) / tile_pencils<T>() * n_split;
+    if (R * N >= (1LL << 31) || blocks > 0x7fffffffLL)
+        return set_error(KX_ERR_ARG, "Bloch exchange: chunk too large for one launch");
+    if (int rc = prof_begin(p, PK_BLOCH, s)) return rc;
+    const unsigned b = (unsigned)blocks;
+    const int nco = (int)n_cols;
+#define KX_BLOCH_LAUNCH(UU) \
+    launch_mode_u<T, FORM, SCALE, UU>(b, smem, s, in, out, nco, n, inner, M, nc, n_split, f, P, F, n_orb, r0, N)
+    int rc;
+    if (U == 2) rc = KX_BLOCH_LAUNCH(2);
+    else if (U == 4) rc = KX_BLOCH_LAUNCH(4);
+    else if (U == 8) rc = KX_BLOCH_LAUNCH(8);
+    else if constexpr (sizeof(T) == 4) {
+        if (U == 6) rc = KX_BLOCH_LAUNCH(6);
+        else if (U == 12) rc = KX_BLOCH_LAUNCH(12);
+        else rc = KX_BLOCH_LAUNCH(16);
+    } else {
+        rc = set_error(KX_ERR_ARG, "Bloch exchange: no kernel for this split");
+    }
+#undef KX_BLOCH_LAUNCH
+    if (rc) return rc;
+    return prof_end(p, s);
+}
+
+// Device workspace of one call: bases, eigenvalues, f table, float32 copies of
+// the orbitals and vectors (float32 plans), chunk buffers A and B.
+struct BlochLayout {
+    size_t Mf[3], Mi[3], lam[3], f, P, F, A, B, partial, total;
+    long long chunk;
+};
+
+template <typename T>
+BlochLayout bloch_layout(const kx_plan *p, int n_orb, int n_vec, int n_kpt) {
+    using T2 = typename Cx<T>::t;
+    BlochLayout L;
+    const size_t N = p->N;
+    size_t off = 0;
+    for (int a = 0; a < 3; ++a) {
+        L.Mf[a] = off;
+        off += al256(sizeof(T2) * p->n[a] * p->n[a]);
+        L.Mi[a] = off;
+        off += al256(sizeof(T2) * p->n[a] * p->n[a]);
+        L.lam[a] = off;
+        off += al256(sizeof(double) * p->n[a]);
+    }
+    L.f = off;
+    off += al256(sizeof(T) * N);
+    const bool f32 = sizeof(T) == 4;
+    L.P = off;
+    off += f32 ? al256(sizeof(T2) * N * n_orb) : 0;
+    L.F = off;
+    off += f32 ? al256(sizeof(T2) * N * n_vec) : 0;
+    L.partial = off;
+    off += al256(sizeof(double) * 2 * p->num_sms * (size_t)std::max(1, n_kpt));
+    const long long pairs = (long long)n_orb * n_vec;
+    const size_t budget = (size_t)2 << 30;  // both chunk buffers
+    long long chunk = (long long)std::max<size_t>(1, budget / (2 * sizeof(T2) * N));
+    if (const char *e = std::getenv("KX_CHUNK_PAIRS"))  // tuning override (pairs per chunk)
+        if (std::atoll(e) > 0) chunk = std::min(chunk, std::atoll(e));
+    chunk = std::min(chunk, pairs);
+    L.chunk = chunk;
+    L.A = off;
+    off += al256(sizeof(T2) * N * chunk);
+    L.B = off;
+    off += al256(sizeof(T2) * N * chunk);
+    L.total = off;
+    return L;
+}
+
+// Vx of the vectors phi at k-point k (out overwritten, or accumulated into when
+// !zero_out).  psi: n_kpt x n_orb x N complex, occ: n_kpt x n_orb (nullable).
+template <typename T>
+int bloch_run(kx_plan *p, int n_kpt, const double *theta, const double *wk, int n_orb, const double *psi,
+              const double *occ, int k, int n_vec, const double *phi, double *out, cudaStream_t s) {
+    using T2 = typename Cx<T>::t;
+    const long long N = (long long)p->N;
+    BlochLayout L = bloch_layout<T>(p, n_orb, n_vec, n_kpt);
+    if (int rc = ensure_workspace(p, L.total)) return rc;
+    char *ws = static_cast<char *>(p->ws.ptr);
+    T2 *Mf[3], *Mi[3];
+    double *lam[3];
+    for (int a = 0; a < 3; ++a) {
+        Mf[a] = reinterpret_cast<T2 *>(ws + L.Mf[a]);
+        Mi[a] = reinterpret_cast<T2 *>(ws + L.Mi[a]);
+        lam[a] = reinterpret_cast<double *>(ws + L.lam[a]);
+    }
+    T *f = reinterpret_cast<T *>(ws + L.f);
+    T2 *A = reinterpret_cast<T2 *>(ws + L.A);
+    T2 *B = reinterpret_cast<T2 *>(ws + L.B);
+    const bool f32 = sizeof(T) == 4;
+    const int blocks = 4 * p->num_sms;
+    KX_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(double2) * (size_t)N * n_vec, s));
+    const T2 *F;
+    if (f32) {
+        T2 *Fw = reinterpret_cast<T2 *>(ws + L.F);
+        if (int rc = prof_begin(p, PK_BLOCH_OTHER, s)) return rc;
+        bloch_to_f32_kernel<<<blocks, 256, 0, s>>>(reinterpret_cast<const double2 *>(phi),
+                                                   reinterpret_cast<float2 *>(Fw), N * n_vec);
+        KX_LAUNCH_CHECK("bloch_to_f32_kernel launch");
+        if (int rc = prof_end(p, s)) return rc;
+        F = Fw;
+    } else {
+        F = reinterpret_cast<const T2 *>(phi);
+    }
+    BlochAxes ax;
+    for (int a = 0; a < 3; ++a) {
+        ax.n[a] = p->n[a];
+        ax.h[a] = p->h[a];
+        ax.bc[a] = p->bc[a];
+        ax.V[a] = p->d_V[a];
+        ax.lam[a] = p->d_lam[a];
+    }
+    ax.order = p->fd_order;
+    const long long pairs = (long long)n_orb * n_vec;
+    for (int q = 0; q < n_kpt; ++q) {
+        for (int a = 0; a < 3; ++a) ax.theta[a] = theta[3 * k + a] - theta[3 * q + a];
+        if (int rc = prof_begin(p, PK_BLOCH_OTHER, s)) return rc;
+        bloch_basis_kernel<T><<<3, 256, 0, s>>>(ax, Mf[0], Mf[1], Mf[2], Mi[0], Mi[1], Mi[2], lam[0], lam[1],
+                                                lam[2]);
+        KX_LAUNCH_CHECK("bloch_basis_kernel launch");
+        bloch_ftable_kernel<T><<<blocks, 256, 0, s>>>(p->n[0], p->n[1], p->n[2], lam[0], lam[1], lam[2], p->kind,
+                                                      p->omega, f);
+        KX_LAUNCH_CHECK("bloch_ftable_kernel launch");
+        const T2 *Pq;
+        const double2 *psi_q = reinterpret_cast<const double2 *>(psi) + (size_t)q * n_orb * N;
+        if (f32) {
+            T2 *Pw = reinterpret_cast<T2 *>(ws + L.P);
+            bloch_to_f32_kernel<<<blocks, 256, 0, s>>>(psi_q, reinterpret_cast<float2 *>(Pw), N * n_orb);
+            KX_LAUNCH_CHECK("bloch_to_f32_kernel launch");
+            Pq = Pw;
+        } else {
+            Pq = reinterpret_cast<const T2 *>(psi_q);
+        }
+        if (int rc = prof_end(p, s)) return rc;
+        const double *occ_q = occ ? occ + (size_t)q * n_orb : nullptr;
+        for (long long r0 = 0; r0 < pairs; r0 += L.chunk) {
+            const long long r1 = std::min(pairs, r0 + L.chunk);
+            const long long R = r1 - r0;
+            int rc;
+            if ((rc = launch_mode<T, true, false>(p, 0, R, nullptr, A, Mf[0], nullptr, Pq, F, n_orb, r0, s))) return rc;
+            if ((rc = launch_mode<T, false, false>(p, 1, R, A, B, Mf[1], nullptr, nullptr, nullptr, n_orb, 0, s)))
+                return rc;
+            if ((rc = launch_mode<T, false, true>(p, 2, R, B, A, Mf[2], f, nullptr, nullptr, n_orb, 0, s))) return rc;
+            if ((rc = launch_mode<T, false, false>(p, 2, R, A, B, Mi[2], nullptr, nullptr, nullptr, n_orb, 0, s)))
+                return rc;
+            if ((rc = launch_mode<T, false, false>(p, 1, R, B, A, Mi[1], nullptr, nullptr, nullptr, n_orb, 0, s)))
+                return rc;
+            if ((rc = launch_mode<T, false, false>(p, 0, R, A, B, Mi[0], nullptr, nullptr, nullptr, n_orb, 0, s)))
+                return rc;
+            if ((rc = prof_begin(p, PK_BLOCH_OTHER, s))) return rc;
+            const long long nv = (r1 - 1) / n_orb - r0 / n_orb + 1;
+            const int ab = (int)std::min<long long>((nv * N + 255) / 256, 8LL * p->num_sms);
+            bloch_accum_kernel<T><<<ab, 256, 0, s>>>(B, r0, r1, n_orb, Pq, occ_q, wk[q],
+                                                     reinterpret_cast<double2 *>(out), N);
+            KX_LAUNCH_CHECK("bloch_accum_kernel launch");
+            if ((rc = prof_end(p, s))) return rc;
+        }
+    }
+    return KX_OK;
+}
+
+template <typename T>
+int bloch_all(kx_plan *p, int n_kpt, const double *theta, const double *wk, int n_orb, const double *psi,
+              const double *occ, double *vx, double *ex, cudaStream_t s) {
+    const size_t N = p->N;
+    for (int k = 0; k < n_kpt; ++k) {
+        const size_t off = (size_t)k * n_orb * N * 2;
+        if (int rc = bloch_run<T>(p, n_kpt, theta, wk, n_orb, psi, occ, k, n_orb, psi + off, vx + off, s))
+            return rc;
+    }
+    if (!ex) return KX_OK;
+    BlochLayout L = bloch_layout<T>(p, n_orb, n_orb, n_kpt);
+    double *partial = reinterpret_cast<double *>(static_cast<char *>(p->ws.ptr) + L.partial);
+    const int nb = 2 * p->num_sms;
+    if (int rc = prof_begin(p, PK_BLOCH_OTHER, s)) return rc;
+    for (int k = 0; k < n_kpt; ++k) {
+        const size_t off = (size_t)k * n_orb * N;
+        bloch_energy_kernel<<<nb, kEThreads, 0, s>>>(reinterpret_cast<const double2 *>(psi) + off,
+                                                     reinterpret_cast<const double2 *>(vx) + off,
+                                                     occ ? occ + (size_t)k * n_orb : nullptr, n_orb, (long long)N,
+                                                     wk[k], partial + (size_t)k * nb);
+        KX_LAUNCH_CHECK("bloch_energy_kernel launch");
+    }
+    bloch_energy_final_kernel<<<1, 32, 0, s>>>(partial, nb * n_kpt, 0.5 * p->dV, ex);
+    KX_LAUNCH_CHECK("bloch_energy_final_kernel launch");
+    return prof_end(p, s);
+}
+
+}  // namespace
+
+int bloch_vx_apply(kx_plan *p, int n_kpt, const double *theta, const double *wk, int n_orb, const double *psi,
+                   const double *occ, int k, int n_vec, const double *phi, double *out, cudaStream_t s) {
+    return p->precision == KX_FP64 ? bloch_run<double>(p, n_kpt, theta, wk, n_orb, psi, occ, k, n_vec, phi, out, s)
+                                   : bloch_run<float>(p, n_kpt, theta, wk, n_orb, psi, occ, k, n_vec, phi, out, s);
+}
+
+int bloch_vx_all(kx_plan *p, int n_kpt, const double *theta, const double *wk, int n_orb, const double *psi,
+                 const double *occ, double *vx, double *ex, cudaStream_t s) {
+    return p->precision == KX_FP64 ? bloch_all<double>(p, n_kpt, theta, wk, n_orb, psi, occ, vx, ex, s)
+                                   : bloch_all<float>(p, n_kpt, theta, wk, n_orb, psi, occ, vx, ex, s);
+}
+
+}  // namespace kx

@@ -2,6 +2,8 @@
 // float64 and tensor-core paths, CUDA-graph batches and the launch-shape tuner.
 #include "kx_internal.h"
 
+#include <cmath>
+#include <cstdint>
 #include <algorithm>
 #include <chrono>
 #include <cstdio>
@@ -490,6 +492,53 @@ int kx_ace_apply(kx_plan *plan, int n_xi, const double *xi, int n_vec, const dou
     if (overlaps(out, (size_t)n_vec, xi, (size_t)n_xi) || overlaps(out, (size_t)n_vec, phi, (size_t)n_vec))
         return set_error(KX_ERR_ARG, "kx_ace_apply: out must not overlap xi or phi");
     return ace_apply_run(plan, n_xi, xi, n_vec, phi, out, reinterpret_cast<cudaStream_t>(stream));
+}
+
+namespace {
+int check_kpoints(kx_plan *plan, const char *fn, int n_kpt, const double *theta, const double *wk, int n_orb,
+                  const double *psi) {
+    if (n_kpt < 1 || n_kpt > 1024) return set_error(KX_ERR_ARG, std::string(fn) + ": n_kpt must be in 1..1024");
+    if (n_orb < 1 || n_orb > 4096) return set_error(KX_ERR_ARG, std::string(fn) + ": n_orb must be in 1..4096");
+    if (!theta || !wk || !psi) return set_error(KX_ERR_ARG, std::string(fn) + ": NULL argument");
+    for (int i = 0; i < 3 * n_kpt; ++i)
+        if (!std::isfinite(theta[i])) return set_error(KX_ERR_ARG, std::string(fn) + ": non-finite phase");
+    for (int i = 0; i < n_kpt; ++i)
+        if (!std::isfinite(wk[i])) return set_error(KX_ERR_ARG, std::string(fn) + ": non-finite weight");
+    if (plan->mp_lmax >= 0)
+        return set_error(KX_ERR_UNSUPPORTED, std::string(fn) + ": plans with multipole boundary values are isolated");
+    return KX_OK;
+}
+bool misaligned16(const void *p) { return reinterpret_cast<uintptr_t>(p) % 16 != 0; }
+}  // namespace
+
+int kx_vx_apply_kpoint(kx_plan *plan, int n_kpt, const double *theta, const double *wk, int n_orb,
+                       const double *psi, const double *occ, int k_index, int n_vec, const double *phi,
+                       double *out, kx_stream stream) {
+    if (int rc = check_plan(plan)) return rc;
+    if (int rc = check_kpoints(plan, "kx_vx_apply_kpoint", n_kpt, theta, wk, n_orb, psi)) return rc;
+    if (k_index < 0 || k_index >= n_kpt) return set_error(KX_ERR_ARG, "kx_vx_apply_kpoint: k_index out of range");
+    if (n_vec < 1 || n_vec > 4096) return set_error(KX_ERR_ARG, "kx_vx_apply_kpoint: n_vec must be in 1..4096");
+    if (!phi || !out) return set_error(KX_ERR_ARG, "kx_vx_apply_kpoint: NULL buffer");
+    if (misaligned16(psi) || misaligned16(phi) || misaligned16(out))
+        return set_error(KX_ERR_ARG, "kx_vx_apply_kpoint: complex buffers must be 16-byte aligned");
+    const size_t c = 2 * plan->N;
+    auto overlaps = [](const double *a, size_t na, const double *b, size_t nb) { return a < b + nb && b < a + na; };
+    if (overlaps(out, c * n_vec, psi, c * n_orb * (size_t)n_kpt) || overlaps(out, c * n_vec, phi, c * n_vec))
+        return set_error(KX_ERR_ARG, "kx_vx_apply_kpoint: out must not overlap psi or phi");
+    return bloch_vx_apply(plan, n_kpt, theta, wk, n_orb, psi, occ, k_index, n_vec, phi, out,
+                          reinterpret_cast<cudaStream_t>(stream));
+}
+
+int kx_vx_kpoints(kx_plan *plan, int n_kpt, const double *theta, const double *wk, int n_orb, const double *psi,
+                  const double *occ, double *vx, double *ex, kx_stream stream) {
+    if (int rc = check_plan(plan)) return rc;
+    if (int rc = check_kpoints(plan, "kx_vx_kpoints", n_kpt, theta, wk, n_orb, psi)) return rc;
+    if (!vx) return set_error(KX_ERR_ARG, "kx_vx_kpoints: NULL buffer");
+    if (misaligned16(psi) || misaligned16(vx))
+        return set_error(KX_ERR_ARG, "kx_vx_kpoints: complex buffers must be 16-byte aligned");
+    const size_t c = 2 * plan->N * (size_t)n_orb * n_kpt;
+    if (vx < psi + c && psi < vx + c) return set_error(KX_ERR_ARG, "kx_vx_kpoints: vx must not overlap psi");
+    return bloch_vx_all(plan, n_kpt, theta, wk, n_orb, psi, occ, vx, ex, reinterpret_cast<cudaStream_t>(stream));
 }
 
 namespace kx {

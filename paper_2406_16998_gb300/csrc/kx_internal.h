@@ -54,7 +54,7 @@ struct TuneParams {
 
 // Per-launch CUDA-event timing by kernel kind (kx_profile / kx_profile_read).
 enum ProfKind { PK_PREP = 0, PK_X3F, PK_X2F, PK_X1, PK_X2I, PK_X3I, PK_FINAL, PK_FP64_MODE, PK_FP64_OTHER,
-                PK_ACE, PK_SETUP, PK_ACC, PK_SLAB, PK_ACE_COMB, PK_MP, PK_FFT, PK_COUNT };
+                PK_ACE, PK_SETUP, PK_ACC, PK_SLAB, PK_ACE_COMB, PK_MP, PK_FFT, PK_BLOCH, PK_BLOCH_OTHER, PK_COUNT };
 struct Profiler {
     bool on = false;
     std::vector<cudaEvent_t> pool;       // reusable events
@@ -190,6 +190,16 @@ size_t fft_partial_count(const kx_plan *p, long chunk);
 // (R x N), output real part into out32 (fp32) or out64; energy into ex
 int fft_passes(kx_plan *p, long R, const int2 *pairs, const float *src32, int rhs, const double *occ, float2 *C,
                float *out32, double *out64, double *ex, double *partial, bool energy_only, cudaStream_t s);
+
+// ---- Bloch-periodic boundary conditions and k-point sums (kx_bloch.cu)
+// Vx of n_vec complex vectors phi at k-point k (out overwritten); psi is
+// n_kpt x n_orb x N complex (interleaved float64), occ n_kpt x n_orb (nullable),
+// theta (n_kpt x 3) and wk (n_kpt) host arrays.
+int bloch_vx_apply(kx_plan *p, int n_kpt, const double *theta, const double *wk, int n_orb, const double *psi,
+                   const double *occ, int k, int n_vec, const double *phi, double *out, cudaStream_t s);
+// Vx psi_nk for every k-point (vx like psi) and, if ex, E_x into ex[0].
+int bloch_vx_all(kx_plan *p, int n_kpt, const double *theta, const double *wk, int n_orb, const double *psi,
+                 const double *occ, double *vx, double *ex, cudaStream_t s);
 
 // ---- multipole boundary values (kx_mp.cu)
 int mp_set(kx_plan *p, int l_max);

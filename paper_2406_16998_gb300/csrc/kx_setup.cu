@@ -6,6 +6,7 @@
 // Sec. 3, Eq. 13: Lk Vk = Vk Lambda_k; Vk orthogonal (Lk symmetric).
 // Sec. 3, Eq. 19: the scaling diagonal holds f(l1_i + l2_j + l3_k).
 #include "kx_internal.h"
+#include "kx_fd.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -16,21 +17,6 @@ namespace {
 
 constexpr int kEigThreads = 256;
 constexpr int kMaxSweeps = 40;
-
-// Centred weight w_p (unit spacing) of the order-2m second-derivative stencil:
-// w_0 = -2 sum_{q=1}^m 1/q^2,  w_p = 2 (-1)^{p+1} (m!)^2 / (p^2 (m-p)! (m+p)!).
-// The ratio (m!)^2 / ((m-p)!(m+p)!) is formed as a product to stay exact-ish.
-__device__ double fd_weight(int m, int p) {
-    if (p == 0) {
-        double s = 0.0;
-        for (int q = 1; q <= m; ++q) s += 1.0 / ((double)q * q);
-        return -2.0 * s;
-    }
-    double r = 1.0;  // prod_{q=1}^{p} (m - p + q) / (m + q) = m! m! / ((m-p)! (m+p)!)
-    for (int q = 1; q <= p; ++q) r *= (double)(m - p + q) / (double)(m + q);
-    double sgn = (p % 2 == 1) ? 1.0 : -1.0;
-    return 2.0 * sgn * r / ((double)p * p);
-}
 
 // One CTA per axis: build Lk in shared memory, diagonalise it by cyclic Jacobi
 // with a round-robin (tournament) ordering so that n/2 disjoint rotations are
@@ -207,15 +193,7 @@ __global__ void ftable_kernel(int n1, int n2, int n3, const double *l1, const do
         int k1 = (int)(idx % n1);
         int k2 = (int)((idx / n1) % n2);
         int k3 = (int)(idx / ((size_t)n1 * n2));
-        double lam = l1[k1] + l2[k2] + l3[k3];
-        double mu = -lam;
-        double f;
-        if (kind == KX_UNSCREENED) {
-            f = 4.0 * M_PI / mu;
-        } else {
-            double a = 4.0 * omega * omega;
-            f = (mu == 0.0) ? M_PI / (omega * omega) : -4.0 * M_PI * expm1(-mu / a) / mu;
-        }
+        double f = kernel_f_value(kind, omega, l1[k1] + l2[k2] + l3[k3]);
         f64[idx] = f;
         f32[idx] = (float)f;
     }

@@ -815,3 +815,148 @@ def test_autotune_then_apply(kx):
     assert plan.status() == kx.KX_OK
     assert relmax(vx.cpu().numpy().T, vx_ref) < TOL[1]["vx"]
     assert abs(ex.item() - ex_ref) < TOL[1]["ex"] * abs(ex_ref)
+
+
+# ---------------------------------------------------------------- Bloch k-points
+# Complex float32 mode products (plans other than KX_FP64): each of the six
+# products sums n float32 terms (relative error ~n 2^-24), so Vx psi is held to
+# 2e-5 of its largest entry and E_x (a float64 sum of many such values) to 2e-6.
+TOL_K = {0: (1e-11, 1e-11), 1: (2e-5, 2e-6), 2: (2e-5, 2e-6)}
+KPOINT_CASES = [
+    # n, h, bc, kind, n_orb, k-grid, phase shift, precision
+    ((12, 10, 14), (0.45, 0.5, 0.4), (P, P, D), U, 3, (2, 2, 1), (0.0, 0.0), 0),   # slab
+    ((16, 8, 16), (0.45, 0.5, 0.4), (P, P, D), U, 3, (2, 2, 1), (0.0, 0.0), 1),
+    ((10, 12, 9), (0.5, 0.45, 0.5), (P, P, P), S, 2, (3, 1, 1), (0.4, -0.3), 0),  # bulk, shifted grid
+    ((10, 12, 9), (0.5, 0.45, 0.5), (P, P, P), S, 2, (3, 1, 1), (0.4, -0.3), 2),
+    ((9, 20, 11), (0.5, 0.4, 0.5), (D, P, D), U, 3, (1, 3, 1), (0.0, 0.0), 0),    # wire
+    ((8, 24, 16), (0.5, 0.4, 0.5), (D, P, D), S, 2, (1, 3, 1), (0.0, 0.0), 1),
+    ((100, 6, 5), (0.3, 0.5, 0.5), (P, D, D), U, 2, (2, 1, 1), (0.0, 0.0), 0),    # several column splits
+    ((128, 8, 8), (0.3, 0.5, 0.5), (P, D, D), S, 2, (2, 1, 1), (0.0, 0.0), 1),
+]
+
+
+def kpoint_inputs(case, seed):
+    n, h, bc, kind, n_orb, counts, shift, prec = KPOINT_CASES[case]
+    sysd = system(n, h, bc, kind, n_orb, seed)
+    theta, wk = workloads.kpoint_grid(sysd, counts)
+    theta[:, 0] += shift[0] if bc[0] == P else 0.0
+    theta[:, 1] += shift[1] if bc[1] == P else 0.0
+    psi = workloads.make_bloch_orbitals(sysd, theta)
+    occ = np.random.default_rng(seed).uniform(0.3, 1.0, (len(wk), n_orb))
+    return sysd, theta, wk, psi, occ, prec
+
+
+def to_dev_orbitals(psi):
+    return dev(np.transpose(psi, (0, 2, 1)))  # (n_kpt, n_orb, N) complex128
+
+
+@pytest.mark.parametrize("case", range(len(KPOINT_CASES)))
+def test_kpoint_vx_and_energy_match_oracle(kx, case):
+    sysd, theta, wk, psi, occ, prec = kpoint_inputs(case, 300 + case)
+    base = oracle.Plan(sysd.n, sysd.h, sysd.bc, sysd.kernel)
+    vx_ref, ex_ref = oracle.vx_kpoints(base, theta, wk, psi, occ)
+    plan = kx.Plan(sysd.n, sysd.h, sysd.bc, sysd.kernel, precision=prec)
+    plan.profile(True)
+    vx, ex = kx.kx_vx_kpoints(plan, theta, wk, to_dev_orbitals(psi), dev(occ))
+    torch.cuda.synchronize()
+    prof = plan.profile_read()
+    vx = vx.cpu().numpy().transpose(0, 2, 1)
+    assert relmax(vx, vx_ref) < TOL_K[prec][0]
+    assert abs(ex.item() - ex_ref) < TOL_K[prec][1] * abs(ex_ref)
+    n_k = len(wk)
+    assert prof["bloch"][1] == 6 * n_k * n_k  # six mode products per (k, q), one chunk each
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_kpoint_apply_to_vectors_in_chunks(kx, prec, monkeypatch):
+    """Vx at one k-point on arbitrary complex vectors, with chunks of 4 pairs that
+    split a vector's bands across chunks, and without occupations."""
+    sysd, theta, wk, psi, _, _ = kpoint_inputs(1, 311)
+    rng = np.random.default_rng(4)
+    phi = rng.standard_normal((sysd.N, 5)) + 1j * rng.standard_normal((sysd.N, 5))
+    base = oracle.Plan(sysd.n, sysd.h, sysd.bc, sysd.kernel)
+    ref = oracle.vx_apply_kpoint(base, theta, wk, psi, None, 2, phi)
+    plan = kx.Plan(sysd.n, sysd.h, sysd.bc, sysd.kernel, precision=prec)
+    monkeypatch.setenv("KX_CHUNK_PAIRS", "4")
+    plan.profile(True)
+    out = kx.kx_vx_apply_kpoint(plan, theta, wk, to_dev_orbitals(psi), 2, dev(phi.T))
+    torch.cuda.synchronize()
+    prof = plan.profile_read()
+    assert prof["bloch"][1] == 6 * len(wk) * 4  # 15 pairs per q in chunks of 4
+    assert relmax(out.cpu().numpy().T, ref) < TOL_K[prec][0]
+
+
+def test_kpoint_gamma_with_real_orbitals_is_the_real_path(kx):
+    n, h, bc, kind = (12, 10, 14), (0.45, 0.5, 0.4), (P, P, D), U
+    sysd = system(n, h, bc, kind, 4, 321)
+    psi = workloads.make_orbitals(sysd)
+    occ = np.array([1.0, 0.9, 0.5, 0.2])
+    plan = kx.Plan(n, h, bc, kind, precision=0)
+    vx_r, ex_r = kx.kx_vx_apply(plan, dev(psi.T), dev(occ))
+    vx_c, ex_c = kx.kx_vx_kpoints(plan, [[0.0, 0.0, 0.0]], [1.0], dev(psi.T.astype(np.complex128)[None]),
+                                  dev(occ[None]))
+    vx_c = vx_c.cpu().numpy()[0]
+    assert relmax(vx_c.real, vx_r.cpu().numpy()) < 1e-11
+    assert np.max(np.abs(vx_c.imag)) < 1e-11 * np.max(np.abs(vx_c.real))
+    assert abs(ex_c.item() - ex_r.item()) < 1e-11 * abs(ex_r.item())
+
+
+def test_kpoint_rejects_bad_arguments(kx):
+    import ctypes
+    sysd, theta, wk, psi, occ, _ = kpoint_inputs(0, 330)
+    plan = kx.Plan(sysd.n, sysd.h, sysd.bc, sysd.kernel, precision=0)
+    psi_d = to_dev_orbitals(psi)
+    phi = psi_d[1].clone()
+    for bad_k in (-1, len(wk)):
+        with pytest.raises(kx.KxError) as ei:
+            kx.kx_vx_apply_kpoint(plan, theta, wk, psi_d, bad_k, phi)
+        assert ei.value.code == kx.KX_ERR_ARG
+    th_bad = theta.copy()
+    th_bad[1, 0] = np.nan
+    with pytest.raises(kx.KxError) as ei:
+        kx.kx_vx_kpoints(plan, th_bad, wk, psi_d)
+    assert ei.value.code == kx.KX_ERR_ARG
+    with pytest.raises(kx.KxError) as ei:
+        kx.kx_vx_apply_kpoint(plan, theta, wk, psi_d, 0, phi, out=psi_d[0])
+    assert ei.value.code == kx.KX_ERR_ARG
+    # a complex buffer that starts 8 bytes into an allocation
+    raw = torch.zeros(2 * plan.N * 3 + 2, dtype=torch.float64, device="cuda")
+    ta = (ctypes.c_double * (3 * len(wk)))(*theta.ravel())
+    wa = (ctypes.c_double * len(wk))(*wk)
+    rc = kx.lib().kx_vx_apply_kpoint(plan.handle, len(wk), ctypes.cast(ta, ctypes.c_void_p),
+                                     ctypes.cast(wa, ctypes.c_void_p), psi.shape[2],
+                                     ctypes.c_void_p(psi_d.data_ptr()), None, 0, 1,
+                                     ctypes.c_void_p(raw.data_ptr() + 8), ctypes.c_void_p(phi.data_ptr()),
+                                     kx._stream())
+    assert rc == kx.KX_ERR_ARG
+    mp = kx.Plan((16, 16, 16), (0.5,) * 3, (D, D, D), U, precision=0)
+    mp.set_multipole(2)
+    x = torch.zeros((1, 1, mp.N), dtype=torch.complex128, device="cuda")
+    with pytest.raises(kx.KxError) as ei:
+        kx.kx_vx_kpoints(mp, [[0.0, 0.0, 0.0]], [1.0], x)
+    assert ei.value.code == kx.KX_ERR_UNSUPPORTED
+    assert plan.status() == kx.KX_OK
+
+
+def test_kpoint_full_size_sampled(kx):
+    """The 64^3 slab with 16 bands on a 2 x 2 k-grid (the k-point workload the
+    benchmark times): two runs are bit-identical, one band's Vx at one k-point
+    matches the oracle, and E_x matches its definition from the returned Vx."""
+    sysd = workloads.K1
+    theta, wk = workloads.kpoint_grid(sysd, workloads.K1_KGRID)
+    psi = workloads.make_bloch_orbitals(sysd, theta)
+    plan = kx.Plan(sysd.n, sysd.h, sysd.bc, sysd.kernel, precision=1)
+    psi_d = to_dev_orbitals(psi)
+    vx, ex = kx.kx_vx_kpoints(plan, theta, wk, psi_d)
+    vx2, ex2 = kx.kx_vx_kpoints(plan, theta, wk, psi_d)
+    torch.cuda.synchronize()
+    assert torch.equal(vx, vx2) and ex.item() == ex2.item()  # deterministic
+    base = oracle.Plan(sysd.n, sysd.h, sysd.bc, sysd.kernel)
+    k, band = 1, 5
+    ref = oracle.vx_apply_kpoint(base, theta, wk, psi, None, k, psi[k][:, band:band + 1])[:, 0]
+    got = vx[k, band].cpu().numpy()
+    assert relmax(got, ref) < TOL_K[1][0]
+    vxn = vx.cpu().numpy()
+    e_def = 0.5 * sysd.dV * sum(wk[q] * np.vdot(psi[q][:, m], vxn[q, m]).real
+                               for q in range(len(wk)) for m in range(sysd.n_orb))
+    assert abs(ex.item() - e_def) < 1e-9 * abs(e_def) and ex.item() < 0

@@ -111,6 +111,38 @@ def make_orbitals(sys: System, n_orb: int | None = None, seed: int | None = None
     return cholesky_qr2(psi, sys.dV)
 
 
+def kpoint_grid(sys: System, counts) -> tuple[np.ndarray, np.ndarray]:
+    """Gamma-centred k-point grid: counts[a] points along each periodic axis (1 on
+    Dirichlet axes), phases per cell theta_a = 2 pi j / counts[a], equal weights
+    summing to 1.  Returns (theta (n_kpt, 3), weights (n_kpt,))."""
+    for a in range(3):
+        if sys.bc[a] == DIRICHLET and counts[a] != 1:
+            raise ValueError("a Dirichlet axis takes a single k-point")
+    grids = [2.0 * np.pi * np.arange(counts[a]) / counts[a] for a in range(3)]
+    theta = np.array([[t1, t2, t3] for t3 in grids[2] for t2 in grids[1] for t1 in grids[0]])
+    return theta, np.full(len(theta), 1.0 / len(theta))
+
+
+def make_bloch_orbitals(sys: System, theta, n_orb: int | None = None, seed: int | None = None) -> np.ndarray:
+    """Seeded complex Bloch orbitals, shape (n_kpt, N, n_orb) complex128: per k-point
+    (u + i u') / sqrt(2) from two make_orbitals draws (periodic along periodic
+    axes), times exp(i theta_a x_a / n_a) along each periodic axis (x_a the grid
+    index), so that psi(x + n_a h_a) = exp(i theta_a) psi(x)."""
+    theta = np.asarray(theta, dtype=np.float64).reshape(-1, 3)
+    base = sys.seed if seed is None else seed
+    n1, n2, n3 = sys.n
+    idx = np.indices((n3, n2, n1))  # [x3, x2, x1]
+    out = []
+    for k, th in enumerate(theta):
+        u = make_orbitals(sys, n_orb, base + 2 * k) + 1j * make_orbitals(sys, n_orb, base + 2 * k + 1)
+        ph = np.zeros((n3, n2, n1))
+        for a in range(3):
+            if sys.bc[a] == PERIODIC:
+                ph += th[a] * idx[2 - a] / sys.n[a]
+        out.append(np.exp(1j * ph).reshape(-1, 1) * u / np.sqrt(2.0))
+    return np.stack(out)
+
+
 def random_field(n_total: int, n_rhs: int, seed: int) -> np.ndarray:
     """Plain N(0,1) right-hand sides, shape (n_total, n_rhs) float64."""
     return np.random.default_rng(seed).standard_normal((n_total, n_rhs))
@@ -157,6 +189,13 @@ C4 = [
 ]
 
 C5 = C3  # differentiation workload runs on the 80^3 periodic screened system
+
+
+# Bloch k-points: a slab periodic in x1 and x2 with vacuum (Dirichlet) along x3,
+# unscreened kernel, 16 bands at each point of a 2 x 2 Gamma-centred k-grid.
+K1 = System(n=(64, 64, 64), h=(0.3,) * 3, bc=(PERIODIC, PERIODIC, DIRICHLET), kernel=UNSCREENED, n_orb=16,
+            n_centres=8, seed=61)
+K1_KGRID = (2, 2, 1)
 
 
 def n_pairs(n_orb: int, ordered: bool = False) -> int:

@@ -379,9 +379,11 @@ def other_workloads(kx, torch, stream, hbm, steps=3):
     batch.close()
     del psis, outs, plans
     # Bloch k-points: the 64^3 slab (periodic x1 and x2, vacuum along x3), 16 bands
-    # on a 2 x 2 k-grid; Vx psi at every k-point is 4 x 4 x 16 x 16 pair solves,
-    # each six complex mode products of 8 n_a N flops (16 N (n1 + n2 + n3) a pair),
-    # in complex float32 on the CUDA cores (float64 plan for the error)
+    # on a 2 x 2 k-grid; Vx psi at every k-point needs the pair blocks (k, q),
+    # q >= k (10 of 16: a reversed block is the conjugate solve), 16 x 16 pair
+    # solves each, six complex mode products of 8 n_a N flops per solve
+    # (16 N (n1 + n2 + n3)), complex float32 on the CUDA cores (float64 plan for
+    # the error)
     kd = workloads.K1
     theta, wk = workloads.kpoint_grid(kd, workloads.K1_KGRID)
     psi_k = torch.from_numpy(np.ascontiguousarray(
@@ -400,7 +402,7 @@ def other_workloads(kx, torch, stream, hbm, steps=3):
     kx.kx_vx_kpoints(plan_k, theta, wk, psi_k, out=vx_k, e_x=ex_k, stream=stream)
     pr = plan_k.profile_read()
     plan_k.profile(False)
-    PK = len(wk) ** 2 * kd.n_orb ** 2
+    PK = len(wk) * (len(wk) + 1) // 2 * kd.n_orb ** 2
     flops_pair = 16.0 * kd.N * sum(kd.n)
     tf = flops_pair * PK / (pr["bloch"][0] / 1e3) / 1e12
     plan_k64 = kx.Plan.for_system(kd, precision=kx.KX_FP64)
@@ -408,6 +410,7 @@ def other_workloads(kx, torch, stream, hbm, steps=3):
     torch.cuda.synchronize()
     res["k1_kpoints_slab_64cube_16bands_2x2"] = {
         "ms_per_apply": ms_k, "pair_solves_per_s": PK / (ms_k / 1e3), "pairs": PK,
+        "pairs_of_the_k_sum": len(wk) ** 2 * kd.n_orb ** 2,
         "mode_products_ms": pr["bloch"][0], "mode_product_launches": pr["bloch"][1],
         "other_kernels_ms": pr["bloch_other"][0], "e_x": ex_k.item(), "status": plan_k.status(),
         "vx_maxrel_vs_fp64_plan": float((vx_k - vx_64).abs().max() / vx_64.abs().max()),

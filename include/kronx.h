@@ -291,7 +291,10 @@ int kx_vx_apply_kpoint(kx_plan *plan, int n_kpt, const double *theta, const doub
 /* kx_vx_kpoints — Vx psi_nk at every k-point into vx (device, layout of psi,
  * not overlapping it) and, if ex != NULL, the exchange energy
  *   E_x = 1/2 dV sum_k w_k sum_n g_nk Re <psi_nk, Vx psi_nk>
- * (Eq. 8 after the Poisson solves) into ex[0] (device float64). */
+ * (Eq. 8 after the Poisson solves) into ex[0] (device float64).  The pairs
+ * of k-points k < q are solved once for both: the solve of (q m, k n) is the
+ * complex conjugate of that of (k n, q m), so n_kpt (n_kpt + 1) / 2 blocks of
+ * n_orb^2 solves are done. */
 int kx_vx_kpoints(kx_plan *plan, int n_kpt, const double *theta, const double *wk, int n_orb, const double *psi,
                   const double *occ, double *vx, double *ex, kx_stream stream);
 

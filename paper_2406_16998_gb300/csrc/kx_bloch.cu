@@ -12,7 +12,8 @@
 // conj(Vk), the inverse with Vk.  The six complex mode products run on the CUDA
 // cores, in float64 for KX_FP64 plans and in float32 (packed f32x2 FMAs) for the
 // others; the pair density is formed inside the first product and f(Lambda) is
-// applied inside the third.
+// applied inside the third.  For Vx psi at every k-point the block of pairs
+// (k, q), q > k, is solved once: read conjugated it is the block (q, k).
 #include "kx_internal.h"
 #include "kx_conv.cuh"
 #include "kx_fd.cuh"
@@ -471,11 +472,56 @@ BlochLayout bloch_layout(const kx_plan *p, int n_orb, int n_vec, int n_kpt) {
     return L;
 }
 
-// Vx of the vectors phi at k-point k (out overwritten, or accumulated into when
-// !zero_out).  psi: n_kpt x n_orb x N complex, occ: n_kpt x n_orb (nullable).
+// The same solves read the other way (kx_vx_kpoints with k < q): the pair
+// (q m, k v) has the density conj(rho) and the phase -theta, and f(L_{-theta})
+// conj(rho) = conj(f(L_theta) rho) (L_{-theta} = conj(L_theta)), so
+// out_m[x] -= sum over the chunk items r = v * n_orb + m in [r0, r1) of
+// w_k g_vk F_v[x] conj(X_{r - r0}[x]) (v ascending, one thread per (m, x)).
 template <typename T>
-int bloch_run(kx_plan *p, int n_kpt, const double *theta, const double *wk, int n_orb, const double *psi,
-              const double *occ, int k, int n_vec, const double *phi, double *out, cudaStream_t s) {
+__global__ void bloch_accum_rev_kernel(const typename Cx<T>::t *__restrict__ X, long long r0, long long r1,
+                                       int n_orb, const typename Cx<T>::t *__restrict__ F,
+                                       const double *__restrict__ occ_k, double wk, double2 *__restrict__ out,
+                                       long long N) {
+    using T2 = typename Cx<T>::t;
+    const long long v_lo = r0 / n_orb, v_hi = (r1 - 1) / n_orb;
+    const long long total = (long long)n_orb * N;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        long long m = e / N, x = e - m * N;
+        T sr = 0, si = 0;
+        bool any = false;
+        for (long long v = v_lo; v <= v_hi; ++v) {
+            long long r = v * n_orb + m;
+            if (r < r0 || r >= r1) continue;
+            any = true;
+            T2 fv = F[v * N + x];
+            T2 xx = X[(r - r0) * N + x];
+            T c = (T)(wk * (occ_k ? occ_k[v] : 1.0));
+            sr = fma(c, fv.x * xx.x + fv.y * xx.y, sr);  // F conj(X)
+            si = fma(c, fv.y * xx.x - fv.x * xx.y, si);
+        }
+        if (!any) continue;
+        double2 o = out[m * N + x];
+        if constexpr (sizeof(T) == 4) {
+            o.x -= f32_to_f64(sr);
+            o.y -= f32_to_f64(si);
+        } else {
+            o.x -= sr;
+            o.y -= si;
+        }
+        out[m * N + x] = o;
+    }
+}
+
+// Solves of the k-point pairs (k, q) for q = q_begin .. n_kpt - 1 with the
+// vectors phi at k (n_vec of them): out_k -= w_q g_mq psi_mq X for every q and,
+// when out_all is given, out_all[q] -= w_k g_vk phi_v conj(X) for q > k (the
+// reversed pairs, phi being psi_k).  psi: n_kpt x n_orb x N complex, occ:
+// n_kpt x n_orb (nullable).  Outputs are accumulated into.
+template <typename T>
+int bloch_sweep(kx_plan *p, int n_kpt, const double *theta, const double *wk, int n_orb, const double *psi,
+                const double *occ, int k, int q_begin, int n_vec, const double *phi, double *out_k,
+                double *out_all, cudaStream_t s) {
     using T2 = typename Cx<T>::t;
     const long long N = (long long)p->N;
     BlochLayout L = bloch_layout<T>(p, n_orb, n_vec, n_kpt);
@@ -493,7 +539,6 @@ int bloch_run(kx_plan *p, int n_kpt, const double *theta, const double *wk, int 
     T2 *B = reinterpret_cast<T2 *>(ws + L.B);
     const bool f32 = sizeof(T) == 4;
     const int blocks = 4 * p->num_sms;
-    KX_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(double2) * (size_t)N * n_vec, s));
     const T2 *F;
     if (f32) {
         T2 *Fw = reinterpret_cast<T2 *>(ws + L.F);
@@ -516,7 +561,8 @@ int bloch_run(kx_plan *p, int n_kpt, const double *theta, const double *wk, int 
     }
     ax.order = p->fd_order;
     const long long pairs = (long long)n_orb * n_vec;
-    for (int q = 0; q < n_kpt; ++q) {
+    const double *occ_k = occ ? occ + (size_t)k * n_orb : nullptr;
+    for (int q = q_begin; q < n_kpt; ++q) {
         for (int a = 0; a < 3; ++a) ax.theta[a] = theta[3 * k + a] - theta[3 * q + a];
         if (int rc = prof_begin(p, PK_BLOCH_OTHER, s)) return rc;
         bloch_basis_kernel<T><<<3, 256, 0, s>>>(ax, Mf[0], Mf[1], Mf[2], Mi[0], Mi[1], Mi[2], lam[0], lam[1],
@@ -537,6 +583,7 @@ int bloch_run(kx_plan *p, int n_kpt, const double *theta, const double *wk, int 
         }
         if (int rc = prof_end(p, s)) return rc;
         const double *occ_q = occ ? occ + (size_t)q * n_orb : nullptr;
+        const bool reverse = out_all && q > k;
         for (long long r0 = 0; r0 < pairs; r0 += L.chunk) {
             const long long r1 = std::min(pairs, r0 + L.chunk);
             const long long R = r1 - r0;
@@ -555,21 +602,38 @@ int bloch_run(kx_plan *p, int n_kpt, const double *theta, const double *wk, int 
             const long long nv = (r1 - 1) / n_orb - r0 / n_orb + 1;
             const int ab = (int)std::min<long long>((nv * N + 255) / 256, 8LL * p->num_sms);
             bloch_accum_kernel<T><<<ab, 256, 0, s>>>(B, r0, r1, n_orb, Pq, occ_q, wk[q],
-                                                     reinterpret_cast<double2 *>(out), N);
+                                                     reinterpret_cast<double2 *>(out_k), N);
             KX_LAUNCH_CHECK("bloch_accum_kernel launch");
+            if (reverse) {
+                const int rb = (int)std::min<long long>((n_orb * N + 255) / 256, 8LL * p->num_sms);
+                double2 *out_q = reinterpret_cast<double2 *>(out_all) + (size_t)q * n_orb * N;
+                bloch_accum_rev_kernel<T><<<rb, 256, 0, s>>>(B, r0, r1, n_orb, F, occ_k, wk[k], out_q, N);
+                KX_LAUNCH_CHECK("bloch_accum_rev_kernel launch");
+            }
             if ((rc = prof_end(p, s))) return rc;
         }
     }
     return KX_OK;
 }
 
+// Vx of the vectors phi at k-point k (out overwritten): every q contributes.
+template <typename T>
+int bloch_run(kx_plan *p, int n_kpt, const double *theta, const double *wk, int n_orb, const double *psi,
+              const double *occ, int k, int n_vec, const double *phi, double *out, cudaStream_t s) {
+    KX_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(double2) * p->N * (size_t)n_vec, s));
+    return bloch_sweep<T>(p, n_kpt, theta, wk, n_orb, psi, occ, k, 0, n_vec, phi, out, nullptr, s);
+}
+
+// Vx psi at every k-point: the pair blocks (k, q) with q >= k are solved once
+// and serve both Vx psi_k and, read conjugated, Vx psi_q.
 template <typename T>
 int bloch_all(kx_plan *p, int n_kpt, const double *theta, const double *wk, int n_orb, const double *psi,
               const double *occ, double *vx, double *ex, cudaStream_t s) {
     const size_t N = p->N;
+    KX_CUDA_TRY(cudaMemsetAsync(vx, 0, sizeof(double2) * N * (size_t)n_orb * n_kpt, s));
     for (int k = 0; k < n_kpt; ++k) {
         const size_t off = (size_t)k * n_orb * N * 2;
-        if (int rc = bloch_run<T>(p, n_kpt, theta, wk, n_orb, psi, occ, k, n_orb, psi + off, vx + off, s))
+        if (int rc = bloch_sweep<T>(p, n_kpt, theta, wk, n_orb, psi, occ, k, k, n_orb, psi + off, vx + off, vx, s))
             return rc;
     }
     if (!ex) return KX_OK;

@@ -864,7 +864,9 @@ def test_kpoint_vx_and_energy_match_oracle(kx, case):
     assert relmax(vx, vx_ref) < TOL_K[prec][0]
     assert abs(ex.item() - ex_ref) < TOL_K[prec][1] * abs(ex_ref)
     n_k = len(wk)
-    assert prof["bloch"][1] == 6 * n_k * n_k  # six mode products per (k, q), one chunk each
+    # six mode products per k-point pair block (k, q), q >= k (the reversed
+    # blocks reuse the same solves, conjugated), one chunk each
+    assert prof["bloch"][1] == 6 * n_k * (n_k + 1) // 2
 
 
 @pytest.mark.parametrize("prec", [0, 1])

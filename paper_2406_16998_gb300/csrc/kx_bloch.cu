@@ -17,6 +17,7 @@
 #include "kx_internal.h"
 #include "kx_conv.cuh"
 #include "kx_fd.cuh"
+#include "kx_tc_ptx.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -35,6 +36,7 @@ constexpr int kBWarps = kBThreads / 32;  // output-column groups of a CTA
 template <typename T> constexpr int pencils_per_thread() { return sizeof(T) == 4 ? 2 : 1; }
 template <typename T> constexpr int tile_pencils() { return 32 * pencils_per_thread<T>(); }
 constexpr size_t kBSmemTarget = 110 * 1024;  // two CTAs per SM where the split allows it
+constexpr size_t kBSmemPipeMax = 200 * 1024;  // pipelined products: operand + two tiles
 
 template <typename T2> __device__ __forceinline__ T2 cmul_conj(T2 a, T2 b) {  // conj(a) b
     T2 r;
@@ -198,6 +200,171 @@ __global__ void __launch_bounds__(kBThreads) bloch_mode_kernel(
                 for (int cl = warp; cl < ncy; cl += kBWarps) out[base[j] + (c0 + cl) * inner] = Ts[cl * ld + ql];
         }
     }
+}
+
+// The products that read a plain input (all but the first): persistent CTAs,
+// each with a fixed column split and a strided run of tiles, the operand staged
+// once, and the next tile copied in (cp.async) while the current one is
+// multiplied; the current tile's buffer then stages the output.  Same mapping
+// and arithmetic as bloch_mode_kernel.
+template <typename T, bool SCALE, int U>
+__global__ void __launch_bounds__(kBThreads) bloch_mode_pipe_kernel(
+    const typename Cx<T>::t *__restrict__ in, typename Cx<T>::t *__restrict__ out, int n_cols, int n, int inner,
+    const typename Cx<T>::t *__restrict__ M, int nc, int n_split, const T *__restrict__ f) {
+    using T2 = typename Cx<T>::t;
+    constexpr int PQ = pencils_per_thread<T>();
+    constexpr int QB = 32 * PQ;
+    constexpr int NCP = 8 * U;
+    extern __shared__ __align__(16) unsigned char bloch_smem[];
+    T2 *Ms = reinterpret_cast<T2 *>(bloch_smem);  // n x NCP
+    const int ld = QB + 1;
+    T2 *const Tb0 = Ms + (size_t)n * NCP;  // two tile buffers of n x ld
+    const int tsz = n * ld;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int split = (int)(blockIdx.x % n_split);
+    const int t_first = (int)(blockIdx.x / n_split);
+    const int t_stride = (int)(gridDim.x / n_split);
+    const int n_tiles = (n_cols + QB - 1) / QB;
+    const int c0 = split * nc;
+    const int ncy = min(nc, n - c0);
+    for (int k = warp; k < n; k += kBWarps)
+        for (int cl = lane; cl < NCP; cl += 32) {
+            T2 z;
+            z.x = z.y = (T)0;
+            Ms[k * NCP + cl] = cl < ncy ? M[(size_t)k * n + c0 + cl] : z;
+        }
+    auto issue = [&](int t, T2 *buf) {
+        const int q0 = t * QB;
+        const int nq = min(QB, n_cols - q0);
+        if (inner == 1) {
+            for (int ql = warp; ql < nq; ql += kBWarps) {
+                const T2 *src = in + (size_t)(q0 + ql) * n;
+                for (int k = lane; k < n; k += 32) {
+                    if constexpr (sizeof(T) == 4) ptx::cp_async8(buf + k * ld + ql, src + k, 8);
+                    else ptx::cp_async16(buf + k * ld + ql, src + k, 16);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < PQ; ++j) {
+                const int ql = lane + 32 * j;
+                if (ql < nq) {
+                    const int q = q0 + ql;
+                    const int o = q / inner;
+                    const T2 *src = in + (size_t)o * n * inner + (q - o * inner);
+                    for (int k = warp; k < n; k += kBWarps) {
+                        if constexpr (sizeof(T) == 4) ptx::cp_async8(buf + k * ld + ql, src + (size_t)k * inner, 8);
+                        else ptx::cp_async16(buf + k * ld + ql, src + (size_t)k * inner, 16);
+                    }
+                }
+            }
+        }
+    };
+    if (t_first < n_tiles) issue(t_first, Tb0);
+    ptx::cp_async_commit();
+    int it = 0;
+    for (int t = t_first; t < n_tiles; t += t_stride, ++it) {
+        T2 *cur = Tb0 + (it & 1) * tsz;
+        if (t + t_stride < n_tiles) issue(t + t_stride, Tb0 + ((it + 1) & 1) * tsz);
+        ptx::cp_async_commit();
+        ptx::cp_async_wait<1>();
+        __syncthreads();
+        const int q0 = t * QB;
+        const int nq = min(QB, n_cols - q0);
+        T2 res[PQ][U];
+        if constexpr (sizeof(T) == 4) {
+            // (sum a_re v, sum a_im v) as two packed accumulators per output
+            float2 accA[PQ][U], accB[PQ][U];
+#pragma unroll
+            for (int j = 0; j < PQ; ++j)
+#pragma unroll
+                for (int u = 0; u < U; ++u) accA[j][u] = accB[j][u] = make_float2(0.f, 0.f);
+            const float2 *mcol = Ms + warp;
+            const float2 *tcol = cur + lane;
+#pragma unroll 2
+            for (int k = 0; k < n; ++k) {
+                float2 ar[PQ], ai[PQ];
+#pragma unroll
+                for (int j = 0; j < PQ; ++j) {
+                    const float2 a = tcol[k * ld + 32 * j];
+                    ar[j] = make_float2(a.x, a.x);
+                    ai[j] = make_float2(a.y, a.y);
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const float2 v = mcol[k * NCP + 8 * u];
+#pragma unroll
+                    for (int j = 0; j < PQ; ++j) {
+                        fma2(accA[j][u], ar[j], v);
+                        fma2(accB[j][u], ai[j], v);
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < PQ; ++j)
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    res[j][u] = make_float2(accA[j][u].x - accB[j][u].y, accA[j][u].y + accB[j][u].x);
+        } else {
+#pragma unroll
+            for (int j = 0; j < PQ; ++j)
+#pragma unroll
+                for (int u = 0; u < U; ++u) res[j][u] = make_double2(0.0, 0.0);
+            for (int k = 0; k < n; ++k) {
+#pragma unroll
+                for (int j = 0; j < PQ; ++j) {
+                    const double2 a = cur[k * ld + lane + 32 * j];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const double2 v = Ms[k * NCP + warp + 8 * u];
+                        res[j][u].x = fma(a.x, v.x, fma(-a.y, v.y, res[j][u].x));
+                        res[j][u].y = fma(a.x, v.y, fma(a.y, v.x, res[j][u].y));
+                    }
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < PQ; ++j) {
+            const int ql = lane + 32 * j;
+            if (ql >= nq) continue;
+            int i_in = 0;
+            if constexpr (SCALE) i_in = (q0 + ql) % inner;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int cl = warp + 8 * u;
+                if (cl < ncy) {
+                    T2 v = res[j][u];
+                    if constexpr (SCALE) {
+                        const T fv = f[(size_t)(c0 + cl) * inner + i_in];
+                        v.x *= fv;
+                        v.y *= fv;
+                    }
+                    cur[cl * ld + ql] = v;
+                }
+            }
+        }
+        __syncthreads();
+        if (inner == 1) {
+            for (int ql = warp; ql < nq; ql += kBWarps) {
+                T2 *dst = out + (size_t)(q0 + ql) * n + c0;
+                for (int cl = lane; cl < ncy; cl += 32) dst[cl] = cur[cl * ld + ql];
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < PQ; ++j) {
+                const int ql = lane + 32 * j;
+                if (ql < nq) {
+                    const int q = q0 + ql;
+                    const int o = q / inner;
+                    T2 *dst = out + (size_t)o * n * inner + (q - o * inner);
+                    for (int cl = warp; cl < ncy; cl += kBWarps) dst[(size_t)(c0 + cl) * inner] = cur[cl * ld + ql];
+                }
+            }
+        }
+        __syncthreads();
+    }
+    ptx::cp_async_wait<0>();
 }
 
 struct BlochAxes {
@@ -427,6 +594,74 @@ int launch_mode(kx_plan *p, int axis, long long R, const typename Cx<T>::t *in, 
     return prof_end(p, s);
 }
 
+// Split for the pipelined products (two tile buffers): all n columns where the
+// shared memory (operand + two tiles) fits 200 KB, else halves.
+template <typename T>
+void choose_split_pipe(int n, int *nc, int *n_split, int *U, size_t *smem) {
+    using T2 = typename Cx<T>::t;
+    const int max_cols = kBWarps * (sizeof(T) == 4 ? 16 : 8);
+    auto bytes = [n](int u) { return sizeof(T2) * ((size_t)n * 8 * u + 2 * (size_t)n * (tile_pencils<T>() + 1)); };
+    int c = std::min(n, max_cols);
+    while (bytes(outputs_for<T>(c)) > kBSmemPipeMax && c > kBWarps) c = (c + 1) / 2;
+    *nc = c;
+    *n_split = (n + c - 1) / c;
+    *U = outputs_for<T>(c);
+    *smem = bytes(*U);
+}
+
+template <typename T, bool SCALE, int U>
+int launch_pipe_u(kx_plan *p, long long n_tiles, size_t smem, cudaStream_t s, const typename Cx<T>::t *in,
+                  typename Cx<T>::t *out, int n_cols, int n, int inner, const typename Cx<T>::t *M, int nc,
+                  int n_split, const T *f) {
+    static int per_sm = 0;  // resident CTAs per SM at this instantiation's shared memory (set once)
+    static size_t per_sm_smem = 0;
+    if (per_sm == 0 || per_sm_smem != smem) {
+        KX_CUDA_TRY(cudaFuncSetAttribute(bloch_mode_pipe_kernel<T, SCALE, U>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBSmemPipeMax));
+        KX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bloch_mode_pipe_kernel<T, SCALE, U>,
+                                                                  kBThreads, smem));
+        per_sm = std::max(per_sm, 1);
+        per_sm_smem = smem;
+    }
+    const long long per_split = std::max(1LL, std::min(n_tiles, (long long)per_sm * p->num_sms / n_split));
+    const unsigned blocks = (unsigned)(per_split * n_split);
+    bloch_mode_pipe_kernel<T, SCALE, U><<<blocks, kBThreads, smem, s>>>(in, out, n_cols, n, inner, M, nc, n_split, f);
+    KX_LAUNCH_CHECK("bloch_mode_pipe_kernel launch");
+    return KX_OK;
+}
+
+template <typename T, bool SCALE>
+int launch_pipe(kx_plan *p, int axis, long long R, const typename Cx<T>::t *in, typename Cx<T>::t *out,
+                const typename Cx<T>::t *M, const T *f, cudaStream_t s) {
+    const int n = p->n[axis];
+    const long long N = (long long)p->N;
+    const int inner = axis == 0 ? 1 : (axis == 1 ? p->n[0] : p->n[0] * p->n[1]);
+    const long long n_cols = R * (N / n);
+    int nc, n_split, U;
+    size_t smem;
+    choose_split_pipe<T>(n, &nc, &n_split, &U, &smem);
+    const long long n_tiles = (n_cols + tile_pencils<T>() - 1) / tile_pencils<T>();
+    if (R * N >= (1LL << 31)) return set_error(KX_ERR_ARG, "Bloch exchange: chunk too large for one launch");
+    if (smem > kBSmemPipeMax) return set_error(KX_ERR_UNSUPPORTED, "Bloch exchange: axis too long for the tile");
+    if (int rc = prof_begin(p, PK_BLOCH, s)) return rc;
+    const int nco = (int)n_cols;
+#define KX_BLOCH_PIPE(UU) launch_pipe_u<T, SCALE, UU>(p, n_tiles, smem, s, in, out, nco, n, inner, M, nc, n_split, f)
+    int rc;
+    if (U == 2) rc = KX_BLOCH_PIPE(2);
+    else if (U == 4) rc = KX_BLOCH_PIPE(4);
+    else if (U == 8) rc = KX_BLOCH_PIPE(8);
+    else if constexpr (sizeof(T) == 4) {
+        if (U == 6) rc = KX_BLOCH_PIPE(6);
+        else if (U == 12) rc = KX_BLOCH_PIPE(12);
+        else rc = KX_BLOCH_PIPE(16);
+    } else {
+        rc = set_error(KX_ERR_ARG, "Bloch exchange: no kernel for this split");
+    }
+#undef KX_BLOCH_PIPE
+    if (rc) return rc;
+    return prof_end(p, s);
+}
+
 // Device workspace of one call: bases, eigenvalues, f table, float32 copies of
 // the orbitals and vectors (float32 plans), chunk buffers A and B.
 struct BlochLayout {
@@ -589,15 +824,11 @@ int bloch_sweep(kx_plan *p, int n_kpt, const double *theta, const double *wk, in
             const long long R = r1 - r0;
             int rc;
             if ((rc = launch_mode<T, true, false>(p, 0, R, nullptr, A, Mf[0], nullptr, Pq, F, n_orb, r0, s))) return rc;
-            if ((rc = launch_mode<T, false, false>(p, 1, R, A, B, Mf[1], nullptr, nullptr, nullptr, n_orb, 0, s)))
-                return rc;
-            if ((rc = launch_mode<T, false, true>(p, 2, R, B, A, Mf[2], f, nullptr, nullptr, n_orb, 0, s))) return rc;
-            if ((rc = launch_mode<T, false, false>(p, 2, R, A, B, Mi[2], nullptr, nullptr, nullptr, n_orb, 0, s)))
-                return rc;
-            if ((rc = launch_mode<T, false, false>(p, 1, R, B, A, Mi[1], nullptr, nullptr, nullptr, n_orb, 0, s)))
-                return rc;
-            if ((rc = launch_mode<T, false, false>(p, 0, R, A, B, Mi[0], nullptr, nullptr, nullptr, n_orb, 0, s)))
-                return rc;
+            if ((rc = launch_pipe<T, false>(p, 1, R, A, B, Mf[1], nullptr, s))) return rc;
+            if ((rc = launch_pipe<T, true>(p, 2, R, B, A, Mf[2], f, s))) return rc;
+            if ((rc = launch_pipe<T, false>(p, 2, R, A, B, Mi[2], nullptr, s))) return rc;
+            if ((rc = launch_pipe<T, false>(p, 1, R, B, A, Mi[1], nullptr, s))) return rc;
+            if ((rc = launch_pipe<T, false>(p, 0, R, A, B, Mi[0], nullptr, s))) return rc;
             if ((rc = prof_begin(p, PK_BLOCH_OTHER, s))) return rc;
             const long long nv = (r1 - 1) / n_orb - r0 / n_orb + 1;
             const int ab = (int)std::min<long long>((nv * N + 255) / 256, 8LL * p->num_sms);

@@ -84,16 +84,18 @@ __global__ void __launch_bounds__(kBThreads) bloch_mode_kernel(
     const int nq = min(QB, n_cols - q0);
     int base[PQ];  // element offset of each owned pencil (inner > 1)
     if (inner == 1) {
+        const int ppi = (int)(N / n);  // pencils per item
+#pragma unroll 4
         for (int ql = warp; ql < nq; ql += kBWarps) {
             const int q = q0 + ql;
             if constexpr (FORM) {
-                const int ppi = (int)(N / n);  // pencils per item
+                // pair indices stay below n_orb * n_vec <= 2^24
                 const int r = q / ppi;
                 const long long x0 = (long long)(q - r * ppi) * n;
-                const long long rr = r0 + r;
-                const long long vv = rr / n_orb, m = rr - vv * n_orb;
-                const T2 *Pp = P + m * N + x0;
-                const T2 *Fp = F + vv * N + x0;
+                const int rr = (int)r0 + r;
+                const int vv = rr / n_orb, m = rr - vv * n_orb;
+                const T2 *Pp = P + (long long)m * N + x0;
+                const T2 *Fp = F + (long long)vv * N + x0;
                 for (int k = lane; k < n; k += 32) Ts[k * ld + ql] = cmul_conj(Pp[k], Fp[k]);
             } else {
                 const T2 *src = in + (size_t)q * n;
@@ -377,7 +379,7 @@ struct BlochAxes {
     const double *lam[3];  // plan's eigenvalues (Dirichlet axes)
 };
 
-// One CTA per axis: the forward operand Mf[k][c] = conj(V[k][c]) and the inverse
+// blockIdx.x = axis, blockIdx.y shares the n x n entries: the forward operand Mf[k][c] = conj(V[k][c]) and the inverse
 // operand Mi[k][c] = V[c][k] in T, and the eigenvalues lam_out (float64).
 template <typename T>
 __global__ void bloch_basis_kernel(BlochAxes ax, typename Cx<T>::t *Mf0, typename Cx<T>::t *Mf1,
@@ -392,7 +394,7 @@ __global__ void bloch_basis_kernel(BlochAxes ax, typename Cx<T>::t *Mf0, typenam
     const bool bloch = ax.bc[a] == KX_PERIODIC;
     const double th = ax.theta[a];
     const double inv_sqrt_n = 1.0 / sqrt((double)n);
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < n * n; e += gridDim.y * blockDim.x) {
         int x = e / n, m = e - x * n;
         double vr, vi;
         if (bloch) {
@@ -414,6 +416,7 @@ __global__ void bloch_basis_kernel(BlochAxes ax, typename Cx<T>::t *Mf0, typenam
         v.y = -v.y;
         Mf[x * n + m] = v;
     }
+    if (blockIdx.y != 0) return;
     const int mo = ax.order / 2;
     const double ih2 = 1.0 / (ax.h[a] * ax.h[a]);
     for (int m = threadIdx.x; m < n; m += blockDim.x) {
@@ -800,7 +803,7 @@ int bloch_sweep(kx_plan *p, int n_kpt, const double *theta, const double *wk, in
     for (int q = q_begin; q < n_kpt; ++q) {
         for (int a = 0; a < 3; ++a) ax.theta[a] = theta[3 * k + a] - theta[3 * q + a];
         if (int rc = prof_begin(p, PK_BLOCH_OTHER, s)) return rc;
-        bloch_basis_kernel<T><<<3, 256, 0, s>>>(ax, Mf[0], Mf[1], Mf[2], Mi[0], Mi[1], Mi[2], lam[0], lam[1],
+        bloch_basis_kernel<T><<<dim3(3, 16), 256, 0, s>>>(ax, Mf[0], Mf[1], Mf[2], Mi[0], Mi[1], Mi[2], lam[0], lam[1],
                                                 lam[2]);
         KX_LAUNCH_CHECK("bloch_basis_kernel launch");
         bloch_ftable_kernel<T><<<blocks, 256, 0, s>>>(p->n[0], p->n[1], p->n[2], lam[0], lam[1], lam[2], p->kind,

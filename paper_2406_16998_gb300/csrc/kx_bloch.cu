@@ -379,8 +379,9 @@ struct BlochAxes {
     const double *lam[3];  // plan's eigenvalues (Dirichlet axes)
 };
 
-// blockIdx.x = axis, blockIdx.y shares the n x n entries: the forward operand Mf[k][c] = conj(V[k][c]) and the inverse
-// operand Mi[k][c] = V[c][k] in T, and the eigenvalues lam_out (float64).
+// blockIdx.x = axis, blockIdx.y shares the n x n entries: the forward operand
+// Mf[k][c] = conj(V[k][c]) and the inverse operand Mi[k][c] = V[c][k] in T, and
+// the eigenvalues lam_out (float64).
 template <typename T>
 __global__ void bloch_basis_kernel(BlochAxes ax, typename Cx<T>::t *Mf0, typename Cx<T>::t *Mf1,
                                    typename Cx<T>::t *Mf2, typename Cx<T>::t *Mi0, typename Cx<T>::t *Mi1,

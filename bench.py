@@ -405,6 +405,11 @@ def other_workloads(kx, torch, stream, hbm, steps=3):
     PK = len(wk) * (len(wk) + 1) // 2 * kd.n_orb ** 2
     flops_pair = 16.0 * kd.N * sum(kd.n)
     tf = flops_pair * PK / (pr["bloch"][0] / 1e3) / 1e12
+    e0.record(stream)
+    e_only = kx.kx_energy_kpoints(plan_k, theta, wk, psi_k, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_e = e0.elapsed_time(e1)
     plan_k64 = kx.Plan.for_system(kd, precision=kx.KX_FP64)
     vx_64, ex_64 = kx.kx_vx_kpoints(plan_k64, theta, wk, psi_k, stream=stream)
     torch.cuda.synchronize()
@@ -413,6 +418,7 @@ def other_workloads(kx, torch, stream, hbm, steps=3):
         "pairs_of_the_k_sum": len(wk) ** 2 * kd.n_orb ** 2,
         "mode_products_ms": pr["bloch"][0], "mode_product_launches": pr["bloch"][1],
         "other_kernels_ms": pr["bloch_other"][0], "e_x": ex_k.item(), "status": plan_k.status(),
+        "energy_only_ms": ms_e, "energy_only_rel_vs_vx_path": abs(e_only.item() - ex_k.item()) / abs(ex_k.item()),
         "vx_maxrel_vs_fp64_plan": float((vx_k - vx_64).abs().max() / vx_64.abs().max()),
         "e_x_rel_vs_fp64_plan": abs(ex_k.item() - ex_64.item()) / abs(ex_64.item()),
         "roofline": {"bound": "alu", "achieved": tf, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",

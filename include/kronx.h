@@ -298,6 +298,14 @@ int kx_vx_apply_kpoint(kx_plan *plan, int n_kpt, const double *theta, const doub
 int kx_vx_kpoints(kx_plan *plan, int n_kpt, const double *theta, const double *wk, int n_orb, const double *psi,
                   const double *occ, double *vx, double *ex, kx_stream stream);
 
+/* kx_energy_kpoints — E_x alone (Eq. 8) into ex[0] (device float64, required)
+ * through Parseval: -1/2 dV sum w_k w_q g_nk g_mq sum f(Lambda) |V^H rho|^2,
+ * rho = conj(psi_mq) psi_nk; only the forward transforms of the blocks
+ * (k, q), q >= k, are computed (the block (q, k) has the conjugate
+ * coefficients and counts twice).  Arguments as kx_vx_kpoints. */
+int kx_energy_kpoints(kx_plan *plan, int n_kpt, const double *theta, const double *wk, int n_orb,
+                      const double *psi, const double *occ, double *ex, kx_stream stream);
+
 /* kx_batch_create — groups n_sys plans (different grids, kernels and orbital
  * counts) into one CUDA graph that runs every system's kx_vx_apply.  Workspaces
  * are reserved here so that the graph holds no allocation.

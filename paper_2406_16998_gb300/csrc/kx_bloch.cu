@@ -37,6 +37,7 @@ template <typename T> constexpr int pencils_per_thread() { return sizeof(T) == 4
 template <typename T> constexpr int tile_pencils() { return 32 * pencils_per_thread<T>(); }
 constexpr size_t kBSmemTarget = 110 * 1024;  // two CTAs per SM where the split allows it
 constexpr size_t kBSmemPipeMax = 200 * 1024;  // pipelined products: operand + two tiles
+constexpr int kBMaxPerSm = 4;                  // resident pipelined CTAs per SM used (energy partial slots)
 
 template <typename T2> __device__ __forceinline__ T2 cmul_conj(T2 a, T2 b) {  // conj(a) b
     T2 r;
@@ -204,15 +205,27 @@ __global__ void __launch_bounds__(kBThreads) bloch_mode_kernel(
     }
 }
 
+// Energy-only epilogue of the third product (E_x through Parseval): item r of
+// the chunk (pair (v, m) = divmod(r0 + r, n_orb)) weighs cb g_q[m] g_k[v], and
+// each CTA writes sum weight f |Y|^2 over its outputs to partial[blockIdx.x].
+struct EnergyArgs {
+    const double *occ_q = nullptr, *occ_k = nullptr;  // nullable: occupations 1
+    int n_orb = 1;
+    long long r0 = 0;
+    double cb = 0.0;
+    double *partial = nullptr;
+};
+
 // The products that read a plain input (all but the first): persistent CTAs,
 // each with a fixed column split and a strided run of tiles, the operand staged
 // once, and the next tile copied in (cp.async) while the current one is
 // multiplied; the current tile's buffer then stages the output.  Same mapping
-// and arithmetic as bloch_mode_kernel.
-template <typename T, bool SCALE, int U>
+// and arithmetic as bloch_mode_kernel.  EPI: 0 plain, 1 output times f (third
+// product), 2 no output, the energy sum instead (third product, EnergyArgs).
+template <typename T, int EPI, int U>
 __global__ void __launch_bounds__(kBThreads) bloch_mode_pipe_kernel(
     const typename Cx<T>::t *__restrict__ in, typename Cx<T>::t *__restrict__ out, int n_cols, int n, int inner,
-    const typename Cx<T>::t *__restrict__ M, int nc, int n_split, const T *__restrict__ f) {
+    const typename Cx<T>::t *__restrict__ M, int nc, int n_split, const T *__restrict__ f, EnergyArgs ea) {
     using T2 = typename Cx<T>::t;
     constexpr int PQ = pencils_per_thread<T>();
     constexpr int QB = 32 * PQ;
@@ -262,6 +275,7 @@ __global__ void __launch_bounds__(kBThreads) bloch_mode_pipe_kernel(
             }
         }
     };
+    double e_acc = 0.0;  // EPI == 2
     if (t_first < n_tiles) issue(t_first, Tb0);
     ptx::cp_async_commit();
     int it = 0;
@@ -331,22 +345,39 @@ __global__ void __launch_bounds__(kBThreads) bloch_mode_pipe_kernel(
             const int ql = lane + 32 * j;
             if (ql >= nq) continue;
             int i_in = 0;
-            if constexpr (SCALE) i_in = (q0 + ql) % inner;
+            double wj = 0.0;
+            if constexpr (EPI != 0) {
+                const int item = (q0 + ql) / inner;
+                i_in = (q0 + ql) - item * inner;
+                if constexpr (EPI == 2) {
+                    const long long rr = ea.r0 + item;
+                    const long long vv = rr / ea.n_orb, mm = rr - vv * ea.n_orb;
+                    wj = ea.cb * (ea.occ_q ? ea.occ_q[mm] : 1.0) * (ea.occ_k ? ea.occ_k[vv] : 1.0);
+                }
+            }
+            T ej = 0;
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const int cl = warp + 8 * u;
                 if (cl < ncy) {
                     T2 v = res[j][u];
-                    if constexpr (SCALE) {
+                    if constexpr (EPI == 1) {
                         const T fv = f[(size_t)(c0 + cl) * inner + i_in];
                         v.x *= fv;
                         v.y *= fv;
                     }
-                    cur[cl * ld + ql] = v;
+                    if constexpr (EPI == 2) {
+                        const T fv = f[(size_t)(c0 + cl) * inner + i_in];
+                        ej = fma(fv, v.x * v.x + v.y * v.y, ej);
+                    } else {
+                        cur[cl * ld + ql] = v;
+                    }
                 }
             }
+            if constexpr (EPI == 2) e_acc += wj * (double)ej;
         }
         __syncthreads();
+        if constexpr (EPI == 2) continue;  // no output
         if (inner == 1) {
             for (int ql = warp; ql < nq; ql += kBWarps) {
                 T2 *dst = out + (size_t)(q0 + ql) * n + c0;
@@ -367,6 +398,17 @@ __global__ void __launch_bounds__(kBThreads) bloch_mode_pipe_kernel(
         __syncthreads();
     }
     ptx::cp_async_wait<0>();
+    if constexpr (EPI == 2) {
+        __shared__ double red[kBWarps];
+        for (int o = 16; o > 0; o >>= 1) e_acc += __shfl_xor_sync(0xffffffffu, e_acc, o);
+        if (lane == 0) red[warp] = e_acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < kBWarps; ++w) t += red[w];
+            ea.partial[blockIdx.x] = t;
+        }
+    }
 }
 
 struct BlochAxes {
@@ -613,30 +655,32 @@ void choose_split_pipe(int n, int *nc, int *n_split, int *U, size_t *smem) {
     *smem = bytes(*U);
 }
 
-template <typename T, bool SCALE, int U>
+template <typename T, int EPI, int U>
 int launch_pipe_u(kx_plan *p, long long n_tiles, size_t smem, cudaStream_t s, const typename Cx<T>::t *in,
                   typename Cx<T>::t *out, int n_cols, int n, int inner, const typename Cx<T>::t *M, int nc,
-                  int n_split, const T *f) {
+                  int n_split, const T *f, const EnergyArgs &ea) {
     static int per_sm = 0;  // resident CTAs per SM at this instantiation's shared memory (set once)
     static size_t per_sm_smem = 0;
     if (per_sm == 0 || per_sm_smem != smem) {
-        KX_CUDA_TRY(cudaFuncSetAttribute(bloch_mode_pipe_kernel<T, SCALE, U>,
+        KX_CUDA_TRY(cudaFuncSetAttribute(bloch_mode_pipe_kernel<T, EPI, U>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBSmemPipeMax));
-        KX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bloch_mode_pipe_kernel<T, SCALE, U>,
+        KX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bloch_mode_pipe_kernel<T, EPI, U>,
                                                                   kBThreads, smem));
         per_sm = std::max(per_sm, 1);
         per_sm_smem = smem;
     }
-    const long long per_split = std::max(1LL, std::min(n_tiles, (long long)per_sm * p->num_sms / n_split));
+    const long long per_split =
+        std::max(1LL, std::min(n_tiles, (long long)std::min(per_sm, kBMaxPerSm) * p->num_sms / n_split));
     const unsigned blocks = (unsigned)(per_split * n_split);
-    bloch_mode_pipe_kernel<T, SCALE, U><<<blocks, kBThreads, smem, s>>>(in, out, n_cols, n, inner, M, nc, n_split, f);
+    bloch_mode_pipe_kernel<T, EPI, U><<<blocks, kBThreads, smem, s>>>(in, out, n_cols, n, inner, M, nc, n_split, f,
+                                                                       ea);
     KX_LAUNCH_CHECK("bloch_mode_pipe_kernel launch");
     return KX_OK;
 }
 
-template <typename T, bool SCALE>
+template <typename T, int EPI>
 int launch_pipe(kx_plan *p, int axis, long long R, const typename Cx<T>::t *in, typename Cx<T>::t *out,
-                const typename Cx<T>::t *M, const T *f, cudaStream_t s) {
+                const typename Cx<T>::t *M, const T *f, cudaStream_t s, const EnergyArgs &ea = EnergyArgs()) {
     const int n = p->n[axis];
     const long long N = (long long)p->N;
     const int inner = axis == 0 ? 1 : (axis == 1 ? p->n[0] : p->n[0] * p->n[1]);
@@ -649,7 +693,8 @@ int launch_pipe(kx_plan *p, int axis, long long R, const typename Cx<T>::t *in, 
     if (smem > kBSmemPipeMax) return set_error(KX_ERR_UNSUPPORTED, "Bloch exchange: axis too long for the tile");
     if (int rc = prof_begin(p, PK_BLOCH, s)) return rc;
     const int nco = (int)n_cols;
-#define KX_BLOCH_PIPE(UU) launch_pipe_u<T, SCALE, UU>(p, n_tiles, smem, s, in, out, nco, n, inner, M, nc, n_split, f)
+#define KX_BLOCH_PIPE(UU) \
+    launch_pipe_u<T, EPI, UU>(p, n_tiles, smem, s, in, out, nco, n, inner, M, nc, n_split, f, ea)
     int rc;
     if (U == 2) rc = KX_BLOCH_PIPE(2);
     else if (U == 4) rc = KX_BLOCH_PIPE(4);
@@ -674,7 +719,7 @@ struct BlochLayout {
 };
 
 template <typename T>
-BlochLayout bloch_layout(const kx_plan *p, int n_orb, int n_vec, int n_kpt) {
+BlochLayout bloch_layout(const kx_plan *p, int n_orb, int n_vec, int n_kpt, size_t partial_doubles = 0) {
     using T2 = typename Cx<T>::t;
     BlochLayout L;
     const size_t N = p->N;
@@ -695,7 +740,7 @@ BlochLayout bloch_layout(const kx_plan *p, int n_orb, int n_vec, int n_kpt) {
     L.F = off;
     off += f32 ? al256(sizeof(T2) * N * n_vec) : 0;
     L.partial = off;
-    off += al256(sizeof(double) * 2 * p->num_sms * (size_t)std::max(1, n_kpt));
+    off += al256(sizeof(double) * std::max(partial_doubles, 2 * (size_t)p->num_sms * std::max(1, n_kpt)));
     const long long pairs = (long long)n_orb * n_vec;
     const size_t budget = (size_t)2 << 30;  // both chunk buffers
     long long chunk = (long long)std::max<size_t>(1, budget / (2 * sizeof(T2) * N));
@@ -828,11 +873,11 @@ int bloch_sweep(kx_plan *p, int n_kpt, const double *theta, const double *wk, in
             const long long R = r1 - r0;
             int rc;
             if ((rc = launch_mode<T, true, false>(p, 0, R, nullptr, A, Mf[0], nullptr, Pq, F, n_orb, r0, s))) return rc;
-            if ((rc = launch_pipe<T, false>(p, 1, R, A, B, Mf[1], nullptr, s))) return rc;
-            if ((rc = launch_pipe<T, true>(p, 2, R, B, A, Mf[2], f, s))) return rc;
-            if ((rc = launch_pipe<T, false>(p, 2, R, A, B, Mi[2], nullptr, s))) return rc;
-            if ((rc = launch_pipe<T, false>(p, 1, R, B, A, Mi[1], nullptr, s))) return rc;
-            if ((rc = launch_pipe<T, false>(p, 0, R, A, B, Mi[0], nullptr, s))) return rc;
+            if ((rc = launch_pipe<T, 0>(p, 1, R, A, B, Mf[1], nullptr, s))) return rc;
+            if ((rc = launch_pipe<T, 1>(p, 2, R, B, A, Mf[2], f, s))) return rc;
+            if ((rc = launch_pipe<T, 0>(p, 2, R, A, B, Mi[2], nullptr, s))) return rc;
+            if ((rc = launch_pipe<T, 0>(p, 1, R, B, A, Mi[1], nullptr, s))) return rc;
+            if ((rc = launch_pipe<T, 0>(p, 0, R, A, B, Mi[0], nullptr, s))) return rc;
             if ((rc = prof_begin(p, PK_BLOCH_OTHER, s))) return rc;
             const long long nv = (r1 - 1) / n_orb - r0 / n_orb + 1;
             const int ab = (int)std::min<long long>((nv * N + 255) / 256, 8LL * p->num_sms);
@@ -889,6 +934,104 @@ int bloch_all(kx_plan *p, int n_kpt, const double *theta, const double *wk, int 
     return prof_end(p, s);
 }
 
+// E_x alone (Eq. 8 through Parseval): forward transforms of the pair blocks
+// (k, q), q >= k, the block (q, k) counted by doubling (its coefficients are
+// the conjugates), the energy sum taken in the third product's epilogue.
+template <typename T>
+int bloch_energy_only(kx_plan *p, int n_kpt, const double *theta, const double *wk, int n_orb, const double *psi,
+                      const double *occ, double *ex, cudaStream_t s) {
+    using T2 = typename Cx<T>::t;
+    const long long N = (long long)p->N;
+    const long long pairs = (long long)n_orb * n_orb;
+    const long long chunk = bloch_layout<T>(p, n_orb, n_orb, n_kpt).chunk;
+    const long long n_launch = (pairs + chunk - 1) / chunk * ((long long)n_kpt * (n_kpt + 1) / 2);
+    const size_t slot = (size_t)kBMaxPerSm * p->num_sms;
+    BlochLayout L = bloch_layout<T>(p, n_orb, n_orb, n_kpt, (size_t)n_launch * slot);
+    if (int rc = ensure_workspace(p, L.total)) return rc;
+    char *ws = static_cast<char *>(p->ws.ptr);
+    T2 *Mf[3];
+    double *lam[3];
+    for (int a = 0; a < 3; ++a) {
+        Mf[a] = reinterpret_cast<T2 *>(ws + L.Mf[a]);
+        lam[a] = reinterpret_cast<double *>(ws + L.lam[a]);
+    }
+    T2 *Mi_unused = reinterpret_cast<T2 *>(ws + L.Mi[0]);
+    T *f = reinterpret_cast<T *>(ws + L.f);
+    T2 *A = reinterpret_cast<T2 *>(ws + L.A);
+    T2 *B = reinterpret_cast<T2 *>(ws + L.B);
+    double *partial = reinterpret_cast<double *>(ws + L.partial);
+    KX_CUDA_TRY(cudaMemsetAsync(partial, 0, sizeof(double) * (size_t)n_launch * slot, s));
+    const bool f32 = sizeof(T) == 4;
+    const int blocks = 4 * p->num_sms;
+    BlochAxes ax;
+    for (int a = 0; a < 3; ++a) {
+        ax.n[a] = p->n[a];
+        ax.h[a] = p->h[a];
+        ax.bc[a] = p->bc[a];
+        ax.V[a] = p->d_V[a];
+        ax.lam[a] = p->d_lam[a];
+    }
+    ax.order = p->fd_order;
+    long long li = 0;
+    for (int k = 0; k < n_kpt; ++k) {
+        const double2 *psi_k = reinterpret_cast<const double2 *>(psi) + (size_t)k * n_orb * N;
+        const T2 *F;
+        if (int rc = prof_begin(p, PK_BLOCH_OTHER, s)) return rc;
+        if (f32) {
+            T2 *Fw = reinterpret_cast<T2 *>(ws + L.F);
+            bloch_to_f32_kernel<<<blocks, 256, 0, s>>>(psi_k, reinterpret_cast<float2 *>(Fw), N * n_orb);
+            KX_LAUNCH_CHECK("bloch_to_f32_kernel launch");
+            F = Fw;
+        } else {
+            F = reinterpret_cast<const T2 *>(psi_k);
+        }
+        if (int rc = prof_end(p, s)) return rc;
+        for (int q = k; q < n_kpt; ++q) {
+            for (int a = 0; a < 3; ++a) ax.theta[a] = theta[3 * k + a] - theta[3 * q + a];
+            if (int rc = prof_begin(p, PK_BLOCH_OTHER, s)) return rc;
+            // the inverse operands are written but not used
+            bloch_basis_kernel<T><<<dim3(3, 16), 256, 0, s>>>(ax, Mf[0], Mf[1], Mf[2], Mi_unused,
+                                                              reinterpret_cast<T2 *>(ws + L.Mi[1]),
+                                                              reinterpret_cast<T2 *>(ws + L.Mi[2]), lam[0], lam[1],
+                                                              lam[2]);
+            KX_LAUNCH_CHECK("bloch_basis_kernel launch");
+            bloch_ftable_kernel<T><<<blocks, 256, 0, s>>>(p->n[0], p->n[1], p->n[2], lam[0], lam[1], lam[2],
+                                                          p->kind, p->omega, f);
+            KX_LAUNCH_CHECK("bloch_ftable_kernel launch");
+            const T2 *Pq;
+            const double2 *psi_q = reinterpret_cast<const double2 *>(psi) + (size_t)q * n_orb * N;
+            if (f32) {
+                T2 *Pw = reinterpret_cast<T2 *>(ws + L.P);
+                bloch_to_f32_kernel<<<blocks, 256, 0, s>>>(psi_q, reinterpret_cast<float2 *>(Pw), N * n_orb);
+                KX_LAUNCH_CHECK("bloch_to_f32_kernel launch");
+                Pq = Pw;
+            } else {
+                Pq = reinterpret_cast<const T2 *>(psi_q);
+            }
+            if (int rc = prof_end(p, s)) return rc;
+            EnergyArgs ea;
+            ea.occ_q = occ ? occ + (size_t)q * n_orb : nullptr;
+            ea.occ_k = occ ? occ + (size_t)k * n_orb : nullptr;
+            ea.n_orb = n_orb;
+            ea.cb = -0.5 * p->dV * wk[k] * wk[q] * (q > k ? 2.0 : 1.0);
+            for (long long r0 = 0; r0 < pairs; r0 += chunk, ++li) {
+                const long long R = std::min(pairs, r0 + chunk) - r0;
+                ea.r0 = r0;
+                ea.partial = partial + (size_t)li * slot;
+                int rc;
+                if ((rc = launch_mode<T, true, false>(p, 0, R, nullptr, A, Mf[0], nullptr, Pq, F, n_orb, r0, s)))
+                    return rc;
+                if ((rc = launch_pipe<T, 0>(p, 1, R, A, B, Mf[1], nullptr, s))) return rc;
+                if ((rc = launch_pipe<T, 2>(p, 2, R, B, nullptr, Mf[2], f, s, ea))) return rc;
+            }
+        }
+    }
+    if (int rc = prof_begin(p, PK_BLOCH_OTHER, s)) return rc;
+    bloch_energy_final_kernel<<<1, 32, 0, s>>>(partial, (int)(n_launch * slot), 1.0, ex);
+    KX_LAUNCH_CHECK("bloch_energy_final_kernel launch");
+    return prof_end(p, s);
+}
+
 }  // namespace
 
 int bloch_vx_apply(kx_plan *p, int n_kpt, const double *theta, const double *wk, int n_orb, const double *psi,
@@ -901,6 +1044,12 @@ int bloch_vx_all(kx_plan *p, int n_kpt, const double *theta, const double *wk, i
                  const double *occ, double *vx, double *ex, cudaStream_t s) {
     return p->precision == KX_FP64 ? bloch_all<double>(p, n_kpt, theta, wk, n_orb, psi, occ, vx, ex, s)
                                    : bloch_all<float>(p, n_kpt, theta, wk, n_orb, psi, occ, vx, ex, s);
+}
+
+int bloch_energy(kx_plan *p, int n_kpt, const double *theta, const double *wk, int n_orb, const double *psi,
+                 const double *occ, double *ex, cudaStream_t s) {
+    return p->precision == KX_FP64 ? bloch_energy_only<double>(p, n_kpt, theta, wk, n_orb, psi, occ, ex, s)
+                                   : bloch_energy_only<float>(p, n_kpt, theta, wk, n_orb, psi, occ, ex, s);
 }
 
 }  // namespace kx

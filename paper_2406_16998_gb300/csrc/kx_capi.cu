@@ -541,6 +541,15 @@ int kx_vx_kpoints(kx_plan *plan, int n_kpt, const double *theta, const double *w
     return bloch_vx_all(plan, n_kpt, theta, wk, n_orb, psi, occ, vx, ex, reinterpret_cast<cudaStream_t>(stream));
 }
 
+int kx_energy_kpoints(kx_plan *plan, int n_kpt, const double *theta, const double *wk, int n_orb,
+                      const double *psi, const double *occ, double *ex, kx_stream stream) {
+    if (int rc = check_plan(plan)) return rc;
+    if (int rc = check_kpoints(plan, "kx_energy_kpoints", n_kpt, theta, wk, n_orb, psi)) return rc;
+    if (!ex) return set_error(KX_ERR_ARG, "kx_energy_kpoints: NULL ex");
+    if (misaligned16(psi)) return set_error(KX_ERR_ARG, "kx_energy_kpoints: psi must be 16-byte aligned");
+    return bloch_energy(plan, n_kpt, theta, wk, n_orb, psi, occ, ex, reinterpret_cast<cudaStream_t>(stream));
+}
+
 namespace kx {
 namespace {
 // grad[a][x] = 2 dV g_a G[a][x] in place

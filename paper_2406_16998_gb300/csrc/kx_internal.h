@@ -200,6 +200,9 @@ int bloch_vx_apply(kx_plan *p, int n_kpt, const double *theta, const double *wk,
 // Vx psi_nk for every k-point (vx like psi) and, if ex, E_x into ex[0].
 int bloch_vx_all(kx_plan *p, int n_kpt, const double *theta, const double *wk, int n_orb, const double *psi,
                  const double *occ, double *vx, double *ex, cudaStream_t s);
+// E_x alone into ex[0] (forward transforms and Parseval).
+int bloch_energy(kx_plan *p, int n_kpt, const double *theta, const double *wk, int n_orb, const double *psi,
+                 const double *occ, double *ex, cudaStream_t s);
 
 // ---- multipole boundary values (kx_mp.cu)
 int mp_set(kx_plan *p, int l_max);

@@ -867,6 +867,12 @@ def test_kpoint_vx_and_energy_match_oracle(kx, case):
     # six mode products per k-point pair block (k, q), q >= k (the reversed
     # blocks reuse the same solves, conjugated), one chunk each
     assert prof["bloch"][1] == 6 * n_k * (n_k + 1) // 2
+    # E_x alone through Parseval: the three forward products per block
+    plan.profile(True)
+    e_only = kx.kx_energy_kpoints(plan, theta, wk, to_dev_orbitals(psi), dev(occ)).item()
+    prof = plan.profile_read()
+    assert prof["bloch"][1] == 3 * n_k * (n_k + 1) // 2
+    assert abs(e_only - ex_ref) < TOL_K[prec][1] * abs(ex_ref)
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -886,6 +892,12 @@ def test_kpoint_apply_to_vectors_in_chunks(kx, prec, monkeypatch):
     prof = plan.profile_read()
     assert prof["bloch"][1] == 6 * len(wk) * 4  # 15 pairs per q in chunks of 4
     assert relmax(out.cpu().numpy().T, ref) < TOL_K[prec][0]
+    # the energy alone in chunks of 4 of the 9 pairs per block (chunks that
+    # split a k-point's bands), with occupations
+    occ = np.random.default_rng(6).uniform(0.2, 1.0, (len(wk), psi.shape[2]))
+    e_ref = oracle.exchange_energy_kpoints(base, theta, wk, psi, occ)
+    e = kx.kx_energy_kpoints(plan, theta, wk, to_dev_orbitals(psi), dev(occ)).item()
+    assert abs(e - e_ref) < TOL_K[prec][1] * abs(e_ref)
 
 
 def test_kpoint_gamma_with_real_orbitals_is_the_real_path(kx):

@@ -46,79 +46,14 @@ template <typename T2> __device__ __forceinline__ T2 cmul_conj(T2 a, T2 b) {  //
     return r;
 }
 
-// One complex mode product on R grid vectors viewed as [outer][n][inner] (items
-// stacked along outer): out[o][c][i] = sum_k M[k][c] in[o][k][i] for the output
-// columns c in [c0, c0 + ncy) of this CTA's split; pencils q = o * inner + i,
-// QB = 32 PQ of them per CTA.  Warp w owns the output columns c0 + w + 8u
-// (u < U, the operand padded with zero columns up to 8U), lane l the pencils
-// l + 32j (j < PQ).  Chunk-relative indices stay below 2^31 (checked at launch).
-// FORM (first product, inner == 1): the input element of chunk item r is
-// conj(P_m[x]) F_v[x] with (v, m) = divmod(r0 + r, n_orb), formed while loading.
-// SCALE (third product, one pencil plane per item): the output is multiplied by
-// f[c * inner + i], the f(Lambda) diagonal.
-template <typename T, bool FORM, bool SCALE, int U>
-__global__ void __launch_bounds__(kBThreads) bloch_mode_kernel(
-    const typename Cx<T>::t *__restrict__ in, typename Cx<T>::t *__restrict__ out, int n_cols, int n, int inner,
-    const typename Cx<T>::t *__restrict__ M, int nc, int n_split, const T *__restrict__ f,
-    const typename Cx<T>::t *__restrict__ P, const typename Cx<T>::t *__restrict__ F, int n_orb, long long r0,
-    long long N) {
-    using T2 = typename Cx<T>::t;
-    constexpr int PQ = pencils_per_thread<T>();
-    constexpr int QB = 32 * PQ;
-    constexpr int NCP = 8 * U;  // padded operand columns
-    extern __shared__ __align__(16) unsigned char bloch_smem[];
-    T2 *Ms = reinterpret_cast<T2 *>(bloch_smem);  // n x NCP: Ms[k * NCP + cl]
-    T2 *Ts = Ms + (size_t)n * NCP;                // n x (QB + 1): Ts[k * ld + ql]
-    const int ld = QB + 1;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int split = (int)(blockIdx.x % n_split);
-    const int tile = (int)(blockIdx.x / n_split);
-    const int c0 = split * nc;
-    const int ncy = min(nc, n - c0);
-    for (int k = warp; k < n; k += kBWarps)
-        for (int cl = lane; cl < NCP; cl += 32) {
-            T2 z;
-            z.x = z.y = (T)0;
-            Ms[k * NCP + cl] = cl < ncy ? M[(size_t)k * n + c0 + cl] : z;
-        }
-    const int q0 = tile * QB;
-    const int nq = min(QB, n_cols - q0);
-    int base[PQ];  // element offset of each owned pencil (inner > 1)
-    if (inner == 1) {
-        const int ppi = (int)(N / n);  // pencils per item
-#pragma unroll 4
-        for (int ql = warp; ql < nq; ql += kBWarps) {
-            const int q = q0 + ql;
-            if constexpr (FORM) {
-                // pair indices stay below n_orb * n_vec <= 2^24
-                const int r = q / ppi;
-                const long long x0 = (long long)(q - r * ppi) * n;
-                const int rr = (int)r0 + r;
-                const int vv = rr / n_orb, m = rr - vv * n_orb;
-                const T2 *Pp = P + (long long)m * N + x0;
-                const T2 *Fp = F + (long long)vv * N + x0;
-                for (int k = lane; k < n; k += 32) Ts[k * ld + ql] = cmul_conj(Pp[k], Fp[k]);
-            } else {
-                const T2 *src = in + (size_t)q * n;
-                for (int k = lane; k < n; k += 32) Ts[k * ld + ql] = src[k];
-            }
-        }
-    } else {
-#pragma unroll
-        for (int j = 0; j < PQ; ++j) {
-            const int ql = lane + 32 * j;
-            const int q = q0 + min(ql, nq - 1);
-            const int o = q / inner;
-            base[j] = o * n * inner + (q - o * inner);
-            if (ql < nq)
-                for (int k = warp; k < n; k += kBWarps) Ts[k * ld + ql] = in[base[j] + k * inner];
-        }
-    }
-    __syncthreads();
-
-    T2 res[PQ][U];
+// res[j][u] = sum_k Ms[k][w + 8u] Ts[k][l + 32j] for the warp w and lane l of
+// the calling thread (operand padded to NCP = 8U columns).  float32: two packed
+// accumulators per output, (sum a_re v, sum a_im v), combined at the end.
+template <typename T, int PQ, int U>
+__device__ __forceinline__ void tile_products(const typename Cx<T>::t *Ts, const typename Cx<T>::t *Ms, int ld,
+                                              int n, int lane, int warp, typename Cx<T>::t (&res)[PQ][U]) {
+    constexpr int NCP = 8 * U;
     if constexpr (sizeof(T) == 4) {
-        // (sum a_re v, sum a_im v) as two packed accumulators per output
         float2 accA[PQ][U], accB[PQ][U];
 #pragma unroll
         for (int j = 0; j < PQ; ++j)
@@ -168,40 +103,80 @@ __global__ void __launch_bounds__(kBThreads) bloch_mode_kernel(
             }
         }
     }
+}
+
+// Stage the output columns [c0, c0 + ncy) of the operand (n x n, M[k][c]) with
+// zero padding up to NCP = 8U columns.
+template <typename T, int U>
+__device__ __forceinline__ void stage_operand(typename Cx<T>::t *Ms, const typename Cx<T>::t *__restrict__ M, int n,
+                                              int c0, int ncy, int lane, int warp) {
+    constexpr int NCP = 8 * U;
+    for (int k = warp; k < n; k += kBWarps)
+        for (int cl = lane; cl < NCP; cl += 32) {
+            typename Cx<T>::t z;
+            z.x = z.y = (T)0;
+            Ms[k * NCP + cl] = cl < ncy ? M[(size_t)k * n + c0 + cl] : z;
+        }
+}
+
+// The first product (mode 1 forward, pencils contiguous): for the R chunk
+// items, out[r][x2, x3][c] = sum_k M[k][c] rho_r[x2, x3][k], where item r is the
+// pair (v, m) = divmod(r0 + r, n_orb) and rho_r = conj(P_m) F_v is formed while
+// the tile is loaded.  Pencils q (N / n per item), QB = 32 PQ of them per CTA;
+// warp w owns the output columns c0 + w + 8u (u < U, operand zero-padded to
+// 8U columns), lane l the pencils l + 32j (j < PQ).  Chunk-relative indices
+// stay below 2^31 and pair indices below 2^24 (checked at launch and entry).
+template <typename T, int U>
+__global__ void __launch_bounds__(kBThreads) bloch_form_kernel(
+    typename Cx<T>::t *__restrict__ out, int n_cols, int n, const typename Cx<T>::t *__restrict__ M, int nc,
+    int n_split, const typename Cx<T>::t *__restrict__ P, const typename Cx<T>::t *__restrict__ F, int n_orb,
+    long long r0, long long N) {
+    using T2 = typename Cx<T>::t;
+    constexpr int PQ = pencils_per_thread<T>();
+    constexpr int QB = 32 * PQ;
+    constexpr int NCP = 8 * U;
+    extern __shared__ __align__(16) unsigned char bloch_smem[];
+    T2 *Ms = reinterpret_cast<T2 *>(bloch_smem);  // n x NCP
+    T2 *Ts = Ms + (size_t)n * NCP;                // n x (QB + 1): Ts[k * ld + ql]
+    const int ld = QB + 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int split = (int)(blockIdx.x % n_split);
+    const int tile = (int)(blockIdx.x / n_split);
+    const int c0 = split * nc;
+    const int ncy = min(nc, n - c0);
+    stage_operand<T, U>(Ms, M, n, c0, ncy, lane, warp);
+    const int q0 = tile * QB;
+    const int nq = min(QB, n_cols - q0);
+    const int ppi = (int)(N / n);  // pencils per item
+#pragma unroll 4
+    for (int ql = warp; ql < nq; ql += kBWarps) {
+        const int q = q0 + ql;
+        const int r = q / ppi;
+        const long long x0 = (long long)(q - r * ppi) * n;
+        const int rr = (int)r0 + r;
+        const int vv = rr / n_orb, m = rr - vv * n_orb;
+        const T2 *Pp = P + (long long)m * N + x0;
+        const T2 *Fp = F + (long long)vv * N + x0;
+        for (int k = lane; k < n; k += 32) Ts[k * ld + ql] = cmul_conj(Pp[k], Fp[k]);
+    }
+    __syncthreads();
+    T2 res[PQ][U];
+    tile_products<T, PQ, U>(Ts, Ms, ld, n, lane, warp, res);
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < PQ; ++j) {
         const int ql = lane + 32 * j;
         if (ql >= nq) continue;
-        int i_in = 0;
-        if constexpr (SCALE) i_in = (q0 + ql) % inner;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int cl = warp + 8 * u;
-            if (cl < ncy) {
-                T2 v = res[j][u];
-                if constexpr (SCALE) {
-                    const T fv = f[(size_t)(c0 + cl) * inner + i_in];
-                    v.x *= fv;
-                    v.y *= fv;
-                }
-                Ts[cl * ld + ql] = v;
-            }
+            if (cl < ncy) Ts[cl * ld + ql] = res[j][u];
         }
     }
     __syncthreads();
-    if (inner == 1) {
-        for (int ql = warp; ql < nq; ql += kBWarps) {
-            T2 *dst = out + (size_t)(q0 + ql) * n + c0;
-            for (int cl = lane; cl < ncy; cl += 32) dst[cl] = Ts[cl * ld + ql];
-        }
-    } else {
-#pragma unroll
-        for (int j = 0; j < PQ; ++j) {
-            const int ql = lane + 32 * j;
-            if (ql < nq)
-                for (int cl = warp; cl < ncy; cl += kBWarps) out[base[j] + (c0 + cl) * inner] = Ts[cl * ld + ql];
-        }
+    for (int ql = warp; ql < nq; ql += kBWarps) {
+        T2 *dst = out + (size_t)(q0 + ql) * n + c0;
+        for (int cl = lane; cl < ncy; cl += 32) dst[cl] = Ts[cl * ld + ql];
     }
 }
 
@@ -220,7 +195,7 @@ struct EnergyArgs {
 // each with a fixed column split and a strided run of tiles, the operand staged
 // once, and the next tile copied in (cp.async) while the current one is
 // multiplied; the current tile's buffer then stages the output.  Same mapping
-// and arithmetic as bloch_mode_kernel.  EPI: 0 plain, 1 output times f (third
+// and arithmetic as bloch_form_kernel.  EPI: 0 plain, 1 output times f (third
 // product), 2 no output, the energy sum instead (third product, EnergyArgs).
 template <typename T, int EPI, int U>
 __global__ void __launch_bounds__(kBThreads) bloch_mode_pipe_kernel(
@@ -242,12 +217,7 @@ __global__ void __launch_bounds__(kBThreads) bloch_mode_pipe_kernel(
     const int n_tiles = (n_cols + QB - 1) / QB;
     const int c0 = split * nc;
     const int ncy = min(nc, n - c0);
-    for (int k = warp; k < n; k += kBWarps)
-        for (int cl = lane; cl < NCP; cl += 32) {
-            T2 z;
-            z.x = z.y = (T)0;
-            Ms[k * NCP + cl] = cl < ncy ? M[(size_t)k * n + c0 + cl] : z;
-        }
+    stage_operand<T, U>(Ms, M, n, c0, ncy, lane, warp);
     auto issue = [&](int t, T2 *buf) {
         const int q0 = t * QB;
         const int nq = min(QB, n_cols - q0);
@@ -288,57 +258,7 @@ __global__ void __launch_bounds__(kBThreads) bloch_mode_pipe_kernel(
         const int q0 = t * QB;
         const int nq = min(QB, n_cols - q0);
         T2 res[PQ][U];
-        if constexpr (sizeof(T) == 4) {
-            // (sum a_re v, sum a_im v) as two packed accumulators per output
-            float2 accA[PQ][U], accB[PQ][U];
-#pragma unroll
-            for (int j = 0; j < PQ; ++j)
-#pragma unroll
-                for (int u = 0; u < U; ++u) accA[j][u] = accB[j][u] = make_float2(0.f, 0.f);
-            const float2 *mcol = Ms + warp;
-            const float2 *tcol = cur + lane;
-#pragma unroll 2
-            for (int k = 0; k < n; ++k) {
-                float2 ar[PQ], ai[PQ];
-#pragma unroll
-                for (int j = 0; j < PQ; ++j) {
-                    const float2 a = tcol[k * ld + 32 * j];
-                    ar[j] = make_float2(a.x, a.x);
-                    ai[j] = make_float2(a.y, a.y);
-                }
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const float2 v = mcol[k * NCP + 8 * u];
-#pragma unroll
-                    for (int j = 0; j < PQ; ++j) {
-                        fma2(accA[j][u], ar[j], v);
-                        fma2(accB[j][u], ai[j], v);
-                    }
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < PQ; ++j)
-#pragma unroll
-                for (int u = 0; u < U; ++u)
-                    res[j][u] = make_float2(accA[j][u].x - accB[j][u].y, accA[j][u].y + accB[j][u].x);
-        } else {
-#pragma unroll
-            for (int j = 0; j < PQ; ++j)
-#pragma unroll
-                for (int u = 0; u < U; ++u) res[j][u] = make_double2(0.0, 0.0);
-            for (int k = 0; k < n; ++k) {
-#pragma unroll
-                for (int j = 0; j < PQ; ++j) {
-                    const double2 a = cur[k * ld + lane + 32 * j];
-#pragma unroll
-                    for (int u = 0; u < U; ++u) {
-                        const double2 v = Ms[k * NCP + warp + 8 * u];
-                        res[j][u].x = fma(a.x, v.x, fma(-a.y, v.y, res[j][u].x));
-                        res[j][u].y = fma(a.x, v.y, fma(a.y, v.x, res[j][u].y));
-                    }
-                }
-            }
-        }
+        tile_products<T, PQ, U>(cur, Ms, ld, n, lane, warp, res);
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < PQ; ++j) {
@@ -588,30 +508,28 @@ void choose_split(int n, int *nc, int *n_split, int *U, size_t *smem) {
     *smem = bytes(*U);
 }
 
-template <typename T, bool FORM, bool SCALE, int U>
-int launch_mode_u(unsigned blocks, size_t smem, cudaStream_t s, const typename Cx<T>::t *in,
-                  typename Cx<T>::t *out, int n_cols, int n, int inner, const typename Cx<T>::t *M, int nc,
-                  int n_split, const T *f, const typename Cx<T>::t *P, const typename Cx<T>::t *F, int n_orb,
-                  long long r0, long long N) {
+template <typename T, int U>
+int launch_form_u(unsigned blocks, size_t smem, cudaStream_t s, typename Cx<T>::t *out, int n_cols, int n,
+                  const typename Cx<T>::t *M, int nc, int n_split, const typename Cx<T>::t *P,
+                  const typename Cx<T>::t *F, int n_orb, long long r0, long long N) {
     static bool attr = false;  // once per instantiation
     if (!attr) {
-        KX_CUDA_TRY(cudaFuncSetAttribute(bloch_mode_kernel<T, FORM, SCALE, U>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        KX_CUDA_TRY(cudaFuncSetAttribute(bloch_form_kernel<T, U>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         200 * 1024));
         attr = true;
     }
-    bloch_mode_kernel<T, FORM, SCALE, U><<<blocks, kBThreads, smem, s>>>(in, out, n_cols, n, inner, M, nc, n_split,
-                                                                         f, P, F, n_orb, r0, N);
-    KX_LAUNCH_CHECK("bloch_mode_kernel launch");
+    bloch_form_kernel<T, U><<<blocks, kBThreads, smem, s>>>(out, n_cols, n, M, nc, n_split, P, F, n_orb, r0, N);
+    KX_LAUNCH_CHECK("bloch_form_kernel launch");
     return KX_OK;
 }
 
-template <typename T, bool FORM, bool SCALE>
-int launch_mode(kx_plan *p, int axis, long long R, const typename Cx<T>::t *in, typename Cx<T>::t *out,
-                const typename Cx<T>::t *M, const T *f, const typename Cx<T>::t *P,
-                const typename Cx<T>::t *F, int n_orb, long long r0, cudaStream_t s) {
-    const int n = p->n[axis];
+// The first product of a chunk: pair densities of items [r0, r0 + R) formed
+// from P (orbitals at q) and F (vectors at k), contracted along axis 0 into out.
+template <typename T>
+int launch_form(kx_plan *p, long long R, typename Cx<T>::t *out, const typename Cx<T>::t *M,
+                const typename Cx<T>::t *P, const typename Cx<T>::t *F, int n_orb, long long r0, cudaStream_t s) {
+    const int n = p->n[0];
     const long long N = (long long)p->N;
-    const int inner = axis == 0 ? 1 : (axis == 1 ? p->n[0] : p->n[0] * p->n[1]);
     const long long n_cols = R * (N / n);
     int nc, n_split, U;
     size_t smem;
@@ -622,20 +540,19 @@ int launch_mode(kx_plan *p, int axis, long long R, const typename Cx<T>::t *in, 
     if (int rc = prof_begin(p, PK_BLOCH, s)) return rc;
     const unsigned b = (unsigned)blocks;
     const int nco = (int)n_cols;
-#define KX_BLOCH_LAUNCH(UU) \
-    launch_mode_u<T, FORM, SCALE, UU>(b, smem, s, in, out, nco, n, inner, M, nc, n_split, f, P, F, n_orb, r0, N)
+#define KX_BLOCH_FORM(UU) launch_form_u<T, UU>(b, smem, s, out, nco, n, M, nc, n_split, P, F, n_orb, r0, N)
     int rc;
-    if (U == 2) rc = KX_BLOCH_LAUNCH(2);
-    else if (U == 4) rc = KX_BLOCH_LAUNCH(4);
-    else if (U == 8) rc = KX_BLOCH_LAUNCH(8);
+    if (U == 2) rc = KX_BLOCH_FORM(2);
+    else if (U == 4) rc = KX_BLOCH_FORM(4);
+    else if (U == 8) rc = KX_BLOCH_FORM(8);
     else if constexpr (sizeof(T) == 4) {
-        if (U == 6) rc = KX_BLOCH_LAUNCH(6);
-        else if (U == 12) rc = KX_BLOCH_LAUNCH(12);
-        else rc = KX_BLOCH_LAUNCH(16);
+        if (U == 6) rc = KX_BLOCH_FORM(6);
+        else if (U == 12) rc = KX_BLOCH_FORM(12);
+        else rc = KX_BLOCH_FORM(16);
     } else {
         rc = set_error(KX_ERR_ARG, "Bloch exchange: no kernel for this split");
     }
-#undef KX_BLOCH_LAUNCH
+#undef KX_BLOCH_FORM
     if (rc) return rc;
     return prof_end(p, s);
 }
@@ -872,7 +789,7 @@ int bloch_sweep(kx_plan *p, int n_kpt, const double *theta, const double *wk, in
             const long long r1 = std::min(pairs, r0 + L.chunk);
             const long long R = r1 - r0;
             int rc;
-            if ((rc = launch_mode<T, true, false>(p, 0, R, nullptr, A, Mf[0], nullptr, Pq, F, n_orb, r0, s))) return rc;
+            if ((rc = launch_form<T>(p, R, A, Mf[0], Pq, F, n_orb, r0, s))) return rc;
             if ((rc = launch_pipe<T, 0>(p, 1, R, A, B, Mf[1], nullptr, s))) return rc;
             if ((rc = launch_pipe<T, 1>(p, 2, R, B, A, Mf[2], f, s))) return rc;
             if ((rc = launch_pipe<T, 0>(p, 2, R, A, B, Mi[2], nullptr, s))) return rc;
@@ -1019,7 +936,7 @@ int bloch_energy_only(kx_plan *p, int n_kpt, const double *theta, const double *
                 ea.r0 = r0;
                 ea.partial = partial + (size_t)li * slot;
                 int rc;
-                if ((rc = launch_mode<T, true, false>(p, 0, R, nullptr, A, Mf[0], nullptr, Pq, F, n_orb, r0, s)))
+                if ((rc = launch_form<T>(p, R, A, Mf[0], Pq, F, n_orb, r0, s)))
                     return rc;
                 if ((rc = launch_pipe<T, 0>(p, 1, R, A, B, Mf[1], nullptr, s))) return rc;
                 if ((rc = launch_pipe<T, 2>(p, 2, R, B, nullptr, Mf[2], f, s, ea))) return rc;

@@ -386,8 +386,8 @@ def other_workloads(kx, torch, stream, hbm, steps=3):
     # the error)
     kd = workloads.K1
     theta, wk = workloads.kpoint_grid(kd, workloads.K1_KGRID)
-    psi_k = torch.from_numpy(np.ascontiguousarray(
-        np.transpose(workloads.make_bloch_orbitals(kd, theta), (0, 2, 1)))).cuda()
+    psi_np = workloads.make_bloch_orbitals(kd, theta)
+    psi_k = torch.from_numpy(np.ascontiguousarray(np.transpose(psi_np, (0, 2, 1)))).cuda()
     plan_k = kx.Plan.for_system(kd, precision=kx.KX_F16X3)
     vx_k = torch.empty_like(psi_k)
     ex_k = torch.empty(1, dtype=torch.float64, device="cuda")
@@ -413,6 +413,16 @@ def other_workloads(kx, torch, stream, hbm, steps=3):
     plan_k64 = kx.Plan.for_system(kd, precision=kx.KX_FP64)
     vx_64, ex_64 = kx.kx_vx_kpoints(plan_k64, theta, wk, psi_k, stream=stream)
     torch.cuda.synchronize()
+    # the oracle as it stands on a bounded sample, beside it: Vx of band 0 at
+    # k-point 1 (its pair solves with every band of every k-point), which is
+    # also a full-size parity check of that band
+    import oracle
+    base = oracle.Plan(kd.n, kd.h, kd.bc, kd.kernel, kd.omega, kd.fd_order)
+    t0 = time.perf_counter()
+    ref_band = oracle.vx_apply_kpoint(base, theta, wk, psi_np, None, 1, psi_np[1][:, :1])[:, 0]
+    dt_o = time.perf_counter() - t0
+    got_band = vx_k[1, 0].cpu().numpy()
+    n_sample = len(wk) * kd.n_orb
     res["k1_kpoints_slab_64cube_16bands_2x2"] = {
         "ms_per_apply": ms_k, "pair_solves_per_s": PK / (ms_k / 1e3), "pairs": PK,
         "pairs_of_the_k_sum": len(wk) ** 2 * kd.n_orb ** 2,
@@ -420,6 +430,11 @@ def other_workloads(kx, torch, stream, hbm, steps=3):
         "other_kernels_ms": pr["bloch_other"][0], "e_x": ex_k.item(), "status": plan_k.status(),
         "energy_only_ms": ms_e, "energy_only_rel_vs_vx_path": abs(e_only.item() - ex_k.item()) / abs(ex_k.item()),
         "vx_maxrel_vs_fp64_plan": float((vx_k - vx_64).abs().max() / vx_64.abs().max()),
+        "vs_oracle_sampled": {"vx_band_maxrel": float(np.max(np.abs(got_band - ref_band)) / np.max(np.abs(ref_band)))},
+        "cpu_baseline": {"value": n_sample / dt_o, "unit": "pair-solves/s", "cores": len(os.sched_getaffinity(0)),
+                         "kind": "oracle",
+                         "sample": f"Vx of band 0 at k-point 1: its {n_sample} pair solves with every band of every "
+                                   f"k-point, {dt_o:.1f} s of NumPy FP64"},
         "e_x_rel_vs_fp64_plan": abs(ex_k.item() - ex_64.item()) / abs(ex_64.item()),
         "roofline": {"bound": "alu", "achieved": tf, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": tf / FP32_ALU_PEAK_TFLOPS, "algorithmic_flops_per_pair": flops_pair}}

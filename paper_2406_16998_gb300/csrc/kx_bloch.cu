@@ -331,6 +331,313 @@ __global__ void __launch_bounds__(kBThreads) bloch_mode_pipe_kernel(
     }
 }
 
+// ---- tensor-core form of the float32 products (axes with n % 8 == 0, n <= 64)
+//
+// A complex product D = A M (A: 128 pencils x n, M: n x n) is one real GEMM
+// [A_r | A_i] (128 x 2n) times B = [[M_r, M_i], [-M_i, M_r]] (2n x 2n): columns
+// [0, n) of the result are D_r, [n, 2n) are D_i.  Both operands are split into
+// fp16 hi and lo (three products hi lo, lo hi into Da, hi hi into Db, fp32 in
+// TMEM); A carries a per-tile power-of-two scale from the tile's maximum, B the
+// fixed 2^14 (|M| <= 1).  Shared-memory layouts are the no-swizzle core-matrix
+// layouts with both operands MN-major: A element (m, kk) at
+// (m/8) 128 + (kk/8) 2048 + (kk%8) 16 + (m%8) 2 bytes, B element (kk, c) at
+// (c/8) 128 + (kk/8) 32n + (kk%8) 16 + (c%8) 2 bytes.
+constexpr int kTcMaxN = 64;  // axes of 32 or 64 points (epilogue halves of 16-column chunks)
+constexpr int kTcLd = 129;  // float2 row stride of the fp32 tile (128 pencils + 1)
+
+__host__ __device__ inline size_t tc_b_bytes(int n) { return (size_t)8 * n * n; }      // one of hi / lo
+__host__ __device__ inline size_t tc_a_bytes(int n) { return (size_t)512 * n; }        // one of hi / lo
+__host__ __device__ inline size_t tc_s_bytes(int n) { return (size_t)8 * n * kTcLd; }  // fp32 tile
+__host__ __device__ inline size_t tc_smem_bytes(int n) {
+    return 1024 + 2 * tc_b_bytes(n) + 2 * tc_a_bytes(n) + tc_s_bytes(n);
+}
+
+// B = [[M_r, M_i], [-M_i, M_r]] 2^14 split into fp16 hi (first 4n^2 halves) and lo.
+__global__ void bloch_tc_bsplit_kernel(const float2 *__restrict__ M, int n, __half *__restrict__ out) {
+    const int n2 = 2 * n;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n2 * n2) return;
+    const int kk = e / n2, c = e - kk * n2;
+    const int k = kk % n, cc = c % n;
+    const float2 m = M[k * n + cc];
+    float v;
+    if (kk < n) v = c < n ? m.x : m.y;
+    else v = c < n ? -m.y : m.x;
+    v *= kVScale;
+    const __half h = __float2half_rn(v);
+    const __half l = __float2half_rn(v - __half2float(h));
+    const size_t off = (size_t)(c >> 3) * 64 + (size_t)(kk >> 3) * (16 * n) + (kk & 7) * 8 + (c & 7);  // halves
+    out[off] = h;
+    out[(size_t)4 * n * n + off] = l;
+}
+
+__device__ __forceinline__ void tc_split_store(uint8_t *hi, uint8_t *lo, int off, const float *w) {
+    __half2 h[4], l[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const __half2 hh = __floats2half2_rn(w[2 * c], w[2 * c + 1]);
+        const float2 hf = __half22float2(hh);
+        h[c] = hh;
+        l[c] = __floats2half2_rn(w[2 * c] - hf.x, w[2 * c + 1] - hf.y);
+    }
+    *reinterpret_cast<uint4 *>(hi + off) = *reinterpret_cast<uint4 *>(h);
+    *reinterpret_cast<uint4 *>(lo + off) = *reinterpret_cast<uint4 *>(l);
+}
+
+// Persistent, one CTA per SM, 256 threads; tiles of 128 pencils, strided.  Per
+// tile: the fp32 tile into shared memory (cp.async, or formed from P and F when
+// FORM), its maximum, the split A, one thread issuing the 3 x 2n/16 products,
+// a bounded wait, and an epilogue in which warp w reads TMEM lane quadrant w % 4
+// for complex columns [w / 4 * n / 2, + n / 2), unscales (times f for EPI 1, the
+// energy sum for EPI 2) and stages the output through the fp32 tile for
+// coalesced stores.  A wait that runs out sets *status and ends the kernel.
+template <bool FORM, int EPI>
+__global__ void __launch_bounds__(256, 1) bloch_tc_kernel(const float2 *__restrict__ in, float2 *__restrict__ out,
+                                                         int n_cols, int n, int inner,
+                                                         const __half *__restrict__ Bs, const float *__restrict__ f,
+                                                         const float2 *__restrict__ P, const float2 *__restrict__ F,
+                                                         int n_orb, long long r0, long long N, EnergyArgs ea,
+                                                         int *status, long long timeout_cycles) {
+    extern __shared__ uint8_t tc_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *Bh = smem, *Bl = Bh + tc_b_bytes(n);
+    uint8_t *Ah = Bl + tc_b_bytes(n), *Al = Ah + tc_a_bytes(n);
+    float2 *S = reinterpret_cast<float2 *>(Al + tc_a_bytes(n));  // [k][m], row stride kTcLd
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tslot;
+    __shared__ float s_wmax[8];
+    __shared__ double s_red[8];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) {
+        ptx::tmem_alloc(&tslot, 256);
+        ptx::tmem_relinquish();
+    }
+    if (tid == 0) {
+        ptx::mbar_init(&bar, 1);
+        ptx::fence_mbar_init();
+    }
+    {  // B hi and lo, once
+        const uint4 *src = reinterpret_cast<const uint4 *>(Bs);
+        uint4 *dst = reinterpret_cast<uint4 *>(Bh);
+        const int n16 = (int)(2 * tc_b_bytes(n) / 16);
+        for (int e = tid; e < n16; e += 256) ptx::cp_async16(dst + e, src + e, 16u);
+        ptx::cp_async_commit();
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem = tslot;
+    const int n2 = 2 * n;
+    // contiguous pencils (inner == 1) at n = 64: the transposed product, so that
+    // a TMEM lane holds one output column across pencils and stores coalesce
+    const bool transposed = inner == 1 && n == 64 && EPI == 0;
+    const uint32_t idesc = transposed ? ptx::idesc_f16(n2, 128, 1, 1) : ptx::idesc_f16(128, n2, 1, 1);
+    const int n_tiles = (n_cols + 127) / 128;
+    uint32_t phase = 0;
+    bool ok = true;
+    double e_acc = 0.0;
+    // the fp32 tile t into S[k][m] (cp.async, or formed from P and F when FORM;
+    // pencils past the end as zeros)
+    auto load_tile = [&](int t) {
+        const int q0 = t * 128;
+        const int nq = min(128, n_cols - q0);
+        if (inner == 1) {
+            const int ppi = (int)(N / n);
+            for (int m = warp; m < 128; m += 8) {
+                float2 *row = S + m;
+                if (m >= nq) {
+                    for (int k = lane; k < n; k += 32) row[k * kTcLd] = make_float2(0.f, 0.f);
+                    continue;
+                }
+                const int q = q0 + m;
+                if constexpr (FORM) {
+                    const int r = q / ppi;
+                    const long long x0 = (long long)(q - r * ppi) * n;
+                    const int rr = (int)r0 + r;
+                    const int vv = rr / n_orb, mm = rr - vv * n_orb;
+                    const float2 *Pp = P + (long long)mm * N + x0;
+                    const float2 *Fp = F + (long long)vv * N + x0;
+                    for (int k = lane; k < n; k += 32) row[k * kTcLd] = cmul_conj(Pp[k], Fp[k]);
+                } else {
+                    const float2 *src = in + (size_t)q * n;
+                    for (int k = lane; k < n; k += 32) ptx::cp_async8(row + k * kTcLd, src + k, 8u);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int m = lane + 32 * j;
+                if (m >= nq) {
+                    for (int k = warp; k < n; k += 8) S[k * kTcLd + m] = make_float2(0.f, 0.f);
+                    continue;
+                }
+                const int q = q0 + m;
+                const int o = q / inner;
+                const float2 *src = in + (size_t)o * n * inner + (q - o * inner);
+                for (int k = warp; k < n; k += 8) ptx::cp_async8(S + k * kTcLd + m, src + (size_t)k * inner, 8u);
+            }
+        }
+        ptx::cp_async_commit();
+    };
+    if (blockIdx.x < n_tiles) load_tile(blockIdx.x);
+    for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+        const int q0 = t * 128;
+        const int nq = min(128, n_cols - q0);
+        ptx::cp_async_wait<0>();
+        __syncthreads();
+        // 1. the tile's maximum and the A scale
+        float mx = 0.f;
+        for (int e = tid; e < n * 128; e += 256) {
+            const float2 v = S[(e >> 7) * kTcLd + (e & 127)];
+            mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+        }
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) s_wmax[warp] = mx;
+        __syncthreads();
+        mx = s_wmax[0];
+#pragma unroll
+        for (int w = 1; w < 8; ++w) mx = fmaxf(mx, s_wmax[w]);
+        // scale 2^e with e = 14 - exponent(max), capped at 100 so that it and
+        // its inverse stay finite: a tile below 2^-86 (vacuum far from the
+        // orbitals) then loses at most its own values, under 2^-100 of any
+        // normal tile
+        int ex = 0;
+        if (mx > 0.f && isfinite(mx)) frexpf(mx, &ex);
+        const int eA = min(14 - ex, 100);
+        const float sA = ldexpf(1.f, eA);
+        const float unscale = ldexpf(1.f, -eA - kVScaleExp);
+        // 2. A = [A_r | A_i] sA, split
+        // consecutive threads take consecutive k: their 8-pencil reads fall on
+        // distinct banks (row stride 129 float2) and their 16-byte core-matrix
+        // rows fill contiguous 128-byte runs
+        for (int task = tid; task < n * 16; task += 256) {
+            const int k = task % n, g = task / n;
+            const float2 *src = S + k * kTcLd + 8 * g;
+            float wr[8], wi[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const float2 v = src[c];
+                wr[c] = v.x * sA;
+                wi[c] = v.y * sA;
+            }
+            tc_split_store(Ah, Al, g * 128 + (k >> 3) * 2048 + (k & 7) * 16, wr);
+            tc_split_store(Ah, Al, g * 128 + ((n + k) >> 3) * 2048 + ((n + k) & 7) * 16, wi);
+        }
+        ptx::fence_proxy_async_smem();
+        __syncthreads();
+        // 3. products; S is free again, so the next tile loads while they run
+        if (tid == 0) {
+            ptx::tc_fence_after();
+            const uint32_t ah0 = ptx::smem_u32(Ah), al0 = ptx::smem_u32(Al);
+            const uint32_t bh0 = ptx::smem_u32(Bh), bl0 = ptx::smem_u32(Bl);
+            const uint32_t gb = 32u * (uint32_t)n;  // B K-group stride
+            const uint32_t da = tmem, db = tmem + (uint32_t)n2;  // n2 = 128 columns when transposed
+            for (int ks = 0; ks < n2 / 16; ++ks) {
+                const uint64_t ah = ptx::sdesc(ah0 + 4096u * ks, 2048, 128), al = ptx::sdesc(al0 + 4096u * ks, 2048, 128);
+                const uint64_t bh = ptx::sdesc(bh0 + 2u * gb * ks, gb, 128), bl = ptx::sdesc(bl0 + 2u * gb * ks, gb, 128);
+                if (transposed) {  // D^T = B^T A^T: the same shared bytes, operand roles swapped
+                    ptx::mma_f16(da, bh, al, idesc, ks > 0 ? 1u : 0u);
+                    ptx::mma_f16(da, bl, ah, idesc, 1u);
+                    ptx::mma_f16(db, bh, ah, idesc, ks > 0 ? 1u : 0u);
+                } else {
+                    ptx::mma_f16(da, ah, bl, idesc, ks > 0 ? 1u : 0u);
+                    ptx::mma_f16(da, al, bh, idesc, 1u);
+                    ptx::mma_f16(db, ah, bh, idesc, ks > 0 ? 1u : 0u);
+                }
+            }
+            ptx::mma_commit(&bar);
+        }
+        if (t + (int)gridDim.x < n_tiles) load_tile(t + gridDim.x);
+        ok = __syncthreads_and(ptx::mbar_wait_bounded(&bar, phase, timeout_cycles));
+        phase ^= 1u;
+        if (!ok) break;
+        ptx::tc_fence_after();
+        // 4. epilogue: TMEM -> registers -> global
+        if (transposed) {
+            // lane row c' of D^T: real (c' < n) or imaginary part of column c' mod n;
+            // warp halves take pencils [0, 64) and [64, 128)
+            const int qd = warp & 3, hh = warp >> 2;
+            const int cr = 32 * qd + lane;
+            const int im = cr >= n ? 1 : 0;
+            const int c = cr - im * n;
+            const uint32_t tl = tmem + ((uint32_t)(32 * qd) << 16);
+            float *ob = reinterpret_cast<float *>(out + (size_t)q0 * n + c) + im;
+            for (int m0 = 64 * hh; m0 < 64 * hh + 64; m0 += 16) {
+                float va[16], vb[16];
+                ptx::tmem_ld16x2(tl + (uint32_t)m0, tl + (uint32_t)(n2 + m0), va, vb);
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    if (m0 + j < nq) ob[(size_t)(m0 + j) * 2 * n] = (va[j] + vb[j]) * unscale;
+            }
+        } else {
+            // complex column c of row m
+            const int qd = warp & 3, hh = warp >> 2;
+            const int m = 32 * qd + lane;
+            const uint32_t tl = tmem + ((uint32_t)(32 * qd) << 16);
+            const int half = n >> 1;
+            const bool valid = m < nq;
+            const int q = q0 + min(m, nq - 1);
+            const int item = q / inner;
+            const int i_in = q - item * inner;
+            float2 *dst = inner == 1 ? out + (size_t)q * n : out + (size_t)item * n * inner + i_in;
+            double wj = 0.0;
+            if constexpr (EPI == 2) {
+                const long long rr = ea.r0 + item;
+                const long long vv = rr / ea.n_orb, mm = rr - vv * ea.n_orb;
+                wj = valid ? ea.cb * (ea.occ_q ? ea.occ_q[mm] : 1.0) * (ea.occ_k ? ea.occ_k[vv] : 1.0) : 0.0;
+            }
+            float ej = 0.f;
+            const int c_end = hh * half + half;
+            for (int c0 = hh * half; c0 < c_end; c0 += 16) {
+                float ra[16], rb[16], ia[16], ib[16];
+                ptx::tmem_ld16x2(tl + (uint32_t)c0, tl + (uint32_t)(n2 + c0), ra, rb);
+                ptx::tmem_ld16x2(tl + (uint32_t)(n + c0), tl + (uint32_t)(n2 + n + c0), ia, ib);
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    if (c0 + c >= c_end) break;
+                    float2 v = make_float2((ra[c] + rb[c]) * unscale, (ia[c] + ib[c]) * unscale);
+                    if constexpr (EPI == 1) {
+                        const float fv = f[(size_t)(c0 + c) * inner + i_in];
+                        v.x *= fv;
+                        v.y *= fv;
+                    }
+                    if constexpr (EPI == 2) {
+                        const float fv = f[(size_t)(c0 + c) * inner + i_in];
+                        ej = fmaf(fv, v.x * v.x + v.y * v.y, ej);
+                    } else if (valid) {
+                        dst[(size_t)(c0 + c) * inner] = v;
+                    }
+                }
+            }
+            if constexpr (EPI == 2) e_acc += wj * (double)ej;
+        }
+        ptx::tc_fence_before();
+    }
+    if (!ok) {
+        if (tid == 0) atomicExch(status, KX_ERR_TIMEOUT);
+        // the products whose wait ran out finish before TMEM is released
+        ptx::mbar_wait_bounded(&bar, phase ^ 1u, timeout_cycles);
+    }
+    ptx::cp_async_wait<0>();
+    if constexpr (EPI == 2) {
+        for (int o = 16; o > 0; o >>= 1) e_acc += __shfl_xor_sync(0xffffffffu, e_acc, o);
+        if (lane == 0) s_red[warp] = e_acc;
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    if constexpr (EPI == 2) {
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < 8; ++w) t += s_red[w];
+            ea.partial[blockIdx.x] = t;
+        }
+    }
+    if (warp == 0) {
+        ptx::tc_fence_after();
+        ptx::tmem_dealloc(tmem, 256);
+    }
+}
+
 struct BlochAxes {
     int n[3];
     double h[3];
@@ -628,10 +935,46 @@ int launch_pipe(kx_plan *p, int axis, long long R, const typename Cx<T>::t *in, 
     return prof_end(p, s);
 }
 
+// Tensor-core products: float32 plans, axes of 32 or 64 points (KX_BLOCH_TC, a
+// tuning and test override, is a bit mask of the axes allowed to use them: 0
+// none, 7 all).
+inline bool tc_axis(const kx_plan *p, int axis) {
+    if (p->precision == KX_FP64) return false;
+    if (const char *e = std::getenv("KX_BLOCH_TC"))
+        if (((std::atoi(e) >> axis) & 1) == 0) return false;
+    const int n = p->n[axis];
+    return n % 32 == 0 && n <= kTcMaxN;
+}
+
+template <bool FORM, int EPI>
+int launch_tc(kx_plan *p, int axis, long long R, const float2 *in, float2 *out, const __half *Bs, const float *f,
+              const float2 *P, const float2 *F, int n_orb, long long r0, cudaStream_t s,
+              const EnergyArgs &ea = EnergyArgs()) {
+    const int n = p->n[axis];
+    const long long N = (long long)p->N;
+    const int inner = axis == 0 ? 1 : (axis == 1 ? p->n[0] : p->n[0] * p->n[1]);
+    const long long n_cols = R * (N / n);
+    if (R * N >= (1LL << 31)) return set_error(KX_ERR_ARG, "Bloch exchange: chunk too large for one launch");
+    const long long n_tiles = (n_cols + 127) / 128;
+    const int grid = (int)std::min<long long>(n_tiles, p->num_sms);
+    const size_t smem = tc_smem_bytes(n);
+    static bool attr = false;  // once per instantiation
+    if (!attr) {
+        KX_CUDA_TRY(cudaFuncSetAttribute(bloch_tc_kernel<FORM, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tc_smem_bytes(kTcMaxN)));
+        attr = true;
+    }
+    if (int rc = prof_begin(p, PK_BLOCH, s)) return rc;
+    bloch_tc_kernel<FORM, EPI><<<grid, 256, smem, s>>>(in, out, (int)n_cols, n, inner, Bs, f, P, F, n_orb, r0, N, ea,
+                                                       p->d_status, 2000000000LL);
+    KX_LAUNCH_CHECK("bloch_tc_kernel launch");
+    return prof_end(p, s);
+}
+
 // Device workspace of one call: bases, eigenvalues, f table, float32 copies of
 // the orbitals and vectors (float32 plans), chunk buffers A and B.
 struct BlochLayout {
-    size_t Mf[3], Mi[3], lam[3], f, P, F, A, B, partial, total;
+    size_t Mf[3], Mi[3], lam[3], Bf[3], Bi[3], f, P, F, A, B, partial, total;
     long long chunk;
 };
 
@@ -648,6 +991,12 @@ BlochLayout bloch_layout(const kx_plan *p, int n_orb, int n_vec, int n_kpt, size
         off += al256(sizeof(T2) * p->n[a] * p->n[a]);
         L.lam[a] = off;
         off += al256(sizeof(double) * p->n[a]);
+        // split tensor-core operands (forward, inverse) of the axes that use them
+        const size_t bsz = tc_axis(p, a) ? al256(2 * tc_b_bytes(p->n[a])) : 0;
+        L.Bf[a] = off;
+        off += bsz;
+        L.Bi[a] = off;
+        off += bsz;
     }
     L.f = off;
     off += al256(sizeof(T) * N);
@@ -772,6 +1121,16 @@ int bloch_sweep(kx_plan *p, int n_kpt, const double *theta, const double *wk, in
         bloch_ftable_kernel<T><<<blocks, 256, 0, s>>>(p->n[0], p->n[1], p->n[2], lam[0], lam[1], lam[2], p->kind,
                                                       p->omega, f);
         KX_LAUNCH_CHECK("bloch_ftable_kernel launch");
+        if constexpr (sizeof(T) == 4) {
+            for (int a = 0; a < 3; ++a) {
+                if (!tc_axis(p, a)) continue;
+                const int nb = (4 * p->n[a] * p->n[a] + 255) / 256;
+                bloch_tc_bsplit_kernel<<<nb, 256, 0, s>>>(Mf[a], p->n[a], reinterpret_cast<__half *>(ws + L.Bf[a]));
+                KX_LAUNCH_CHECK("bloch_tc_bsplit_kernel launch");
+                bloch_tc_bsplit_kernel<<<nb, 256, 0, s>>>(Mi[a], p->n[a], reinterpret_cast<__half *>(ws + L.Bi[a]));
+                KX_LAUNCH_CHECK("bloch_tc_bsplit_kernel launch");
+            }
+        }
         const T2 *Pq;
         const double2 *psi_q = reinterpret_cast<const double2 *>(psi) + (size_t)q * n_orb * N;
         if (f32) {
@@ -789,12 +1148,35 @@ int bloch_sweep(kx_plan *p, int n_kpt, const double *theta, const double *wk, in
             const long long r1 = std::min(pairs, r0 + L.chunk);
             const long long R = r1 - r0;
             int rc;
-            if ((rc = launch_form<T>(p, R, A, Mf[0], Pq, F, n_orb, r0, s))) return rc;
-            if ((rc = launch_pipe<T, 0>(p, 1, R, A, B, Mf[1], nullptr, s))) return rc;
-            if ((rc = launch_pipe<T, 1>(p, 2, R, B, A, Mf[2], f, s))) return rc;
-            if ((rc = launch_pipe<T, 0>(p, 2, R, A, B, Mi[2], nullptr, s))) return rc;
-            if ((rc = launch_pipe<T, 0>(p, 1, R, B, A, Mi[1], nullptr, s))) return rc;
-            if ((rc = launch_pipe<T, 0>(p, 0, R, A, B, Mi[0], nullptr, s))) return rc;
+            if constexpr (sizeof(T) == 4) {
+                auto Bf = [&](int a) { return reinterpret_cast<const __half *>(ws + L.Bf[a]); };
+                auto Bi = [&](int a) { return reinterpret_cast<const __half *>(ws + L.Bi[a]); };
+                rc = tc_axis(p, 0) ? launch_tc<true, 0>(p, 0, R, nullptr, A, Bf(0), nullptr, Pq, F, n_orb, r0, s)
+                                   : launch_form<T>(p, R, A, Mf[0], Pq, F, n_orb, r0, s);
+                if (rc) return rc;
+                rc = tc_axis(p, 1) ? launch_tc<false, 0>(p, 1, R, A, B, Bf(1), nullptr, nullptr, nullptr, n_orb, 0, s)
+                                   : launch_pipe<T, 0>(p, 1, R, A, B, Mf[1], nullptr, s);
+                if (rc) return rc;
+                rc = tc_axis(p, 2) ? launch_tc<false, 1>(p, 2, R, B, A, Bf(2), f, nullptr, nullptr, n_orb, 0, s)
+                                   : launch_pipe<T, 1>(p, 2, R, B, A, Mf[2], f, s);
+                if (rc) return rc;
+                rc = tc_axis(p, 2) ? launch_tc<false, 0>(p, 2, R, A, B, Bi(2), nullptr, nullptr, nullptr, n_orb, 0, s)
+                                   : launch_pipe<T, 0>(p, 2, R, A, B, Mi[2], nullptr, s);
+                if (rc) return rc;
+                rc = tc_axis(p, 1) ? launch_tc<false, 0>(p, 1, R, B, A, Bi(1), nullptr, nullptr, nullptr, n_orb, 0, s)
+                                   : launch_pipe<T, 0>(p, 1, R, B, A, Mi[1], nullptr, s);
+                if (rc) return rc;
+                rc = tc_axis(p, 0) ? launch_tc<false, 0>(p, 0, R, A, B, Bi(0), nullptr, nullptr, nullptr, n_orb, 0, s)
+                                   : launch_pipe<T, 0>(p, 0, R, A, B, Mi[0], nullptr, s);
+                if (rc) return rc;
+            } else {
+                if ((rc = launch_form<T>(p, R, A, Mf[0], Pq, F, n_orb, r0, s))) return rc;
+                if ((rc = launch_pipe<T, 0>(p, 1, R, A, B, Mf[1], nullptr, s))) return rc;
+                if ((rc = launch_pipe<T, 1>(p, 2, R, B, A, Mf[2], f, s))) return rc;
+                if ((rc = launch_pipe<T, 0>(p, 2, R, A, B, Mi[2], nullptr, s))) return rc;
+                if ((rc = launch_pipe<T, 0>(p, 1, R, B, A, Mi[1], nullptr, s))) return rc;
+                if ((rc = launch_pipe<T, 0>(p, 0, R, A, B, Mi[0], nullptr, s))) return rc;
+            }
             if ((rc = prof_begin(p, PK_BLOCH_OTHER, s))) return rc;
             const long long nv = (r1 - 1) / n_orb - r0 / n_orb + 1;
             const int ab = (int)std::min<long long>((nv * N + 255) / 256, 8LL * p->num_sms);
@@ -915,6 +1297,15 @@ int bloch_energy_only(kx_plan *p, int n_kpt, const double *theta, const double *
             bloch_ftable_kernel<T><<<blocks, 256, 0, s>>>(p->n[0], p->n[1], p->n[2], lam[0], lam[1], lam[2],
                                                           p->kind, p->omega, f);
             KX_LAUNCH_CHECK("bloch_ftable_kernel launch");
+            if constexpr (sizeof(T) == 4) {
+                for (int a = 0; a < 3; ++a) {
+                    if (!tc_axis(p, a)) continue;
+                    const int nb = (4 * p->n[a] * p->n[a] + 255) / 256;
+                    bloch_tc_bsplit_kernel<<<nb, 256, 0, s>>>(Mf[a], p->n[a],
+                                                              reinterpret_cast<__half *>(ws + L.Bf[a]));
+                    KX_LAUNCH_CHECK("bloch_tc_bsplit_kernel launch");
+                }
+            }
             const T2 *Pq;
             const double2 *psi_q = reinterpret_cast<const double2 *>(psi) + (size_t)q * n_orb * N;
             if (f32) {
@@ -936,10 +1327,24 @@ int bloch_energy_only(kx_plan *p, int n_kpt, const double *theta, const double *
                 ea.r0 = r0;
                 ea.partial = partial + (size_t)li * slot;
                 int rc;
-                if ((rc = launch_form<T>(p, R, A, Mf[0], Pq, F, n_orb, r0, s)))
-                    return rc;
-                if ((rc = launch_pipe<T, 0>(p, 1, R, A, B, Mf[1], nullptr, s))) return rc;
-                if ((rc = launch_pipe<T, 2>(p, 2, R, B, nullptr, Mf[2], f, s, ea))) return rc;
+                if constexpr (sizeof(T) == 4) {
+                    auto Bf = [&](int a) { return reinterpret_cast<const __half *>(ws + L.Bf[a]); };
+                    rc = tc_axis(p, 0) ? launch_tc<true, 0>(p, 0, R, nullptr, A, Bf(0), nullptr, Pq, F, n_orb, r0, s)
+                                       : launch_form<T>(p, R, A, Mf[0], Pq, F, n_orb, r0, s);
+                    if (rc) return rc;
+                    rc = tc_axis(p, 1)
+                             ? launch_tc<false, 0>(p, 1, R, A, B, Bf(1), nullptr, nullptr, nullptr, n_orb, 0, s)
+                             : launch_pipe<T, 0>(p, 1, R, A, B, Mf[1], nullptr, s);
+                    if (rc) return rc;
+                    rc = tc_axis(p, 2)
+                             ? launch_tc<false, 2>(p, 2, R, B, nullptr, Bf(2), f, nullptr, nullptr, n_orb, 0, s, ea)
+                             : launch_pipe<T, 2>(p, 2, R, B, nullptr, Mf[2], f, s, ea);
+                    if (rc) return rc;
+                } else {
+                    if ((rc = launch_form<T>(p, R, A, Mf[0], Pq, F, n_orb, r0, s))) return rc;
+                    if ((rc = launch_pipe<T, 0>(p, 1, R, A, B, Mf[1], nullptr, s))) return rc;
+                    if ((rc = launch_pipe<T, 2>(p, 2, R, B, nullptr, Mf[2], f, s, ea))) return rc;
+                }
             }
         }
     }

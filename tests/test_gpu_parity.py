@@ -832,6 +832,9 @@ KPOINT_CASES = [
     ((8, 24, 16), (0.5, 0.4, 0.5), (D, P, D), S, 2, (1, 3, 1), (0.0, 0.0), 1),
     ((100, 6, 5), (0.3, 0.5, 0.5), (P, D, D), U, 2, (2, 1, 1), (0.0, 0.0), 0),    # several column splits
     ((128, 8, 8), (0.3, 0.5, 0.5), (P, D, D), S, 2, (2, 1, 1), (0.0, 0.0), 1),
+    # axes of 32 and 64 points take the tensor-core products on float32 plans
+    ((32, 16, 64), (0.45, 0.5, 0.4), (P, P, D), U, 3, (2, 2, 1), (0.0, 0.0), 1),
+    ((64, 32, 8), (0.3, 0.4, 0.5), (P, D, P), S, 2, (2, 1, 2), (0.3, 0.1), 1),
 ]
 
 
@@ -873,6 +876,32 @@ def test_kpoint_vx_and_energy_match_oracle(kx, case):
     prof = plan.profile_read()
     assert prof["bloch"][1] == 3 * n_k * (n_k + 1) // 2
     assert abs(e_only - ex_ref) < TOL_K[prec][1] * abs(ex_ref)
+
+
+@pytest.mark.parametrize("case", [8, 9])
+def test_kpoint_tensor_core_and_cuda_core_products(kx, case, monkeypatch):
+    """Axes of 32 and 64 points run their products on the tensor cores (split
+    fp16, per-tile scale); with KX_BLOCH_TC=0 the same plan uses the CUDA-core
+    kernels.  Both match the oracle; chunks of 5 pairs make tiles straddle
+    items."""
+    sysd, theta, wk, psi, occ, prec = kpoint_inputs(case, 340 + case)
+    base = oracle.Plan(sysd.n, sysd.h, sysd.bc, sysd.kernel)
+    vx_ref, ex_ref = oracle.vx_kpoints(base, theta, wk, psi, occ)
+    plan = kx.Plan(sysd.n, sysd.h, sysd.bc, sysd.kernel, precision=prec)
+    monkeypatch.setenv("KX_CHUNK_PAIRS", "5")
+    out = {}
+    for tc in ("1", "0"):
+        monkeypatch.setenv("KX_BLOCH_TC", tc)
+        vx, ex = kx.kx_vx_kpoints(plan, theta, wk, to_dev_orbitals(psi), dev(occ))
+        e_only = kx.kx_energy_kpoints(plan, theta, wk, to_dev_orbitals(psi), dev(occ)).item()
+        torch.cuda.synchronize()
+        assert plan.status() == kx.KX_OK
+        vx = vx.cpu().numpy().transpose(0, 2, 1)
+        assert relmax(vx, vx_ref) < TOL_K[prec][0], tc
+        assert abs(ex.item() - ex_ref) < TOL_K[prec][1] * abs(ex_ref), tc
+        assert abs(e_only - ex_ref) < TOL_K[prec][1] * abs(ex_ref), tc
+        out[tc] = vx
+    assert relmax(out["1"], out["0"]) < TOL_K[prec][0]
 
 
 @pytest.mark.parametrize("prec", [0, 1])

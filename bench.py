@@ -381,9 +381,10 @@ def other_workloads(kx, torch, stream, hbm, steps=3):
     # Bloch k-points: the 64^3 slab (periodic x1 and x2, vacuum along x3), 16 bands
     # on a 2 x 2 k-grid; Vx psi at every k-point needs the pair blocks (k, q),
     # q >= k (10 of 16: a reversed block is the conjugate solve), 16 x 16 pair
-    # solves each, six complex mode products of 8 n_a N flops per solve
-    # (16 N (n1 + n2 + n3)), complex float32 on the CUDA cores (float64 plan for
-    # the error)
+    # solves each, six complex mode products per solve on the tensor cores (axes
+    # of 64 points): each reads and writes the solve's complex float32 grid
+    # vector once, 16 N bytes, so 96 N bytes per solve (the HBM roofline);
+    # 16 N (n1 + n2 + n3) useful flops per solve (float64 plan for the error)
     kd = workloads.K1
     theta, wk = workloads.kpoint_grid(kd, workloads.K1_KGRID)
     psi_np = workloads.make_bloch_orbitals(kd, theta)
@@ -404,7 +405,9 @@ def other_workloads(kx, torch, stream, hbm, steps=3):
     plan_k.profile(False)
     PK = len(wk) * (len(wk) + 1) // 2 * kd.n_orb ** 2
     flops_pair = 16.0 * kd.N * sum(kd.n)
+    bytes_pair = 96.0 * kd.N
     tf = flops_pair * PK / (pr["bloch"][0] / 1e3) / 1e12
+    gbs_k = bytes_pair * PK / (pr["bloch"][0] / 1e3) / 1e9
     e0.record(stream)
     e_only = kx.kx_energy_kpoints(plan_k, theta, wk, psi_k, stream=stream)
     e1.record(stream)
@@ -436,8 +439,9 @@ def other_workloads(kx, torch, stream, hbm, steps=3):
                          "sample": f"Vx of band 0 at k-point 1: its {n_sample} pair solves with every band of every "
                                    f"k-point, {dt_o:.1f} s of NumPy FP64"},
         "e_x_rel_vs_fp64_plan": abs(ex_k.item() - ex_64.item()) / abs(ex_64.item()),
-        "roofline": {"bound": "alu", "achieved": tf, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": tf / FP32_ALU_PEAK_TFLOPS, "algorithmic_flops_per_pair": flops_pair}}
+        "useful_tflops": tf,
+        "roofline": {"bound": "hbm", "achieved": gbs_k, "peak": hbm, "unit": "GB/s", "frac": gbs_k / hbm,
+                     "algorithmic_bytes_per_pair": bytes_pair}}
     return res
 
 

@@ -441,8 +441,40 @@ __global__ void __launch_bounds__(256, 1) bloch_tc_kernel(const float2 *__restri
     auto load_tile = [&](int t) {
         const int q0 = t * 128;
         const int nq = min(128, n_cols - q0);
-        if (inner == 1) {
+        if (FORM) {
+            // four pencils per warp at a time, all their loads issued before use
+            // (n is 32 or 64: one or two values per lane and pencil)
             const int ppi = (int)(N / n);
+            for (int m = warp; m < 128; m += 32) {
+                float2 pv[4][2], fv[4][2];
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int mb = m + 8 * b;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) pv[b][h] = fv[b][h] = make_float2(0.f, 0.f);
+                    if (mb < nq) {
+                        const int q = q0 + mb;
+                        const int r = q / ppi;
+                        const long long x0 = (long long)(q - r * ppi) * n;
+                        const int rr = (int)r0 + r;
+                        const int vv = rr / n_orb, mm = rr - vv * n_orb;
+                        const float2 *Pp = P + (long long)mm * N + x0;
+                        const float2 *Fp = F + (long long)vv * N + x0;
+#pragma unroll
+                        for (int h = 0; h < 2; ++h)
+                            if (lane + 32 * h < n) {
+                                pv[b][h] = Pp[lane + 32 * h];
+                                fv[b][h] = Fp[lane + 32 * h];
+                            }
+                    }
+                }
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+#pragma unroll
+                    for (int h = 0; h < 2; ++h)
+                        if (lane + 32 * h < n) S[(lane + 32 * h) * kTcLd + m + 8 * b] = cmul_conj(pv[b][h], fv[b][h]);
+            }
+        } else if (inner == 1) {
             for (int m = warp; m < 128; m += 8) {
                 float2 *row = S + m;
                 if (m >= nq) {
@@ -450,15 +482,7 @@ __global__ void __launch_bounds__(256, 1) bloch_tc_kernel(const float2 *__restri
                     continue;
                 }
                 const int q = q0 + m;
-                if constexpr (FORM) {
-                    const int r = q / ppi;
-                    const long long x0 = (long long)(q - r * ppi) * n;
-                    const int rr = (int)r0 + r;
-                    const int vv = rr / n_orb, mm = rr - vv * n_orb;
-                    const float2 *Pp = P + (long long)mm * N + x0;
-                    const float2 *Fp = F + (long long)vv * N + x0;
-                    for (int k = lane; k < n; k += 32) row[k * kTcLd] = cmul_conj(Pp[k], Fp[k]);
-                } else {
+                {
                     const float2 *src = in + (size_t)q * n;
                     for (int k = lane; k < n; k += 32) ptx::cp_async8(row + k * kTcLd, src + k, 8u);
                 }
@@ -548,6 +572,17 @@ __global__ void __launch_bounds__(256, 1) bloch_tc_kernel(const float2 *__restri
             ptx::mma_commit(&bar);
         }
         if (t + (int)gridDim.x < n_tiles) load_tile(t + gridDim.x);
+        // EPI 1 and 2: this thread's f(Lambda) values (row m, its n / 2 columns),
+        // fetched while the products run
+        float fpre[kTcMaxN / 2];
+        if constexpr (EPI != 0) {
+            const int m = 32 * (warp & 3) + lane, hh = warp >> 2;
+            const int q = q0 + min(m, nq - 1);
+            const int i_in = q - (q / inner) * inner;
+#pragma unroll
+            for (int c = 0; c < kTcMaxN / 2; ++c)
+                fpre[c] = c < (n >> 1) ? f[(size_t)(hh * (n >> 1) + c) * inner + i_in] : 0.f;
+        }
         ok = __syncthreads_and(ptx::mbar_wait_bounded(&bar, phase, timeout_cycles));
         phase ^= 1u;
         if (!ok) break;
@@ -587,22 +622,25 @@ __global__ void __launch_bounds__(256, 1) bloch_tc_kernel(const float2 *__restri
                 wj = valid ? ea.cb * (ea.occ_q ? ea.occ_q[mm] : 1.0) * (ea.occ_k ? ea.occ_k[vv] : 1.0) : 0.0;
             }
             float ej = 0.f;
-            const int c_end = hh * half + half;
-            for (int c0 = hh * half; c0 < c_end; c0 += 16) {
+            // half is 16 or 32: one or two chunks of 16 columns (indices fixed at
+            // compile time so that fpre stays in registers)
+#pragma unroll
+            for (int cc = 0; cc < kTcMaxN / 32; ++cc) {
+                if (16 * cc >= half) break;
+                const int c0 = hh * half + 16 * cc;
                 float ra[16], rb[16], ia[16], ib[16];
                 ptx::tmem_ld16x2(tl + (uint32_t)c0, tl + (uint32_t)(n2 + c0), ra, rb);
                 ptx::tmem_ld16x2(tl + (uint32_t)(n + c0), tl + (uint32_t)(n2 + n + c0), ia, ib);
 #pragma unroll
                 for (int c = 0; c < 16; ++c) {
-                    if (c0 + c >= c_end) break;
                     float2 v = make_float2((ra[c] + rb[c]) * unscale, (ia[c] + ib[c]) * unscale);
                     if constexpr (EPI == 1) {
-                        const float fv = f[(size_t)(c0 + c) * inner + i_in];
+                        const float fv = fpre[16 * cc + c];
                         v.x *= fv;
                         v.y *= fv;
                     }
                     if constexpr (EPI == 2) {
-                        const float fv = f[(size_t)(c0 + c) * inner + i_in];
+                        const float fv = fpre[16 * cc + c];
                         ej = fmaf(fv, v.x * v.x + v.y * v.y, ej);
                     } else if (valid) {
                         dst[(size_t)(c0 + c) * inner] = v;

@@ -835,6 +835,10 @@ KPOINT_CASES = [
     # axes of 32 and 64 points take the tensor-core products on float32 plans
     ((32, 16, 64), (0.45, 0.5, 0.4), (P, P, D), U, 3, (2, 2, 1), (0.0, 0.0), 1),
     ((64, 32, 8), (0.3, 0.4, 0.5), (P, D, P), S, 2, (2, 1, 2), (0.3, 0.1), 1),
+    # 64 pencils per item: 128-pencil tensor-core tiles straddle two items, and
+    # 9 pairs leave a ragged last tile (first product, and the f-scaled third)
+    ((64, 8, 8), (0.3, 0.5, 0.5), (P, D, D), U, 3, (2, 1, 1), (0.0, 0.0), 1),
+    ((8, 8, 64), (0.5, 0.5, 0.3), (D, D, P), S, 3, (1, 1, 3), (0.0, 0.0), 1),
 ]
 
 
@@ -878,7 +882,7 @@ def test_kpoint_vx_and_energy_match_oracle(kx, case):
     assert abs(e_only - ex_ref) < TOL_K[prec][1] * abs(ex_ref)
 
 
-@pytest.mark.parametrize("case", [8, 9])
+@pytest.mark.parametrize("case", [8, 9, 10, 11])
 def test_kpoint_tensor_core_and_cuda_core_products(kx, case, monkeypatch):
     """Axes of 32 and 64 points run their products on the tensor cores (split
     fp16, per-tile scale); with KX_BLOCH_TC=0 the same plan uses the CUDA-core

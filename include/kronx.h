@@ -272,9 +272,15 @@ int kx_ace_apply(kx_plan *plan, int n_xi, const double *xi, int n_vec, const dou
  *   occ    in: n_kpt x n_orb occupations g_mq (device) or NULL for 1.
  * The forward transform contracts each axis with conj(Vk), the inverse with Vk;
  * along a Bloch axis Vk[x][m] = e^{i (2 pi m + theta) x / n} / sqrt(n).  The mode
- * products run in complex float64 on the CUDA cores for KX_FP64 plans and in
- * complex float32 (float64 accumulation of Vx across bands) for the others
- * (relative error ~1e-6).  Queued on the stream, no host synchronisation.
+ * products run in complex float64 on the CUDA cores for KX_FP64 plans; for the
+ * others in complex float32 data, on the tensor cores (fp16 hi/lo split
+ * products, fp32 accumulation) along axes of 32 or 64 points and on the CUDA
+ * cores along the rest, with float64 accumulation of Vx across bands (relative
+ * error ~1e-6).  The environment variable KX_BLOCH_TC, read at each call, is a
+ * bit mask of the axes allowed the tensor-core products (default all; 0 none).
+ * A bounded wait inside a tensor-core product that runs out records
+ * KX_ERR_TIMEOUT in the plan status (kx_plan_status).  Queued on the stream,
+ * no host synchronisation.
  * KX_ERR_UNSUPPORTED for plans with multipole boundary values; KX_ERR_SINGULAR
  * does not arise past kx_plan_create (an unscreened plan has a Dirichlet axis
  * or is rejected there). */

@@ -9,11 +9,13 @@
 // with the stencil's symbol (w_0 + 2 sum_p w_p cos(p kappa_m)) / h^2 as
 // eigenvalue, so the complex basis of each q is written in closed form; Dirichlet
 // axes keep the plan's real eigenvectors.  The forward transform contracts with
-// conj(Vk), the inverse with Vk.  The six complex mode products run on the CUDA
-// cores, in float64 for KX_FP64 plans and in float32 (packed f32x2 FMAs) for the
-// others; the pair density is formed inside the first product and f(Lambda) is
-// applied inside the third.  For Vx psi at every k-point the block of pairs
-// (k, q), q > k, is solved once: read conjugated it is the block (q, k).
+// conj(Vk), the inverse with Vk.  The six complex mode products run on the
+// tensor cores (split fp16 products, float32 plans, axes of 32 or 64 points:
+// bloch_tc_kernel) or on the CUDA cores (float64 for KX_FP64 plans, float32 with
+// packed f32x2 FMAs otherwise: bloch_form_kernel, bloch_mode_pipe_kernel); the
+// pair density is formed inside the first product and f(Lambda) is applied
+// inside the third.  For Vx psi at every k-point the block of pairs (k, q),
+// q > k, is solved once: read conjugated it is the block (q, k).
 #include "kx_internal.h"
 #include "kx_conv.cuh"
 #include "kx_fd.cuh"
@@ -331,7 +333,7 @@ __global__ void __launch_bounds__(kBThreads) bloch_mode_pipe_kernel(
     }
 }
 
-// ---- tensor-core form of the float32 products (axes with n % 8 == 0, n <= 64)
+// ---- tensor-core form of the float32 products (axes of 32 or 64 points)
 //
 // A complex product D = A M (A: 128 pencils x n, M: n x n) is one real GEMM
 // [A_r | A_i] (128 x 2n) times B = [[M_r, M_i], [-M_i, M_r]] (2n x 2n): columns
@@ -385,12 +387,17 @@ __device__ __forceinline__ void tc_split_store(uint8_t *hi, uint8_t *lo, int off
 }
 
 // Persistent, one CTA per SM, 256 threads; tiles of 128 pencils, strided.  Per
-// tile: the fp32 tile into shared memory (cp.async, or formed from P and F when
-// FORM), its maximum, the split A, one thread issuing the 3 x 2n/16 products,
-// a bounded wait, and an epilogue in which warp w reads TMEM lane quadrant w % 4
-// for complex columns [w / 4 * n / 2, + n / 2), unscales (times f for EPI 1, the
-// energy sum for EPI 2) and stages the output through the fp32 tile for
-// coalesced stores.  A wait that runs out sets *status and ends the kernel.
+// tile: its maximum over the fp32 tile in shared memory, the split A, one
+// thread issuing the 3 x 2n/16 products and, while they run, the next tile's
+// fp32 values copied in (cp.async, or formed from P and F when FORM) and this
+// tile's f(Lambda) values fetched (EPI 1, 2); then a bounded wait and an
+// epilogue in which warp w reads TMEM lane quadrant w % 4 for complex columns
+// [w / 4 * n / 2, + n / 2), unscales (times f for EPI 1, the energy sum for
+// EPI 2) and stores from registers, consecutive pencils in consecutive lanes.
+// For contiguous pencils at n = 64 (mode 1) it computes the transpose D^T =
+// B^T A^T instead (same shared bytes, operand roles swapped), so that a lane
+// holds one output column and consecutive lanes store consecutive addresses.
+// A wait that runs out sets *status and ends the kernel.
 template <bool FORM, int EPI>
 __global__ void __launch_bounds__(256, 1) bloch_tc_kernel(const float2 *__restrict__ in, float2 *__restrict__ out,
                                                          int n_cols, int n, int inner,

@@ -31,6 +31,10 @@
  *     this boundary.  kx_last_error_detail() gives a one-line explanation of the
  *     last failure on the calling host thread.
  *   - Integration weights: <a, b> = dV * sum(a * b), dV = h1*h2*h3.
+ *   - A plan owns one workspace: calls on the same plan must be issued from one
+ *     host thread and on one stream at a time (or be ordered by the caller);
+ *     different plans are independent.  Complex grid vectors (k-point calls)
+ *     are interleaved (re, im) float64 pairs, 16-byte aligned.
  */
 #ifndef KRONX_H
 #define KRONX_H

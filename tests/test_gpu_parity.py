@@ -1007,3 +1007,53 @@ def test_kpoint_full_size_sampled(kx):
     e_def = 0.5 * sysd.dV * sum(wk[q] * np.vdot(psi[q][:, m], vxn[q, m]).real
                                for q in range(len(wk)) for m in range(sysd.n_orb))
     assert abs(ex.item() - e_def) < 1e-9 * abs(e_def) and ex.item() < 0
+
+
+# ---------------------------------------------------------------- invariances (no oracle)
+@pytest.mark.parametrize("prec", [0, 1])
+def test_invariances_on_gpu(kx, prec):
+    """Orbital rotation (E_x fixed, Vx psi -> (Vx psi) U), axis permutation (the
+    transposed grid gives the transposed result) and scaling (Vx(c psi) =
+    c^3 Vx(psi), E_x(c psi) = c^4 E_x(psi)) through the CUDA path."""
+    n, h, bc, kind = (16, 24, 32), (0.45, 0.4, 0.5), (D, P, D), S
+    sysd = system(n, h, bc, kind, 5, 401)
+    psi = workloads.make_orbitals(sysd)
+    plan = kx.Plan(n, h, bc, kind, precision=prec)
+    vx0, ex0 = kx.kx_vx_apply(plan, dev(psi.T))
+    vx0 = vx0.cpu().numpy().T
+    ex0 = ex0.item()
+    tv, te = TOL[prec]["vx"], TOL[prec]["ex"]
+    # rotation
+    U, _ = np.linalg.qr(np.random.default_rng(9).standard_normal((5, 5)))
+    vxr, exr = kx.kx_vx_apply(plan, dev((psi @ U).T))
+    assert relmax(vxr.cpu().numpy().T, vx0 @ U) < 10 * tv
+    assert abs(exr.item() - ex0) < 10 * te * abs(ex0)
+    # axis permutation x1 <-> x2
+    n_p, h_p, bc_p = (n[1], n[0], n[2]), (h[1], h[0], h[2]), (bc[1], bc[0], bc[2])
+    cube = psi.reshape(n[2], n[1], n[0], 5)
+    psi_p = np.ascontiguousarray(cube.transpose(0, 2, 1, 3)).reshape(-1, 5)
+    plan_p = kx.Plan(n_p, h_p, bc_p, kind, precision=prec)
+    vxp, exp_ = kx.kx_vx_apply(plan_p, dev(psi_p.T))
+    ref_p = vx0.reshape(n[2], n[1], n[0], 5).transpose(0, 2, 1, 3).reshape(-1, 5)
+    assert relmax(vxp.cpu().numpy().T, ref_p) < 10 * tv
+    assert abs(exp_.item() - ex0) < 10 * te * abs(ex0)
+    # scaling
+    c = 1.7
+    vxs, exs = kx.kx_vx_apply(plan, dev((c * psi).T))
+    assert relmax(vxs.cpu().numpy().T, c ** 3 * vx0) < 10 * tv
+    assert abs(exs.item() - c ** 4 * ex0) < 10 * te * abs(c ** 4 * ex0)
+
+
+@pytest.mark.parametrize("case", [1, 9])
+def test_kpoint_gauge_invariance(kx, case):
+    """A global phase per k-point on the Bloch orbitals (a gauge change) leaves
+    E_x unchanged and multiplies Vx psi_k by the same phase."""
+    sysd, theta, wk, psi, occ, prec = kpoint_inputs(case, 420 + case)
+    plan = kx.Plan(sysd.n, sysd.h, sysd.bc, sysd.kernel, precision=prec)
+    vx0, ex0 = kx.kx_vx_kpoints(plan, theta, wk, to_dev_orbitals(psi), dev(occ))
+    vx0 = vx0.cpu().numpy()
+    alpha = np.random.default_rng(11).uniform(0, 2 * np.pi, len(wk))
+    ph = np.exp(1j * alpha)
+    vx1, ex1 = kx.kx_vx_kpoints(plan, theta, wk, to_dev_orbitals(psi * ph[:, None, None]), dev(occ))
+    assert relmax(vx1.cpu().numpy(), vx0 * ph[:, None, None]) < 5 * TOL_K[prec][0]
+    assert abs(ex1.item() - ex0.item()) < 5 * TOL_K[prec][1] * abs(ex0.item())

@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(kBThreads) bloch_mode_pipe_kernel(
 // (m/8) 128 + (kk/8) 2048 + (kk%8) 16 + (m%8) 2 bytes, B element (kk, c) at
 // (c/8) 128 + (kk/8) 32n + (kk%8) 16 + (c%8) 2 bytes.
 constexpr int kTcMaxN = 64;  // axes of 32 or 64 points (epilogue halves of 16-column chunks)
-constexpr int kTcLd = 129;  // float2 row stride of the fp32 tile (128 pencils + 1)
+constexpr int kTcLd = 130;  // float2 row stride of the fp32 tile (128 pencils + 2: 16-byte rows)
 
 __host__ __device__ inline size_t tc_b_bytes(int n) { return (size_t)8 * n * n; }      // one of hi / lo
 __host__ __device__ inline size_t tc_a_bytes(int n) { return (size_t)512 * n; }        // one of hi / lo
@@ -518,9 +518,9 @@ __global__ void __launch_bounds__(256, 1) bloch_tc_kernel(const float2 *__restri
         __syncthreads();
         // 1. the tile's maximum and the A scale
         float mx = 0.f;
-        for (int e = tid; e < n * 128; e += 256) {
-            const float2 v = S[(e >> 7) * kTcLd + (e & 127)];
-            mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+        for (int e = tid; e < n * 64; e += 256) {  // two complex values per load
+            const float4 v = reinterpret_cast<const float4 *>(S + (e >> 6) * kTcLd)[e & 63];
+            mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
         }
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         if (lane == 0) s_wmax[warp] = mx;
@@ -543,13 +543,15 @@ __global__ void __launch_bounds__(256, 1) bloch_tc_kernel(const float2 *__restri
         // rows fill contiguous 128-byte runs
         for (int task = tid; task < n * 16; task += 256) {
             const int k = task % n, g = task / n;
-            const float2 *src = S + k * kTcLd + 8 * g;
+            const float4 *src = reinterpret_cast<const float4 *>(S + k * kTcLd + 8 * g);
             float wr[8], wi[8];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const float2 v = src[c];
-                wr[c] = v.x * sA;
-                wi[c] = v.y * sA;
+            for (int c = 0; c < 4; ++c) {
+                const float4 v = src[c];
+                wr[2 * c] = v.x * sA;
+                wi[2 * c] = v.y * sA;
+                wr[2 * c + 1] = v.z * sA;
+                wi[2 * c + 1] = v.w * sA;
             }
             tc_split_store(Ah, Al, g * 128 + (k >> 3) * 2048 + (k & 7) * 16, wr);
             tc_split_store(Ah, Al, g * 128 + ((n + k) >> 3) * 2048 + ((n + k) & 7) * 16, wi);

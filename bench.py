@@ -408,6 +408,19 @@ def other_workloads(kx, torch, stream, hbm, steps=3):
     bytes_pair = 96.0 * kd.N
     tf = flops_pair * PK / (pr["bloch"][0] / 1e3) / 1e12
     gbs_k = bytes_pair * PK / (pr["bloch"][0] / 1e3) / 1e9
+    # the same apply with the CUDA-core products (KX_BLOCH_TC=0), for comparison
+    vx_cc = torch.empty_like(psi_k)
+    os.environ["KX_BLOCH_TC"] = "0"
+    try:
+        kx.kx_vx_kpoints(plan_k, theta, wk, psi_k, out=vx_cc, stream=stream)
+        plan_k.profile(True)
+        kx.kx_vx_kpoints(plan_k, theta, wk, psi_k, out=vx_cc, stream=stream)
+        pr_cc = plan_k.profile_read()
+        plan_k.profile(False)
+    finally:
+        del os.environ["KX_BLOCH_TC"]
+    cc_rel = float((vx_cc - vx_k).abs().max() / vx_k.abs().max())
+    del vx_cc
     e0.record(stream)
     e_only = kx.kx_energy_kpoints(plan_k, theta, wk, psi_k, stream=stream)
     e1.record(stream)
@@ -430,6 +443,7 @@ def other_workloads(kx, torch, stream, hbm, steps=3):
         "ms_per_apply": ms_k, "pair_solves_per_s": PK / (ms_k / 1e3), "pairs": PK,
         "pairs_of_the_k_sum": len(wk) ** 2 * kd.n_orb ** 2,
         "mode_products_ms": pr["bloch"][0], "mode_product_launches": pr["bloch"][1],
+        "cuda_core_mode_products_ms": pr_cc["bloch"][0], "cuda_core_vx_maxrel_vs_tensor_core": cc_rel,
         "other_kernels_ms": pr["bloch_other"][0], "e_x": ex_k.item(), "status": plan_k.status(),
         "energy_only_ms": ms_e, "energy_only_rel_vs_vx_path": abs(e_only.item() - ex_k.item()) / abs(ex_k.item()),
         "vx_maxrel_vs_fp64_plan": float((vx_k - vx_64).abs().max() / vx_64.abs().max()),

@@ -27,8 +27,8 @@ def kx():
 def test_header_declares_the_boundary():
     names = header_functions()
     for required in ["kx_plan_create", "kx_plan_destroy", "kx_vx_apply", "kx_energy", "kx_apply_fL", "kx_ace",
-                     "kx_ace_apply", "kx_vx_apply_kpoint", "kx_vx_kpoints", "kx_energy_kpoints", "kx_batch_create", "kx_batch_run", "kx_autotune", "kx_last_error_detail",
-                     "kx_strerror"]:
+                     "kx_ace_apply", "kx_vx_apply_kpoint", "kx_vx_kpoints", "kx_energy_kpoints", "kx_batch_create",
+                     "kx_batch_run", "kx_autotune", "kx_last_error_detail", "kx_strerror"]:
         assert required in names
 
 
@@ -85,3 +85,7 @@ def test_null_arguments(kx):
     assert L.kx_apply_fL(None, 1, None, None, None) == 1
     assert L.kx_plan_destroy(None) == 0
     assert L.kx_batch_destroy(None) == 0
+    # the k-point calls reject a missing plan before any argument is used
+    assert L.kx_vx_kpoints(None, 1, None, None, 1, None, None, None, None, None) == 1
+    assert L.kx_vx_apply_kpoint(None, 1, None, None, 1, None, None, 0, 1, None, None, None) == 1
+    assert L.kx_energy_kpoints(None, 1, None, None, 1, None, None, None, None) == 1

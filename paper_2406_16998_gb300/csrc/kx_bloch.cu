@@ -772,8 +772,9 @@ __global__ void bloch_to_f32_kernel(const double2 *__restrict__ src, float2 *__r
 
 // out_v[x] -= sum over the chunk items r = v * n_orb + m in [r0, r1) of
 // w_q g_mq psi_m[x] X_{r - r0}[x] (m ascending, one thread per (v, x)).
+// (memory-latency bound: six blocks per SM, 42 registers)
 template <typename T>
-__global__ void bloch_accum_kernel(const typename Cx<T>::t *__restrict__ X, long long r0, long long r1, int n_orb,
+__global__ void __launch_bounds__(256, 6) bloch_accum_kernel(const typename Cx<T>::t *__restrict__ X, long long r0, long long r1, int n_orb,
                                    const typename Cx<T>::t *__restrict__ P, const double *__restrict__ occ_q,
                                    double wq, double2 *__restrict__ out, long long N) {
     using T2 = typename Cx<T>::t;
@@ -1075,7 +1076,7 @@ BlochLayout bloch_layout(const kx_plan *p, int n_orb, int n_vec, int n_kpt, size
 // out_m[x] -= sum over the chunk items r = v * n_orb + m in [r0, r1) of
 // w_k g_vk F_v[x] conj(X_{r - r0}[x]) (v ascending, one thread per (m, x)).
 template <typename T>
-__global__ void bloch_accum_rev_kernel(const typename Cx<T>::t *__restrict__ X, long long r0, long long r1,
+__global__ void __launch_bounds__(256, 6) bloch_accum_rev_kernel(const typename Cx<T>::t *__restrict__ X, long long r0, long long r1,
                                        int n_orb, const typename Cx<T>::t *__restrict__ F,
                                        const double *__restrict__ occ_k, double wk, double2 *__restrict__ out,
                                        long long N) {

@@ -41,3 +41,18 @@ def pair_list(n_orb: int):
 def pair_at(n_orb: int, k: int):
     """(i, j) of entry k of the library's pair enumeration."""
     return pair_list(n_orb)[k]
+
+
+def kpoint_blocks(n_kpt: int):
+    """The k-point pair blocks (k, q), q >= k, in the order kx_vx_kpoints solves
+    them; the block (k, q) serves Vx psi_k and, read conjugated, Vx psi_q."""
+    return [(k, q) for k in range(n_kpt) for q in range(k, n_kpt)]
+
+
+def kpoint_block_range(n_kpt: int, rank: int, world: int):
+    """[begin, end) of kpoint_blocks owned by `rank` of `world` ranks (count-balanced;
+    the partial Vx psi of the ranks add up to the whole)."""
+    if world < 1 or not (0 <= rank < world):
+        raise ValueError("need 0 <= rank < world")
+    B = n_kpt * (n_kpt + 1) // 2
+    return (rank * B) // world, ((rank + 1) * B) // world

@@ -308,6 +308,19 @@ int kx_vx_apply_kpoint(kx_plan *plan, int n_kpt, const double *theta, const doub
 int kx_vx_kpoints(kx_plan *plan, int n_kpt, const double *theta, const double *wk, int n_orb, const double *psi,
                   const double *occ, double *vx, double *ex, kx_stream stream);
 
+/* kx_vx_kpoint_blocks — the part of kx_vx_kpoints that the k-point blocks
+ * [block_begin, block_end) contribute, for a split across GPUs: the blocks are
+ * (k, q), q >= k, numbered k-major (k = 0: q = 0..n_kpt-1, then k = 1: q =
+ * 1..n_kpt-1, ...; n_kpt (n_kpt + 1) / 2 of them); block (k, q) adds q's bands
+ * to Vx psi_k and, for q > k, k's bands to Vx psi_q.  vx (layout of psi) is
+ * overwritten with the partial sums of every k-point and ex[0] (if not NULL)
+ * with the matching partial E_x, so that the partials of disjoint ranges
+ * covering all blocks add up to kx_vx_kpoints.  Other arguments as
+ * kx_vx_kpoints; KX_ERR_ARG for a range outside [0, n_kpt (n_kpt + 1) / 2]. */
+int kx_vx_kpoint_blocks(kx_plan *plan, int n_kpt, const double *theta, const double *wk, int n_orb,
+                        const double *psi, const double *occ, long long block_begin, long long block_end, double *vx,
+                        double *ex, kx_stream stream);
+
 /* kx_energy_kpoints — E_x alone (Eq. 8) into ex[0] (device float64, required)
  * through Parseval: -1/2 dV sum w_k w_q g_nk g_mq sum f(Lambda) |V^H rho|^2,
  * rho = conj(psi_mq) psi_nk; only the forward transforms of the blocks

@@ -50,6 +50,7 @@ SIGNATURES = {
     "kx_vx_apply_kpoint": (_c_int, [_vp, _c_int, _vp, _vp, _c_int, _vp, _vp, _c_int, _c_int, _vp, _vp, _vp]),
     "kx_vx_kpoints": (_c_int, [_vp, _c_int, _vp, _vp, _c_int, _vp, _vp, _vp, _vp, _vp]),
     "kx_energy_kpoints": (_c_int, [_vp, _c_int, _vp, _vp, _c_int, _vp, _vp, _vp, _vp]),
+    "kx_vx_kpoint_blocks": (_c_int, [_vp, _c_int, _vp, _vp, _c_int, _vp, _vp, _ll, _ll, _vp, _vp, _vp]),
     "kx_energy_gradient": (_c_int, [_vp, _c_int, _vp, _vp, _vp, _vp, _vp]),
     "kx_batch_create": (_c_int, [_c_int, _vp, _vp, ctypes.POINTER(_vp)]),
     "kx_batch_run": (_c_int, [_vp, _vp, _vp, _vp, _vp]),
@@ -376,6 +377,26 @@ def kx_vx_kpoints(plan: Plan, theta, wk, psi, occ=None, out=None, e_x=None, stre
                                _dptr(psi, "psi", torch.complex128, (n_kpt, n_orb, plan.N)), occ_p,
                                _dptr(out, "vx", torch.complex128, (n_kpt, n_orb, plan.N)),
                                _dptr(e_x, "e_x", torch.float64, (1,)), _stream(stream)))
+    return out, e_x
+
+
+def kx_vx_kpoint_blocks(plan: Plan, theta, wk, psi, block_begin: int, block_end: int, occ=None, out=None, e_x=None,
+                        stream=None):
+    """Partial (Vx psi at every k-point, E_x) from the k-point blocks
+    [block_begin, block_end) (see kx_vx_kpoint_blocks and shard.kpoint_blocks)."""
+    torch = _torch()
+    n_kpt, ta, wa = _kpoint_host(theta, wk)
+    n_orb = psi.shape[1]
+    if out is None:
+        out = torch.empty_like(psi)
+    if e_x is None:
+        e_x = torch.empty(1, dtype=torch.float64, device=psi.device)
+    occ_p = None if occ is None else _dptr(occ, "occ", torch.float64, (n_kpt, n_orb))
+    _check(lib().kx_vx_kpoint_blocks(plan.handle, n_kpt, ctypes.cast(ta, _vp), ctypes.cast(wa, _vp), n_orb,
+                                     _dptr(psi, "psi", torch.complex128, (n_kpt, n_orb, plan.N)), occ_p,
+                                     int(block_begin), int(block_end),
+                                     _dptr(out, "vx", torch.complex128, (n_kpt, n_orb, plan.N)),
+                                     _dptr(e_x, "e_x", torch.float64, (1,)), _stream(stream)))
     return out, e_x
 
 

@@ -1118,7 +1118,7 @@ __global__ void __launch_bounds__(256, 6) bloch_accum_rev_kernel(const typename 
 // n_kpt x n_orb (nullable).  Outputs are accumulated into.
 template <typename T>
 int bloch_sweep(kx_plan *p, int n_kpt, const double *theta, const double *wk, int n_orb, const double *psi,
-                const double *occ, int k, int q_begin, int n_vec, const double *phi, double *out_k,
+                const double *occ, int k, int q_begin, int q_end, int n_vec, const double *phi, double *out_k,
                 double *out_all, cudaStream_t s) {
     using T2 = typename Cx<T>::t;
     const long long N = (long long)p->N;
@@ -1160,7 +1160,7 @@ int bloch_sweep(kx_plan *p, int n_kpt, const double *theta, const double *wk, in
     ax.order = p->fd_order;
     const long long pairs = (long long)n_orb * n_vec;
     const double *occ_k = occ ? occ + (size_t)k * n_orb : nullptr;
-    for (int q = q_begin; q < n_kpt; ++q) {
+    for (int q = q_begin; q < q_end; ++q) {
         for (int a = 0; a < 3; ++a) ax.theta[a] = theta[3 * k + a] - theta[3 * q + a];
         if (int rc = prof_begin(p, PK_BLOCH_OTHER, s)) return rc;
         bloch_basis_kernel<T><<<dim3(3, 16), 256, 0, s>>>(ax, Mf[0], Mf[1], Mf[2], Mi[0], Mi[1], Mi[2], lam[0], lam[1],
@@ -1248,20 +1248,30 @@ template <typename T>
 int bloch_run(kx_plan *p, int n_kpt, const double *theta, const double *wk, int n_orb, const double *psi,
               const double *occ, int k, int n_vec, const double *phi, double *out, cudaStream_t s) {
     KX_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(double2) * p->N * (size_t)n_vec, s));
-    return bloch_sweep<T>(p, n_kpt, theta, wk, n_orb, psi, occ, k, 0, n_vec, phi, out, nullptr, s);
+    return bloch_sweep<T>(p, n_kpt, theta, wk, n_orb, psi, occ, k, 0, n_kpt, n_vec, phi, out, nullptr, s);
 }
 
 // Vx psi at every k-point: the pair blocks (k, q) with q >= k are solved once
 // and serve both Vx psi_k and, read conjugated, Vx psi_q.
 template <typename T>
 int bloch_all(kx_plan *p, int n_kpt, const double *theta, const double *wk, int n_orb, const double *psi,
-              const double *occ, double *vx, double *ex, cudaStream_t s) {
+              const double *occ, long long b_begin, long long b_end, double *vx, double *ex, cudaStream_t s) {
     const size_t N = p->N;
     KX_CUDA_TRY(cudaMemsetAsync(vx, 0, sizeof(double2) * N * (size_t)n_orb * n_kpt, s));
+    // blocks (k, q), q >= k, numbered k-major: the blocks of row k are
+    // [row_start(k), row_start(k) + n_kpt - k)
+    long long row_start = 0;
     for (int k = 0; k < n_kpt; ++k) {
-        const size_t off = (size_t)k * n_orb * N * 2;
-        if (int rc = bloch_sweep<T>(p, n_kpt, theta, wk, n_orb, psi, occ, k, k, n_orb, psi + off, vx + off, vx, s))
-            return rc;
+        const long long row_end = row_start + (n_kpt - k);
+        const long long lo = std::max(b_begin, row_start), hi = std::min(b_end, row_end);
+        if (lo < hi) {
+            const size_t off = (size_t)k * n_orb * N * 2;
+            const int q0 = k + (int)(lo - row_start), q1 = k + (int)(hi - row_start);
+            if (int rc = bloch_sweep<T>(p, n_kpt, theta, wk, n_orb, psi, occ, k, q0, q1, n_orb, psi + off, vx + off,
+                                        vx, s))
+                return rc;
+        }
+        row_start = row_end;
     }
     if (!ex) return KX_OK;
     BlochLayout L = bloch_layout<T>(p, n_orb, n_orb, n_kpt);
@@ -1411,9 +1421,10 @@ int bloch_vx_apply(kx_plan *p, int n_kpt, const double *theta, const double *wk,
 }
 
 int bloch_vx_all(kx_plan *p, int n_kpt, const double *theta, const double *wk, int n_orb, const double *psi,
-                 const double *occ, double *vx, double *ex, cudaStream_t s) {
-    return p->precision == KX_FP64 ? bloch_all<double>(p, n_kpt, theta, wk, n_orb, psi, occ, vx, ex, s)
-                                   : bloch_all<float>(p, n_kpt, theta, wk, n_orb, psi, occ, vx, ex, s);
+                 const double *occ, long long b_begin, long long b_end, double *vx, double *ex, cudaStream_t s) {
+    return p->precision == KX_FP64
+               ? bloch_all<double>(p, n_kpt, theta, wk, n_orb, psi, occ, b_begin, b_end, vx, ex, s)
+               : bloch_all<float>(p, n_kpt, theta, wk, n_orb, psi, occ, b_begin, b_end, vx, ex, s);
 }
 
 int bloch_energy(kx_plan *p, int n_kpt, const double *theta, const double *wk, int n_orb, const double *psi,

@@ -538,7 +538,25 @@ int kx_vx_kpoints(kx_plan *plan, int n_kpt, const double *theta, const double *w
         return set_error(KX_ERR_ARG, "kx_vx_kpoints: complex buffers must be 16-byte aligned");
     const size_t c = 2 * plan->N * (size_t)n_orb * n_kpt;
     if (vx < psi + c && psi < vx + c) return set_error(KX_ERR_ARG, "kx_vx_kpoints: vx must not overlap psi");
-    return bloch_vx_all(plan, n_kpt, theta, wk, n_orb, psi, occ, vx, ex, reinterpret_cast<cudaStream_t>(stream));
+    return bloch_vx_all(plan, n_kpt, theta, wk, n_orb, psi, occ, 0, (long long)n_kpt * (n_kpt + 1) / 2, vx, ex,
+                        reinterpret_cast<cudaStream_t>(stream));
+}
+
+int kx_vx_kpoint_blocks(kx_plan *plan, int n_kpt, const double *theta, const double *wk, int n_orb,
+                        const double *psi, const double *occ, long long block_begin, long long block_end, double *vx,
+                        double *ex, kx_stream stream) {
+    if (int rc = check_plan(plan)) return rc;
+    if (int rc = check_kpoints(plan, "kx_vx_kpoint_blocks", n_kpt, theta, wk, n_orb, psi)) return rc;
+    const long long B = (long long)n_kpt * (n_kpt + 1) / 2;
+    if (block_begin < 0 || block_end > B || block_begin > block_end)
+        return set_error(KX_ERR_ARG, "kx_vx_kpoint_blocks: need 0 <= block_begin <= block_end <= n_kpt (n_kpt + 1) / 2");
+    if (!vx) return set_error(KX_ERR_ARG, "kx_vx_kpoint_blocks: NULL buffer");
+    if (misaligned16(psi) || misaligned16(vx))
+        return set_error(KX_ERR_ARG, "kx_vx_kpoint_blocks: complex buffers must be 16-byte aligned");
+    const size_t c = 2 * plan->N * (size_t)n_orb * n_kpt;
+    if (vx < psi + c && psi < vx + c) return set_error(KX_ERR_ARG, "kx_vx_kpoint_blocks: vx must not overlap psi");
+    return bloch_vx_all(plan, n_kpt, theta, wk, n_orb, psi, occ, block_begin, block_end, vx, ex,
+                        reinterpret_cast<cudaStream_t>(stream));
 }
 
 int kx_energy_kpoints(kx_plan *plan, int n_kpt, const double *theta, const double *wk, int n_orb,

@@ -197,9 +197,11 @@ int fft_passes(kx_plan *p, long R, const int2 *pairs, const float *src32, int rh
 // theta (n_kpt x 3) and wk (n_kpt) host arrays.
 int bloch_vx_apply(kx_plan *p, int n_kpt, const double *theta, const double *wk, int n_orb, const double *psi,
                    const double *occ, int k, int n_vec, const double *phi, double *out, cudaStream_t s);
-// Vx psi_nk for every k-point (vx like psi) and, if ex, E_x into ex[0].
+// Vx psi_nk for every k-point (vx like psi) and, if ex, E_x into ex[0], from the
+// k-point blocks [b_begin, b_end) of the (k, q >= k) enumeration (all of them:
+// [0, n_kpt (n_kpt + 1) / 2)).
 int bloch_vx_all(kx_plan *p, int n_kpt, const double *theta, const double *wk, int n_orb, const double *psi,
-                 const double *occ, double *vx, double *ex, cudaStream_t s);
+                 const double *occ, long long b_begin, long long b_end, double *vx, double *ex, cudaStream_t s);
 // E_x alone into ex[0] (forward transforms and Parseval).
 int bloch_energy(kx_plan *p, int n_kpt, const double *theta, const double *wk, int n_orb, const double *psi,
                  const double *occ, double *ex, cudaStream_t s);

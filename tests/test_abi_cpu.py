@@ -27,7 +27,7 @@ def kx():
 def test_header_declares_the_boundary():
     names = header_functions()
     for required in ["kx_plan_create", "kx_plan_destroy", "kx_vx_apply", "kx_energy", "kx_apply_fL", "kx_ace",
-                     "kx_ace_apply", "kx_vx_apply_kpoint", "kx_vx_kpoints", "kx_energy_kpoints", "kx_batch_create",
+                     "kx_ace_apply", "kx_vx_apply_kpoint", "kx_vx_kpoints", "kx_vx_kpoint_blocks", "kx_energy_kpoints", "kx_batch_create",
                      "kx_batch_run", "kx_autotune", "kx_last_error_detail", "kx_strerror"]:
         assert required in names
 

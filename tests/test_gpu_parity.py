@@ -1057,3 +1057,30 @@ def test_kpoint_gauge_invariance(kx, case):
     vx1, ex1 = kx.kx_vx_kpoints(plan, theta, wk, to_dev_orbitals(psi * ph[:, None, None]), dev(occ))
     assert relmax(vx1.cpu().numpy(), vx0 * ph[:, None, None]) < 5 * TOL_K[prec][0]
     assert abs(ex1.item() - ex0.item()) < 5 * TOL_K[prec][1] * abs(ex0.item())
+
+
+@pytest.mark.parametrize("case", [0, 1])
+def test_kpoint_block_ranges_sum_to_full(kx, case):
+    """kx_vx_kpoint_blocks over the ranges a multi-GPU split would give each rank
+    (shard.kpoint_block_range) adds up to kx_vx_kpoints; an empty range gives
+    zeros; a range past the last block is rejected."""
+    from paper_2406_16998_gb300 import shard
+    sysd, theta, wk, psi, occ, prec = kpoint_inputs(case, 450 + case)
+    plan = kx.Plan(sysd.n, sysd.h, sysd.bc, sysd.kernel, precision=prec)
+    psi_d, occ_d = to_dev_orbitals(psi), dev(occ)
+    full, ef = kx.kx_vx_kpoints(plan, theta, wk, psi_d, occ_d)
+    full = full.cpu().numpy()
+    acc, e = np.zeros_like(full), 0.0
+    for rank in range(3):
+        a, b = shard.kpoint_block_range(len(wk), rank, 3)
+        part, ep = kx.kx_vx_kpoint_blocks(plan, theta, wk, psi_d, a, b, occ_d)
+        acc += part.cpu().numpy()
+        e += ep.item()
+    assert relmax(acc, full) < 1e-12
+    assert abs(e - ef.item()) < 1e-12 * abs(ef.item())
+    zero, ez = kx.kx_vx_kpoint_blocks(plan, theta, wk, psi_d, 2, 2, occ_d)
+    assert zero.abs().max().item() == 0.0 and ez.item() == 0.0
+    B = len(wk) * (len(wk) + 1) // 2
+    with pytest.raises(kx.KxError) as ei:
+        kx.kx_vx_kpoint_blocks(plan, theta, wk, psi_d, 0, B + 1, occ_d)
+    assert ei.value.code == kx.KX_ERR_ARG

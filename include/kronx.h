@@ -75,7 +75,7 @@ typedef struct CUstream_st *kx_stream;
 #define KX_ERR_NOMEM       3 /* a device or host allocation failed                    */
 #define KX_ERR_CUDA        4 /* a CUDA runtime call or kernel launch failed            */
 #define KX_ERR_TIMEOUT     5 /* a bounded wait inside a kernel ran out                 */
-#define KX_ERR_UNSUPPORTED 6 /* valid request outside what this build implements      */
+#define KX_ERR_UNSUPPORTED 6 /* valid request outside what the library implements     */
 
 /* Grid and finite-difference operator (Sec. 3, Eqs. 11-12).
  *   n[a]      points per axis, 2 <= n[a] <= 128; for KX_F16X3, n[a] % 8 == 0.
@@ -345,7 +345,7 @@ int kx_batch_run(kx_batch *batch, const double *const *psi, double *const *vx_ps
 /* kx_batch_destroy — frees the batch (not its plans).  NULL is accepted. */
 int kx_batch_destroy(kx_batch *batch);
 
-/* kx_autotune — times the launch shapes this build offers for `plan` at n_orb
+/* kx_autotune — times the launch shapes the library offers for `plan` at n_orb
  * orbitals (for up to budget_ms milliseconds, on an internal stream, with
  * synthetic orbitals) and keeps the fastest in the plan.  Synchronous. */
 int kx_autotune(kx_plan *plan, int n_orb, int budget_ms);

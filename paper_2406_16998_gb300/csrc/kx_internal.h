@@ -28,7 +28,7 @@ int cuda_error(cudaError_t e, const char *what);
         if (_e != cudaSuccess) return ::kx::cuda_error(_e, what); \
     } while (0)
 
-constexpr int kMaxN = 128;       // per-axis limit of this build
+constexpr int kMaxN = 128;       // per-axis limit of the library
 constexpr int kOrbBlock = 4;     // orbitals per block of the pair enumeration
 constexpr int kGroupSlots = 2 * kOrbBlock;
 

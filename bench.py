@@ -561,6 +561,124 @@ def multipole_legs(kx, torch, stream, plan, psi, ms_zero, bf16, steps=3):
     return res
 
 
+def matmul_peaks(torch, reps=5):
+    """Dense matmul peaks of this GPU that the float64 and float32 legs are
+    measured against: torch.matmul (cuBLAS) in float64 (4096^3) and in float32
+    with TF32 allowed (8192^3), best of `reps` under CUDA events after a
+    warm-up.  A benchmark of the library GEMMs, not a GPU setting."""
+    res = {}
+    for name, dtype, n, tf32 in (("fp64", torch.float64, 4096, False), ("tf32", torch.float32, 8192, True)):
+        prev = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        try:
+            a = torch.randn(n, n, dtype=dtype, device="cuda")
+            b = torch.randn(n, n, dtype=dtype, device="cuda")
+            c = torch.matmul(a, b)
+            torch.cuda.synchronize()
+            best = 1e30
+            for _ in range(reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b, out=c)
+                e1.record()
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            res[name + "_tflops"] = 2.0 * n ** 3 / (best / 1e3) / 1e12
+            res[name + "_shape"] = f"{n}x{n}x{n}"
+            del a, b, c
+        finally:
+            torch.backends.cuda.matmul.allow_tf32 = prev
+    res["how"] = "torch.matmul best of %d (CUDA events); fp64 plain, fp32 with allow_tf32" % reps
+    return res
+
+
+def c1_leg(kx, torch, stream, fp64_peak, reps=5):
+    """Config 1 in full on the float64 plan: 32^3 isolated box, h = 0.5, 4
+    orbitals.  The configuration counts the 16 ordered pairs; the library
+    solves the 10 unordered ones (the ordered and symmetric sums agree).  Time
+    per apply (best and median of `reps`), its float64 roofline fraction, and
+    the error against the oracle over all 16 ordered pairs."""
+    import oracle
+    sysd = workloads.C1
+    psi_h = workloads.make_orbitals(sysd)
+    psi = torch.from_numpy(np.ascontiguousarray(psi_h.T)).cuda()
+    plan = kx.Plan.for_system(sysd, precision=kx.KX_FP64)
+    vx = torch.empty_like(psi)
+    ex = torch.empty(1, dtype=torch.float64, device="cuda")
+    kx.kx_vx_apply(plan, psi, out=vx, e_x=ex, stream=stream)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        kx.kx_vx_apply(plan, psi, out=vx, e_x=ex, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    op = oracle.Plan(sysd.n, sysd.h, sysd.bc, sysd.kernel, sysd.omega)
+    t0 = time.perf_counter()
+    vx_ref, ex_ref = oracle.vx_apply(op, psi_h, ordered=True)
+    dt_o = time.perf_counter() - t0
+    P_sym = sysd.n_orb * (sysd.n_orb + 1) // 2
+    useful = workloads.useful_flops_per_pair(sysd.n) * P_sym
+    best = min(times)
+    ach = useful / (best / 1e3) / 1e12
+    return {"ms_per_apply_best": best, "ms_per_apply_median": statistics.median(times), "repeats": reps,
+            "ordered_pairs": sysd.n_orb ** 2, "solves": P_sym,
+            "vx_psi_maxrel_vs_oracle": float(np.max(np.abs(vx.cpu().numpy().T - vx_ref)) / np.max(np.abs(vx_ref))),
+            "e_x_rel_vs_oracle": abs(ex.item() - ex_ref) / abs(ex_ref), "e_x": ex.item(),
+            "oracle_s": dt_o, "status": plan.status(),
+            "roofline": {"bound": "fp64", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                         "frac": ach / fp64_peak,
+                         "note": "launch-bound at this size (2.0e8 flops); peak = measured torch.matmul float64"}}
+
+
+def c5_leg(kx, torch, stream):
+    """Config 5: E_x of the 80^3 periodic screened 256-orbital system through
+    the autograd function (forward kx_energy: forward products and the
+    Parseval sum; backward kx_energy_gradient: pair products recomputed, Vx psi,
+    2 dV g Vx psi), split-precision forward, float64 energy sums.  Forward and
+    backward times (CUDA events), and the gradient and energy against the
+    float64 plan's kx_energy_gradient on the same orbitals."""
+    sysd = workloads.C5
+    psi = torch.from_numpy(np.ascontiguousarray(workloads.make_orbitals(sysd).T)).cuda()
+    plan = kx.Plan.for_system(sysd, precision=kx.KX_F16X3)
+    P = sysd.n_orb * (sysd.n_orb + 1) // 2
+    x = psi.clone().requires_grad_(True)
+    kx.exchange_energy(x, plan).backward()  # warm-up (sizes the workspaces)
+    torch.cuda.synchronize()
+    fw, bw = [], []
+    for _ in range(3):
+        x.grad = None
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        E = kx.exchange_energy(x, plan)
+        e1.record(stream)
+        E.backward()
+        e2.record(stream)
+        torch.cuda.synchronize()
+        fw.append(e0.elapsed_time(e1))
+        bw.append(e1.elapsed_time(e2))
+    g = x.grad.detach()
+    e_split = E.item()
+    del x
+    plan64 = kx.Plan.for_system(sysd, precision=kx.KX_FP64)
+    t0 = time.perf_counter()
+    g64, e64 = kx.kx_energy_gradient(plan64, psi)
+    torch.cuda.synchronize()
+    dt64 = time.perf_counter() - t0
+    res = {"forward_ms": min(fw), "backward_ms": min(bw), "repeats": 3, "pairs": P,
+           "forward_pair_solves_per_s": P / (min(fw) / 1e3), "backward_pair_solves_per_s": P / (min(bw) / 1e3),
+           "grad_maxrel_vs_fp64_plan": float((g - g64).abs().max() / g64.abs().max()),
+           "e_x_rel_vs_fp64_plan": abs(e_split - e64.item()) / abs(e64.item()), "e_x": e_split,
+           "fp64_gradient_s": dt64, "status": plan.status(),
+           "targets": {"grad": 1e-5, "e_x": 1e-6}}
+    del g, g64, psi, plan, plan64
+    return res
+
+
 def issued_tensor_flops_per_pair(n, fused=True):
     """Tensor-core flops the split path issues per pair: three fp16 products per
     mode product, M padded to 128-row tiles, K and N padded to multiples of 16."""
@@ -687,17 +805,27 @@ def main():
         ex64 = torch.empty(1, dtype=torch.float64, device="cuda")
         kx.kx_vx_apply(plan64, psi, out=vx64, e_x=ex64)
         torch.cuda.synchronize()
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        kx.kx_vx_apply(plan64, psi, out=vx64, e_x=ex64)
-        f1.record(stream)
-        torch.cuda.synchronize()
-        ms64 = f0.elapsed_time(f1)
+        t64 = []
+        for _ in range(3):
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            kx.kx_vx_apply(plan64, psi, out=vx64, e_x=ex64)
+            f1.record(stream)
+            torch.cuda.synchronize()
+            t64.append(f0.elapsed_time(f1))
+        ms64 = statistics.median(t64)
         err_vx = float((vx_split - vx64).abs().max() / vx64.abs().max())
         err_ex = abs(ex_split - ex64.item()) / abs(ex64.item())
-        out["fp64_gpu"] = {"ms_per_step": ms64, "pair_solves_per_s": P / (ms64 / 1e3),
-                           "speedup_split_vs_fp64": ms64 / ms_step}
+        mm = matmul_peaks(torch)
+        out["measured_matmul_peaks"] = mm
+        ach64 = P * useful / (ms64 / 1e3) / 1e12
+        out["fp64_gpu"] = {"ms_per_step": ms64, "ms_per_step_all": t64, "pair_solves_per_s": P / (ms64 / 1e3),
+                           "speedup_split_vs_fp64": ms64 / ms_step,
+                           "roofline": {"bound": "fp64", "achieved": ach64, "peak": mm["fp64_tflops"],
+                                        "unit": "TFLOP/s", "frac": ach64 / mm["fp64_tflops"],
+                                        "peak_source": "measured torch.matmul float64 4096^3 (cuBLAS DGEMM)"}}
+        out["c1_fp64_32cube_4orb"] = c1_leg(kx, torch, stream, mm["fp64_tflops"])
         out["error"] = {"vx_psi_maxrel_vs_fp64_gpu": err_vx, "e_x_rel_vs_fp64_gpu": err_ex,
                         "targets": {"vx_psi": 1e-5, "e_x": 1e-6}, "e_x": ex_split}
         del plan64, vx64
@@ -716,6 +844,7 @@ def main():
         out["multipole"] = multipole_legs(kx, torch, stream, plan, psi, ms_step, bf16)
         out["multipole"]["e_x_zero_boundary"] = ex_split
         out["other_workloads"] = other_workloads(kx, torch, stream, hbm)
+        out["c5_autograd_80cube_256orb"] = c5_leg(kx, torch, stream)
         line, done, vx_ref, ex_ref = cpu_baseline(psi_h)
         out["cpu_baseline"] = line
         # the split path over the same first pairs of the list, against the oracle

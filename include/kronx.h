@@ -62,7 +62,14 @@ typedef struct CUstream_st *kx_stream;
 #define KX_FP64  0 /* plain float64 on the CUDA cores (the baseline path)            */
 #define KX_F16X3 1 /* tensor cores: fp16 hi/lo split of both operands, three products
                       (hi*hi + hi*lo + lo*hi) accumulated in fp32, per-pair power-of-two
-                      scaling; energy and outputs accumulated in fp32/fp64            */
+                      scaling; energy and outputs accumulated in fp32/fp64.
+                      BF16X3, BF16X6 and TF32X3 splits were considered and dropped on
+                      purpose: an fp16 hi + lo pair carries 22 significand bits at the
+                      bf16 rate with three products, where bf16 x3 carries 16 bits
+                      (short of the 1e-5 / 1e-6 targets), bf16 x6 needs twice the
+                      products and tf32 runs at half the fp16 rate with twice the
+                      operand bytes; fp16's narrow exponent range is handled by
+                      the power-of-two scales                                        */
 #define KX_FFT32 2 /* fully periodic grids only: f(L) through the DFT (the eigenvectors of
                       a periodic axis are Fourier modes), float32 complex Stockham FFTs
                       of radix 2, 3, 4, 5; every n[a] a product of 2, 3 and 5; the
@@ -176,9 +183,11 @@ int kx_apply_fL(kx_plan *plan, int n_rhs, const double *b, double *x, kx_stream 
  * precision) and the caller's b and x are the only other memory it touches.
  *   Limit: n_rhs * N <= 2,621,440 grid values per call; larger requests return
  *   KX_ERR_ARG with the numbers (split them into several calls).
- *   First call on a device: looks up the array's device address once
- *   (cudaGetSymbolAddress) with the plan's device current; make that first call
- *   before any stream capture.
+ *   Every call looks up the array's device address (cudaGetSymbolAddress, which
+ *   allocates nothing) with the plan's device current, so no address is kept
+ *   across a cudaDeviceReset.  The first call on a device may load the
+ *   library's tensor-core device code and the array with it, as any first
+ *   launch does; make that first call before any stream capture.
  *   All calls share the array and it keeps the previous call's contents (the
  *   entry point clears what must start at zero); calls whose GPU work overlaps
  *   (different streams or host threads on one device) race on it.

@@ -1274,7 +1274,11 @@ int bloch_all(kx_plan *p, int n_kpt, const double *theta, const double *wk, int 
         row_start = row_end;
     }
     if (!ex) return KX_OK;
+    // the energy partials live in the plan workspace; an empty block range ran
+    // no sweep, so the workspace may still be unsized (or sized for a smaller
+    // call): size it here before any kernel writes into it
     BlochLayout L = bloch_layout<T>(p, n_orb, n_orb, n_kpt);
+    if (int rc = ensure_workspace(p, L.total)) return rc;
     double *partial = reinterpret_cast<double *>(static_cast<char *>(p->ws.ptr) + L.partial);
     const int nb = 2 * p->num_sms;
     if (int rc = prof_begin(p, PK_BLOCH_OTHER, s)) return rc;

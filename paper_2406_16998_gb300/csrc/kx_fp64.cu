@@ -18,7 +18,10 @@ constexpr int kModeThreads = 256;
 
 // out[o][c][i] = sum_k M[k][c] in[o][k][i]   with M = V (forward) or V^T (inverse),
 // viewing each of the R grid vectors as [outer][n][inner] along `axis`.
-// Pencils ("columns") are q = o*inner + i.
+// Pencils ("columns") are q = o*inner + i, kTQ of them per CTA.  Index work is
+// kept off the per-element path: each thread finds the (o, i) of its one
+// pencil with a single 32-bit division, then walks k with a fixed stride;
+// the V copy and the contiguous (inner == 1) tiles use 2D loops.
 __global__ void __launch_bounds__(kModeThreads) mode_f64_kernel(const double *__restrict__ in,
                                                                double *__restrict__ out, long long n_cols,
                                                                int n, long long inner,
@@ -26,28 +29,30 @@ __global__ void __launch_bounds__(kModeThreads) mode_f64_kernel(const double *__
     extern __shared__ double sm[];
     double *Ms = sm;                 // n*n: Ms[k*n + c]
     double *Ts = sm + n * n;         // n*(kTQ+1): Ts[k*(kTQ+1) + q]
-    const int tid = threadIdx.x;
-    for (int e = tid; e < n * n; e += blockDim.x) {
-        int k = e / n, c = e % n;
-        Ms[e] = inverse ? V[c * n + k] : V[k * n + c];
-    }
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    constexpr int kWarps = kModeThreads / 32;
+    for (int k = warp; k < n; k += kWarps)
+        for (int c = lane; c < n; c += 32) Ms[k * n + c] = inverse ? V[c * n + k] : V[k * n + c];
     const int ld = kTQ + 1;
     const long long q0 = (long long)blockIdx.x * kTQ;
     const int nq = (int)min((long long)kTQ, n_cols - q0);
-    // load the tile (element (q, k) at o*n*inner + k*inner + i)
+    const int ql = tid % kTQ, cg = tid / kTQ;  // this thread's pencil and column group (4 groups)
+    // element (q, k) sits at o*n*inner + k*inner + i
+    long long base = 0;
     if (inner == 1) {
+        // pencils are contiguous rows of n values: warps take rows, lanes take k
         const double *src = in + q0 * n;
-        for (int e = tid; e < nq * n; e += blockDim.x) Ts[(e % n) * ld + e / n] = src[e];
+        for (int r = warp; r < nq; r += kWarps)
+            for (int k = lane; k < n; k += 32) Ts[k * ld + r] = src[(long long)r * n + k];
     } else {
-        for (int e = tid; e < nq * n; e += blockDim.x) {
-            int k = e / nq, ql = e % nq;
-            long long q = q0 + ql;
-            long long o = q / inner, i = q % inner;
-            Ts[k * ld + ql] = in[(o * n + k) * inner + i];
+        if (ql < nq) {
+            const unsigned q = (unsigned)(q0 + ql), in32 = (unsigned)inner;  // n_cols < 2^31
+            const unsigned o = q / in32, i = q - o * in32;
+            base = (long long)o * n * inner + i;
+            for (int k = cg; k < n; k += kModeThreads / kTQ) Ts[k * ld + ql] = in[base + (long long)k * inner];
         }
     }
     __syncthreads();
-    const int ql = tid % kTQ, cg = tid / kTQ;  // 4 column groups
     double acc[kMaxN / 4];
 #pragma unroll
     for (int u = 0; u < kMaxN / 4; ++u) acc[u] = 0.0;
@@ -72,14 +77,10 @@ __global__ void __launch_bounds__(kModeThreads) mode_f64_kernel(const double *__
     __syncthreads();
     if (inner == 1) {
         double *dst = out + q0 * n;
-        for (int e = tid; e < nq * n; e += blockDim.x) dst[e] = Ts[(e % n) * ld + e / n];
-    } else {
-        for (int e = tid; e < nq * n; e += blockDim.x) {
-            int c = e / nq, qq = e % nq;
-            long long q = q0 + qq;
-            long long o = q / inner, i = q % inner;
-            out[(o * n + c) * inner + i] = Ts[c * ld + qq];
-        }
+        for (int r = warp; r < nq; r += kWarps)
+            for (int c = lane; c < n; c += 32) dst[(long long)r * n + c] = Ts[c * ld + r];
+    } else if (ql < nq) {
+        for (int c = cg; c < n; c += kModeThreads / kTQ) out[base + (long long)c * inner] = Ts[c * ld + ql];
     }
 }
 

@@ -1800,21 +1800,17 @@ constexpr size_t kNoAllocBytes = 3 * kNoAllocMaxElems * sizeof(float) + 5 * kNoA
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-constexpr int kNoAllocMaxDevices = 64;
-void *g_noalloc_ptr[kNoAllocMaxDevices] = {};  // device address of the array, per device
-
-// Set-up, once per device with that device current: the host-side name of the
-// array is only a stand-in, so the kernels get the address the runtime reports.
-int noalloc_scratch(int dev, void **out) {
-    if (dev < 0 || dev >= kNoAllocMaxDevices)
-        return set_error(KX_ERR_UNSUPPORTED, "kx_apply_fL_noalloc: device index beyond 63");
-    if (g_noalloc_ptr[dev] == nullptr) {
-        void *ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess) return cuda_error(e, "kx_apply_fL_noalloc: cudaGetSymbolAddress of the static scratch");
-        g_noalloc_ptr[dev] = ptr;
-    }
-    *out = g_noalloc_ptr[dev];
+// The host-side name of the array is only a stand-in, so the kernels get the
+// address the runtime reports for the current device.  It is looked up on
+// every call (the lookup allocates nothing): a cached address would outlive a
+// cudaDeviceReset, after which the module and its array are loaded anew.  On
+// the first call on a device the lookup may load this module's device code,
+// and the array with it, like any first launch from the module.
+int noalloc_scratch(void **out) {
+    void *ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_error(e, "kx_apply_fL_noalloc: cudaGetSymbolAddress of the static scratch");
+    *out = ptr;
     return KX_OK;
 }
 
@@ -1841,7 +1837,7 @@ int tc_apply_fL_noalloc(kx_plan *p, int n_rhs, const double *b, double *x, cudaS
     KX_CUDA_TRY(cudaGetDevice(&dev));
     if (dev != p->device) return set_error(KX_ERR_ARG, "kx_apply_fL_noalloc: call on the plan's device");
     void *base = nullptr;
-    if (int rc = noalloc_scratch(dev, &base)) return rc;
+    if (int rc = noalloc_scratch(&base)) return rc;
     const size_t elems = (size_t)n_rhs * (size_t)N;
     float *b32 = reinterpret_cast<float *>(base);
     float *T0 = b32 + elems;

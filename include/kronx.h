@@ -222,6 +222,23 @@ int kx_vx_apply_pairs(kx_plan *plan, int n_orb, const double *psi, const double 
                       long long pair_begin, long long pair_end, double *vx_psi, double *e_x,
                       kx_stream stream);
 
+/* kx_vx_apply_block_pairs — the part of kx_vx_apply contributed by an explicit
+ * set of orbital block pairs: the unit of a two-dimensional block-cyclic split
+ * of the pair solves across GPUs (Sec. 3: the pair systems are independent;
+ * the paper's own split is by bands and domains, Sec. 4).  Orbitals are
+ * grouped in blocks of four as in kx_vx_apply_pairs; block pair (I, J), I <= J,
+ * holds the pairs (i, j) with i in block I and j in block J (i <= j when I = J).
+ *   blocks    HOST array of 2 * n_blocks ints, (I, J) per block pair, 0 <= I
+ *             <= J < ceil(n_orb / 4), each block pair at most once, any order;
+ *             read during the call only.
+ *   n_blocks  0 .. nb (nb + 1) / 2 (0 gives zeros).
+ *   vx_psi, e_x receive the partial sums of Eqs. 3-5 over those pairs
+ *   (overwritten): block-pair sets that partition the list sum to kx_vx_apply.
+ * Other arguments as in kx_vx_apply. */
+int kx_vx_apply_block_pairs(kx_plan *plan, int n_orb, const double *psi, const double *occ,
+                            const int *blocks, int n_blocks, double *vx_psi, double *e_x,
+                            kx_stream stream);
+
 /* kx_vx_apply_host — kx_vx_apply on HOST buffers (pinned memory recommended):
  * copies psi (and occ) to library-owned device buffers, runs the apply and
  * copies vx_psi and e_x back; returns after all of it has finished.  With

@@ -43,6 +43,7 @@ SIGNATURES = {
     "kx_vx_apply": (_c_int, [_vp, _c_int, _vp, _vp, _vp, _vp, _vp]),
     "kx_vx_apply_host": (_c_int, [_vp, _c_int, _vp, _vp, _vp, _vp, _vp]),
     "kx_vx_apply_pairs": (_c_int, [_vp, _c_int, _vp, _vp, _ll, _ll, _vp, _vp, _vp]),
+    "kx_vx_apply_block_pairs": (_c_int, [_vp, _c_int, _vp, _vp, _vp, _c_int, _vp, _vp, _vp]),
     "kx_energy": (_c_int, [_vp, _c_int, _vp, _vp, _vp, _vp]),
     "kx_ace": (_c_int, [_vp, _c_int, _vp, _vp, _vp, _vp, _vp]),
     "kx_ace_apply": (_c_int, [_vp, _c_int, _vp, _c_int, _vp, _vp, _vp]),
@@ -264,6 +265,24 @@ def kx_vx_apply_pairs(plan: Plan, psi, pair_begin, pair_end, occ=None, out=None,
                                    _dptr(occ, "occ", torch.float64, (n_orb,)), int(pair_begin), int(pair_end),
                                    _dptr(out, "out", torch.float64, (n_orb, plan.N)),
                                    _dptr(e_x, "e_x", torch.float64, (1,)), _stream(stream)))
+    return out, e_x
+
+
+def kx_vx_apply_block_pairs(plan: Plan, psi, blocks, occ=None, out=None, e_x=None, stream=None):
+    """Partial (Vx psi, E_x) over the orbital block pairs `blocks` (a sequence of
+    (I, J), I <= J, blocks of four orbitals); see kx_vx_apply_block_pairs."""
+    torch = _torch()
+    n_orb = psi.shape[0]
+    flat = [int(x) for bp in blocks for x in bp]
+    arr = (ctypes.c_int * max(1, len(flat)))(*flat)
+    if out is None:
+        out = torch.empty_like(psi)
+    if e_x is None:
+        e_x = torch.empty(1, dtype=torch.float64, device=psi.device)
+    _check(lib().kx_vx_apply_block_pairs(plan.handle, n_orb, _dptr(psi, "psi", torch.float64, (n_orb, plan.N)),
+                                         _dptr(occ, "occ", torch.float64, (n_orb,)), ctypes.cast(arr, _vp),
+                                         len(flat) // 2, _dptr(out, "out", torch.float64, (n_orb, plan.N)),
+                                         _dptr(e_x, "e_x", torch.float64, (1,)), _stream(stream)))
     return out, e_x
 
 

@@ -59,11 +59,19 @@ int ensure_workspace(kx_plan *p, size_t bytes) {
 // inside an off-diagonal block all (i, j) row-major.  Each block pair is one
 // accumulation group.  [begin, end) restricts the list to a sub-range of this
 // enumeration (groups are cut at the range ends).
+// With p->blk_mode set, the block pairs of p->blk_req (I <= J each, in the
+// given order) are enumerated instead, each whole; begin / end are ignored.
 int ensure_pairs(kx_plan *p, int n_orb, cudaStream_t s, long long begin, long long end) {
     (void)s;
     const long long P_all = (long long)n_orb * (n_orb + 1) / 2;
     if (end < 0) end = P_all;
-    if (p->ws_norb == n_orb && p->pr_begin == begin && p->pr_end == end) return KX_OK;
+    if (p->blk_mode) {
+        begin = 0;
+        end = P_all;
+        if (p->ws_norb == n_orb && p->blk_cur == p->blk_req) return KX_OK;
+    } else if (p->ws_norb == n_orb && p->blk_cur.empty() && p->pr_begin == begin && p->pr_end == end) {
+        return KX_OK;
+    }
     ++p->config_version;  // the list is rebuilt in place
     std::vector<int> pairs, slots;
     std::vector<Group> groups;
@@ -72,9 +80,22 @@ int ensure_pairs(kx_plan *p, int n_orb, cudaStream_t s, long long begin, long lo
     pairs.reserve(2 * (size_t)(end - begin));
     slots.reserve(2 * (size_t)(end - begin));
     const int nb = (n_orb + kOrbBlock - 1) / kOrbBlock;
+    // the block pairs to visit: all (I <= J) row-major, or the explicit list
+    std::vector<int> visit;
+    if (p->blk_mode) {
+        visit = p->blk_req;
+    } else {
+        visit.reserve((size_t)nb * (nb + 1));
+        for (int IB = 0; IB < nb; ++IB)
+            for (int JB = IB; JB < nb; ++JB) {
+                visit.push_back(IB);
+                visit.push_back(JB);
+            }
+    }
     long long k = 0;
-    for (int IB = 0; IB < nb; ++IB) {
-        for (int JB = IB; JB < nb; ++JB) {
+    for (size_t v = 0; v + 1 < visit.size(); v += 2) {
+        {
+            const int IB = visit[v], JB = visit[v + 1];
             const int I0 = IB * kOrbBlock, bi = std::min(kOrbBlock, n_orb - I0);
             const int J0 = JB * kOrbBlock, bj = std::min(kOrbBlock, n_orb - J0);
             Group g{};
@@ -144,6 +165,10 @@ int ensure_pairs(kx_plan *p, int n_orb, cudaStream_t s, long long begin, long lo
     p->ws_norb = n_orb;
     p->pr_begin = begin;
     p->pr_end = end;
+    if (p->blk_mode)
+        p->blk_cur = p->blk_req;
+    else
+        p->blk_cur.clear();
     return KX_OK;
 }
 
@@ -381,6 +406,37 @@ int kx_vx_apply_pairs(kx_plan *plan, int n_orb, const double *psi, const double 
         return KX_OK;
     }
     return dispatch_vx(plan, n_orb, psi, occ, vx_psi, e_x, false, s, (long)pair_begin, (long)pair_end);
+}
+
+int kx_vx_apply_block_pairs(kx_plan *plan, int n_orb, const double *psi, const double *occ, const int *blocks,
+                            int n_blocks, double *vx_psi, double *e_x, kx_stream stream) {
+    if (int rc = check_plan(plan)) return rc;
+    if (n_orb < 1 || n_orb > 4096) return set_error(KX_ERR_ARG, "kx_vx_apply_block_pairs: n_orb must be in 1..4096");
+    if (!psi || !vx_psi) return set_error(KX_ERR_ARG, "kx_vx_apply_block_pairs: NULL buffer");
+    if (psi == vx_psi) return set_error(KX_ERR_ARG, "kx_vx_apply_block_pairs: vx_psi must not overlap psi");
+    const int nb = (n_orb + kOrbBlock - 1) / kOrbBlock;
+    if (n_blocks < 0 || n_blocks > nb * (nb + 1) / 2 || (n_blocks > 0 && !blocks))
+        return set_error(KX_ERR_ARG, "kx_vx_apply_block_pairs: need 0 <= n_blocks <= nb (nb + 1) / 2 and a list");
+    std::vector<int> req(blocks, blocks + 2 * (size_t)n_blocks);
+    std::vector<unsigned char> seen((size_t)nb * nb, 0);
+    for (int b = 0; b < n_blocks; ++b) {
+        const int I = req[2 * b], J = req[2 * b + 1];
+        if (I < 0 || J < I || J >= nb)
+            return set_error(KX_ERR_ARG, "kx_vx_apply_block_pairs: each block pair needs 0 <= I <= J < ceil(n_orb / 4)");
+        if (seen[(size_t)I * nb + J]++)
+            return set_error(KX_ERR_ARG, "kx_vx_apply_block_pairs: a block pair appears twice");
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (n_blocks == 0) {
+        KX_CUDA_TRY(cudaMemsetAsync(vx_psi, 0, sizeof(double) * (size_t)n_orb * plan->N, s));
+        if (e_x) KX_CUDA_TRY(cudaMemsetAsync(e_x, 0, sizeof(double), s));
+        return KX_OK;
+    }
+    plan->blk_req.swap(req);
+    plan->blk_mode = true;
+    int rc = dispatch_vx(plan, n_orb, psi, occ, vx_psi, e_x, false, s);
+    plan->blk_mode = false;
+    return rc;
 }
 
 int kx_energy(kx_plan *plan, int n_orb, const double *psi, const double *occ, double *e_x, kx_stream stream) {

@@ -100,6 +100,7 @@ struct kx_plan_s {
     double *d_V[3] = {nullptr, nullptr, nullptr};     // n[a] x n[a], row-major V[x][k]
     double *d_f64 = nullptr;                          // N, index k1 + n1 (k2 + n2 k3)
     float *d_f32 = nullptr;                           // N, same layout
+    float *d_f32T = nullptr;                          // N, k2 fastest: k2 + n2 (k1 + n1 k3) (KX_F16X3)
 
     // tensor-core operands (device): per axis, hi and lo fp16 blocks of the
     // np x np zero-padded, 2^14-scaled V in 8x8 core-matrix order
@@ -117,6 +118,11 @@ struct kx_plan_s {
     // accumulation groups, rebuilt when n_orb or the pair range changes.
     int ws_norb = -1;
     long long pr_begin = -1, pr_end = -1;
+    // explicit block-pair list (kx_vx_apply_block_pairs): when blk_mode is set,
+    // ensure_pairs enumerates the block pairs of blk_req instead of a range;
+    // blk_cur is the list the current enumeration was built from (empty: range)
+    bool blk_mode = false;
+    std::vector<int> blk_req, blk_cur;
     int *d_pairs = nullptr;       // int2 per item (i, j), i <= j
     int *d_item_slot = nullptr;   // int2 per item: slots of i and j inside its group
     int *d_groups = nullptr;      // kx::Group per group

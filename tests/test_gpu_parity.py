@@ -1191,3 +1191,38 @@ def test_c5_central_differences(kx, c5):
         assert abs(fd - c5["g64"][k, r].item()) < 1e-6 * gmax64
         assert abs(fd - c5["grad"][k, r].item()) < TOL[1]["vx"] * gmax
     assert plan64.status() == kx.KX_OK
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_block_pair_shares_match_oracle_and_sum_to_full(kx, prec):
+    """kx_vx_apply_block_pairs over the 2D block-cyclic shares of four ranks:
+    each share against the oracle's sums over its pairs, the shares summing to
+    kx_vx_apply; an empty share gives zeros; a repeated or out-of-range block
+    pair is rejected."""
+    from paper_2406_16998_gb300 import shard
+    n, h, bc, kind = (24, 40, 16), (0.45, 0.4, 0.5), (D, P, D), S
+    sysd = system(n, h, bc, kind, 11, 480)
+    psi = workloads.make_orbitals(sysd)
+    op = oracle.Plan(n, h, bc, kind)
+    plan = kx.Plan(n, h, bc, kind, precision=prec)
+    psi_d = dev(psi.T)
+    full, ef = kx.kx_vx_apply(plan, psi_d)
+    acc, e = torch.zeros_like(full), 0.0
+    world = 4
+    for r in range(world):
+        bps = shard.rank_block_pairs(sysd.n_orb, r, world)
+        part, ep = kx.kx_vx_apply_block_pairs(plan, psi_d, bps)
+        ref, e_ref = oracle.vx_apply(op, psi, pairs=shard.pairs_of_block_pairs(sysd.n_orb, bps))
+        assert relmax(part.cpu().numpy().T, ref) < TOL[prec]["vx"]
+        assert abs(ep.item() - e_ref) < TOL[prec]["ex"] * abs(e_ref)
+        acc += part
+        e += ep.item()
+    assert relmax(acc.cpu().numpy(), full.cpu().numpy()) < (1e-12 if prec == 0 else 1e-6)
+    assert abs(e - ef.item()) < (1e-12 if prec == 0 else 1e-7) * abs(ef.item())
+    zero, ez = kx.kx_vx_apply_block_pairs(plan, psi_d, [])
+    assert zero.abs().max().item() == 0.0 and ez.item() == 0.0
+    for bad in ([(0, 1), (0, 1)], [(1, 0)], [(0, 3)]):
+        with pytest.raises(kx.KxError) as ei:
+            kx.kx_vx_apply_block_pairs(plan, psi_d, bad)
+        assert ei.value.code == kx.KX_ERR_ARG
+    assert plan.status() == kx.KX_OK

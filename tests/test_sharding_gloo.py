@@ -143,3 +143,65 @@ def test_two_rank_gloo_kpoint_blocks_sum_to_full():
     e = sum(0.5 * base.dV * wk[k] * occ[k, n] * np.vdot(psi[k][:, n], got[k][:, n]).real
             for k in range(len(wk)) for n in range(sysd.n_orb))
     assert abs(e - ex) < 1e-12 * abs(ex)
+
+
+# ------------------------------------------------------ block-cyclic split + reduce-scatter
+BC_SYS = dict(n=(10, 12, 14), h=(0.5, 0.45, 0.4), bc=(0, 1, 0), kernel=1, n_orb=11, n_centres=3, seed=79)
+
+
+def test_block_cyclic_owners_partition_the_pairs():
+    for n_orb in (1, 4, 11, 64, 256):
+        allp = sorted(shard.pair_list(n_orb))
+        for world in (1, 2, 3, 4, 6, 8):
+            pr, pc = shard.process_grid(world)
+            assert pr * pc == world and pr <= pc
+            got = []
+            for r in range(world):
+                bps = shard.rank_block_pairs(n_orb, r, world)
+                assert all(shard.block_owner(I, J, world) == r and I <= J for I, J in bps)
+                got += shard.pairs_of_block_pairs(n_orb, bps)
+            assert sorted(got) == allp
+            rows = [shard.row_range(n_orb, r, world) for r in range(world)]
+            assert rows[0][0] == 0 and rows[-1][1] == n_orb
+            assert all(rows[r][1] == rows[r + 1][0] for r in range(world - 1))
+
+
+def _bc_rank_main(rank, world, port, out_dir):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    sysd = workloads.System(**BC_SYS)
+    psi = workloads.make_orbitals(sysd)
+    op = oracle.Plan(sysd.n, sysd.h, sysd.bc, sysd.kernel, sysd.omega)
+
+    def partial(bps):  # this rank's block pairs with oracle arithmetic (the GPU call on a GPU rank)
+        vx, ex = oracle.vx_apply(op, psi, pairs=shard.pairs_of_block_pairs(sysd.n_orb, bps))
+        return torch.from_numpy(np.ascontiguousarray(vx.T)), ex
+
+    rows, ex = shard.sharded_exchange(partial, sysd.n_orb, rank, world)
+    a, b = shard.row_range(sysd.n_orb, rank, world)
+    np.save(os.path.join(out_dir, f"rows{rank}.npy"), rows.numpy())
+    np.save(os.path.join(out_dir, f"ex{rank}.npy"), np.array([ex, a, b]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 4])
+def test_block_cyclic_reduce_scatter_gives_each_rank_its_rows(world):
+    """Each rank computes its block pairs of the 2D block-cyclic split, one
+    reduce-scatter leaves it the summed rows it owns, one scalar all-reduce
+    gives E_x; together the rows are the oracle's full Vx psi."""
+    with tempfile.TemporaryDirectory() as d:
+        mp.start_processes(_bc_rank_main, args=(world, _free_port(), d), nprocs=world, start_method="spawn")
+        got = [(np.load(os.path.join(d, f"rows{r}.npy")), np.load(os.path.join(d, f"ex{r}.npy")))
+               for r in range(world)]
+    sysd = workloads.System(**BC_SYS)
+    psi = workloads.make_orbitals(sysd)
+    op = oracle.Plan(sysd.n, sysd.h, sysd.bc, sysd.kernel, sysd.omega)
+    vx, ex = oracle.vx_apply(op, psi)
+    full = np.concatenate([g[0] for g in got])
+    assert full.shape == (sysd.n_orb, op.N)
+    assert np.max(np.abs(full - vx.T)) < 1e-12 * np.abs(vx).max()
+    for r, (rows, meta) in enumerate(got):
+        assert (int(meta[1]), int(meta[2])) == shard.row_range(sysd.n_orb, r, world)
+        assert abs(meta[0] - ex) < 1e-12 * abs(ex)

@@ -100,7 +100,6 @@ struct kx_plan_s {
     double *d_V[3] = {nullptr, nullptr, nullptr};     // n[a] x n[a], row-major V[x][k]
     double *d_f64 = nullptr;                          // N, index k1 + n1 (k2 + n2 k3)
     float *d_f32 = nullptr;                           // N, same layout
-    float *d_f32T = nullptr;                          // N, k2 fastest: k2 + n2 (k1 + n1 k3) (KX_F16X3)
 
     // tensor-core operands (device): per axis, hi and lo fp16 blocks of the
     // np x np zero-padded, 2^14-scaled V in 8x8 core-matrix order

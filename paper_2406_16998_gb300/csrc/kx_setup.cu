@@ -184,10 +184,9 @@ __global__ void __launch_bounds__(kEigThreads) eig1d_kernel(int n0, int n1, int 
     for (int k = tid; k < n; k += blockDim.x) lam[k] = lam_s[perm[k]];
 }
 
-// f(l1_k1 + l2_k2 + l3_k3) for every spectral point, float64 and float32, and
-// (tensor-core plans) a float32 copy with k2 fastest, index k2 + n2 (k1 + n1 k3).
+// f(l1_k1 + l2_k2 + l3_k3) for every spectral point, float64 and float32.
 __global__ void ftable_kernel(int n1, int n2, int n3, const double *l1, const double *l2, const double *l3,
-                              int kind, double omega, double *f64, float *f32, float *f32T) {
+                              int kind, double omega, double *f64, float *f32) {
     size_t N = (size_t)n1 * n2 * n3;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < N;
          idx += (size_t)gridDim.x * blockDim.x) {
@@ -197,7 +196,6 @@ __global__ void ftable_kernel(int n1, int n2, int n3, const double *l1, const do
         double f = kernel_f_value(kind, omega, l1[k1] + l2[k2] + l3[k3]);
         f64[idx] = f;
         f32[idx] = (float)f;
-        if (f32T) f32T[(size_t)k2 + (size_t)n2 * ((size_t)k1 + (size_t)n1 * k3)] = (float)f;
     }
 }
 
@@ -240,7 +238,6 @@ int plan_setup(kx_plan *p) {
     }
     KX_CUDA_TRY(cudaMalloc(&p->d_f64, sizeof(double) * p->N));
     KX_CUDA_TRY(cudaMalloc(&p->d_f32, sizeof(float) * p->N));
-    if (p->precision == KX_F16X3) KX_CUDA_TRY(cudaMalloc(&p->d_f32T, sizeof(float) * p->N));
     KX_CUDA_TRY(cudaMalloc(&p->d_status, sizeof(int)));
     KX_CUDA_TRY(cudaMemset(p->d_status, 0, sizeof(int)));
 
@@ -253,7 +250,7 @@ int plan_setup(kx_plan *p) {
     KX_LAUNCH_CHECK("eig1d_kernel launch");
     int blocks = (int)std::min<size_t>((p->N + 255) / 256, (size_t)4 * p->num_sms);
     ftable_kernel<<<blocks, 256>>>(p->n[0], p->n[1], p->n[2], p->d_lam[0], p->d_lam[1], p->d_lam[2], p->kind,
-                                   p->omega, p->d_f64, p->d_f32, p->d_f32T);
+                                   p->omega, p->d_f64, p->d_f32);
     KX_LAUNCH_CHECK("ftable_kernel launch");
     if (p->precision == KX_F16X3) {
         for (int a = 0; a < 3; ++a) {
@@ -284,7 +281,6 @@ void plan_free(kx_plan *p) {
     }
     cudaFree(p->d_f64);
     cudaFree(p->d_f32);
-    cudaFree(p->d_f32T);
     cudaFree(p->d_fft_tw);
     cudaFree(p->d_fft_f);
     cudaFree(p->d_status);

@@ -775,7 +775,6 @@ struct SlabArgs {
     const float *in_max;    // per item
     float *out_max;         // per item (nullable)
     const float *f32;
-    const float *f32T;      // f with k2 fastest: k2 + n2 (k1 + n1 k3) (V-operand form)
     float fmax, sq1, sq2;   // fmax, sqrt(n1), sqrt(n2) (each with a small margin)
     double *e_partial;
     const int2 *pairs;
@@ -1272,497 +1271,6 @@ __global__ void __launch_bounds__(kSlabThreads, 1) tc_slab_kernel(const SlabArgs
     }
 }
 
-// ---------------------------------------------------------------------------
-// Slab kernel, V-operand form.  The same four middle products of Eq. 19 per
-// k3 plane, but with the eigenvector block as the A operand (M = 128 rows: the
-// output index of the 1D transform, n of them valid) and the plane data as
-// the B operand, PL planes side by side along N.  Every D row then belongs to
-// one output index, and each epilogue thread writes only its own row as the
-// next B operand, so no stage transposes:
-//   F1  Y1[k2][x1] = sum_x2 V2[x2][k2] P[x2][x1]   A = V2^T (MN-major), B = P     (MN-major, producers)
-//   F2  Y2[k1][k2] = sum_x1 V1[x1][k1] Y1[k2][x1]  A = V1^T (MN-major), B = Y1^T  (K-major,  row k2 of D1)
-//   S   energy sum f Y2^2;  Z = f Y2               (f table with k2 fastest)
-//   I1  W[x1][k2]  = sum_k1 V1[x1][k1] Z[k1][k2]   A = V1   (K-major),  B = Z     (MN-major, row k1 of D2)
-//   I2  O[x2][x1]  = sum_k2 V2[x2][k2] W[x1][k2]   A = V2   (K-major),  B = W^T   (K-major,  row x1 of D3)
-//   O   D4 row x2 -> the output plane's row x2 (contiguous stores)
-// The A operand (V, held once in shared memory) is shared by the PL planes of
-// a unit, so a product reads 4 KB of A and PL x 1.5 n bytes of B per k-step
-// instead of 4 KB + 1.5 n per plane; with PL = 2 at n = 96 an instruction is
-// bound by the tensor pipe rather than by shared-memory operand reads.  Rows
-// m >= np of the M = 128 tile read whatever follows the V block in shared
-// memory (finite data of the other blocks); their D rows are never read.
-// Two units are in flight (TMEM slot, B buffer and epilogue group g = unit &
-// 1).  DUAL keeps two accumulators per product (the odd hi*hi k-steps in the
-// second, summed in round-to-nearest) and is used with PL = 1.
-// ---------------------------------------------------------------------------
-constexpr int kS2EpiWarps = 16;                           // two groups of eight
-constexpr int kS2ProdWarps = 3;
-constexpr int kS2ProdThreads = 32 * kS2ProdWarps;
-constexpr int kS2MmaWarp = kS2EpiWarps + kS2ProdWarps;
-constexpr int kS2Threads = 32 * (kS2MmaWarp + 1);         // 640: 20 warps, 96 registers each
-constexpr int kS2U = 6;                                   // producer loads in flight per thread
-
-// D(16 consecutive columns) of this lane, both accumulators added when DUAL.
-template <bool DUAL>
-__device__ __forceinline__ void s2_ld16(uint32_t ta, uint32_t tb, float *v) {
-    if (DUAL) {
-        float vb[16];
-        ptx::tmem_ld16x2(ta, tb, v, vb);
-#pragma unroll
-        for (int k = 0; k < 16; ++k) v[k] += vb[k];
-    } else {
-        ptx::tmem_ld16(ta, v);
-    }
-}
-
-// One product D = A_hi B_hi + A_hi B_lo + A_lo B_hi over nks k-steps; the two
-// small cross products first, then the hi*hi steps (split over da / db when
-// DUAL).  Descriptors advance by a_inc / b_inc (16-byte units) per k-step.
-template <bool DUAL>
-__device__ __forceinline__ void s2_issue(uint32_t da, uint32_t db, uint64_t ah0, uint64_t al0, uint64_t bh0,
-                                         uint64_t bl0, uint32_t a_inc, uint32_t b_inc, uint32_t idesc, int nks) {
-    {
-        uint64_t ah = ah0, al = al0, bh = bh0, bl = bl0;
-        for (int ks = 0; ks < nks; ++ks) {
-            ptx::mma_f16(da, ah, bl, idesc, ks > 0 ? 1u : 0u);
-            ptx::mma_f16(da, al, bh, idesc, 1u);
-            ah += a_inc;
-            al += a_inc;
-            bh += b_inc;
-            bl += b_inc;
-        }
-    }
-    uint64_t ah = ah0, bh = bh0;
-    for (int ks = 0; ks < nks; ++ks) {
-        if (DUAL && (ks & 1))
-            ptx::mma_f16(db, ah, bh, idesc, ks > 1 ? 1u : 0u);
-        else
-            ptx::mma_f16(da, ah, bh, idesc, 1u);
-        ah += a_inc;
-        bh += b_inc;
-    }
-}
-
-// Per-plane constants of a unit: item, k3, the four split exponents, the
-// energy weight, and whether the plane exists (the last unit may be short).
-struct S2Plane {
-    long long item, k3;
-    int e1, e2, e3, e4;
-    double w;
-    bool ok;
-};
-
-__device__ __forceinline__ S2Plane s2_plane(const SlabArgs &a, long long pl) {
-    S2Plane r;
-    r.ok = pl < a.total_units;  // total_units counts planes here
-    if (!r.ok) pl = 0;
-    r.item = (unsigned)pl / (unsigned)a.n3;
-    r.k3 = (unsigned)pl % (unsigned)a.n3;
-    const float b1 = __ldg(a.in_max + r.item);
-    const float b2 = b1 * a.sq2, b3 = a.fmax * a.sq1 * b2, b4 = a.sq1 * b3;
-    r.e1 = scale_exp(b1);
-    r.e2 = scale_exp(b2);
-    r.e3 = scale_exp(b3);
-    r.e4 = scale_exp(b4);
-    r.w = 0.0;
-    if (r.ok && a.e_partial != nullptr && !a.rhs_mode) {
-        const int2 ij = a.pairs[r.item];
-        r.w = (ij.x == ij.y) ? 1.0 : 2.0;
-        if (a.occ) r.w *= a.occ[ij.x] * a.occ[ij.y];
-    }
-    return r;
-}
-
-template <int PL, bool DUAL>
-__global__ void __launch_bounds__(kS2Threads, 1) tc_slab2_kernel(const SlabArgs a) {
-    extern __shared__ uint8_t smem_raw[];
-    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const int n1 = a.n1, n2 = a.n2, np1 = a.np1, np2 = a.np2, npm = max(np1, np2);
-    uint8_t *V1hi = smem;
-    uint8_t *V1lo = V1hi + np1 * np1 * 2;
-    uint8_t *V2hi = V1lo + np1 * np1 * 2;
-    uint8_t *V2lo = V2hi + np2 * np2 * 2;
-    const int half_b = PL * 2 * np1 * np2;  // bytes of one fp16 half of a B operand
-    uint8_t *buf0 = V2lo + np2 * np2 * 2;  // per slot: B hi | B lo
-    __shared__ SlabBars bars;
-    __shared__ uint32_t tmem_slot;
-    __shared__ volatile int s_abort;
-    __shared__ double s_red[kS2EpiWarps];
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t slot_cols = (uint32_t)(PL * npm * (DUAL ? 2 : 1));
-    if (warp == kS2MmaWarp) {
-        ptx::tmem_alloc(&tmem_slot, 512);
-        ptx::tmem_relinquish();
-    }
-    if (tid == 0) {
-        for (int b = 0; b < 2; ++b) {
-            ptx::mbar_init(&bars.full[b], kS2ProdThreads);
-            ptx::mbar_init(&bars.empty[b], 1);
-            ptx::mbar_init(&bars.tfull[b], 1);
-            ptx::mbar_init(&bars.ready[b], 256);
-        }
-        ptx::mbar_init(&bars.drain, 1);
-        ptx::fence_mbar_init();
-        s_abort = 0;
-    }
-    {
-        const uint4 *s1 = reinterpret_cast<const uint4 *>(a.V1s);
-        const uint4 *s2 = reinterpret_cast<const uint4 *>(a.V2s);
-        uint4 *d1 = reinterpret_cast<uint4 *>(V1hi);
-        uint4 *d2 = reinterpret_cast<uint4 *>(V2hi);
-        const int c1 = (4 * np1 * np1) / 16, c2 = (4 * np2 * np2) / 16;
-        for (int i = tid; i < c1; i += blockDim.x) d1[i] = __ldg(s1 + i);
-        for (int i = tid; i < c2; i += blockDim.x) d2[i] = __ldg(s2 + i);
-        // the B buffers (and, for small planes, the tail the padded A rows may
-        // reach: up to 8 KB past the last V block) start zeroed
-        uint4 *z = reinterpret_cast<uint4 *>(buf0);
-        const int cz = (4 * half_b + max(0, 8192 - 4 * half_b)) / 16;
-        for (int i = tid; i < cz; i += blockDim.x) z[i] = make_uint4(0u, 0u, 0u, 0u);
-    }
-    ptx::fence_proxy_async_smem();
-    ptx::tc_fence_before();
-    __syncthreads();
-    ptx::tc_fence_after();
-    const uint32_t tmem = tmem_slot;
-    const long long total_planes = a.total_units;
-    const long long total_units = (total_planes + PL - 1) / PL;
-    const int n_my = (int)((total_units - blockIdx.x + gridDim.x - 1) / gridDim.x);
-    const long long n12 = (long long)n1 * n2;
-
-    if (warp == kS2MmaWarp) {
-        // ------------------------------------------------------------------ MMA issue
-        if (lane == 0) {
-            const uint32_t sV1h = ptx::smem_u32(V1hi), sV1l = ptx::smem_u32(V1lo);
-            const uint32_t sV2h = ptx::smem_u32(V2hi), sV2l = ptx::smem_u32(V2lo);
-            // A descriptors (V^T: MN-major; V: K-major) and their k-step increments
-            const uint64_t aF1h = ptx::sdesc(sV2h, np2 * 16, 128), aF1l = ptx::sdesc(sV2l, np2 * 16, 128);
-            const uint64_t aF2h = ptx::sdesc(sV1h, np1 * 16, 128), aF2l = ptx::sdesc(sV1l, np1 * 16, 128);
-            const uint64_t aI1h = ptx::sdesc(sV1h, 128, np1 * 16), aI1l = ptx::sdesc(sV1l, 128, np1 * 16);
-            const uint64_t aI2h = ptx::sdesc(sV2h, 128, np2 * 16), aI2l = ptx::sdesc(sV2l, 128, np2 * 16);
-            const int NB1 = PL * np1 / 8, NB2 = PL * np2 / 8;
-            const uint32_t idF1 = ptx::idesc_f16(128, PL * np1, 1, 1), idF2 = ptx::idesc_f16(128, PL * np2, 1, 0);
-            const uint32_t idI1 = ptx::idesc_f16(128, PL * np2, 0, 1), idI2 = ptx::idesc_f16(128, PL * np1, 0, 0);
-            int jn[2] = {0, 1}, sn[2] = {0, 0};
-            bool ok = true;
-            long long last = clock64();
-            while (ok && (jn[0] < n_my || jn[1] < n_my)) {
-                bool progressed = false;
-#pragma unroll
-                for (int g = 0; g < 2; ++g) {
-                    const int j = jn[g], st = sn[g];
-                    if (j >= n_my) continue;
-                    bool go;
-                    if (st == 0)
-                        go = ptx::mbar_test_wait(&bars.full[g], (uint32_t)((j >> 1) & 1)) &&
-                             (j < 2 || ptx::mbar_test_wait(&bars.ready[g], 1u));
-                    else
-                        go = ptx::mbar_test_wait(&bars.ready[g], (uint32_t)((st - 1) & 1));
-                    if (!go) continue;
-                    ptx::tc_fence_after();
-                    const uint32_t bh = ptx::smem_u32(buf0 + g * 2 * half_b), bl = bh + (uint32_t)half_b;
-                    const uint32_t da = tmem + (uint32_t)g * slot_cols, db = da + (uint32_t)(PL * npm);
-                    if (st == 0)
-                        s2_issue<DUAL>(da, db, aF1h, aF1l, ptx::sdesc(bh, NB1 * 128, 128),
-                                       ptx::sdesc(bl, NB1 * 128, 128), (uint32_t)(np2 * 32) >> 4,
-                                       (uint32_t)(2 * NB1 * 128) >> 4, idF1, np2 >> 4);
-                    else if (st == 1)
-                        s2_issue<DUAL>(da, db, aF2h, aF2l, ptx::sdesc(bh, 128, np1 * 16),
-                                       ptx::sdesc(bl, 128, np1 * 16), (uint32_t)(np1 * 32) >> 4, 256u >> 4, idF2,
-                                       np1 >> 4);
-                    else if (st == 2)
-                        s2_issue<DUAL>(da, db, aI1h, aI1l, ptx::sdesc(bh, NB2 * 128, 128),
-                                       ptx::sdesc(bl, NB2 * 128, 128), 256u >> 4, (uint32_t)(2 * NB2 * 128) >> 4,
-                                       idI1, np1 >> 4);
-                    else
-                        s2_issue<DUAL>(da, db, aI2h, aI2l, ptx::sdesc(bh, 128, np2 * 16),
-                                       ptx::sdesc(bl, 128, np2 * 16), 256u >> 4, 256u >> 4, idI2, np2 >> 4);
-                    ptx::mma_commit(&bars.tfull[g]);
-                    if (st == 3) ptx::mma_commit(&bars.empty[g]);
-                    if (++sn[g] == 4) {
-                        sn[g] = 0;
-                        jn[g] += 2;
-                    }
-                    progressed = true;
-                }
-                const long long now = clock64();
-                if (progressed) {
-                    last = now;
-                } else if (s_abort) {
-                    ok = false;
-                } else if (now - last > a.timeout_cycles) {
-                    s_abort = 1;
-                    atomicExch(a.status, KX_ERR_TIMEOUT);
-                    ok = false;
-                }
-            }
-            if (!ok) {
-                ptx::mma_commit(&bars.drain);
-                ptx::mbar_wait_bounded(&bars.drain, 0, a.timeout_cycles);
-            }
-        }
-        __syncwarp();
-    } else if (warp >= kS2EpiWarps) {
-        // ------------------------------------------------------------------ producers: B of F1
-        // Task t: row r = t % 8 of core matrix (kb, nb), i.e. x2 = 8 kb + r and
-        // the 8 N-values n = 8 nb.. (plane n / np1, x1 = n % np1).  The 8
-        // threads of a core matrix write its 128 contiguous bytes; their global
-        // reads are 8 rows x 32 bytes of the plane.
-        const int ptid = tid - kS2EpiWarps * 32;
-        const int NB1 = PL * np1 / 8, KB1 = np2 / 8;
-        const int ntask = KB1 * NB1 * 8;
-        const int r = ptid & 7;
-        for (int it = 0; it < n_my; ++it) {
-            const int sl = it & 1;
-            const long long u = blockIdx.x + (long long)it * gridDim.x;
-            if (it + 2 < n_my) {
-                // pull the planes of unit it+2 into L2 while this one waits for its buffer
-                const long long u2 = u + 2LL * gridDim.x;
-                for (int p = 0; p < PL; ++p) {
-                    const long long pl = u2 * PL + p;
-                    if (pl >= total_planes) break;
-                    const long long item = (unsigned)pl / (unsigned)a.n3, k3 = (unsigned)pl % (unsigned)a.n3;
-                    const char *src = reinterpret_cast<const char *>(a.in + item * a.N + k3 * n12);
-                    for (int l = ptid; l < (int)((n12 * 4) >> 7); l += kS2ProdThreads)
-                        ptx::prefetch_l2(src + ((long long)l << 7));
-                }
-            }
-            bool ok = it < 2 || slab_wait(&bars.empty[sl], (uint32_t)(((it >> 1) - 1) & 1), a, &s_abort);
-            if (!ok || s_abort) break;
-            // the unit's planes (kept in scalars: a run-time index into arrays
-            // would put them in local memory)
-            const float *src0, *src1 = nullptr;
-            float sc0, sc1 = 0.f;
-            bool ok0, ok1 = false;
-            {
-                const long long pl = u * PL;
-                ok0 = pl < total_planes;
-                const long long q0 = ok0 ? pl : 0;
-                const long long it0 = (unsigned)q0 / (unsigned)a.n3, k30 = (unsigned)q0 % (unsigned)a.n3;
-                src0 = a.in + it0 * a.N + k30 * n12;
-                sc0 = ldexpf(1.f, scale_exp(__ldg(a.in_max + it0)));
-                if (PL == 2) {
-                    ok1 = pl + 1 < total_planes;
-                    const long long q1 = ok1 ? pl + 1 : 0;
-                    const long long it1 = (unsigned)q1 / (unsigned)a.n3, k31 = (unsigned)q1 % (unsigned)a.n3;
-                    src1 = a.in + it1 * a.N + k31 * n12;
-                    sc1 = ldexpf(1.f, scale_exp(__ldg(a.in_max + it1)));
-                }
-            }
-            uint8_t *Bhi = buf0 + sl * 2 * half_b;
-            uint8_t *Blo = Bhi + half_b;
-            int nb = (ptid >> 3) % NB1, kb = (ptid >> 3) / NB1;  // advanced by kS2ProdThreads / 8 tasks per step
-            for (int t0 = ptid; t0 < ntask; t0 += kS2ProdThreads * kS2U) {
-                float v[kS2U][8];
-                int offs[kS2U];
-#pragma unroll
-                for (int i = 0; i < kS2U; ++i) {
-                    const int t = t0 + i * kS2ProdThreads;
-                    offs[i] = -1;
-                    if (t < ntask) {
-                        const int x2 = 8 * kb + r, n0 = 8 * nb;
-                        const int p = (PL == 2 && n0 >= np1) ? 1 : 0;
-                        const int x1 = n0 - p * np1;
-                        offs[i] = kb * (NB1 * 128) + nb * 128 + r * 16;
-                        if (x2 < n2 && x1 < n1 && (p ? ok1 : ok0)) {
-                            ld8((p ? src1 : src0) + (long long)x2 * n1 + x1, v[i]);
-                            const float scp = p ? sc1 : sc0;
-#pragma unroll
-                            for (int c = 0; c < 8; ++c) v[i][c] *= scp;
-                        } else {
-#pragma unroll
-                            for (int c = 0; c < 8; ++c) v[i][c] = 0.f;
-                        }
-                    }
-                    nb += kS2ProdThreads / 8;
-                    while (nb >= NB1) {
-                        nb -= NB1;
-                        ++kb;
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < kS2U; ++i)
-                    if (offs[i] >= 0) store_split8(Bhi, Blo, offs[i], v[i]);
-            }
-            ptx::fence_proxy_async_smem();
-            ptx::mbar_arrive(&bars.full[sl]);
-        }
-    } else {
-        // ------------------------------------------------------------------ epilogue: group g = warp / 8
-        // Warp w reads TMEM lane quadrant q = w % 4 (rows m = 32 q + lane) and,
-        // for PL = 2, plane h = (w / 4) % 2 (its columns [h np, h np + np)); for
-        // PL = 1 the two halves take alternate 16-column chunks.
-        const int g = warp >> 3, q = warp & 3, h = (warp >> 2) & 1;
-        const int m = 32 * q + lane;
-        const int pp = PL == 2 ? h : 0;              // this thread's plane
-        const int c0 = PL == 2 ? 0 : 16 * h;          // first chunk and chunk step
-        const int cs = PL == 2 ? 16 : 32;
-        const uint32_t ta0 = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)g * slot_cols;
-        const uint32_t tb0 = ta0 + (uint32_t)(PL * npm);
-        uint8_t *Bhi = buf0 + g * 2 * half_b;
-        uint8_t *Blo = Bhi + half_b;
-        const int NB2 = PL * np2 / 8;
-        double e_acc = 0.0;
-        bool ok = true;
-        for (int j = g; j < n_my && ok; j += 2) {
-            const long long u = blockIdx.x + (long long)j * gridDim.x;
-            const S2Plane P = s2_plane(a, u * PL + pp);
-            // ---- E1: D1 row k2 = m -> B of F2 (K-major, N row n = pp np2 + m, K = x1)
-            ok = __all_sync(0xffffffffu, slab_wait(&bars.tfull[g], 0u, a, &s_abort));
-            if (!ok) break;
-            ptx::tc_fence_after();
-            {
-                const float s12 = ldexpf(1.f, P.e2 - P.e1 - kVScaleExp);
-                const bool wr = m < np2, val = m < n2;
-                const int n = pp * np2 + m;
-                const int rowoff = (n >> 3) * (np1 * 16) + (n & 7) * 16;
-                const uint32_t col = (uint32_t)(pp * np1);
-                for (int c = c0; c < np1; c += cs) {
-                    float v[16];
-                    s2_ld16<DUAL>(ta0 + col + c, tb0 + col + c, v);
-                    if (wr) {
-#pragma unroll
-                        for (int hh = 0; hh < 2; ++hh) {
-                            float w[8];
-#pragma unroll
-                            for (int k = 0; k < 8; ++k) w[k] = val ? v[8 * hh + k] * s12 : 0.f;
-                            store_split8(Bhi, Blo, rowoff + ((c >> 3) + hh) * 128, w);
-                        }
-                    }
-                }
-            }
-            ptx::fence_proxy_async_smem();
-            ptx::tc_fence_before();
-            ptx::mbar_arrive(&bars.ready[g]);
-            // ---- E2: D2 row k1 = m: energy, Z = f Y2 -> B of I1 (MN-major, K row k1 = m)
-            {
-                const bool val = m < n1 && P.ok;
-                const bool wr = m < np1;
-                const float *frow = a.f32T + ((long long)P.k3 * n1 + (val ? m : 0)) * n2;
-                float fcur[16], fnext[16];
-                auto fetch = [&](int c, float *dst) {
-#pragma unroll
-                    for (int hh = 0; hh < 2; ++hh) {
-                        if (val && c + 8 * hh < n2) {
-                            ld8(frow + c + 8 * hh, dst + 8 * hh);
-                        } else {
-#pragma unroll
-                            for (int k = 0; k < 8; ++k) dst[8 * hh + k] = 0.f;
-                        }
-                    }
-                };
-                fetch(c0, fcur);
-                ok = __all_sync(0xffffffffu, slab_wait(&bars.tfull[g], 1u, a, &s_abort));
-                if (!ok) break;
-                ptx::tc_fence_after();
-                const float u2 = ldexpf(1.f, -(P.e2 + kVScaleExp));
-                const float s3 = ldexpf(1.f, P.e3);
-                const uint32_t col = (uint32_t)(pp * np2);
-                const int rowoff = (m >> 3) * (NB2 * 128) + (m & 7) * 16;
-                float e_row = 0.f;
-                for (int c = c0; c < np2; c += cs) {
-                    if (c + cs < np2) fetch(c + cs, fnext);
-                    float v[16];
-                    s2_ld16<DUAL>(ta0 + col + c, tb0 + col + c, v);
-#pragma unroll
-                    for (int k = 0; k < 16; ++k) {
-                        const float y = v[k] * u2;
-                        const float fy = fcur[k] * y;
-                        e_row = fmaf(fy, y, e_row);
-                        v[k] = fy * s3;
-                        fcur[k] = fnext[k];
-                    }
-                    if (wr) {
-#pragma unroll
-                        for (int hh = 0; hh < 2; ++hh)
-                            store_split8(Bhi, Blo, rowoff + (((int)col + c) / 8 + hh) * 128, v + 8 * hh);
-                    }
-                }
-                if (val) e_acc += P.w * (double)e_row;
-            }
-            ptx::fence_proxy_async_smem();
-            ptx::tc_fence_before();
-            ptx::mbar_arrive(&bars.ready[g]);
-            // ---- E3: D3 row x1 = m -> B of I2 (K-major, N row n = pp np1 + m, K = k2)
-            ok = __all_sync(0xffffffffu, slab_wait(&bars.tfull[g], 0u, a, &s_abort));
-            if (!ok) break;
-            ptx::tc_fence_after();
-            {
-                const float s34 = ldexpf(1.f, P.e4 - P.e3 - kVScaleExp);
-                const bool wr = m < np1, val = m < n1;
-                const int n = pp * np1 + m;
-                const int rowoff = (n >> 3) * (np2 * 16) + (n & 7) * 16;
-                const uint32_t col = (uint32_t)(pp * np2);
-                for (int c = c0; c < np2; c += cs) {
-                    float v[16];
-                    s2_ld16<DUAL>(ta0 + col + c, tb0 + col + c, v);
-                    if (wr) {
-#pragma unroll
-                        for (int hh = 0; hh < 2; ++hh) {
-                            float w[8];
-#pragma unroll
-                            for (int k = 0; k < 8; ++k) w[k] = val ? v[8 * hh + k] * s34 : 0.f;
-                            store_split8(Bhi, Blo, rowoff + ((c >> 3) + hh) * 128, w);
-                        }
-                    }
-                }
-            }
-            ptx::fence_proxy_async_smem();
-            ptx::tc_fence_before();
-            ptx::mbar_arrive(&bars.ready[g]);
-            // ---- O: D4 row x2 = m -> output plane row x2 (x1 contiguous), per-item maximum
-            ok = __all_sync(0xffffffffu, slab_wait(&bars.tfull[g], 1u, a, &s_abort));
-            if (!ok) break;
-            ptx::tc_fence_after();
-            {
-                const float u4 = ldexpf(1.f, -(P.e4 + kVScaleExp));
-                const bool val = m < n2 && P.ok;
-                float *orow = a.out + P.item * a.N + P.k3 * n12 + (long long)(val ? m : 0) * n1;
-                const uint32_t col = (uint32_t)(pp * np1);
-                float my_max = 0.f;
-                for (int c = c0; c < np1; c += cs) {
-                    float v[16];
-                    s2_ld16<DUAL>(ta0 + col + c, tb0 + col + c, v);
-                    if (!val) continue;
-#pragma unroll
-                    for (int hh = 0; hh < 2; ++hh) {
-                        if (c + 8 * hh >= n1) continue;
-                        float w[8];
-#pragma unroll
-                        for (int k = 0; k < 8; ++k) {
-                            w[k] = v[8 * hh + k] * u4;
-                            my_max = fmaxf(my_max, fabsf(w[k]));
-                        }
-                        float4 *dst = reinterpret_cast<float4 *>(orow + c + 8 * hh);
-                        dst[0] = make_float4(w[0], w[1], w[2], w[3]);
-                        dst[1] = make_float4(w[4], w[5], w[6], w[7]);
-                    }
-                }
-                track_max(a.out_max, P.item, my_max, val);
-            }
-            ptx::tc_fence_before();
-            ptx::mbar_arrive(&bars.ready[g]);
-        }
-        if (a.e_partial != nullptr) {
-            double e = e_acc;
-            for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-            if (lane == 0) s_red[warp] = e;
-            ptx::named_bar(1, kS2EpiWarps * 32);
-            if (tid == 0) {
-                double sum = 0.0;
-                for (int w = 0; w < kS2EpiWarps; ++w) sum += s_red[w];
-                a.e_partial[blockIdx.x] = sum;
-            }
-        }
-    }
-    ptx::tc_fence_before();
-    __syncthreads();
-    if (warp == kS2MmaWarp) {
-        ptx::tc_fence_after();
-        ptx::tmem_dealloc(tmem, 512);
-    }
-}
-
 // Accumulation of one chunk, group by group: one thread per four grid points
 // visits the group's items in order, adding g_j psi_j phi_ij to orbital i and
 // g_i psi_i phi_ij to orbital j in shared-memory partial sums (one per orbital
@@ -2003,82 +1511,6 @@ int launch_slab(kx_plan *p, long R, const float *in, const float *in_max, float 
     return prof_end(p, s);
 }
 
-// V-operand slab kernel (tc_slab2_kernel): shared memory of V1, V2 (hi and lo
-// each), two slots of B buffers for PL planes, and the zeroed tail small
-// planes need; TMEM of two slots of PL x max(np1, np2) columns (x2 with DUAL).
-size_t slab2_smem(const kx_plan *p, int PL) {
-    const size_t np1 = p->np[0], np2 = p->np[1];
-    const size_t bufs = 8 * (size_t)PL * np1 * np2;
-    return 1024 + 4 * np1 * np1 + 4 * np2 * np2 + bufs + (bufs < 8192 ? 8192 - bufs : 0);
-}
-
-// Variant of the V-operand slab kernel for this plan: 2 = two planes per unit
-// with single accumulators, 1 = one plane per unit with two accumulators, 0 =
-// none fits (the older slab kernel or the separate passes are used).
-// KX_SLAB2 overrides the choice (tuning and comparison runs).
-int slab2_variant(const kx_plan *p) {
-    const int npm = std::max(p->np[0], p->np[1]);
-    auto fits = [&](int PL, bool dual) {
-        return slab2_smem(p, PL) <= kSlabSmemMax && 2 * PL * npm * (dual ? 2 : 1) <= 512;
-    };
-    int v = fits(2, false) ? 2 : (fits(1, true) ? 1 : 0);
-    if (const char *e = std::getenv("KX_SLAB2")) {
-        const int want = std::atoi(e);
-        if (want == 0) return 0;
-        if (want == 2 && fits(2, false)) return 2;
-        if (want == 1 && fits(1, true)) return 1;
-    }
-    return v;
-}
-
-int launch_slab2(kx_plan *p, int variant, long R, const float *in, const float *in_max, float *out, float *out_max,
-                 double *e_partial, const int2 *pairs, const double *occ, int rhs_mode, cudaStream_t s,
-                 int *grid_out) {
-    SlabArgs a{};
-    a.n1 = p->n[0];
-    a.n2 = p->n[1];
-    a.n3 = p->n[2];
-    a.np1 = p->np[0];
-    a.np2 = p->np[1];
-    a.N = (long long)p->N;
-    a.total_units = (long long)R * a.n3;  // planes
-    a.in = in;
-    a.out = out;
-    a.V1s = p->d_Vs[0];
-    a.V2s = p->d_Vs[1];
-    a.in_max = in_max;
-    a.out_max = out_max;
-    a.f32 = p->d_f32;
-    a.f32T = p->d_f32T;
-    a.fmax = (float)(p->fmax * 1.0001);
-    a.sq1 = (float)(std::sqrt((double)a.n1) * 1.0001);
-    a.sq2 = (float)(std::sqrt((double)a.n2) * 1.0001);
-    a.e_partial = e_partial;
-    a.pairs = pairs;
-    a.occ = occ;
-    a.rhs_mode = rhs_mode;
-    a.status = p->d_status;
-    a.timeout_cycles = 4000000000LL;  // ~2 s at the SM clock
-    const int PL = variant == 2 ? 2 : 1;
-    // at least 120 KB so that one CTA (and one 512-column TMEM allocation) sits on each SM
-    const size_t smem = std::max<size_t>(slab2_smem(p, PL), 120 * 1024);
-    const long long units = (a.total_units + PL - 1) / PL;
-    const int grid = (int)std::max(1LL, std::min<long long>(units, (long long)p->num_sms));
-    if (grid_out) *grid_out = grid;
-    if (int rc = prof_begin(p, PK_SLAB, s)) return rc;
-    if (PL == 2) {
-        KX_CUDA_TRY(cudaFuncSetAttribute(tc_slab2_kernel<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem));
-        tc_slab2_kernel<2, false><<<grid, kS2Threads, smem, s>>>(a);
-    } else {
-        KX_CUDA_TRY(cudaFuncSetAttribute(tc_slab2_kernel<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem));
-        tc_slab2_kernel<1, true><<<grid, kS2Threads, smem, s>>>(a);
-    }
-    KX_LAUNCH_CHECK("tc_slab2_kernel launch");
-    return prof_end(p, s);
-}
-
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct TcLayout {
@@ -2120,16 +1552,12 @@ int run_passes(kx_plan *p, PassArgs a, long R, float *T0, float *T1, float *mx, 
     a.out_max = mx1;
     if ((rc = launch_pass<P_X3F>(p, a, 2, s, nullptr))) return rc;
 
-    const int v2 = energy_only ? 0 : slab2_variant(p);
-    if (!energy_only && use_slab(p) && (v2 > 0 || slab_fits(p))) {
+    if (!energy_only && slab_fits(p) && use_slab(p)) {
         // X2F, X1 and X2I fused: T0 -> T1 without the intermediate round trips
         int grid = 0;
-        if (v2 > 0)
-            rc = launch_slab2(p, v2, R, T0, mx1, T1, mx4, ex ? partial : nullptr, a.pairs, a.occ, a.rhs_mode, s,
-                              &grid);
-        else
-            rc = launch_slab(p, R, T0, mx1, T1, mx4, ex ? partial : nullptr, a.pairs, a.occ, a.rhs_mode, s, &grid);
-        if (rc) return rc;
+        if ((rc = launch_slab(p, R, T0, mx1, T1, mx4, ex ? partial : nullptr, a.pairs, a.occ, a.rhs_mode, s,
+                              &grid)))
+            return rc;
         if (ex) {
             if ((rc = prof_begin(p, PK_FINAL, s))) return rc;
             energy_add_kernel<<<1, 32, 0, s>>>(partial, grid, -0.5 * p->dV, ex);

@@ -310,7 +310,7 @@ def measured_traffic(kind, units_per_launch):
     return None, "no ncu capture for this kernel"
 
 
-def other_workloads(kx, torch, stream, hbm, steps=3):
+def other_workloads(kx, torch, stream, hbm, bf16, steps=3):
     """Context lines beside the headline: the split path on the 80^3 periodic
     screened 256-orbital system (32896 pairs), the same system through the FFT
     variant, the batch of eight systems (26400 pairs) replayed as one CUDA graph,
@@ -365,7 +365,9 @@ def other_workloads(kx, torch, stream, hbm, steps=3):
         psis.append(torch.from_numpy(np.ascontiguousarray(workloads.make_orbitals(sd).T)).cuda())
         outs.append(torch.empty_like(psis[-1]))
         P4 += sd.n_orb * (sd.n_orb + 1) // 2
-    batch = kx.Batch(plans, [sd.n_orb for sd in workloads.C4])
+    t0 = time.perf_counter()
+    batch = kx.Batch(plans, [sd.n_orb for sd in workloads.C4])  # tunes each plan (400 ms budget)
+    create_s = time.perf_counter() - t0
     exs = torch.empty(len(plans), dtype=torch.float64, device="cuda")
     batch.run(psis, outs, e_x=exs, stream=stream)
     e0.record(stream)
@@ -374,8 +376,32 @@ def other_workloads(kx, torch, stream, hbm, steps=3):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
+    useful = sum(workloads.useful_flops_per_pair(sd.n) * sd.n_orb * (sd.n_orb + 1) // 2 for sd in workloads.C4)
+    tf = useful / (ms / 1e3) / 1e12
+    # per system: orbital 0's row of Vx psi (its pair solves with every orbital)
+    # against the oracle, and E_x against 1/2 dV sum_i <psi_i, (Vx psi)_i>
+    import oracle
+    errs, t_or = [], 0.0
+    for k, sd in enumerate(workloads.C4):
+        psi_h = psis[k].cpu().numpy().T
+        op = oracle.Plan(sd.n, sd.h, sd.bc, sd.kernel, sd.omega, sd.fd_order)
+        t1 = time.perf_counter()
+        ref, _ = oracle.vx_apply(op, psi_h, ordered=True, pairs=[(0, j) for j in range(sd.n_orb)])
+        t_or += time.perf_counter() - t1
+        got = outs[k][0].cpu().numpy()
+        vxh = outs[k].cpu().numpy()
+        e_id = 0.5 * sd.dV * float(np.einsum("ij,ij->", psis[k].cpu().numpy(), vxh))
+        errs.append({"system": sd.name, "row0_vx_maxrel_vs_oracle": float(np.max(np.abs(got - ref[:, 0])) /
+                                                                            np.max(np.abs(ref[:, 0]))),
+                     "e_x": exs[k].item(), "e_x_rel_vs_identity": abs(exs[k].item() - e_id) / abs(e_id),
+                     "tuning": plans[k].tuning()})
     res["c4_batch_8_systems"] = {"ms_per_batch": ms, "pair_solves_per_s": P4 / (ms / 1e3), "pairs": P4,
-                                 "status": [p.status() for p in plans]}
+                                 "status": [p.status() for p in plans], "batch_create_s": create_s,
+                                 "useful_tflops": tf,
+                                 "roofline": {"bound": "tensor", "achieved": tf, "peak": bf16 / 3.0, "unit": "TFLOP/s",
+                                              "frac": tf / (bf16 / 3.0),
+                                              "peak_source": "measured bf16_tflops / 3 (three fp16 products)"},
+                                 "per_system": errs, "oracle_rows_s": t_or}
     batch.close()
     del psis, outs, plans
     # Bloch k-points: the 64^3 slab (periodic x1 and x2, vacuum along x3), 16 bands
@@ -717,6 +743,11 @@ def main():
     vx = torch.empty_like(psi)
     ex = torch.empty(1, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
+    # launch shapes chosen by the library's tuner for this grid and orbital count
+    t0 = time.perf_counter()
+    kx.kx_autotune(plan, n_orb, 6000)
+    tune_s = time.perf_counter() - t0
+    tuning = dict(plan.tuning(), tune_s=tune_s)
 
     for _ in range(max(3, args.warmup)):
         kx.kx_vx_apply(plan, psi, out=vx, e_x=ex)
@@ -784,7 +815,8 @@ def main():
            "config": {"workload": WORKLOAD, "grid": list(SYS.n), "h_bohr": SYS.h[0], "bc": "dirichlet",
                       "kernel": "unscreened", "fd_order": SYS.fd_order, "n_orb": n_orb, "pairs_per_step": P,
                       "precision": "f16x3: fp16 hi/lo split of both operands, 3 tcgen05 products, fp32 accumulate",
-                      "l2": "inputs larger than L2 (psi 453 MB float64, fp32 scratch > 1 GB per chunk)"},
+                      "l2": "inputs larger than L2 (psi 453 MB float64, fp32 scratch > 1 GB per chunk)",
+                      "tuning": tuning},
            "vx_psi_ms": ms_step, "roofline": roof, "kernels": kern, "gpu_launches": gpu_launches,
            "clocks": clk}
     n1, n2, n3 = SYS.n
@@ -843,7 +875,7 @@ def main():
         out["ace"] = ace_legs(kx, torch, stream, plan, psi, vx_split, hbm)
         out["multipole"] = multipole_legs(kx, torch, stream, plan, psi, ms_step, bf16)
         out["multipole"]["e_x_zero_boundary"] = ex_split
-        out["other_workloads"] = other_workloads(kx, torch, stream, hbm)
+        out["other_workloads"] = other_workloads(kx, torch, stream, hbm, bf16)
         out["c5_autograd_80cube_256orb"] = c5_leg(kx, torch, stream)
         line, done, vx_ref, ex_ref = cpu_baseline(psi_h)
         out["cpu_baseline"] = line

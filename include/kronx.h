@@ -356,8 +356,11 @@ int kx_energy_kpoints(kx_plan *plan, int n_kpt, const double *theta, const doubl
                       const double *psi, const double *occ, double *ex, kx_stream stream);
 
 /* kx_batch_create — groups n_sys plans (different grids, kernels and orbital
- * counts) into one CUDA graph that runs every system's kx_vx_apply.  Workspaces
- * are reserved here so that the graph holds no allocation.
+ * counts) into one CUDA graph that runs every system's kx_vx_apply.  Each
+ * distinct KX_F16X3 plan that is not tuned yet is first passed to kx_autotune
+ * at its orbital count with a 400 ms budget (shapes tuned earlier in the
+ * process are reused; KX_AUTOTUNE=0 in the environment skips this).
+ * Workspaces are reserved here so that the graph holds no allocation.
  *   plans[n_sys], n_orb[n_sys]  host arrays.  out: host pointer for the handle. */
 int kx_batch_create(int n_sys, kx_plan *const *plans, const int *n_orb, kx_batch **out);
 
@@ -372,9 +375,25 @@ int kx_batch_run(kx_batch *batch, const double *const *psi, double *const *vx_ps
 int kx_batch_destroy(kx_batch *batch);
 
 /* kx_autotune — times the launch shapes the library offers for `plan` at n_orb
- * orbitals (for up to budget_ms milliseconds, on an internal stream, with
- * synthetic orbitals) and keeps the fastest in the plan.  Synchronous. */
+ * orbitals and keeps the fastest in the plan: fused or separate middle passes
+ * (the k3-slice kernel or three pass kernels), pairs per chunk (the default
+ * from the workspace budget and fixed sizes 256 .. 2048), and the number of
+ * shared-memory A stages of the pass kernels.  Each candidate is timed as the
+ * best of three applies after a warm-up, on an internal stream, with synthetic
+ * orbitals (smooth products of sines: the timing does not depend on the
+ * values), until budget_ms milliseconds have passed.  The choice is also kept
+ * in a process-wide table keyed by grid, precision, device model and n_orb:
+ * a later call for the same shape takes it from there without timing.
+ * KX_FP64 and KX_FFT32 plans have a single launch shape (no-op).  Synchronous;
+ * allocates 16 n_orb N bytes for the duration of the call. */
 int kx_autotune(kx_plan *plan, int n_orb, int budget_ms);
+
+/* kx_plan_tuning — the plan's current launch-shape choices (host pointers,
+ * each may be NULL): pairs per chunk (0 = from the workspace budget), fused
+ * middle passes (1) or not (0), pass-kernel A stages (0 = as many as fit), and
+ * the best apply time the tuner measured (0 if the plan was not tuned). */
+int kx_plan_tuning(const kx_plan *plan, long long *chunk_pairs, int *fuse_slab, int *pass_stages,
+                   float *tuned_ms);
 
 /* kx_plan_status — reads and clears the plan's device status word (set by a
  * kernel whose bounded wait ran out).  Synchronises `stream`.  *status_out

@@ -57,6 +57,8 @@ SIGNATURES = {
     "kx_batch_run": (_c_int, [_vp, _vp, _vp, _vp, _vp]),
     "kx_batch_destroy": (_c_int, [_vp]),
     "kx_autotune": (_c_int, [_vp, _c_int, _c_int]),
+    "kx_plan_tuning": (_c_int, [_vp, ctypes.POINTER(_ll), ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
+                                ctypes.POINTER(ctypes.c_float)]),
     "kx_plan_status": (_c_int, [_vp, ctypes.POINTER(_c_int), _vp]),
     "kx_selftest_wait": (_c_int, [_vp, _ll, _vp]),
     "kx_profile": (_c_int, [_vp, _c_int]),
@@ -209,6 +211,13 @@ class Plan:
         ln = np.zeros(k, dtype=np.int64)
         _check(lib().kx_profile_read(self.handle, k, ms.ctypes.data_as(_vp), ln.ctypes.data_as(_vp)))
         return {name: (float(ms[i]), int(ln[i])) for i, name in enumerate(self.PROFILE_KINDS)}
+
+    def tuning(self):
+        """{chunk_pairs, fuse_slab, pass_stages, tuned_ms} of the plan's launch shapes (kx_plan_tuning)."""
+        ch, fz, st, ms = _ll(0), _c_int(0), _c_int(0), ctypes.c_float(0.0)
+        _check(lib().kx_plan_tuning(self.handle, ctypes.byref(ch), ctypes.byref(fz), ctypes.byref(st),
+                                    ctypes.byref(ms)))
+        return {"chunk_pairs": ch.value, "fuse_slab": fz.value, "pass_stages": st.value, "tuned_ms": ms.value}
 
     def status(self, stream=None):
         st = ctypes.c_int(0)

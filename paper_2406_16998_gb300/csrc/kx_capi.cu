@@ -9,6 +9,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -232,6 +234,34 @@ static int dispatch_vx(kx_plan *p, int n_orb, const double *psi, const double *o
 static int check_plan(const kx_plan *p) {
     if (!p) return set_error(KX_ERR_ARG, "plan is NULL");
     return KX_OK;
+}
+
+// Launch shapes chosen by kx_autotune, kept for the life of the process and
+// keyed by what the kernels' launch shapes depend on (grid, precision, device
+// model and orbital count), so that later plans of the same shape start tuned.
+static std::mutex g_tune_mu;
+static std::map<std::string, TuneParams> g_tune_table;
+
+static std::string tune_key(const kx_plan *p, int n_orb) {
+    char name[256] = "";
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, p->device) == cudaSuccess) std::snprintf(name, sizeof(name), "%s", prop.name);
+    char buf[512];
+    std::snprintf(buf, sizeof(buf), "%d,%d,%d|%d|%d|%s", p->n[0], p->n[1], p->n[2], p->precision, n_orb, name);
+    return buf;
+}
+
+static bool tune_lookup(kx_plan *p, int n_orb) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_table.find(tune_key(p, n_orb));
+    if (it == g_tune_table.end()) return false;
+    p->tune = it->second;
+    return true;
+}
+
+static void tune_store(const kx_plan *p, int n_orb) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_table[tune_key(p, n_orb)] = p->tune;
 }
 
 }  // namespace kx
@@ -717,6 +747,22 @@ int kx_batch_create(int n_sys, kx_plan *const *plans, const int *n_orb, kx_batch
     if (!b) return set_error(KX_ERR_NOMEM, "kx_batch_create: host allocation failed");
     b->plans.assign(plans, plans + n_sys);
     b->n_orb.assign(n_orb, n_orb + n_sys);
+    // launch shapes: each distinct plan is tuned once at its orbital count
+    // (a short budget; shapes tuned earlier in the process are reused), unless
+    // KX_AUTOTUNE=0
+    const char *at = std::getenv("KX_AUTOTUNE");
+    const bool autotune = !(at && std::atoi(at) == 0);
+    for (int i = 0; i < n_sys; ++i) {
+        bool seen = false;
+        for (int j = 0; j < i; ++j) seen = seen || plans[j] == plans[i];
+        if (autotune && !seen && !plans[i]->tune.tuned && plans[i]->precision == KX_F16X3) {
+            int rc = kx_autotune(plans[i], n_orb[i], 400);
+            if (rc) {
+                delete b;
+                return rc;
+            }
+        }
+    }
     for (int i = 0; i < n_sys; ++i) {
         int rc = reserve(plans[i], n_orb[i]);
         if (rc) {
@@ -788,6 +834,7 @@ int kx_autotune(kx_plan *plan, int n_orb, int budget_ms) {
     if (int rc = check_plan(plan)) return rc;
     if (n_orb < 1 || n_orb > 4096 || budget_ms < 0) return set_error(KX_ERR_ARG, "kx_autotune: bad arguments");
     if (plan->precision == KX_FP64 || plan->precision == KX_FFT32) return KX_OK;  // single launch shape
+    if (tune_lookup(plan, n_orb)) return KX_OK;  // this shape was tuned earlier in the process
     const size_t vec = sizeof(double) * (size_t)n_orb * plan->N;
     double *buf = nullptr;
     KX_CUDA_TRY(cudaMalloc(&buf, 2 * vec + sizeof(double)));
@@ -814,39 +861,79 @@ int kx_autotune(kx_plan *plan, int n_orb, int budget_ms) {
     TuneParams best = orig;
     float best_ms = 1e30f;
     const long P = (long)n_orb * (n_orb + 1) / 2;
+    // candidates: fused or separate middle passes, pairs per chunk (the default
+    // from the workspace budget first, then fixed sizes), A stages of the passes
+    const long dflt = [&] {
+        TuneParams keep = plan->tune;
+        plan->tune.chunk_pairs = 0;
+        long c = tc_default_chunk(plan, n_orb);
+        plan->tune = keep;
+        return c;
+    }();
+    std::vector<long> chunks = {dflt};
+    for (long c : {256L, 512L, 1024L, 2048L})
+        if (c != dflt && c <= std::max(2 * P, 256L) && c <= 2 * dflt) chunks.push_back(c);
     const int fuse[] = {1, 0};
-    const long chunks[] = {256, 512, 1024, 2048};
+    const int stages[] = {0, 2};
     auto t_start = std::chrono::steady_clock::now();
     int rc = KX_OK;
+    bool over = false;
     for (int fz : fuse) {
         for (long ch : chunks) {
-            if (ch > 2 * P && ch != chunks[0]) continue;
-            double elapsed = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
-            if (elapsed > budget_ms && best_ms < 1e30f) break;
-            plan->tune.fuse_slab = fz;
-            plan->tune.chunk_pairs = ch;
-            rc = tc_vx(plan, n_orb, psi, nullptr, vx, ex, false, s);  // warm-up (also sizes the workspace)
-            if (rc) break;
-            cudaEventRecord(e0, s);
-            rc = tc_vx(plan, n_orb, psi, nullptr, vx, ex, false, s);
-            cudaEventRecord(e1, s);
-            if (rc) break;
-            cudaEventSynchronize(e1);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best_ms) {
-                best_ms = ms;
-                best = plan->tune;
+            for (int st : stages) {
+                double elapsed =
+                    std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+                if (elapsed > budget_ms && best_ms < 1e30f) {
+                    over = true;
+                    break;
+                }
+                plan->tune.fuse_slab = fz;
+                plan->tune.chunk_pairs = ch;
+                plan->tune.pass_stages = st;
+                rc = tc_vx(plan, n_orb, psi, nullptr, vx, ex, false, s);  // warm-up (also sizes the workspace)
+                if (rc) break;
+                float ms = 1e30f;
+                for (int r = 0; r < 3 && rc == KX_OK; ++r) {  // best of three
+                    cudaEventRecord(e0, s);
+                    rc = tc_vx(plan, n_orb, psi, nullptr, vx, ex, false, s);
+                    cudaEventRecord(e1, s);
+                    cudaEventSynchronize(e1);
+                    float t = 0.f;
+                    cudaEventElapsedTime(&t, e0, e1);
+                    ms = std::min(ms, t);
+                }
+                if (rc) break;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = plan->tune;
+                }
             }
+            if (rc || over) break;
         }
-        if (rc) break;
+        if (rc || over) break;
     }
-    plan->tune = rc ? orig : best;
+    if (rc) {
+        plan->tune = orig;
+    } else {
+        plan->tune = best;
+        plan->tune.tuned = 1;
+        plan->tune.tuned_ms = best_ms;
+        tune_store(plan, n_orb);
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaStreamDestroy(s);
     cudaFree(buf);
     return rc;
+}
+
+int kx_plan_tuning(const kx_plan *plan, long long *chunk_pairs, int *fuse_slab, int *pass_stages, float *tuned_ms) {
+    if (int rc = check_plan(plan)) return rc;
+    if (chunk_pairs) *chunk_pairs = plan->tune.chunk_pairs;
+    if (fuse_slab) *fuse_slab = plan->tune.fuse_slab;
+    if (pass_stages) *pass_stages = plan->tune.pass_stages;
+    if (tuned_ms) *tuned_ms = plan->tune.tuned ? plan->tune.tuned_ms : 0.f;
+    return KX_OK;
 }
 
 }  // extern "C"

@@ -50,6 +50,9 @@ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 struct TuneParams {
     long chunk_pairs = 0;     // pairs per chunk (0 = choose from the workspace budget)
     int fuse_slab = 1;        // fuse the mode-2/mode-1 products of each k3 slice into one kernel
+    int pass_stages = 0;      // shared A stages of the pass kernels (0 = as many as fit, at most 4)
+    int tuned = 0;            // set by kx_autotune (or taken from the process-wide table of tuned shapes)
+    float tuned_ms = 0.f;     // best apply time measured by the tuner
 };
 
 // Per-launch CUDA-event timing by kernel kind (kx_profile / kx_profile_read).

@@ -1437,6 +1437,7 @@ int launch_pass(const kx_plan *p, PassArgs a, int axis, cudaStream_t s, int *gri
     a.clk = g_clkbuf + (long long)PASS * kClk * 4096;
 #endif
     a.stages = pass_stages(a.np, false);  // X1's mid operand reuses its tile's A stage
+    if (p->tune.pass_stages > 0) a.stages = std::min(a.stages, p->tune.pass_stages);
     const size_t smem = pass_smem(a.np, a.stages, false);
     KX_CUDA_TRY(cudaFuncSetAttribute(tc_pass_kernel<PASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const long long n_tiles = (a.total_rows + 127) / 128;

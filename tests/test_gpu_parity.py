@@ -830,12 +830,28 @@ def test_autotune_then_apply(kx):
     op = oracle.Plan(n, h, bc, S)
     vx_ref, ex_ref = oracle.vx_apply(op, psi)
     plan = kx.Plan(n, h, bc, S, precision=1)
+    assert plan.tuning()["tuned_ms"] == 0.0
     kx.kx_autotune(plan, 6, 200)
+    t = plan.tuning()
+    assert t["tuned_ms"] > 0.0 and t["fuse_slab"] in (0, 1) and t["pass_stages"] in (0, 2)
     vx, ex = kx.kx_vx_apply(plan, dev(psi.T))
     torch.cuda.synchronize()
     assert plan.status() == kx.KX_OK
     assert relmax(vx.cpu().numpy().T, vx_ref) < TOL[1]["vx"]
     assert abs(ex.item() - ex_ref) < TOL[1]["ex"] * abs(ex_ref)
+    # a second plan of the same shape takes the choice from the process-wide table
+    plan2 = kx.Plan(n, h, bc, S, precision=1)
+    kx.kx_autotune(plan2, 6, 200)
+    assert plan2.tuning() == t
+    # every candidate shape gives the same result within the split tolerance
+    for fz, st in ((0, 2), (1, 0)):
+        import os
+        os.environ["KX_SLAB"] = str(fz)
+        try:
+            vx2, _ = kx.kx_vx_apply(plan2, dev(psi.T))
+        finally:
+            del os.environ["KX_SLAB"]
+        assert relmax(vx2.cpu().numpy().T, vx_ref) < TOL[1]["vx"]
 
 
 # ---------------------------------------------------------------- Bloch k-points
@@ -1226,3 +1242,35 @@ def test_block_pair_shares_match_oracle_and_sum_to_full(kx, prec):
             kx.kx_vx_apply_block_pairs(plan, psi_d, bad)
         assert ei.value.code == kx.KX_ERR_ARG
     assert plan.status() == kx.KX_OK
+
+
+def test_c4_batch_of_the_eight_systems_against_oracle(kx):
+    """Config 4 as configured: the eight systems of uneven grids, boundary
+    conditions and kernels (16-128 orbitals) in one batch graph, each plan tuned
+    by kx_batch_create.  For every system, orbital 0's row of Vx psi (its pair
+    solves with every orbital) against the oracle, E_x against
+    1/2 dV sum_i <psi_i, (Vx psi)_i>, and a second run bit-identical to the first."""
+    plans, psis, outs = [], [], []
+    for sd in workloads.C4:
+        plans.append(kx.Plan.for_system(sd, precision=1))
+        psis.append(dev(workloads.make_orbitals(sd).T))
+        outs.append(torch.empty_like(psis[-1]))
+    batch = kx.Batch(plans, [sd.n_orb for sd in workloads.C4])
+    exs = torch.empty(len(plans), dtype=torch.float64, device="cuda")
+    batch.run(psis, outs, e_x=exs)
+    torch.cuda.synchronize()
+    first = [o.clone() for o in outs]
+    batch.run(psis, outs, e_x=exs)
+    torch.cuda.synchronize()
+    for k, sd in enumerate(workloads.C4):
+        assert plans[k].status() == kx.KX_OK
+        assert plans[k].tuning()["tuned_ms"] > 0.0
+        assert torch.equal(first[k], outs[k])
+        psi_h = psis[k].cpu().numpy()
+        vxh = outs[k].cpu().numpy()
+        e_id = 0.5 * sd.dV * float(np.einsum("ij,ij->", psi_h, vxh))
+        assert abs(exs[k].item() - e_id) < 1e-6 * abs(e_id)
+        op = oracle.Plan(sd.n, sd.h, sd.bc, sd.kernel, sd.omega, sd.fd_order)
+        ref, _ = oracle.vx_apply(op, psi_h.T, ordered=True, pairs=[(0, j) for j in range(sd.n_orb)])
+        assert np.max(np.abs(vxh[0] - ref[:, 0])) < TOL[1]["vx"] * np.abs(ref[:, 0]).max(), sd.name
+    batch.close()

@@ -685,6 +685,335 @@ __global__ void __launch_bounds__(256, 1) bloch_tc_kernel(const float2 *__restri
     }
 }
 
+// Warp-specialised form of bloch_tc_kernel (same operands, layouts, scales and
+// arithmetic): 8 epilogue warps (0-7, TMEM lane quadrant w % 4, complex
+// columns [w / 4 * n / 2, + n / 2), or in transposed mode pencils [64 (w / 4),
+// + 64)) and 4 producer warps (8-11).  Two TMEM slots of 256 columns: while the
+// epilogue drains tile i from slot i & 1, the producers take tile i + 1's
+// maximum, wait until tile i's products have read A, split tile i + 1 into A,
+// issue its products into the other slot (once the epilogue has freed it) and
+// copy tile i + 2 into the fp32 tile.  The tile's scale exponent goes to the
+// epilogue through shared memory and a per-slot mbarrier.  Every wait is
+// bounded; producers agree on the outcome of theirs with a barrier vote.
+constexpr int kTwEpiWarps = 8, kTwProdWarps = 8;
+constexpr int kTwThreads = 32 * (kTwEpiWarps + kTwProdWarps);
+constexpr int kTwProd = 32 * kTwProdWarps;
+
+template <bool FORM, int EPI>
+__global__ void __launch_bounds__(kTwThreads, 1) bloch_tc_ws_kernel(
+    const float2 *__restrict__ in, float2 *__restrict__ out, int n_cols, int n, int inner,
+    const __half *__restrict__ Bs, const float *__restrict__ f, const float2 *__restrict__ P,
+    const float2 *__restrict__ F, int n_orb, long long r0, long long N, EnergyArgs ea, int *status,
+    long long timeout_cycles) {
+    extern __shared__ uint8_t tc_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *Bh = smem, *Bl = Bh + tc_b_bytes(n);
+    uint8_t *Ah = Bl + tc_b_bytes(n), *Al = Ah + tc_a_bytes(n);
+    float2 *S = reinterpret_cast<float2 *>(Al + tc_a_bytes(n));  // [k][m], row stride kTcLd
+    __shared__ uint64_t mma_done[2], epi_done[2], sc_full[2], drain;
+    __shared__ int s_eA[2];
+    __shared__ uint32_t tslot;
+    __shared__ float s_wmax[kTwProdWarps];
+    __shared__ double s_red[kTwEpiWarps];
+    __shared__ volatile int s_abort;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) {
+        ptx::tmem_alloc(&tslot, 512);
+        ptx::tmem_relinquish();
+    }
+    if (tid == 0) {
+        for (int b = 0; b < 2; ++b) {
+            ptx::mbar_init(&mma_done[b], 1);
+            ptx::mbar_init(&epi_done[b], 32 * kTwEpiWarps);
+            ptx::mbar_init(&sc_full[b], 1);
+        }
+        ptx::mbar_init(&drain, 1);
+        ptx::fence_mbar_init();
+        s_abort = 0;
+    }
+    if (warp >= kTwEpiWarps) {  // B hi and lo, once (its copies complete before the first split)
+        const uint4 *src = reinterpret_cast<const uint4 *>(Bs);
+        uint4 *dst = reinterpret_cast<uint4 *>(Bh);
+        const int n16 = (int)(2 * tc_b_bytes(n) / 16);
+        for (int e = tid - 32 * kTwEpiWarps; e < n16; e += kTwProd) ptx::cp_async16(dst + e, src + e, 16u);
+        ptx::cp_async_commit();
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem = tslot;
+    const int n2 = 2 * n;
+    const bool transposed = inner == 1 && n == 64 && EPI == 0;
+    const uint32_t idesc = transposed ? ptx::idesc_f16(n2, 128, 1, 1) : ptx::idesc_f16(128, n2, 1, 1);
+    const int n_tiles = (n_cols + 127) / 128;
+    const int n_my = blockIdx.x < n_tiles ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    auto timed_out = [&]() {
+        s_abort = 1;
+        atomicExch(status, KX_ERR_TIMEOUT);
+    };
+    auto wait = [&](uint64_t *bar, uint32_t parity) {
+        const long long t0 = clock64();
+        while (!ptx::mbar_try_wait(bar, parity)) {
+            if (s_abort) return false;
+            if (clock64() - t0 > timeout_cycles) {
+                timed_out();
+                return false;
+            }
+        }
+        return true;
+    };
+    double e_acc = 0.0;
+
+    if (warp >= kTwEpiWarps) {
+        // ------------------------------------------------------------ producers
+        const int pt = tid - 32 * kTwEpiWarps, pw = warp - kTwEpiWarps;
+        // the fp32 tile of local tile i into S[k][m] (cp.async, or formed from P
+        // and F when FORM; pencils past the end as zeros)
+        auto load_tile = [&](int i) {
+            const int q0 = (blockIdx.x + i * gridDim.x) * 128;
+            const int nq = min(128, n_cols - q0);
+            if (FORM) {
+                const int ppi = (int)(N / n);
+                for (int m0 = pw; m0 < 128; m0 += 4 * kTwProdWarps) {
+                    float2 pv[4][2], fv[4][2];
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const int mb = m0 + kTwProdWarps * b;
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) pv[b][h] = fv[b][h] = make_float2(0.f, 0.f);
+                        if (mb < nq) {
+                            const int q = q0 + mb;
+                            const int r = q / ppi;
+                            const long long x0 = (long long)(q - r * ppi) * n;
+                            const int rr = (int)r0 + r;
+                            const int vv = rr / n_orb, mm = rr - vv * n_orb;
+                            const float2 *Pp = P + (long long)mm * N + x0;
+                            const float2 *Fp = F + (long long)vv * N + x0;
+#pragma unroll
+                            for (int h = 0; h < 2; ++h)
+                                if (lane + 32 * h < n) {
+                                    pv[b][h] = Pp[lane + 32 * h];
+                                    fv[b][h] = Fp[lane + 32 * h];
+                                }
+                        }
+                    }
+#pragma unroll
+                    for (int b = 0; b < 4; ++b)
+#pragma unroll
+                        for (int h = 0; h < 2; ++h)
+                            if (lane + 32 * h < n)
+                                S[(lane + 32 * h) * kTcLd + m0 + kTwProdWarps * b] = cmul_conj(pv[b][h], fv[b][h]);
+                }
+            } else if (inner == 1) {
+                for (int m = pw; m < 128; m += kTwProdWarps) {
+                    float2 *row = S + m;
+                    if (m >= nq) {
+                        for (int k = lane; k < n; k += 32) row[k * kTcLd] = make_float2(0.f, 0.f);
+                        continue;
+                    }
+                    const float2 *src = in + (size_t)(q0 + m) * n;
+                    for (int k = lane; k < n; k += 32) ptx::cp_async8(row + k * kTcLd, src + k, 8u);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int m = lane + 32 * j;
+                    if (m >= nq) {
+                        for (int k = pw; k < n; k += kTwProdWarps) S[k * kTcLd + m] = make_float2(0.f, 0.f);
+                        continue;
+                    }
+                    const int q = q0 + m;
+                    const int o = q / inner;
+                    const float2 *src = in + (size_t)o * n * inner + (q - o * inner);
+                    for (int k = pw; k < n; k += kTwProdWarps)
+                        ptx::cp_async8(S + k * kTcLd + m, src + (size_t)k * inner, 8u);
+                }
+            }
+            ptx::cp_async_commit();
+        };
+        const uint32_t ah0 = ptx::smem_u32(Ah), al0 = ptx::smem_u32(Al);
+        const uint32_t bh0 = ptx::smem_u32(Bh), bl0 = ptx::smem_u32(Bl);
+        const uint32_t gb = 32u * (uint32_t)n;  // B K-group stride
+        if (n_my > 0) load_tile(0);
+        bool ok = true;
+        for (int i = 0; i < n_my && ok; ++i) {
+            const int sl = i & 1;
+            ptx::cp_async_wait<0>();
+            ok = ptx::named_bar_and(1, kTwProd, !s_abort);
+            if (!ok) break;
+            // 1. the tile's maximum and the A scale (capped at 2^100, as in bloch_tc_kernel)
+            float mx = 0.f;
+            for (int e = pt; e < n * 64; e += kTwProd) {  // two complex values per load
+                const float4 v = reinterpret_cast<const float4 *>(S + (e >> 6) * kTcLd)[e & 63];
+                mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+            }
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            if (lane == 0) s_wmax[pw] = mx;
+            // A is free once tile i - 1's products have completed
+            bool w_ok = i == 0 || wait(&mma_done[sl ^ 1], (uint32_t)(((i - 1) >> 1) & 1));
+            ok = ptx::named_bar_and(1, kTwProd, w_ok);
+            if (!ok) break;
+            mx = s_wmax[0];
+#pragma unroll
+            for (int w = 1; w < kTwProdWarps; ++w) mx = fmaxf(mx, s_wmax[w]);
+            int ex = 0;
+            if (mx > 0.f && isfinite(mx)) frexpf(mx, &ex);
+            const int eA = min(14 - ex, 100);
+            const float sA = ldexpf(1.f, eA);
+            // 2. A = [A_r | A_i] sA, split
+            for (int task = pt; task < n * 16; task += kTwProd) {
+                const int k = task % n, g = task / n;
+                const float4 *src = reinterpret_cast<const float4 *>(S + k * kTcLd + 8 * g);
+                float wr[8], wi[8];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const float4 v = src[c];
+                    wr[2 * c] = v.x * sA;
+                    wi[2 * c] = v.y * sA;
+                    wr[2 * c + 1] = v.z * sA;
+                    wi[2 * c + 1] = v.w * sA;
+                }
+                tc_split_store(Ah, Al, g * 128 + (k >> 3) * 2048 + (k & 7) * 16, wr);
+                tc_split_store(Ah, Al, g * 128 + ((n + k) >> 3) * 2048 + ((n + k) & 7) * 16, wi);
+            }
+            ptx::fence_proxy_async_smem();
+            // 3. products into slot sl once the epilogue has drained it (tile i - 2)
+            w_ok = i < 2 || pt != 0 || wait(&epi_done[sl], (uint32_t)(((i - 2) >> 1) & 1));
+            ok = ptx::named_bar_and(1, kTwProd, w_ok);
+            if (!ok) break;
+            if (pt == 0) {
+                s_eA[sl] = eA;
+                ptx::mbar_arrive(&sc_full[sl]);
+                ptx::tc_fence_after();
+                const uint32_t da = tmem + 256u * (uint32_t)sl, db = da + (uint32_t)n2;
+                for (int ks = 0; ks < n2 / 16; ++ks) {
+                    const uint64_t ah = ptx::sdesc(ah0 + 4096u * ks, 2048, 128),
+                                   al = ptx::sdesc(al0 + 4096u * ks, 2048, 128);
+                    const uint64_t bh = ptx::sdesc(bh0 + 2u * gb * ks, gb, 128),
+                                   bl = ptx::sdesc(bl0 + 2u * gb * ks, gb, 128);
+                    if (transposed) {  // D^T = B^T A^T: the same shared bytes, operand roles swapped
+                        ptx::mma_f16(da, bh, al, idesc, ks > 0 ? 1u : 0u);
+                        ptx::mma_f16(da, bl, ah, idesc, 1u);
+                        ptx::mma_f16(db, bh, ah, idesc, ks > 0 ? 1u : 0u);
+                    } else {
+                        ptx::mma_f16(da, ah, bl, idesc, ks > 0 ? 1u : 0u);
+                        ptx::mma_f16(da, al, bh, idesc, 1u);
+                        ptx::mma_f16(db, ah, bh, idesc, ks > 0 ? 1u : 0u);
+                    }
+                }
+                ptx::mma_commit(&mma_done[sl]);
+            }
+            // 4. S is free: the next tile loads while the products and the epilogue run
+            if (i + 1 < n_my) load_tile(i + 1);
+        }
+        ptx::cp_async_wait<0>();
+        if (pt == 0 && s_abort) {
+            // a wait gave up: the products already issued finish before TMEM is released
+            ptx::mma_commit(&drain);
+            ptx::mbar_wait_bounded(&drain, 0, timeout_cycles);
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        for (int i = 0; i < n_my; ++i) {
+            const int sl = i & 1;
+            const int q0 = (blockIdx.x + i * gridDim.x) * 128;
+            const int nq = min(128, n_cols - q0);
+            // EPI 1 and 2: this thread's f(Lambda) values (row m, its n / 2 columns),
+            // fetched before the products are waited for
+            float fpre[kTcMaxN / 2];
+            if constexpr (EPI != 0) {
+                const int m = 32 * (warp & 3) + lane, hh = warp >> 2;
+                const int q = q0 + min(m, nq - 1);
+                const int i_in = q - (q / inner) * inner;
+#pragma unroll
+                for (int c = 0; c < kTcMaxN / 2; ++c)
+                    fpre[c] = c < (n >> 1) ? f[(size_t)(hh * (n >> 1) + c) * inner + i_in] : 0.f;
+            }
+            const uint32_t par = (uint32_t)((i >> 1) & 1);
+            const bool ok = __all_sync(0xffffffffu, wait(&sc_full[sl], par) && wait(&mma_done[sl], par));
+            if (!ok) break;
+            ptx::tc_fence_after();
+            const float unscale = ldexpf(1.f, -s_eA[sl] - kVScaleExp);
+            const uint32_t slot = tmem + 256u * (uint32_t)sl;
+            if (transposed) {
+                const int qd = warp & 3, hh = warp >> 2;
+                const int cr = 32 * qd + lane;
+                const int im = cr >= n ? 1 : 0;
+                const int c = cr - im * n;
+                const uint32_t tl = slot + ((uint32_t)(32 * qd) << 16);
+                float *ob = reinterpret_cast<float *>(out + (size_t)q0 * n + c) + im;
+                for (int m0 = 64 * hh; m0 < 64 * hh + 64; m0 += 16) {
+                    float va[16], vb[16];
+                    ptx::tmem_ld16x2(tl + (uint32_t)m0, tl + (uint32_t)(n2 + m0), va, vb);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (m0 + j < nq) ob[(size_t)(m0 + j) * 2 * n] = (va[j] + vb[j]) * unscale;
+                }
+            } else {
+                const int qd = warp & 3, hh = warp >> 2;
+                const int m = 32 * qd + lane;
+                const uint32_t tl = slot + ((uint32_t)(32 * qd) << 16);
+                const int half = n >> 1;
+                const bool valid = m < nq;
+                const int q = q0 + min(m, nq - 1);
+                const int item = q / inner;
+                const int i_in = q - item * inner;
+                float2 *dst = inner == 1 ? out + (size_t)q * n : out + (size_t)item * n * inner + i_in;
+                double wj = 0.0;
+                if constexpr (EPI == 2) {
+                    const long long rr = ea.r0 + item;
+                    const long long vv = rr / ea.n_orb, mm = rr - vv * ea.n_orb;
+                    wj = valid ? ea.cb * (ea.occ_q ? ea.occ_q[mm] : 1.0) * (ea.occ_k ? ea.occ_k[vv] : 1.0) : 0.0;
+                }
+                float ej = 0.f;
+#pragma unroll
+                for (int cc = 0; cc < kTcMaxN / 32; ++cc) {
+                    if (16 * cc >= half) break;
+                    const int c0 = hh * half + 16 * cc;
+                    float ra[16], rb[16], ia[16], ib[16];
+                    ptx::tmem_ld16x2(tl + (uint32_t)c0, tl + (uint32_t)(n2 + c0), ra, rb);
+                    ptx::tmem_ld16x2(tl + (uint32_t)(n + c0), tl + (uint32_t)(n2 + n + c0), ia, ib);
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) {
+                        float2 v = make_float2((ra[c] + rb[c]) * unscale, (ia[c] + ib[c]) * unscale);
+                        if constexpr (EPI == 1) {
+                            const float fv = fpre[16 * cc + c];
+                            v.x *= fv;
+                            v.y *= fv;
+                        }
+                        if constexpr (EPI == 2) {
+                            const float fv = fpre[16 * cc + c];
+                            ej = fmaf(fv, v.x * v.x + v.y * v.y, ej);
+                        } else if (valid) {
+                            dst[(size_t)(c0 + c) * inner] = v;
+                        }
+                    }
+                }
+                if constexpr (EPI == 2) e_acc += wj * (double)ej;
+            }
+            ptx::tc_fence_before();
+            ptx::mbar_arrive(&epi_done[sl]);
+        }
+        if constexpr (EPI == 2) {
+            for (int o = 16; o > 0; o >>= 1) e_acc += __shfl_xor_sync(0xffffffffu, e_acc, o);
+            if (lane == 0) s_red[warp] = e_acc;
+        }
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    if constexpr (EPI == 2) {
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < kTwEpiWarps; ++w) t += s_red[w];
+            ea.partial[blockIdx.x] = t;
+        }
+    }
+    if (warp == 0) {
+        ptx::tc_fence_after();
+        ptx::tmem_dealloc(tmem, 512);
+    }
+}
+
 struct BlochAxes {
     int n[3];
     double h[3];
@@ -1012,9 +1341,22 @@ int launch_tc(kx_plan *p, int axis, long long R, const float2 *in, float2 *out, 
                                          (int)tc_smem_bytes(kTcMaxN)));
         attr = true;
     }
+    // warp-specialised form unless KX_BLOCH_WS=0 (comparison runs)
+    const char *ws_env = std::getenv("KX_BLOCH_WS");
+    const bool ws = !(ws_env && std::atoi(ws_env) == 0);
+    static bool attr_ws = false;
+    if (ws && !attr_ws) {
+        KX_CUDA_TRY(cudaFuncSetAttribute(bloch_tc_ws_kernel<FORM, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tc_smem_bytes(kTcMaxN)));
+        attr_ws = true;
+    }
     if (int rc = prof_begin(p, PK_BLOCH, s)) return rc;
-    bloch_tc_kernel<FORM, EPI><<<grid, 256, smem, s>>>(in, out, (int)n_cols, n, inner, Bs, f, P, F, n_orb, r0, N, ea,
-                                                       p->d_status, 2000000000LL);
+    if (ws)
+        bloch_tc_ws_kernel<FORM, EPI><<<grid, kTwThreads, smem, s>>>(in, out, (int)n_cols, n, inner, Bs, f, P, F,
+                                                                     n_orb, r0, N, ea, p->d_status, 2000000000LL);
+    else
+        bloch_tc_kernel<FORM, EPI><<<grid, 256, smem, s>>>(in, out, (int)n_cols, n, inner, Bs, f, P, F, n_orb, r0, N,
+                                                           ea, p->d_status, 2000000000LL);
     KX_LAUNCH_CHECK("bloch_tc_kernel launch");
     return prof_end(p, s);
 }

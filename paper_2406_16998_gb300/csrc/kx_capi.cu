@@ -56,10 +56,15 @@ int ensure_workspace(kx_plan *p, size_t bytes) {
     return KX_OK;
 }
 
-// Pair enumeration: orbitals in blocks of kOrbBlock; block pairs (I, J), I <= J,
-// in row-major order; inside a diagonal block the upper triangle row-major,
-// inside an off-diagonal block all (i, j) row-major.  Each block pair is one
-// accumulation group.  [begin, end) restricts the list to a sub-range of this
+// Pair enumeration: orbitals in blocks of kOrbBlock (nb blocks); block pairs
+// (I, J), I <= J, first every pair without the last block column-major
+// (J = 0 .. nb-2, I = 0 .. J), then the last block's pairs (I, nb-1) for
+// I = 0 .. nb-1; inside a diagonal block the upper triangle row-major, inside an
+// off-diagonal block all (i, j) row-major.  Each block pair is one accumulation
+// group.  Early groups need only the first orbitals (a host-buffer call starts
+// while later orbitals are still being copied), and each block's rows are
+// final as soon as its pair with the last block is done (their copies back
+// overlap the rest).  [begin, end) restricts the list to a sub-range of this
 // enumeration (groups are cut at the range ends).
 // With p->blk_mode set, the block pairs of p->blk_req (I <= J each, in the
 // given order) are enumerated instead, each whole; begin / end are ignored.
@@ -88,11 +93,15 @@ int ensure_pairs(kx_plan *p, int n_orb, cudaStream_t s, long long begin, long lo
         visit = p->blk_req;
     } else {
         visit.reserve((size_t)nb * (nb + 1));
-        for (int IB = 0; IB < nb; ++IB)
-            for (int JB = IB; JB < nb; ++JB) {
+        for (int JB = 0; JB + 1 < nb; ++JB)
+            for (int IB = 0; IB <= JB; ++IB) {
                 visit.push_back(IB);
                 visit.push_back(JB);
             }
+        for (int IB = 0; IB < nb; ++IB) {
+            visit.push_back(IB);
+            visit.push_back(nb - 1);
+        }
     }
     long long k = 0;
     for (size_t v = 0; v + 1 < visit.size(); v += 2) {
@@ -126,9 +135,12 @@ int ensure_pairs(kx_plan *p, int n_orb, cudaStream_t s, long long begin, long lo
         }
     }
     first.push_back((int)(pairs.size() / 2));
-    std::vector<int> last(n_orb, -1);
+    std::vector<int> last(n_orb, -1), maxorb(groups.size(), 0);
     for (size_t gi = 0; gi < groups.size(); ++gi)
-        for (int t = 0; t < groups[gi].n_slots; ++t) last[groups[gi].orb[t]] = (int)gi;
+        for (int t = 0; t < groups[gi].n_slots; ++t) {
+            last[groups[gi].orb[t]] = (int)gi;
+            maxorb[gi] = std::max(maxorb[gi], groups[gi].orb[t]);
+        }
     const size_t P = pairs.size() / 2;
     if (P > p->pairs_cap) {
         cudaFree(p->d_pairs);
@@ -164,6 +176,7 @@ int ensure_pairs(kx_plan *p, int n_orb, cudaStream_t s, long long begin, long lo
     }
     p->h_group_first = first;
     p->h_orb_last = last;
+    p->h_group_maxorb = maxorb;
     p->ws_norb = n_orb;
     p->pr_begin = begin;
     p->pr_end = end;
@@ -498,8 +511,42 @@ int kx_vx_apply_host(kx_plan *plan, int n_orb, const double *psi, const double *
     double *d_vx = d_psi + (size_t)n_orb * plan->N;
     double *d_ex = d_vx + (size_t)n_orb * plan->N;
     double *d_occ = occ ? d_ex + 1 : nullptr;
-    KX_CUDA_TRY(cudaMemcpyAsync(d_psi, psi, vec, cudaMemcpyHostToDevice, s));
     if (occ) KX_CUDA_TRY(cudaMemcpyAsync(d_occ, occ, sizeof(double) * n_orb, cudaMemcpyHostToDevice, s));
+    // The orbitals go over in pieces of whole orbital blocks on their own stream
+    // (after the work already queued on s), each with an event; the split path
+    // starts on the first pieces while the later ones are still copying (its
+    // pair order needs the first orbitals first).  Float64 plans and plans with
+    // multipole boundary values take the orbitals in one copy first.
+    const bool by_pieces = plan->precision != KX_FP64 && plan->mp_lmax < 0;
+    if (by_pieces) {
+        if (!plan->h2d_stream) KX_CUDA_TRY(cudaStreamCreateWithFlags(&plan->h2d_stream, cudaStreamNonBlocking));
+        const int nb = (n_orb + kOrbBlock - 1) / kOrbBlock;
+        const int n_pieces = std::min(8, nb);
+        const int bpp = (nb + n_pieces - 1) / n_pieces;  // blocks per piece
+        InputPieces pcs;
+        for (int b0 = 0; b0 < nb; b0 += bpp) pcs.end.push_back(std::min(n_orb, (b0 + bpp) * kOrbBlock));
+        while (plan->h2d_events.size() < pcs.end.size() + 1) {
+            cudaEvent_t ev;
+            KX_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+            plan->h2d_events.push_back(ev);
+        }
+        cudaEvent_t start = plan->h2d_events.back();
+        KX_CUDA_TRY(cudaEventRecord(start, s));
+        KX_CUDA_TRY(cudaStreamWaitEvent(plan->h2d_stream, start, 0));
+        int o0 = 0;
+        for (size_t k = 0; k < pcs.end.size(); ++k) {
+            const int o1 = pcs.end[k];
+            KX_CUDA_TRY(cudaMemcpyAsync(d_psi + (size_t)o0 * plan->N, psi + (size_t)o0 * plan->N,
+                                        sizeof(double) * (size_t)(o1 - o0) * plan->N, cudaMemcpyHostToDevice,
+                                        plan->h2d_stream));
+            KX_CUDA_TRY(cudaEventRecord(plan->h2d_events[k], plan->h2d_stream));
+            pcs.ready.push_back(plan->h2d_events[k]);
+            o0 = o1;
+        }
+        plan->in_pieces = pcs;
+    } else {
+        KX_CUDA_TRY(cudaMemcpyAsync(d_psi, psi, vec, cudaMemcpyHostToDevice, s));
+    }
     // rows of Vx psi that the split path reports final are copied back on the
     // plan's copy stream while the later chunks compute
     struct Ctx {
@@ -536,6 +583,7 @@ int kx_vx_apply_host(kx_plan *plan, int n_orb, const double *psi, const double *
     if (plan->mp_lmax >= 0) plan->final_hook = FinalHook{};
     int rc = dispatch_vx(plan, n_orb, d_psi, d_occ, d_vx, d_ex, false, s);
     plan->final_hook = FinalHook{};
+    plan->in_pieces = InputPieces{};
     if (!rc) rc = ctx.rc;
     // the copy stream's work joins the caller's stream before the rest is read
     cudaEvent_t done;
@@ -546,6 +594,7 @@ int kx_vx_apply_host(kx_plan *plan, int n_orb, const double *psi, const double *
     if (e != cudaSuccess) return cuda_error(e, "kx_vx_apply_host copy join");
     if (rc) {
         cudaStreamSynchronize(s);
+        if (plan->h2d_stream) cudaStreamSynchronize(plan->h2d_stream);  // the caller's psi is read until then
         return rc;
     }
     if (ctx.copied < n_orb)

@@ -81,6 +81,14 @@ struct FinalHook {
     void (*fn)(void *ctx, int o0, int o1, cudaStream_t s) = nullptr;
     void *ctx = nullptr;
 };
+// Orbitals that arrive in pieces (kx_vx_apply_host): piece k holds orbitals
+// [end[k-1], end[k]) and is on the device once ready[k] has completed; the
+// split path waits for (and converts) a piece only before the first chunk that
+// needs it.
+struct InputPieces {
+    std::vector<int> end;
+    std::vector<cudaEvent_t> ready;
+};
 }  // namespace kx
 
 struct kx_plan_s {
@@ -137,6 +145,10 @@ struct kx_plan_s {
     kx::FinalHook final_hook;
     cudaStream_t copy_stream = nullptr;
     std::vector<cudaEvent_t> copy_events;
+    kx::InputPieces in_pieces;                // set only for the duration of a host-buffer call
+    cudaStream_t h2d_stream = nullptr;
+    std::vector<cudaEvent_t> h2d_events;
+    std::vector<int> h_group_maxorb;          // per group: its largest orbital index
     // pair {i, j} in the current pair range (n_orb x n_orb bytes, symmetric)
     unsigned char *d_pair_mask = nullptr;
     size_t pair_mask_cap = 0;

@@ -296,6 +296,10 @@ void plan_free(kx_plan *p) {
     p->copy_events.clear();
     if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
     p->copy_stream = nullptr;
+    for (cudaEvent_t e : p->h2d_events) cudaEventDestroy(e);
+    p->h2d_events.clear();
+    if (p->h2d_stream) cudaStreamDestroy(p->h2d_stream);
+    p->h2d_stream = nullptr;
 }
 
 }  // namespace kx

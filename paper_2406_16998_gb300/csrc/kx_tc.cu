@@ -1679,13 +1679,41 @@ int tc_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, double *v
     const long long N = (long long)p->N;
 
     KX_CUDA_TRY(cudaMemsetAsync(L.orb_max, 0, sizeof(float) * n_orb, s));
-    {
-        dim3 g((unsigned)std::min<long long>((N + 255) / 256, 64), (unsigned)n_orb);
-        if ((rc = prof_begin(p, PK_PREP, s))) return rc;
-        prep_kernel<<<g, 256, 0, s>>>(psi, L.psi32, L.orb_max, n_orb, N);
+    // fp64 -> fp32 copies and maxima of orbitals [o0, o1)
+    auto prep_range = [&](int o0, int o1) -> int {
+        if (o1 <= o0) return KX_OK;
+        dim3 g((unsigned)std::min<long long>((N + 255) / 256, 64), (unsigned)(o1 - o0));
+        if (int r = prof_begin(p, PK_PREP, s)) return r;
+        prep_kernel<<<g, 256, 0, s>>>(psi + (size_t)o0 * N, L.psi32 + (size_t)o0 * N, L.orb_max + o0, o1 - o0, N);
         KX_LAUNCH_CHECK("prep_kernel launch");
-        if ((rc = prof_end(p, s))) return rc;
+        return prof_end(p, s);
+    };
+    // orbitals arriving in pieces: each is waited for and converted before the
+    // first chunk that needs it (the multipole correction needs all of them first)
+    const InputPieces &pc = p->in_pieces;
+    const bool pieces = !pc.end.empty() && !energy_only && !mp_tc_eligible(p, n_orb, psi);
+    int prepped = 0;  // pieces converted so far
+    auto need = [&](int o_need) -> int {
+        while (prepped < (int)pc.end.size() && (prepped == 0 ? 0 : pc.end[prepped - 1]) < o_need) {
+            KX_CUDA_TRY(cudaStreamWaitEvent(s, pc.ready[prepped], 0));
+            if (int r = prep_range(prepped == 0 ? 0 : pc.end[prepped - 1], pc.end[prepped])) return r;
+            ++prepped;
+        }
+        return KX_OK;
+    };
+    if (pieces) {
+        if (!pc.end.empty() && pc.end.back() < n_orb) return set_error(KX_ERR_ARG, "input pieces do not cover the orbitals");
+    } else {
+        for (size_t k = 0; k < pc.ready.size(); ++k) KX_CUDA_TRY(cudaStreamWaitEvent(s, pc.ready[k], 0));
+        if ((rc = prep_range(0, n_orb))) return rc;
     }
+    auto piece_of = [&](int o) {
+        int k = 0;
+        while (k + 1 < (int)pc.end.size() && pc.end[k] <= o) ++k;
+        return k;
+    };
+    const int nb = (n_orb + kOrbBlock - 1) / kOrbBlock;
+    const std::vector<int> &maxorb = p->h_group_maxorb;
     if (ex) KX_CUDA_TRY(cudaMemsetAsync(ex, 0, sizeof(double), s));
     if (!energy_only) {
         // with multipole boundary values the accumulator starts from the boundary
@@ -1702,7 +1730,25 @@ int tc_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, double *v
     int g0 = 0, o_fin = 0;
     while (g0 < n_groups) {
         int g1 = g0 + 1;
-        while (g1 < n_groups && first[g1 + 1] - first[g0] <= chunk) ++g1;
+        while (g1 < n_groups && first[g1 + 1] - first[g0] <= chunk) {
+            if (pieces) {
+                // the first two pieces each end a chunk (their successors are still
+                // copying); later pieces have arrived by the time they are needed.
+                // Among the last block's pairs (each finishes a row block) eight per
+                // chunk, so that finished rows are copied back while the rest computes
+                // (smaller chunks there cost more than the copies they hide)
+                const bool last0 = maxorb[g0] / kOrbBlock == nb - 1 && maxorb[g1] / kOrbBlock == nb - 1;
+                const int pg0 = piece_of(maxorb[g0]);
+                if (pg0 < 2 && piece_of(maxorb[g1]) > pg0) break;
+                if (last0 && g1 - g0 >= 8) break;
+            }
+            ++g1;
+        }
+        if (pieces) {
+            int o_need = 0;
+            for (int g = g0; g < g1; ++g) o_need = std::max(o_need, maxorb[g] + 1);
+            if ((rc = need(o_need))) return rc;
+        }
         const long c0 = first[g0];
         const long R = first[g1] - c0;
         KX_CUDA_TRY(cudaMemsetAsync(L.mx, 0, sizeof(float) * 4 * chunk, s));
@@ -1737,6 +1783,7 @@ int tc_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, double *v
         }
         g0 = g1;
     }
+    if (pieces && (rc = need(n_orb))) return rc;  // every piece is on the device when the call's work ends
     if (!energy_only) return finalize_rows(p, L.acc, vx, o_fin, n_orb, s);
     return KX_OK;
 }

@@ -30,21 +30,23 @@ def pair_range(n_orb: int, rank: int, world: int):
 ORB_BLOCK = 4  # orbitals per block of the library's pair enumeration
 
 
+def n_blocks(n_orb: int) -> int:
+    return (n_orb + ORB_BLOCK - 1) // ORB_BLOCK
+
+
+def block_pairs(n_orb: int):
+    """The library's order of the orbital block pairs (I, J), I <= J: every pair
+    without the last block column-major (J = 0 .. nb-2, I = 0 .. J), then the
+    last block's pairs (I, nb-1), I = 0 .. nb-1."""
+    nb = n_blocks(n_orb)
+    return [(I, J) for J in range(nb - 1) for I in range(J + 1)] + [(I, nb - 1) for I in range(nb)]
+
+
 def pair_list(n_orb: int):
     """The library's enumeration of the unordered pairs (i <= j): orbitals in
-    blocks of ORB_BLOCK, block pairs (I, J), I <= J, row-major; inside a
+    blocks of ORB_BLOCK, block pairs in the order of block_pairs; inside a
     diagonal block i <= j row-major, inside an off-diagonal block all (i, j)."""
-    out = []
-    nb = (n_orb + ORB_BLOCK - 1) // ORB_BLOCK
-    for IB in range(nb):
-        for JB in range(IB, nb):
-            I = range(IB * ORB_BLOCK, min(n_orb, (IB + 1) * ORB_BLOCK))
-            J = range(JB * ORB_BLOCK, min(n_orb, (JB + 1) * ORB_BLOCK))
-            for i in I:
-                for j in J:
-                    if IB != JB or j >= i:
-                        out.append((i, j))
-    return out
+    return pairs_of_block_pairs(n_orb, block_pairs(n_orb))
 
 
 def pair_at(n_orb: int, k: int):
@@ -68,16 +70,6 @@ def kpoint_block_range(n_kpt: int, rank: int, world: int):
 
 
 # ------------------------------------------------- two-dimensional block-cyclic split
-def n_blocks(n_orb: int) -> int:
-    return (n_orb + ORB_BLOCK - 1) // ORB_BLOCK
-
-
-def block_pairs(n_orb: int):
-    """All orbital block pairs (I, J), I <= J, row-major (the library's order)."""
-    nb = n_blocks(n_orb)
-    return [(I, J) for I in range(nb) for J in range(I, nb)]
-
-
 def process_grid(world: int):
     """(pr, pc), pr * pc = world, pr the largest divisor of world <= sqrt(world)."""
     if world < 1:

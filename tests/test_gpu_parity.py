@@ -252,11 +252,13 @@ def test_multipole_vx_and_energy_match_oracle(kx, prec):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-def test_multipole_pair_ranges_host_path_and_batch(kx, prec):
+def test_multipole_pair_ranges_host_path_and_batch(kx, prec, monkeypatch):
     """With boundary values from the expansion: pair ranges add up to the full
     apply, the host-buffer entry point and a captured batch give the device
-    path's result."""
+    path's result (the batch with the plan's launch shapes as they are: a tuned
+    shape may take the separate middle passes, which round differently)."""
     from paper_2406_16998_gb300 import shard
+    monkeypatch.setenv("KX_AUTOTUNE", "0")
     n, h, bc = MP_GRID
     psi = workloads.make_orbitals(system(n, h, bc, U, 6, 79))
     plan = kx.Plan(n, h, bc, U, precision=prec)
@@ -780,9 +782,11 @@ def test_pair_ranges_sum_to_full_apply(kx, prec):
 
 @pytest.mark.parametrize("prec", [0, 1])
 def test_host_buffers_match_device_path(kx, prec, monkeypatch):
-    """kx_vx_apply_host (host buffers; rows of Vx psi copied back chunk by chunk
-    as they become final) gives the device path's result bit for bit, over
-    several chunks of the pair list."""
+    """kx_vx_apply_host (host buffers; the orbitals copied in pieces that the
+    first chunks start on, rows of Vx psi copied back chunk by chunk as they
+    become final) gives the device path's Vx psi bit for bit, over several
+    chunks of the pair list; E_x to the last bits (the host path cuts its chunks
+    at the copy pieces, which regroups the float64 energy sum)."""
     monkeypatch.setenv("KX_CHUNK_PAIRS", "16")
     n, h, bc = (24, 16, 32), (0.4, 0.45, 0.5), (D, P, D)
     sysd = system(n, h, bc, S, 12, 61)
@@ -798,7 +802,7 @@ def test_host_buffers_match_device_path(kx, prec, monkeypatch):
         vx_h, ex_h = kx.kx_vx_apply_host(plan, psi_h)
         assert plan.status() == kx.KX_OK
         assert np.array_equal(vx_h.numpy(), vx)
-        assert ex_h == ex.item()
+        assert abs(ex_h - ex.item()) <= 1e-13 * abs(ex.item())
 
 
 def test_unaligned_output_pointer(kx):

@@ -44,7 +44,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["kronx", "reference"], default="kronx")
     ap.add_argument("--no-extras", action="store_true", help="skip FP64/e2e/oracle legs (profiling runs)")
-    ap.add_argument("--profile-case", choices=["small", "ace", "multipole", "fft", "kpoints"], default=None,
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the launch-shape tuner (profiling runs: keeps its trial launches out of a capture)")
+    ap.add_argument("--profile-case", choices=["small", "ace", "multipole", "fft", "kpoints", "fp64"], default=None,
                     help="small: one apply of a small case of the same kernels (96^3, 8 orbitals); ace: three "
                          "ACE operator applies at 96^3 with 64 + 64 vectors; multipole: two applies of the "
                          "headline system with boundary values to order 4; fft: the first 64 pairs of the "
@@ -83,6 +85,16 @@ def run_profile_case(which="small"):
         torch.cuda.synchronize()
         print(json.dumps({"profile_case": "kpoints", "maxabs": out.abs().max().item(), "status": plan.status()}),
               flush=True)
+        return
+    if which == "fp64":
+        # the float64 path (the speed-up denominator) on the small case below
+        case = workloads.System(n=(96, 96, 96), h=(0.25,) * 3, bc=(workloads.DIRICHLET,) * 3,
+                                kernel=workloads.UNSCREENED, n_orb=8, n_centres=4, seed=5, name="profile-small")
+        psi = torch.from_numpy(np.ascontiguousarray(workloads.make_orbitals(case).T)).cuda()
+        plan = kx.Plan.for_system(case, precision=kx.KX_FP64)
+        vx, ex = kx.kx_vx_apply(plan, psi)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "fp64", "e_x": ex.item(), "status": plan.status()}), flush=True)
         return
     if which == "multipole":
         plan = kx.Plan.for_system(SYS, precision=kx.KX_F16X3)
@@ -745,9 +757,10 @@ def main():
     stream = torch.cuda.current_stream()
     # launch shapes chosen by the library's tuner for this grid and orbital count
     t0 = time.perf_counter()
-    kx.kx_autotune(plan, n_orb, 6000)
+    if not args.no_tune:
+        kx.kx_autotune(plan, n_orb, 6000)
     tune_s = time.perf_counter() - t0
-    tuning = dict(plan.tuning(), tune_s=tune_s)
+    tuning = dict(plan.tuning(), tune_s=tune_s, tuned=not args.no_tune)
 
     for _ in range(max(3, args.warmup)):
         kx.kx_vx_apply(plan, psi, out=vx, e_x=ex)

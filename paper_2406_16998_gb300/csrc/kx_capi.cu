@@ -517,7 +517,8 @@ int kx_vx_apply_host(kx_plan *plan, int n_orb, const double *psi, const double *
     // starts on the first pieces while the later ones are still copying (its
     // pair order needs the first orbitals first).  Float64 plans and plans with
     // multipole boundary values take the orbitals in one copy first.
-    const bool by_pieces = plan->precision != KX_FP64 && plan->mp_lmax < 0;
+    const char *pe = std::getenv("KX_HOST_PIECES");  // 0: one copy first (comparison runs)
+    const bool by_pieces = plan->precision != KX_FP64 && plan->mp_lmax < 0 && !(pe && std::atoi(pe) == 0);
     if (by_pieces) {
         if (!plan->h2d_stream) KX_CUDA_TRY(cudaStreamCreateWithFlags(&plan->h2d_stream, cudaStreamNonBlocking));
         const int nb = (n_orb + kOrbBlock - 1) / kOrbBlock;

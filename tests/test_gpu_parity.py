@@ -1182,15 +1182,16 @@ def test_c5_central_differences(kx, c5):
     (orbital, grid point) entries of the 80^3 / 256-orbital system, against the
     float64 gradient and the split-precision autograd gradient.  Only the pair
     solves that involve the perturbed orbital change E_x, so the orbital is
-    moved to the front of the set and E_x is taken over the first block row of
-    the pair list (kx_vx_apply_pairs over pairs [0, 1018): orbitals 0..3 with
-    every orbital), which holds all of them; the other pairs cancel in the
-    difference.  About 32 float64 solves of 1018 pairs (~20 s of GPU time)."""
+    moved to the front of the set and E_x is taken over the block pairs of
+    orbital block 0 with every block (kx_vx_apply_block_pairs: orbitals 0..3
+    with every orbital, 1018 pairs), which hold all of them; the other pairs
+    cancel in the difference.  About 32 float64 solves of 1018 pairs (~20 s of
+    GPU time)."""
     from paper_2406_16998_gb300 import shard
     sysd, psi, plan64 = c5["sysd"], c5["psi"], c5["plan64"]
     n_orb, N = psi.shape
-    row0 = sum(1 for i, _ in shard.pair_list(n_orb) if i < shard.ORB_BLOCK)
-    assert shard.pair_list(n_orb)[row0 - 1][0] < shard.ORB_BLOCK <= shard.pair_list(n_orb)[row0][0]
+    row0 = [(0, J) for J in range(shard.n_blocks(n_orb))]
+    assert len(shard.pairs_of_block_pairs(n_orb, row0)) == 1018
     rng = np.random.default_rng(5)
     step = 1e-4
     gmax64 = c5["g64"].abs().max().item()
@@ -1205,7 +1206,7 @@ def test_c5_central_differences(kx, c5):
         e = []
         for d in (step, -step):
             p[0, r] = v0 + d
-            kx.kx_vx_apply_pairs(plan64, p, 0, row0, out=out, e_x=ep)
+            kx.kx_vx_apply_block_pairs(plan64, p, row0, out=out, e_x=ep)
             e.append(ep.item())
         fd = (e[0] - e[1]) / (2 * step)
         assert abs(fd - c5["g64"][k, r].item()) < 1e-6 * gmax64
@@ -1278,3 +1279,28 @@ def test_c4_batch_of_the_eight_systems_against_oracle(kx):
         ref, _ = oracle.vx_apply(op, psi_h.T, ordered=True, pairs=[(0, j) for j in range(sd.n_orb)])
         assert np.max(np.abs(vxh[0] - ref[:, 0])) < TOL[1]["vx"] * np.abs(ref[:, 0]).max(), sd.name
     batch.close()
+
+
+@pytest.mark.parametrize("n_orb", [1, 5, 9, 30])
+def test_host_path_pieces_and_ragged_blocks(kx, n_orb, monkeypatch):
+    """kx_vx_apply_host with the orbitals sent in pieces for sizes that leave a
+    ragged last orbital block, a single block (every group holds the last
+    block) and more pieces than the first two chunk cuts: Vx psi bit for bit
+    the device path's, E_x to the last bits, both against the oracle; with
+    occupations."""
+    monkeypatch.setenv("KX_CHUNK_PAIRS", "24")
+    n, h, bc = (16, 24, 32), (0.45, 0.4, 0.5), (D, D, P)
+    sysd = system(n, h, bc, S, n_orb, 500 + n_orb)
+    psi = workloads.make_orbitals(sysd)
+    occ = np.random.default_rng(n_orb).uniform(0.3, 1.0, n_orb)
+    op = oracle.Plan(n, h, bc, S)
+    vx_ref, ex_ref = oracle.vx_apply(op, psi, occ=occ)
+    plan = kx.Plan(n, h, bc, S, precision=1)
+    vx, ex = kx.kx_vx_apply(plan, dev(psi.T), occ=dev(occ))
+    vx_h, ex_h = kx.kx_vx_apply_host(plan, torch.from_numpy(np.ascontiguousarray(psi.T)).pin_memory(),
+                                     occ_host=torch.from_numpy(occ))
+    assert plan.status() == kx.KX_OK
+    assert np.array_equal(vx_h.numpy(), vx.cpu().numpy())
+    assert abs(ex_h - ex.item()) <= 1e-13 * abs(ex.item())
+    assert relmax(vx_h.numpy().T, vx_ref) < TOL[1]["vx"]
+    assert abs(ex_h - ex_ref) < TOL[1]["ex"] * abs(ex_ref)

@@ -1356,133 +1356,6 @@ __global__ void __launch_bounds__(kAccThreads) acc_kernel(const float *__restric
     }
 }
 
-// The same accumulation with orbitals kept resident across groups: up to
-// kGroupSlots orbitals sit in shared-memory positions with their psi and their
-// running accumulator; a group that shares orbitals with the previous one
-// (consecutive groups of the pair list share their column block J) reuses
-// them, so each accumulator is read and written once per run of groups that
-// holds it instead of once per group.  Per group the contributions are summed
-// from zero and then added to the running accumulator, exactly as acc_kernel
-// adds them to the value it reads back, so both give the same bits.  Thread 0
-// plans each group's positions: evictions first (written back), then loads.
-__global__ void __launch_bounds__(kAccThreads) acc_res_kernel(const float *__restrict__ phi,
-                                                             const Group *__restrict__ groups, int g0, int g1,
-                                                             int item0, const int2 *__restrict__ item_slot,
-                                                             const float *__restrict__ psi32,
-                                                             const double *__restrict__ occ, float *__restrict__ acc,
-                                                             long long N) {
-    // dynamic shared memory (48 KB): psi of the resident orbital at each
-    // position, its running accumulator, and this group's contributions
-    extern __shared__ float4 acc_dyn[];
-    float4 (*ps)[kAccThreads] = reinterpret_cast<float4 (*)[kAccThreads]>(acc_dyn);
-    float4 (*ra)[kAccThreads] = reinterpret_cast<float4 (*)[kAccThreads]>(acc_dyn + kGroupSlots * kAccThreads);
-    float4 (*as)[kAccThreads] = reinterpret_cast<float4 (*)[kAccThreads]>(acc_dyn + 2 * kGroupSlots * kAccThreads);
-    __shared__ Group G;
-    __shared__ int res[kGroupSlots];        // orbital at each position (-1: free)
-    __shared__ int pos[kGroupSlots];        // position of each slot of the current group
-    __shared__ int evict[kGroupSlots];      // positions to write back before this group (orbital, or -1)
-    __shared__ int load[kGroupSlots];       // positions to fill for this group (orbital, or -1)
-    __shared__ float gs[kGroupSlots];       // occupation of each slot
-    __shared__ int2 sl_s[kGroupItems];
-    const int tid = threadIdx.x;
-    const long long N4 = N >> 2;
-    const long long x4 = (long long)blockIdx.x * kAccThreads + tid;
-    const bool valid = x4 < N4;
-    const float4 *phi4 = reinterpret_cast<const float4 *>(phi);
-    const float4 *psi4 = reinterpret_cast<const float4 *>(psi32);
-    float4 *acc4 = reinterpret_cast<float4 *>(acc);
-    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (tid < kGroupSlots) res[tid] = -1;
-    for (int g = g0; g <= g1; ++g) {
-        __syncthreads();
-        if (tid == 0) {
-            // g == g1: a final pass that only writes back everything resident
-            int need[kGroupSlots];
-            int ns = 0;
-            if (g < g1) {
-                G = groups[g];
-                ns = G.n_slots;
-            }
-            for (int s = 0; s < ns; ++s) need[s] = G.orb[s];
-            bool keep[kGroupSlots];
-            for (int q = 0; q < kGroupSlots; ++q) {
-                keep[q] = false;
-                for (int s = 0; s < ns; ++s) keep[q] = keep[q] || (res[q] >= 0 && res[q] == need[s]);
-                evict[q] = (res[q] >= 0 && !keep[q]) ? res[q] : -1;
-                load[q] = -1;
-                if (!keep[q]) res[q] = -1;
-            }
-            for (int s = 0; s < ns; ++s) {
-                int at = -1;
-                for (int q = 0; q < kGroupSlots; ++q)
-                    if (res[q] == need[s]) at = q;
-                if (at < 0) {
-                    for (int q = 0; q < kGroupSlots && at < 0; ++q)
-                        if (res[q] < 0) at = q;
-                    res[at] = need[s];
-                    load[at] = need[s];
-                }
-                pos[s] = at;
-            }
-        }
-        __syncthreads();
-        // write back evicted accumulators, fill new positions with psi and the accumulator
-#pragma unroll
-        for (int q = 0; q < kGroupSlots; ++q) {
-            if (evict[q] >= 0 && valid) acc4[(long long)evict[q] * N4 + x4] = ra[q][tid];
-            if (load[q] >= 0) {
-                const long long off = (long long)load[q] * N4 + x4;
-                ps[q][tid] = valid ? __ldg(psi4 + off) : z;
-                ra[q][tid] = valid ? acc4[off] : z;
-            }
-        }
-        if (g == g1) break;
-        const int ns = G.n_slots, ni = G.n_items, fi = G.first_item;
-        if (tid < ns) gs[tid] = occ ? (float)occ[G.orb[tid]] : 1.f;
-        if (tid < ni) sl_s[tid] = item_slot[fi + tid];
-        float4 f[kGroupItems];
-#pragma unroll
-        for (int k = 0; k < kGroupItems; ++k)
-            f[k] = (valid && k < ni) ? __ldg(phi4 + (long long)(fi + k - item0) * N4 + x4) : z;
-#pragma unroll
-        for (int q = 0; q < kGroupSlots; ++q) as[q][tid] = z;
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < kGroupItems; ++k) {
-            if (k >= ni) break;
-            const int2 sl = sl_s[k];
-            const int pi_ = pos[sl.x], pj_ = pos[sl.y];
-            const float4 pj = ps[pj_][tid];
-            const float gj = gs[sl.y];
-            float4 ai = as[pi_][tid];
-            ai.x = fmaf(gj * pj.x, f[k].x, ai.x);
-            ai.y = fmaf(gj * pj.y, f[k].y, ai.y);
-            ai.z = fmaf(gj * pj.z, f[k].z, ai.z);
-            ai.w = fmaf(gj * pj.w, f[k].w, ai.w);
-            as[pi_][tid] = ai;
-            if (sl.x != sl.y) {
-                const float4 pi = ps[pi_][tid];
-                const float gi = gs[sl.x];
-                float4 aj = as[pj_][tid];
-                aj.x = fmaf(gi * pi.x, f[k].x, aj.x);
-                aj.y = fmaf(gi * pi.y, f[k].y, aj.y);
-                aj.z = fmaf(gi * pi.z, f[k].z, aj.z);
-                aj.w = fmaf(gi * pi.w, f[k].w, aj.w);
-                as[pj_][tid] = aj;
-            }
-        }
-        // the group's sums join the running accumulators
-#pragma unroll
-        for (int s = 0; s < kGroupSlots; ++s) {
-            if (s < ns) {
-                const int q = pos[s];
-                const float4 d = as[q][tid], o = ra[q][tid];
-                ra[q][tid] = make_float4(o.x + d.x, o.y + d.y, o.z + d.z, o.w + d.w);
-            }
-        }
-    }
-}
-
 // psi (fp64) -> psi32 and per-vector max |value|.
 __global__ void prep_kernel(const double *__restrict__ src, float *__restrict__ dst, float *__restrict__ vmax,
                             int n_vec, long long N) {
@@ -1533,22 +1406,6 @@ __global__ void selftest_wait_kernel(long long max_cycles, int *status) {
     }
     __syncthreads();
     if (threadIdx.x == 0 && !ptx::mbar_wait_bounded(&bar, 0, max_cycles)) atomicExch(status, KX_ERR_TIMEOUT);
-}
-
-// KX_ACC_RESIDENT=0 selects the accumulation kernel that reloads every
-// group's orbitals and accumulators (comparison runs; both give the same bits).
-constexpr int kAccResBytes = 3 * kGroupSlots * kAccThreads * 16;
-bool acc_resident() {
-    const char *e = std::getenv("KX_ACC_RESIDENT");
-    if (e && std::atoi(e) == 0) return false;
-    static bool attr = false;  // 48 KB of dynamic shared memory needs the opt-in
-    if (!attr) {
-        if (cudaFuncSetAttribute(acc_res_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kAccResBytes) !=
-            cudaSuccess)
-            return false;
-        attr = true;
-    }
-    return true;
 }
 
 size_t stage_bytes_of(int np) { return 2 * a_half_bytes(np); }
@@ -1911,14 +1768,9 @@ int tc_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, double *v
         if (!energy_only) {
             const unsigned blocks = (unsigned)((N / 4 + kAccThreads - 1) / kAccThreads);
             if ((rc = prof_begin(p, PK_ACC, s))) return rc;
-            if (acc_resident())
-                acc_res_kernel<<<blocks, kAccThreads, kAccResBytes, s>>>(
-                    L.T0, reinterpret_cast<const Group *>(p->d_groups), g0, g1, (int)c0,
-                    reinterpret_cast<const int2 *>(p->d_item_slot), L.psi32, occ, L.acc, N);
-            else
-                acc_kernel<<<blocks, kAccThreads, 0, s>>>(L.T0, reinterpret_cast<const Group *>(p->d_groups), g0, g1,
-                                                         (int)c0, reinterpret_cast<const int2 *>(p->d_item_slot),
-                                                         L.psi32, occ, L.acc, N);
+            acc_kernel<<<blocks, kAccThreads, 0, s>>>(L.T0, reinterpret_cast<const Group *>(p->d_groups), g0, g1,
+                                                     (int)c0, reinterpret_cast<const int2 *>(p->d_item_slot),
+                                                     L.psi32, occ, L.acc, N);
             KX_LAUNCH_CHECK("acc_kernel launch");
             if ((rc = prof_end(p, s))) return rc;
         }

@@ -1014,6 +1014,333 @@ __global__ void __launch_bounds__(kTwThreads, 1) bloch_tc_ws_kernel(
     }
 }
 
+// ---- tensor-core products of strided pencils (axes 2 and 3) with per-item scales
+//
+// Same operands and arithmetic as bloch_tc_kernel (A = [A_r | A_i], the split B,
+// three products into Da and Db), but A is written straight from registers:
+// along axes 2 and 3 the 8 pencils of a group are one contiguous 64-byte run for
+// each k, which a producer thread loads, scales by the power of two of its
+// item's maximum, splits and stores as the real (kk = k) and imaginary
+// (kk = n + k) core-matrix rows.  Item maxima come from the previous product's
+// epilogue (each epilogue records the largest component it writes, per item) or,
+// for the first of these products, from the bound sqrt(n1) max|psi_m| max|phi_v|
+// on the mode-1 output (the Bloch bases are unitary).  Warp roles follow the
+// Gamma-point pass kernels: 8 epilogue warps (TMEM lane quadrant w % 4, complex
+// columns [w / 4 n / 2, + n / 2)), 8 producer warps in two groups of four that
+// take alternate tiles (group g fills A stage g), one MMA warp, two TMEM slots.
+// A's core matrices sit 144 bytes apart along the pencils, so that the 16-byte
+// rows the producers write for one k land on distinct bank groups:
+//   A element (m, kk) at (m/8) 144 + (kk/8) 2304 + (kk%8) 16 + (m%8) 2 bytes.
+constexpr int kBpEpiWarps = 8, kBpProdWarps = 8, kBpGroupThreads = 128;
+constexpr int kBpMmaWarp = kBpEpiWarps + kBpProdWarps;
+constexpr int kBpThreads = 32 * (kBpMmaWarp + 1);
+constexpr int kBpCore = 144;
+constexpr int kBpU = 4;  // producer tasks (64 bytes each) in flight per thread
+__host__ __device__ inline size_t bp_a_bytes(int n) { return (size_t)(n / 4) * 16 * kBpCore; }  // one of hi / lo
+__host__ __device__ inline size_t bp_smem_bytes(int n) { return 1024 + 2 * tc_b_bytes(n) + 4 * bp_a_bytes(n); }
+
+struct BpArgs {
+    const float2 *in;
+    float2 *out;
+    int n, inner;
+    long long n_cols, ppi;  // pencils, pencils per item (N / n)
+    const __half *Bs;
+    const float *f;
+    const float *in_max;                 // per item; nullptr: the bound below
+    const float *pmax, *fmax;            // bound of item r: mul pmax[m] fmax[v], r0 + r = v n_orb + m
+    float bound_mul;
+    long long r0;
+    int n_orb;
+    float *out_max;                      // per item, zeroed by the caller (nullable)
+    EnergyArgs ea;
+    int *status;
+    long long timeout_cycles;
+};
+
+// Split exponent of an item: e with max 2^e < 2^14, capped at 100 (as the
+// per-tile scale of bloch_tc_kernel) so that it and its inverse stay finite.
+__device__ __forceinline__ int bp_item_exp(const BpArgs &a, long long item) {
+    float mx;
+    if (a.in_max) {
+        mx = a.in_max[item];
+    } else {
+        const long long r = a.r0 + item;
+        const long long v = r / a.n_orb, m = r - v * a.n_orb;
+        mx = a.bound_mul * a.pmax[m] * a.fmax[v];
+    }
+    int ex = 0;
+    if (mx > 0.f && isfinite(mx)) frexpf(mx, &ex);
+    return min(14 - ex, 100);
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(kBpThreads, 1) bloch_pass_kernel(const BpArgs a) {
+    extern __shared__ uint8_t bp_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(bp_raw) + 1023) & ~uintptr_t(1023));
+    const int n = a.n, n2 = 2 * n;
+    uint8_t *Bh = smem, *Bl = Bh + tc_b_bytes(n);
+    uint8_t *stage0 = Bl + tc_b_bytes(n);  // stage s: hi at stage0 + 2 s ab, lo ab further
+    const size_t ab = bp_a_bytes(n);
+    __shared__ uint64_t full[2], empty[2], tfull[2], tempty[2], drain;
+    __shared__ uint32_t tslot;
+    __shared__ volatile int s_abort;
+    __shared__ double s_red[kBpEpiWarps];
+    __shared__ const float2 *s_p0[2][16];
+    __shared__ float s_sc[2][16];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == kBpMmaWarp) {
+        ptx::tmem_alloc(&tslot, 512);
+        ptx::tmem_relinquish();
+    }
+    if (tid == 0) {
+        for (int s = 0; s < 2; ++s) {
+            ptx::mbar_init(&full[s], kBpGroupThreads);
+            ptx::mbar_init(&empty[s], 1);
+            ptx::mbar_init(&tfull[s], 1);
+            ptx::mbar_init(&tempty[s], 32 * kBpEpiWarps);
+        }
+        ptx::mbar_init(&drain, 1);
+        ptx::fence_mbar_init();
+        s_abort = 0;
+    }
+    {  // B hi and lo, once
+        const uint4 *src = reinterpret_cast<const uint4 *>(a.Bs);
+        uint4 *dst = reinterpret_cast<uint4 *>(Bh);
+        const int n16 = (int)(2 * tc_b_bytes(n) / 16);
+        for (int e = tid; e < n16; e += kBpThreads) dst[e] = __ldg(src + e);
+    }
+    ptx::fence_proxy_async_smem();
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem = tslot;
+    const long long n_tiles = (a.n_cols + 127) / 128;
+    const int n_my = (int)((n_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x);
+    auto wait = [&](uint64_t *bar, uint32_t parity) {
+        const long long t0 = clock64();
+        while (!ptx::mbar_try_wait(bar, parity)) {
+            if (s_abort) return false;
+            if (clock64() - t0 > a.timeout_cycles) {
+                s_abort = 1;
+                atomicExch(a.status, KX_ERR_TIMEOUT);
+                return false;
+            }
+        }
+        return true;
+    };
+
+    if (warp == kBpMmaWarp) {
+        // ---------------------------------------------------------------- MMA issue
+        if (lane == 0) {
+            const uint32_t idesc = ptx::idesc_f16(128, n2, 1, 1);
+            const uint32_t bh0 = ptx::smem_u32(Bh), bl0 = ptx::smem_u32(Bl);
+            const uint32_t gb = 32u * (uint32_t)n;  // B K-group stride
+            bool ok = true;
+            for (int it = 0; it < n_my && ok; ++it) {
+                const int s = it & 1;  // A stage and TMEM slot
+                ok = wait(&full[s], (uint32_t)((it >> 1) & 1));
+                if (ok && it >= 2) ok = wait(&tempty[s], (uint32_t)(((it >> 1) - 1) & 1));
+                if (!ok) break;
+                ptx::tc_fence_after();
+                const uint32_t ah0 = ptx::smem_u32(stage0 + 2 * s * ab), al0 = ah0 + (uint32_t)ab;
+                const uint32_t da = tmem + 256u * (uint32_t)s, db = da + (uint32_t)n2;
+                for (int ks = 0; ks < n2 / 16; ++ks) {
+                    const uint32_t ao = (uint32_t)(2 * 16 * kBpCore * ks);
+                    const uint64_t ah = ptx::sdesc(ah0 + ao, 16 * kBpCore, kBpCore),
+                                   al = ptx::sdesc(al0 + ao, 16 * kBpCore, kBpCore);
+                    const uint64_t bh = ptx::sdesc(bh0 + 2u * gb * ks, gb, 128),
+                                   bl = ptx::sdesc(bl0 + 2u * gb * ks, gb, 128);
+                    ptx::mma_f16(da, ah, bl, idesc, ks > 0 ? 1u : 0u);
+                    ptx::mma_f16(da, al, bh, idesc, 1u);
+                    ptx::mma_f16(db, ah, bh, idesc, ks > 0 ? 1u : 0u);
+                }
+                ptx::mma_commit(&empty[s]);
+                ptx::mma_commit(&tfull[s]);
+            }
+            if (!ok) {
+                // a wait gave up: the products already issued finish before TMEM is released
+                ptx::mma_commit(&drain);
+                ptx::mbar_wait_bounded(&drain, 0, a.timeout_cycles);
+            }
+        }
+        __syncwarp();
+    } else if (warp >= kBpEpiWarps) {
+        // ---------------------------------------------------------------- producers
+        const int ptid = tid - 32 * kBpEpiWarps;
+        const int grp = ptid / kBpGroupThreads, gtid = ptid % kBpGroupThreads;
+        const int bar_id = 2 + grp;
+        const int ntask = 16 * n;  // 16 pencil groups x n values of k
+        for (int it = grp; it < n_my; it += 2) {
+            bool ok = it < 2 || wait(&empty[grp], (uint32_t)(((it >> 1) - 1) & 1));
+            ok = ptx::named_bar_and(bar_id, kBpGroupThreads, ok && !s_abort);
+            if (!ok) break;
+            const long long q0 = (blockIdx.x + (long long)it * gridDim.x) * 128;
+            if (gtid < 16) {  // group gtid: its first pencil's address and its item's scale
+                const long long q = q0 + 8 * gtid;
+                if (q < a.n_cols) {
+                    const long long o = q / a.inner;
+                    s_p0[grp][gtid] = a.in + o * n * a.inner + (q - o * a.inner);
+                    s_sc[grp][gtid] = ldexpf(1.f, bp_item_exp(a, q / a.ppi));
+                } else {
+                    s_p0[grp][gtid] = nullptr;
+                    s_sc[grp][gtid] = 0.f;
+                }
+            }
+            ptx::named_bar(bar_id, kBpGroupThreads);
+            if (it + 2 < n_my) {  // the group's next tile into L2 (one 128-byte line per 16 pencils and k)
+                const long long qn = (blockIdx.x + (long long)(it + 2) * gridDim.x) * 128;
+                for (int l = gtid; l < 8 * n; l += kBpGroupThreads) {
+                    const long long q = qn + 16 * (l & 7);
+                    if (q < a.n_cols) {
+                        const long long o = q / a.inner;
+                        ptx::prefetch_l2(a.in + o * n * a.inner + (q - o * a.inner) + (long long)(l >> 3) * a.inner);
+                    }
+                }
+            }
+            uint8_t *Ahi = stage0 + 2 * grp * ab, *Alo = Ahi + ab;
+            for (int t0 = gtid; t0 < ntask; t0 += kBpGroupThreads * kBpU) {
+                float4 v[kBpU][4];
+#pragma unroll
+                for (int r = 0; r < kBpU; ++r) {  // every load of the batch first
+                    const int t = t0 + r * kBpGroupThreads;
+                    const float2 *p = t < ntask ? s_p0[grp][t & 15] : nullptr;
+                    if (p != nullptr) {
+                        const float4 *src = reinterpret_cast<const float4 *>(p + (long long)(t >> 4) * a.inner);
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) v[r][c] = __ldg(src + c);
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) v[r][c] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < kBpU; ++r) {
+                    const int t = t0 + r * kBpGroupThreads;
+                    if (t >= ntask) continue;
+                    const int g = t & 15, k = t >> 4;
+                    const float sc = s_sc[grp][g];
+                    float wr[8], wi[8];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        wr[2 * c] = v[r][c].x * sc;
+                        wi[2 * c] = v[r][c].y * sc;
+                        wr[2 * c + 1] = v[r][c].z * sc;
+                        wi[2 * c + 1] = v[r][c].w * sc;
+                    }
+                    const int ki = n + k;
+                    tc_split_store(Ahi, Alo, g * kBpCore + (k >> 3) * (16 * kBpCore) + (k & 7) * 16, wr);
+                    tc_split_store(Ahi, Alo, g * kBpCore + (ki >> 3) * (16 * kBpCore) + (ki & 7) * 16, wi);
+                }
+            }
+            ptx::fence_proxy_async_smem();
+            ptx::mbar_arrive(&full[grp]);
+        }
+    } else {
+        // ---------------------------------------------------------------- epilogue
+        const int qd = warp & 3, hh = warp >> 2;
+        const int m = 32 * qd + lane;
+        const int half = n >> 1;
+        double e_acc = 0.0;
+        for (int it = 0; it < n_my; ++it) {
+            const int b = it & 1;
+            const long long q0 = (blockIdx.x + (long long)it * gridDim.x) * 128;
+            const int nq = (int)min(128LL, a.n_cols - q0);
+            const bool valid = m < nq;
+            const long long q = q0 + min(m, nq - 1);
+            const long long item = q / a.ppi;
+            const long long o = q / a.inner;
+            const long long i_in = q - o * a.inner;
+            const float unscale = ldexpf(1.f, -bp_item_exp(a, item) - kVScaleExp);
+            float fpre[kTcMaxN / 2];
+            if constexpr (EPI != 0) {
+#pragma unroll
+                for (int c = 0; c < kTcMaxN / 2; ++c)
+                    fpre[c] = c < half ? a.f[(long long)(hh * half + c) * a.inner + i_in] : 0.f;
+            }
+            double wj = 0.0;
+            if constexpr (EPI == 2) {
+                const long long rr = a.ea.r0 + item;
+                const long long vv = rr / a.ea.n_orb, mm = rr - vv * a.ea.n_orb;
+                wj = valid ? a.ea.cb * (a.ea.occ_q ? a.ea.occ_q[mm] : 1.0) * (a.ea.occ_k ? a.ea.occ_k[vv] : 1.0)
+                           : 0.0;
+            }
+            if (!__all_sync(0xffffffffu, wait(&tfull[b], (uint32_t)((it >> 1) & 1)))) break;
+            ptx::tc_fence_after();
+            const uint32_t tl = tmem + 256u * (uint32_t)b + ((uint32_t)(32 * qd) << 16);
+            float2 *dst = a.out + o * n * a.inner + i_in;
+            float my_max = 0.f, ej = 0.f;
+            // 8 complex columns at a time (real and imaginary parts, Da and Db)
+#pragma unroll
+            for (int cc = 0; cc < kTcMaxN / 16; ++cc) {
+                if (8 * cc >= half) break;
+                const int c0 = hh * half + 8 * cc;
+                float ra[8], rb[8], ia[8], ib[8];
+                ptx::tmem_ld8x4(tl + (uint32_t)c0, tl + (uint32_t)(n2 + c0), tl + (uint32_t)(n + c0),
+                                tl + (uint32_t)(n2 + n + c0), ra, rb, ia, ib);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    float2 v = make_float2((ra[c] + rb[c]) * unscale, (ia[c] + ib[c]) * unscale);
+                    if constexpr (EPI == 1) {
+                        v.x *= fpre[8 * cc + c];
+                        v.y *= fpre[8 * cc + c];
+                    }
+                    if constexpr (EPI == 2) {
+                        ej = fmaf(fpre[8 * cc + c], v.x * v.x + v.y * v.y, ej);
+                    } else if (valid) {
+                        dst[(long long)(c0 + c) * a.inner] = v;
+                        my_max = fmaxf(my_max, fmaxf(fabsf(v.x), fabsf(v.y)));
+                    }
+                }
+            }
+            if constexpr (EPI == 2) {
+                e_acc += wj * (double)ej;
+            } else if (a.out_max != nullptr) {
+                // one atomic per warp when its 32 pencils belong to one item
+                const long long item0 = __shfl_sync(0xffffffffu, item, 0);
+                if (__all_sync(0xffffffffu, !valid || item == item0)) {
+                    float r = my_max;
+                    for (int off = 16; off > 0; off >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, off));
+                    if (lane == 0 && r > 0.f) atomicMax(reinterpret_cast<int *>(a.out_max + item0), __float_as_int(r));
+                } else if (valid && my_max > 0.f) {
+                    atomicMax(reinterpret_cast<int *>(a.out_max + item), __float_as_int(my_max));
+                }
+            }
+            ptx::tc_fence_before();
+            ptx::mbar_arrive(&tempty[b]);
+        }
+        if constexpr (EPI == 2) {
+            for (int off = 16; off > 0; off >>= 1) e_acc += __shfl_xor_sync(0xffffffffu, e_acc, off);
+            if (lane == 0) s_red[warp] = e_acc;
+        }
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    if constexpr (EPI == 2) {
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < kBpEpiWarps; ++w) t += s_red[w];
+            a.ea.partial[blockIdx.x] = t;
+        }
+    }
+    if (warp == kBpMmaWarp) {
+        ptx::tc_fence_after();
+        ptx::tmem_dealloc(tmem, 512);
+    }
+}
+
+// max (|re| + |im|) of each of the vectors x[v] (N values each) into vmax[v]
+// (zeroed before): an upper bound of the modulus, for the split scales above.
+__global__ void bloch_vmax_kernel(const float2 *__restrict__ x, long long N, float *__restrict__ vmax) {
+    const float2 *v = x + (long long)blockIdx.y * N;
+    float m = 0.f;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
+        const float2 a = v[e];
+        m = fmaxf(m, fabsf(a.x) + fabsf(a.y));
+    }
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(reinterpret_cast<int *>(vmax + blockIdx.y), __float_as_int(m));
+}
+
 struct BlochAxes {
     int n[3];
     double h[3];
@@ -1361,10 +1688,71 @@ int launch_tc(kx_plan *p, int axis, long long R, const float2 *in, float2 *out, 
     return prof_end(p, s);
 }
 
+// Products along axes 2 and 3 through bloch_pass_kernel: both axes on the
+// tensor cores with pencil groups of 8 contiguous values (n1 and n1 n2
+// multiples of 8), unless KX_BLOCH_PASS=0 (comparison runs).
+inline bool bp_axes(const kx_plan *p) {
+    if (const char *e = std::getenv("KX_BLOCH_PASS"))
+        if (std::atoi(e) == 0) return false;
+    return tc_axis(p, 1) && tc_axis(p, 2) && p->n[0] % 8 == 0;
+}
+
+template <int EPI>
+int launch_bp(kx_plan *p, int axis, long long R, const float2 *in, float2 *out, const __half *Bs, const float *f,
+              const float *in_max, const float *pmax, const float *fmax, long long r0, int n_orb, float *out_max,
+              cudaStream_t s, const EnergyArgs &ea = EnergyArgs()) {
+    const int n = p->n[axis];
+    const long long N = (long long)p->N;
+    if (R * N >= (1LL << 31)) return set_error(KX_ERR_ARG, "Bloch exchange: chunk too large for one launch");
+    BpArgs a;
+    a.in = in;
+    a.out = out;
+    a.n = n;
+    a.inner = axis == 1 ? p->n[0] : p->n[0] * p->n[1];
+    a.ppi = N / n;
+    a.n_cols = R * a.ppi;
+    a.Bs = Bs;
+    a.f = f;
+    a.in_max = in_max;
+    a.pmax = pmax;
+    a.fmax = fmax;
+    a.bound_mul = 1.001f * std::sqrt((float)p->n[0]);  // |mode-1 output| <= sqrt(n1) max|rho|
+    a.r0 = r0;
+    a.n_orb = n_orb;
+    a.out_max = out_max;
+    a.ea = ea;
+    a.status = p->d_status;
+    a.timeout_cycles = 2000000000LL;
+    const long long n_tiles = (a.n_cols + 127) / 128;
+    if (n_tiles == 0) return KX_OK;
+    if (out_max) KX_CUDA_TRY(cudaMemsetAsync(out_max, 0, sizeof(float) * R, s));
+    static bool attr = false;  // once per instantiation
+    if (!attr) {
+        KX_CUDA_TRY(cudaFuncSetAttribute(bloch_pass_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bp_smem_bytes(kTcMaxN)));
+        attr = true;
+    }
+    const int grid = (int)std::min<long long>(n_tiles, p->num_sms);
+    if (int rc = prof_begin(p, PK_BLOCH, s)) return rc;
+    bloch_pass_kernel<EPI><<<grid, kBpThreads, bp_smem_bytes(n), s>>>(a);
+    KX_LAUNCH_CHECK("bloch_pass_kernel launch");
+    return prof_end(p, s);
+}
+
+// Per-vector maxima of n_vec float32 vectors (vmax zeroed here first).
+inline int vector_maxima(kx_plan *p, const float2 *x, long long N, int n_vec, float *vmax, cudaStream_t s) {
+    KX_CUDA_TRY(cudaMemsetAsync(vmax, 0, sizeof(float) * n_vec, s));
+    const dim3 g((unsigned)std::min<long long>((N + 255) / 256, 64), (unsigned)n_vec);
+    bloch_vmax_kernel<<<g, 256, 0, s>>>(x, N, vmax);
+    KX_LAUNCH_CHECK("bloch_vmax_kernel launch");
+    return KX_OK;
+}
+
 // Device workspace of one call: bases, eigenvalues, f table, float32 copies of
-// the orbitals and vectors (float32 plans), chunk buffers A and B.
+// the orbitals and vectors and their maxima (float32 plans), chunk buffers A and
+// B and two per-item maximum arrays.
 struct BlochLayout {
-    size_t Mf[3], Mi[3], lam[3], Bf[3], Bi[3], f, P, F, A, B, partial, total;
+    size_t Mf[3], Mi[3], lam[3], Bf[3], Bi[3], f, P, F, Pmax, Fmax, mx0, mx1, A, B, partial, total;
     long long chunk;
 };
 
@@ -1395,6 +1783,10 @@ BlochLayout bloch_layout(const kx_plan *p, int n_orb, int n_vec, int n_kpt, size
     off += f32 ? al256(sizeof(T2) * N * n_orb) : 0;
     L.F = off;
     off += f32 ? al256(sizeof(T2) * N * n_vec) : 0;
+    L.Pmax = off;
+    off += f32 ? al256(sizeof(float) * n_orb) : 0;
+    L.Fmax = off;
+    off += f32 ? al256(sizeof(float) * n_vec) : 0;
     L.partial = off;
     off += al256(sizeof(double) * std::max(partial_doubles, 2 * (size_t)p->num_sms * std::max(1, n_kpt)));
     const long long pairs = (long long)n_orb * n_vec;
@@ -1404,6 +1796,10 @@ BlochLayout bloch_layout(const kx_plan *p, int n_orb, int n_vec, int n_kpt, size
         if (std::atoll(e) > 0) chunk = std::min(chunk, std::atoll(e));
     chunk = std::min(chunk, pairs);
     L.chunk = chunk;
+    L.mx0 = off;
+    off += f32 ? al256(sizeof(float) * chunk) : 0;
+    L.mx1 = off;
+    off += f32 ? al256(sizeof(float) * chunk) : 0;
     L.A = off;
     off += al256(sizeof(T2) * N * chunk);
     L.B = off;
@@ -1486,6 +1882,10 @@ int bloch_sweep(kx_plan *p, int n_kpt, const double *theta, const double *wk, in
         bloch_to_f32_kernel<<<blocks, 256, 0, s>>>(reinterpret_cast<const double2 *>(phi),
                                                    reinterpret_cast<float2 *>(Fw), N * n_vec);
         KX_LAUNCH_CHECK("bloch_to_f32_kernel launch");
+        if (bp_axes(p))
+            if (int rc = vector_maxima(p, reinterpret_cast<const float2 *>(Fw), N, n_vec,
+                                       reinterpret_cast<float *>(ws + L.Fmax), s))
+                return rc;
         if (int rc = prof_end(p, s)) return rc;
         F = Fw;
     } else {
@@ -1527,6 +1927,10 @@ int bloch_sweep(kx_plan *p, int n_kpt, const double *theta, const double *wk, in
             T2 *Pw = reinterpret_cast<T2 *>(ws + L.P);
             bloch_to_f32_kernel<<<blocks, 256, 0, s>>>(psi_q, reinterpret_cast<float2 *>(Pw), N * n_orb);
             KX_LAUNCH_CHECK("bloch_to_f32_kernel launch");
+            if (bp_axes(p))
+                if (int rc = vector_maxima(p, reinterpret_cast<const float2 *>(Pw), N, n_orb,
+                                           reinterpret_cast<float *>(ws + L.Pmax), s))
+                    return rc;
             Pq = Pw;
         } else {
             Pq = reinterpret_cast<const T2 *>(psi_q);
@@ -1544,18 +1948,35 @@ int bloch_sweep(kx_plan *p, int n_kpt, const double *theta, const double *wk, in
                 rc = tc_axis(p, 0) ? launch_tc<true, 0>(p, 0, R, nullptr, A, Bf(0), nullptr, Pq, F, n_orb, r0, s)
                                    : launch_form<T>(p, R, A, Mf[0], Pq, F, n_orb, r0, s);
                 if (rc) return rc;
-                rc = tc_axis(p, 1) ? launch_tc<false, 0>(p, 1, R, A, B, Bf(1), nullptr, nullptr, nullptr, n_orb, 0, s)
-                                   : launch_pipe<T, 0>(p, 1, R, A, B, Mf[1], nullptr, s);
-                if (rc) return rc;
-                rc = tc_axis(p, 2) ? launch_tc<false, 1>(p, 2, R, B, A, Bf(2), f, nullptr, nullptr, n_orb, 0, s)
-                                   : launch_pipe<T, 1>(p, 2, R, B, A, Mf[2], f, s);
-                if (rc) return rc;
-                rc = tc_axis(p, 2) ? launch_tc<false, 0>(p, 2, R, A, B, Bi(2), nullptr, nullptr, nullptr, n_orb, 0, s)
-                                   : launch_pipe<T, 0>(p, 2, R, A, B, Mi[2], nullptr, s);
-                if (rc) return rc;
-                rc = tc_axis(p, 1) ? launch_tc<false, 0>(p, 1, R, B, A, Bi(1), nullptr, nullptr, nullptr, n_orb, 0, s)
-                                   : launch_pipe<T, 0>(p, 1, R, B, A, Mi[1], nullptr, s);
-                if (rc) return rc;
+                if (bp_axes(p)) {
+                    // axes 2 and 3 with per-item scales: the bound from the orbital
+                    // maxima, then the maxima each product records
+                    float *mx0 = reinterpret_cast<float *>(ws + L.mx0), *mx1 = reinterpret_cast<float *>(ws + L.mx1);
+                    const float *pm = reinterpret_cast<const float *>(ws + L.Pmax);
+                    const float *fm = reinterpret_cast<const float *>(ws + L.Fmax);
+                    if ((rc = launch_bp<0>(p, 1, R, A, B, Bf(1), nullptr, nullptr, pm, fm, r0, n_orb, mx0, s))) return rc;
+                    if ((rc = launch_bp<1>(p, 2, R, B, A, Bf(2), f, mx0, nullptr, nullptr, 0, n_orb, mx1, s))) return rc;
+                    if ((rc = launch_bp<0>(p, 2, R, A, B, Bi(2), nullptr, mx1, nullptr, nullptr, 0, n_orb, mx0, s)))
+                        return rc;
+                    if ((rc = launch_bp<0>(p, 1, R, B, A, Bi(1), nullptr, mx0, nullptr, nullptr, 0, n_orb, nullptr, s)))
+                        return rc;
+                } else {
+                    rc = tc_axis(p, 1)
+                             ? launch_tc<false, 0>(p, 1, R, A, B, Bf(1), nullptr, nullptr, nullptr, n_orb, 0, s)
+                             : launch_pipe<T, 0>(p, 1, R, A, B, Mf[1], nullptr, s);
+                    if (rc) return rc;
+                    rc = tc_axis(p, 2) ? launch_tc<false, 1>(p, 2, R, B, A, Bf(2), f, nullptr, nullptr, n_orb, 0, s)
+                                       : launch_pipe<T, 1>(p, 2, R, B, A, Mf[2], f, s);
+                    if (rc) return rc;
+                    rc = tc_axis(p, 2)
+                             ? launch_tc<false, 0>(p, 2, R, A, B, Bi(2), nullptr, nullptr, nullptr, n_orb, 0, s)
+                             : launch_pipe<T, 0>(p, 2, R, A, B, Mi[2], nullptr, s);
+                    if (rc) return rc;
+                    rc = tc_axis(p, 1)
+                             ? launch_tc<false, 0>(p, 1, R, B, A, Bi(1), nullptr, nullptr, nullptr, n_orb, 0, s)
+                             : launch_pipe<T, 0>(p, 1, R, B, A, Mi[1], nullptr, s);
+                    if (rc) return rc;
+                }
                 rc = tc_axis(p, 0) ? launch_tc<false, 0>(p, 0, R, A, B, Bi(0), nullptr, nullptr, nullptr, n_orb, 0, s)
                                    : launch_pipe<T, 0>(p, 0, R, A, B, Mi[0], nullptr, s);
                 if (rc) return rc;
@@ -1684,6 +2105,10 @@ int bloch_energy_only(kx_plan *p, int n_kpt, const double *theta, const double *
             T2 *Fw = reinterpret_cast<T2 *>(ws + L.F);
             bloch_to_f32_kernel<<<blocks, 256, 0, s>>>(psi_k, reinterpret_cast<float2 *>(Fw), N * n_orb);
             KX_LAUNCH_CHECK("bloch_to_f32_kernel launch");
+            if (bp_axes(p))
+                if (int rc = vector_maxima(p, reinterpret_cast<const float2 *>(Fw), N, n_orb,
+                                           reinterpret_cast<float *>(ws + L.Fmax), s))
+                    return rc;
             F = Fw;
         } else {
             F = reinterpret_cast<const T2 *>(psi_k);
@@ -1716,6 +2141,10 @@ int bloch_energy_only(kx_plan *p, int n_kpt, const double *theta, const double *
                 T2 *Pw = reinterpret_cast<T2 *>(ws + L.P);
                 bloch_to_f32_kernel<<<blocks, 256, 0, s>>>(psi_q, reinterpret_cast<float2 *>(Pw), N * n_orb);
                 KX_LAUNCH_CHECK("bloch_to_f32_kernel launch");
+                if (bp_axes(p))
+                    if (int rc = vector_maxima(p, reinterpret_cast<const float2 *>(Pw), N, n_orb,
+                                               reinterpret_cast<float *>(ws + L.Pmax), s))
+                        return rc;
                 Pq = Pw;
             } else {
                 Pq = reinterpret_cast<const T2 *>(psi_q);
@@ -1736,14 +2165,25 @@ int bloch_energy_only(kx_plan *p, int n_kpt, const double *theta, const double *
                     rc = tc_axis(p, 0) ? launch_tc<true, 0>(p, 0, R, nullptr, A, Bf(0), nullptr, Pq, F, n_orb, r0, s)
                                        : launch_form<T>(p, R, A, Mf[0], Pq, F, n_orb, r0, s);
                     if (rc) return rc;
-                    rc = tc_axis(p, 1)
-                             ? launch_tc<false, 0>(p, 1, R, A, B, Bf(1), nullptr, nullptr, nullptr, n_orb, 0, s)
-                             : launch_pipe<T, 0>(p, 1, R, A, B, Mf[1], nullptr, s);
-                    if (rc) return rc;
-                    rc = tc_axis(p, 2)
-                             ? launch_tc<false, 2>(p, 2, R, B, nullptr, Bf(2), f, nullptr, nullptr, n_orb, 0, s, ea)
-                             : launch_pipe<T, 2>(p, 2, R, B, nullptr, Mf[2], f, s, ea);
-                    if (rc) return rc;
+                    if (bp_axes(p)) {
+                        float *mx0 = reinterpret_cast<float *>(ws + L.mx0);
+                        const float *pm = reinterpret_cast<const float *>(ws + L.Pmax);
+                        const float *fm = reinterpret_cast<const float *>(ws + L.Fmax);
+                        if ((rc = launch_bp<0>(p, 1, R, A, B, Bf(1), nullptr, nullptr, pm, fm, r0, n_orb, mx0, s)))
+                            return rc;
+                        if ((rc = launch_bp<2>(p, 2, R, B, nullptr, Bf(2), f, mx0, nullptr, nullptr, 0, n_orb, nullptr,
+                                               s, ea)))
+                            return rc;
+                    } else {
+                        rc = tc_axis(p, 1)
+                                 ? launch_tc<false, 0>(p, 1, R, A, B, Bf(1), nullptr, nullptr, nullptr, n_orb, 0, s)
+                                 : launch_pipe<T, 0>(p, 1, R, A, B, Mf[1], nullptr, s);
+                        if (rc) return rc;
+                        rc = tc_axis(p, 2)
+                                 ? launch_tc<false, 2>(p, 2, R, B, nullptr, Bf(2), f, nullptr, nullptr, n_orb, 0, s, ea)
+                                 : launch_pipe<T, 2>(p, 2, R, B, nullptr, Mf[2], f, s, ea);
+                        if (rc) return rc;
+                    }
                 } else {
                     if ((rc = launch_form<T>(p, R, A, Mf[0], Pq, F, n_orb, r0, s))) return rc;
                     if ((rc = launch_pipe<T, 0>(p, 1, R, A, B, Mf[1], nullptr, s))) return rc;

@@ -1057,17 +1057,17 @@ struct BpArgs {
     long long timeout_cycles;
 };
 
-// Split exponent of an item: e with max 2^e < 2^14, capped at 100 (as the
-// per-tile scale of bloch_tc_kernel) so that it and its inverse stay finite.
-__device__ __forceinline__ int bp_item_exp(const BpArgs &a, long long item) {
-    float mx;
-    if (a.in_max) {
-        mx = a.in_max[item];
-    } else {
-        const long long r = a.r0 + item;
-        const long long v = r / a.n_orb, m = r - v * a.n_orb;
-        mx = a.bound_mul * a.pmax[m] * a.fmax[v];
-    }
+// Maximum of an item's input, and its split exponent: e with max 2^e < 2^14,
+// capped at 100 (as the per-tile scale of bloch_tc_kernel) so that it and its
+// inverse stay finite.  Pencil counts are below 2^31 (checked at launch), so
+// the index arithmetic of this kernel uses 32-bit division.
+__device__ __forceinline__ float bp_item_max(const BpArgs &a, unsigned item) {
+    if (a.in_max) return a.in_max[item];
+    const long long r = a.r0 + item;
+    const long long v = r / a.n_orb, m = r - v * a.n_orb;
+    return a.bound_mul * a.pmax[m] * a.fmax[v];
+}
+__device__ __forceinline__ int bp_exp(float mx) {
     int ex = 0;
     if (mx > 0.f && isfinite(mx)) frexpf(mx, &ex);
     return min(14 - ex, 100);
@@ -1170,31 +1170,36 @@ __global__ void __launch_bounds__(kBpThreads, 1) bloch_pass_kernel(const BpArgs 
         const int grp = ptid / kBpGroupThreads, gtid = ptid % kBpGroupThreads;
         const int bar_id = 2 + grp;
         const int ntask = 16 * n;  // 16 pencil groups x n values of k
+        const unsigned inner = (unsigned)a.inner, ppi = (unsigned)a.ppi;
+        // first pencil of group g of local tile it (>= n_cols past the end) and its address
+        auto gq = [&](int it, int g) { return (unsigned)((blockIdx.x + (long long)it * gridDim.x) * 128 + 8 * g); };
+        auto addr = [&](unsigned q) {
+            const unsigned o = q / inner;
+            return a.in + (long long)o * n * inner + (q - o * inner);
+        };
+        // the descriptor of the group's first tile; later ones are written after
+        // each tile, their item maxima loaded at its start (published by the vote
+        // that opens the next iteration)
+        if (gtid < 16 && grp < n_my) {
+            const unsigned q = gq(grp, gtid);
+            const bool in = q < a.n_cols;
+            s_p0[grp][gtid] = in ? addr(q) : nullptr;
+            s_sc[grp][gtid] = in ? ldexpf(1.f, bp_exp(bp_item_max(a, q / ppi))) : 0.f;
+        }
         for (int it = grp; it < n_my; it += 2) {
             bool ok = it < 2 || wait(&empty[grp], (uint32_t)(((it >> 1) - 1) & 1));
             ok = ptx::named_bar_and(bar_id, kBpGroupThreads, ok && !s_abort);
             if (!ok) break;
-            const long long q0 = (blockIdx.x + (long long)it * gridDim.x) * 128;
-            if (gtid < 16) {  // group gtid: its first pencil's address and its item's scale
-                const long long q = q0 + 8 * gtid;
-                if (q < a.n_cols) {
-                    const long long o = q / a.inner;
-                    s_p0[grp][gtid] = a.in + o * n * a.inner + (q - o * a.inner);
-                    s_sc[grp][gtid] = ldexpf(1.f, bp_item_exp(a, q / a.ppi));
-                } else {
-                    s_p0[grp][gtid] = nullptr;
-                    s_sc[grp][gtid] = 0.f;
-                }
+            const bool more = it + 2 < n_my;
+            float nxt_mx = 0.f;
+            if (gtid < 16 && more) {
+                const unsigned q = gq(it + 2, gtid);
+                if (q < a.n_cols) nxt_mx = bp_item_max(a, q / ppi);
             }
-            ptx::named_bar(bar_id, kBpGroupThreads);
-            if (it + 2 < n_my) {  // the group's next tile into L2 (one 128-byte line per 16 pencils and k)
-                const long long qn = (blockIdx.x + (long long)(it + 2) * gridDim.x) * 128;
+            if (more) {  // the group's next tile into L2 (one 128-byte line per 16 pencils and k)
                 for (int l = gtid; l < 8 * n; l += kBpGroupThreads) {
-                    const long long q = qn + 16 * (l & 7);
-                    if (q < a.n_cols) {
-                        const long long o = q / a.inner;
-                        ptx::prefetch_l2(a.in + o * n * a.inner + (q - o * a.inner) + (long long)(l >> 3) * a.inner);
-                    }
+                    const unsigned q = gq(it + 2, 2 * (l & 7));
+                    if (q < a.n_cols) ptx::prefetch_l2(addr(q) + (long long)(l >> 3) * inner);
                 }
             }
             uint8_t *Ahi = stage0 + 2 * grp * ab, *Alo = Ahi + ab;
@@ -1234,6 +1239,13 @@ __global__ void __launch_bounds__(kBpThreads, 1) bloch_pass_kernel(const BpArgs 
             }
             ptx::fence_proxy_async_smem();
             ptx::mbar_arrive(&full[grp]);
+            ptx::named_bar(bar_id, kBpGroupThreads);  // every thread is done with this descriptor
+            if (gtid < 16 && more) {
+                const unsigned q = gq(it + 2, gtid);
+                const bool in = q < a.n_cols;
+                s_p0[grp][gtid] = in ? addr(q) : nullptr;
+                s_sc[grp][gtid] = in ? ldexpf(1.f, bp_exp(nxt_mx)) : 0.f;
+            }
         }
     } else {
         // ---------------------------------------------------------------- epilogue
@@ -1250,7 +1262,7 @@ __global__ void __launch_bounds__(kBpThreads, 1) bloch_pass_kernel(const BpArgs 
             const long long item = q / a.ppi;
             const long long o = q / a.inner;
             const long long i_in = q - o * a.inner;
-            const float unscale = ldexpf(1.f, -bp_item_exp(a, item) - kVScaleExp);
+            const float unscale = ldexpf(1.f, -bp_exp(bp_item_max(a, (unsigned)item)) - kVScaleExp);
             float fpre[kTcMaxN / 2];
             if constexpr (EPI != 0) {
 #pragma unroll
@@ -1322,6 +1334,245 @@ __global__ void __launch_bounds__(kBpThreads, 1) bloch_pass_kernel(const BpArgs 
             a.ea.partial[blockIdx.x] = t;
         }
     }
+    if (warp == kBpMmaWarp) {
+        ptx::tc_fence_after();
+        ptx::tmem_dealloc(tmem, 512);
+    }
+}
+
+// ---- the same for the contiguous axis (axis 1, n = 64), forward product with
+// the pair density formed on the way (FORM) or inverse product
+//
+// The 128 pencils of a tile are contiguous in memory and belong to one item
+// (pencils per item a multiple of 128), so a tile is one 64 KB run (two, P and
+// F, when FORM) with one split scale.  A is K-major: a producer task loads 8
+// complex values of one pencil (64 contiguous bytes) and writes its real and
+// imaginary 16-byte core-matrix rows; core matrices sit 144 bytes apart along
+// K, so that the 8 tasks of a pencil land on distinct bank groups:
+//   A element (m, kk) at (m/8) (2n/8) 144 + (kk/8) 144 + (m%8) 16 + (kk%8) 2 bytes.
+// The products compute the transpose D^T = B^T A^T (as bloch_tc_kernel does for
+// contiguous pencils), so that a TMEM lane holds one output component across
+// pencils and consecutive lanes store consecutive addresses.  The output feeds
+// either the next product (whose scale comes from the bound sqrt(n1) max|rho|)
+// or the accumulation, so no maximum is recorded.
+template <bool FORM>
+__global__ void __launch_bounds__(kBpThreads, 1) bloch_pass0_kernel(const BpArgs a, const float2 *__restrict__ P,
+                                                                    const float2 *__restrict__ F, long long N) {
+    extern __shared__ uint8_t bp_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(bp_raw) + 1023) & ~uintptr_t(1023));
+    const int n = a.n, n2 = 2 * n, nkc = n / 8;
+    const int sbo = (n2 / 8) * kBpCore;  // A: stride of 8-pencil groups
+    uint8_t *Bh = smem, *Bl = Bh + tc_b_bytes(n);
+    uint8_t *stage0 = Bl + tc_b_bytes(n);
+    const size_t ab = bp_a_bytes(n);
+    __shared__ uint64_t full[2], empty[2], tfull[2], tempty[2], drain;
+    __shared__ uint32_t tslot;
+    __shared__ volatile int s_abort;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == kBpMmaWarp) {
+        ptx::tmem_alloc(&tslot, 512);
+        ptx::tmem_relinquish();
+    }
+    if (tid == 0) {
+        for (int s = 0; s < 2; ++s) {
+            ptx::mbar_init(&full[s], kBpGroupThreads);
+            ptx::mbar_init(&empty[s], 1);
+            ptx::mbar_init(&tfull[s], 1);
+            ptx::mbar_init(&tempty[s], 32 * kBpEpiWarps);
+        }
+        ptx::mbar_init(&drain, 1);
+        ptx::fence_mbar_init();
+        s_abort = 0;
+    }
+    {  // B hi and lo, once
+        const uint4 *src = reinterpret_cast<const uint4 *>(a.Bs);
+        uint4 *dst = reinterpret_cast<uint4 *>(Bh);
+        const int n16 = (int)(2 * tc_b_bytes(n) / 16);
+        for (int e = tid; e < n16; e += kBpThreads) dst[e] = __ldg(src + e);
+    }
+    ptx::fence_proxy_async_smem();
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem = tslot;
+    const long long n_tiles = (a.n_cols + 127) / 128;
+    const int n_my = (int)((n_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x);
+    const unsigned ppi = (unsigned)a.ppi;
+    auto wait = [&](uint64_t *bar, uint32_t parity) {
+        const long long t0 = clock64();
+        while (!ptx::mbar_try_wait(bar, parity)) {
+            if (s_abort) return false;
+            if (clock64() - t0 > a.timeout_cycles) {
+                s_abort = 1;
+                atomicExch(a.status, KX_ERR_TIMEOUT);
+                return false;
+            }
+        }
+        return true;
+    };
+    auto tile_q0 = [&](int it) { return (unsigned)((blockIdx.x + (long long)it * gridDim.x) * 128); };
+
+    if (warp == kBpMmaWarp) {
+        // ---------------------------------------------------------------- MMA issue: D^T = B^T A^T
+        if (lane == 0) {
+            const uint32_t idesc = ptx::idesc_f16(n2, 128, 1, 0);
+            const uint32_t bh0 = ptx::smem_u32(Bh), bl0 = ptx::smem_u32(Bl);
+            const uint32_t gb = 32u * (uint32_t)n;
+            bool ok = true;
+            for (int it = 0; it < n_my && ok; ++it) {
+                const int s = it & 1;
+                ok = wait(&full[s], (uint32_t)((it >> 1) & 1));
+                if (ok && it >= 2) ok = wait(&tempty[s], (uint32_t)(((it >> 1) - 1) & 1));
+                if (!ok) break;
+                ptx::tc_fence_after();
+                const uint32_t ah0 = ptx::smem_u32(stage0 + 2 * s * ab), al0 = ah0 + (uint32_t)ab;
+                const uint32_t da = tmem + 256u * (uint32_t)s, db = da + 128u;
+                for (int ks = 0; ks < n2 / 16; ++ks) {
+                    const uint32_t ao = (uint32_t)(2 * kBpCore * ks);
+                    const uint64_t ah = ptx::sdesc(ah0 + ao, kBpCore, (uint32_t)sbo),
+                                   al = ptx::sdesc(al0 + ao, kBpCore, (uint32_t)sbo);
+                    const uint64_t bh = ptx::sdesc(bh0 + 2u * gb * ks, gb, 128),
+                                   bl = ptx::sdesc(bl0 + 2u * gb * ks, gb, 128);
+                    ptx::mma_f16(da, bh, al, idesc, ks > 0 ? 1u : 0u);
+                    ptx::mma_f16(da, bl, ah, idesc, 1u);
+                    ptx::mma_f16(db, bh, ah, idesc, ks > 0 ? 1u : 0u);
+                }
+                ptx::mma_commit(&empty[s]);
+                ptx::mma_commit(&tfull[s]);
+            }
+            if (!ok) {
+                ptx::mma_commit(&drain);
+                ptx::mbar_wait_bounded(&drain, 0, a.timeout_cycles);
+            }
+        }
+        __syncwarp();
+    } else if (warp >= kBpEpiWarps) {
+        // ---------------------------------------------------------------- producers
+        const int ptid = tid - 32 * kBpEpiWarps;
+        const int grp = ptid / kBpGroupThreads, gtid = ptid % kBpGroupThreads;
+        const int bar_id = 2 + grp;
+        const int ntask = 128 * nkc;  // 128 pencils x n / 8 chunks
+        constexpr int U = FORM ? 2 : 4;
+        // first value of the tile (its pencils are consecutive, of one item)
+        auto base = [&](unsigned q0, const float2 *&p, const float2 *&f) {
+            if (FORM) {
+                const unsigned item = q0 / ppi;
+                const long long rr = a.r0 + item;
+                const long long vv = rr / a.n_orb, mm = rr - vv * a.n_orb;
+                const long long x0 = (long long)(q0 - item * ppi) * n;
+                p = P + mm * N + x0;
+                f = F + vv * N + x0;
+            } else {
+                p = a.in + (long long)q0 * n;
+                f = nullptr;
+            }
+        };
+        // the item maximum of the group's next tile is loaded a tile ahead
+        float mx_cur = grp < n_my ? bp_item_max(a, tile_q0(grp) / ppi) : 0.f;
+        for (int it = grp; it < n_my; it += 2) {
+            bool ok = it < 2 || wait(&empty[grp], (uint32_t)(((it >> 1) - 1) & 1));
+            ok = ptx::named_bar_and(bar_id, kBpGroupThreads, ok && !s_abort);
+            if (!ok) break;
+            const unsigned q0 = tile_q0(it);
+            const int nq = (int)min(128LL, a.n_cols - q0);
+            const float sc = ldexpf(1.f, bp_exp(mx_cur));
+            const bool more = it + 2 < n_my;
+            if (more) {
+                const unsigned qn = tile_q0(it + 2);
+                mx_cur = bp_item_max(a, qn / ppi);
+                const float2 *pn, *fn;  // the next tile into L2, one 128-byte line per thread and step
+                base(qn, pn, fn);
+                const int lines = (int)min(128LL, a.n_cols - qn) * n / 16;
+                for (int l = gtid; l < lines; l += kBpGroupThreads) {
+                    ptx::prefetch_l2(pn + 16 * l);
+                    if (FORM) ptx::prefetch_l2(fn + 16 * l);
+                }
+            }
+            const float2 *pb, *fb;
+            base(q0, pb, fb);
+            uint8_t *Ahi = stage0 + 2 * grp * ab, *Alo = Ahi + ab;
+            for (int t0 = gtid; t0 < ntask; t0 += kBpGroupThreads * U) {
+                float4 v[U][4], w[FORM ? U : 1][4];
+#pragma unroll
+                for (int r = 0; r < U; ++r) {  // every load of the batch first
+                    const int t = t0 + r * kBpGroupThreads;
+                    const int m = t / nkc, kc = t - m * nkc;
+                    if (t < ntask && m < nq) {
+                        const long long off = (long long)m * n + 8 * kc;
+                        const float4 *sp = reinterpret_cast<const float4 *>(pb + off);
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) v[r][c] = __ldg(sp + c);
+                        if (FORM) {
+                            const float4 *sf = reinterpret_cast<const float4 *>(fb + off);
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) w[FORM ? r : 0][c] = __ldg(sf + c);
+                        }
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            v[r][c] = make_float4(0.f, 0.f, 0.f, 0.f);
+                            if (FORM) w[FORM ? r : 0][c] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < U; ++r) {
+                    const int t = t0 + r * kBpGroupThreads;
+                    if (t >= ntask) continue;
+                    const int m = t / nkc, kc = t - m * nkc;
+                    float wr[8], wi[8];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        float2 x0 = make_float2(v[r][c].x, v[r][c].y), x1 = make_float2(v[r][c].z, v[r][c].w);
+                        if (FORM) {
+                            x0 = cmul_conj(x0, make_float2(w[FORM ? r : 0][c].x, w[FORM ? r : 0][c].y));
+                            x1 = cmul_conj(x1, make_float2(w[FORM ? r : 0][c].z, w[FORM ? r : 0][c].w));
+                        }
+                        wr[2 * c] = x0.x * sc;
+                        wi[2 * c] = x0.y * sc;
+                        wr[2 * c + 1] = x1.x * sc;
+                        wi[2 * c + 1] = x1.y * sc;
+                    }
+                    const int row = (m >> 3) * sbo + (m & 7) * 16;
+                    tc_split_store(Ahi, Alo, row + kc * kBpCore, wr);
+                    tc_split_store(Ahi, Alo, row + (nkc + kc) * kBpCore, wi);
+                }
+            }
+            ptx::fence_proxy_async_smem();
+            ptx::mbar_arrive(&full[grp]);
+        }
+    } else {
+        // ---------------------------------------------------------------- epilogue
+        // lane row c' of D^T: real (c' < n) or imaginary part of column c' mod n;
+        // warps 0-3 take pencils [0, 64) of the tile, warps 4-7 pencils [64, 128)
+        const int qd = warp & 3, hh = warp >> 2;
+        const int cr = 32 * qd + lane;
+        const int im = cr >= n ? 1 : 0;
+        const int c = cr - im * n;
+        for (int it = 0; it < n_my; ++it) {
+            const int b = it & 1;
+            const unsigned q0 = tile_q0(it);
+            const int nq = (int)min(128LL, a.n_cols - q0);
+            const float unscale = ldexpf(1.f, -bp_exp(bp_item_max(a, q0 / ppi)) - kVScaleExp);
+            if (!__all_sync(0xffffffffu, wait(&tfull[b], (uint32_t)((it >> 1) & 1)))) break;
+            ptx::tc_fence_after();
+            const uint32_t tl = tmem + 256u * (uint32_t)b + ((uint32_t)(32 * qd) << 16);
+            float *ob = reinterpret_cast<float *>(a.out + (long long)q0 * n + c) + im;
+            for (int m0 = 64 * hh; m0 < 64 * hh + 64; m0 += 16) {
+                float va[16], vb[16];
+                ptx::tmem_ld16x2(tl + (uint32_t)m0, tl + (uint32_t)(128 + m0), va, vb);
+                if (cr < n2) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (m0 + j < nq) ob[(long long)(m0 + j) * n2] = (va[j] + vb[j]) * unscale;
+                }
+            }
+            ptx::tc_fence_before();
+            ptx::mbar_arrive(&tempty[b]);
+        }
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
     if (warp == kBpMmaWarp) {
         ptx::tc_fence_after();
         ptx::tmem_dealloc(tmem, 512);
@@ -1739,6 +1990,53 @@ int launch_bp(kx_plan *p, int axis, long long R, const float2 *in, float2 *out, 
     return prof_end(p, s);
 }
 
+// Products along axis 1 through bloch_pass0_kernel: n1 = 64 on the tensor cores,
+// a multiple of 128 pencils per item, axes 2 and 3 through bloch_pass_kernel
+// (whose last inverse product records the maxima this one's scales need).
+inline bool bp0_axis(const kx_plan *p) {
+    return bp_axes(p) && tc_axis(p, 0) && p->n[0] == 64 && (p->N / 64) % 128 == 0;
+}
+
+template <bool FORM>
+int launch_bp0(kx_plan *p, long long R, const float2 *in, float2 *out, const __half *Bs, const float2 *P,
+               const float2 *F, const float *in_max, const float *pmax, const float *fmax, long long r0, int n_orb,
+               cudaStream_t s) {
+    const int n = p->n[0];
+    const long long N = (long long)p->N;
+    if (R * N >= (1LL << 31)) return set_error(KX_ERR_ARG, "Bloch exchange: chunk too large for one launch");
+    BpArgs a;
+    a.in = in;
+    a.out = out;
+    a.n = n;
+    a.inner = 1;
+    a.ppi = N / n;
+    a.n_cols = R * a.ppi;
+    a.Bs = Bs;
+    a.f = nullptr;
+    a.in_max = in_max;
+    a.pmax = pmax;
+    a.fmax = fmax;
+    a.bound_mul = 1.001f;  // |rho| <= max|psi_m| max|phi_v|
+    a.r0 = r0;
+    a.n_orb = n_orb;
+    a.out_max = nullptr;
+    a.status = p->d_status;
+    a.timeout_cycles = 2000000000LL;
+    const long long n_tiles = (a.n_cols + 127) / 128;
+    if (n_tiles == 0) return KX_OK;
+    static bool attr = false;  // once per instantiation
+    if (!attr) {
+        KX_CUDA_TRY(cudaFuncSetAttribute(bloch_pass0_kernel<FORM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bp_smem_bytes(kTcMaxN)));
+        attr = true;
+    }
+    const int grid = (int)std::min<long long>(n_tiles, p->num_sms);
+    if (int rc = prof_begin(p, PK_BLOCH, s)) return rc;
+    bloch_pass0_kernel<FORM><<<grid, kBpThreads, bp_smem_bytes(n), s>>>(a, P, F, N);
+    KX_LAUNCH_CHECK("bloch_pass0_kernel launch");
+    return prof_end(p, s);
+}
+
 // Per-vector maxima of n_vec float32 vectors (vmax zeroed here first).
 inline int vector_maxima(kx_plan *p, const float2 *x, long long N, int n_vec, float *vmax, cudaStream_t s) {
     KX_CUDA_TRY(cudaMemsetAsync(vmax, 0, sizeof(float) * n_vec, s));
@@ -1945,8 +2243,12 @@ int bloch_sweep(kx_plan *p, int n_kpt, const double *theta, const double *wk, in
             if constexpr (sizeof(T) == 4) {
                 auto Bf = [&](int a) { return reinterpret_cast<const __half *>(ws + L.Bf[a]); };
                 auto Bi = [&](int a) { return reinterpret_cast<const __half *>(ws + L.Bi[a]); };
-                rc = tc_axis(p, 0) ? launch_tc<true, 0>(p, 0, R, nullptr, A, Bf(0), nullptr, Pq, F, n_orb, r0, s)
-                                   : launch_form<T>(p, R, A, Mf[0], Pq, F, n_orb, r0, s);
+                if (bp0_axis(p))
+                    rc = launch_bp0<true>(p, R, nullptr, A, Bf(0), Pq, F, nullptr, reinterpret_cast<const float *>(ws + L.Pmax),
+                                          reinterpret_cast<const float *>(ws + L.Fmax), r0, n_orb, s);
+                else
+                    rc = tc_axis(p, 0) ? launch_tc<true, 0>(p, 0, R, nullptr, A, Bf(0), nullptr, Pq, F, n_orb, r0, s)
+                                       : launch_form<T>(p, R, A, Mf[0], Pq, F, n_orb, r0, s);
                 if (rc) return rc;
                 if (bp_axes(p)) {
                     // axes 2 and 3 with per-item scales: the bound from the orbital
@@ -1958,7 +2260,8 @@ int bloch_sweep(kx_plan *p, int n_kpt, const double *theta, const double *wk, in
                     if ((rc = launch_bp<1>(p, 2, R, B, A, Bf(2), f, mx0, nullptr, nullptr, 0, n_orb, mx1, s))) return rc;
                     if ((rc = launch_bp<0>(p, 2, R, A, B, Bi(2), nullptr, mx1, nullptr, nullptr, 0, n_orb, mx0, s)))
                         return rc;
-                    if ((rc = launch_bp<0>(p, 1, R, B, A, Bi(1), nullptr, mx0, nullptr, nullptr, 0, n_orb, nullptr, s)))
+                    if ((rc = launch_bp<0>(p, 1, R, B, A, Bi(1), nullptr, mx0, nullptr, nullptr, 0, n_orb,
+                                           bp0_axis(p) ? mx1 : nullptr, s)))
                         return rc;
                 } else {
                     rc = tc_axis(p, 1)
@@ -1977,8 +2280,13 @@ int bloch_sweep(kx_plan *p, int n_kpt, const double *theta, const double *wk, in
                              : launch_pipe<T, 0>(p, 1, R, B, A, Mi[1], nullptr, s);
                     if (rc) return rc;
                 }
-                rc = tc_axis(p, 0) ? launch_tc<false, 0>(p, 0, R, A, B, Bi(0), nullptr, nullptr, nullptr, n_orb, 0, s)
-                                   : launch_pipe<T, 0>(p, 0, R, A, B, Mi[0], nullptr, s);
+                if (bp0_axis(p))
+                    rc = launch_bp0<false>(p, R, A, B, Bi(0), nullptr, nullptr,
+                                           reinterpret_cast<const float *>(ws + L.mx1), nullptr, nullptr, 0, n_orb, s);
+                else
+                    rc = tc_axis(p, 0)
+                             ? launch_tc<false, 0>(p, 0, R, A, B, Bi(0), nullptr, nullptr, nullptr, n_orb, 0, s)
+                             : launch_pipe<T, 0>(p, 0, R, A, B, Mi[0], nullptr, s);
                 if (rc) return rc;
             } else {
                 if ((rc = launch_form<T>(p, R, A, Mf[0], Pq, F, n_orb, r0, s))) return rc;
@@ -2162,8 +2470,12 @@ int bloch_energy_only(kx_plan *p, int n_kpt, const double *theta, const double *
                 int rc;
                 if constexpr (sizeof(T) == 4) {
                     auto Bf = [&](int a) { return reinterpret_cast<const __half *>(ws + L.Bf[a]); };
-                    rc = tc_axis(p, 0) ? launch_tc<true, 0>(p, 0, R, nullptr, A, Bf(0), nullptr, Pq, F, n_orb, r0, s)
-                                       : launch_form<T>(p, R, A, Mf[0], Pq, F, n_orb, r0, s);
+                    if (bp0_axis(p))
+                        rc = launch_bp0<true>(p, R, nullptr, A, Bf(0), Pq, F, nullptr, reinterpret_cast<const float *>(ws + L.Pmax),
+                                              reinterpret_cast<const float *>(ws + L.Fmax), r0, n_orb, s);
+                    else
+                        rc = tc_axis(p, 0) ? launch_tc<true, 0>(p, 0, R, nullptr, A, Bf(0), nullptr, Pq, F, n_orb, r0, s)
+                                           : launch_form<T>(p, R, A, Mf[0], Pq, F, n_orb, r0, s);
                     if (rc) return rc;
                     if (bp_axes(p)) {
                         float *mx0 = reinterpret_cast<float *>(ws + L.mx0);

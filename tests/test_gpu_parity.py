@@ -880,6 +880,10 @@ KPOINT_CASES = [
     # 9 pairs leave a ragged last tile (first product, and the f-scaled third)
     ((64, 8, 8), (0.3, 0.5, 0.5), (P, D, D), U, 3, (2, 1, 1), (0.0, 0.0), 1),
     ((8, 8, 64), (0.5, 0.5, 0.3), (D, D, P), S, 3, (1, 1, 3), (0.0, 0.0), 1),
+    # every axis of 32 or 64 points: axes 2 and 3 take the pass kernel with
+    # per-item scales, and with 64 points along axis 1 that axis does too
+    ((32, 32, 32), (0.4, 0.45, 0.5), (P, P, D), U, 3, (2, 2, 1), (0.2, -0.1), 1),
+    ((64, 32, 32), (0.3, 0.4, 0.5), (P, D, P), S, 2, (2, 1, 2), (0.0, 0.3), 1),
 ]
 
 
@@ -947,6 +951,36 @@ def test_kpoint_tensor_core_and_cuda_core_products(kx, case, monkeypatch):
         assert abs(e_only - ex_ref) < TOL_K[prec][1] * abs(ex_ref), tc
         out[tc] = vx
     assert relmax(out["1"], out["0"]) < TOL_K[prec][0]
+
+
+@pytest.mark.parametrize("case", [12, 13])
+def test_kpoint_pass_kernels_and_tile_kernels(kx, case, monkeypatch):
+    """With every axis of 32 or 64 points the products run in the pass kernels
+    (split scales per item: a bound from the orbital maxima for the first ones,
+    then the maxima the previous product recorded); KX_BLOCH_PASS=0 takes the
+    per-tile-maximum kernels instead.  Both match the oracle, with whole chunks
+    and with chunks of 5 pairs, and E_x alone agrees."""
+    sysd, theta, wk, psi, occ, prec = kpoint_inputs(case, 360 + case)
+    base = oracle.Plan(sysd.n, sysd.h, sysd.bc, sysd.kernel)
+    vx_ref, ex_ref = oracle.vx_kpoints(base, theta, wk, psi, occ)
+    plan = kx.Plan(sysd.n, sysd.h, sysd.bc, sysd.kernel, precision=prec)
+    out = {}
+    for chunk in (None, "5"):
+        if chunk:
+            monkeypatch.setenv("KX_CHUNK_PAIRS", chunk)
+        for bp in ("1", "0"):
+            monkeypatch.setenv("KX_BLOCH_PASS", bp)
+            vx, ex = kx.kx_vx_kpoints(plan, theta, wk, to_dev_orbitals(psi), dev(occ))
+            e_only = kx.kx_energy_kpoints(plan, theta, wk, to_dev_orbitals(psi), dev(occ)).item()
+            torch.cuda.synchronize()
+            assert plan.status() == kx.KX_OK
+            vx = vx.cpu().numpy().transpose(0, 2, 1)
+            assert relmax(vx, vx_ref) < TOL_K[prec][0], (chunk, bp)
+            assert abs(ex.item() - ex_ref) < TOL_K[prec][1] * abs(ex_ref), (chunk, bp)
+            assert abs(e_only - ex_ref) < TOL_K[prec][1] * abs(ex_ref), (chunk, bp)
+            out[(chunk, bp)] = vx
+    assert relmax(out[(None, "1")], out[(None, "0")]) < TOL_K[prec][0]
+    assert relmax(out[("5", "1")], out[(None, "1")]) < TOL_K[prec][0]
 
 
 @pytest.mark.parametrize("prec", [0, 1])

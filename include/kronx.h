@@ -210,10 +210,12 @@ int kx_vx_apply(kx_plan *plan, int n_orb, const double *psi, const double *occ,
  * [pair_begin, pair_end) of the library's list of the n_orb (n_orb+1)/2
  * unordered pairs (i <= j).  The list groups orbitals in blocks of four
  * (block b = orbitals 4b .. 4b+3 of nb blocks, the last possibly shorter) and
- * visits the block pairs (I, J), I <= J, in this order: every pair without the
- * last block column-major (J = 0 .. nb-2, I = 0 .. J), then (I, nb-1) for
- * I = 0 .. nb-1; inside a diagonal block (I, I) the pairs i <= j row-major,
- * inside an off-diagonal block all (i, j) row-major.
+ * visits the block pairs (I, J), I <= J, in this order: those of the leading
+ * block columns J < jc column-major (J = 0 .. jc-1, I = 0 .. J), jc being the
+ * fewest columns that hold ceil(15% of nb (nb+1)/2) block pairs, then the rest
+ * row-major (I = 0 .. nb-1, J = max(I, jc) .. nb-1); inside a diagonal block
+ * (I, I) the pairs i <= j row-major, inside an off-diagonal block all (i, j)
+ * row-major.
  * vx_psi and e_x receive the
  * partial sums of Eqs. 3-5 over that range (overwritten, not added), so that
  * ranges covering the list sum to the full result: the unit a multi-GPU split

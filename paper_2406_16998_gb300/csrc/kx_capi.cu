@@ -57,15 +57,23 @@ int ensure_workspace(kx_plan *p, size_t bytes) {
 }
 
 // Pair enumeration: orbitals in blocks of kOrbBlock (nb blocks); block pairs
-// (I, J), I <= J, first every pair without the last block column-major
-// (J = 0 .. nb-2, I = 0 .. J), then the last block's pairs (I, nb-1) for
-// I = 0 .. nb-1; inside a diagonal block the upper triangle row-major, inside an
-// off-diagonal block all (i, j) row-major.  Each block pair is one accumulation
-// group.  Early groups need only the first orbitals (a host-buffer call starts
-// while later orbitals are still being copied), and each block's rows are
-// final as soon as its pair with the last block is done (their copies back
-// overlap the rest).  [begin, end) restricts the list to a sub-range of this
-// enumeration (groups are cut at the range ends).
+// (I, J), I <= J, first those of the leading columns J < jc column-major
+// (J = 0 .. jc-1, I = 0 .. J; jc the fewest columns holding 15% of the block
+// pairs), then the rest row-major (I = 0 .. nb-1, J = max(I, jc) .. nb-1);
+// inside a diagonal block the upper triangle row-major, inside an off-diagonal
+// block all (i, j) row-major.  Each block pair is one accumulation group.  The
+// leading columns need only the first orbitals (a host-buffer call starts while
+// later orbitals are still being copied); after them the row blocks become
+// final one after another (their copies back overlap the rest).  [begin, end)
+// restricts the list to a sub-range of this enumeration (groups are cut at the
+// range ends).
+int leading_columns(int nb) {
+    const long long tot = (long long)nb * (nb + 1) / 2, want = (15 * tot + 99) / 100;
+    int jc = 1;
+    while (jc < nb && (long long)jc * (jc + 1) / 2 < want) ++jc;
+    return jc;
+}
+
 // With p->blk_mode set, the block pairs of p->blk_req (I <= J each, in the
 // given order) are enumerated instead, each whole; begin / end are ignored.
 int ensure_pairs(kx_plan *p, int n_orb, cudaStream_t s, long long begin, long long end) {
@@ -87,21 +95,23 @@ int ensure_pairs(kx_plan *p, int n_orb, cudaStream_t s, long long begin, long lo
     pairs.reserve(2 * (size_t)(end - begin));
     slots.reserve(2 * (size_t)(end - begin));
     const int nb = (n_orb + kOrbBlock - 1) / kOrbBlock;
-    // the block pairs to visit: all (I <= J) row-major, or the explicit list
+    // the block pairs to visit: all (I <= J) in the order above, or the explicit list
     std::vector<int> visit;
     if (p->blk_mode) {
         visit = p->blk_req;
     } else {
         visit.reserve((size_t)nb * (nb + 1));
-        for (int JB = 0; JB + 1 < nb; ++JB)
+        const int jc = leading_columns(nb);
+        for (int JB = 0; JB < jc; ++JB)
             for (int IB = 0; IB <= JB; ++IB) {
                 visit.push_back(IB);
                 visit.push_back(JB);
             }
-        for (int IB = 0; IB < nb; ++IB) {
-            visit.push_back(IB);
-            visit.push_back(nb - 1);
-        }
+        for (int IB = 0; IB < nb; ++IB)
+            for (int JB = std::max(IB, jc); JB < nb; ++JB) {
+                visit.push_back(IB);
+                visit.push_back(JB);
+            }
     }
     long long k = 0;
     for (size_t v = 0; v + 1 < visit.size(); v += 2) {

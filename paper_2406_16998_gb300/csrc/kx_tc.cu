@@ -1712,7 +1712,6 @@ int tc_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, double *v
         while (k + 1 < (int)pc.end.size() && pc.end[k] <= o) ++k;
         return k;
     };
-    const int nb = (n_orb + kOrbBlock - 1) / kOrbBlock;
     const std::vector<int> &maxorb = p->h_group_maxorb;
     if (ex) KX_CUDA_TRY(cudaMemsetAsync(ex, 0, sizeof(double), s));
     if (!energy_only) {
@@ -1727,6 +1726,20 @@ int tc_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, double *v
     const int2 *pairs = reinterpret_cast<const int2 *>(p->d_pairs);
     const float mid_bound = fmax_sqrt(p);
 
+    // pairs a chunk of a host-buffer call holds before it may end at a finished
+    // row block (KX_ROW_CHUNK overrides: comparison runs)
+    int row_chunk = 384;
+    if (const char *e = std::getenv("KX_ROW_CHUNK")) row_chunk = std::max(1, std::atoi(e));
+    // row_end[g]: groups [0, g) finish a row block (group g - 1 is the last one of
+    // some orbital); tail: that row block is among the last three
+    std::vector<char> row_end((size_t)n_groups + 1, 0), tail((size_t)n_groups + 1, 0);
+    if (pieces)
+        for (int o = 0; o < n_orb; ++o) {
+            const int g = p->h_orb_last[o] + 1;
+            if (g < 1 || g > n_groups) continue;
+            row_end[g] = 1;
+            if (o >= n_orb - 3 * kOrbBlock) tail[g] = 1;
+        }
     int g0 = 0, o_fin = 0;
     while (g0 < n_groups) {
         int g1 = g0 + 1;
@@ -1734,13 +1747,12 @@ int tc_vx(kx_plan *p, int n_orb, const double *psi, const double *occ, double *v
             if (pieces) {
                 // the first two pieces each end a chunk (their successors are still
                 // copying); later pieces have arrived by the time they are needed.
-                // Among the last block's pairs (each finishes a row block) eight per
-                // chunk, so that finished rows are copied back while the rest computes
-                // (smaller chunks there cost more than the copies they hide)
-                const bool last0 = maxorb[g0] / kOrbBlock == nb - 1 && maxorb[g1] / kOrbBlock == nb - 1;
+                // A chunk ends where a row block becomes final once it holds
+                // row_chunk pairs (at every one of the last three), so that
+                // finished rows are copied back while the rest computes
                 const int pg0 = piece_of(maxorb[g0]);
                 if (pg0 < 2 && piece_of(maxorb[g1]) > pg0) break;
-                if (last0 && g1 - g0 >= 8) break;
+                if (row_end[g1] && (first[g1] - first[g0] >= row_chunk || tail[g1])) break;
             }
             ++g1;
         }

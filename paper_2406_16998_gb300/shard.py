@@ -34,12 +34,23 @@ def n_blocks(n_orb: int) -> int:
     return (n_orb + ORB_BLOCK - 1) // ORB_BLOCK
 
 
+def leading_columns(nb: int) -> int:
+    """The fewest leading block columns that hold 15% of the block pairs."""
+    want = (15 * (nb * (nb + 1) // 2) + 99) // 100
+    jc = 1
+    while jc < nb and jc * (jc + 1) // 2 < want:
+        jc += 1
+    return jc
+
+
 def block_pairs(n_orb: int):
-    """The library's order of the orbital block pairs (I, J), I <= J: every pair
-    without the last block column-major (J = 0 .. nb-2, I = 0 .. J), then the
-    last block's pairs (I, nb-1), I = 0 .. nb-1."""
+    """The library's order of the orbital block pairs (I, J), I <= J: those of the
+    leading columns J < jc column-major (J = 0 .. jc-1, I = 0 .. J), then the rest
+    row-major (I = 0 .. nb-1, J = max(I, jc) .. nb-1)."""
     nb = n_blocks(n_orb)
-    return [(I, J) for J in range(nb - 1) for I in range(J + 1)] + [(I, nb - 1) for I in range(nb)]
+    jc = leading_columns(nb)
+    return ([(I, J) for J in range(jc) for I in range(J + 1)] +
+            [(I, J) for I in range(nb) for J in range(max(I, jc), nb)])
 
 
 def pair_list(n_orb: int):

@@ -1679,9 +1679,9 @@ __global__ void bloch_to_f32_kernel(const double2 *__restrict__ src, float2 *__r
 
 // out_v[x] -= sum over the chunk items r = v * n_orb + m in [r0, r1) of
 // w_q g_mq psi_m[x] X_{r - r0}[x] (m ascending, one thread per (v, x)).
-// (memory-latency bound: six blocks per SM, 42 registers)
+// (memory-latency bound: four orbitals' loads in flight per thread, four blocks per SM)
 template <typename T>
-__global__ void __launch_bounds__(256, 6) bloch_accum_kernel(const typename Cx<T>::t *__restrict__ X, long long r0, long long r1, int n_orb,
+__global__ void __launch_bounds__(256, 4) bloch_accum_kernel(const typename Cx<T>::t *__restrict__ X, long long r0, long long r1, int n_orb,
                                    const typename Cx<T>::t *__restrict__ P, const double *__restrict__ occ_q,
                                    double wq, double2 *__restrict__ out, long long N) {
     using T2 = typename Cx<T>::t;
@@ -1693,7 +1693,23 @@ __global__ void __launch_bounds__(256, 6) bloch_accum_kernel(const typename Cx<T
         long long v = v_lo + vl;
         long long m0 = max(0LL, r0 - v * n_orb), m1 = min((long long)n_orb, r1 - v * n_orb);
         T sr = 0, si = 0;
-        for (long long m = m0; m < m1; ++m) {
+        // four orbitals' loads issued together, the sums still in ascending m
+        long long m = m0;
+        for (; m + 4 <= m1; m += 4) {
+            T2 p[4], xx[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                p[u] = P[(m + u) * N + x];
+                xx[u] = X[(v * n_orb + m + u - r0) * N + x];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const T c = (T)(wq * (occ_q ? occ_q[m + u] : 1.0));
+                sr = fma(c, p[u].x * xx[u].x - p[u].y * xx[u].y, sr);
+                si = fma(c, p[u].x * xx[u].y + p[u].y * xx[u].x, si);
+            }
+        }
+        for (; m < m1; ++m) {
             T2 p = P[m * N + x];
             T2 xx = X[(v * n_orb + m - r0) * N + x];
             T c = (T)(wq * (occ_q ? occ_q[m] : 1.0));
@@ -2112,7 +2128,7 @@ BlochLayout bloch_layout(const kx_plan *p, int n_orb, int n_vec, int n_kpt, size
 // out_m[x] -= sum over the chunk items r = v * n_orb + m in [r0, r1) of
 // w_k g_vk F_v[x] conj(X_{r - r0}[x]) (v ascending, one thread per (m, x)).
 template <typename T>
-__global__ void __launch_bounds__(256, 6) bloch_accum_rev_kernel(const typename Cx<T>::t *__restrict__ X, long long r0, long long r1,
+__global__ void __launch_bounds__(256, 4) bloch_accum_rev_kernel(const typename Cx<T>::t *__restrict__ X, long long r0, long long r1,
                                        int n_orb, const typename Cx<T>::t *__restrict__ F,
                                        const double *__restrict__ occ_k, double wk, double2 *__restrict__ out,
                                        long long N) {
@@ -2123,18 +2139,32 @@ __global__ void __launch_bounds__(256, 6) bloch_accum_rev_kernel(const typename 
          e += (long long)gridDim.x * blockDim.x) {
         long long m = e / N, x = e - m * N;
         T sr = 0, si = 0;
-        bool any = false;
-        for (long long v = v_lo; v <= v_hi; ++v) {
-            long long r = v * n_orb + m;
-            if (r < r0 || r >= r1) continue;
-            any = true;
-            T2 fv = F[v * N + x];
-            T2 xx = X[(r - r0) * N + x];
-            T c = (T)(wk * (occ_k ? occ_k[v] : 1.0));
-            sr = fma(c, fv.x * xx.x + fv.y * xx.y, sr);  // F conj(X)
-            si = fma(c, fv.y * xx.x - fv.x * xx.y, si);
+        // the vectors v whose item v n_orb + m lies in [r0, r1): a contiguous run
+        const long long va = max(v_lo, (r0 - m + n_orb - 1) / n_orb), vb = min(v_hi, (r1 - 1 - m) / n_orb);
+        if (r1 - 1 - m < 0 || va > vb) continue;
+        // four vectors' loads issued together, the sums still in ascending v
+        long long v = va;
+        for (; v + 4 <= vb + 1; v += 4) {
+            T2 fv[4], xx[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                fv[u] = F[(v + u) * N + x];
+                xx[u] = X[((v + u) * n_orb + m - r0) * N + x];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const T c = (T)(wk * (occ_k ? occ_k[v + u] : 1.0));
+                sr = fma(c, fv[u].x * xx[u].x + fv[u].y * xx[u].y, sr);  // F conj(X)
+                si = fma(c, fv[u].y * xx[u].x - fv[u].x * xx[u].y, si);
+            }
         }
-        if (!any) continue;
+        for (; v <= vb; ++v) {
+            T2 f1 = F[v * N + x];
+            T2 x1 = X[(v * n_orb + m - r0) * N + x];
+            T c = (T)(wk * (occ_k ? occ_k[v] : 1.0));
+            sr = fma(c, f1.x * x1.x + f1.y * x1.y, sr);
+            si = fma(c, f1.y * x1.x - f1.x * x1.y, si);
+        }
         double2 o = out[m * N + x];
         if constexpr (sizeof(T) == 4) {
             o.x -= f32_to_f64(sr);

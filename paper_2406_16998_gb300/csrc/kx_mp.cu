@@ -500,7 +500,8 @@ constexpr int kCtM = 128;                 // grid points per tile
 constexpr size_t kCtA = 128 * 64 * 2;     // hi (or lo) of A_k: 128 points x 64 orbitals fp16
 constexpr size_t kCtB = 64 * 64 * 2;      // hi (or lo) of B_k
 constexpr size_t kCtStage = 2 * kCtA + 2 * kCtB;
-constexpr size_t kCtSmem = 2 * kCtStage + 1024;
+constexpr int kCtStages = 3;               // B_{k+1} is copied while A_k is built and k-1's products run
+constexpr size_t kCtSmem = kCtStages * kCtStage + 1024;
 
 // scale exponents: e_psi from max|psi|, per k the exponents of max|h_k| and max|C_k|
 // out: sc[k] = s_psi s_h,k (the A scale), sc[K + k] = t_k, sc[2K] = 1 / (s_psi S)
@@ -586,8 +587,10 @@ __device__ __forceinline__ void ct_issue(uint32_t da, uint32_t db, uint32_t a_hi
 // acc_i(x) = T[x][i] (the float32 accumulator of the pair loop starts from the
 // correction); e_part[CTA] = sum over its tiles of g_i psi_i(x) T[x][i].
 // Persistent: CTA walks the tiles blockIdx.x, + gridDim.x, ...; for each tile
-// the K harmonics go through two shared stages (A_k built by all threads, B_k
-// copied from the pre-split array), one thread issuing each k's products.
+// the K harmonics go through a ring of three shared stages (A_k built by all
+// threads; B_k copied from the pre-split array one harmonic ahead, so that the
+// copy's latency overlaps the build of A_{k-1}), one thread issuing each k's
+// products; all eight warps then read T (two per TMEM lane quadrant).
 __global__ void __launch_bounds__(256, 1) mp_combine_tc_kernel(const double *__restrict__ psi, int n,
                                                                const __half *__restrict__ Bs,
                                                                const float *__restrict__ H, int K,
@@ -597,7 +600,7 @@ __global__ void __launch_bounds__(256, 1) mp_combine_tc_kernel(const double *__r
                                                                int *status, long long timeout_cycles) {
     extern __shared__ uint8_t ct_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(ct_raw) + 1023) & ~uintptr_t(1023));
-    __shared__ uint64_t bar[2];
+    __shared__ uint64_t bar[kCtStages];
     __shared__ uint32_t tslot;
     __shared__ double red[8];
     __shared__ volatile int s_abort;
@@ -607,8 +610,7 @@ __global__ void __launch_bounds__(256, 1) mp_combine_tc_kernel(const double *__r
         ptx::tmem_relinquish();
     }
     if (tid == 0) {
-        ptx::mbar_init(&bar[0], 1);
-        ptx::mbar_init(&bar[1], 1);
+        for (int b = 0; b < kCtStages; ++b) ptx::mbar_init(&bar[b], 1);
         ptx::fence_mbar_init();
         s_abort = 0;
     }
@@ -622,8 +624,25 @@ __global__ void __launch_bounds__(256, 1) mp_combine_tc_kernel(const double *__r
     // j = 8 (jh + 2u) + jl, u < 4: eight neighbouring lanes fill one 128-byte
     // core matrix (the eight orbitals of a K group at one point group)
     const int jl = tid & 7, mg = (tid >> 3) & 15, jh = tid >> 7;
-    uint32_t uses[2] = {0u, 0u};  // commits issued per stage
-    uint32_t waited[2] = {0u, 0u};
+    uint32_t uses[kCtStages] = {0u, 0u, 0u};  // commits issued per stage
+    uint32_t waited[kCtStages] = {0u, 0u, 0u};
+    // B_k (2 x 8 KB of the pre-split array) into stage b, one cp.async group
+    auto copy_b = [&](int k, int b) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(Bs + (size_t)k * 8192);
+        uint8_t *dst = smem + b * kCtStage + 2 * kCtA;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) ptx::cp_async16(dst + 16 * (tid + 256 * q), src + tid + 256 * q, 16u);
+        ptx::cp_async_commit();
+    };
+    // the products that last read stage b are done (each thread waits by itself;
+    // a timeout is acted on after the next block barrier)
+    auto free_stage = [&](int b) {
+        if (uses[b] > waited[b]) {
+            if (!ptx::mbar_wait_bounded(&bar[b], waited[b] & 1u, timeout_cycles)) s_abort = 1;
+            ++waited[b];
+            ptx::tc_fence_after();
+        }
+    };
     bool ok = true;
     double e_acc = 0.0;
     for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
@@ -652,23 +671,17 @@ __global__ void __launch_bounds__(256, 1) mp_combine_tc_kernel(const double *__r
             hn0 = __ldg(hs);
             hn1 = __ldg(hs + 1);
         }
+        // every stage is free at a tile's start (the previous tile's products were
+        // waited for); stage k % 3 is freed before B_k is copied into it
+        free_stage(0);
+        copy_b(0, 0);
         for (int k = 0; k < K && ok; ++k) {
-            const int b = k & 1;
+            const int b = k % kCtStages;
             uint8_t *st = smem + b * kCtStage;
-            if (uses[b] > waited[b]) {
-                // the products that last read this stage are done (each thread waits by
-                // itself; a timeout is acted on after the block barrier below)
-                if (!ptx::mbar_wait_bounded(&bar[b], waited[b] & 1u, timeout_cycles)) s_abort = 1;
-                ++waited[b];
-                ptx::tc_fence_after();
-            }
-            // B_k: 2 x 8 KB from the pre-split array, copied while A_k is built
-            {
-                const uint4 *src = reinterpret_cast<const uint4 *>(Bs + (size_t)k * 8192);
-                uint8_t *dst = st + 2 * kCtA;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) ptx::cp_async16(dst + 16 * (tid + 256 * q), src + tid + 256 * q, 16u);
-                ptx::cp_async_commit();
+            if (k + 1 < K) {
+                const int bn = (k + 1) % kCtStages;
+                free_stage(bn);
+                copy_b(k + 1, bn);
             }
             // A_k: (h_k psi_j) at the 8 points, scaled by sc[k]
             const float sk = sc[k];
@@ -687,7 +700,10 @@ __global__ void __launch_bounds__(256, 1) mp_combine_tc_kernel(const double *__r
                 for (int c = 0; c < 8; ++c) w[c] = pv[u][c] * hv[c];
                 mt_split_store(st, st + kCtA, mg * 128 + (j >> 3) * 2048 + (j & 7) * 16, w);
             }
-            ptx::cp_async_wait<0>();
+            if (k + 1 < K)
+                ptx::cp_async_wait<1>();  // B_k has landed; B_{k+1} may still be copying
+            else
+                ptx::cp_async_wait<0>();
             ptx::fence_proxy_async_smem();
             __syncthreads();
             if (s_abort) {
@@ -703,19 +719,20 @@ __global__ void __launch_bounds__(256, 1) mp_combine_tc_kernel(const double *__r
             ++uses[b];
         }
         // the tile's last products are done: read T, update Vx psi, energy
-        for (int b = 0; b < 2 && ok; ++b)
+        for (int b = 0; b < kCtStages && ok; ++b)
             while (ok && uses[b] > waited[b]) {
                 ok = __syncthreads_and(ptx::mbar_wait_bounded(&bar[b], waited[b] & 1u, timeout_cycles));
                 ++waited[b];
             }
         if (!ok) break;
         ptx::tc_fence_after();
-        if (warp < 4) {
-            const int m = warp * 32 + lane;
+        {
+            const int q = warp & 3, hcol = warp >> 2;  // lane quadrant, orbital half
+            const int m = q * 32 + lane;
             const long long x = tile * kCtM + m;
-            const uint32_t tl = tmem + ((uint32_t)(32 * warp) << 16);
+            const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
             float ef = 0.f;
-            for (int c0 = 0; c0 < 64; c0 += 16) {
+            for (int c0 = 32 * hcol; c0 < 32 * hcol + 32; c0 += 16) {
                 float va[16], vb[16];
                 ptx::tmem_ld16x2(tl + c0, tl + 64 + c0, va, vb);
                 if (x >= N) continue;
@@ -737,7 +754,7 @@ __global__ void __launch_bounds__(256, 1) mp_combine_tc_kernel(const double *__r
     }
     if (!ok && tid == 0) atomicExch(status, KX_ERR_TIMEOUT);
     // products still in flight after an early exit finish before TMEM is released
-    for (int b = 0; b < 2; ++b)
+    for (int b = 0; b < kCtStages; ++b)
         for (; uses[b] > waited[b]; ++waited[b]) ptx::mbar_wait_bounded(&bar[b], waited[b] & 1u, timeout_cycles);
     for (int o = 16; o > 0; o >>= 1) e_acc += __shfl_xor_sync(0xffffffffu, e_acc, o);
     if (lane == 0) red[warp] = e_acc;

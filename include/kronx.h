@@ -72,8 +72,10 @@ typedef struct CUstream_st *kx_stream;
                       the power-of-two scales                                        */
 #define KX_FFT32 2 /* fully periodic grids only: f(L) through the DFT (the eigenvectors of
                       a periodic axis are Fourier modes), float32 complex Stockham FFTs
-                      of radix 2, 3, 4, 5; every n[a] a product of 2, 3 and 5; the
-                      FFT variant the Kronecker form is compared with (Sec. 3, Fig. 1) */
+                      of radix 2, 3, 4, 5 (axes of 80 points: a 16 x 5 four-step
+                      transform in registers); every n[a] a product of 2, 3 and 5,
+                      at most 128 (KX_ERR_UNSUPPORTED otherwise); the FFT variant the
+                      Kronecker form is compared with (Sec. 3, Fig. 1)                */
 
 /* Error codes. */
 #define KX_OK              0

@@ -10,7 +10,8 @@
 //      by Parseval), inverse transform
 //   C  per x3 plane: inverse 2D transform, real part / N.
 // Each batch of line transforms is a mixed-radix (4, 2, 3, 5) Stockham FFT whose
-// stages are spread over the CTA's threads (lines x butterflies).
+// stages are spread over the CTA's threads (lines x butterflies); lines of 80
+// points instead take a four-step transform (16 x 5) held in registers.
 #include "kx_internal.h"
 
 #include <cmath>
@@ -119,12 +120,128 @@ __device__ __forceinline__ void fft_stage(const float2 *a, float2 *b, int n, int
     }
 }
 
+// ---- lines of 80 points in registers: 80 = 16 x 5 (four-step)
+//
+// With x_p,q = x[p + 16 q] (p < 16, q < 5):
+//   X[k5 + 5 k16] = sum_p W80^(p k5) W16^(p k16) sum_q x_p,q W5^(q k5),
+// so phase 1 takes each p's five values through a 5-point DFT and the twiddle
+// W80^(p k5) (into the scratch buffer at k5 16 + p) and phase 2 takes each
+// k5's sixteen values through a 16-point DFT (4 x 4 with twiddles W16^(b k4))
+// into X.  Tasks are ordered lines first, so that with the padded plane rows
+// (or the 64-line columns of pass B) consecutive threads touch distinct banks.
+// W5 and W16 are the constants cos, sin of 2 pi k / 5 and 2 pi k / 16; W80
+// comes from the line's twiddle table.  sg = -1 conjugates (inverse).
+__device__ __forceinline__ void dft4_reg(float2 &v0, float2 &v1, float2 &v2, float2 &v3, float sg) {
+    const float2 a = make_float2(v0.x + v2.x, v0.y + v2.y);
+    const float2 b = make_float2(v0.x - v2.x, v0.y - v2.y);
+    const float2 c = make_float2(v1.x + v3.x, v1.y + v3.y);
+    const float2 t = make_float2(v1.x - v3.x, v1.y - v3.y);
+    const float2 d = make_float2(sg * t.y, -sg * t.x);  // -i sg t
+    v0 = make_float2(a.x + c.x, a.y + c.y);
+    v2 = make_float2(a.x - c.x, a.y - c.y);
+    v1 = make_float2(b.x + d.x, b.y + d.y);
+    v3 = make_float2(b.x - d.x, b.y - d.y);
+}
+
+__device__ __forceinline__ void dft5_reg(float2 *x, float sg) {
+    constexpr float c1 = 0.30901699437494742f, c2 = -0.80901699437494742f;  // cos 2pi/5, cos 4pi/5
+    constexpr float s1 = 0.95105651629515357f, s2 = 0.58778525229247313f;   // sin 2pi/5, sin 4pi/5
+    const float2 t1 = make_float2(x[1].x + x[4].x, x[1].y + x[4].y);
+    const float2 t2 = make_float2(x[2].x + x[3].x, x[2].y + x[3].y);
+    const float2 t3 = make_float2(x[1].x - x[4].x, x[1].y - x[4].y);
+    const float2 t4 = make_float2(x[2].x - x[3].x, x[2].y - x[3].y);
+    const float2 a1 = make_float2(x[0].x + c1 * t1.x + c2 * t2.x, x[0].y + c1 * t1.y + c2 * t2.y);
+    const float2 a2 = make_float2(x[0].x + c2 * t1.x + c1 * t2.x, x[0].y + c2 * t1.y + c1 * t2.y);
+    const float2 b1 = make_float2(s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y);
+    const float2 b2 = make_float2(s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y);
+    const float2 m1 = make_float2(sg * b1.y, -sg * b1.x);  // -i sg b1
+    const float2 m2 = make_float2(sg * b2.y, -sg * b2.x);
+    x[0] = make_float2(x[0].x + t1.x + t2.x, x[0].y + t1.y + t2.y);
+    x[1] = make_float2(a1.x + m1.x, a1.y + m1.y);
+    x[4] = make_float2(a1.x - m1.x, a1.y - m1.y);
+    x[2] = make_float2(a2.x + m2.x, a2.y + m2.y);
+    x[3] = make_float2(a2.x - m2.x, a2.y - m2.y);
+}
+
+// x[0..16) in natural order -> X[0..16) in natural order
+__device__ __forceinline__ void dft16_reg(float2 *x, float sg) {
+    // cos and sin of 2 pi k / 16, k = 0 .. 9 (the twiddle exponents b k4 <= 9)
+    constexpr float C[10] = {1.f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508978f, 0.f,
+                             -0.38268343236508978f, -0.70710678118654752f, -0.92387953251128674f, -1.f,
+                             -0.92387953251128674f};
+    constexpr float S[10] = {0.f, 0.38268343236508978f, 0.70710678118654752f, 0.92387953251128674f, 1.f,
+                             0.92387953251128674f, 0.70710678118654752f, 0.38268343236508978f, 0.f,
+                             -0.38268343236508978f};
+    // columns b: 4-point DFTs of x[b], x[4 + b], x[8 + b], x[12 + b] (index a), then W16^(b k4)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        dft4_reg(x[b], x[4 + b], x[8 + b], x[12 + b], sg);
+#pragma unroll
+        for (int k4 = 1; k4 < 4; ++k4) {
+            if (b == 0) continue;
+            const float wr = C[b * k4], wi = -sg * S[b * k4];
+            const float2 v = x[4 * k4 + b];
+            x[4 * k4 + b] = make_float2(v.x * wr - v.y * wi, v.x * wi + v.y * wr);
+        }
+    }
+    // rows k4: 4-point DFTs over b; X[k4 + 4 kb] from row k4's output kb
+    float2 y[16];
+#pragma unroll
+    for (int k4 = 0; k4 < 4; ++k4) {
+        float2 v0 = x[4 * k4], v1 = x[4 * k4 + 1], v2 = x[4 * k4 + 2], v3 = x[4 * k4 + 3];
+        dft4_reg(v0, v1, v2, v3, sg);
+        y[k4] = v0;
+        y[k4 + 4] = v1;
+        y[k4 + 8] = v2;
+        y[k4 + 12] = v3;
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) x[k] = y[k];
+}
+
+// 80-point transforms of nl lines (layout as in fft_stage), a -> b -> a; returns a.
+__device__ float2 *fft80_lines(float2 *a, float2 *b, int nl, int lstride, int st, const float2 *W, bool inv) {
+    const float sg = inv ? -1.f : 1.f;
+    const unsigned m_nl = div_magic(nl);
+    for (int task = threadIdx.x; task < nl * 16; task += blockDim.x) {  // phase 1: (line, p)
+        const int p = (int)fast_div(task, m_nl), l = task - p * nl;
+        const float2 *al = a + l * lstride;
+        float2 x[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) x[q] = al[(p + 16 * q) * st];
+        dft5_reg(x, sg);
+        float2 *bl = b + l * lstride;
+        bl[p * st] = x[0];
+#pragma unroll
+        for (int k5 = 1; k5 < 5; ++k5) {
+            float2 w = W[p * k5];
+            w.y *= sg;
+            bl[(16 * k5 + p) * st] = cmul(x[k5], w);
+        }
+    }
+    __syncthreads();
+    for (int task = threadIdx.x; task < nl * 5; task += blockDim.x) {  // phase 2: (line, k5)
+        const int k5 = (int)fast_div(task, m_nl), l = task - k5 * nl;
+        const float2 *bl = b + l * lstride + 16 * k5 * st;
+        float2 x[16];
+#pragma unroll
+        for (int p = 0; p < 16; ++p) x[p] = bl[p * st];
+        dft16_reg(x, sg);
+        float2 *al = a + l * lstride;
+#pragma unroll
+        for (int k16 = 0; k16 < 16; ++k16) al[(k5 + 5 * k16) * st] = x[k16];
+    }
+    __syncthreads();
+    return a;
+}
+
 // Stockham FFT of nl lines (see fft_stage for the layout) by the whole CTA;
 // the inverse uses conjugate twiddles and is unnormalised.  Returns the buffer
 // that holds the result (a or b, by the number of stages).  Every thread of
 // the CTA must call it; it ends with a barrier.
 __device__ float2 *fft_lines(float2 *a, float2 *b, const FftAxis &ax, int nl, int lstride, int st, const float2 *W,
                              bool inv) {
+    if (ax.n == 80) return fft80_lines(a, b, nl, lstride, st, W, inv);
     const float sg = inv ? -1.f : 1.f;
     const bool lines_fast = st != 1;
     int Ns = 1;
@@ -170,8 +287,9 @@ __global__ void __launch_bounds__(256) fft_plane_fwd_kernel(const FftGeom G, con
         p1 = src32 + (long long)ij.y * G.N + x3 * G.n12;
     }
     load_twiddles(G.tw, Ws);
+    const unsigned m_n1 = div_magic(G.n1);  // plane index e < 2^14: multiply-high division by n1
     for (int e = threadIdx.x; e < G.n12; e += blockDim.x) {
-        const int x1 = e % G.n1, x2 = e / G.n1;
+        const int x2 = (int)fast_div(e, m_n1), x1 = e - x2 * G.n1;
         A[x2 * ld + x1] = make_float2(p1 ? __ldg(p0 + e) * __ldg(p1 + e) : __ldg(p0 + e), 0.f);
     }
     __syncthreads();
@@ -179,7 +297,10 @@ __global__ void __launch_bounds__(256) fft_plane_fwd_kernel(const FftGeom G, con
     float2 *O1 = (R1 == A) ? B : A;
     const float2 *R2 = fft_lines(R1, O1, G.ax[1], G.n1, 1, ld, Ws + 128, false);  // columns: along x2
     float2 *dst = C + item * G.N + x3 * G.n12;
-    for (int e = threadIdx.x; e < G.n12; e += blockDim.x) dst[e] = R2[(e / G.n1) * ld + e % G.n1];
+    for (int e = threadIdx.x; e < G.n12; e += blockDim.x) {
+        const int x2 = (int)fast_div(e, m_n1);
+        dst[e] = R2[x2 * ld + e - x2 * G.n1];
+    }
 }
 
 // Pass B: kFftLine lines along x3 (plane positions blockIdx.x * kFftLine + l) of
@@ -253,7 +374,11 @@ __global__ void __launch_bounds__(256) fft_plane_inv_kernel(const FftGeom G, con
     const long long item = blockIdx.y;
     const float2 *src = C + item * G.N + x3 * G.n12;
     load_twiddles(G.tw, Ws);
-    for (int e = threadIdx.x; e < G.n12; e += blockDim.x) A[(e / G.n1) * ld + e % G.n1] = src[e];
+    const unsigned m_n1 = div_magic(G.n1);  // plane index e < 2^14: multiply-high division by n1
+    for (int e = threadIdx.x; e < G.n12; e += blockDim.x) {
+        const int x2 = (int)fast_div(e, m_n1);
+        A[x2 * ld + e - x2 * G.n1] = src[e];
+    }
     __syncthreads();
     float2 *R1 = fft_lines(A, B, G.ax[1], G.n1, 1, ld, Ws + 128, true);  // columns: along x2
     float2 *O1 = (R1 == A) ? B : A;
@@ -261,7 +386,8 @@ __global__ void __launch_bounds__(256) fft_plane_inv_kernel(const FftGeom G, con
     const float inv_n = 1.f / (float)G.N;
     const long long base = item * G.N + x3 * G.n12;
     for (int e = threadIdx.x; e < G.n12; e += blockDim.x) {
-        const float v = R2[(e / G.n1) * ld + e % G.n1].x * inv_n;
+        const int x2 = (int)fast_div(e, m_n1);
+        const float v = R2[x2 * ld + e - x2 * G.n1].x * inv_n;
         if (out64)
             out64[base + e] = (double)v;
         else
@@ -320,8 +446,8 @@ size_t line_smem(const kx_plan *p) { return sizeof(float2) * 2 * (size_t)p->n[2]
 
 bool fft_supported(const int *n, const int *bc) {
     FftAxis ax;
-    for (int a = 0; a < 3; ++a)
-        if (bc[a] != KX_PERIODIC || !factor_235(n[a], ax)) return false;
+    for (int a = 0; a < 3; ++a)  // the twiddle tables hold 128 entries per axis
+        if (bc[a] != KX_PERIODIC || n[a] > 128 || !factor_235(n[a], ax)) return false;
     return sizeof(float2) * 2 * (size_t)n[1] * (n[0] + 1) <= 200 * 1024;
 }
 

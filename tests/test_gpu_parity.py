@@ -410,7 +410,8 @@ def test_multipole_full_size_row(kx):
 # --------------------------------------------------------------------------
 # FFT variant for fully periodic grids (KX_FFT32)
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("n", [(20, 24, 30), (16, 15, 18), (9, 10, 12)])
+# (axes of 80 points take the register four-step path, 16 x 5, on each axis in turn)
+@pytest.mark.parametrize("n", [(20, 24, 30), (16, 15, 18), (9, 10, 12), (80, 9, 10), (12, 80, 9), (10, 12, 80)])
 def test_fft_apply_fL_matches_oracle(kx, n):
     h, bc = (0.45, 0.5, 0.4), (P, P, P)
     op = oracle.Plan(n, h, bc, S)
@@ -443,6 +444,9 @@ def test_fft_rejects_unsupported_grids(kx):
     assert ei.value.code == kx.KX_ERR_UNSUPPORTED
     with pytest.raises(kx.KxError) as ei:
         kx.Plan((14, 16, 16), (0.5,) * 3, (P, P, P), S, precision=kx.KX_FFT32)  # 14 = 2 x 7
+    assert ei.value.code == kx.KX_ERR_UNSUPPORTED
+    with pytest.raises(kx.KxError) as ei:
+        kx.Plan((8, 8, 160), (0.5,) * 3, (P, P, P), S, precision=kx.KX_FFT32)  # 160 > 128 points
     assert ei.value.code == kx.KX_ERR_UNSUPPORTED
     plan = kx.Plan((16, 16, 16), (0.5,) * 3, (P, P, P), S, precision=kx.KX_FFT32)
     b = dev(workloads.random_field(plan.N, 1, 3).T)

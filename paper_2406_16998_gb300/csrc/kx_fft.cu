@@ -20,7 +20,8 @@
 namespace kx {
 namespace {
 
-constexpr int kFftLine = 64;  // lines per CTA in pass B
+constexpr int kFftLine = 32;  // lines per CTA in pass B (40 KB of shared memory at n3 = 80: 5 CTAs per SM)
+constexpr int kFftPlaneThreads = 512;  // passes A and C: two planes (2 x 104 KB at 80^2) and 32 warps per SM
 
 struct FftAxis {
     int n, nr;
@@ -269,7 +270,7 @@ __device__ __forceinline__ void load_twiddles(const float2 *__restrict__ tw, flo
 }
 
 // Pass A: x3 plane blockIdx.x of item blockIdx.y; source psi_i psi_j (pairs) or src32.
-__global__ void __launch_bounds__(256) fft_plane_fwd_kernel(const FftGeom G, const int2 *__restrict__ pairs,
+__global__ void __launch_bounds__(kFftPlaneThreads) fft_plane_fwd_kernel(const FftGeom G, const int2 *__restrict__ pairs,
                                                             const float *__restrict__ src32, int rhs,
                                                             float2 *__restrict__ C) {
     extern __shared__ float2 fsm[];
@@ -288,9 +289,21 @@ __global__ void __launch_bounds__(256) fft_plane_fwd_kernel(const FftGeom G, con
     }
     load_twiddles(G.tw, Ws);
     const unsigned m_n1 = div_magic(G.n1);  // plane index e < 2^14: multiply-high division by n1
-    for (int e = threadIdx.x; e < G.n12; e += blockDim.x) {
-        const int x2 = (int)fast_div(e, m_n1), x1 = e - x2 * G.n1;
-        A[x2 * ld + x1] = make_float2(p1 ? __ldg(p0 + e) * __ldg(p1 + e) : __ldg(p0 + e), 0.f);
+    // four loads in flight per thread before their values are stored
+    for (int e0 = threadIdx.x; e0 < G.n12; e0 += 4 * blockDim.x) {
+        float v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = e0 + u * blockDim.x;
+            v[u] = e < G.n12 ? (p1 ? __ldg(p0 + e) * __ldg(p1 + e) : __ldg(p0 + e)) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e >= G.n12) break;
+            const int x2 = (int)fast_div(e, m_n1), x1 = e - x2 * G.n1;
+            A[x2 * ld + x1] = make_float2(v[u], 0.f);
+        }
     }
     __syncthreads();
     float2 *R1 = fft_lines(A, B, G.ax[0], G.n2, ld, 1, Ws, false);  // rows: along x1
@@ -319,14 +332,24 @@ __global__ void __launch_bounds__(256) fft_axis3_kernel(const FftGeom G, float2 
     const long long p0 = (long long)blockIdx.x * kFftLine;
     float2 *col = C + item * G.N + p0;
     load_twiddles(G.tw, Ws);
-    for (int e = tid; e < G.n3 * kFftLine; e += blockDim.x) {  // e = x3 * kFftLine + l
-        const int x3 = e / kFftLine, l = e % kFftLine;
-        A[e] = (p0 + l < G.n12) ? col[x3 * G.n12 + l] : make_float2(0.f, 0.f);
+    for (int e0 = tid; e0 < G.n3 * kFftLine; e0 += 4 * blockDim.x) {  // e = x3 * kFftLine + l, four in flight
+        float2 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = e0 + u * blockDim.x;
+            const int x3 = e / kFftLine, l = e % kFftLine;
+            v[u] = (e < G.n3 * kFftLine && p0 + l < G.n12) ? col[x3 * G.n12 + l] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e < G.n3 * kFftLine) A[e] = v[u];
+        }
     }
     __syncthreads();
     float2 *Rr = fft_lines(A, B, G.ax[2], kFftLine, 1, kFftLine, Ws + 256, false);
     float2 *Or = (Rr == A) ? B : A;
-    float ef = 0.f;  // at most n3 * kFftLine / blockDim = 32 terms per thread
+    float ef = 0.f;  // at most n3 * kFftLine / blockDim = 16 terms per thread
     for (int k = tid; k < G.n3 * kFftLine; k += blockDim.x) {
         const int k3 = k / kFftLine, l = k % kFftLine;
         const float f = (p0 + l < G.n12) ? __ldg(ftab + k3 * G.n12 + p0 + l) : 0.f;
@@ -364,7 +387,7 @@ __global__ void __launch_bounds__(256) fft_axis3_kernel(const FftGeom G, float2 
 
 // Pass C: inverse 2D transform of x3 plane blockIdx.x of item blockIdx.y; real part / N
 // into out32 (fp32) or out64 (fp64, right-hand-side mode).
-__global__ void __launch_bounds__(256) fft_plane_inv_kernel(const FftGeom G, const float2 *__restrict__ C,
+__global__ void __launch_bounds__(kFftPlaneThreads) fft_plane_inv_kernel(const FftGeom G, const float2 *__restrict__ C,
                                                             float *__restrict__ out32, double *__restrict__ out64) {
     extern __shared__ float2 fsm[];
     __shared__ float2 Ws[3 * 128];
@@ -375,9 +398,20 @@ __global__ void __launch_bounds__(256) fft_plane_inv_kernel(const FftGeom G, con
     const float2 *src = C + item * G.N + x3 * G.n12;
     load_twiddles(G.tw, Ws);
     const unsigned m_n1 = div_magic(G.n1);  // plane index e < 2^14: multiply-high division by n1
-    for (int e = threadIdx.x; e < G.n12; e += blockDim.x) {
-        const int x2 = (int)fast_div(e, m_n1);
-        A[x2 * ld + e - x2 * G.n1] = src[e];
+    for (int e0 = threadIdx.x; e0 < G.n12; e0 += 4 * blockDim.x) {  // four loads in flight per thread
+        float2 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = e0 + u * blockDim.x;
+            v[u] = e < G.n12 ? src[e] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e >= G.n12) break;
+            const int x2 = (int)fast_div(e, m_n1);
+            A[x2 * ld + e - x2 * G.n1] = v[u];
+        }
     }
     __syncthreads();
     float2 *R1 = fft_lines(A, B, G.ax[1], G.n1, 1, ld, Ws + 128, true);  // columns: along x2
@@ -515,7 +549,7 @@ int fft_passes(kx_plan *p, long R, const int2 *pairs, const float *src32, int rh
     int rc;
     const dim3 gp((unsigned)p->n[2], (unsigned)R);
     if ((rc = prof_begin(p, PK_FFT, s))) return rc;
-    fft_plane_fwd_kernel<<<gp, 256, ps, s>>>(G, pairs, src32, rhs, C);
+    fft_plane_fwd_kernel<<<gp, kFftPlaneThreads, ps, s>>>(G, pairs, src32, rhs, C);
     KX_LAUNCH_CHECK("fft_plane_fwd_kernel launch");
     const unsigned groups = (unsigned)((G.n12 + kFftLine - 1) / kFftLine);
     double *e_part = (ex != nullptr && !rhs) ? partial : nullptr;
@@ -527,7 +561,7 @@ int fft_passes(kx_plan *p, long R, const int2 *pairs, const float *src32, int rh
         KX_LAUNCH_CHECK("fft_energy_reduce_kernel launch");
     }
     if (!energy_only) {
-        fft_plane_inv_kernel<<<gp, 256, ps, s>>>(G, C, out32, out64);
+        fft_plane_inv_kernel<<<gp, kFftPlaneThreads, ps, s>>>(G, C, out32, out64);
         KX_LAUNCH_CHECK("fft_plane_inv_kernel launch");
     }
     return prof_end(p, s);

@@ -9,6 +9,8 @@
 //   B  per line along x3: transform, scale by f (and sum f |Y|^2 for the energy
 //      by Parseval), inverse transform
 //   C  per x3 plane: inverse 2D transform, real part / N.
+// The sources are real, so only the spectrum columns k1 <= n1 / 2 are kept (the
+// rest are conjugates), which halves pass B and the x2 transforms.
 // Each batch of line transforms is a mixed-radix (4, 2, 3, 5) Stockham FFT whose
 // stages are spread over the CTA's threads (lines x butterflies); lines of 80
 // points instead take a four-step transform (16 x 5) held in registers.
@@ -31,7 +33,8 @@ struct FftAxis {
 struct FftGeom {
     FftAxis ax[3];
     int n1, n2, n3;
-    long long N, n12;
+    int h1;              // n1 / 2 + 1: the spectrum columns k1 kept (the sources are real)
+    long long N, n12, nh;  // nh = h1 n2 spectrum points per x3 plane
     const float2 *tw;  // per axis 128 entries: exp(-2 pi i t / n_a), t < n_a
 };
 
@@ -308,11 +311,14 @@ __global__ void __launch_bounds__(kFftPlaneThreads) fft_plane_fwd_kernel(const F
     __syncthreads();
     float2 *R1 = fft_lines(A, B, G.ax[0], G.n2, ld, 1, Ws, false);  // rows: along x1
     float2 *O1 = (R1 == A) ? B : A;
-    const float2 *R2 = fft_lines(R1, O1, G.ax[1], G.n1, 1, ld, Ws + 128, false);  // columns: along x2
-    float2 *dst = C + item * G.N + x3 * G.n12;
-    for (int e = threadIdx.x; e < G.n12; e += blockDim.x) {
-        const int x2 = (int)fast_div(e, m_n1);
-        dst[e] = R2[x2 * ld + e - x2 * G.n1];
+    // columns along x2 for k1 < h1 only: the source is real, so its spectrum is
+    // Hermitian and the columns k1 > n1 / 2 are conjugates of kept ones
+    const float2 *R2 = fft_lines(R1, O1, G.ax[1], G.h1, 1, ld, Ws + 128, false);
+    float2 *dst = C + item * G.N + x3 * G.nh;  // [k2][k1 < h1]
+    const unsigned m_h1 = div_magic(G.h1);
+    for (int e = threadIdx.x; e < G.nh; e += blockDim.x) {
+        const int k2 = (int)fast_div(e, m_h1);
+        dst[e] = R2[k2 * ld + e - k2 * G.h1];
     }
 }
 
@@ -338,7 +344,7 @@ __global__ void __launch_bounds__(256) fft_axis3_kernel(const FftGeom G, float2 
         for (int u = 0; u < 4; ++u) {
             const int e = e0 + u * blockDim.x;
             const int x3 = e / kFftLine, l = e % kFftLine;
-            v[u] = (e < G.n3 * kFftLine && p0 + l < G.n12) ? col[x3 * G.n12 + l] : make_float2(0.f, 0.f);
+            v[u] = (e < G.n3 * kFftLine && p0 + l < G.nh) ? col[x3 * G.nh + l] : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -349,12 +355,21 @@ __global__ void __launch_bounds__(256) fft_axis3_kernel(const FftGeom G, float2 
     __syncthreads();
     float2 *Rr = fft_lines(A, B, G.ax[2], kFftLine, 1, kFftLine, Ws + 256, false);
     float2 *Or = (Rr == A) ? B : A;
+    // energy by Parseval over the half spectrum: the columns 0 < k1 < n1 / 2 stand
+    // for themselves and their conjugates (weight 2), k1 = 0 and k1 = n1 / 2 once
     float ef = 0.f;  // at most n3 * kFftLine / blockDim = 16 terms per thread
+    const unsigned m_h1 = div_magic(G.h1);
     for (int k = tid; k < G.n3 * kFftLine; k += blockDim.x) {
         const int k3 = k / kFftLine, l = k % kFftLine;
-        const float f = (p0 + l < G.n12) ? __ldg(ftab + k3 * G.n12 + p0 + l) : 0.f;
+        const int p = (int)p0 + l;  // < nh < 2^14
+        float f = 0.f, wk = 0.f;
+        if (p < G.nh) {
+            const int k2 = (int)fast_div(p, m_h1), k1 = p - k2 * G.h1;
+            f = __ldg(ftab + k3 * G.n12 + (long long)k2 * G.n1 + k1);
+            wk = (k1 == 0 || 2 * k1 == G.n1) ? 1.f : 2.f;
+        }
         const float2 y = Rr[k];
-        ef = fmaf(f, y.x * y.x + y.y * y.y, ef);
+        ef = fmaf(f * wk, y.x * y.x + y.y * y.y, ef);
         Rr[k] = make_float2(y.x * f, y.y * f);
     }
     double e = (double)ef;
@@ -363,7 +378,7 @@ __global__ void __launch_bounds__(256) fft_axis3_kernel(const FftGeom G, float2 
         const float2 *R2 = fft_lines(Rr, Or, G.ax[2], kFftLine, 1, kFftLine, Ws + 256, true);
         for (int k = tid; k < G.n3 * kFftLine; k += blockDim.x) {
             const int x3 = k / kFftLine, l = k % kFftLine;
-            if (p0 + l < G.n12) col[x3 * G.n12 + l] = R2[k];
+            if (p0 + l < G.nh) col[x3 * G.nh + l] = R2[k];
         }
     }
     if (e_part != nullptr) {
@@ -395,26 +410,39 @@ __global__ void __launch_bounds__(kFftPlaneThreads) fft_plane_inv_kernel(const F
     float2 *A = fsm, *B = fsm + (size_t)G.n2 * ld;
     const int x3 = blockIdx.x;
     const long long item = blockIdx.y;
-    const float2 *src = C + item * G.N + x3 * G.n12;
+    const float2 *src = C + item * G.N + x3 * G.nh;  // [k2][k1 < h1]
     load_twiddles(G.tw, Ws);
-    const unsigned m_n1 = div_magic(G.n1);  // plane index e < 2^14: multiply-high division by n1
-    for (int e0 = threadIdx.x; e0 < G.n12; e0 += 4 * blockDim.x) {  // four loads in flight per thread
+    const unsigned m_n1 = div_magic(G.n1);  // plane indices < 2^14: multiply-high division
+    const unsigned m_h1 = div_magic(G.h1);
+    for (int e0 = threadIdx.x; e0 < G.nh; e0 += 4 * blockDim.x) {  // four loads in flight per thread
         float2 v[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int e = e0 + u * blockDim.x;
-            v[u] = e < G.n12 ? src[e] : make_float2(0.f, 0.f);
+            v[u] = e < G.nh ? src[e] : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int e = e0 + u * blockDim.x;
-            if (e >= G.n12) break;
-            const int x2 = (int)fast_div(e, m_n1);
-            A[x2 * ld + e - x2 * G.n1] = v[u];
+            if (e >= G.nh) break;
+            const int k2 = (int)fast_div(e, m_h1);
+            A[k2 * ld + e - k2 * G.h1] = v[u];
         }
     }
     __syncthreads();
-    float2 *R1 = fft_lines(A, B, G.ax[1], G.n1, 1, ld, Ws + 128, true);  // columns: along x2
+    float2 *R1 = fft_lines(A, B, G.ax[1], G.h1, 1, ld, Ws + 128, true);  // kept columns: along x2
+    // the other columns of each row by symmetry: the inverse along x3 and x2 of a
+    // Hermitian spectrum leaves Z(-k1) = conj Z(k1) in every row x2
+    const int nm = G.n1 - G.h1;
+    if (nm > 0) {
+        const unsigned m_nm = div_magic(nm);
+        for (int e = threadIdx.x; e < G.n2 * nm; e += blockDim.x) {
+            const int x2 = (int)fast_div(e, m_nm), k1 = G.h1 + e - x2 * nm;
+            const float2 z = R1[x2 * ld + G.n1 - k1];
+            R1[x2 * ld + k1] = make_float2(z.x, -z.y);
+        }
+        __syncthreads();
+    }
     float2 *O1 = (R1 == A) ? B : A;
     const float2 *R2 = fft_lines(R1, O1, G.ax[0], G.n2, ld, 1, Ws, true);  // rows: along x1
     const float inv_n = 1.f / (float)G.N;
@@ -469,6 +497,8 @@ FftGeom geom(const kx_plan *p) {
     G.n3 = p->n[2];
     G.N = (long long)p->N;
     G.n12 = (long long)p->n[0] * p->n[1];
+    G.h1 = p->n[0] / 2 + 1;
+    G.nh = (long long)G.h1 * p->n[1];
     G.tw = reinterpret_cast<const float2 *>(p->d_fft_tw);
     return G;
 }
@@ -535,7 +565,7 @@ int fft_setup(kx_plan *p) {
 }
 
 size_t fft_partial_count(const kx_plan *p, long chunk) {
-    const long long groups = ((long long)p->n[0] * p->n[1] + kFftLine - 1) / kFftLine;
+    const long long groups = ((long long)(p->n[0] / 2 + 1) * p->n[1] + kFftLine - 1) / kFftLine;
     return (size_t)std::max<long long>(4096, groups * chunk);
 }
 
@@ -551,7 +581,7 @@ int fft_passes(kx_plan *p, long R, const int2 *pairs, const float *src32, int rh
     if ((rc = prof_begin(p, PK_FFT, s))) return rc;
     fft_plane_fwd_kernel<<<gp, kFftPlaneThreads, ps, s>>>(G, pairs, src32, rhs, C);
     KX_LAUNCH_CHECK("fft_plane_fwd_kernel launch");
-    const unsigned groups = (unsigned)((G.n12 + kFftLine - 1) / kFftLine);
+    const unsigned groups = (unsigned)((G.nh + kFftLine - 1) / kFftLine);  // pass B: half-spectrum positions
     double *e_part = (ex != nullptr && !rhs) ? partial : nullptr;
     fft_axis3_kernel<<<dim3(groups, (unsigned)R), 256, ls, s>>>(G, C, p->d_fft_f, pairs, occ, rhs,
                                                                     energy_only ? 1 : 0, e_part);

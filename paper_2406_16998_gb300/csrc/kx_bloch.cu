@@ -1728,6 +1728,80 @@ __global__ void __launch_bounds__(256, 4) bloch_accum_kernel(const typename Cx<T
     }
 }
 
+// The float32 forms of bloch_accum_kernel (forward sums, REV false) and
+// bloch_accum_rev_kernel (reversed, REV true) with two neighbouring points per
+// thread: 16-byte loads, so that each thread keeps 128 bytes of its four
+// items' loads in flight (N even).  Same terms in the same order per point.
+template <bool REV>
+__global__ void __launch_bounds__(256, 3) bloch_accum2_kernel(const float2 *__restrict__ X, long long r0, long long r1,
+                                                              int n_orb, const float2 *__restrict__ Y,
+                                                              const double *__restrict__ occ, double w,
+                                                              double2 *__restrict__ out, long long N) {
+    const long long v_lo = r0 / n_orb, v_hi = (r1 - 1) / n_orb;
+    const long long N2 = N / 2;
+    // forward: one thread per (vector v, point pair), Y = P, sum over m;
+    // reversed: one thread per (band m, point pair), Y = F, sum over v
+    const long long rows = REV ? (long long)n_orb : v_hi - v_lo + 1;
+    const long long total = rows * N2;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long rl = e / N2, x = 2 * (e - rl * N2);
+        long long a, b;  // the summed index runs over [a, b]
+        long long orow;  // output row
+        if (REV) {
+            const long long m = rl;
+            if (r1 - 1 - m < 0) continue;
+            a = max(v_lo, (r0 - m + n_orb - 1) / n_orb);
+            b = min(v_hi, (r1 - 1 - m) / n_orb);
+            if (a > b) continue;
+            orow = m;
+        } else {
+            const long long v = v_lo + rl;
+            a = max(0LL, r0 - v * n_orb);
+            b = min((long long)n_orb, r1 - v * n_orb) - 1;
+            orow = v;
+        }
+        // item of summed index t: forward r = orow n_orb + t, reversed r = t n_orb + orow
+        auto item = [&](long long t) { return REV ? t * n_orb + orow - r0 : orow * n_orb + t - r0; };
+        float sr0 = 0.f, si0 = 0.f, sr1 = 0.f, si1 = 0.f;
+        auto term = [&](float c, float4 y, float4 xx) {
+            if (REV) {  // Y conj(X)
+                sr0 = fmaf(c, y.x * xx.x + y.y * xx.y, sr0);
+                si0 = fmaf(c, y.y * xx.x - y.x * xx.y, si0);
+                sr1 = fmaf(c, y.z * xx.z + y.w * xx.w, sr1);
+                si1 = fmaf(c, y.w * xx.z - y.z * xx.w, si1);
+            } else {  // Y X
+                sr0 = fmaf(c, y.x * xx.x - y.y * xx.y, sr0);
+                si0 = fmaf(c, y.x * xx.y + y.y * xx.x, si0);
+                sr1 = fmaf(c, y.z * xx.z - y.w * xx.w, sr1);
+                si1 = fmaf(c, y.z * xx.w + y.w * xx.z, si1);
+            }
+        };
+        long long t = a;
+        for (; t + 4 <= b + 1; t += 4) {
+            float4 y[4], xx[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                y[u] = *reinterpret_cast<const float4 *>(Y + (t + u) * N + x);
+                xx[u] = *reinterpret_cast<const float4 *>(X + item(t + u) * N + x);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) term((float)(w * (occ ? occ[t + u] : 1.0)), y[u], xx[u]);
+        }
+        for (; t <= b; ++t)
+            term((float)(w * (occ ? occ[t] : 1.0)), *reinterpret_cast<const float4 *>(Y + t * N + x),
+                 *reinterpret_cast<const float4 *>(X + item(t) * N + x));
+        double2 *o = out + orow * N + x;
+        double2 o0 = o[0], o1 = o[1];
+        o0.x -= f32_to_f64(sr0);
+        o0.y -= f32_to_f64(si0);
+        o1.x -= f32_to_f64(sr1);
+        o1.y -= f32_to_f64(si1);
+        o[0] = o0;
+        o[1] = o1;
+    }
+}
+
 // partial[k * nb + b] = w_k sum_n g_kn sum_x Re(conj(psi_kn[x]) vx_kn[x]) over a
 // grid-stride share (block b of nb).
 constexpr int kEThreads = 256;
@@ -2328,14 +2402,28 @@ int bloch_sweep(kx_plan *p, int n_kpt, const double *theta, const double *wk, in
             }
             if ((rc = prof_begin(p, PK_BLOCH_OTHER, s))) return rc;
             const long long nv = (r1 - 1) / n_orb - r0 / n_orb + 1;
-            const int ab = (int)std::min<long long>((nv * N + 255) / 256, 8LL * p->num_sms);
-            bloch_accum_kernel<T><<<ab, 256, 0, s>>>(B, r0, r1, n_orb, Pq, occ_q, wk[q],
-                                                     reinterpret_cast<double2 *>(out_k), N);
+            // float32 sums with an even N: two points per thread (16-byte loads)
+            const bool pairs2 = sizeof(T) == 4 && N % 2 == 0;
+            const long long per = pairs2 ? 2 : 1;
+            const int ab = (int)std::min<long long>((nv * N / per + 255) / 256, 8LL * p->num_sms);
+            if constexpr (sizeof(T) == 4) {
+                if (pairs2)
+                    bloch_accum2_kernel<false><<<ab, 256, 0, s>>>(B, r0, r1, n_orb, Pq, occ_q, wk[q],
+                                                                  reinterpret_cast<double2 *>(out_k), N);
+            }
+            if (!pairs2)
+                bloch_accum_kernel<T><<<ab, 256, 0, s>>>(B, r0, r1, n_orb, Pq, occ_q, wk[q],
+                                                         reinterpret_cast<double2 *>(out_k), N);
             KX_LAUNCH_CHECK("bloch_accum_kernel launch");
             if (reverse) {
-                const int rb = (int)std::min<long long>((n_orb * N + 255) / 256, 8LL * p->num_sms);
+                const int rb = (int)std::min<long long>((n_orb * N / per + 255) / 256, 8LL * p->num_sms);
                 double2 *out_q = reinterpret_cast<double2 *>(out_all) + (size_t)q * n_orb * N;
-                bloch_accum_rev_kernel<T><<<rb, 256, 0, s>>>(B, r0, r1, n_orb, F, occ_k, wk[k], out_q, N);
+                if constexpr (sizeof(T) == 4) {
+                    if (pairs2)
+                        bloch_accum2_kernel<true><<<rb, 256, 0, s>>>(B, r0, r1, n_orb, F, occ_k, wk[k], out_q, N);
+                }
+                if (!pairs2)
+                    bloch_accum_rev_kernel<T><<<rb, 256, 0, s>>>(B, r0, r1, n_orb, F, occ_k, wk[k], out_q, N);
                 KX_LAUNCH_CHECK("bloch_accum_rev_kernel launch");
             }
             if ((rc = prof_end(p, s))) return rc;

@@ -11,7 +11,9 @@
 // axes keep the plan's real eigenvectors.  The forward transform contracts with
 // conj(Vk), the inverse with Vk.  The six complex mode products run on the
 // tensor cores (split fp16 products, float32 plans, axes of 32 or 64 points:
-// bloch_tc_kernel) or on the CUDA cores (float64 for KX_FP64 plans, float32 with
+// the pass kernels with per-item scales, bloch_pass_kernel and
+// bloch_pass0_kernel, when every axis qualifies, else bloch_tc_ws_kernel with
+// per-tile scales) or on the CUDA cores (float64 for KX_FP64 plans, float32 with
 // packed f32x2 FMAs otherwise: bloch_form_kernel, bloch_mode_pipe_kernel); the
 // pair density is formed inside the first product and f(Lambda) is applied
 // inside the third.  For Vx psi at every k-point the block of pairs (k, q),

@@ -850,12 +850,26 @@ def main():
         vx_pin = torch.empty_like(psi_pin).pin_memory()
         kx.kx_vx_apply_host(plan, psi_pin, out=vx_pin)
         k_e2e = max(3, min(args.steps, 10))
+        t_steps = []
         t0 = time.perf_counter()
         for _ in range(k_e2e):
+            ts = time.perf_counter()
             kx.kx_vx_apply_host(plan, psi_pin, out=vx_pin)
+            t_steps.append(1e3 * (time.perf_counter() - ts))
         dt = time.perf_counter() - t0
+        # the host link's rates in the same process (one pinned copy each way), beside the end-to-end number
+        c0, c1, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        c0.record(stream)
+        vx.copy_(psi_pin, non_blocking=True)
+        c1.record(stream)
+        vx_pin.copy_(vx, non_blocking=True)
+        c2.record(stream)
+        torch.cuda.synchronize()
+        nb = psi_pin.numel() * 8
         out["e2e"] = {"value": P * k_e2e / dt, "unit": UNIT, "h2d_bytes_per_step": psi_pin.numel() * 8,
-                      "d2h_bytes_per_step": vx_pin.numel() * 8 + 8, "ms_per_step": 1e3 * dt / k_e2e}
+                      "d2h_bytes_per_step": vx_pin.numel() * 8 + 8, "ms_per_step": 1e3 * dt / k_e2e,
+                      "ms_each": [round(t, 3) for t in t_steps],
+                      "link_gbs": {"h2d": nb / c0.elapsed_time(c1) / 1e6, "d2h": nb / c1.elapsed_time(c2) / 1e6}}
 
         # float64 GPU path on the same inputs: the speed-up denominator and the full-size error reference
         plan64 = kx.Plan.for_system(SYS, precision=kx.KX_FP64)

@@ -10,7 +10,8 @@
 //      by Parseval), inverse transform
 //   C  per x3 plane: inverse 2D transform, real part / N.
 // The sources are real, so only the spectrum columns k1 <= n1 / 2 are kept (the
-// rest are conjugates), which halves pass B and the x2 transforms.
+// rest are conjugates), which halves pass B and the x2 transforms, and two real
+// rows share one complex transform along x1.
 // Each batch of line transforms is a mixed-radix (4, 2, 3, 5) Stockham FFT whose
 // stages are spread over the CTA's threads (lines x butterflies); lines of 80
 // points instead take a four-step transform (16 x 5) held in registers.
@@ -305,15 +306,32 @@ __global__ void __launch_bounds__(kFftPlaneThreads) fft_plane_fwd_kernel(const F
             const int e = e0 + u * blockDim.x;
             if (e >= G.n12) break;
             const int x2 = (int)fast_div(e, m_n1), x1 = e - x2 * G.n1;
-            A[x2 * ld + x1] = make_float2(v[u], 0.f);
+            // rows 2j and 2j + 1 as the real and imaginary parts of packed row j
+            float *z = reinterpret_cast<float *>(A + (x2 >> 1) * ld + x1);
+            z[x2 & 1] = v[u];
+            if (x2 == G.n2 - 1 && (x2 & 1) == 0) z[1] = 0.f;  // an odd last row pairs with zeros
         }
     }
     __syncthreads();
-    float2 *R1 = fft_lines(A, B, G.ax[0], G.n2, ld, 1, Ws, false);  // rows: along x1
-    float2 *O1 = (R1 == A) ? B : A;
+    // rows along x1: one complex transform per two real rows, Z = DFT(a + i b),
+    // then A(k) = (Z(k) + conj Z(-k)) / 2 and B(k) = (Z(k) - conj Z(-k)) / 2i for
+    // the kept columns k1 < h1 into the other buffer's rows 2j and 2j + 1
+    const int n2p = (G.n2 + 1) / 2;
+    float2 *Z = fft_lines(A, B, G.ax[0], n2p, ld, 1, Ws, false);
+    float2 *R1 = (Z == A) ? B : A;
+    {
+        const unsigned m_h1 = div_magic(G.h1);
+        for (int e = threadIdx.x; e < n2p * G.h1; e += blockDim.x) {
+            const int j = (int)fast_div(e, m_h1), k = e - j * G.h1;
+            const float2 z = Z[j * ld + k], zc = Z[j * ld + (k == 0 ? 0 : G.n1 - k)];
+            R1[2 * j * ld + k] = make_float2(0.5f * (z.x + zc.x), 0.5f * (z.y - zc.y));
+            if (2 * j + 1 < G.n2) R1[(2 * j + 1) * ld + k] = make_float2(0.5f * (z.y + zc.y), -0.5f * (z.x - zc.x));
+        }
+    }
+    __syncthreads();
     // columns along x2 for k1 < h1 only: the source is real, so its spectrum is
     // Hermitian and the columns k1 > n1 / 2 are conjugates of kept ones
-    const float2 *R2 = fft_lines(R1, O1, G.ax[1], G.h1, 1, ld, Ws + 128, false);
+    const float2 *R2 = fft_lines(R1, Z, G.ax[1], G.h1, 1, ld, Ws + 128, false);
     float2 *dst = C + item * G.N + x3 * G.nh;  // [k2][k1 < h1]
     const unsigned m_h1 = div_magic(G.h1);
     for (int e = threadIdx.x; e < G.nh; e += blockDim.x) {
@@ -431,25 +449,33 @@ __global__ void __launch_bounds__(kFftPlaneThreads) fft_plane_inv_kernel(const F
     }
     __syncthreads();
     float2 *R1 = fft_lines(A, B, G.ax[1], G.h1, 1, ld, Ws + 128, true);  // kept columns: along x2
-    // the other columns of each row by symmetry: the inverse along x3 and x2 of a
-    // Hermitian spectrum leaves Z(-k1) = conj Z(k1) in every row x2
-    const int nm = G.n1 - G.h1;
-    if (nm > 0) {
-        const unsigned m_nm = div_magic(nm);
-        for (int e = threadIdx.x; e < G.n2 * nm; e += blockDim.x) {
-            const int x2 = (int)fast_div(e, m_nm), k1 = G.h1 + e - x2 * nm;
-            const float2 z = R1[x2 * ld + G.n1 - k1];
-            R1[x2 * ld + k1] = make_float2(z.x, -z.y);
+    float2 *Zp = (R1 == A) ? B : A;
+    // two rows per complex inverse along x1: packed row j holds Z(k) = A(k) + i B(k)
+    // for every k1, A and B the spectra of rows 2j and 2j + 1, whose columns
+    // k1 > n1 / 2 are the conjugates of kept ones (the inverse along x3 and x2 of a
+    // Hermitian spectrum leaves every row Hermitian in k1); the inverse of Z is
+    // then row 2j in its real part and row 2j + 1 in its imaginary part
+    const int n2p = (G.n2 + 1) / 2;
+    for (int e = threadIdx.x; e < n2p * G.n1; e += blockDim.x) {
+        const int j = (int)fast_div(e, m_n1), k = e - j * G.n1;
+        const bool kept = k < G.h1;
+        const int ks = kept ? k : G.n1 - k;
+        float2 a = R1[2 * j * ld + ks];
+        float2 b = (2 * j + 1 < G.n2) ? R1[(2 * j + 1) * ld + ks] : make_float2(0.f, 0.f);
+        if (!kept) {
+            a.y = -a.y;
+            b.y = -b.y;
         }
-        __syncthreads();
+        Zp[j * ld + k] = make_float2(a.x - b.y, a.y + b.x);
     }
-    float2 *O1 = (R1 == A) ? B : A;
-    const float2 *R2 = fft_lines(R1, O1, G.ax[0], G.n2, ld, 1, Ws, true);  // rows: along x1
+    __syncthreads();
+    const float2 *R2 = fft_lines(Zp, R1, G.ax[0], n2p, ld, 1, Ws, true);  // packed rows: along x1
     const float inv_n = 1.f / (float)G.N;
     const long long base = item * G.N + x3 * G.n12;
     for (int e = threadIdx.x; e < G.n12; e += blockDim.x) {
         const int x2 = (int)fast_div(e, m_n1);
-        const float v = R2[x2 * ld + e - x2 * G.n1].x * inv_n;
+        const float2 z = R2[(x2 >> 1) * ld + e - x2 * G.n1];
+        const float v = ((x2 & 1) ? z.y : z.x) * inv_n;
         if (out64)
             out64[base + e] = (double)v;
         else
